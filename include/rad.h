@@ -1,0 +1,231 @@
+/*
+ * librad — GB300 (sm_103a) hierarchical block low-rank cavity radiation.
+ *
+ * C ABI of the hot path of Baburin, Ballani, Peterson and Knezevic,
+ * "Hierarchical Block Low-rank Approximation of Cavity Radiation":
+ * view-factor entries (Eq. 10), cluster tree (§4.1, Algorithm 1), block tree
+ * with the admissibility condition (§4.2, Algorithm 2, Eq. 28), cross
+ * approximation of admissible blocks (§4.3, Eqs. 30-31), the block low-rank
+ * matrix-vector product (§5.2) and a GMRES solve of the reflection system
+ * (Eq. 11) that returns the facet flux (Eq. 12).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns an int status: RAD_OK (0) or one of the RAD_E* codes.
+ *   rad_last_error() returns a message for the calling thread's last failure.
+ *   No C++ exception crosses this interface.
+ * - Array arguments may be HOST or DEVICE pointers (the library asks the CUDA
+ *   runtime which one it was given).  Host arrays are copied to the device
+ *   inside the call; device arrays must be on the current device.  The caller
+ *   owns every array it passes; the library keeps no reference after return.
+ * - All arrays are indexed in the caller's facet order; the tree permutation
+ *   is internal.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *   ordered on it.  Calls that must size buffers from device results (tree
+ *   build, compression, solve) synchronise that stream before returning;
+ *   rad_hmatvec does not.
+ * - The library owns the rad_htree handle and every device buffer inside it
+ *   (rad_htree_free releases them).  A handle is used on the device that was
+ *   current when it was built.  Calls on one handle must not overlap.
+ * - Floating-point facet data is double precision.  Facets must be
+ *   non-degenerate (positive area) and finite, else RAD_EINVAL.
+ */
+#ifndef RAD_H
+#define RAD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RAD_OK        0
+#define RAD_EINVAL    1   /* bad argument or state                         */
+#define RAD_ENOMEM    2   /* a device allocation failed                    */
+#define RAD_ENOTCONV  3   /* GMRES did not reach the tolerance             */
+#define RAD_ECUDA     4   /* a CUDA runtime call failed                    */
+#define RAD_ELIMIT    5   /* a size limit of this library was exceeded     */
+
+/* storage / vector element types */
+#define RAD_F64   0
+#define RAD_F32   1
+#define RAD_BF16  2
+
+/* cross-approximation pivoting (§1: the paper uses full pivoting) */
+#define RAD_ACA_PARTIAL 0
+#define RAD_ACA_FULL    1
+
+typedef struct rad_htree rad_htree;
+
+/* §4.1-4.2.  leaf_size = n_min of Algorithm 1 (a cluster with at most
+ * leaf_size facets is a leaf, >= 1); eta_adm = c of Eq. (28), > 0. */
+typedef struct {
+    int32_t leaf_size;
+    int32_t reserved;
+    double  eta_adm;
+} rad_tree_params;
+
+/* §4.3.  tol = eps_rel of Eq. (31) (>= 0); max_rank caps the rank of every
+ * admissible block (<= 128; a block that would need more, or more than its
+ * storage break-even rank m n / (m + n), is stored dense instead);
+ * pivoting = RAD_ACA_PARTIAL or RAD_ACA_FULL; factor_dtype (RAD_F64, RAD_F32
+ * or RAD_BF16) is the storage type of the U, V factors and near_dtype
+ * (RAD_F64 or RAD_F32) that of the dense blocks.  near_dtype = RAD_F64
+ * requires factor_dtype = RAD_F64 (the FP64 path); the other combinations
+ * compute in FP32 with FP32 accumulation. */
+typedef struct {
+    double  tol;
+    int32_t max_rank;
+    int32_t pivoting;
+    int32_t factor_dtype;
+    int32_t near_dtype;
+} rad_aca_params;
+
+/* GMRES on C y = b, C = I - diag(1 - eps) F (Eq. 11).  Stops when every
+ * column's relative residual ||b - C y|| / ||b|| <= tol; restart = Krylov
+ * dimension per cycle (1..64); max_iter = total Arnoldi steps per column. */
+typedef struct {
+    double  tol;
+    int32_t restart;
+    int32_t max_iter;
+} rad_solve_params;
+
+typedef struct {
+    int32_t status;              /* RAD_OK or RAD_ENOTCONV                     */
+    int32_t iters;               /* Arnoldi steps taken (max over columns)     */
+    int32_t restarts;            /* restart cycles                             */
+    int32_t matvecs;             /* block matrix products applied             */
+    double  max_rel_residual;    /* max over columns of ||b - C y|| / ||b||,
+                                    recomputed with the stored operator       */
+} rad_solve_info;
+
+typedef struct {
+    int64_t n;                   /* facets                                     */
+    int32_t leaf_size;
+    int32_t n_nodes;             /* clusters in the tree                      */
+    int32_t n_leaf_clusters;
+    int32_t depth;               /* levels (root = level 0)                   */
+    int64_t n_blocks;            /* leaf blocks of the block tree             */
+    int64_t n_admissible;        /* admissible leaf blocks                    */
+    int32_t compressed;          /* 1 after rad_compress_aca                  */
+    int32_t factor_dtype;
+    int32_t near_dtype;
+    int32_t max_rank_used;       /* largest ACA rank stored                   */
+    int64_t n_dense_fallback;    /* admissible blocks stored dense            */
+    int64_t near_entries;        /* sum m n over dense blocks                 */
+    int64_t far_entries;         /* sum k (m + n) over low-rank blocks         */
+    int64_t sum_rank;            /* sum k over low-rank blocks                 */
+    int64_t aca_entries;         /* entries evaluated by ACA                   */
+    int64_t bytes_near;
+    int64_t bytes_far;
+} rad_htree_stats;
+
+/* -------------------------------------------------------------------------
+ * rad_build_htree — A1-A3: facet geometry (§3.1), cluster tree (Algorithm 1)
+ * and block tree (Algorithm 2 with Eq. 28), all on the GPU.
+ *   n      facets (>= 1, < 2^31)
+ *   verts  n x 3 x 3 doubles, row-major (facet, vertex, xyz), triangles wound
+ *          so that (v1 - v0) x (v2 - v0) points into the cavity
+ *   out    receives the new handle (NULL on failure)
+ * The tree, permutation and block partition are deterministic and identical
+ * bit for bit to Algorithms 1-2 evaluated in FP64 with the split rule:
+ * longest bounding-box axis of the centroids (ties: lowest axis), left child
+ * = the floor(n/2) facets first in (coordinate, facet index) order.
+ * ------------------------------------------------------------------------- */
+int rad_build_htree(int64_t n, const double* verts, const rad_tree_params* p,
+                    void* stream, rad_htree** out);
+
+/* Same as rad_build_htree from facet data (§3.1): centroids n x 3, unit
+ * normals n x 3 (pointing into the cavity), areas n (all row-major). */
+int rad_build_htree_facets(int64_t n, const double* centroid, const double* normal,
+                           const double* area, const rad_tree_params* p,
+                           void* stream, rad_htree** out);
+
+/* Test hook: wraps a caller's dense n x n view-factor matrix F (row-major,
+ * F[i*n + j] = F_ij, §3.2) as a single dense block stored in FP64, already
+ * "compressed".  Lets closed-form pins (e.g. Eq. 5) drive rad_solve_flux. */
+int rad_htree_from_dense(int64_t n, const double* F, void* stream, rad_htree** out);
+
+/* -------------------------------------------------------------------------
+ * rad_compress_aca — A4-A5: dense blocks get their entries (Eq. 10, 1-point
+ * centroid rule); admissible blocks are approximated by ACA (Eq. 30) until
+ * ||X - U V^T||_F <= tol ||X||_F (Eq. 31; estimated for partial pivoting,
+ * exact for full pivoting).  May be called again to recompress with other
+ * parameters.  Full pivoting holds every admissible block densely while it
+ * runs: RAD_ELIMIT if that exceeds 8 GiB.
+ * ------------------------------------------------------------------------- */
+int rad_compress_aca(rad_htree* h, const rad_aca_params* p, void* stream);
+
+/* -------------------------------------------------------------------------
+ * rad_hmatvec — A6: Y = F X (§5.2), F the stored block low-rank matrix.
+ *   dtype  RAD_F64 or RAD_F32: element type of x and y
+ *   x      column-major n x nrhs, column c at x + c*ldx (ldx >= n)
+ *   y      column-major n x nrhs, column c at y + c*ldy (ldy >= n)
+ *   nrhs   1 .. 4096
+ * Requires a compressed handle.  Device arrays: asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx,
+                void* y, int64_t ldy, int64_t nrhs, void* stream);
+
+/* -------------------------------------------------------------------------
+ * rad_solve_flux — A7-A8: for each of the m temperature fields T(:, c)
+ * (Kelvin), solves C y_c = eps o eta_c and C z = eps (Eq. 11,
+ * eta = T^4, Eq. 8) by batched GMRES in FP64 on the stored operator, then
+ * writes the facet flux of Eq. (12) in the form
+ *     q(:, c) = sigma eps o ( F y_c - eta_c o F z ),
+ * the net flux into each facet (W m^-2).
+ *   eps    n emissivities in (0, 1]
+ *   T      column-major n x m, column c at T + c*ldT
+ *   q      column-major n x m, column c at q + c*ldq (output)
+ *   m      1 .. 1024 fields
+ *   sigma  Stefan-Boltzmann constant (the caller's value; 5.670374419e-8)
+ *   info   optional (may be NULL)
+ * Returns RAD_ENOTCONV (q still written) if a column misses the tolerance.
+ * ------------------------------------------------------------------------- */
+int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64_t ldT,
+                   int64_t m, double sigma, const rad_solve_params* p,
+                   double* q, int64_t ldq, rad_solve_info* info, void* stream);
+
+/* -------------------------------------------------------------------------
+ * rad_solve_reflection — A7 alone: solves C Y = B (Eq. 11, C = I -
+ * diag(1 - eps) F) for nrhs arbitrary right-hand sides by the same batched
+ * GMRES as rad_solve_flux (the paper applies C^-1 through its LU factors,
+ * §5.2; this library iterates with the stored F instead).
+ *   B, Y   column-major n x nrhs (ldB, ldY >= n); nrhs 1 .. 1024
+ * Returns RAD_ENOTCONV (Y still written) if a column misses the tolerance.
+ * ------------------------------------------------------------------------- */
+int rad_solve_reflection(const rad_htree* h, const double* eps, const double* B, int64_t ldB, int64_t nrhs,
+                         const rad_solve_params* p, double* Y, int64_t ldY, rad_solve_info* info, void* stream);
+
+/* ----------------------------- introspection ----------------------------- */
+int rad_htree_get_stats(const rad_htree* h, rad_htree_stats* s);
+
+/* Cluster tree, host arrays.  perm[p] = facet at tree position p (n);
+ * per cluster (n_nodes, breadth-first, root first): begin, end, level,
+ * child (2 ints, -1 for a leaf), bbox (lo xyz, hi xyz).  Any array may be
+ * NULL. */
+int rad_htree_export_tree(const rad_htree* h, int32_t* perm, int32_t* begin,
+                          int32_t* end, int32_t* level, int32_t* child, double* bbox);
+
+/* Leaf blocks, host arrays of n_blocks in (row begin, column begin) order:
+ * row/column cluster ids, admissible flag, stored rank (-1 = stored dense). */
+int rad_htree_export_blocks(const rad_htree* h, int32_t* row_node, int32_t* col_node,
+                            int32_t* admissible, int32_t* rank);
+
+/* One stored block (index into the export order) as FP64 host arrays:
+ * dense blocks fill D (m x n, row-major); low-rank blocks fill U (m x k)
+ * and V (n x k), both row-major.  Arrays may be NULL to skip them. */
+int rad_htree_export_block(const rad_htree* h, int64_t block, double* D, double* U, double* V);
+
+int rad_htree_free(rad_htree* h);
+
+const char* rad_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int rad_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAD_H */

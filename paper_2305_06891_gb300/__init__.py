@@ -1,0 +1,368 @@
+"""GB300 hierarchical block low-rank cavity radiation.
+
+Thin Python binding of the C ABI in ``include/rad.h`` (``librad.so``).  The
+functions carry the C names and only marshal arguments: every step of the
+hot path (geometry, trees, ACA, block matrix products, GMRES, flux) runs in
+the library's CUDA kernels.  There is no CPU fallback: importing this module
+fails loudly (ImportError at the first call) when the compiled library is
+missing; build it with ``python -m paper_2305_06891_gb300.build``.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); matrices
+are passed column-major (the binding makes a column-major copy when needed).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librad.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "rad.h")
+
+SIGMA_SB = 5.670374419e-8
+
+RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ENOTCONV, RAD_ECUDA, RAD_ELIMIT = range(6)
+RAD_F64, RAD_F32, RAD_BF16 = 0, 1, 2
+RAD_ACA_PARTIAL, RAD_ACA_FULL = 0, 1
+_DT = {"f64": RAD_F64, "f32": RAD_F32, "bf16": RAD_BF16}
+_PIV = {"partial": RAD_ACA_PARTIAL, "full": RAD_ACA_FULL}
+
+
+class RadError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"librad error {code}: {msg}")
+        self.code = code
+
+
+class _TreeParams(C.Structure):
+    _fields_ = [("leaf_size", C.c_int32), ("reserved", C.c_int32), ("eta_adm", C.c_double)]
+
+
+class _AcaParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_rank", C.c_int32), ("pivoting", C.c_int32),
+                ("factor_dtype", C.c_int32), ("near_dtype", C.c_int32)]
+
+
+class _SolveParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("max_iter", C.c_int32)]
+
+
+class _SolveInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("restarts", C.c_int32),
+                ("matvecs", C.c_int32), ("max_rel_residual", C.c_double)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("leaf_size", C.c_int32), ("n_nodes", C.c_int32),
+                ("n_leaf_clusters", C.c_int32), ("depth", C.c_int32), ("n_blocks", C.c_int64),
+                ("n_admissible", C.c_int64), ("compressed", C.c_int32), ("factor_dtype", C.c_int32),
+                ("near_dtype", C.c_int32), ("max_rank_used", C.c_int32), ("n_dense_fallback", C.c_int64),
+                ("near_entries", C.c_int64), ("far_entries", C.c_int64), ("sum_rank", C.c_int64),
+                ("aca_entries", C.c_int64), ("bytes_near", C.c_int64), ("bytes_far", C.c_int64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2305_06891_gb300.build` "
+                          "(this package has no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    H = C.c_void_p
+    sig = {
+        "rad_version": (C.c_int, []),
+        "rad_last_error": (C.c_char_p, []),
+        "rad_build_htree": (C.c_int, [i64, vp, C.POINTER(_TreeParams), vp, C.POINTER(H)]),
+        "rad_build_htree_facets": (C.c_int, [i64, vp, vp, vp, C.POINTER(_TreeParams), vp, C.POINTER(H)]),
+        "rad_htree_from_dense": (C.c_int, [i64, vp, vp, C.POINTER(H)]),
+        "rad_compress_aca": (C.c_int, [H, C.POINTER(_AcaParams), vp]),
+        "rad_hmatvec": (C.c_int, [H, i32, vp, i64, vp, i64, i64, vp]),
+        "rad_solve_flux": (C.c_int, [H, vp, vp, i64, i64, dbl, C.POINTER(_SolveParams), vp, i64,
+                                     C.POINTER(_SolveInfo), vp]),
+        "rad_solve_reflection": (C.c_int, [H, vp, vp, i64, i64, C.POINTER(_SolveParams), vp, i64,
+                                           C.POINTER(_SolveInfo), vp]),
+        "rad_htree_get_stats": (C.c_int, [H, C.POINTER(_Stats)]),
+        "rad_htree_export_tree": (C.c_int, [H, vp, vp, vp, vp, vp, vp]),
+        "rad_htree_export_blocks": (C.c_int, [H, vp, vp, vp, vp]),
+        "rad_htree_export_block": (C.c_int, [H, i64, vp, vp, vp]),
+        "rad_htree_free": (C.c_int, [H]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+class _LazyLib:
+    """Loads librad.so on first use; raises ImportError if it is missing."""
+    _h = None
+
+    def __getattr__(self, name):
+        if _LazyLib._h is None:
+            _LazyLib._h = _load()
+        return getattr(_LazyLib._h, name)
+
+
+_lib = _LazyLib()
+
+
+def load_library():
+    """Load librad.so now (raises ImportError when it has not been built)."""
+    _lib.rad_version()
+    return LIB_PATH
+
+
+def header_functions() -> list[str]:
+    """Names of every function declared in include/rad.h."""
+    txt = open(HEADER_PATH).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*|void)\s+(rad_\w+)\s*\(", txt, re.M)))
+
+
+def _check(rc: int):
+    if rc != RAD_OK:
+        raise RadError(rc, _lib.rad_last_error().decode())
+
+
+def _torch():
+    try:
+        import torch
+        return torch
+    except ImportError:  # pragma: no cover
+        return None
+
+
+def _is_tensor(a) -> bool:
+    t = _torch()
+    return t is not None and isinstance(a, t.Tensor)
+
+
+def _stream(stream, *arrays):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    t = _torch()
+    if t is not None and any(_is_tensor(a) and a.is_cuda for a in arrays):
+        return C.c_void_p(t.cuda.current_stream().cuda_stream)
+    return C.c_void_p(0)
+
+
+def _ptr(a) -> C.c_void_p:
+    if _is_tensor(a):
+        return C.c_void_p(a.data_ptr())
+    return C.c_void_p(a.ctypes.data)
+
+
+def _f64_rowmajor(a, shape_last: int | None = None):
+    """float64, C-contiguous (tensor or numpy)."""
+    if _is_tensor(a):
+        t = _torch()
+        return a.to(t.float64).contiguous()
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _colmajor(a, dtype):
+    """2-D column-major copy/view with the requested element type; returns
+    (array, n_rows, n_cols, ld)."""
+    if _is_tensor(a):
+        t = _torch()
+        td = {np.float64: t.float64, np.float32: t.float32}[dtype]
+        a2 = a.reshape(-1, 1) if a.dim() == 1 else a
+        a2 = a2.to(td)
+        if a2.stride(0) != 1 or (a2.shape[1] > 1 and a2.stride(1) < a2.shape[0]):
+            a2 = a2.t().contiguous().t()
+        ld = a2.stride(1) if a2.shape[1] > 1 else a2.shape[0]
+        return a2, a2.shape[0], a2.shape[1], max(ld, a2.shape[0])
+    a2 = np.asarray(a, dtype=dtype)
+    if a2.ndim == 1:
+        a2 = a2.reshape(-1, 1)
+    a2 = np.asfortranarray(a2)
+    return a2, a2.shape[0], a2.shape[1], a2.shape[0]
+
+
+class HTree:
+    """Owns one ``rad_htree*``; freed with :func:`rad_htree_free` or on GC."""
+
+    def __init__(self, ptr: int, n: int):
+        self._p = C.c_void_p(ptr)
+        self.n = n
+
+    @property
+    def ptr(self) -> C.c_void_p:
+        if not self._p:
+            raise RadError(RAD_EINVAL, "handle already freed")
+        return self._p
+
+    def free(self):
+        if self._p:
+            _lib.rad_htree_free(self._p)
+            self._p = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def rad_version() -> int:
+    return _lib.rad_version()
+
+
+def rad_last_error() -> str:
+    return _lib.rad_last_error().decode()
+
+
+def rad_build_htree(verts, leaf_size: int = 32, eta_adm: float = 1.0, stream=None) -> HTree:
+    """A1-A3 on the GPU: facets of the triangles ``verts`` (N, 3, 3)."""
+    v = _f64_rowmajor(verts)
+    n = int(v.shape[0])
+    out = C.c_void_p()
+    p = _TreeParams(int(leaf_size), 0, float(eta_adm))
+    _check(_lib.rad_build_htree(n, _ptr(v), C.byref(p), _stream(stream, v), C.byref(out)))
+    return HTree(out.value, n)
+
+
+def rad_build_htree_facets(centroid, normal, area, leaf_size: int = 32, eta_adm: float = 1.0,
+                           stream=None) -> HTree:
+    c, nr, a = _f64_rowmajor(centroid), _f64_rowmajor(normal), _f64_rowmajor(area)
+    n = int(a.shape[0])
+    out = C.c_void_p()
+    p = _TreeParams(int(leaf_size), 0, float(eta_adm))
+    _check(_lib.rad_build_htree_facets(n, _ptr(c), _ptr(nr), _ptr(a), C.byref(p), _stream(stream, c),
+                                       C.byref(out)))
+    return HTree(out.value, n)
+
+
+def rad_htree_from_dense(F, stream=None) -> HTree:
+    Fm = _f64_rowmajor(F)
+    n = int(Fm.shape[0])
+    out = C.c_void_p()
+    _check(_lib.rad_htree_from_dense(n, _ptr(Fm), _stream(stream, Fm), C.byref(out)))
+    return HTree(out.value, n)
+
+
+def rad_compress_aca(h: HTree, tol: float, max_rank: int = 64, pivoting: str = "partial",
+                     factor_dtype: str = "f32", near_dtype: str = "f32", stream=None) -> None:
+    p = _AcaParams(float(tol), int(max_rank), _PIV[pivoting], _DT[factor_dtype], _DT[near_dtype])
+    _check(_lib.rad_compress_aca(h.ptr, C.byref(p), _stream(stream)))
+
+
+def rad_hmatvec(h: HTree, x, y=None, stream=None):
+    """Y = F X.  ``x``: (N,) or (N, nrhs), float64 or float32, host or device."""
+    is_t = _is_tensor(x)
+    if is_t:
+        t = _torch()
+        dt = np.float64 if x.dtype == t.float64 else np.float32
+    else:
+        dt = np.float64 if np.asarray(x).dtype == np.float64 else np.float32
+    xc, n, nrhs, ldx = _colmajor(x, dt)
+    if y is None:
+        if is_t:
+            y = t.empty((nrhs, n), dtype=xc.dtype, device=xc.device).t()
+        else:
+            y = np.empty((n, nrhs), dtype=dt, order="F")
+        ldy = n
+    else:
+        ldy = (y.stride(1) if y.dim() == 2 else n) if _is_tensor(y) else n
+    _check(_lib.rad_hmatvec(h.ptr, RAD_F64 if dt == np.float64 else RAD_F32, _ptr(xc), ldx, _ptr(y), ldy,
+                            nrhs, _stream(stream, xc, y)))
+    if (_is_tensor(x) and x.dim() == 1) or (not _is_tensor(x) and np.ndim(x) == 1):
+        return y[:, 0]
+    return y
+
+
+def rad_solve_flux(h: HTree, eps, T, sigma: float = SIGMA_SB, tol: float = 1e-10, restart: int = 30,
+                   max_iter: int = 1000, q=None, stream=None, raise_on_notconv: bool = False):
+    """A7-A8: flux q (N, m) for temperature fields T (N,) or (N, m).
+
+    Returns ``(q, info)``; ``info`` is a dict with status, iters, restarts,
+    matvecs and max_rel_residual.
+    """
+    Tc, n, m, ldT = _colmajor(T, np.float64)
+    e = _f64_rowmajor(eps)
+    if q is None:
+        if _is_tensor(Tc):
+            t = _torch()
+            q = t.empty((m, n), dtype=t.float64, device=Tc.device).t()
+        else:
+            q = np.empty((n, m), dtype=np.float64, order="F")
+    ldq = n
+    p = _SolveParams(float(tol), int(restart), int(max_iter))
+    info = _SolveInfo()
+    rc = _lib.rad_solve_flux(h.ptr, _ptr(e), _ptr(Tc), ldT, m, float(sigma), C.byref(p), _ptr(q), ldq,
+                             C.byref(info), _stream(stream, e, Tc, q))
+    if rc != RAD_OK and (rc != RAD_ENOTCONV or raise_on_notconv):
+        _check(rc)
+    d = {k: getattr(info, k) for k, _ in _SolveInfo._fields_}
+    if (_is_tensor(T) and T.dim() == 1) or (not _is_tensor(T) and np.ndim(T) == 1):
+        q = q[:, 0]
+    return q, d
+
+
+def rad_solve_reflection(h: HTree, eps, B, tol: float = 1e-10, restart: int = 30, max_iter: int = 1000,
+                         Y=None, stream=None, raise_on_notconv: bool = False):
+    """A7: Y solving C Y = B (Eq. 11) for B (N,) or (N, nrhs).  Returns (Y, info)."""
+    Bc, n, nrhs, ldB = _colmajor(B, np.float64)
+    e = _f64_rowmajor(eps)
+    if Y is None:
+        if _is_tensor(Bc):
+            t = _torch()
+            Y = t.empty((nrhs, n), dtype=t.float64, device=Bc.device).t()
+        else:
+            Y = np.empty((n, nrhs), dtype=np.float64, order="F")
+    p = _SolveParams(float(tol), int(restart), int(max_iter))
+    info = _SolveInfo()
+    rc = _lib.rad_solve_reflection(h.ptr, _ptr(e), _ptr(Bc), ldB, nrhs, C.byref(p), _ptr(Y), n, C.byref(info),
+                                   _stream(stream, e, Bc, Y))
+    if rc != RAD_OK and (rc != RAD_ENOTCONV or raise_on_notconv):
+        _check(rc)
+    d = {k: getattr(info, k) for k, _ in _SolveInfo._fields_}
+    if (_is_tensor(B) and B.dim() == 1) or (not _is_tensor(B) and np.ndim(B) == 1):
+        Y = Y[:, 0]
+    return Y, d
+
+
+def rad_htree_get_stats(h: HTree) -> dict:
+    s = _Stats()
+    _check(_lib.rad_htree_get_stats(h.ptr, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+
+def rad_htree_export_tree(h: HTree) -> dict:
+    st = rad_htree_get_stats(h)
+    nn, n = st["n_nodes"], st["n"]
+    out = dict(perm=np.empty(n, np.int32), begin=np.empty(nn, np.int32), end=np.empty(nn, np.int32),
+               level=np.empty(nn, np.int32), child=np.empty((nn, 2), np.int32), bbox=np.empty((nn, 6)))
+    _check(_lib.rad_htree_export_tree(h.ptr, *(C.c_void_p(out[k].ctypes.data) for k in
+                                                ("perm", "begin", "end", "level", "child", "bbox"))))
+    return out
+
+
+def rad_htree_export_blocks(h: HTree) -> dict:
+    nb = rad_htree_get_stats(h)["n_blocks"]
+    out = {k: np.empty(nb, np.int32) for k in ("row_node", "col_node", "admissible", "rank")}
+    _check(_lib.rad_htree_export_blocks(h.ptr, *(C.c_void_p(out[k].ctypes.data) for k in
+                                                  ("row_node", "col_node", "admissible", "rank"))))
+    return out
+
+
+def rad_htree_export_block(h: HTree, b: int, m: int, n: int, rank: int):
+    """Stored block ``b`` (export order): D (m, n) if dense, else (U, V)."""
+    if rank < 0:
+        D = np.empty((m, n))
+        _check(_lib.rad_htree_export_block(h.ptr, int(b), C.c_void_p(D.ctypes.data), None, None))
+        return D
+    U = np.zeros((m, max(rank, 0)))
+    V = np.zeros((n, max(rank, 0)))
+    _check(_lib.rad_htree_export_block(h.ptr, int(b), None, C.c_void_p(U.ctypes.data) if rank else None,
+                                       C.c_void_p(V.ctypes.data) if rank else None))
+    return U, V
+
+
+def rad_htree_free(h: HTree) -> None:
+    h.free()
+
+
+__all__ = [n for n in dir() if n.startswith("rad_")] + ["HTree", "RadError", "SIGMA_SB", "header_functions"]

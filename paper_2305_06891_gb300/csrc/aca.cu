@@ -1,0 +1,611 @@
+// A4-A5: dense blocks (entries of Eq. 10) and cross approximation of the
+// admissible blocks (§4.3, Eqs. 30-31), plus packing of the factors and the
+// row-tile tables used by the matrix-vector product.
+//
+// ACA runs one CTA per admissible block.  Rows and columns of the block are
+// evaluated on the fly from the tree-ordered facet geometry; the residual
+// row/column are written straight into the block's slot of the U/V scratch
+// (column-major, room for kmax columns); pivots come from block-wide
+// warp-shuffle argmax reductions (ties: lowest index); the Frobenius-norm
+// estimate of the cross and all dot products accumulate in FP64.
+//
+// Partial pivoting: first pivot row 0; column pivot = argmax |residual row|;
+// a residual row whose largest modulus is <= max(1e-300, 1e-14 x largest
+// pivot so far) is marked used and the lowest unused row is tried instead;
+// next row = argmax |u_k| over unused rows; stop when
+// |u_k| |v_k| <= tol ||S_k||_F with
+// ||S_k||^2 = ||S_{k-1}||^2 + 2 sum_{l<k} (u_k.u_l)(v_k.v_l) + |u_k|^2 |v_k|^2.
+// Full pivoting keeps the whole residual and stops when
+// ||R_k||_F <= tol ||X||_F (Eq. 31 exactly).
+// A block whose rank would exceed kmax = min(max_rank, m n / (m + n)) is
+// stored dense.
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "rad_device.cuh"
+
+namespace rad {
+
+namespace {
+
+struct AcaJob {
+    int r0, c0, m, n, kmax, pad;
+    long long offU, offV, offUsed;
+};
+
+constexpr int kAcaNT = 256;
+
+// lowest index i < m with used[i] == 0, or -1; all threads receive it
+__device__ int lowest_unused(const unsigned char* used, int m, int* sm) {
+    int best = 0x7fffffff;
+    for (int i = threadIdx.x; i < m; i += kAcaNT)
+        if (!used[i]) { best = i; break; }
+    best = __reduce_min_sync(0xffffffffu, best);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sm[warp] = best;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < kAcaNT / 32 ? sm[lane] : 0x7fffffff;
+        t = __reduce_min_sync(0xffffffffu, t);
+        if (lane == 0) sm[kAcaNT / 32] = t;
+    }
+    __syncthreads();
+    const int r = sm[kAcaNT / 32];
+    __syncthreads();
+    return r == 0x7fffffff ? -1 : r;
+}
+
+// For l < k: out[l] = sum_j a_j * B[l*ld + j] over this thread's j; plus
+// out[k] = sum_j a_j^2.  Results (FP64) land in red[0..k] for every thread.
+template <class CT>
+__device__ void cross_dots(const CT* a, const CT* B, int len, long long ld, int k, double (*part)[kMaxRank + 1],
+                           double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int l = 0; l <= k; ++l) {
+        double s = 0.0;
+        const CT* bl = (l < k) ? B + (long long)l * ld : a;
+        for (int j = threadIdx.x; j < len; j += kAcaNT) s += (double)a[j] * (double)bl[j];
+        s = warp_sum(s);
+        if (lane == 0) part[warp][l] = s;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x <= k) {
+        double s = 0.0;
+        for (int w = 0; w < kAcaNT / 32; ++w) s += part[w][threadIdx.x];
+        red[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+template <class CT>
+__global__ void __launch_bounds__(kAcaNT)
+aca_partial_kernel(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict__ order, CT* Upool, CT* Vpool,
+                   unsigned char* used_pool, int* __restrict__ rank_out, long long* __restrict__ evals_out,
+                   double tol) {
+    __shared__ double s_row[kMaxRank];
+    __shared__ double part[kAcaNT / 32][kMaxRank + 1];
+    __shared__ double s_cv[kMaxRank + 1];
+    __shared__ double s_cu[kMaxRank + 1];
+    __shared__ ArgMax am_sm[kAcaNT / 32 + 1];
+    __shared__ int i_sm[kAcaNT / 32 + 1];
+
+    const int bidx = order[blockIdx.x];
+    const AcaJob jb = jobs[bidx];
+    const int m = jb.m, n = jb.n, kmax = jb.kmax;
+    CT* U = Upool + jb.offU;
+    CT* V = Vpool + jb.offV;
+    unsigned char* used = used_pool + jb.offUsed;
+
+    int i = 0, k = 0, status = 0;  // status: 1 converged, 2 rank cap
+    double norm2 = 0.0, scale = 0.0;
+    long long evals = 0;
+    for (int guard = 0; guard <= m + kmax + 1; ++guard) {
+        if (k >= kmax) { status = 2; break; }
+        // residual of pivot row i: X(i,:) - sum_l U(i,l) V(:,l)
+        if ((int)threadIdx.x < k) s_row[threadIdx.x] = (double)U[(long long)threadIdx.x * m + i];
+        __syncthreads();
+        CT* vk = V + (long long)k * n;
+        ArgMax best{-1.0, 0x7fffffff};
+        for (int j = threadIdx.x; j < n; j += kAcaNT) {
+            CT r = Entry<CT>::eval(g, jb.r0 + i, jb.c0 + j);
+            for (int l = 0; l < k; ++l) r -= (CT)s_row[l] * V[(long long)l * n + j];
+            vk[j] = r;
+            best = am_better(best, ArgMax{fabs((double)r), j});
+        }
+        best = block_argmax<kAcaNT>(best, am_sm);
+        evals += n;
+        if (threadIdx.x == 0) used[i] = 1;
+        __syncthreads();
+        if (!(best.v > fmax(1e-300, 1e-14 * scale))) {
+            const int nxt = lowest_unused(used, m, i_sm);
+            if (nxt < 0) { status = 1; break; }
+            i = nxt;
+            continue;
+        }
+        scale = fmax(scale, best.v);
+        const int jp = best.i;
+        const CT piv = vk[jp];
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += kAcaNT) vk[j] = vk[j] / piv;
+        // (v_k . v_l) for l < k and |v_k|^2; each thread reads its own j
+        cross_dots<CT>(vk, V, n, n, k, part, s_cv);
+        // residual of pivot column jp
+        if ((int)threadIdx.x < k) s_row[threadIdx.x] = (double)V[(long long)threadIdx.x * n + jp];
+        __syncthreads();
+        CT* uk = U + (long long)k * m;
+        ArgMax bu{-1.0, 0x7fffffff};
+        for (int r = threadIdx.x; r < m; r += kAcaNT) {
+            CT u = Entry<CT>::eval(g, jb.r0 + r, jb.c0 + jp);
+            for (int l = 0; l < k; ++l) u -= (CT)s_row[l] * U[(long long)l * m + r];
+            uk[r] = u;
+            if (!used[r]) bu = am_better(bu, ArgMax{fabs((double)u), r});
+        }
+        evals += m;
+        cross_dots<CT>(uk, U, m, m, k, part, s_cu);
+        bu = block_argmax<kAcaNT>(bu, am_sm);
+        double cross = 0.0;
+        for (int l = 0; l < k; ++l) cross += s_cu[l] * s_cv[l];
+        const double uu = s_cu[k], vv = s_cv[k];
+        norm2 = norm2 + 2.0 * cross + uu * vv;
+        ++k;
+        if (sqrt(uu) * sqrt(vv) <= tol * sqrt(fmax(norm2, 0.0))) { status = 1; break; }
+        if (bu.v < 0.0) { status = 1; break; }
+        i = bu.i;
+    }
+    if (threadIdx.x == 0) {
+        rank_out[bidx] = status == 1 ? k : -1;
+        evals_out[bidx] = evals;
+    }
+}
+
+// Full pivoting: the residual R (m x n, column-major) lives in scratch.
+template <class CT>
+__global__ void __launch_bounds__(kAcaNT)
+aca_full_kernel(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict__ order, CT* Upool, CT* Vpool,
+                CT* Rpool, const long long* __restrict__ offR, int* __restrict__ rank_out,
+                long long* __restrict__ evals_out, double tol) {
+    __shared__ double red[kAcaNT / 32 + 1];
+    __shared__ ArgMax am_sm[kAcaNT / 32 + 1];
+    const int bidx = order[blockIdx.x];
+    const AcaJob jb = jobs[bidx];
+    const int m = jb.m, n = jb.n, kmax = jb.kmax;
+    const long long mn = (long long)m * n;
+    CT* R = Rpool + offR[bidx];
+    CT* U = Upool + jb.offU;
+    CT* V = Vpool + jb.offV;
+    double s = 0.0;
+    for (long long e = threadIdx.x; e < mn; e += kAcaNT) {
+        const int jj = (int)(e / m), ii = (int)(e - (long long)jj * m);
+        const CT x = Entry<CT>::eval(g, jb.r0 + ii, jb.c0 + jj);
+        R[e] = x;
+        s += (double)x * (double)x;
+    }
+    const double normX2 = block_sum<kAcaNT, double>(s, red);
+    double normR2 = normX2;
+    int k = 0, status = 0;
+    for (;;) {
+        if (sqrt(normR2) <= tol * sqrt(normX2)) { status = 1; break; }
+        if (k >= kmax) { status = 2; break; }
+        // pivot: largest |R|, ties to the lowest (row, column) row-major
+        ArgMax best{-1.0, 0x7fffffff};
+        for (long long e = threadIdx.x; e < mn; e += kAcaNT) {
+            const int jj = (int)(e / m), ii = (int)(e - (long long)jj * m);
+            best = am_better(best, ArgMax{fabs((double)R[e]), ii * n + jj});
+        }
+        best = block_argmax<kAcaNT>(best, am_sm);
+        const int ip = best.i / n, jp = best.i - ip * n;
+        const CT piv = R[(long long)jp * m + ip];
+        CT* uk = U + (long long)k * m;
+        CT* vk = V + (long long)k * n;
+        for (int r = threadIdx.x; r < m; r += kAcaNT) uk[r] = R[(long long)jp * m + r];
+        for (int c = threadIdx.x; c < n; c += kAcaNT) vk[c] = R[(long long)c * m + ip] / piv;
+        __syncthreads();
+        s = 0.0;
+        for (long long e = threadIdx.x; e < mn; e += kAcaNT) {
+            const int jj = (int)(e / m), ii = (int)(e - (long long)jj * m);
+            const CT x = R[e] - uk[ii] * vk[jj];
+            R[e] = x;
+            s += (double)x * (double)x;
+        }
+        normR2 = block_sum<kAcaNT, double>(s, red);
+        ++k;
+    }
+    if (threadIdx.x == 0) {
+        rank_out[bidx] = status == 1 ? k : -1;
+        evals_out[bidx] = mn;
+    }
+}
+
+// Dense blocks: entries of Eq. (10), column-major, stored as S.
+struct NearWork {
+    int desc;
+    int chunk;
+};
+constexpr int kNearChunk = 8192;
+
+template <class S, class CT>
+__global__ void __launch_bounds__(256)
+near_assemble_kernel(Geo g, const NearDesc* __restrict__ nd, const NearWork* __restrict__ work, S* pool) {
+    const NearWork w = work[blockIdx.x];
+    const NearDesc d = nd[w.desc];
+    const long long mn = (long long)d.m * d.n;
+    const long long e0 = (long long)w.chunk * kNearChunk;
+    const long long e1 = min(mn, e0 + kNearChunk);
+    S* D = pool + d.off;
+    for (long long e = e0 + threadIdx.x; e < e1; e += 256) {
+        const int jj = (int)(e / d.m), ii = (int)(e - (long long)jj * d.m);
+        D[e] = Store<S>::put((double)Entry<CT>::eval(g, d.r0 + ii, d.c0 + jj));
+    }
+}
+
+// Copy the first k columns of U and V from the ACA scratch to the packed
+// factor pool, converting to the storage type.
+struct PackJob {
+    long long srcU, srcV, dstU, dstV;
+    int m, n, k, pad;
+};
+template <class CT, class S>
+__global__ void __launch_bounds__(256)
+pack_kernel(const PackJob* __restrict__ jobs, const CT* __restrict__ Us, const CT* __restrict__ Vs, S* pool) {
+    const PackJob j = jobs[blockIdx.x];
+    const long long nu = (long long)j.m * j.k, nv = (long long)j.n * j.k;
+    for (long long e = threadIdx.x; e < nu; e += 256) pool[j.dstU + e] = Store<S>::put((double)Us[j.srcU + e]);
+    for (long long e = threadIdx.x; e < nv; e += 256) pool[j.dstV + e] = Store<S>::put((double)Vs[j.srcV + e]);
+}
+
+__global__ void transpose_dense_kernel(int n, const double* __restrict__ F, double* __restrict__ D) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nn = (long long)n * n;
+    if (e >= nn) return;
+    const int j = (int)(e / n), i = (int)(e - (long long)j * n);
+    D[e] = F[(long long)i * n + j];
+}
+
+template <class CT>
+void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>& jobs, std::vector<int>& ranks,
+                std::vector<long long>& evals, std::vector<std::vector<double>>* unused, Scratch& ws,
+                CT*& Us, CT*& Vs, cudaStream_t s) {
+    (void)unused;
+    const int nj = (int)jobs.size();
+    long long su = 0, sv = 0, sused = 0;
+    for (auto& j : jobs) {
+        su = std::max(su, j.offU + (long long)j.m * j.kmax);
+        sv = std::max(sv, j.offV + (long long)j.n * j.kmax);
+        sused = std::max(sused, j.offUsed + j.m);
+    }
+    Us = ws.get_n<CT>(std::max<long long>(su, 1));
+    Vs = ws.get_n<CT>(std::max<long long>(sv, 1));
+    AcaJob* d_jobs = ws.get_n<AcaJob>(nj);
+    h2d(d_jobs, jobs, s);
+    // schedule the largest blocks first
+    std::vector<int> order(nj);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const long long wa = (long long)(jobs[a].m + jobs[a].n) * std::max(1, jobs[a].kmax);
+        const long long wb = (long long)(jobs[b].m + jobs[b].n) * std::max(1, jobs[b].kmax);
+        return wa > wb;
+    });
+    int* d_order = ws.get_n<int>(nj);
+    h2d(d_order, order, s);
+    int* d_rank = ws.get_n<int>(nj);
+    long long* d_evals = ws.get_n<long long>(nj);
+    const Geo g = geo_view(h->geo.as<double>(), h->n);
+    if (p->pivoting == RAD_ACA_FULL) {
+        std::vector<long long> offR(nj);
+        long long sr = 0;
+        for (int b = 0; b < nj; ++b) {
+            offR[b] = sr;
+            sr += round_up((long long)jobs[b].m * jobs[b].n, 8);
+        }
+        RAD_REQUIRE(sr * (long long)sizeof(CT) <= (8ll << 30), RAD_ELIMIT,
+                    "full-pivot ACA needs more than 8 GiB of residual storage; use partial pivoting");
+        CT* R = ws.get_n<CT>(std::max<long long>(sr, 1));
+        long long* d_offR = ws.get_n<long long>(nj);
+        h2d(d_offR, offR, s);
+        aca_full_kernel<CT><<<nj, kAcaNT, 0, s>>>(g, d_jobs, d_order, Us, Vs, R, d_offR, d_rank, d_evals, p->tol);
+    } else {
+        unsigned char* used = ws.get_n<unsigned char>(std::max<long long>(sused, 1));
+        RAD_CUDA(cudaMemsetAsync(used, 0, std::max<long long>(sused, 1), s));
+        aca_partial_kernel<CT><<<nj, kAcaNT, 0, s>>>(g, d_jobs, d_order, Us, Vs, used, d_rank, d_evals, p->tol);
+    }
+    RAD_CHECK_LAUNCH();
+    ranks.resize(nj);
+    evals.resize(nj);
+    RAD_CUDA(cudaMemcpyAsync(ranks.data(), d_rank, sizeof(int) * nj, cudaMemcpyDeviceToHost, s));
+    RAD_CUDA(cudaMemcpyAsync(evals.data(), d_evals, sizeof(long long) * nj, cudaMemcpyDeviceToHost, s));
+    RAD_CUDA(cudaStreamSynchronize(s));
+}
+
+template <class S, class CT>
+void launch_near(rad_htree* h, cudaStream_t s) {
+    Scratch ws(s);
+    std::vector<NearWork> work;
+    for (int d = 0; d < (int)h->near_h.size(); ++d) {
+        const long long mn = (long long)h->near_h[d].m * h->near_h[d].n;
+        for (long long c = 0; c * kNearChunk < mn; ++c) work.push_back(NearWork{d, (int)c});
+    }
+    if (work.empty()) return;
+    NearDesc* d_nd = ws.get_n<NearDesc>(h->near_h.size());
+    h2d(d_nd, h->near_h, s);
+    NearWork* d_work = ws.get_n<NearWork>(work.size());
+    h2d(d_work, work, s);
+    const Geo g = geo_view(h->geo.as<double>(), h->n);
+    near_assemble_kernel<S, CT><<<(unsigned)work.size(), 256, 0, s>>>(g, d_nd, d_work, h->near_pool.as<S>());
+    RAD_CHECK_LAUNCH();
+}
+
+template <class CT, class S>
+void launch_pack(rad_htree* h, const std::vector<PackJob>& jobs, const CT* Us, const CT* Vs, cudaStream_t s) {
+    if (jobs.empty()) return;
+    Scratch ws(s);
+    PackJob* d_jobs = ws.get_n<PackJob>(jobs.size());
+    h2d(d_jobs, jobs, s);
+    pack_kernel<CT, S><<<(unsigned)jobs.size(), 256, 0, s>>>(d_jobs, Us, Vs, h->far_pool.as<S>());
+    RAD_CHECK_LAUNCH();
+}
+
+template <class CT>
+void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
+    Scratch ws(s);
+    // admissible blocks -> ACA jobs
+    std::vector<int> adm;
+    for (int b = 0; b < (int)h->blocks.size(); ++b)
+        if (h->blocks[b].admissible) adm.push_back(b);
+    std::vector<AcaJob> jobs;
+    jobs.reserve(adm.size());
+    long long ou = 0, ov = 0, oused = 0;
+    for (int b : adm) {
+        const BlockH& bk = h->blocks[b];
+        const int m = bk.r1 - bk.r0, n = bk.c1 - bk.c0;
+        const long long brk = (long long)m * n / (m + n);
+        const int kmax = (int)std::min<long long>({(long long)p->max_rank, brk, (long long)kMaxRank});
+        jobs.push_back(AcaJob{bk.r0, bk.c0, m, n, kmax, 0, ou, ov, oused});
+        ou += round_up((long long)m * kmax, 8);
+        ov += round_up((long long)n * kmax, 8);
+        oused += round_up(m, 16);
+    }
+    RAD_REQUIRE((ou + ov) * (long long)sizeof(CT) <= (64ll << 30), RAD_ELIMIT, "ACA scratch exceeds 64 GiB");
+    std::vector<int> ranks;
+    std::vector<long long> evals;
+    CT* Us = nullptr;
+    CT* Vs = nullptr;
+    if (!jobs.empty()) launch_aca<CT>(h, p, jobs, ranks, evals, nullptr, ws, Us, Vs, s);
+
+    // storage plan
+    h->near_h.clear();
+    h->far_h.clear();
+    h->near_block.clear();
+    h->far_block.clear();
+    h->aca_entries = 0;
+    for (auto e : evals) h->aca_entries += e;
+    const int ns = dtype_size(h->near_dtype);
+    const int fs = dtype_size(h->factor_dtype);
+    long long near_off = 0, far_off = 0;
+    std::vector<PackJob> pack;
+    int64_t fallback = 0;
+    int maxk = 0;
+    long long sum_far_entries = 0;
+    std::vector<int> rank_of(h->blocks.size(), -1);
+    for (size_t a = 0; a < adm.size(); ++a) rank_of[adm[a]] = ranks[a];
+    std::vector<int> job_of(h->blocks.size(), -1);
+    for (size_t a = 0; a < adm.size(); ++a) job_of[adm[a]] = (int)a;
+    for (int b = 0; b < (int)h->blocks.size(); ++b) {
+        BlockH& bk = h->blocks[b];
+        const int m = bk.r1 - bk.r0, n = bk.c1 - bk.c0;
+        const int rk = bk.admissible ? rank_of[b] : -1;
+        bk.rank = rk;
+        if (rk < 0) {
+            if (bk.admissible) ++fallback;
+            bk.store_idx = (int)h->near_h.size();
+            h->near_h.push_back(NearDesc{bk.r0, bk.c0, m, n, near_off});
+            h->near_block.push_back(b);
+            near_off += round_up((long long)m * n, 16);
+        } else {
+            bk.store_idx = (int)h->far_h.size();
+            FarDesc fd{bk.r0, bk.c0, m, n, rk, 0, far_off, 0};
+            far_off += round_up((long long)m * rk, 16);
+            fd.offV = far_off;
+            far_off += round_up((long long)n * rk, 16);
+            h->far_h.push_back(fd);
+            h->far_block.push_back(b);
+            maxk = std::max(maxk, rk);
+            sum_far_entries += (long long)rk * (m + n);
+            if (rk > 0) {
+                const AcaJob& j = jobs[job_of[b]];
+                pack.push_back(PackJob{j.offU, j.offV, fd.offU, fd.offV, m, n, rk, 0});
+            }
+        }
+    }
+    h->near_pool.alloc((size_t)std::max<long long>(near_off, 16) * ns);
+    h->far_pool.alloc((size_t)std::max<long long>(far_off, 16) * fs);
+    if (h->near_dtype == RAD_F64) launch_near<double, double>(h, s);
+    else launch_near<float, float>(h, s);
+    if (h->factor_dtype == RAD_F64) launch_pack<CT, double>(h, pack, Us, Vs, s);
+    else if (h->factor_dtype == RAD_F32) launch_pack<CT, float>(h, pack, Us, Vs, s);
+    else launch_pack<CT, __nv_bfloat16>(h, pack, Us, Vs, s);
+    h->n_dense_fallback = fallback;
+    h->max_rank_used = maxk;
+    h->far_entries = sum_far_entries;
+    long long ne = 0;
+    for (auto& d : h->near_h) ne += (long long)d.m * d.n;
+    h->near_entries = ne;
+    finalize_operator(h, s);
+    RAD_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
+    RAD_REQUIRE(p != nullptr, RAD_EINVAL, "null aca params");
+    RAD_REQUIRE(p->tol >= 0.0 && p->tol == p->tol, RAD_EINVAL, "tol must be >= 0");
+    RAD_REQUIRE(p->max_rank >= 0 && p->max_rank <= kMaxRank, RAD_EINVAL, "max_rank must be in [0, 128]");
+    RAD_REQUIRE(p->pivoting == RAD_ACA_PARTIAL || p->pivoting == RAD_ACA_FULL, RAD_EINVAL, "bad pivoting");
+    RAD_REQUIRE(p->near_dtype == RAD_F64 || p->near_dtype == RAD_F32, RAD_EINVAL, "near_dtype must be F64 or F32");
+    RAD_REQUIRE(p->factor_dtype == RAD_F64 || p->factor_dtype == RAD_F32 || p->factor_dtype == RAD_BF16,
+                RAD_EINVAL, "bad factor_dtype");
+    RAD_REQUIRE((p->near_dtype == RAD_F64) == (p->factor_dtype == RAD_F64), RAD_EINVAL,
+                "near_dtype F64 requires factor_dtype F64 and vice versa");
+    RAD_REQUIRE(!h->from_dense, RAD_EINVAL, "a dense-wrapped handle cannot be recompressed");
+    h->compressed = false;
+    h->factor_dtype = p->factor_dtype;
+    h->near_dtype = p->near_dtype;
+    h->tol = p->tol;
+    h->pivoting = p->pivoting;
+    if (p->near_dtype == RAD_F64) compress_t<double>(h, p, s);
+    else compress_t<float>(h, p, s);
+    h->compressed = true;
+}
+
+void finalize_operator(rad_htree* h, cudaStream_t s) {
+    const int n = (int)h->n;
+    // row tiles: leaf clusters in tree order, cut into <= 64-row pieces
+    std::vector<std::pair<int, int>> leaves;
+    if (h->from_dense) {
+        leaves.push_back({0, n});
+    } else {
+        for (auto& nd : h->nodes)
+            if (nd.leaf) leaves.push_back({nd.begin, nd.end});
+        std::sort(leaves.begin(), leaves.end());
+    }
+    std::vector<TileDesc> tiles;
+    std::vector<int> tile_at(n + 1, -1);
+    for (auto& lf : leaves)
+        for (int r = lf.first; r < lf.second; r += kTileRows) {
+            tile_at[r] = (int)tiles.size();
+            tiles.push_back(TileDesc{r, std::min(kTileRows, lf.second - r), 0, 0});
+        }
+    std::vector<std::vector<int2>> per(tiles.size());
+    for (int d = 0; d < (int)h->near_h.size(); ++d) {
+        const NearDesc& nd = h->near_h[d];
+        int r = nd.r0;
+        while (r < nd.r0 + nd.m) {
+            const int t = tile_at[r];
+            RAD_REQUIRE(t >= 0, RAD_ECUDA, "internal: block rows do not align with tiles");
+            per[t].push_back(make_int2(d, r - nd.r0));
+            r += tiles[t].rows;
+        }
+    }
+    std::vector<int> trow;
+    int toff = 0;
+    std::vector<int> nz;
+    for (int d = 0; d < (int)h->far_h.size(); ++d) {
+        FarDesc& fd = h->far_h[d];
+        fd.toff = toff;
+        for (int l = 0; l < fd.k; ++l) trow.push_back(d);
+        toff += fd.k;
+        if (fd.k == 0) continue;
+        nz.push_back(d);
+        int r = fd.r0;
+        while (r < fd.r0 + fd.m) {
+            const int t = tile_at[r];
+            RAD_REQUIRE(t >= 0, RAD_ECUDA, "internal: block rows do not align with tiles");
+            per[t].push_back(make_int2(d | kFarBit, r - fd.r0));
+            r += tiles[t].rows;
+        }
+    }
+    std::stable_sort(nz.begin(), nz.end(), [&](int a, int b) { return h->far_h[a].n > h->far_h[b].n; });
+    std::vector<int2> entries;
+    for (size_t t = 0; t < tiles.size(); ++t) {
+        tiles[t].e0 = (int)entries.size();
+        entries.insert(entries.end(), per[t].begin(), per[t].end());
+        tiles[t].e1 = (int)entries.size();
+    }
+    h->n_tiles = (int)tiles.size();
+    h->sum_rank = toff;
+    h->n_far_nz = (int)nz.size();
+    h->d_tiles.alloc(sizeof(TileDesc) * std::max<size_t>(1, tiles.size()));
+    h->d_entries.alloc(sizeof(int2) * std::max<size_t>(1, entries.size()));
+    h->d_near.alloc(sizeof(NearDesc) * std::max<size_t>(1, h->near_h.size()));
+    h->d_far.alloc(sizeof(FarDesc) * std::max<size_t>(1, h->far_h.size()));
+    h->d_trow.alloc(sizeof(int) * std::max<size_t>(1, trow.size()));
+    h->d_far_nz.alloc(sizeof(int) * std::max<size_t>(1, nz.size()));
+    h2d(h->d_tiles.as<TileDesc>(), tiles, s);
+    h2d(h->d_entries.as<int2>(), entries, s);
+    h2d(h->d_near.as<NearDesc>(), h->near_h, s);
+    h2d(h->d_far.as<FarDesc>(), h->far_h, s);
+    h2d(h->d_trow.as<int>(), trow, s);
+    h2d(h->d_far_nz.as<int>(), nz, s);
+}
+
+void load_dense_operator(rad_htree* h, const double* F_dev, cudaStream_t s) {
+    const int n = (int)h->n;
+    h->near_dtype = RAD_F64;
+    h->factor_dtype = RAD_F64;
+    h->near_h.assign(1, NearDesc{0, 0, n, n, 0});
+    h->far_h.clear();
+    h->near_block.assign(1, 0);
+    h->far_block.clear();
+    h->near_pool.alloc(sizeof(double) * (size_t)n * n);
+    h->far_pool.alloc(16 * sizeof(double));
+    const long long nn = (long long)n * n;
+    transpose_dense_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, F_dev, h->near_pool.as<double>());
+    RAD_CHECK_LAUNCH();
+    h->near_entries = nn;
+    h->far_entries = 0;
+    h->blocks.assign(1, BlockH{0, 0, 0, n, 0, n, 0, -1, 0});
+    finalize_operator(h, s);
+    RAD_CUDA(cudaStreamSynchronize(s));
+    h->compressed = true;
+}
+
+static void to_double(const void* src, int dt, size_t cnt, std::vector<double>& out) {
+    out.resize(cnt);
+    if (dt == RAD_F64) {
+        std::memcpy(out.data(), src, cnt * 8);
+    } else if (dt == RAD_F32) {
+        const float* f = static_cast<const float*>(src);
+        for (size_t i = 0; i < cnt; ++i) out[i] = f[i];
+    } else {
+        const uint16_t* b = static_cast<const uint16_t*>(src);
+        for (size_t i = 0; i < cnt; ++i) {
+            uint32_t bits = (uint32_t)b[i] << 16;
+            float f;
+            std::memcpy(&f, &bits, 4);
+            out[i] = f;
+        }
+    }
+}
+
+void export_block(const rad_htree* h, int64_t b, double* D, double* U, double* V) {
+    RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed");
+    RAD_REQUIRE(b >= 0 && b < (int64_t)h->blocks.size(), RAD_EINVAL, "block index out of range");
+    const BlockH& bk = h->blocks[b];
+    const int m = bk.r1 - bk.r0, n = bk.c1 - bk.c0;
+    std::vector<unsigned char> raw;
+    std::vector<double> cm;
+    if (bk.rank < 0) {
+        const NearDesc& d = h->near_h[bk.store_idx];
+        const int sz = dtype_size(h->near_dtype);
+        raw.resize((size_t)m * n * sz);
+        RAD_CUDA(cudaMemcpy(raw.data(), static_cast<const char*>(h->near_pool.p) + d.off * sz, raw.size(),
+                            cudaMemcpyDeviceToHost));
+        to_double(raw.data(), h->near_dtype, (size_t)m * n, cm);
+        if (D)
+            for (int i = 0; i < m; ++i)
+                for (int j = 0; j < n; ++j) D[(size_t)i * n + j] = cm[(size_t)j * m + i];
+    } else {
+        const FarDesc& f = h->far_h[bk.store_idx];
+        const int sz = dtype_size(h->factor_dtype);
+        const int k = f.k;
+        if (U && k) {
+            raw.resize((size_t)m * k * sz);
+            RAD_CUDA(cudaMemcpy(raw.data(), static_cast<const char*>(h->far_pool.p) + f.offU * sz, raw.size(),
+                                cudaMemcpyDeviceToHost));
+            to_double(raw.data(), h->factor_dtype, (size_t)m * k, cm);
+            for (int i = 0; i < m; ++i)
+                for (int l = 0; l < k; ++l) U[(size_t)i * k + l] = cm[(size_t)l * m + i];
+        }
+        if (V && k) {
+            raw.resize((size_t)n * k * sz);
+            RAD_CUDA(cudaMemcpy(raw.data(), static_cast<const char*>(h->far_pool.p) + f.offV * sz, raw.size(),
+                                cudaMemcpyDeviceToHost));
+            to_double(raw.data(), h->factor_dtype, (size_t)n * k, cm);
+            for (int j = 0; j < n; ++j)
+                for (int l = 0; l < k; ++l) V[(size_t)j * k + l] = cm[(size_t)l * n + j];
+        }
+    }
+}
+
+}  // namespace rad

@@ -1,0 +1,358 @@
+// C ABI entry points of librad (declared in include/rad.h).  Every entry
+// point catches all C++ exceptions and turns them into status codes.
+
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+
+#include "rad_common.cuh"
+
+namespace rad {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void fail(int code, const std::string& msg) { throw Error{code, msg}; }
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+void DevBuf::alloc(size_t b) {
+    release();
+    if (b == 0) return;
+    RAD_CUDA(cudaMalloc(&p, b));
+    bytes = b;
+}
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+Scratch::~Scratch() {
+    for (void* q : ptrs) cudaFreeAsync(q, s);
+}
+void* Scratch::get(size_t bytes) {
+    void* q = nullptr;
+    RAD_CUDA(cudaMallocAsync(&q, bytes ? bytes : 16, s));
+    ptrs.push_back(q);
+    return q;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+const void* to_device(const void* p, size_t bytes, Scratch& ws) {
+    if (is_device_ptr(p)) return p;
+    void* d = ws.get(bytes);
+    RAD_CUDA(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, ws.s));
+    return d;
+}
+
+// column-major (rows x cols, leading dim ld) host or device array -> compact
+// device copy with leading dim rows
+static const void* stage_in_2d(const void* p, int64_t rows, int64_t cols, int64_t ld, size_t esz, Scratch& ws) {
+    if (is_device_ptr(p)) return p;
+    void* d = ws.get(esz * rows * cols);
+    RAD_CUDA(cudaMemcpy2DAsync(d, esz * rows, p, esz * ld, esz * rows, cols, cudaMemcpyHostToDevice, ws.s));
+    return d;
+}
+
+template <class F>
+static int guarded(F&& f) {
+    try {
+        f();
+        return RAD_OK;
+    } catch (const Error& e) {
+        g_last_error = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return RAD_ENOMEM;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return RAD_ECUDA;
+    } catch (...) {
+        g_last_error = "unknown error";
+        return RAD_ECUDA;
+    }
+}
+
+static void check_tree_params(int64_t n, const rad_tree_params* p) {
+    RAD_REQUIRE(p != nullptr, RAD_EINVAL, "null tree params");
+    RAD_REQUIRE(n >= 1 && n < (int64_t)(INT_MAX / 8), RAD_EINVAL, "n must be in [1, 2^28)");
+    RAD_REQUIRE(p->leaf_size >= 1, RAD_EINVAL, "leaf_size must be >= 1");
+    RAD_REQUIRE(std::isfinite(p->eta_adm) && p->eta_adm > 0.0, RAD_EINVAL, "eta_adm must be > 0");
+}
+
+}  // namespace rad
+
+using namespace rad;
+
+extern "C" {
+
+int rad_version(void) { return 10000; }
+
+const char* rad_last_error(void) { return g_last_error.c_str(); }
+
+int rad_build_htree(int64_t n, const double* verts, const rad_tree_params* p, void* stream, rad_htree** out) {
+    return guarded([&] {
+        RAD_REQUIRE(out != nullptr && verts != nullptr, RAD_EINVAL, "null argument");
+        *out = nullptr;
+        check_tree_params(n, p);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        auto h = std::make_unique<rad_htree>();
+        h->n = n;
+        h->leaf_size = p->leaf_size;
+        h->eta = p->eta_adm;
+        RAD_CUDA(cudaGetDevice(&h->device));
+        Scratch ws(s);
+        const double* v = to_device_t(verts, 9 * (size_t)n, ws);
+        double* geo_user = ws.get_n<double>(7 * (size_t)n);
+        build_geometry_from_tris(h.get(), v, geo_user, s);
+        build_trees(h.get(), geo_user, s);
+        RAD_CUDA(cudaStreamSynchronize(s));
+        *out = h.release();
+    });
+}
+
+int rad_build_htree_facets(int64_t n, const double* centroid, const double* normal, const double* area,
+                           const rad_tree_params* p, void* stream, rad_htree** out) {
+    return guarded([&] {
+        RAD_REQUIRE(out != nullptr && centroid && normal && area, RAD_EINVAL, "null argument");
+        *out = nullptr;
+        check_tree_params(n, p);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        auto h = std::make_unique<rad_htree>();
+        h->n = n;
+        h->leaf_size = p->leaf_size;
+        h->eta = p->eta_adm;
+        RAD_CUDA(cudaGetDevice(&h->device));
+        Scratch ws(s);
+        const double* c = to_device_t(centroid, 3 * (size_t)n, ws);
+        const double* nr = to_device_t(normal, 3 * (size_t)n, ws);
+        const double* a = to_device_t(area, (size_t)n, ws);
+        double* geo_user = ws.get_n<double>(7 * (size_t)n);
+        build_geometry_from_facets(h.get(), c, nr, a, geo_user, s);
+        build_trees(h.get(), geo_user, s);
+        RAD_CUDA(cudaStreamSynchronize(s));
+        *out = h.release();
+    });
+}
+
+int rad_htree_from_dense(int64_t n, const double* F, void* stream, rad_htree** out) {
+    return guarded([&] {
+        RAD_REQUIRE(out != nullptr && F != nullptr, RAD_EINVAL, "null argument");
+        *out = nullptr;
+        RAD_REQUIRE(n >= 1 && n <= 46340, RAD_EINVAL, "n must be in [1, 46340]");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        auto h = std::make_unique<rad_htree>();
+        h->n = n;
+        h->leaf_size = (int)n;
+        h->eta = 1.0;
+        h->from_dense = true;
+        RAD_CUDA(cudaGetDevice(&h->device));
+        h->nodes.assign(1, NodeShape{0, (int)n, 0, -1, -1, 1});
+        h->boxes.assign(1, NodeBox{{0, 0, 0}, {0, 0, 0}});
+        h->depth = 1;
+        h->perm_h.resize(n);
+        for (int i = 0; i < (int)n; ++i) h->perm_h[i] = i;
+        h->perm.alloc(sizeof(int) * n);
+        h->iperm.alloc(sizeof(int) * n);
+        h2d(h->perm.as<int>(), h->perm_h, s);
+        h2d(h->iperm.as<int>(), h->perm_h, s);
+        Scratch ws(s);
+        const double* Fd = to_device_t(F, (size_t)n * n, ws);
+        load_dense_operator(h.get(), Fd, s);
+        *out = h.release();
+    });
+}
+
+int rad_compress_aca(rad_htree* h, const rad_aca_params* p, void* stream) {
+    return guarded([&] {
+        RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null handle");
+        compress(h, p, static_cast<cudaStream_t>(stream));
+    });
+}
+
+int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx, void* y, int64_t ldy, int64_t nrhs,
+                void* stream) {
+    return guarded([&] {
+        RAD_REQUIRE(h != nullptr && x != nullptr && y != nullptr, RAD_EINVAL, "null argument");
+        RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed (call rad_compress_aca)");
+        RAD_REQUIRE(dtype == RAD_F64 || dtype == RAD_F32, RAD_EINVAL, "dtype must be RAD_F64 or RAD_F32");
+        RAD_REQUIRE(nrhs >= 1 && nrhs <= 4096, RAD_EINVAL, "nrhs must be in [1, 4096]");
+        RAD_REQUIRE(ldx >= h->n && ldy >= h->n, RAD_EINVAL, "leading dimension smaller than n");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const int n = (int)h->n;
+        const int nr = (int)nrhs;
+        const size_t esz = dtype == RAD_F64 ? 8 : 4;
+        const bool op64 = h->op_is_f64();
+        const size_t osz = op64 ? 8 : 4;
+        Scratch ws(s);
+        const void* xd = stage_in_2d(x, n, nr, ldx, esz, ws);
+        const int64_t ldxd = is_device_ptr(x) ? ldx : n;
+        void* X = ws.get(osz * n * nr);
+        void* Y = ws.get(osz * n * nr);
+        void* T = ws.get(apply_workspace_bytes(h, nr));
+        gather_user_to_tree(h, dtype, xd, ldxd, nr, X, nr, op64, s);
+        apply_tree(h, X, nr, Y, nr, nr, Epi{kStore, nullptr, nullptr, nullptr, 0}, T, s);
+        if (is_device_ptr(y)) {
+            scatter_tree_to_user(h, Y, nr, nr, op64, dtype, y, ldy, s);
+        } else {
+            void* yd = ws.get(esz * n * nr);
+            scatter_tree_to_user(h, Y, nr, nr, op64, dtype, yd, n, s);
+            RAD_CUDA(cudaMemcpy2DAsync(y, esz * ldy, yd, esz * n, esz * n, nr, cudaMemcpyDeviceToHost, s));
+            RAD_CUDA(cudaStreamSynchronize(s));
+        }
+    });
+}
+
+int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64_t ldT, int64_t m, double sigma,
+                   const rad_solve_params* p, double* q, int64_t ldq, rad_solve_info* info, void* stream) {
+    int solve_status = RAD_OK;
+    const int rc = guarded([&] {
+        RAD_REQUIRE(h != nullptr && eps && T && q && p, RAD_EINVAL, "null argument");
+        RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed (call rad_compress_aca)");
+        RAD_REQUIRE(m >= 1 && m <= 1024, RAD_EINVAL, "m must be in [1, 1024]");
+        RAD_REQUIRE(ldT >= h->n && ldq >= h->n, RAD_EINVAL, "leading dimension smaller than n");
+        RAD_REQUIRE(p->restart >= 1 && p->restart <= 64, RAD_EINVAL, "restart must be in [1, 64]");
+        RAD_REQUIRE(p->max_iter >= 1, RAD_EINVAL, "max_iter must be >= 1");
+        RAD_REQUIRE(p->tol > 0.0 && std::isfinite(p->tol), RAD_EINVAL, "tol must be > 0");
+        RAD_REQUIRE(std::isfinite(sigma), RAD_EINVAL, "sigma must be finite");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const int n = (int)h->n;
+        Scratch ws(s);
+        const double* epsd = to_device_t(eps, (size_t)n, ws);
+        const double* Td = static_cast<const double*>(stage_in_2d(T, n, m, ldT, 8, ws));
+        const int64_t ldTd = is_device_ptr(T) ? ldT : n;
+        const bool qdev = is_device_ptr(q);
+        double* qd = qdev ? q : ws.get_n<double>((size_t)n * m);
+        rad_solve_info local{};
+        solve_flux(h, epsd, Td, ldTd, (int)m, sigma, p, qd, qdev ? ldq : n, &local, s);
+        if (!qdev) {
+            RAD_CUDA(cudaMemcpy2DAsync(q, 8 * ldq, qd, 8 * (size_t)n, 8 * (size_t)n, m, cudaMemcpyDeviceToHost, s));
+            RAD_CUDA(cudaStreamSynchronize(s));
+        }
+        if (info) *info = local;
+        solve_status = local.status;
+        if (solve_status != RAD_OK) set_last_error("GMRES did not reach the tolerance");
+    });
+    return rc != RAD_OK ? rc : solve_status;
+}
+
+int rad_solve_reflection(const rad_htree* h, const double* eps, const double* B, int64_t ldB, int64_t nrhs,
+                         const rad_solve_params* p, double* Y, int64_t ldY, rad_solve_info* info, void* stream) {
+    int solve_status = RAD_OK;
+    const int rc = guarded([&] {
+        RAD_REQUIRE(h != nullptr && eps && B && Y && p, RAD_EINVAL, "null argument");
+        RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed (call rad_compress_aca)");
+        RAD_REQUIRE(nrhs >= 1 && nrhs <= 1024, RAD_EINVAL, "nrhs must be in [1, 1024]");
+        RAD_REQUIRE(ldB >= h->n && ldY >= h->n, RAD_EINVAL, "leading dimension smaller than n");
+        RAD_REQUIRE(p->restart >= 1 && p->restart <= 64, RAD_EINVAL, "restart must be in [1, 64]");
+        RAD_REQUIRE(p->max_iter >= 1, RAD_EINVAL, "max_iter must be >= 1");
+        RAD_REQUIRE(p->tol > 0.0 && std::isfinite(p->tol), RAD_EINVAL, "tol must be > 0");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const int n = (int)h->n;
+        Scratch ws(s);
+        const double* epsd = to_device_t(eps, (size_t)n, ws);
+        const double* Bd = static_cast<const double*>(stage_in_2d(B, n, nrhs, ldB, 8, ws));
+        const int64_t ldBd = is_device_ptr(B) ? ldB : n;
+        const bool ydev = is_device_ptr(Y);
+        double* Yd = ydev ? Y : ws.get_n<double>((size_t)n * nrhs);
+        rad_solve_info local{};
+        solve_reflection(h, epsd, Bd, ldBd, (int)nrhs, p, Yd, ydev ? ldY : n, &local, s);
+        if (!ydev) {
+            RAD_CUDA(cudaMemcpy2DAsync(Y, 8 * ldY, Yd, 8 * (size_t)n, 8 * (size_t)n, nrhs, cudaMemcpyDeviceToHost, s));
+            RAD_CUDA(cudaStreamSynchronize(s));
+        }
+        if (info) *info = local;
+        solve_status = local.status;
+        if (solve_status != RAD_OK) set_last_error("GMRES did not reach the tolerance");
+    });
+    return rc != RAD_OK ? rc : solve_status;
+}
+
+int rad_htree_get_stats(const rad_htree* h, rad_htree_stats* st) {
+    return guarded([&] {
+        RAD_REQUIRE(h != nullptr && st != nullptr, RAD_EINVAL, "null argument");
+        std::memset(st, 0, sizeof(*st));
+        st->n = h->n;
+        st->leaf_size = h->leaf_size;
+        st->n_nodes = (int32_t)h->nodes.size();
+        int leaves = 0;
+        for (auto& nd : h->nodes) leaves += nd.leaf;
+        st->n_leaf_clusters = leaves;
+        st->depth = h->depth;
+        st->n_blocks = (int64_t)h->blocks.size();
+        st->n_admissible = h->n_admissible;
+        st->compressed = h->compressed ? 1 : 0;
+        st->factor_dtype = h->factor_dtype;
+        st->near_dtype = h->near_dtype;
+        st->max_rank_used = h->max_rank_used;
+        st->n_dense_fallback = h->n_dense_fallback;
+        st->near_entries = h->near_entries;
+        st->far_entries = h->far_entries;
+        st->sum_rank = h->sum_rank;
+        st->aca_entries = h->aca_entries;
+        st->bytes_near = h->near_entries * dtype_size(h->near_dtype);
+        st->bytes_far = h->far_entries * dtype_size(h->factor_dtype);
+    });
+}
+
+int rad_htree_export_tree(const rad_htree* h, int32_t* perm, int32_t* begin, int32_t* end, int32_t* level,
+                          int32_t* child, double* bbox) {
+    return guarded([&] {
+        RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null handle");
+        if (perm) std::memcpy(perm, h->perm_h.data(), sizeof(int32_t) * h->perm_h.size());
+        for (size_t q = 0; q < h->nodes.size(); ++q) {
+            const NodeShape& nd = h->nodes[q];
+            if (begin) begin[q] = nd.begin;
+            if (end) end[q] = nd.end;
+            if (level) level[q] = nd.level;
+            if (child) {
+                child[2 * q] = nd.child0;
+                child[2 * q + 1] = nd.child1;
+            }
+            if (bbox)
+                for (int k = 0; k < 3; ++k) {
+                    bbox[6 * q + k] = h->boxes[q].lo[k];
+                    bbox[6 * q + 3 + k] = h->boxes[q].hi[k];
+                }
+        }
+    });
+}
+
+int rad_htree_export_blocks(const rad_htree* h, int32_t* row_node, int32_t* col_node, int32_t* admissible,
+                            int32_t* rank) {
+    return guarded([&] {
+        RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null handle");
+        for (size_t b = 0; b < h->blocks.size(); ++b) {
+            const BlockH& bk = h->blocks[b];
+            if (row_node) row_node[b] = bk.row_node;
+            if (col_node) col_node[b] = bk.col_node;
+            if (admissible) admissible[b] = bk.admissible;
+            if (rank) rank[b] = bk.rank;
+        }
+    });
+}
+
+int rad_htree_export_block(const rad_htree* h, int64_t block, double* D, double* U, double* V) {
+    return guarded([&] {
+        RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null handle");
+        export_block(h, block, D, U, V);
+    });
+}
+
+int rad_htree_free(rad_htree* h) {
+    return guarded([&] { delete h; });
+}
+
+}  // extern "C"

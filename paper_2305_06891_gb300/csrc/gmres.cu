@@ -1,0 +1,417 @@
+// A7-A8: batched restarted GMRES on the reflection system of Eq. (11),
+//   C y = b,  C = I - diag(1 - eps) F,
+// for the m + 1 right-hand sides b_c = eps o eta_c (c < m) and b_m = eps,
+// followed by the facet flux of Eq. (12):
+//   q_c = sigma eps o ( F y_c - eta_c o F z ),  z = y_m.
+//
+// All vectors are FP64, in tree order, row-major N x (m+1) so that one block
+// matrix product serves every column at once.  Each Arnoldi step is one
+// product with the reflection epilogue fused in, two classical Gram-Schmidt
+// passes (CGS2) with FP64 inner products reduced in a fixed order, a norm, a
+// normalisation (which also writes the FP32 copy the FP32 operator reads)
+// and a Givens update done on the device per column.  Only the per-column
+// residual estimates cross to the host each step.  A column stops when its
+// estimate reaches tol; every restart recomputes the true residual
+// b - C y with the stored operator.
+
+#include <algorithm>
+#include <cmath>
+
+#include "rad_device.cuh"
+
+namespace rad {
+
+namespace {
+
+constexpr int kChunkRows = 256;
+
+__global__ void rhs_kernel(int n, int m, const double* __restrict__ eps, const double* __restrict__ T, long long ldT,
+                           const int* __restrict__ perm, double* __restrict__ eps_t, double* __restrict__ B) {
+    const int nc = m + 1;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n * nc) return;
+    const int p = (int)(e / nc), c = (int)(e - (long long)p * nc);
+    const int u = perm[p];
+    const double ep = eps[u];
+    if (c < m) {
+        const double t = T[u + (long long)c * ldT];
+        B[e] = ep * ((t * t) * (t * t));
+    } else {
+        B[e] = ep;
+        eps_t[p] = ep;
+    }
+}
+
+// partial[(chunk * L + l) * nc + c] = sum over the chunk's rows of
+// A_l[i][c] * Bv[i][c],  A_l = A + l * strideA.
+__global__ void __launch_bounds__(256)
+mdot_kernel(const double* __restrict__ A, long long strideA, int L, const double* __restrict__ Bv, int n, int nc,
+            double* __restrict__ partial) {
+    __shared__ double red[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int c = blockIdx.y * 32 + tx;
+    const int r0 = blockIdx.x * kChunkRows;
+    const int r1 = min(n, r0 + kChunkRows);
+    for (int l0 = 0; l0 < L; l0 += 4) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        if (c < nc) {
+            for (int i = r0 + ty; i < r1; i += 8) {
+                const double bv = Bv[(long long)i * nc + c];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (l0 + q < L) acc[q] += A[(l0 + q) * strideA + (long long)i * nc + c] * bv;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            red[ty][tx] = acc[q];
+            __syncthreads();
+            if (ty == 0 && l0 + q < L && c < nc) {
+                double s = 0.0;
+                for (int w = 0; w < 8; ++w) s += red[w][tx];
+                partial[((long long)blockIdx.x * L + l0 + q) * nc + c] = s;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// out[l * nc + c] (+)= sum_chunk partial[chunk][l][c]   (fixed order)
+__global__ void reduce_chunks_kernel(const double* __restrict__ partial, int chunks, int L, int nc, double* out,
+                                     int accumulate) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= L * nc) return;
+    double s = 0.0;
+    for (int k = 0; k < chunks; ++k) s += partial[(long long)k * L * nc + e];
+    out[e] = accumulate ? out[e] + s : s;
+}
+
+// W[i][c] -= sum_{l<L} V_l[i][c] h[l][c]   for active columns
+__global__ void cgs_update_kernel(const double* __restrict__ V, long long strideV, int L, const double* __restrict__ h,
+                                  const int* __restrict__ active, double* __restrict__ W, int n, int nc) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n * nc) return;
+    const int c = (int)(e % nc);
+    if (!active[c]) return;
+    double w = W[e];
+    for (int l = 0; l < L; ++l) w -= V[l * strideV + e] * h[l * nc + c];
+    W[e] = w;
+}
+
+// V_next = W / hn (active columns with hn > 0), else 0; optional FP32 copy.
+__global__ void normalize_kernel(const double* __restrict__ W, const double* __restrict__ hn2,
+                                 const int* __restrict__ active, double* __restrict__ Vn, float* __restrict__ X32,
+                                 int n, int nc) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n * nc) return;
+    const int c = (int)(e % nc);
+    const double hn = sqrt(hn2[c]);
+    const double v = (active[c] && hn > 0.0) ? W[e] / hn : 0.0;
+    Vn[e] = v;
+    if (X32) X32[e] = (float)v;
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, long long cnt) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < cnt) b[e] = (float)a[e];
+}
+
+// Per column: apply the previous Givens rotations to the new Hessenberg
+// column, form the next rotation, update g and the residual estimate.
+// Hm layout: Hm[(j * (R + 1) + l) * nc + c] = H(l, j).
+__global__ void givens_kernel(int j, int R, int nc, double* __restrict__ Hm, const double* __restrict__ hn2,
+                              double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                              const double* __restrict__ bnorm, double* __restrict__ resid, int* __restrict__ active,
+                              int* __restrict__ jc, double tol) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc || !active[c]) return;
+    double* hcol = Hm + (long long)j * (R + 1) * nc;
+    for (int i = 0; i < j; ++i) {
+        const double a = hcol[i * nc + c], b = hcol[(i + 1) * nc + c];
+        const double C = cs[i * nc + c], S = sn[i * nc + c];
+        hcol[i * nc + c] = C * a + S * b;
+        hcol[(i + 1) * nc + c] = -S * a + C * b;
+    }
+    const double a = hcol[j * nc + c];
+    const double b = sqrt(hn2[c]);
+    const double r = hypot(a, b);
+    double C = 1.0, S = 0.0;
+    if (r > 0.0) {
+        C = a / r;
+        S = b / r;
+    }
+    cs[j * nc + c] = C;
+    sn[j * nc + c] = S;
+    hcol[j * nc + c] = r;
+    const double gj = g[j * nc + c];
+    g[(j + 1) * nc + c] = -S * gj;
+    g[j * nc + c] = C * gj;
+    const double res = fabs(g[(j + 1) * nc + c]) / bnorm[c];
+    resid[c] = res;
+    jc[c] = j + 1;
+    if (!(res > tol) || !(b > 0.0)) active[c] = 0;
+}
+
+// y = R^-1 g per column (R upper triangular, jc[c] x jc[c]).
+__global__ void trisolve_kernel(int R, int nc, const double* __restrict__ Hm, const double* __restrict__ g,
+                                const int* __restrict__ jc, double* __restrict__ ycoef) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const int J = jc[c];
+    for (int i = J - 1; i >= 0; --i) {
+        double s = g[i * nc + c];
+        for (int k = i + 1; k < J; ++k) s -= Hm[((long long)k * (R + 1) + i) * nc + c] * ycoef[k * nc + c];
+        const double d = Hm[((long long)i * (R + 1) + i) * nc + c];
+        ycoef[i * nc + c] = d != 0.0 ? s / d : 0.0;
+    }
+}
+
+// X[i][c] += sum_{l < jc[c]} V_l[i][c] y[l][c]
+__global__ void update_x_kernel(const double* __restrict__ V, long long strideV, int Lmax,
+                                const double* __restrict__ ycoef, const int* __restrict__ jc, double* __restrict__ X,
+                                int n, int nc) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n * nc) return;
+    const int c = (int)(e % nc);
+    const int J = min(jc[c], Lmax);
+    double x = X[e];
+    for (int l = 0; l < J; ++l) x += V[l * strideV + e] * ycoef[l * nc + c];
+    X[e] = x;
+}
+
+// start a cycle: V_0 = R / beta for active columns, g = beta e_1
+__global__ void start_cycle_kernel(const double* __restrict__ Rv, const double* __restrict__ beta2,
+                                   const int* __restrict__ active, double* __restrict__ V0, float* __restrict__ X32,
+                                   int n, int nc) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n * nc) return;
+    const int c = (int)(e % nc);
+    const double b = sqrt(beta2[c]);
+    const double v = (active[c] && b > 0.0) ? Rv[e] / b : 0.0;
+    V0[e] = v;
+    if (X32) X32[e] = (float)v;
+}
+
+__global__ void init_g_kernel(int R, int nc, const double* __restrict__ beta2, double* __restrict__ g,
+                              int* __restrict__ jc) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    for (int l = 0; l <= R; ++l) g[l * nc + c] = 0.0;
+    g[c] = sqrt(beta2[c]);
+    jc[c] = 0;
+}
+
+template <class FT>
+__global__ void flux_kernel(int n, int m, const FT* __restrict__ FY, const int* __restrict__ perm,
+                            const double* __restrict__ eps, const double* __restrict__ T, long long ldT, double sigma,
+                            double* __restrict__ q, long long ldq) {
+    const int nc = m + 1;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n * m) return;
+    const int p = (int)(e / m), c = (int)(e - (long long)p * m);
+    const int u = perm[p];
+    const double t = T[u + (long long)c * ldT];
+    const double eta = (t * t) * (t * t);
+    q[u + (long long)c * ldq] =
+        sigma * eps[u] * ((double)FY[(long long)p * nc + c] - eta * (double)FY[(long long)p * nc + m]);
+}
+
+inline unsigned grid_for(long long cnt, int bs = 256) { return (unsigned)((cnt + bs - 1) / bs); }
+
+struct ColReducer {
+    int n, nc, chunks;
+    double* partial;
+    cudaStream_t s;
+    // out[l][c] (+)= sum_i A_l[i][c] Bv[i][c]
+    void dots(const double* A, long long strideA, int L, const double* Bv, double* out, bool accumulate) {
+        dim3 grid(chunks, (nc + 31) / 32);
+        mdot_kernel<<<grid, 256, 0, s>>>(A, strideA, L, Bv, n, nc, partial);
+        RAD_CHECK_LAUNCH();
+        reduce_chunks_kernel<<<grid_for((long long)L * nc), 256, 0, s>>>(partial, chunks, L, nc, out,
+                                                                          accumulate ? 1 : 0);
+        RAD_CHECK_LAUNCH();
+    }
+};
+
+}  // namespace
+
+// GMRES on C X = B in tree order (row-major N x nc).  X receives the solution.
+static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B, int nc, const rad_solve_params* p,
+                       double* X, rad_solve_info* info, Scratch& ws, cudaStream_t s) {
+    const int n = (int)h->n;
+    const int R = p->restart;
+    const double tol = p->tol;
+    const bool op64 = h->op_is_f64();
+    const long long nv = (long long)n * nc;
+    double* W = ws.get_n<double>(nv);
+    double* V = ws.get_n<double>(nv * (R + 1));
+    float* X32 = op64 ? nullptr : ws.get_n<float>(nv);
+    void* Tws = ws.get(apply_workspace_bytes(h, nc));
+    double* Hm = ws.get_n<double>((long long)R * (R + 1) * nc);
+    double* cs = ws.get_n<double>((long long)R * nc);
+    double* sn = ws.get_n<double>((long long)R * nc);
+    double* g = ws.get_n<double>((long long)(R + 1) * nc);
+    double* ycoef = ws.get_n<double>((long long)R * nc);
+    double* bnorm2 = ws.get_n<double>(nc);
+    double* bnorm = ws.get_n<double>(nc);
+    double* beta2 = ws.get_n<double>(nc);
+    double* hn2 = ws.get_n<double>(nc);
+    double* resid = ws.get_n<double>(nc);
+    int* active = ws.get_n<int>(nc);
+    int* jc = ws.get_n<int>(nc);
+    const int chunks = (n + kChunkRows - 1) / kChunkRows;
+    ColReducer red{n, nc, chunks, ws.get_n<double>((long long)chunks * (R + 1) * nc), s};
+
+    RAD_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * nv, s));
+    red.dots(B, 0, 1, B, bnorm2, false);
+    std::vector<double> hb2(nc), hbeta(nc);
+    RAD_CUDA(cudaMemcpyAsync(hb2.data(), bnorm2, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    RAD_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> hbn(nc);
+    for (int c = 0; c < nc; ++c) hbn[c] = hb2[c] > 0.0 ? std::sqrt(hb2[c]) : 1.0;
+    RAD_CUDA(cudaMemcpyAsync(bnorm, hbn.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, s));
+    // initial residual = B (x0 = 0)
+    RAD_CUDA(cudaMemcpyAsync(W, B, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+    RAD_CUDA(cudaMemcpyAsync(beta2, bnorm2, sizeof(double) * nc, cudaMemcpyDeviceToDevice, s));
+    hbeta = hb2;
+
+    auto apply_C = [&](const double* vin, const float* vin32, double* out, int mode) {
+        Epi epi{mode, eps_t, vin, mode == kResid ? B : nullptr, nc};
+        apply_tree(h, op64 ? (const void*)vin : (const void*)vin32, nc, out, nc, nc, epi, Tws, s);
+    };
+
+    int total_iters = 0, restarts = 0, matvecs = 0, status = RAD_OK;
+    double prev_max = INFINITY, max_rel = 0.0;
+    std::vector<int> hact(nc);
+    for (;;) {
+        // columns still above tolerance take part in this cycle
+        max_rel = 0.0;
+        int n_act = 0;
+        for (int c = 0; c < nc; ++c) {
+            const double rel = std::sqrt(std::max(hbeta[c], 0.0)) / hbn[c];
+            max_rel = std::max(max_rel, rel);
+            hact[c] = rel > tol ? 1 : 0;
+            n_act += hact[c];
+        }
+        if (n_act == 0) break;
+        if (total_iters >= p->max_iter || !(max_rel < 0.9 * prev_max)) {
+            status = RAD_ENOTCONV;
+            break;
+        }
+        prev_max = max_rel;
+        RAD_CUDA(cudaMemcpyAsync(active, hact.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+        start_cycle_kernel<<<grid_for(nv), 256, 0, s>>>(W, beta2, active, V, X32, n, nc);
+        RAD_CHECK_LAUNCH();
+        init_g_kernel<<<grid_for(nc), 128, 0, s>>>(R, nc, beta2, g, jc);
+        RAD_CHECK_LAUNCH();
+        for (int j = 0; j < R && total_iters < p->max_iter; ++j) {
+            double* Vj = V + (long long)j * nv;
+            double* hcol = Hm + (long long)j * (R + 1) * nc;
+            // w = C v_j
+            apply_C(Vj, X32, W, kReflect);
+            ++matvecs;
+            // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2
+            for (int pass = 0; pass < 2; ++pass) {
+                double* hbuf = pass == 0 ? hcol : ycoef;  // ycoef doubles as scratch here
+                red.dots(V, nv, j + 1, W, hbuf, false);
+                cgs_update_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, j + 1, hbuf, active, W, n, nc);
+                RAD_CHECK_LAUNCH();
+                if (pass == 1) {
+                    reduce_chunks_kernel<<<grid_for((long long)(j + 1) * nc), 256, 0, s>>>(ycoef, 1, j + 1, nc,
+                                                                                            hcol, 1);
+                    RAD_CHECK_LAUNCH();
+                }
+            }
+            red.dots(W, 0, 1, W, hn2, false);
+            normalize_kernel<<<grid_for(nv), 256, 0, s>>>(W, hn2, active, V + (long long)(j + 1) * nv, X32, n, nc);
+            RAD_CHECK_LAUNCH();
+            givens_kernel<<<grid_for(nc, 128), 128, 0, s>>>(j, R, nc, Hm, hn2, cs, sn, g, bnorm, resid, active, jc,
+                                                            tol);
+            RAD_CHECK_LAUNCH();
+            ++total_iters;
+            RAD_CUDA(cudaMemcpyAsync(hact.data(), active, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+            RAD_CUDA(cudaStreamSynchronize(s));
+            int still = 0;
+            for (int c = 0; c < nc; ++c) still += hact[c];
+            if (still == 0) break;
+        }
+        // x += V y
+        trisolve_kernel<<<grid_for(nc, 128), 128, 0, s>>>(R, nc, Hm, g, jc, ycoef);
+        RAD_CHECK_LAUNCH();
+        update_x_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, R, ycoef, jc, X, n, nc);
+        RAD_CHECK_LAUNCH();
+        // true residual r = b - C x
+        if (X32) {
+            to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(X, X32, nv);
+            RAD_CHECK_LAUNCH();
+        }
+        apply_C(X, X32, W, kResid);
+        ++matvecs;
+        red.dots(W, 0, 1, W, beta2, false);
+        RAD_CUDA(cudaMemcpyAsync(hbeta.data(), beta2, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+        RAD_CUDA(cudaStreamSynchronize(s));
+        ++restarts;
+    }
+    if (info) {
+        info->status = status;
+        info->iters = total_iters;
+        info->restarts = restarts;
+        info->matvecs = matvecs;
+        info->max_rel_residual = max_rel;
+    }
+}
+
+void solve_flux(const rad_htree* h, const double* eps_dev, const double* T_dev, int64_t ldT, int m, double sigma,
+                const rad_solve_params* p, double* q_dev, int64_t ldq, rad_solve_info* info, cudaStream_t s) {
+    const int n = (int)h->n;
+    const int nc = m + 1;
+    const bool op64 = h->op_is_f64();
+    const long long nv = (long long)n * nc;
+    Scratch ws(s);
+    double* eps_t = ws.get_n<double>(n);
+    double* B = ws.get_n<double>(nv);
+    double* X = ws.get_n<double>(nv);
+    rhs_kernel<<<grid_for(nv), 256, 0, s>>>(n, m, eps_dev, T_dev, ldT, h->perm.as<int>(), eps_t, B);
+    RAD_CHECK_LAUNCH();
+    rad_solve_info local{};
+    gmres_tree(h, eps_t, B, nc, p, X, &local, ws, s);
+    // flux, Eq. (12): FY = F [Y z]
+    void* Tws = ws.get(apply_workspace_bytes(h, nc));
+    if (op64) {
+        double* FY = ws.get_n<double>(nv);
+        apply_tree(h, X, nc, FY, nc, nc, Epi{kStore, nullptr, nullptr, nullptr, 0}, Tws, s);
+        flux_kernel<double><<<grid_for((long long)n * m), 256, 0, s>>>(n, m, FY, h->perm.as<int>(), eps_dev, T_dev,
+                                                                      ldT, sigma, q_dev, ldq);
+    } else {
+        float* X32 = ws.get_n<float>(nv);
+        float* FY = ws.get_n<float>(nv);
+        to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(X, X32, nv);
+        RAD_CHECK_LAUNCH();
+        apply_tree(h, X32, nc, FY, nc, nc, Epi{kStore, nullptr, nullptr, nullptr, 0}, Tws, s);
+        flux_kernel<float><<<grid_for((long long)n * m), 256, 0, s>>>(n, m, FY, h->perm.as<int>(), eps_dev, T_dev,
+                                                                     ldT, sigma, q_dev, ldq);
+    }
+    RAD_CHECK_LAUNCH();
+    ++local.matvecs;
+    RAD_CUDA(cudaStreamSynchronize(s));
+    if (info) *info = local;
+}
+
+void solve_reflection(const rad_htree* h, const double* eps_dev, const double* B_dev, int64_t ldB, int nrhs,
+                      const rad_solve_params* p, double* Y_dev, int64_t ldY, rad_solve_info* info, cudaStream_t s) {
+    const int n = (int)h->n;
+    const long long nv = (long long)n * nrhs;
+    Scratch ws(s);
+    double* eps_t = ws.get_n<double>(n);
+    double* B = ws.get_n<double>(nv);
+    double* X = ws.get_n<double>(nv);
+    gather_user_to_tree(h, RAD_F64, eps_dev, n, 1, eps_t, 1, true, s);
+    gather_user_to_tree(h, RAD_F64, B_dev, ldB, nrhs, B, nrhs, true, s);
+    rad_solve_info local{};
+    gmres_tree(h, eps_t, B, nrhs, p, X, &local, ws, s);
+    scatter_tree_to_user(h, X, nrhs, nrhs, true, RAD_F64, Y_dev, ldY, s);
+    RAD_CUDA(cudaStreamSynchronize(s));
+    if (info) *info = local;
+}
+
+}  // namespace rad

@@ -1,0 +1,248 @@
+// Internal declarations shared by the librad translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "rad.h"
+
+namespace rad {
+
+// ------------------------------------------------------------ error plumbing
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg);
+void set_last_error(const std::string& msg);
+
+#define RAD_CUDA(call)                                                            \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            (void)cudaGetLastError();                                             \
+            ::rad::fail(e_ == cudaErrorMemoryAllocation ? RAD_ENOMEM : RAD_ECUDA, \
+                        std::string(#call) + " -> " + cudaGetErrorString(e_));    \
+        }                                                                         \
+    } while (0)
+
+#define RAD_CHECK_LAUNCH() RAD_CUDA(cudaGetLastError())
+
+#define RAD_REQUIRE(cond, code, msg)          \
+    do {                                      \
+        if (!(cond)) ::rad::fail(code, msg);  \
+    } while (0)
+
+// ------------------------------------------------------------ memory helpers
+// A device buffer owned by a handle; released with cudaFree.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void alloc(size_t b);
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Per-call stream-ordered workspace; everything is freed (stream-ordered)
+// when the object goes out of scope.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    Scratch(const Scratch&) = delete;
+    ~Scratch();
+    void* get(size_t bytes);
+    template <class T> T* get_n(size_t n) { return static_cast<T*>(get(n * sizeof(T))); }
+};
+
+bool is_device_ptr(const void* p);
+// Returns a device copy of `count` elements of a host or device array.
+const void* to_device(const void* p, size_t bytes, Scratch& ws);
+template <class T>
+const T* to_device_t(const T* p, size_t n, Scratch& ws) {
+    return static_cast<const T*>(to_device(p, n * sizeof(T), ws));
+}
+template <class T>
+void h2d(T* dst, const std::vector<T>& v, cudaStream_t s) {
+    if (!v.empty()) RAD_CUDA(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+}
+
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+inline int dtype_size(int dt) { return dt == RAD_F64 ? 8 : dt == RAD_F32 ? 4 : 2; }
+
+// ------------------------------------------------------------ data layout
+// Facet geometry in tree order, structure of arrays (7 x n doubles):
+// cx, cy, cz, nx, ny, nz, area.
+struct Geo {
+    const double* cx;
+    const double* cy;
+    const double* cz;
+    const double* nx;
+    const double* ny;
+    const double* nz;
+    const double* area;
+};
+inline Geo geo_view(const double* base, int64_t n) {
+    return Geo{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n, base + 6 * n};
+}
+
+// Cluster shape (fixed by n and leaf_size) plus its bounding box.
+struct NodeShape {
+    int begin, end, level, child0, child1, leaf;
+};
+struct NodeBox {
+    double lo[3], hi[3];
+};
+
+// Dense block: rows [r0, r0+m), cols [c0, c0+n), column-major m x n at off.
+struct NearDesc {
+    int r0, c0, m, n;
+    long long off;
+};
+// Low-rank block: U column-major m x k at offU, V column-major n x k at offV;
+// its V^T x lives at rows [toff, toff+k) of the T workspace.
+struct FarDesc {
+    int r0, c0, m, n, k, toff;
+    long long offU, offV;
+};
+// Row tile: rows [r0, r0+rows) (rows <= 64) and its entries [e0, e1).
+struct TileDesc {
+    int r0, rows, e0, e1;
+};
+// Tile entry: x = block id (bit 31 set for a low-rank block), y = row offset
+// of the tile inside the block.
+constexpr int kFarBit = int(0x80000000u);
+
+constexpr int kTileRows = 64;
+constexpr int kMaxRank = 128;
+
+// Canonical leaf block (export order = sorted by (r0, c0)).
+struct BlockH {
+    int row_node, col_node;
+    int r0, r1, c0, c1;
+    int admissible;
+    int rank;        // -1: stored dense
+    int store_idx;   // index into near or far descriptor arrays
+};
+
+// Device view of a compressed operator, passed by value to the kernels.
+struct OpView {
+    int n_tiles;
+    const TileDesc* tiles;
+    const int2* entries;
+    const NearDesc* nd;
+    const void* near_pool;
+    const FarDesc* fd;
+    const void* far_pool;
+    int sum_rank;
+    const int* trow_block;   // T row -> far block
+    int n_far_nz;
+    const int* far_nz;       // far blocks with k > 0, largest n first
+};
+
+}  // namespace rad
+
+// The opaque handle (global namespace: it is the C type rad_htree).
+struct rad_htree {
+    int64_t n = 0;
+    int leaf_size = 0;
+    double eta = 0.0;
+    int device = 0;
+    bool from_dense = false;
+
+    rad::DevBuf geo;     // 7 x n doubles, tree order
+    rad::DevBuf perm;    // int32, tree position -> facet
+    rad::DevBuf iperm;   // int32, facet -> tree position
+
+    std::vector<rad::NodeShape> nodes;
+    std::vector<rad::NodeBox> boxes;
+    std::vector<int> perm_h;
+    int depth = 0;
+
+    std::vector<rad::BlockH> blocks;   // canonical order
+    int64_t n_admissible = 0;
+
+    // compressed operator
+    bool compressed = false;
+    int factor_dtype = RAD_F64;
+    int near_dtype = RAD_F64;
+    double tol = 0.0;
+    int pivoting = RAD_ACA_PARTIAL;
+    std::vector<rad::NearDesc> near_h;
+    std::vector<rad::FarDesc> far_h;
+    std::vector<int> near_block;      // near desc -> canonical block
+    std::vector<int> far_block;       // far desc -> canonical block
+    rad::DevBuf near_pool, far_pool;
+    rad::DevBuf d_near, d_far, d_tiles, d_entries, d_trow, d_far_nz;
+    int n_tiles = 0;
+    int sum_rank = 0;
+    int n_far_nz = 0;
+    int max_rank_used = 0;
+    int64_t n_dense_fallback = 0;
+    int64_t near_entries = 0, far_entries = 0, aca_entries = 0;
+
+    rad::OpView view() const {
+        rad::OpView v;
+        v.n_tiles = n_tiles;
+        v.tiles = d_tiles.as<rad::TileDesc>();
+        v.entries = d_entries.as<int2>();
+        v.nd = d_near.as<rad::NearDesc>();
+        v.near_pool = near_pool.p;
+        v.fd = d_far.as<rad::FarDesc>();
+        v.far_pool = far_pool.p;
+        v.sum_rank = sum_rank;
+        v.trow_block = d_trow.as<int>();
+        v.n_far_nz = n_far_nz;
+        v.far_nz = d_far_nz.as<int>();
+        return v;
+    }
+    bool op_is_f64() const { return near_dtype == RAD_F64; }
+};
+
+namespace rad {
+// tree.cu
+void build_geometry_from_tris(rad_htree* h, const double* verts_dev, double* geo_user, cudaStream_t s);
+void build_geometry_from_facets(rad_htree* h, const double* c, const double* nrm, const double* a,
+                                double* geo_user, cudaStream_t s);
+void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s);
+// aca.cu
+void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s);
+void finalize_operator(rad_htree* h, cudaStream_t s);
+void load_dense_operator(rad_htree* h, const double* F_dev_rowmajor, cudaStream_t s);
+void export_block(const rad_htree* h, int64_t b, double* D, double* U, double* V);
+// hmatvec.cu
+// Epilogue of the tree-order product Y = F X (row-major, leading dims ldx/ldy):
+//   kStore:   Y = F X
+//   kReflect: Y = Xin - (1 - eps) o F X            (C applied, Eq. 11)
+//   kResid:   Y = B - (Xin - (1 - eps) o F X)      (residual of Eq. 11)
+enum EpiMode { kStore = 0, kReflect = 1, kResid = 2 };
+struct Epi {
+    int mode;
+    const double* eps;   // tree order
+    const double* xin;   // FP64 vectors, row-major, leading dim ld64
+    const double* b;     // FP64 right-hand sides, leading dim ld64
+    int ld64;
+};
+void apply_tree(const rad_htree* h, const void* X, int ldx, void* Y, int ldy, int nrhs,
+                const Epi& epi, void* T_ws, cudaStream_t s);
+size_t apply_workspace_bytes(const rad_htree* h, int nrhs);
+void gather_user_to_tree(const rad_htree* h, int dtype_in, const void* x, int64_t ldx, int nrhs,
+                         void* X, int ldX, bool op64, cudaStream_t s);
+void scatter_tree_to_user(const rad_htree* h, const void* Y, int ldY, int nrhs, bool op64,
+                          int dtype_out, void* y, int64_t ldy, cudaStream_t s);
+// gmres.cu
+void solve_flux(const rad_htree* h, const double* eps_dev, const double* T_dev, int64_t ldT,
+                int m, double sigma, const rad_solve_params* p, double* q_dev, int64_t ldq,
+                rad_solve_info* info, cudaStream_t s);
+void solve_reflection(const rad_htree* h, const double* eps_dev, const double* B_dev, int64_t ldB, int nrhs,
+                      const rad_solve_params* p, double* Y_dev, int64_t ldY, rad_solve_info* info, cudaStream_t s);
+}  // namespace rad

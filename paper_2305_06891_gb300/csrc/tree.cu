@@ -1,0 +1,478 @@
+// A1-A3: facet geometry (§3.1), cluster tree (§4.1, Algorithm 1) and block
+// tree (§4.2, Algorithm 2 with the admissibility condition Eq. 28).
+//
+// The cluster tree is built level by level, one CTA per cluster:
+//   1. bounding box of the cluster's centroids (exact min/max reduction);
+//   2. split axis = longest box extent (ties: lowest axis);
+//   3. radix select (8 passes of 8 bits over an order-preserving 64-bit key
+//      of the coordinate) of the floor(n/2)-th smallest (coordinate, index);
+//   4. stable partition into left/right halves, so that every cluster keeps
+//      its facets in ascending facet index.
+// The cluster shapes (ranges) depend only on n and leaf_size and are laid
+// out breadth first on the host; only boxes and the permutation are computed
+// on the device.  The result is deterministic and equal bit for bit to the
+// recursive definition evaluated in FP64.
+//
+// The block tree runs in one CTA that walks the candidate blocks level by
+// level, classifying each as admissible (low-rank leaf), dense leaf (a
+// cluster has no children) or split into 4 children, with block scans for
+// deterministic compaction.
+
+#include <algorithm>
+#include <cfloat>
+
+#include "rad_device.cuh"
+
+namespace rad {
+
+namespace {
+
+// --------------------------------------------------------------- geometry
+// centroid c = ((v0 + v1) + v2) / 3, n = (v1 - v0) x (v2 - v0), A = |n| / 2.
+// The centroid feeds the bit-exact tree, so its arithmetic is pinned with
+// explicit round-to-nearest intrinsics (no contraction).
+__global__ void geometry_tris_kernel(int n, const double* __restrict__ verts, double* __restrict__ geo,
+                                     int* __restrict__ bad) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n) return;
+    const double* v = verts + 9ll * f;
+    double c[3], e1[3], e2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        c[k] = __ddiv_rn(__dadd_rn(__dadd_rn(v[k], v[3 + k]), v[6 + k]), 3.0);
+        e1[k] = __dsub_rn(v[3 + k], v[k]);
+        e2[k] = __dsub_rn(v[6 + k], v[k]);
+    }
+    const double nx = __dsub_rn(__dmul_rn(e1[1], e2[2]), __dmul_rn(e1[2], e2[1]));
+    const double ny = __dsub_rn(__dmul_rn(e1[2], e2[0]), __dmul_rn(e1[0], e2[2]));
+    const double nz = __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0]));
+    const double nn = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(nx, nx), __dmul_rn(ny, ny)), __dmul_rn(nz, nz)));
+    const bool ok = isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2]) && isfinite(nn) && nn > 0.0;
+    if (!ok) atomicOr(bad, 1);
+    const int64_t N = n;
+    geo[f] = c[0];
+    geo[N + f] = c[1];
+    geo[2 * N + f] = c[2];
+    geo[3 * N + f] = ok ? nx / nn : 0.0;
+    geo[4 * N + f] = ok ? ny / nn : 0.0;
+    geo[5 * N + f] = ok ? nz / nn : 0.0;
+    geo[6 * N + f] = 0.5 * nn;
+}
+
+__global__ void geometry_facets_kernel(int n, const double* __restrict__ c, const double* __restrict__ nrm,
+                                       const double* __restrict__ a, double* __restrict__ geo,
+                                       int* __restrict__ bad) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n) return;
+    const int64_t N = n;
+    bool ok = isfinite(a[f]) && a[f] > 0.0;
+    for (int k = 0; k < 3; ++k) {
+        ok = ok && isfinite(c[3ll * f + k]) && isfinite(nrm[3ll * f + k]);
+        geo[k * N + f] = c[3ll * f + k];
+        geo[(3 + k) * N + f] = nrm[3ll * f + k];
+    }
+    geo[6 * N + f] = a[f];
+    if (!ok) atomicOr(bad, 1);
+}
+
+// --------------------------------------------------------------- cluster tree
+__device__ __forceinline__ unsigned long long order_key(double x) {
+    x = x + 0.0;  // -0.0 -> +0.0: equal coordinates get equal keys
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+constexpr int kTreeNT = 1024;
+
+__device__ __forceinline__ void warp_minmax(double& lo, double& hi) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+}
+
+__global__ void __launch_bounds__(kTreeNT)
+tree_level_kernel(const NodeShape* __restrict__ shapes, NodeBox* __restrict__ boxes, int first,
+                  const double* __restrict__ cx, const double* __restrict__ cy, const double* __restrict__ cz,
+                  const int* __restrict__ idx_in, int* __restrict__ idx_out,
+                  unsigned long long* __restrict__ keys, int* __restrict__ err) {
+    constexpr int NT = kTreeNT;
+    __shared__ double s_lo[3][NT / 32], s_hi[3][NT / 32];
+    __shared__ unsigned int hist[256];
+    __shared__ int scan_sm[NT / 32 + 1];
+    __shared__ int sel_digit, sel_want;
+    __shared__ double s_box[6];
+
+    const int node = first + blockIdx.x;
+    const NodeShape nd = shapes[node];
+    const int b = nd.begin, e = nd.end, n = e - b;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // 1. bounding box of the centroids (exact, order independent)
+    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int p = b + threadIdx.x; p < e; p += NT) {
+        const int f = idx_in[p];
+        const double x[3] = {cx[f], cy[f], cz[f]};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], x[k]);
+            hi[k] = fmax(hi[k], x[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        warp_minmax(lo[k], hi[k]);
+        if (lane == 0) {
+            s_lo[k][warp] = lo[k];
+            s_hi[k][warp] = hi[k];
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double l = lane < NT / 32 ? s_lo[k][lane] : DBL_MAX;
+            double h = lane < NT / 32 ? s_hi[k][lane] : -DBL_MAX;
+            warp_minmax(l, h);
+            if (lane == 0) {
+                s_box[k] = l;
+                s_box[3 + k] = h;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        NodeBox bx;
+        for (int k = 0; k < 3; ++k) {
+            bx.lo[k] = s_box[k];
+            bx.hi[k] = s_box[3 + k];
+        }
+        boxes[node] = bx;
+    }
+    if (nd.leaf) {
+        for (int p = b + threadIdx.x; p < e; p += NT) idx_out[p] = idx_in[p];
+        return;
+    }
+
+    // 2. split axis: largest extent, ties to the lowest axis
+    const double ext0 = __dsub_rn(s_box[3], s_box[0]);
+    const double ext1 = __dsub_rn(s_box[4], s_box[1]);
+    const double ext2 = __dsub_rn(s_box[5], s_box[2]);
+    int axis = 0;
+    double best = ext0;
+    if (ext1 > best) { axis = 1; best = ext1; }
+    if (ext2 > best) { axis = 2; }
+    const double* ca = axis == 0 ? cx : axis == 1 ? cy : cz;
+    for (int p = b + threadIdx.x; p < e; p += NT) keys[p] = order_key(ca[idx_in[p]]);
+    __syncthreads();
+
+    // 3. radix select of the pivot key: the (h-1)-th smallest, h = floor(n/2)
+    const int h = n / 2;
+    unsigned long long prefix = 0ull, mask = 0ull;
+    int want = h - 1;
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 56 - 8 * pass;
+        for (int t = threadIdx.x; t < 256; t += NT) hist[t] = 0u;
+        __syncthreads();
+        for (int p = b + threadIdx.x; p < e; p += NT) {
+            const unsigned long long k = keys[p];
+            if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 0xffull], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int cum = 0, d = 0;
+            for (; d < 255; ++d) {
+                if (want < cum + (int)hist[d]) break;
+                cum += (int)hist[d];
+            }
+            sel_digit = d;
+            sel_want = want - cum;
+        }
+        __syncthreads();
+        prefix |= (unsigned long long)sel_digit << shift;
+        mask |= 0xffull << shift;
+        want = sel_want;
+        __syncthreads();
+    }
+    const unsigned long long pkey = prefix;
+    const int n_eq_left = want + 1;  // equal keys that go left, in index order
+
+    // 4. stable partition (left: key < pivot, or key == pivot among the
+    //    first n_eq_left equal keys in list order)
+    int lbase = 0, rbase = 0, eqbase = 0;
+    for (int s = b; s < e; s += NT) {
+        const int p = s + threadIdx.x;
+        const bool valid = p < e;
+        const unsigned long long k = valid ? keys[p] : 0ull;
+        const int isless = (valid && k < pkey) ? 1 : 0;
+        const int iseq = (valid && k == pkey) ? 1 : 0;
+        int eqtot;
+        const int eqr = block_excl_scan<NT, int>(iseq, scan_sm, eqtot);
+        const int goleft = (isless || (iseq && eqbase + eqr < n_eq_left)) ? 1 : 0;
+        int ltot;
+        const int lp = block_excl_scan<NT, int>(goleft, scan_sm, ltot);
+        const int cnt = min(NT, e - s);
+        if (valid) {
+            const int f = idx_in[p];
+            const int dst = goleft ? b + lbase + lp : b + h + rbase + ((int)threadIdx.x - lp);
+            const bool ok = goleft ? dst < b + h : (dst >= b + h && dst < e);
+            if (ok) idx_out[dst] = f;
+            else atomicOr(err, 4);
+        }
+        lbase += ltot;
+        rbase += cnt - ltot;
+        eqbase += eqtot;
+    }
+    if (threadIdx.x == 0 && lbase != h) atomicOr(err, 2);
+}
+
+__global__ void gather_geo_kernel(int n, const double* __restrict__ geo_user, const int* __restrict__ perm,
+                                  double* __restrict__ geo_tree, int* __restrict__ iperm) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int f = perm[p];
+    const int64_t N = n;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) geo_tree[k * N + p] = geo_user[k * N + f];
+    iperm[f] = p;
+}
+
+// --------------------------------------------------------------- block tree
+// Eq. (28) in squared form on the centroid boxes, FP64 with every product
+// and sum rounded separately (no contraction):
+//   admissible <=> dist^2 > 0 and min(diam_s^2, diam_t^2) <= (eta*eta) dist^2
+__device__ __forceinline__ double sq3(double a, double b, double c) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
+}
+__device__ __forceinline__ bool admissible(const NodeBox& s, const NodeBox& t, double eta) {
+    double g[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double a = __dsub_rn(t.lo[k], s.hi[k]);
+        const double c = __dsub_rn(s.lo[k], t.hi[k]);
+        g[k] = fmax(0.0, fmax(a, c));
+    }
+    const double dist2 = sq3(g[0], g[1], g[2]);
+    if (!(dist2 > 0.0)) return false;
+    const double ds = sq3(__dsub_rn(s.hi[0], s.lo[0]), __dsub_rn(s.hi[1], s.lo[1]), __dsub_rn(s.hi[2], s.lo[2]));
+    const double dt = sq3(__dsub_rn(t.hi[0], t.lo[0]), __dsub_rn(t.hi[1], t.lo[1]), __dsub_rn(t.hi[2], t.lo[2]));
+    return fmin(ds, dt) <= __dmul_rn(__dmul_rn(eta, eta), dist2);
+}
+
+__global__ void __launch_bounds__(kTreeNT)
+block_tree_kernel(const NodeShape* __restrict__ shapes, const NodeBox* __restrict__ boxes, double eta,
+                  int2* candA, int2* candB, int cap_cand, int2* __restrict__ far_out, int cap_far,
+                  int2* __restrict__ near_out, int cap_near, int* __restrict__ counters) {
+    constexpr int NT = kTreeNT;
+    constexpr unsigned long long M21 = (1ull << 21) - 1ull;
+    __shared__ unsigned long long scan_sm[NT / 32 + 1];
+    int2* cur = candA;
+    int2* nxt = candB;
+    if (threadIdx.x == 0) cur[0] = make_int2(0, 0);
+    __syncthreads();
+    int ncur = 1, nfar = 0, nnear = 0, overflow = 0, max_cand = 1;
+    for (int level = 0; level < 64 && ncur > 0; ++level) {
+        int nnext = 0;
+        for (int s = 0; s < ncur; s += NT) {
+            const int t = s + (int)threadIdx.x;
+            const bool valid = t < ncur;
+            int cls = -1;
+            int2 pr = make_int2(0, 0);
+            if (valid) {
+                pr = cur[t];
+                const NodeShape ns = shapes[pr.x], nt = shapes[pr.y];
+                if (admissible(boxes[pr.x], boxes[pr.y], eta)) cls = 1;
+                else if (ns.leaf || nt.leaf) cls = 2;
+                else cls = 0;
+            }
+            const unsigned long long packed =
+                !valid ? 0ull : cls == 1 ? 1ull : cls == 2 ? (1ull << 21) : (1ull << 42);
+            unsigned long long tot;
+            const unsigned long long ex = block_excl_scan<NT, unsigned long long>(packed, scan_sm, tot);
+            if (valid) {
+                if (cls == 1) {
+                    const int pos = nfar + (int)(ex & M21);
+                    if (pos < cap_far) far_out[pos] = pr;
+                } else if (cls == 2) {
+                    const int pos = nnear + (int)((ex >> 21) & M21);
+                    if (pos < cap_near) near_out[pos] = pr;
+                } else {
+                    const NodeShape ns = shapes[pr.x], nt = shapes[pr.y];
+                    const int base = nnext + 4 * (int)(ex >> 42);
+                    const int cs[2] = {ns.child0, ns.child1};
+                    const int ct[2] = {nt.child0, nt.child1};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (base + q < cap_cand) nxt[base + q] = make_int2(cs[q >> 1], ct[q & 1]);
+                }
+            }
+            nfar += (int)(tot & M21);
+            nnear += (int)((tot >> 21) & M21);
+            nnext += 4 * (int)(tot >> 42);
+        }
+        __syncthreads();
+        if (nnext > cap_cand) {
+            overflow = 1;
+            max_cand = max(max_cand, nnext);
+            break;
+        }
+        max_cand = max(max_cand, nnext);
+        int2* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+        ncur = nnext;
+    }
+    if (threadIdx.x == 0) {
+        counters[0] = nfar;
+        counters[1] = nnear;
+        counters[2] = overflow || nfar > cap_far || nnear > cap_near || ncur > 0 && overflow;
+        counters[3] = max_cand;
+    }
+}
+
+}  // namespace
+
+void build_geometry_from_tris(rad_htree* h, const double* verts_dev, double* geo_user, cudaStream_t s) {
+    Scratch ws(s);
+    int* bad = ws.get_n<int>(1);
+    RAD_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    const int n = (int)h->n;
+    geometry_tris_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, verts_dev, geo_user, bad);
+    RAD_CHECK_LAUNCH();
+    int hb = 0;
+    RAD_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RAD_CUDA(cudaStreamSynchronize(s));
+    RAD_REQUIRE(hb == 0, RAD_EINVAL, "degenerate or non-finite triangle in verts");
+}
+
+void build_geometry_from_facets(rad_htree* h, const double* c, const double* nrm, const double* a,
+                                double* geo_user, cudaStream_t s) {
+    Scratch ws(s);
+    int* bad = ws.get_n<int>(1);
+    RAD_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    const int n = (int)h->n;
+    geometry_facets_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, c, nrm, a, geo_user, bad);
+    RAD_CHECK_LAUNCH();
+    int hb = 0;
+    RAD_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RAD_CUDA(cudaStreamSynchronize(s));
+    RAD_REQUIRE(hb == 0, RAD_EINVAL, "non-finite facet data or non-positive area");
+}
+
+void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
+    const int n = (int)h->n;
+    const int leaf = h->leaf_size;
+    // cluster shapes, breadth first: Algorithm 1's recursion on sizes only
+    std::vector<NodeShape>& nodes = h->nodes;
+    nodes.clear();
+    nodes.push_back(NodeShape{0, n, 0, -1, -1, n <= leaf ? 1 : 0});
+    for (size_t q = 0; q < nodes.size(); ++q) {
+        NodeShape nd = nodes[q];
+        if (nd.leaf) continue;
+        const int half = (nd.end - nd.begin) / 2;
+        const int c0 = (int)nodes.size();
+        nodes[q].child0 = c0;
+        nodes[q].child1 = c0 + 1;
+        const int sz0 = half, sz1 = nd.end - nd.begin - half;
+        nodes.push_back(NodeShape{nd.begin, nd.begin + half, nd.level + 1, -1, -1, sz0 <= leaf ? 1 : 0});
+        nodes.push_back(NodeShape{nd.begin + half, nd.end, nd.level + 1, -1, -1, sz1 <= leaf ? 1 : 0});
+    }
+    const int n_nodes = (int)nodes.size();
+    int depth = 0;
+    for (auto& nd : nodes) depth = std::max(depth, nd.level + 1);
+    h->depth = depth;
+    std::vector<int> level_first(depth + 1, n_nodes);
+    for (int q = n_nodes - 1; q >= 0; --q) level_first[nodes[q].level] = q;
+    level_first[depth] = n_nodes;
+
+    Scratch ws(s);
+    NodeShape* d_shapes = ws.get_n<NodeShape>(n_nodes);
+    NodeBox* d_boxes = ws.get_n<NodeBox>(n_nodes);
+    int* idx[2] = {ws.get_n<int>(n), ws.get_n<int>(n)};
+    unsigned long long* keys = ws.get_n<unsigned long long>(n);
+    int* err = ws.get_n<int>(1);
+    RAD_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    h2d(d_shapes, nodes, s);
+    std::vector<int> ident(n);
+    for (int i = 0; i < n; ++i) ident[i] = i;
+    h2d(idx[0], ident, s);
+    h2d(idx[1], ident, s);
+
+    const double* cx = geo_user;
+    const double* cy = geo_user + n;
+    const double* cz = geo_user + 2ll * n;
+    for (int lv = 0; lv < depth; ++lv) {
+        const int cnt = level_first[lv + 1] - level_first[lv];
+        tree_level_kernel<<<cnt, kTreeNT, 0, s>>>(d_shapes, d_boxes, level_first[lv], cx, cy, cz,
+                                                  idx[lv & 1], idx[(lv + 1) & 1], keys, err);
+        RAD_CHECK_LAUNCH();
+    }
+    int* perm_final = idx[depth & 1];
+
+    h->perm.alloc(sizeof(int) * n);
+    h->iperm.alloc(sizeof(int) * n);
+    h->geo.alloc(sizeof(double) * 7 * (size_t)n);
+    RAD_CUDA(cudaMemcpyAsync(h->perm.p, perm_final, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    gather_geo_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, geo_user, perm_final, h->geo.as<double>(),
+                                                      h->iperm.as<int>());
+    RAD_CHECK_LAUNCH();
+
+    // block tree: single CTA, retry with larger buffers on overflow
+    const int base_cap = (int)std::min<int64_t>(1 << 28, 160ll * (n / std::max(1, leaf) + 1) + 4096);
+    int cap = base_cap;
+    std::vector<int2> far_pairs, near_pairs;
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        Scratch bw(s);
+        int2* candA = bw.get_n<int2>(cap);
+        int2* candB = bw.get_n<int2>(cap);
+        int2* far_out = bw.get_n<int2>(cap);
+        int2* near_out = bw.get_n<int2>(cap);
+        int* counters = bw.get_n<int>(4);
+        block_tree_kernel<<<1, kTreeNT, 0, s>>>(d_shapes, d_boxes, h->eta, candA, candB, cap, far_out, cap,
+                                                near_out, cap, counters);
+        RAD_CHECK_LAUNCH();
+        int hc[4];
+        RAD_CUDA(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        RAD_CUDA(cudaStreamSynchronize(s));
+        if (hc[2]) {
+            const int64_t need = std::max<int64_t>({(int64_t)hc[0], (int64_t)hc[1], (int64_t)hc[3]});
+            RAD_REQUIRE(cap < (1 << 28), RAD_ELIMIT, "block tree too large");
+            cap = (int)std::min<int64_t>(1 << 28, std::max<int64_t>(4ll * cap, need + 1024));
+            continue;
+        }
+        far_pairs.resize(hc[0]);
+        near_pairs.resize(hc[1]);
+        if (hc[0]) RAD_CUDA(cudaMemcpyAsync(far_pairs.data(), far_out, sizeof(int2) * hc[0], cudaMemcpyDeviceToHost, s));
+        if (hc[1]) RAD_CUDA(cudaMemcpyAsync(near_pairs.data(), near_out, sizeof(int2) * hc[1], cudaMemcpyDeviceToHost, s));
+        RAD_CUDA(cudaStreamSynchronize(s));
+        break;
+    }
+    RAD_REQUIRE(!(far_pairs.empty() && near_pairs.empty()), RAD_ELIMIT, "block tree did not fit");
+
+    h->boxes.resize(n_nodes);
+    h->perm_h.resize(n);
+    RAD_CUDA(cudaMemcpyAsync(h->boxes.data(), d_boxes, sizeof(NodeBox) * n_nodes, cudaMemcpyDeviceToHost, s));
+    RAD_CUDA(cudaMemcpyAsync(h->perm_h.data(), perm_final, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+    int herr = 0;
+    RAD_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RAD_CUDA(cudaStreamSynchronize(s));
+    RAD_REQUIRE(herr == 0, RAD_ECUDA, "internal error in the cluster-tree partition");
+
+    std::vector<BlockH>& blocks = h->blocks;
+    blocks.clear();
+    blocks.reserve(far_pairs.size() + near_pairs.size());
+    auto add = [&](int2 pr, int adm) {
+        const NodeShape& a = nodes[pr.x];
+        const NodeShape& b = nodes[pr.y];
+        blocks.push_back(BlockH{pr.x, pr.y, a.begin, a.end, b.begin, b.end, adm, adm ? 0 : -1, -1});
+    };
+    for (auto pr : far_pairs) add(pr, 1);
+    for (auto pr : near_pairs) add(pr, 0);
+    std::sort(blocks.begin(), blocks.end(), [](const BlockH& x, const BlockH& y) {
+        return x.r0 != y.r0 ? x.r0 < y.r0 : x.c0 < y.c0;
+    });
+    h->n_admissible = (int64_t)far_pairs.size();
+}
+
+}  // namespace rad

@@ -1,0 +1,85 @@
+"""GPU block low-rank matvec (§5.2) against the oracle's dense F x."""
+import numpy as np
+import pytest
+
+import cavities as cv
+from gpu_common import rad, rel
+from oracle import SIGMA_SB, geometry, viewfactor
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c1():
+    c = cv.config1()
+    f = geometry.facets_from_triangles(c.verts)
+    return c, viewfactor.dense(f)
+
+
+@pytest.fixture(scope="module")
+def cyl():
+    verts = cv.closed_cylinder(1.0, 4.0, 56, 36, 5)     # 4,592 facets
+    f = geometry.facets_from_triangles(verts)
+    return verts, viewfactor.dense(f)
+
+
+def test_c1_fp64_matvec_within_1e6(c1):
+    c, F = c1
+    r = rad()
+    h = r.rad_build_htree(c.verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-6, 64, "partial", "f64", "f64")
+    x = SIGMA_SB * c.T[:, 0] ** 4
+    y = r.rad_hmatvec(h, x)
+    assert rel(y, F @ x) <= 1e-6
+
+
+def test_fp64_exact_when_tolerance_vanishes(cyl):
+    verts, F = cyl
+    r = rad()
+    h = r.rad_build_htree(verts, 32, 1.0)
+    r.rad_compress_aca(h, 0.0, 128, "full", "f64", "f64")
+    x = np.random.default_rng(0).uniform(size=F.shape[0])
+    assert rel(r.rad_hmatvec(h, x), F @ x) <= 1e-12
+
+
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 17, 65, 130])
+def test_multi_rhs_fp64_and_fp32(cyl, nrhs):
+    verts, F = cyl
+    r = rad()
+    X = np.random.default_rng(nrhs).uniform(0.5, 1.5, size=(F.shape[0], nrhs))
+    Yref = F @ X
+    h = r.rad_build_htree(verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-9, 64, "partial", "f64", "f64")
+    Y = r.rad_hmatvec(h, X)
+    for c in range(nrhs):
+        assert rel(Y[:, c], Yref[:, c]) <= 1e-7, c
+    r.rad_compress_aca(h, 1e-8, 64, "partial", "f32", "f32")
+    Y32 = r.rad_hmatvec(h, X.astype(np.float32))
+    for c in range(nrhs):
+        assert rel(Y32[:, c], Yref[:, c]) <= 1e-6, c
+
+
+def test_bf16_factors(cyl):
+    verts, F = cyl
+    r = rad()
+    h = r.rad_build_htree(verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-6, 64, "partial", "bf16", "f32")
+    x = np.random.default_rng(1).uniform(0.5, 1.5, size=F.shape[0]).astype(np.float32)
+    e = rel(r.rad_hmatvec(h, x), F @ x)
+    assert e <= 1e-2
+
+
+def test_device_strided_and_host_paths_agree(cyl):
+    import torch
+    verts, F = cyl
+    r = rad()
+    h = r.rad_build_htree(verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-7, 64, "partial", "f32", "f32")
+    n = F.shape[0]
+    X = np.random.default_rng(2).uniform(size=(n, 5))
+    Yh = r.rad_hmatvec(h, X)
+    big = torch.zeros((5, n + 7), dtype=torch.float64, device="cuda")
+    big[:, :n] = torch.as_tensor(X.T, device="cuda")
+    Xd = big.t()[:n]                                     # column-major view, ld = n + 7
+    Yd = r.rad_hmatvec(h, Xd)
+    np.testing.assert_array_equal(Yd.cpu().numpy(), Yh)

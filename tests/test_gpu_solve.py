@@ -1,0 +1,92 @@
+"""GPU GMRES reflection solve (Eq. 11) and flux (Eq. 12) against closed
+forms and the oracle's direct solve."""
+import numpy as np
+import pytest
+
+import cavities as cv
+from gpu_common import rad, rel
+from oracle import SIGMA_SB, geometry, radiosity, viewfactor
+
+pytestmark = pytest.mark.gpu
+
+
+def test_two_grey_planes_eq5():
+    r = rad()
+    h = r.rad_htree_from_dense(np.array([[0.0, 1.0], [1.0, 0.0]]))
+    for e1, e2, T1, T2 in [(0.3, 0.8, 400.0, 900.0), (0.9, 0.1, 1200.0, 300.0)]:
+        q, info = r.rad_solve_flux(h, np.array([e1, e2]), np.array([T1, T2]), SIGMA_SB, tol=1e-14)
+        want = radiosity.two_planes_flux(e2, e1, T2, T1, SIGMA_SB)
+        assert abs(q[0] - want) <= 1e-12 * abs(want)
+        assert abs(q[1] + want) <= 1e-12 * abs(want)
+
+
+def test_closed_cavity_and_uniform_temperature():
+    r = rad()
+    n = 9
+    F = (np.ones((n, n)) - np.eye(n)) / (n - 1)
+    h = r.rad_htree_from_dense(F)
+    eps = np.linspace(0.2, 0.9, n)
+    Y, info = r.rad_solve_reflection(h, eps, eps, tol=1e-14)
+    np.testing.assert_allclose(Y, 1.0, rtol=1e-12)
+    q, _ = r.rad_solve_flux(h, eps, np.full(n, 500.0), SIGMA_SB, tol=1e-14)
+    assert np.abs(q).max() <= 1e-12 * SIGMA_SB * 500.0 ** 4
+
+
+def test_c1_fp64_flux_within_1e6_and_conserves_energy():
+    c = cv.config1()
+    f = geometry.facets_from_triangles(c.verts)
+    F = viewfactor.dense(f)
+    q_ref, _, _ = radiosity.solve_flux(F, c.eps, c.T, SIGMA_SB)
+    r = rad()
+    h = r.rad_build_htree(c.verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-6, 64, "partial", "f64", "f64")
+    q, info = r.rad_solve_flux(h, c.eps, c.T, SIGMA_SB, tol=1e-12)
+    assert info["status"] == 0
+    assert rel(q, q_ref) <= 1e-6
+    assert abs((f.area * q[:, 0]).sum()) <= 1e-6 * (f.area * np.abs(q[:, 0])).sum()
+
+
+def test_multi_field_fp64_and_fp32():
+    verts = cv.closed_cylinder(1.0, 4.0, 40, 24, 4)
+    f = geometry.facets_from_triangles(verts)
+    F = viewfactor.dense(f)
+    rng = np.random.default_rng(9)
+    eps = rng.uniform(0.3, 0.9, f.size)
+    T = rng.uniform(300, 1200, (f.size, 5))
+    q_ref, Y_ref, z_ref = radiosity.solve_flux(F, eps, T, SIGMA_SB)
+    r = rad()
+    h = r.rad_build_htree(verts, 24, 1.0)
+    r.rad_compress_aca(h, 1e-9, 64, "partial", "f64", "f64")
+    q, info = r.rad_solve_flux(h, eps, T, SIGMA_SB, tol=1e-12)
+    for c in range(5):
+        assert rel(q[:, c], q_ref[:, c]) <= 1e-6
+    B = np.concatenate([eps[:, None] * T ** 4, eps[:, None]], axis=1)
+    Y, info = r.rad_solve_reflection(h, eps, B, tol=1e-12)
+    assert rel(Y[:, :5], Y_ref) <= 1e-8 and rel(Y[:, 5], z_ref) <= 1e-8
+    r.rad_compress_aca(h, 1e-8, 64, "partial", "f32", "f32")
+    q32, info = r.rad_solve_flux(h, eps, T, SIGMA_SB, tol=1e-7)
+    assert rel(q32, q_ref) <= 1e-5
+
+
+def test_not_converged_is_reported():
+    c = cv.config1()
+    r = rad()
+    h = r.rad_build_htree(c.verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-6, 64, "partial", "f64", "f64")
+    q, info = r.rad_solve_flux(h, c.eps, c.T, SIGMA_SB, tol=1e-14, max_iter=2)
+    assert info["status"] == r.RAD_ENOTCONV
+    assert info["iters"] == 2
+    with pytest.raises(r.RadError):
+        r.rad_solve_flux(h, c.eps, c.T, SIGMA_SB, tol=1e-14, max_iter=2, raise_on_notconv=True)
+
+
+def test_device_buffers_equal_host_buffers():
+    import torch
+    c = cv.config1()
+    r = rad()
+    h = r.rad_build_htree(c.verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-6, 64, "partial", "f64", "f64")
+    qh, _ = r.rad_solve_flux(h, c.eps, c.T, SIGMA_SB, tol=1e-12)
+    qd, _ = r.rad_solve_flux(h, torch.as_tensor(c.eps, device="cuda"), torch.as_tensor(c.T, device="cuda"),
+                             SIGMA_SB, tol=1e-12)
+    np.testing.assert_array_equal(qd.cpu().numpy(), qh)
