@@ -17,9 +17,17 @@ pivoting as the faster, less reliable alternative):
   row 0.  Column pivot: argmax |residual row| (ties: lowest).  A residual row
   whose largest modulus is <= max(1e-300, 1e-14 * largest pivot so far) is
   marked used and the lowest unused row is tried instead.  Next row: argmax
-  |u_k| over unused rows.  Stop when |u_k| |v_k| <= eps_rel ||S_k||_F, with
-  ||S_k||_F^2 = ||S_{k-1}||_F^2 + 2 sum_{l<k} (u_k.u_l)(v_k.v_l)
+  |u_k| over unused rows.  Candidate stop when |u_k| |v_k| <= eps_rel ||S_k||_F,
+  with ||S_k||_F^2 = ||S_{k-1}||_F^2 + 2 sum_{l<k} (u_k.u_l)(v_k.v_l)
   + |u_k|^2 |v_k|^2.
+  The paper warns that partial pivoting is less reliable; that candidate stop
+  can fire while rows the pivots never visited are still poorly
+  approximated.  So a candidate stop is verified (at most 4 times per block)
+  on S = 256 sampled residual entries at rows i_s = floor(s m / S) and columns
+  j_s = (s * 2654435761 + c * 40503) mod n (s < S, c = checks done so far):
+  ||R||_F^2 is estimated as (m n / S) sum_s r_s^2; if that exceeds
+  eps_rel^2 ||S_k||_F^2 the iteration continues from the row of the largest
+  |r_s| (ties: lowest s).
 
 Both return (U, V, converged) with U (m, k), V (n, k).  ``converged`` is
 False when the rank cap was reached first (the caller then stores the block
@@ -69,6 +77,7 @@ def aca_partial(get_row, get_col, m: int, n: int, tol: float, max_rank: int,
     used = np.zeros(m, dtype=bool)
     norm2_S = 0.0
     scale = 0.0
+    checks = 0
     i = 0
     while True:
         if len(us) >= max_rank:
@@ -101,11 +110,48 @@ def aca_partial(get_row, get_col, m: int, n: int, tol: float, max_rank: int,
         us.append(u)
         vs.append(v)
         if math.sqrt(uu) * math.sqrt(vv) <= tol * math.sqrt(max(norm2_S, 0.0)):
-            return _stack(us, m), _stack(vs, n), True
+            if checks >= MAX_CHECKS:
+                return _stack(us, m), _stack(vs, n), True
+            est2, worst_row = _sampled_residual(get_row, us, vs, m, n, checks)
+            checks += 1
+            if est2 <= tol * tol * norm2_S:
+                return _stack(us, m), _stack(vs, n), True
+            if stats is not None:
+                stats["rejected_stops"] = stats.get("rejected_stops", 0) + 1
+            if used[worst_row]:
+                free = np.flatnonzero(~used)
+                if free.size == 0:
+                    return _stack(us, m), _stack(vs, n), True
+                worst_row = int(free[0])
+            i = worst_row
+            continue
         cand = np.where(used, -1.0, np.abs(u))
         if not (cand >= 0).any():
             return _stack(us, m), _stack(vs, n), True
         i = int(np.argmax(cand))
+
+
+SAMPLES = 256
+MAX_CHECKS = 4
+
+
+def sample_positions(m: int, n: int, check: int):
+    """Rows and columns of the S residual samples of verification ``check``."""
+    s = np.arange(SAMPLES, dtype=np.int64)
+    return (s * m) // SAMPLES, (s * 2654435761 + check * 40503) % n
+
+
+def _sampled_residual(get_row, us, vs, m, n, check):
+    rows, cols = sample_positions(m, n, check)
+    r = np.empty(SAMPLES)
+    for s in range(SAMPLES):
+        i, j = int(rows[s]), int(cols[s])
+        x = float(np.asarray(get_row(i))[j])
+        for u_l, v_l in zip(us, vs):
+            x -= u_l[i] * v_l[j]
+        r[s] = x
+    est2 = (m * n / SAMPLES) * float((r * r).sum())
+    return est2, int(rows[int(np.argmax(np.abs(r)))])
 
 
 def _stack(vecs, length):

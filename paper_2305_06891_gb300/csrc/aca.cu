@@ -12,9 +12,15 @@
 // Partial pivoting: first pivot row 0; column pivot = argmax |residual row|;
 // a residual row whose largest modulus is <= max(1e-300, 1e-14 x largest
 // pivot so far) is marked used and the lowest unused row is tried instead;
-// next row = argmax |u_k| over unused rows; stop when
+// next row = argmax |u_k| over unused rows; candidate stop when
 // |u_k| |v_k| <= tol ||S_k||_F with
 // ||S_k||^2 = ||S_{k-1}||^2 + 2 sum_{l<k} (u_k.u_l)(v_k.v_l) + |u_k|^2 |v_k|^2.
+// Partial pivoting is the less reliable rule (§1), and that candidate stop
+// can fire early, so it is verified (at most kMaxChecks times per block) on
+// kSamples residual entries at rows floor(s m / S) and columns
+// (s * 2654435761 + c * 40503) mod n, c = checks so far: if
+// (m n / S) sum r_s^2 > tol^2 ||S_k||^2 the iteration resumes from the row of
+// the largest |r_s| (ties: lowest s).
 // Full pivoting keeps the whole residual and stops when
 // ||R_k||_F <= tol ||X||_F (Eq. 31 exactly).
 // A block whose rank would exceed kmax = min(max_rank, m n / (m + n)) is
@@ -36,6 +42,8 @@ struct AcaJob {
 };
 
 constexpr int kAcaNT = 256;
+constexpr int kSamples = kAcaNT;   // one sampled residual entry per thread
+constexpr int kMaxChecks = 4;
 
 // lowest index i < m with used[i] == 0, or -1; all threads receive it
 __device__ int lowest_unused(const unsigned char* used, int m, int* sm) {
@@ -90,6 +98,7 @@ aca_partial_kernel(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict
     __shared__ double s_cu[kMaxRank + 1];
     __shared__ ArgMax am_sm[kAcaNT / 32 + 1];
     __shared__ int i_sm[kAcaNT / 32 + 1];
+    __shared__ double red_sm[kAcaNT / 32 + 1];
 
     const int bidx = order[blockIdx.x];
     const AcaJob jb = jobs[bidx];
@@ -98,10 +107,10 @@ aca_partial_kernel(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict
     CT* V = Vpool + jb.offV;
     unsigned char* used = used_pool + jb.offUsed;
 
-    int i = 0, k = 0, status = 0;  // status: 1 converged, 2 rank cap
+    int i = 0, k = 0, status = 0, checks = 0;  // status: 1 converged, 2 rank cap
     double norm2 = 0.0, scale = 0.0;
     long long evals = 0;
-    for (int guard = 0; guard <= m + kmax + 1; ++guard) {
+    for (int guard = 0; guard <= m + kmax + kMaxChecks + 2; ++guard) {
         if (k >= kmax) { status = 2; break; }
         // residual of pivot row i: X(i,:) - sum_l U(i,l) V(:,l)
         if ((int)threadIdx.x < k) s_row[threadIdx.x] = (double)U[(long long)threadIdx.x * m + i];
@@ -150,7 +159,28 @@ aca_partial_kernel(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict
         const double uu = s_cu[k], vv = s_cv[k];
         norm2 = norm2 + 2.0 * cross + uu * vv;
         ++k;
-        if (sqrt(uu) * sqrt(vv) <= tol * sqrt(fmax(norm2, 0.0))) { status = 1; break; }
+        if (sqrt(uu) * sqrt(vv) <= tol * sqrt(fmax(norm2, 0.0))) {
+            if (checks >= kMaxChecks) { status = 1; break; }
+            // verify the candidate stop on sampled residual entries
+            const int sidx = threadIdx.x;
+            const int si = (int)(((long long)sidx * m) / kSamples);
+            const int sj = (int)(((unsigned long long)sidx * 2654435761ull + (unsigned long long)checks * 40503ull) %
+                                 (unsigned long long)n);
+            CT x = Entry<CT>::eval(g, jb.r0 + si, jb.c0 + sj);
+            for (int l = 0; l < k; ++l) x -= U[(long long)l * m + si] * V[(long long)l * n + sj];
+            const double r2 = block_sum<kAcaNT, double>((double)x * (double)x, red_sm);
+            const ArgMax bs = block_argmax<kAcaNT>(ArgMax{fabs((double)x), sidx}, am_sm);
+            ++checks;
+            evals += kSamples;
+            if (((double)m * (double)n / kSamples) * r2 <= tol * tol * fmax(norm2, 0.0)) { status = 1; break; }
+            int wi = (int)(((long long)bs.i * m) / kSamples);
+            if (used[wi]) {
+                wi = lowest_unused(used, m, i_sm);
+                if (wi < 0) { status = 1; break; }
+            }
+            i = wi;
+            continue;
+        }
         if (bu.v < 0.0) { status = 1; break; }
         i = bu.i;
     }
@@ -453,7 +483,9 @@ void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     h->near_dtype = p->near_dtype;
     h->tol = p->tol;
     h->pivoting = p->pivoting;
-    if (p->near_dtype == RAD_F64) compress_t<double>(h, p, s);
+    // ACA arithmetic: FP64 for the FP64 path and for tolerances near FP32
+    // resolution; FP32 (FP64 centroid differences, FP64 norms) otherwise.
+    if (p->near_dtype == RAD_F64 || p->tol < 2e-6) compress_t<double>(h, p, s);
     else compress_t<float>(h, p, s);
     h->compressed = true;
 }

@@ -107,3 +107,42 @@ def test_partial_norm_estimate_is_exact_frobenius_of_the_cross():
     exact = float(np.linalg.norm(U @ V.T) ** 2)
     assert abs(st["norm2_S"] - exact) <= 1e-12 * exact
     assert st["rows"][0] == 0
+
+
+def test_sampled_verification_repairs_early_partial_stops():
+    """The plain partial-pivot stop rule can fire early (the paper calls
+    partial pivoting less reliable); with the sampled verification every block
+    of this cylinder meets Eq. (31) within 2x."""
+    f = geometry.facets_from_triangles(cv.closed_cylinder(1.0, 4.0, 32, 20, 3))
+    t = htree.build_cluster_tree(f.c, 16)
+    Ft = viewfactor.dense(f.subset(t.perm))
+    blocks = [b for b in htree.build_block_tree(t, 1.0) if b.admissible]
+    tol = 1e-5
+
+    def worst(checks):
+        saved = aca.MAX_CHECKS
+        aca.MAX_CHECKS = checks
+        try:
+            w = 0.0
+            for b in blocks:
+                X = Ft[b.row.begin:b.row.end, b.col.begin:b.col.end]
+                nx = np.linalg.norm(X)
+                if nx == 0:
+                    continue
+                m, n = X.shape
+                U, V, ok = aca.aca_partial(lambda i: X[i], lambda j: X[:, j], m, n, tol,
+                                           max(1, min(64, m * n // (m + n))))
+                if ok:
+                    w = max(w, np.linalg.norm(X - U @ V.T) / nx / tol)
+            return w
+        finally:
+            aca.MAX_CHECKS = saved
+
+    assert worst(aca.MAX_CHECKS) <= 2.0
+    assert worst(0) > 3.0
+
+
+def test_sample_positions_cover_rows_and_stay_in_range():
+    rows, cols = aca.sample_positions(37, 11, 2)
+    assert rows.min() == 0 and rows.max() == 36 and cols.min() >= 0 and cols.max() < 11
+    assert len(set(rows.tolist())) == 37
