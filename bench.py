@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark: flux solves per second of the block low-rank cavity-radiation
+hot path on one GB300 (or N independent replicas, one per GPU).
+
+Workload (the closed-cylinder cavity): 19,936 inward-facing triangles
+(R = 1, H = 4), emissivity U[0.3, 0.9], 64 temperature fields U[300, 1200] K,
+leaf size 64, eta = 1, ACA tol 1e-5 (partial pivoting with sampled
+verification), FP32 storage with FP32 accumulation, GMRES (restart 30) on the
+reflection system to a relative residual of 1e-7 with FP64 Krylov vectors.
+
+One step = the whole hot path on freshly uploaded inputs: facet geometry,
+cluster tree, block tree, dense blocks, ACA, then the flux solve for all 64
+fields (GMRES on 65 right-hand sides: 64 fields + the shared z = C^-1 eps,
+and the flux epilogue).  value = fields solved per second.
+
+Timing: W warm-up steps, then K steps between a barrier + synchronize; each
+step is bracketed by CUDA events on the launching stream, and a 256 MiB
+buffer is written between steps to flush L2 (129 MB).  The per-kernel
+profile (CUDA events inside librad) gives the dominant kernel's duration for
+the roofline; nvidia-smi samples clocks during the timed steps.
+
+--impl reference times the FP64 CPU oracle (dense assembly, LU, flux) on the
+host cores on a bounded sample of the same workload, extrapolated to the
+full cavity.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import cavities as cv  # noqa: E402
+
+METRIC = "flux solves/s"
+UNIT = "solves/s"
+FIELDS = 64
+LEAF, ETA, ACA_TOL, SOLVE_TOL, RESTART = 64, 1.0, 1e-5, 1e-7, 30
+SIGMA = 5.670374419e-8
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, rank: int, world: int):
+    import torch
+    import paper_2305_06891_gb300 as rad
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cav = cv.config2(m=FIELDS)
+    n = cav.n
+    verts_h, eps_h = cav.verts, cav.eps
+    T_h = np.asfortranarray(cav.T)
+    verts_d = torch.as_tensor(verts_h, device=dev)
+    eps_d = torch.as_tensor(eps_h, device=dev)
+    T_d = torch.as_tensor(cav.T, device=dev).t().contiguous().t()
+    q_d = torch.empty((FIELDS, n), dtype=torch.float64, device=dev).t()
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(storage="f32", verts=verts_d, eps=eps_d, T=T_d, q=q_d):
+        h = rad.rad_build_htree(verts, LEAF, ETA)
+        rad.rad_compress_aca(h, ACA_TOL, 64, "partial", storage, storage)
+        q, info = rad.rad_solve_flux(h, eps, T, SIGMA, tol=SOLVE_TOL, restart=RESTART, max_iter=600, q=q)
+        return h, info
+
+    for _ in range(args.warmup):
+        h, info = step()
+        h.free()
+    torch.cuda.synchronize()
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    launches0 = rad.rad_launch_count()
+    rad.rad_profile_enable(True)
+    times, infos = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h, info = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        infos.append(info)
+        st = rad.rad_htree_get_stats(h)
+        h.free()
+    torch.cuda.synchronize()
+    prof = rad.rad_profile_read()
+    rad.rad_profile_enable(False)
+    launches = rad.rad_launch_count() - launches0
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    # ---- one-off measurements (not in the timed region)
+    extra = {}
+    if rank == 0:
+        extra = measure_extras(args, rad, torch, dev, cav, verts_d, eps_d, T_d, flush, stream)
+    return dict(times=times, total_ms=total_ms, infos=infos, stats=st, prof=prof, launches=launches, clocks=clk,
+                extra=extra, n=n, cav=cav, T_h=T_h)
+
+
+def measure_extras(args, rad, torch, dev, cav, verts_d, eps_d, T_d, flush, stream):
+    out = {}
+    n = cav.n
+    # single-RHS block matvec on the bench operator (HBM bound)
+    h = rad.rad_build_htree(verts_d, LEAF, ETA)
+    rad.rad_compress_aca(h, ACA_TOL, 64, "partial", "f32", "f32")
+    st = rad.rad_htree_get_stats(h)
+    x = torch.as_tensor(SIGMA * cav.T[:, 0] ** 4, device=dev, dtype=torch.float32)
+    y = torch.empty(n, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        rad.rad_hmatvec(h, x, y)
+    reps = 20
+    ts = []
+    rad.rad_profile_enable(True)
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rad.rad_hmatvec(h, x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    prof = rad.rad_profile_read()
+    rad.rad_profile_enable(False)
+    op_bytes = st["bytes_near"] + st["bytes_far"]
+    vec_bytes = 4 * (2 * n + 2 * st["sum_rank"])
+    kern_ms = (prof.get("hmv_rows", (1, 0.0))[1] + prof.get("hmv_far_vt", (1, 0.0))[1]) / reps
+    hbm, _, src = load_peaks()
+    out["hmatvec"] = {
+        "unit": "GB/s", "operator_bytes": op_bytes,
+        "gbs_kernels": (op_bytes + vec_bytes) / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else None,
+        "gbs_call": (op_bytes + vec_bytes) / (statistics.median(ts) * 1e-3) / 1e9,
+        "frac_kernels": ((op_bytes + vec_bytes) / (kern_ms * 1e-3) / 1e9) / hbm if kern_ms > 0 else None,
+        "peak_gbs": hbm, "peak_kind": src, "ms_kernels": kern_ms, "ms_call_median": statistics.median(ts),
+        "per_kernel_ms": {k: v[1] / reps for k, v in prof.items()}}
+    h.free()
+    # the plain FP64 GPU path: same step with FP64 storage and arithmetic
+    if not args.no_fp64:
+        ts64 = []
+        for it in range(2):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = rad.rad_build_htree(verts_d, LEAF, ETA)
+            rad.rad_compress_aca(h, ACA_TOL, 64, "partial", "f64", "f64")
+            q, info = rad.rad_solve_flux(h, eps_d, T_d, SIGMA, tol=SOLVE_TOL, restart=RESTART, max_iter=600)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it:
+                ts64.append(e0.elapsed_time(e1))
+            h.free()
+        out["fp64_path"] = {"ms_per_step": ts64[0], "value": FIELDS / (ts64[0] * 1e-3), "unit": UNIT,
+                            "gmres_iters": info["iters"], "max_rel_residual": info["max_rel_residual"]}
+    # end to end through the C ABI with host buffers (copies inside)
+    verts_h = np.ascontiguousarray(cav.verts)
+    T_h = np.asfortranarray(cav.T)
+    q_h = np.empty((n, FIELDS), order="F")
+    e2e = []
+    for it in range(max(2, min(args.steps, 5)) + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = rad.rad_build_htree(verts_h, LEAF, ETA)
+        rad.rad_compress_aca(h, ACA_TOL, 64, "partial", "f32", "f32")
+        rad.rad_solve_flux(h, cav.eps, T_h, SIGMA, tol=SOLVE_TOL, restart=RESTART, max_iter=600, q=q_h)
+        t1 = time.perf_counter()
+        h.free()
+        if it:
+            e2e.append(t1 - t0)
+    out["e2e"] = {"value": FIELDS / statistics.median(e2e), "unit": UNIT,
+                  "h2d_bytes_per_step": int(verts_h.nbytes + cav.eps.nbytes + T_h.nbytes),
+                  "d2h_bytes_per_step": int(q_h.nbytes), "ms_per_step": 1e3 * statistics.median(e2e)}
+    return out
+
+
+def roofline(prof: dict, st: dict, steps: int, clocks: dict, nc: int):
+    """Dominant kernel of the timed steps and its roofline."""
+    hbm, smax, src = load_peaks()
+    if not prof:
+        return None
+    name, (cnt, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    avg_s = ms / cnt * 1e-3
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
+    if name == "hmm_rows":
+        flops = 2.0 * nc * (st["near_entries"] + st["far_u_entries"])
+        ach = flops / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None, "launches": cnt, "avg_ms": ms / cnt,
+                "peak_note": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz"}
+    if name == "hmm_far_vt":
+        flops = 2.0 * nc * st["far_v_entries"]
+        ach = flops / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None, "launches": cnt, "avg_ms": ms / cnt,
+                "peak_note": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz"}
+    if name in ("aca_partial", "near_assemble"):
+        # view-factor entry evaluations: ~ 24 FP32 + 3 FP64 operations each
+        ents = st["aca_entries"] if name == "aca_partial" else st["near_entries"]
+        flops = 27.0 * ents / steps * steps
+        ach = flops / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None, "launches": cnt, "avg_ms": ms / cnt,
+                "peak_note": "entry evaluations x 27 flops vs FP32 issue peak"}
+    # vector-bound GMRES kernels and the rest: HBM
+    return {"kernel": name, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
+            "traffic": None, "launches": cnt, "avg_ms": ms / cnt}
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_step(cav, rows_sample=1024, lu_n=3072, seed=0):
+    """Time the FP64 oracle on a bounded sample and extrapolate to the full
+    cavity.  Returns (extrapolated seconds per full flux solve of 64 fields,
+    description)."""
+    from oracle import geometry, radiosity, viewfactor
+    n = cav.n
+    f = geometry.facets_from_triangles(cav.verts)
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(n, rows_sample, replace=False))
+    t0 = time.perf_counter()
+    Fr = viewfactor.rows(f, rows)
+    t_asm = (time.perf_counter() - t0) * n / rows_sample
+    sub = np.arange(lu_n)
+    fs = f.subset(sub)
+    Fs = viewfactor.dense(fs)
+    T = cav.T[sub]
+    t0 = time.perf_counter()
+    q, Y, z = radiosity.solve_flux(Fs, cav.eps[sub], T, SIGMA)
+    t_solve = (time.perf_counter() - t0)
+    # dense LU is O(n^3); the flux products F @ [Y z] are O(n^2): split the
+    # measured time into the two by timing the product alone
+    t0 = time.perf_counter()
+    _ = Fs @ np.concatenate([Y, z[:, None]], axis=1)
+    t_mm = time.perf_counter() - t0
+    t_lu = max(t_solve - 2 * t_mm, 1e-9)
+    scale3 = (n / lu_n) ** 3
+    scale2 = (n / lu_n) ** 2
+    total = t_asm + t_lu * scale3 + 2 * t_mm * scale2
+    desc = (f"F rows {rows_sample}/{n} (assembly x{n / rows_sample:.1f}); direct solve + flux on the leading "
+            f"{lu_n} facets (LU x(n/{lu_n})^3, F@Y x(n/{lu_n})^2); 64 fields")
+    return total, desc, Fr.sum()
+
+
+def run_reference(args):
+    cav = cv.config2(m=FIELDS)
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        oracle_step(cav)
+    vals, wall = [], []
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        t, desc, _ = oracle_step(cav, seed=s)
+        vals.append(t)
+    elapsed = time.perf_counter() - t0
+    t = statistics.median(vals)
+    value = FIELDS / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(),
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores, "sample": desc,
+                             "wall_s": elapsed},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict():
+    return {"workload": "closed_cylinder_19936_64fields_fp32", "n_facets": 19936, "fields": FIELDS,
+            "leaf_size": LEAF, "eta_adm": ETA, "aca_tol": ACA_TOL, "aca_pivoting": "partial+sampled check",
+            "solve_tol": SOLVE_TOL, "gmres_restart": RESTART, "storage": "f32 near + f32 factors",
+            "accumulation": "f32 (operator), f64 (Krylov, inner products, residuals)",
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return 0
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    r = run_ours(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+    st = r["stats"]
+    times = r["times"]
+    ms_per_step = r["total_ms"] / args.steps
+    value = world * FIELDS * args.steps / (r["total_ms"] * 1e-3)
+    nc = FIELDS + 1
+    steps = args.steps
+    prof = {k: (v[0], v[1]) for k, v in r["prof"].items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": config_dict(),
+        "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
+        "gpu_launches": int(r["launches"]),
+        "clocks": r["clocks"],
+        "roofline": roofline(prof, st, steps, r["clocks"], nc),
+        "kernels_ms_per_step": {k: v[1] / steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+        "gmres": {"iters": r["infos"][-1]["iters"], "restarts": r["infos"][-1]["restarts"],
+                  "matvecs": r["infos"][-1]["matvecs"], "max_rel_residual": r["infos"][-1]["max_rel_residual"]},
+        "operator": {k: st[k] for k in ("n_blocks", "n_admissible", "near_entries", "far_entries", "sum_rank",
+                                         "max_rank_used", "n_dense_fallback", "bytes_near", "bytes_far")},
+    }
+    ex = r["extra"]
+    line["e2e"] = ex.get("e2e")
+    line["hmatvec"] = ex.get("hmatvec")
+    if "fp64_path" in ex:
+        line["fp64_path"] = ex["fp64_path"]
+        line["speedup_vs_fp64_gpu"] = value / world / ex["fp64_path"]["value"]
+    if not args.no_cpu_baseline:
+        t, desc, _ = oracle_step(r["cav"])
+        line["cpu_baseline"] = {"value": FIELDS / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": desc}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

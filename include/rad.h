@@ -119,6 +119,9 @@ typedef struct {
     int64_t aca_entries;         /* entries evaluated by ACA                   */
     int64_t bytes_near;
     int64_t bytes_far;
+    int64_t far_u_entries;       /* sum k m over low-rank blocks (U factors)   */
+    int64_t far_v_entries;       /* sum k n over low-rank blocks (V factors)   */
+    int64_t n_tiles;             /* row tiles of the product (<= 64 rows)      */
 } rad_htree_stats;
 
 /* -------------------------------------------------------------------------
@@ -221,6 +224,17 @@ int rad_htree_export_block(const rad_htree* h, int64_t block, double* D, double*
 int rad_htree_free(rad_htree* h);
 
 const char* rad_last_error(void);
+
+/* ------------------------------------------------------------ tracing
+ * rad_launch_count: kernels this library has launched in this process.
+ * rad_profile_enable(1) clears the record and starts timing the library's
+ * kernels with CUDA events on their launch streams (0 stops it).
+ * rad_profile_read aggregates the record by kernel name (synchronising the
+ * events): up to max_kernels entries, names as 48-byte NUL-terminated slots,
+ * launch counts and summed milliseconds; returns the number of names. */
+int64_t rad_launch_count(void);
+int rad_profile_enable(int32_t on);
+int rad_profile_read(int32_t max_kernels, char* names, int64_t* counts, double* total_ms);
 
 /* Library version: major * 10000 + minor * 100 + patch. */
 int rad_version(void);

@@ -61,7 +61,8 @@ class _Stats(C.Structure):
                 ("n_admissible", C.c_int64), ("compressed", C.c_int32), ("factor_dtype", C.c_int32),
                 ("near_dtype", C.c_int32), ("max_rank_used", C.c_int32), ("n_dense_fallback", C.c_int64),
                 ("near_entries", C.c_int64), ("far_entries", C.c_int64), ("sum_rank", C.c_int64),
-                ("aca_entries", C.c_int64), ("bytes_near", C.c_int64), ("bytes_far", C.c_int64)]
+                ("aca_entries", C.c_int64), ("bytes_near", C.c_int64), ("bytes_far", C.c_int64),
+                ("far_u_entries", C.c_int64), ("far_v_entries", C.c_int64), ("n_tiles", C.c_int64)]
 
 
 def _load():
@@ -88,6 +89,9 @@ def _load():
         "rad_htree_export_blocks": (C.c_int, [H, vp, vp, vp, vp]),
         "rad_htree_export_block": (C.c_int, [H, i64, vp, vp, vp]),
         "rad_htree_free": (C.c_int, [H]),
+        "rad_launch_count": (C.c_int64, []),
+        "rad_profile_enable": (C.c_int, [i32]),
+        "rad_profile_read": (C.c_int, [i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -363,6 +367,29 @@ def rad_htree_export_block(h: HTree, b: int, m: int, n: int, rank: int):
 
 def rad_htree_free(h: HTree) -> None:
     h.free()
+
+
+def rad_launch_count() -> int:
+    """Kernels launched by librad in this process."""
+    return int(_lib.rad_launch_count())
+
+
+def rad_profile_enable(on: bool = True) -> None:
+    """Start (clearing the record) or stop per-kernel CUDA-event timing."""
+    _check(_lib.rad_profile_enable(1 if on else 0))
+
+
+def rad_profile_read(max_kernels: int = 64) -> dict:
+    """{kernel name: (launches, total ms)} of the profile record."""
+    names = C.create_string_buffer(48 * max_kernels)
+    counts = np.zeros(max_kernels, np.int64)
+    ms = np.zeros(max_kernels, np.float64)
+    k = _lib.rad_profile_read(max_kernels, names, C.c_void_p(counts.ctypes.data), C.c_void_p(ms.ctypes.data))
+    out = {}
+    for i in range(min(k, max_kernels)):
+        nm = names.raw[48 * i:48 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(counts[i]), float(ms[i]))
+    return out
 
 
 __all__ = [n for n in dir() if n.startswith("rad_")] + ["HTree", "RadError", "SIGMA_SB", "header_functions"]

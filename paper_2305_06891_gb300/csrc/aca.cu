@@ -334,11 +334,11 @@ void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>
         CT* R = ws.get_n<CT>(std::max<long long>(sr, 1));
         long long* d_offR = ws.get_n<long long>(nj);
         h2d(d_offR, offR, s);
-        aca_full_kernel<CT><<<nj, kAcaNT, 0, s>>>(g, d_jobs, d_order, Us, Vs, R, d_offR, d_rank, d_evals, p->tol);
+        { ProfScope ps_("aca_full", s); aca_full_kernel<CT><<<nj, kAcaNT, 0, s>>>(g, d_jobs, d_order, Us, Vs, R, d_offR, d_rank, d_evals, p->tol); }
     } else {
         unsigned char* used = ws.get_n<unsigned char>(std::max<long long>(sused, 1));
         RAD_CUDA(cudaMemsetAsync(used, 0, std::max<long long>(sused, 1), s));
-        aca_partial_kernel<CT><<<nj, kAcaNT, 0, s>>>(g, d_jobs, d_order, Us, Vs, used, d_rank, d_evals, p->tol);
+        { ProfScope ps_("aca_partial", s); aca_partial_kernel<CT><<<nj, kAcaNT, 0, s>>>(g, d_jobs, d_order, Us, Vs, used, d_rank, d_evals, p->tol); }
     }
     RAD_CHECK_LAUNCH();
     ranks.resize(nj);
@@ -362,7 +362,7 @@ void launch_near(rad_htree* h, cudaStream_t s) {
     NearWork* d_work = ws.get_n<NearWork>(work.size());
     h2d(d_work, work, s);
     const Geo g = geo_view(h->geo.as<double>(), h->n);
-    near_assemble_kernel<S, CT><<<(unsigned)work.size(), 256, 0, s>>>(g, d_nd, d_work, h->near_pool.as<S>());
+    { ProfScope ps_("near_assemble", s); near_assemble_kernel<S, CT><<<(unsigned)work.size(), 256, 0, s>>>(g, d_nd, d_work, h->near_pool.as<S>()); }
     RAD_CHECK_LAUNCH();
 }
 
@@ -372,7 +372,7 @@ void launch_pack(rad_htree* h, const std::vector<PackJob>& jobs, const CT* Us, c
     Scratch ws(s);
     PackJob* d_jobs = ws.get_n<PackJob>(jobs.size());
     h2d(d_jobs, jobs, s);
-    pack_kernel<CT, S><<<(unsigned)jobs.size(), 256, 0, s>>>(d_jobs, Us, Vs, h->far_pool.as<S>());
+    { ProfScope ps_("aca_pack", s); pack_kernel<CT, S><<<(unsigned)jobs.size(), 256, 0, s>>>(d_jobs, Us, Vs, h->far_pool.as<S>()); }
     RAD_CHECK_LAUNCH();
 }
 
@@ -572,7 +572,7 @@ void load_dense_operator(rad_htree* h, const double* F_dev, cudaStream_t s) {
     h->near_pool.alloc(sizeof(double) * (size_t)n * n);
     h->far_pool.alloc(16 * sizeof(double));
     const long long nn = (long long)n * n;
-    transpose_dense_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, F_dev, h->near_pool.as<double>());
+    { ProfScope ps_("dense_load", s); transpose_dense_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, F_dev, h->near_pool.as<double>()); }
     RAD_CHECK_LAUNCH();
     h->near_entries = nn;
     h->far_entries = 0;

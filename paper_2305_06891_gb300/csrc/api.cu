@@ -1,11 +1,15 @@
 // C ABI entry points of librad (declared in include/rad.h).  Every entry
 // point catches all C++ exceptions and turns them into status codes.
 
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
+#include <string>
 
 #include "rad_common.cuh"
 
@@ -17,6 +21,69 @@ thread_local std::string g_last_error;
 
 void fail(int code, const std::string& msg) { throw Error{code, msg}; }
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+// ------------------------------------------------------------ launch accounting
+namespace {
+std::atomic<long long> g_launches{0};
+struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(const char* name, cudaStream_t st) : s(st) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    ProfRec r{name, nullptr, nullptr};
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    cudaEventRecord(r.a, s);
+    idx = (int)g_prof.size();
+    g_prof.push_back(r);
+}
+ProfScope::~ProfScope() {
+    if (idx < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (idx < (int)g_prof.size()) cudaEventRecord(g_prof[idx].b, s);
+}
+
+static void clear_profile() {
+    for (auto& r : g_prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_prof.clear();
+}
+
+// Keep freed stream-ordered allocations cached in the device's default pool
+// (process-local setting), so that repeated calls do not return memory to
+// the driver and allocate it again.
+static void keep_pool_warm() {
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    for (int d : done)
+        if (d == dev) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    (void)cudaGetLastError();
+    done.push_back(dev);
+}
 
 void DevBuf::alloc(size_t b) {
     release();
@@ -68,6 +135,7 @@ static const void* stage_in_2d(const void* p, int64_t rows, int64_t cols, int64_
 template <class F>
 static int guarded(F&& f) {
     try {
+        keep_pool_warm();
         f();
         return RAD_OK;
     } catch (const Error& e) {
@@ -99,6 +167,42 @@ using namespace rad;
 extern "C" {
 
 int rad_version(void) { return 10000; }
+
+int64_t rad_launch_count(void) { return g_launches.load(); }
+
+int rad_profile_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    clear_profile();
+    g_prof_on = on != 0;
+    return RAD_OK;
+}
+
+int rad_profile_read(int32_t max_kernels, char* names, int64_t* counts, double* total_ms) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::map<std::string, std::pair<int64_t, double>> agg;
+    for (auto& r : g_prof) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        auto& e = agg[r.name];
+        e.first += 1;
+        e.second += ms;
+    }
+    int k = 0;
+    for (auto& kv : agg) {
+        if (k >= max_kernels) break;
+        if (names) {
+            std::strncpy(names + 48 * k, kv.first.c_str(), 47);
+            names[48 * k + 47] = 0;
+        }
+        if (counts) counts[k] = kv.second.first;
+        if (total_ms) total_ms[k] = kv.second.second;
+        ++k;
+    }
+    return (int)agg.size();
+}
 
 const char* rad_last_error(void) { return g_last_error.c_str(); }
 
@@ -304,6 +408,11 @@ int rad_htree_get_stats(const rad_htree* h, rad_htree_stats* st) {
         st->aca_entries = h->aca_entries;
         st->bytes_near = h->near_entries * dtype_size(h->near_dtype);
         st->bytes_far = h->far_entries * dtype_size(h->factor_dtype);
+        for (auto& f : h->far_h) {
+            st->far_u_entries += (int64_t)f.k * f.m;
+            st->far_v_entries += (int64_t)f.k * f.n;
+        }
+        st->n_tiles = h->n_tiles;
     });
 }
 

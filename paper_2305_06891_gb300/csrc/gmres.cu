@@ -225,10 +225,10 @@ struct ColReducer {
     // out[l][c] (+)= sum_i A_l[i][c] Bv[i][c]
     void dots(const double* A, long long strideA, int L, const double* Bv, double* out, bool accumulate) {
         dim3 grid(chunks, (nc + 31) / 32);
-        mdot_kernel<<<grid, 256, 0, s>>>(A, strideA, L, Bv, n, nc, partial);
+        { ProfScope ps_("gmres_dots", s); mdot_kernel<<<grid, 256, 0, s>>>(A, strideA, L, Bv, n, nc, partial); }
         RAD_CHECK_LAUNCH();
-        reduce_chunks_kernel<<<grid_for((long long)L * nc), 256, 0, s>>>(partial, chunks, L, nc, out,
-                                                                          accumulate ? 1 : 0);
+        { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<grid_for((long long)L * nc), 256, 0, s>>>(partial, chunks, L, nc, out,
+                                                                          accumulate ? 1 : 0); }
         RAD_CHECK_LAUNCH();
     }
 };
@@ -300,9 +300,9 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
         }
         prev_max = max_rel;
         RAD_CUDA(cudaMemcpyAsync(active, hact.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
-        start_cycle_kernel<<<grid_for(nv), 256, 0, s>>>(W, beta2, active, V, X32, n, nc);
+        { ProfScope ps_("gmres_small", s); start_cycle_kernel<<<grid_for(nv), 256, 0, s>>>(W, beta2, active, V, X32, n, nc); }
         RAD_CHECK_LAUNCH();
-        init_g_kernel<<<grid_for(nc), 128, 0, s>>>(R, nc, beta2, g, jc);
+        { ProfScope ps_("gmres_small", s); init_g_kernel<<<grid_for(nc), 128, 0, s>>>(R, nc, beta2, g, jc); }
         RAD_CHECK_LAUNCH();
         for (int j = 0; j < R && total_iters < p->max_iter; ++j) {
             double* Vj = V + (long long)j * nv;
@@ -314,19 +314,19 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
             for (int pass = 0; pass < 2; ++pass) {
                 double* hbuf = pass == 0 ? hcol : ycoef;  // ycoef doubles as scratch here
                 red.dots(V, nv, j + 1, W, hbuf, false);
-                cgs_update_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, j + 1, hbuf, active, W, n, nc);
+                { ProfScope ps_("gmres_cgs_update", s); cgs_update_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, j + 1, hbuf, active, W, n, nc); }
                 RAD_CHECK_LAUNCH();
                 if (pass == 1) {
-                    reduce_chunks_kernel<<<grid_for((long long)(j + 1) * nc), 256, 0, s>>>(ycoef, 1, j + 1, nc,
-                                                                                            hcol, 1);
+                    { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<grid_for((long long)(j + 1) * nc), 256, 0, s>>>(ycoef, 1, j + 1, nc,
+                                                                                            hcol, 1); }
                     RAD_CHECK_LAUNCH();
                 }
             }
             red.dots(W, 0, 1, W, hn2, false);
-            normalize_kernel<<<grid_for(nv), 256, 0, s>>>(W, hn2, active, V + (long long)(j + 1) * nv, X32, n, nc);
+            { ProfScope ps_("gmres_normalize", s); normalize_kernel<<<grid_for(nv), 256, 0, s>>>(W, hn2, active, V + (long long)(j + 1) * nv, X32, n, nc); }
             RAD_CHECK_LAUNCH();
-            givens_kernel<<<grid_for(nc, 128), 128, 0, s>>>(j, R, nc, Hm, hn2, cs, sn, g, bnorm, resid, active, jc,
-                                                            tol);
+            { ProfScope ps_("gmres_small", s); givens_kernel<<<grid_for(nc, 128), 128, 0, s>>>(j, R, nc, Hm, hn2, cs, sn, g, bnorm, resid, active, jc,
+                                                            tol); }
             RAD_CHECK_LAUNCH();
             ++total_iters;
             RAD_CUDA(cudaMemcpyAsync(hact.data(), active, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
@@ -336,13 +336,13 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
             if (still == 0) break;
         }
         // x += V y
-        trisolve_kernel<<<grid_for(nc, 128), 128, 0, s>>>(R, nc, Hm, g, jc, ycoef);
+        { ProfScope ps_("gmres_small", s); trisolve_kernel<<<grid_for(nc, 128), 128, 0, s>>>(R, nc, Hm, g, jc, ycoef); }
         RAD_CHECK_LAUNCH();
-        update_x_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, R, ycoef, jc, X, n, nc);
+        { ProfScope ps_("gmres_update_x", s); update_x_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, R, ycoef, jc, X, n, nc); }
         RAD_CHECK_LAUNCH();
         // true residual r = b - C x
         if (X32) {
-            to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(X, X32, nv);
+            { ProfScope ps_("gmres_convert", s); to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(X, X32, nv); }
             RAD_CHECK_LAUNCH();
         }
         apply_C(X, X32, W, kResid);
@@ -371,7 +371,7 @@ void solve_flux(const rad_htree* h, const double* eps_dev, const double* T_dev, 
     double* eps_t = ws.get_n<double>(n);
     double* B = ws.get_n<double>(nv);
     double* X = ws.get_n<double>(nv);
-    rhs_kernel<<<grid_for(nv), 256, 0, s>>>(n, m, eps_dev, T_dev, ldT, h->perm.as<int>(), eps_t, B);
+    { ProfScope ps_("gmres_rhs", s); rhs_kernel<<<grid_for(nv), 256, 0, s>>>(n, m, eps_dev, T_dev, ldT, h->perm.as<int>(), eps_t, B); }
     RAD_CHECK_LAUNCH();
     rad_solve_info local{};
     gmres_tree(h, eps_t, B, nc, p, X, &local, ws, s);
@@ -380,16 +380,16 @@ void solve_flux(const rad_htree* h, const double* eps_dev, const double* T_dev, 
     if (op64) {
         double* FY = ws.get_n<double>(nv);
         apply_tree(h, X, nc, FY, nc, nc, Epi{kStore, nullptr, nullptr, nullptr, 0}, Tws, s);
-        flux_kernel<double><<<grid_for((long long)n * m), 256, 0, s>>>(n, m, FY, h->perm.as<int>(), eps_dev, T_dev,
-                                                                      ldT, sigma, q_dev, ldq);
+        { ProfScope ps_("flux", s); flux_kernel<double><<<grid_for((long long)n * m), 256, 0, s>>>(n, m, FY, h->perm.as<int>(), eps_dev, T_dev,
+                                                                      ldT, sigma, q_dev, ldq); }
     } else {
         float* X32 = ws.get_n<float>(nv);
         float* FY = ws.get_n<float>(nv);
-        to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(X, X32, nv);
+        { ProfScope ps_("gmres_convert", s); to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(X, X32, nv); }
         RAD_CHECK_LAUNCH();
         apply_tree(h, X32, nc, FY, nc, nc, Epi{kStore, nullptr, nullptr, nullptr, 0}, Tws, s);
-        flux_kernel<float><<<grid_for((long long)n * m), 256, 0, s>>>(n, m, FY, h->perm.as<int>(), eps_dev, T_dev,
-                                                                     ldT, sigma, q_dev, ldq);
+        { ProfScope ps_("flux", s); flux_kernel<float><<<grid_for((long long)n * m), 256, 0, s>>>(n, m, FY, h->perm.as<int>(), eps_dev, T_dev,
+                                                                     ldT, sigma, q_dev, ldq); }
     }
     RAD_CHECK_LAUNCH();
     ++local.matvecs;

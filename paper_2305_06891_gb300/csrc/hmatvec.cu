@@ -246,10 +246,10 @@ void launch_multi(const rad_htree* h, const AT* X, int ldx, AT* T, int ldt, void
                   const Epi& epi, cudaStream_t s) {
     const OpView op = h->view();
     if (op.n_far_nz > 0) {
-        phase1_multi<FS, AT, RN><<<op.n_far_nz, 256, 0, s>>>(op, X, ldx, T, ldt, nc);
+        { ProfScope ps_("hmm_far_vt", s); phase1_multi<FS, AT, RN><<<op.n_far_nz, 256, 0, s>>>(op, X, ldx, T, ldt, nc); }
         RAD_CHECK_LAUNCH();
     }
-    phase2_multi<NS, FS, AT, RN><<<op.n_tiles, 256, 0, s>>>(op, X, ldx, T, ldt, Y, ldy, nc, epi);
+    { ProfScope ps_("hmm_rows", s); phase2_multi<NS, FS, AT, RN><<<op.n_tiles, 256, 0, s>>>(op, X, ldx, T, ldt, Y, ldy, nc, epi); }
     RAD_CHECK_LAUNCH();
 }
 
@@ -259,10 +259,10 @@ void apply_t(const rad_htree* h, const AT* X, int ldx, void* Y, int ldy, int nrh
     const OpView op = h->view();
     if (nrhs == 1) {
         if (op.sum_rank > 0) {
-            phase1_single<FS, AT><<<(op.sum_rank + 7) / 8, 256, 0, s>>>(op, X, T);
+            { ProfScope ps_("hmv_far_vt", s); phase1_single<FS, AT><<<(op.sum_rank + 7) / 8, 256, 0, s>>>(op, X, T); }
             RAD_CHECK_LAUNCH();
         }
-        phase2_single<NS, FS, AT><<<op.n_tiles, 256, 0, s>>>(op, X, T, Y, epi);
+        { ProfScope ps_("hmv_rows", s); phase2_single<NS, FS, AT><<<op.n_tiles, 256, 0, s>>>(op, X, T, Y, epi); }
         RAD_CHECK_LAUNCH();
         return;
     }
@@ -337,11 +337,11 @@ void gather_user_to_tree(const rad_htree* h, int dtype_in, const void* x, int64_
     const unsigned grid = (unsigned)((tot + 255) / 256);
     const int* perm = h->perm.as<int>();
     if (dtype_in == RAD_F64) {
-        if (op64) gather_kernel<double, double><<<grid, 256, 0, s>>>(n, nrhs, (const double*)x, ldx, perm, (double*)X, ldX);
-        else gather_kernel<double, float><<<grid, 256, 0, s>>>(n, nrhs, (const double*)x, ldx, perm, (float*)X, ldX);
+        if (op64) { ProfScope ps_("permute", s); gather_kernel<double, double><<<grid, 256, 0, s>>>(n, nrhs, (const double*)x, ldx, perm, (double*)X, ldX); }
+        else { ProfScope ps_("permute", s); gather_kernel<double, float><<<grid, 256, 0, s>>>(n, nrhs, (const double*)x, ldx, perm, (float*)X, ldX); }
     } else {
-        if (op64) gather_kernel<float, double><<<grid, 256, 0, s>>>(n, nrhs, (const float*)x, ldx, perm, (double*)X, ldX);
-        else gather_kernel<float, float><<<grid, 256, 0, s>>>(n, nrhs, (const float*)x, ldx, perm, (float*)X, ldX);
+        if (op64) { ProfScope ps_("permute", s); gather_kernel<float, double><<<grid, 256, 0, s>>>(n, nrhs, (const float*)x, ldx, perm, (double*)X, ldX); }
+        else { ProfScope ps_("permute", s); gather_kernel<float, float><<<grid, 256, 0, s>>>(n, nrhs, (const float*)x, ldx, perm, (float*)X, ldX); }
     }
     RAD_CHECK_LAUNCH();
 }
@@ -353,11 +353,11 @@ void scatter_tree_to_user(const rad_htree* h, const void* Y, int ldY, int nrhs, 
     const unsigned grid = (unsigned)((tot + 255) / 256);
     const int* perm = h->perm.as<int>();
     if (dtype_out == RAD_F64) {
-        if (op64) scatter_kernel<double, double><<<grid, 256, 0, s>>>(n, nrhs, (const double*)Y, ldY, perm, (double*)y, ldy);
-        else scatter_kernel<float, double><<<grid, 256, 0, s>>>(n, nrhs, (const float*)Y, ldY, perm, (double*)y, ldy);
+        if (op64) { ProfScope ps_("permute", s); scatter_kernel<double, double><<<grid, 256, 0, s>>>(n, nrhs, (const double*)Y, ldY, perm, (double*)y, ldy); }
+        else { ProfScope ps_("permute", s); scatter_kernel<float, double><<<grid, 256, 0, s>>>(n, nrhs, (const float*)Y, ldY, perm, (double*)y, ldy); }
     } else {
-        if (op64) scatter_kernel<double, float><<<grid, 256, 0, s>>>(n, nrhs, (const double*)Y, ldY, perm, (float*)y, ldy);
-        else scatter_kernel<float, float><<<grid, 256, 0, s>>>(n, nrhs, (const float*)Y, ldY, perm, (float*)y, ldy);
+        if (op64) { ProfScope ps_("permute", s); scatter_kernel<double, float><<<grid, 256, 0, s>>>(n, nrhs, (const double*)Y, ldY, perm, (float*)y, ldy); }
+        else { ProfScope ps_("permute", s); scatter_kernel<float, float><<<grid, 256, 0, s>>>(n, nrhs, (const float*)Y, ldY, perm, (float*)y, ldy); }
     }
     RAD_CHECK_LAUNCH();
 }

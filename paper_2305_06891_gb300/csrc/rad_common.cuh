@@ -31,7 +31,24 @@ void set_last_error(const std::string& msg);
         }                                                                         \
     } while (0)
 
-#define RAD_CHECK_LAUNCH() RAD_CUDA(cudaGetLastError())
+void note_launch();
+#define RAD_CHECK_LAUNCH()                \
+    do {                                  \
+        ::rad::note_launch();             \
+        RAD_CUDA(cudaGetLastError());     \
+    } while (0)
+
+// Optional per-kernel event timing (rad_profile_enable).  A scope records a
+// start event on construction and a stop event on destruction, on the given
+// stream; it costs nothing while profiling is off.
+struct ProfScope {
+    int idx = -1;
+    cudaStream_t s;
+    ProfScope(const char* name, cudaStream_t st);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+};
 
 #define RAD_REQUIRE(cond, code, msg)          \
     do {                                      \

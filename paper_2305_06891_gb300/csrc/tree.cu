@@ -338,7 +338,7 @@ void build_geometry_from_tris(rad_htree* h, const double* verts_dev, double* geo
     int* bad = ws.get_n<int>(1);
     RAD_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
     const int n = (int)h->n;
-    geometry_tris_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, verts_dev, geo_user, bad);
+    { ProfScope ps_("geometry", s); geometry_tris_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, verts_dev, geo_user, bad); }
     RAD_CHECK_LAUNCH();
     int hb = 0;
     RAD_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -352,7 +352,7 @@ void build_geometry_from_facets(rad_htree* h, const double* c, const double* nrm
     int* bad = ws.get_n<int>(1);
     RAD_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
     const int n = (int)h->n;
-    geometry_facets_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, c, nrm, a, geo_user, bad);
+    { ProfScope ps_("geometry", s); geometry_facets_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, c, nrm, a, geo_user, bad); }
     RAD_CHECK_LAUNCH();
     int hb = 0;
     RAD_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -404,8 +404,8 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     const double* cz = geo_user + 2ll * n;
     for (int lv = 0; lv < depth; ++lv) {
         const int cnt = level_first[lv + 1] - level_first[lv];
-        tree_level_kernel<<<cnt, kTreeNT, 0, s>>>(d_shapes, d_boxes, level_first[lv], cx, cy, cz,
-                                                  idx[lv & 1], idx[(lv + 1) & 1], keys, err);
+        { ProfScope ps_("cluster_tree", s); tree_level_kernel<<<cnt, kTreeNT, 0, s>>>(d_shapes, d_boxes, level_first[lv], cx, cy, cz,
+                                                  idx[lv & 1], idx[(lv + 1) & 1], keys, err); }
         RAD_CHECK_LAUNCH();
     }
     int* perm_final = idx[depth & 1];
@@ -414,8 +414,8 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     h->iperm.alloc(sizeof(int) * n);
     h->geo.alloc(sizeof(double) * 7 * (size_t)n);
     RAD_CUDA(cudaMemcpyAsync(h->perm.p, perm_final, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
-    gather_geo_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, geo_user, perm_final, h->geo.as<double>(),
-                                                      h->iperm.as<int>());
+    { ProfScope ps_("geometry", s); gather_geo_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, geo_user, perm_final, h->geo.as<double>(),
+                                                      h->iperm.as<int>()); }
     RAD_CHECK_LAUNCH();
 
     // block tree: single CTA, retry with larger buffers on overflow
@@ -429,8 +429,8 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
         int2* far_out = bw.get_n<int2>(cap);
         int2* near_out = bw.get_n<int2>(cap);
         int* counters = bw.get_n<int>(4);
-        block_tree_kernel<<<1, kTreeNT, 0, s>>>(d_shapes, d_boxes, h->eta, candA, candB, cap, far_out, cap,
-                                                near_out, cap, counters);
+        { ProfScope ps_("block_tree", s); block_tree_kernel<<<1, kTreeNT, 0, s>>>(d_shapes, d_boxes, h->eta, candA, candB, cap, far_out, cap,
+                                                near_out, cap, counters); }
         RAD_CHECK_LAUNCH();
         int hc[4];
         RAD_CUDA(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
