@@ -262,6 +262,7 @@ def rad_hmatvec(h: HTree, x, y=None, stream=None):
     else:
         dt = np.float64 if np.asarray(x).dtype == np.float64 else np.float32
     xc, n, nrhs, ldx = _colmajor(x, dt)
+    y_given = y is not None
     if y is None:
         if is_t:
             y = t.empty((nrhs, n), dtype=xc.dtype, device=xc.device).t()
@@ -272,7 +273,8 @@ def rad_hmatvec(h: HTree, x, y=None, stream=None):
         ldy = (y.stride(1) if y.dim() == 2 else n) if _is_tensor(y) else n
     _check(_lib.rad_hmatvec(h.ptr, RAD_F64 if dt == np.float64 else RAD_F32, _ptr(xc), ldx, _ptr(y), ldy,
                             nrhs, _stream(stream, xc, y)))
-    if (_is_tensor(x) and x.dim() == 1) or (not _is_tensor(x) and np.ndim(x) == 1):
+    one_d = (_is_tensor(x) and x.dim() == 1) or (not _is_tensor(x) and np.ndim(x) == 1)
+    if one_d and not y_given:
         return y[:, 0]
     return y
 

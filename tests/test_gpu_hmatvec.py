@@ -83,3 +83,16 @@ def test_device_strided_and_host_paths_agree(cyl):
     Xd = big.t()[:n]                                     # column-major view, ld = n + 7
     Yd = r.rad_hmatvec(h, Xd)
     np.testing.assert_array_equal(Yd.cpu().numpy(), Yh)
+
+
+def test_caller_provided_outputs(c1):
+    import torch
+    c, F = c1
+    r = rad()
+    h = r.rad_build_htree(c.verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-6, 64, "partial", "f32", "f32")
+    x = torch.as_tensor(c.T[:, 0], device="cuda", dtype=torch.float32)
+    y = torch.empty_like(x)
+    out = r.rad_hmatvec(h, x, y)
+    assert out.data_ptr() == y.data_ptr()
+    assert rel(y.cpu().numpy(), F @ c.T[:, 0]) <= 1e-6
