@@ -87,21 +87,31 @@ __device__ void cross_dots(const CT* a, const CT* B, int len, long long ld, int 
     __syncthreads();
 }
 
-template <class CT>
-__global__ void __launch_bounds__(kAcaNT)
-aca_partial_kernel(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict__ order, CT* Upool, CT* Vpool,
-                   unsigned char* used_pool, int* __restrict__ rank_out, long long* __restrict__ evals_out,
-                   double tol) {
-    __shared__ double s_row[kMaxRank];
-    __shared__ double part[kAcaNT / 32][kMaxRank + 1];
-    __shared__ double s_cv[kMaxRank + 1];
-    __shared__ double s_cu[kMaxRank + 1];
-    __shared__ ArgMax am_sm[kAcaNT / 32 + 1];
-    __shared__ int i_sm[kAcaNT / 32 + 1];
-    __shared__ double red_sm[kAcaNT / 32 + 1];
+// Shared memory of one ACA CTA: the CTA-wide path and the per-warp path.
+struct AcaSmem {
+    double s_row[kMaxRank];
+    double part[kAcaNT / 32][kMaxRank + 1];
+    double s_cv[kMaxRank + 1];
+    double s_cu[kMaxRank + 1];
+    ArgMax am_sm[kAcaNT / 32 + 1];
+    int i_sm[kAcaNT / 32 + 1];
+    double red_sm[kAcaNT / 32 + 1];
+    double w_a[kAcaNT / 32][kMaxRank];   // per warp: pivot row/column of U, V
+    double w_c[kAcaNT / 32][kMaxRank];   // per warp: (v_k . v_l)
+};
 
-    const int bidx = order[blockIdx.x];
-    const AcaJob jb = jobs[bidx];
+// One admissible block on a whole CTA (blocks larger than 256 x 256).
+template <class CT>
+__device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upool, CT* Vpool,
+                              unsigned char* used_pool, int* __restrict__ rank_out,
+                              long long* __restrict__ evals_out, double tol, AcaSmem& sm) {
+    double* s_row = sm.s_row;
+    double (*part)[kMaxRank + 1] = sm.part;
+    double* s_cv = sm.s_cv;
+    double* s_cu = sm.s_cu;
+    ArgMax* am_sm = sm.am_sm;
+    int* i_sm = sm.i_sm;
+    double* red_sm = sm.red_sm;
     const int m = jb.m, n = jb.n, kmax = jb.kmax;
     CT* U = Upool + jb.offU;
     CT* V = Vpool + jb.offV;
@@ -188,6 +198,156 @@ aca_partial_kernel(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict
         rank_out[bidx] = status == 1 ? k : -1;
         evals_out[bidx] = evals;
     }
+}
+
+
+// One admissible block (m, n <= 256) on a single warp: no block barriers,
+// shuffle reductions, and the used-row flags of rows lane + 32 t in bit t of
+// a register.  Same pivoting, stopping and verification rules as the CTA
+// path.
+template <class CT>
+__device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upool, CT* Vpool,
+                               int* __restrict__ rank_out, long long* __restrict__ evals_out, double tol,
+                               double* s_a, double* s_c) {
+    const int lane = threadIdx.x & 31;
+    const int m = jb.m, n = jb.n, kmax = jb.kmax;
+    CT* U = Upool + jb.offU;
+    CT* V = Vpool + jb.offV;
+    unsigned used = 0u;
+    int i = 0, k = 0, status = 0, checks = 0;
+    double norm2 = 0.0, scale = 0.0;
+    long long evals = 0;
+    for (int guard = 0; guard <= m + kmax + kMaxChecks + 2; ++guard) {
+        if (k >= kmax) { status = 2; break; }
+        for (int l = lane; l < k; l += 32) s_a[l] = (double)U[(long long)l * m + i];
+        __syncwarp();
+        CT* vk = V + (long long)k * n;
+        ArgMax best{-1.0, 0x7fffffff};
+        for (int j = lane; j < n; j += 32) {
+            CT r = Entry<CT>::eval(g, jb.r0 + i, jb.c0 + j);
+            for (int l = 0; l < k; ++l) r -= (CT)s_a[l] * V[(long long)l * n + j];
+            vk[j] = r;
+            best = am_better(best, ArgMax{fabs((double)r), j});
+        }
+        best = warp_argmax(best);
+        evals += n;
+        if ((i & 31) == lane) used |= 1u << (i >> 5);
+        if (!(best.v > fmax(1e-300, 1e-14 * scale))) {
+            int cand = 0x7fffffff;
+            for (int t = 0; t < 8 && lane + 32 * t < m; ++t)
+                if (!((used >> t) & 1u)) { cand = lane + 32 * t; break; }
+            cand = __reduce_min_sync(0xffffffffu, cand);
+            if (cand == 0x7fffffff) { status = 1; break; }
+            i = cand;
+            __syncwarp();
+            continue;
+        }
+        scale = fmax(scale, best.v);
+        const int jp = best.i;
+        __syncwarp();
+        const CT piv = vk[jp];
+        __syncwarp();
+        double vv = 0.0;
+        for (int j = lane; j < n; j += 32) {
+            const CT v = vk[j] / piv;
+            vk[j] = v;
+            vv += (double)v * (double)v;
+        }
+        vv = warp_sum(vv);
+        for (int l = 0; l < k; ++l) {
+            double p = 0.0;
+            for (int j = lane; j < n; j += 32) p += (double)vk[j] * (double)V[(long long)l * n + j];
+            p = warp_sum(p);
+            if (lane == 0) s_c[l] = p;
+        }
+        __syncwarp();
+        for (int l = lane; l < k; l += 32) s_a[l] = (double)V[(long long)l * n + jp];
+        __syncwarp();
+        CT* uk = U + (long long)k * m;
+        ArgMax bu{-1.0, 0x7fffffff};
+        double uu = 0.0;
+        for (int r = lane; r < m; r += 32) {
+            CT u = Entry<CT>::eval(g, jb.r0 + r, jb.c0 + jp);
+            for (int l = 0; l < k; ++l) u -= (CT)s_a[l] * U[(long long)l * m + r];
+            uk[r] = u;
+            uu += (double)u * (double)u;
+            if (!((used >> (r >> 5)) & 1u)) bu = am_better(bu, ArgMax{fabs((double)u), r});
+        }
+        uu = warp_sum(uu);
+        double cross = 0.0;
+        for (int l = 0; l < k; ++l) {
+            double p = 0.0;
+            for (int r = lane; r < m; r += 32) p += (double)uk[r] * (double)U[(long long)l * m + r];
+            p = warp_sum(p);
+            cross += p * s_c[l];
+        }
+        bu = warp_argmax(bu);
+        evals += m;
+        norm2 = norm2 + 2.0 * cross + uu * vv;
+        ++k;
+        if (sqrt(uu) * sqrt(vv) <= tol * sqrt(fmax(norm2, 0.0))) {
+            if (checks >= kMaxChecks) { status = 1; break; }
+            double r2 = 0.0;
+            ArgMax bs{-1.0, 0x7fffffff};
+            for (int t = 0; t < kSamples / 32; ++t) {
+                const int sidx = lane + 32 * t;
+                const int si = (int)(((long long)sidx * m) / kSamples);
+                const int sj = (int)(((unsigned long long)sidx * 2654435761ull +
+                                      (unsigned long long)checks * 40503ull) % (unsigned long long)n);
+                CT x = Entry<CT>::eval(g, jb.r0 + si, jb.c0 + sj);
+                for (int l = 0; l < k; ++l) x -= U[(long long)l * m + si] * V[(long long)l * n + sj];
+                r2 += (double)x * (double)x;
+                bs = am_better(bs, ArgMax{fabs((double)x), sidx});
+            }
+            r2 = warp_sum(r2);
+            bs = warp_argmax(bs);
+            ++checks;
+            evals += kSamples;
+            if (((double)m * (double)n / kSamples) * r2 <= tol * tol * fmax(norm2, 0.0)) { status = 1; break; }
+            int wi = (int)(((long long)bs.i * m) / kSamples);
+            const unsigned wused = __shfl_sync(0xffffffffu, (used >> (wi >> 5)) & 1u, wi & 31);
+            if (wused) {
+                int cand = 0x7fffffff;
+                for (int t = 0; t < 8 && lane + 32 * t < m; ++t)
+                    if (!((used >> t) & 1u)) { cand = lane + 32 * t; break; }
+                cand = __reduce_min_sync(0xffffffffu, cand);
+                if (cand == 0x7fffffff) { status = 1; break; }
+                wi = cand;
+            }
+            i = wi;
+            __syncwarp();
+            continue;
+        }
+        if (bu.v < 0.0) { status = 1; break; }
+        i = bu.i;
+        __syncwarp();
+    }
+    if (lane == 0) {
+        rank_out[bidx] = status == 1 ? k : -1;
+        evals_out[bidx] = evals;
+    }
+}
+
+// Blocks [0, n_big) of the grid take one large block each (CTA path); the
+// rest take eight small blocks each (one per warp).
+template <class CT>
+__global__ void __launch_bounds__(kAcaNT, 4)
+aca_partial_kernel(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict__ big, int n_big,
+                   const int* __restrict__ small, int n_small, CT* Upool, CT* Vpool, unsigned char* used_pool,
+                   int* __restrict__ rank_out, long long* __restrict__ evals_out, double tol) {
+    __shared__ AcaSmem sm;
+    if ((int)blockIdx.x < n_big) {
+        const int bidx = big[blockIdx.x];
+        const AcaJob jb = jobs[bidx];
+        aca_cta_block<CT>(g, jb, bidx, Upool, Vpool, used_pool, rank_out, evals_out, tol, sm);
+        return;
+    }
+    const int warp = threadIdx.x >> 5;
+    const int w = ((int)blockIdx.x - n_big) * (kAcaNT / 32) + warp;
+    if (w >= n_small) return;
+    const int bidx = small[w];
+    const AcaJob jb = jobs[bidx];
+    aca_warp_block<CT>(g, jb, bidx, Upool, Vpool, rank_out, evals_out, tol, sm.w_a[warp], sm.w_c[warp]);
 }
 
 // Full pivoting: the residual R (m x n, column-major) lives in scratch.
@@ -338,7 +498,18 @@ void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>
     } else {
         unsigned char* used = ws.get_n<unsigned char>(std::max<long long>(sused, 1));
         RAD_CUDA(cudaMemsetAsync(used, 0, std::max<long long>(sused, 1), s));
-        { ProfScope ps_("aca_partial", s); aca_partial_kernel<CT><<<nj, kAcaNT, 0, s>>>(g, d_jobs, d_order, Us, Vs, used, d_rank, d_evals, p->tol); }
+        std::vector<int> big, small;
+        for (int b : order) {
+            if (jobs[b].m <= 256 && jobs[b].n <= 256) small.push_back(b);
+            else big.push_back(b);
+        }
+        int* d_big = ws.get_n<int>(std::max<size_t>(1, big.size()));
+        int* d_small = ws.get_n<int>(std::max<size_t>(1, small.size()));
+        h2d(d_big, big, s);
+        h2d(d_small, small, s);
+        const int nb = (int)big.size(), nsm = (int)small.size();
+        const int grid = nb + (nsm + kAcaNT / 32 - 1) / (kAcaNT / 32);
+        { ProfScope ps_("aca_partial", s); aca_partial_kernel<CT><<<grid, kAcaNT, 0, s>>>(g, d_jobs, d_big, nb, d_small, nsm, Us, Vs, used, d_rank, d_evals, p->tol); }
     }
     RAD_CHECK_LAUNCH();
     ranks.resize(nj);
