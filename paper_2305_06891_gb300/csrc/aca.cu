@@ -100,7 +100,8 @@ struct AcaSmem {
     double w_c[kAcaNT / 32][kMaxRank];   // per warp: (v_k . v_l)
 };
 
-// One admissible block on a whole CTA (blocks larger than 256 x 256).
+// One admissible block on a whole CTA (blocks with more than 1024 rows or
+// 4096 columns).
 template <class CT>
 __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upool, CT* Vpool,
                               unsigned char* used_pool, int* __restrict__ rank_out,
@@ -201,10 +202,31 @@ __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upoo
 }
 
 
-// One admissible block (m, n <= 256) on a single warp: no block barriers,
-// shuffle reductions, and the used-row flags of rows lane + 32 t in bit t of
-// a register.  Same pivoting, stopping and verification rules as the CTA
-// path.
+// p[q] = sum_j a_j * B[(l0 + q) ld + j] over the warp (q < 4, l0 + q < k),
+// with the four shuffle reductions interleaved.
+template <class CT>
+__device__ __forceinline__ void warp_dots4(const CT* a, const CT* B, int len, long long ld, int l0, int k,
+                                           double p[4]) {
+    const int lane = threadIdx.x & 31;
+    const int nq = min(4, k - l0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p[q] = 0.0;
+    for (int j = lane; j < len; j += 32) {
+        const double aj = (double)a[j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < nq) p[q] += aj * (double)B[(long long)(l0 + q) * ld + j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) p[q] += __shfl_xor_sync(0xffffffffu, p[q], o);
+}
+
+// One admissible block (m <= 1024 rows) on a single warp: no block
+// barriers, shuffle reductions, and the used-row flags of rows lane + 32 t in
+// bit t of a register.  Same pivoting, stopping and verification rules as
+// the CTA path.
 template <class CT>
 __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upool, CT* Vpool,
                                int* __restrict__ rank_out, long long* __restrict__ evals_out, double tol,
@@ -234,7 +256,7 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
         if ((i & 31) == lane) used |= 1u << (i >> 5);
         if (!(best.v > fmax(1e-300, 1e-14 * scale))) {
             int cand = 0x7fffffff;
-            for (int t = 0; t < 8 && lane + 32 * t < m; ++t)
+            for (int t = 0; t < 32 && lane + 32 * t < m; ++t)
                 if (!((used >> t) & 1u)) { cand = lane + 32 * t; break; }
             cand = __reduce_min_sync(0xffffffffu, cand);
             if (cand == 0x7fffffff) { status = 1; break; }
@@ -254,11 +276,11 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
             vv += (double)v * (double)v;
         }
         vv = warp_sum(vv);
-        for (int l = 0; l < k; ++l) {
-            double p = 0.0;
-            for (int j = lane; j < n; j += 32) p += (double)vk[j] * (double)V[(long long)l * n + j];
-            p = warp_sum(p);
-            if (lane == 0) s_c[l] = p;
+        for (int l0 = 0; l0 < k; l0 += 4) {
+            double p[4];
+            warp_dots4<CT>(vk, V, n, n, l0, k, p);
+            if (lane == 0)
+                for (int q = 0; q < 4 && l0 + q < k; ++q) s_c[l0 + q] = p[q];
         }
         __syncwarp();
         for (int l = lane; l < k; l += 32) s_a[l] = (double)V[(long long)l * n + jp];
@@ -275,11 +297,10 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
         }
         uu = warp_sum(uu);
         double cross = 0.0;
-        for (int l = 0; l < k; ++l) {
-            double p = 0.0;
-            for (int r = lane; r < m; r += 32) p += (double)uk[r] * (double)U[(long long)l * m + r];
-            p = warp_sum(p);
-            cross += p * s_c[l];
+        for (int l0 = 0; l0 < k; l0 += 4) {
+            double p[4];
+            warp_dots4<CT>(uk, U, m, m, l0, k, p);
+            for (int q = 0; q < 4 && l0 + q < k; ++q) cross += p[q] * s_c[l0 + q];
         }
         bu = warp_argmax(bu);
         evals += m;
@@ -308,7 +329,7 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
             const unsigned wused = __shfl_sync(0xffffffffu, (used >> (wi >> 5)) & 1u, wi & 31);
             if (wused) {
                 int cand = 0x7fffffff;
-                for (int t = 0; t < 8 && lane + 32 * t < m; ++t)
+                for (int t = 0; t < 32 && lane + 32 * t < m; ++t)
                     if (!((used >> t) & 1u)) { cand = lane + 32 * t; break; }
                 cand = __reduce_min_sync(0xffffffffu, cand);
                 if (cand == 0x7fffffff) { status = 1; break; }
@@ -500,7 +521,7 @@ void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>
         RAD_CUDA(cudaMemsetAsync(used, 0, std::max<long long>(sused, 1), s));
         std::vector<int> big, small;
         for (int b : order) {
-            if (jobs[b].m <= 256 && jobs[b].n <= 256) small.push_back(b);
+            if (jobs[b].m <= 1024 && jobs[b].n <= 4096) small.push_back(b);
             else big.push_back(b);
         }
         int* d_big = ws.get_n<int>(std::max<size_t>(1, big.size()));
