@@ -72,11 +72,11 @@ __device__ void cross_dots(const CT* a, const CT* B, int len, long long ld, int 
                            double* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int l = 0; l <= k; ++l) {
-        double s = 0.0;
+        CT s = 0;
         const CT* bl = (l < k) ? B + (long long)l * ld : a;
-        for (int j = threadIdx.x; j < len; j += kAcaNT) s += (double)a[j] * (double)bl[j];
+        for (int j = threadIdx.x; j < len; j += kAcaNT) s += a[j] * bl[j];
         s = warp_sum(s);
-        if (lane == 0) part[warp][l] = s;
+        if (lane == 0) part[warp][l] = (double)s;
     }
     __syncthreads();
     if ((int)threadIdx.x <= k) {
@@ -88,15 +88,18 @@ __device__ void cross_dots(const CT* a, const CT* B, int len, long long ld, int 
 }
 
 // Shared memory of one ACA CTA: the CTA-wide path and the per-warp path.
+// Per-element arithmetic runs in CT; only per-step scalars (cross terms,
+// the running ||S_k||^2) are FP64.
+template <class CT>
 struct AcaSmem {
-    double s_row[kMaxRank];
+    CT s_row[kMaxRank];
     double part[kAcaNT / 32][kMaxRank + 1];
     double s_cv[kMaxRank + 1];
     double s_cu[kMaxRank + 1];
-    ArgMax am_sm[kAcaNT / 32 + 1];
+    ArgMaxT<CT> am_sm[kAcaNT / 32 + 1];
     int i_sm[kAcaNT / 32 + 1];
-    double red_sm[kAcaNT / 32 + 1];
-    double w_a[kAcaNT / 32][kMaxRank];   // per warp: pivot row/column of U, V
+    CT red_sm[kAcaNT / 32 + 1];
+    CT w_a[kAcaNT / 32][kMaxRank];       // per warp: pivot row/column of U, V
     double w_c[kAcaNT / 32][kMaxRank];   // per warp: (v_k . v_l)
 };
 
@@ -105,14 +108,14 @@ struct AcaSmem {
 template <class CT>
 __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upool, CT* Vpool,
                               unsigned char* used_pool, int* __restrict__ rank_out,
-                              long long* __restrict__ evals_out, double tol, AcaSmem& sm) {
-    double* s_row = sm.s_row;
+                              long long* __restrict__ evals_out, double tol, AcaSmem<CT>& sm) {
+    CT* s_row = sm.s_row;
     double (*part)[kMaxRank + 1] = sm.part;
     double* s_cv = sm.s_cv;
     double* s_cu = sm.s_cu;
-    ArgMax* am_sm = sm.am_sm;
+    ArgMaxT<CT>* am_sm = sm.am_sm;
     int* i_sm = sm.i_sm;
-    double* red_sm = sm.red_sm;
+    CT* red_sm = sm.red_sm;
     const int m = jb.m, n = jb.n, kmax = jb.kmax;
     CT* U = Upool + jb.offU;
     CT* V = Vpool + jb.offV;
@@ -124,27 +127,27 @@ __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upoo
     for (int guard = 0; guard <= m + kmax + kMaxChecks + 2; ++guard) {
         if (k >= kmax) { status = 2; break; }
         // residual of pivot row i: X(i,:) - sum_l U(i,l) V(:,l)
-        if ((int)threadIdx.x < k) s_row[threadIdx.x] = (double)U[(long long)threadIdx.x * m + i];
+        if ((int)threadIdx.x < k) s_row[threadIdx.x] = U[(long long)threadIdx.x * m + i];
         __syncthreads();
         CT* vk = V + (long long)k * n;
-        ArgMax best{-1.0, 0x7fffffff};
+        ArgMaxT<CT> best{CT(-1), 0x7fffffff};
         for (int j = threadIdx.x; j < n; j += kAcaNT) {
             CT r = Entry<CT>::eval(g, jb.r0 + i, jb.c0 + j);
-            for (int l = 0; l < k; ++l) r -= (CT)s_row[l] * V[(long long)l * n + j];
+            for (int l = 0; l < k; ++l) r -= s_row[l] * V[(long long)l * n + j];
             vk[j] = r;
-            best = am_better(best, ArgMax{fabs((double)r), j});
+            best = am_better(best, ArgMaxT<CT>{fabs(r), j});
         }
         best = block_argmax<kAcaNT>(best, am_sm);
         evals += n;
         if (threadIdx.x == 0) used[i] = 1;
         __syncthreads();
-        if (!(best.v > fmax(1e-300, 1e-14 * scale))) {
+        if (!((double)best.v > fmax(1e-300, 1e-14 * scale))) {
             const int nxt = lowest_unused(used, m, i_sm);
             if (nxt < 0) { status = 1; break; }
             i = nxt;
             continue;
         }
-        scale = fmax(scale, best.v);
+        scale = fmax(scale, (double)best.v);
         const int jp = best.i;
         const CT piv = vk[jp];
         __syncthreads();
@@ -152,15 +155,15 @@ __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upoo
         // (v_k . v_l) for l < k and |v_k|^2; each thread reads its own j
         cross_dots<CT>(vk, V, n, n, k, part, s_cv);
         // residual of pivot column jp
-        if ((int)threadIdx.x < k) s_row[threadIdx.x] = (double)V[(long long)threadIdx.x * n + jp];
+        if ((int)threadIdx.x < k) s_row[threadIdx.x] = V[(long long)threadIdx.x * n + jp];
         __syncthreads();
         CT* uk = U + (long long)k * m;
-        ArgMax bu{-1.0, 0x7fffffff};
+        ArgMaxT<CT> bu{CT(-1), 0x7fffffff};
         for (int r = threadIdx.x; r < m; r += kAcaNT) {
             CT u = Entry<CT>::eval(g, jb.r0 + r, jb.c0 + jp);
-            for (int l = 0; l < k; ++l) u -= (CT)s_row[l] * U[(long long)l * m + r];
+            for (int l = 0; l < k; ++l) u -= s_row[l] * U[(long long)l * m + r];
             uk[r] = u;
-            if (!used[r]) bu = am_better(bu, ArgMax{fabs((double)u), r});
+            if (!used[r]) bu = am_better(bu, ArgMaxT<CT>{fabs(u), r});
         }
         evals += m;
         cross_dots<CT>(uk, U, m, m, k, part, s_cu);
@@ -179,8 +182,8 @@ __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upoo
                                  (unsigned long long)n);
             CT x = Entry<CT>::eval(g, jb.r0 + si, jb.c0 + sj);
             for (int l = 0; l < k; ++l) x -= U[(long long)l * m + si] * V[(long long)l * n + sj];
-            const double r2 = block_sum<kAcaNT, double>((double)x * (double)x, red_sm);
-            const ArgMax bs = block_argmax<kAcaNT>(ArgMax{fabs((double)x), sidx}, am_sm);
+            const double r2 = (double)block_sum<kAcaNT, CT>(x * x, red_sm);
+            const ArgMaxT<CT> bs = block_argmax<kAcaNT>(ArgMaxT<CT>{fabs(x), sidx}, am_sm);
             ++checks;
             evals += kSamples;
             if (((double)m * (double)n / kSamples) * r2 <= tol * tol * fmax(norm2, 0.0)) { status = 1; break; }
@@ -192,7 +195,7 @@ __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upoo
             i = wi;
             continue;
         }
-        if (bu.v < 0.0) { status = 1; break; }
+        if (bu.v < CT(0)) { status = 1; break; }
         i = bu.i;
     }
     if (threadIdx.x == 0) {
@@ -209,18 +212,19 @@ __device__ __forceinline__ void warp_dots4(const CT* a, const CT* B, int len, lo
                                            double p[4]) {
     const int lane = threadIdx.x & 31;
     const int nq = min(4, k - l0);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) p[q] = 0.0;
+    CT t[4] = {CT(0), CT(0), CT(0), CT(0)};
     for (int j = lane; j < len; j += 32) {
-        const double aj = (double)a[j];
+        const CT aj = a[j];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (q < nq) p[q] += aj * (double)B[(long long)(l0 + q) * ld + j];
+            if (q < nq) t[q] += aj * B[(long long)(l0 + q) * ld + j];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) p[q] += __shfl_xor_sync(0xffffffffu, p[q], o);
+        for (int q = 0; q < 4; ++q) t[q] += __shfl_xor_sync(0xffffffffu, t[q], o);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p[q] = (double)t[q];
 }
 
 // One admissible block (m <= 1024 rows) on a single warp: no block
@@ -230,7 +234,7 @@ __device__ __forceinline__ void warp_dots4(const CT* a, const CT* B, int len, lo
 template <class CT>
 __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upool, CT* Vpool,
                                int* __restrict__ rank_out, long long* __restrict__ evals_out, double tol,
-                               double* s_a, double* s_c) {
+                               CT* s_a, double* s_c) {
     const int lane = threadIdx.x & 31;
     const int m = jb.m, n = jb.n, kmax = jb.kmax;
     CT* U = Upool + jb.offU;
@@ -241,20 +245,20 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
     long long evals = 0;
     for (int guard = 0; guard <= m + kmax + kMaxChecks + 2; ++guard) {
         if (k >= kmax) { status = 2; break; }
-        for (int l = lane; l < k; l += 32) s_a[l] = (double)U[(long long)l * m + i];
+        for (int l = lane; l < k; l += 32) s_a[l] = U[(long long)l * m + i];
         __syncwarp();
         CT* vk = V + (long long)k * n;
-        ArgMax best{-1.0, 0x7fffffff};
+        ArgMaxT<CT> best{CT(-1), 0x7fffffff};
         for (int j = lane; j < n; j += 32) {
             CT r = Entry<CT>::eval(g, jb.r0 + i, jb.c0 + j);
-            for (int l = 0; l < k; ++l) r -= (CT)s_a[l] * V[(long long)l * n + j];
+            for (int l = 0; l < k; ++l) r -= s_a[l] * V[(long long)l * n + j];
             vk[j] = r;
-            best = am_better(best, ArgMax{fabs((double)r), j});
+            best = am_better(best, ArgMaxT<CT>{fabs(r), j});
         }
         best = warp_argmax(best);
         evals += n;
         if ((i & 31) == lane) used |= 1u << (i >> 5);
-        if (!(best.v > fmax(1e-300, 1e-14 * scale))) {
+        if (!((double)best.v > fmax(1e-300, 1e-14 * scale))) {
             int cand = 0x7fffffff;
             for (int t = 0; t < 32 && lane + 32 * t < m; ++t)
                 if (!((used >> t) & 1u)) { cand = lane + 32 * t; break; }
@@ -264,18 +268,18 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
             __syncwarp();
             continue;
         }
-        scale = fmax(scale, best.v);
+        scale = fmax(scale, (double)best.v);
         const int jp = best.i;
         __syncwarp();
         const CT piv = vk[jp];
         __syncwarp();
-        double vv = 0.0;
+        CT vvp = 0;
         for (int j = lane; j < n; j += 32) {
             const CT v = vk[j] / piv;
             vk[j] = v;
-            vv += (double)v * (double)v;
+            vvp += v * v;
         }
-        vv = warp_sum(vv);
+        const double vv = (double)warp_sum(vvp);
         for (int l0 = 0; l0 < k; l0 += 4) {
             double p[4];
             warp_dots4<CT>(vk, V, n, n, l0, k, p);
@@ -283,19 +287,19 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
                 for (int q = 0; q < 4 && l0 + q < k; ++q) s_c[l0 + q] = p[q];
         }
         __syncwarp();
-        for (int l = lane; l < k; l += 32) s_a[l] = (double)V[(long long)l * n + jp];
+        for (int l = lane; l < k; l += 32) s_a[l] = V[(long long)l * n + jp];
         __syncwarp();
         CT* uk = U + (long long)k * m;
-        ArgMax bu{-1.0, 0x7fffffff};
-        double uu = 0.0;
+        ArgMaxT<CT> bu{CT(-1), 0x7fffffff};
+        CT uup = 0;
         for (int r = lane; r < m; r += 32) {
             CT u = Entry<CT>::eval(g, jb.r0 + r, jb.c0 + jp);
-            for (int l = 0; l < k; ++l) u -= (CT)s_a[l] * U[(long long)l * m + r];
+            for (int l = 0; l < k; ++l) u -= s_a[l] * U[(long long)l * m + r];
             uk[r] = u;
-            uu += (double)u * (double)u;
-            if (!((used >> (r >> 5)) & 1u)) bu = am_better(bu, ArgMax{fabs((double)u), r});
+            uup += u * u;
+            if (!((used >> (r >> 5)) & 1u)) bu = am_better(bu, ArgMaxT<CT>{fabs(u), r});
         }
-        uu = warp_sum(uu);
+        const double uu = (double)warp_sum(uup);
         double cross = 0.0;
         for (int l0 = 0; l0 < k; l0 += 4) {
             double p[4];
@@ -308,8 +312,8 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
         ++k;
         if (sqrt(uu) * sqrt(vv) <= tol * sqrt(fmax(norm2, 0.0))) {
             if (checks >= kMaxChecks) { status = 1; break; }
-            double r2 = 0.0;
-            ArgMax bs{-1.0, 0x7fffffff};
+            CT r2p = 0;
+            ArgMaxT<CT> bs{CT(-1), 0x7fffffff};
             for (int t = 0; t < kSamples / 32; ++t) {
                 const int sidx = lane + 32 * t;
                 const int si = (int)(((long long)sidx * m) / kSamples);
@@ -317,10 +321,10 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
                                       (unsigned long long)checks * 40503ull) % (unsigned long long)n);
                 CT x = Entry<CT>::eval(g, jb.r0 + si, jb.c0 + sj);
                 for (int l = 0; l < k; ++l) x -= U[(long long)l * m + si] * V[(long long)l * n + sj];
-                r2 += (double)x * (double)x;
-                bs = am_better(bs, ArgMax{fabs((double)x), sidx});
+                r2p += x * x;
+                bs = am_better(bs, ArgMaxT<CT>{fabs(x), sidx});
             }
-            r2 = warp_sum(r2);
+            const double r2 = (double)warp_sum(r2p);
             bs = warp_argmax(bs);
             ++checks;
             evals += kSamples;
@@ -339,7 +343,7 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
             __syncwarp();
             continue;
         }
-        if (bu.v < 0.0) { status = 1; break; }
+        if (bu.v < CT(0)) { status = 1; break; }
         i = bu.i;
         __syncwarp();
     }
@@ -356,7 +360,7 @@ __global__ void __launch_bounds__(kAcaNT, 4)
 aca_partial_kernel(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict__ big, int n_big,
                    const int* __restrict__ small, int n_small, CT* Upool, CT* Vpool, unsigned char* used_pool,
                    int* __restrict__ rank_out, long long* __restrict__ evals_out, double tol) {
-    __shared__ AcaSmem sm;
+    __shared__ AcaSmem<CT> sm;
     if ((int)blockIdx.x < n_big) {
         const int bidx = big[blockIdx.x];
         const AcaJob jb = jobs[bidx];
@@ -447,7 +451,7 @@ near_assemble_kernel(Geo g, const NearDesc* __restrict__ nd, const NearWork* __r
     S* D = pool + d.off;
     for (long long e = e0 + threadIdx.x; e < e1; e += 256) {
         const int jj = (int)(e / d.m), ii = (int)(e - (long long)jj * d.m);
-        D[e] = Store<S>::put((double)Entry<CT>::eval(g, d.r0 + ii, d.c0 + jj));
+        D[e] = Store<S>::put(Entry<CT>::eval(g, d.r0 + ii, d.c0 + jj));
     }
 }
 
@@ -462,8 +466,8 @@ __global__ void __launch_bounds__(256)
 pack_kernel(const PackJob* __restrict__ jobs, const CT* __restrict__ Us, const CT* __restrict__ Vs, S* pool) {
     const PackJob j = jobs[blockIdx.x];
     const long long nu = (long long)j.m * j.k, nv = (long long)j.n * j.k;
-    for (long long e = threadIdx.x; e < nu; e += 256) pool[j.dstU + e] = Store<S>::put((double)Us[j.srcU + e]);
-    for (long long e = threadIdx.x; e < nv; e += 256) pool[j.dstV + e] = Store<S>::put((double)Vs[j.srcV + e]);
+    for (long long e = threadIdx.x; e < nu; e += 256) pool[j.dstU + e] = Store<S>::put(Us[j.srcU + e]);
+    for (long long e = threadIdx.x; e < nv; e += 256) pool[j.dstV + e] = Store<S>::put(Vs[j.srcV + e]);
 }
 
 __global__ void transpose_dense_kernel(int n, const double* __restrict__ F, double* __restrict__ D) {
@@ -502,7 +506,7 @@ void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>
     h2d(d_order, order, s);
     int* d_rank = ws.get_n<int>(nj);
     long long* d_evals = ws.get_n<long long>(nj);
-    const Geo g = geo_view(h->geo.as<double>(), h->n);
+    const Geo g = geo_view(h->geo.as<double>(), h->geo32.as<float>(), h->n);
     if (p->pivoting == RAD_ACA_FULL) {
         std::vector<long long> offR(nj);
         long long sr = 0;
@@ -553,7 +557,7 @@ void launch_near(rad_htree* h, cudaStream_t s) {
     h2d(d_nd, h->near_h, s);
     NearWork* d_work = ws.get_n<NearWork>(work.size());
     h2d(d_work, work, s);
-    const Geo g = geo_view(h->geo.as<double>(), h->n);
+    const Geo g = geo_view(h->geo.as<double>(), h->geo32.as<float>(), h->n);
     { ProfScope ps_("near_assemble", s); near_assemble_kernel<S, CT><<<(unsigned)work.size(), 256, 0, s>>>(g, d_nd, d_work, h->near_pool.as<S>()); }
     RAD_CHECK_LAUNCH();
 }

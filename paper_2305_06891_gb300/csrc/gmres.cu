@@ -23,7 +23,7 @@ namespace rad {
 
 namespace {
 
-constexpr int kChunkRows = 256;
+constexpr int kChunkRows = 64;
 
 __global__ void rhs_kernel(int n, int m, const double* __restrict__ eps, const double* __restrict__ T, long long ldT,
                            const int* __restrict__ perm, double* __restrict__ eps_t, double* __restrict__ B) {

@@ -97,8 +97,12 @@ inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int dtype_size(int dt) { return dt == RAD_F64 ? 8 : dt == RAD_F32 ? 4 : 2; }
 
 // ------------------------------------------------------------ data layout
-// Facet geometry in tree order, structure of arrays (7 x n doubles):
-// cx, cy, cz, nx, ny, nz, area.
+// Facet geometry in tree order, structure of arrays: 7 x n doubles (cx, cy,
+// cz, nx, ny, nz, area) plus an FP32 copy of 10 x n floats in which every
+// centroid coordinate is split into hi = fl32(c) and lo = fl32(c - hi), so
+// that c_j - c_i = (hi_j - hi_i) + (lo_j - lo_i) keeps ~FP64-relative
+// accuracy for nearby facets using FP32 arithmetic only (GB300's FP64 pipe
+// is narrow); then nx, ny, nz, area as floats.
 struct Geo {
     const double* cx;
     const double* cy;
@@ -107,9 +111,21 @@ struct Geo {
     const double* ny;
     const double* nz;
     const double* area;
+    const float* xh;
+    const float* xl;
+    const float* yh;
+    const float* yl;
+    const float* zh;
+    const float* zl;
+    const float* fnx;
+    const float* fny;
+    const float* fnz;
+    const float* farea;
 };
-inline Geo geo_view(const double* base, int64_t n) {
-    return Geo{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n, base + 6 * n};
+inline Geo geo_view(const double* base, const float* b32, int64_t n) {
+    return Geo{base,         base + n,     base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n,
+               base + 6 * n, b32,          b32 + n,      b32 + 2 * n,  b32 + 3 * n,  b32 + 4 * n,
+               b32 + 5 * n,  b32 + 6 * n,  b32 + 7 * n,  b32 + 8 * n,  b32 + 9 * n};
 }
 
 // Cluster shape (fixed by n and leaf_size) plus its bounding box.
@@ -177,6 +193,7 @@ struct rad_htree {
     bool from_dense = false;
 
     rad::DevBuf geo;     // 7 x n doubles, tree order
+    rad::DevBuf geo32;   // 10 x n floats, tree order (hi/lo centroids)
     rad::DevBuf perm;    // int32, tree position -> facet
     rad::DevBuf iperm;   // int32, facet -> tree position
 

@@ -38,36 +38,40 @@ __device__ __forceinline__ T block_sum(T v, T* sm) {
 }
 
 // Largest magnitude; ties go to the lowest index.  v < 0 marks "no candidate".
-struct ArgMax {
-    double v;
+template <class T>
+struct ArgMaxT {
+    T v;
     int i;
 };
-__device__ __forceinline__ ArgMax am_better(ArgMax a, ArgMax b) {
+using ArgMax = ArgMaxT<double>;
+template <class T>
+__device__ __forceinline__ ArgMaxT<T> am_better(ArgMaxT<T> a, ArgMaxT<T> b) {
     return (b.v > a.v || (b.v == a.v && b.i < a.i)) ? b : a;
 }
-__device__ __forceinline__ ArgMax warp_argmax(ArgMax a) {
+template <class T>
+__device__ __forceinline__ ArgMaxT<T> warp_argmax(ArgMaxT<T> a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        ArgMax b;
+        ArgMaxT<T> b;
         b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
         b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
         a = am_better(a, b);
     }
     return a;
 }
-template <int NT>
-__device__ __forceinline__ ArgMax block_argmax(ArgMax a, ArgMax* sm) {
+template <int NT, class T>
+__device__ __forceinline__ ArgMaxT<T> block_argmax(ArgMaxT<T> a, ArgMaxT<T>* sm) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     a = warp_argmax(a);
     if (lane == 0) sm[warp] = a;
     __syncthreads();
     if (warp == 0) {
-        ArgMax t = lane < NT / 32 ? sm[lane] : ArgMax{-1.0, 0x7fffffff};
+        ArgMaxT<T> t = lane < NT / 32 ? sm[lane] : ArgMaxT<T>{T(-1), 0x7fffffff};
         t = warp_argmax(t);
         if (lane == 0) sm[NT / 32] = t;
     }
     __syncthreads();
-    ArgMax r = sm[NT / 32];
+    ArgMaxT<T> r = sm[NT / 32];
     __syncthreads();
     return r;
 }
@@ -121,19 +125,21 @@ __device__ __forceinline__ double vf_entry64(const Geo& g, int i, int j) {
     return (a * inv) * (b * inv) * (g.area[j] * (1.0 / kPi));
 }
 
-// Same entry with the centroid difference taken in FP64 (no cancellation
-// between nearby facets) and the remaining arithmetic in FP32.
+// Same entry in FP32 arithmetic only.  The centroid difference is taken on
+// hi/lo split coordinates, (hi_j - hi_i) + (lo_j - lo_i): the hi difference
+// is exact for nearby facets (Sterbenz) and the lo terms restore the bits
+// lost when the coordinates were rounded, so there is no cancellation.
 __device__ __forceinline__ float vf_entry32(const Geo& g, int i, int j) {
     if (i == j) return 0.0f;
-    const float dx = (float)(g.cx[j] - g.cx[i]);
-    const float dy = (float)(g.cy[j] - g.cy[i]);
-    const float dz = (float)(g.cz[j] - g.cz[i]);
+    const float dx = (g.xh[j] - g.xh[i]) + (g.xl[j] - g.xl[i]);
+    const float dy = (g.yh[j] - g.yh[i]) + (g.yl[j] - g.yl[i]);
+    const float dz = (g.zh[j] - g.zh[i]) + (g.zl[j] - g.zl[i]);
     const float r2 = dx * dx + dy * dy + dz * dz;
-    const float a = (float)g.nx[i] * dx + (float)g.ny[i] * dy + (float)g.nz[i] * dz;
-    const float b = -((float)g.nx[j] * dx + (float)g.ny[j] * dy + (float)g.nz[j] * dz);
+    const float a = g.fnx[i] * dx + g.fny[i] * dy + g.fnz[i] * dz;
+    const float b = -(g.fnx[j] * dx + g.fny[j] * dy + g.fnz[j] * dz);
     if (!(a > 0.0f) || !(b > 0.0f) || !(r2 > 0.0f)) return 0.0f;
     const float inv = 1.0f / r2;
-    return (a * inv) * (b * inv) * ((float)g.area[j] * (float)(1.0 / kPi));
+    return (a * inv) * (b * inv) * (g.farea[j] * (float)(1.0 / kPi));
 }
 
 template <class CT> struct Entry;
@@ -148,14 +154,17 @@ template <> struct Entry<float> {
 template <class S> struct Store;
 template <> struct Store<double> {
     static __device__ __forceinline__ double put(double v) { return v; }
+    static __device__ __forceinline__ double put(float v) { return (double)v; }
     static __device__ __forceinline__ double get(double v) { return v; }
 };
 template <> struct Store<float> {
     static __device__ __forceinline__ float put(double v) { return (float)v; }
+    static __device__ __forceinline__ float put(float v) { return v; }
     static __device__ __forceinline__ float get(float v) { return v; }
 };
 template <> struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 put(double v) { return __float2bfloat16_rn((float)v); }
+    static __device__ __forceinline__ __nv_bfloat16 put(float v) { return __float2bfloat16_rn(v); }
     static __device__ __forceinline__ float get(__nv_bfloat16 v) { return __bfloat162float(v); }
 };
 

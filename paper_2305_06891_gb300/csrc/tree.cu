@@ -238,6 +238,22 @@ __global__ void gather_geo_kernel(int n, const double* __restrict__ geo_user, co
     iperm[f] = p;
 }
 
+// FP32 view of the tree-ordered geometry: centroids split into hi/lo floats.
+__global__ void geo32_kernel(int n, const double* __restrict__ geo, float* __restrict__ g32) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t N = n;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double c = geo[k * N + p];
+        const float hi = __double2float_rn(c);
+        g32[(2 * k) * N + p] = hi;
+        g32[(2 * k + 1) * N + p] = __double2float_rn(c - (double)hi);
+    }
+#pragma unroll
+    for (int k = 3; k < 7; ++k) g32[(k + 3) * N + p] = __double2float_rn(geo[k * N + p]);
+}
+
 // --------------------------------------------------------------- block tree
 // Eq. (28) in squared form on the centroid boxes, FP64 with every product
 // and sum rounded separately (no contraction):
@@ -416,6 +432,9 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     RAD_CUDA(cudaMemcpyAsync(h->perm.p, perm_final, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
     { ProfScope ps_("geometry", s); gather_geo_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, geo_user, perm_final, h->geo.as<double>(),
                                                       h->iperm.as<int>()); }
+    RAD_CHECK_LAUNCH();
+    h->geo32.alloc(sizeof(float) * 10 * (size_t)n);
+    { ProfScope ps_("geometry", s); geo32_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, h->geo.as<double>(), h->geo32.as<float>()); }
     RAD_CHECK_LAUNCH();
 
     // block tree: single CTA, retry with larger buffers on overflow
