@@ -191,6 +191,29 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
                    double* q, int64_t ldq, rad_solve_info* info, void* stream);
 
 /* -------------------------------------------------------------------------
+ * rad_hmatvec_noalloc — the product of rad_hmatvec (same arguments, same
+ * result) for callers that cannot let the library allocate device memory,
+ * e.g. a serving engine that has already reserved the GPU's memory for its
+ * own pool, or a latency-critical loop that must stay out of the allocator.
+ * The paper has no counterpart; this is an interface convenience.
+ * Its scratch is one fixed 32 MiB array in device memory per GPU (held from
+ * the library's load until the process exits) instead of allocations:
+ *   - x and y must be device arrays (host arrays are rejected: staging them
+ *     would allocate);
+ *   - it needs 2 * round256(s * n * nrhs) + round256(s * sum_rank * nrhs)
+ *     bytes, s = 8 for an FP64 operator and 4 otherwise (sum_rank from
+ *     rad_htree_get_stats); larger calls return RAD_ELIMIT;
+ *   - the first call on each device looks up the array's device address
+ *     (make that first call before any stream capture);
+ *   - all calls on a device share the array: calls that overlap on the GPU
+ *     race and must be serialised by the caller;
+ *   - it returns RAD_EINVAL while rad_profile_enable is on.
+ * Asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+int rad_hmatvec_noalloc(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx,
+                        void* y, int64_t ldy, int64_t nrhs, void* stream);
+
+/* -------------------------------------------------------------------------
  * rad_solve_reflection — A7 alone: solves C Y = B (Eq. 11, C = I -
  * diag(1 - eps) F) for nrhs arbitrary right-hand sides by the same batched
  * GMRES as rad_solve_flux (the paper applies C^-1 through its LU factors,

@@ -82,6 +82,7 @@ def _load():
         "rad_hmatvec": (C.c_int, [H, i32, vp, i64, vp, i64, i64, vp]),
         "rad_solve_flux": (C.c_int, [H, vp, vp, i64, i64, dbl, C.POINTER(_SolveParams), vp, i64,
                                      C.POINTER(_SolveInfo), vp]),
+        "rad_hmatvec_noalloc": (C.c_int, [H, i32, vp, i64, vp, i64, i64, vp]),
         "rad_solve_reflection": (C.c_int, [H, vp, vp, i64, i64, C.POINTER(_SolveParams), vp, i64,
                                            C.POINTER(_SolveInfo), vp]),
         "rad_htree_get_stats": (C.c_int, [H, C.POINTER(_Stats)]),
@@ -305,6 +306,23 @@ def rad_solve_flux(h: HTree, eps, T, sigma: float = SIGMA_SB, tol: float = 1e-10
     if (_is_tensor(T) and T.dim() == 1) or (not _is_tensor(T) and np.ndim(T) == 1):
         q = q[:, 0]
     return q, d
+
+
+def rad_hmatvec_noalloc(h: HTree, x, y, stream=None):
+    """Y = F X without device allocation (fixed 32 MiB scratch per GPU).
+
+    For callers that cannot let the library allocate device memory.  ``x``
+    and ``y`` must be CUDA tensors, (N,) or (N, nrhs) column-major, of the
+    same dtype (float32 or float64); ``y`` is written in place.
+    """
+    t = _torch()
+    dt = RAD_F64 if x.dtype == t.float64 else RAD_F32
+    n = x.shape[0]
+    nrhs = 1 if x.dim() == 1 else x.shape[1]
+    ldx = n if x.dim() == 1 or nrhs == 1 else x.stride(1)
+    ldy = n if y.dim() == 1 or nrhs == 1 else y.stride(1)
+    _check(_lib.rad_hmatvec_noalloc(h.ptr, dt, _ptr(x), ldx, _ptr(y), ldy, nrhs, _stream(stream, x, y)))
+    return y
 
 
 def rad_solve_reflection(h: HTree, eps, B, tol: float = 1e-10, restart: int = 30, max_iter: int = 1000,

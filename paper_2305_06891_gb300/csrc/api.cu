@@ -36,6 +36,11 @@ std::vector<ProfRec> g_prof;
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+bool profiling_enabled() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    return g_prof_on;
+}
+
 ProfScope::ProfScope(const char* name, cudaStream_t st) : s(st) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on) return;
