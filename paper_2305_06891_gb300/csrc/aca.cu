@@ -433,49 +433,75 @@ aca_full_kernel(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict__ 
     }
 }
 
-// Dense blocks: entries of Eq. (10), column-major, stored as S.
-struct NearWork {
-    int desc;
-    int chunk;
+// ------------------------------------------------------------ panel fill
+// Dense pieces: columns [bc0, bc0 + ncols) of a dense block, restricted to
+// the rows of tile `tile`, go to panel columns [col, col + ncols); rows of
+// the panel beyond the tile's rows are zero.
+struct DenseWork {
+    int tile, bc0, ncols, col;
 };
-constexpr int kNearChunk = 8192;
-
 template <class S, class CT>
 __global__ void __launch_bounds__(256)
-near_assemble_kernel(Geo g, const NearDesc* __restrict__ nd, const NearWork* __restrict__ work, S* pool) {
-    const NearWork w = work[blockIdx.x];
-    const NearDesc d = nd[w.desc];
-    const long long mn = (long long)d.m * d.n;
-    const long long e0 = (long long)w.chunk * kNearChunk;
-    const long long e1 = min(mn, e0 + kNearChunk);
-    S* D = pool + d.off;
-    for (long long e = e0 + threadIdx.x; e < e1; e += 256) {
-        const int jj = (int)(e / d.m), ii = (int)(e - (long long)jj * d.m);
-        D[e] = Store<S>::put(Entry<CT>::eval(g, d.r0 + ii, d.c0 + jj));
+dense_fill_kernel(Geo g, const Tile* __restrict__ tiles, const DenseWork* __restrict__ work, S* pool) {
+    const DenseWork w = work[blockIdx.x];
+    const Tile t = tiles[w.tile];
+    S* P = pool + t.noff + (long long)w.col * t.ld;
+    const int cnt = w.ncols * t.ld;
+    for (int e = threadIdx.x; e < cnt; e += 256) {
+        const int c = e / t.ld, i = e - c * t.ld;
+        P[e] = i < t.rows ? Store<S>::put(Entry<CT>::eval(g, t.r0 + i, w.bc0 + c)) : Store<S>::put(CT(0));
     }
 }
 
-// Copy the first k columns of U and V from the ACA scratch to the packed
-// factor pool, converting to the storage type.
-struct PackJob {
-    long long srcU, srcV, dstU, dstV;
-    int m, n, k, pad;
+// Low-rank pieces: rows [ro, ro + tile rows) of U_b (ACA scratch, m x k
+// column-major) go to low-rank panel columns [col, col + k).
+struct UWork {
+    int tile, ro, m, k, col, pad;
+    long long src;
 };
 template <class CT, class S>
 __global__ void __launch_bounds__(256)
-pack_kernel(const PackJob* __restrict__ jobs, const CT* __restrict__ Us, const CT* __restrict__ Vs, S* pool) {
-    const PackJob j = jobs[blockIdx.x];
-    const long long nu = (long long)j.m * j.k, nv = (long long)j.n * j.k;
-    for (long long e = threadIdx.x; e < nu; e += 256) pool[j.dstU + e] = Store<S>::put(Us[j.srcU + e]);
-    for (long long e = threadIdx.x; e < nv; e += 256) pool[j.dstV + e] = Store<S>::put(Vs[j.srcV + e]);
+u_fill_kernel(const Tile* __restrict__ tiles, const UWork* __restrict__ work, const CT* __restrict__ Us, S* pool) {
+    const UWork w = work[blockIdx.x];
+    const Tile t = tiles[w.tile];
+    S* P = pool + t.foff + (long long)w.col * t.ld;
+    const int cnt = w.k * t.ld;
+    for (int e = threadIdx.x; e < cnt; e += 256) {
+        const int l = e / t.ld, i = e - l * t.ld;
+        P[e] = i < t.rows ? Store<S>::put(Us[w.src + (long long)l * w.m + w.ro + i]) : Store<S>::put(CT(0));
+    }
 }
 
-__global__ void transpose_dense_kernel(int n, const double* __restrict__ F, double* __restrict__ D) {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nn = (long long)n * n;
-    if (e >= nn) return;
-    const int j = (int)(e / n), i = (int)(e - (long long)j * n);
-    D[e] = F[(long long)i * n + j];
+// V^T rows of block b (ACA scratch V_b, n x k column-major) go to rows
+// [grow, grow + k) of its group's V panel.
+struct VWork {
+    int group, grow, n, k;
+    long long src;
+};
+template <class CT, class S>
+__global__ void __launch_bounds__(256)
+v_fill_kernel(const Group* __restrict__ groups, const VWork* __restrict__ work, const CT* __restrict__ Vs, S* pool) {
+    const VWork w = work[blockIdx.x];
+    const Group gr = groups[w.group];
+    S* P = pool + gr.voff;
+    const int cnt = w.n * w.k;
+    for (int e = threadIdx.x; e < cnt; e += 256) {
+        const int j = e / w.k, l = e - j * w.k;
+        P[(long long)j * gr.ld + w.grow + l] = Store<S>::put(Vs[w.src + (long long)l * w.n + j]);
+    }
+}
+
+// A caller's dense F (row-major n x n, FP64) as the dense panels of 64-row
+// tiles.
+__global__ void __launch_bounds__(256)
+dense_from_matrix_kernel(int n, const Tile* __restrict__ tiles, const double* __restrict__ F, double* pool) {
+    const Tile t = tiles[blockIdx.y];
+    const long long cnt = (long long)n * t.ld;
+    double* P = pool + t.noff;
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < cnt; e += (long long)gridDim.x * 256) {
+        const int c = (int)(e / t.ld), i = (int)(e - (long long)c * t.ld);
+        P[e] = i < t.rows ? F[(long long)(t.r0 + i) * n + c] : 0.0;
+    }
 }
 
 template <class CT>
@@ -544,32 +570,98 @@ void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>
     RAD_CUDA(cudaStreamSynchronize(s));
 }
 
-template <class S, class CT>
-void launch_near(rad_htree* h, cudaStream_t s) {
-    Scratch ws(s);
-    std::vector<NearWork> work;
-    for (int d = 0; d < (int)h->near_h.size(); ++d) {
-        const long long mn = (long long)h->near_h[d].m * h->near_h[d].n;
-        for (long long c = 0; c * kNearChunk < mn; ++c) work.push_back(NearWork{d, (int)c});
+// Row tiles: leaf clusters (or [0, n) for a dense-wrapped matrix) cut into
+// pieces of at most 64 rows.
+static void make_tiles(rad_htree* h, std::vector<Tile>& tiles, std::vector<int>& tile_at) {
+    const int n = (int)h->n;
+    std::vector<std::pair<int, int>> leaves;
+    if (h->from_dense) {
+        leaves.push_back({0, n});
+    } else {
+        for (auto& nd : h->nodes)
+            if (nd.leaf) leaves.push_back({nd.begin, nd.end});
+        std::sort(leaves.begin(), leaves.end());
     }
+    tiles.clear();
+    tile_at.assign(n + 1, -1);
+    for (auto& lf : leaves)
+        for (int r = lf.first; r < lf.second; r += kTileRows) {
+            tile_at[r] = (int)tiles.size();
+            Tile t{};
+            t.r0 = r;
+            t.rows = std::min(kTileRows, lf.second - r);
+            t.ld = (int)round_up(t.rows, 4);
+            tiles.push_back(t);
+        }
+}
+
+// Tiles covering rows [r0, r1) of a block (block rows are cluster ranges,
+// which are unions of consecutive tiles).
+template <class F>
+static void for_tiles(const std::vector<Tile>& tiles, const std::vector<int>& tile_at, int r0, int r1, F&& f) {
+    int r = r0;
+    while (r < r1) {
+        const int t = tile_at[r];
+        RAD_REQUIRE(t >= 0, RAD_ECUDA, "internal: block rows do not align with row tiles");
+        f(t);
+        r += tiles[t].rows;
+    }
+}
+
+static void upload_operator(rad_htree* h, const std::vector<std::vector<int>>& xi,
+                            const std::vector<std::vector<int>>& ti, cudaStream_t s) {
+    std::vector<int> xidx, tidx;
+    for (size_t t = 0; t < h->tiles_h.size(); ++t) {
+        h->tiles_h[t].ixn = (int)xidx.size();
+        h->tiles_h[t].ixf = (int)tidx.size();
+        xidx.insert(xidx.end(), xi[t].begin(), xi[t].end());
+        tidx.insert(tidx.end(), ti[t].begin(), ti[t].end());
+    }
+    std::vector<GWork> gwork;
+    for (int g = 0; g < (int)h->groups_h.size(); ++g)
+        for (int r = 0; r < h->groups_h[g].M; r += kTileRows)
+            gwork.push_back(GWork{g, r, std::min(kTileRows, h->groups_h[g].M - r), 0});
+    h->n_tiles = (int)h->tiles_h.size();
+    h->n_gwork = (int)gwork.size();
+    h->d_tiles.alloc(sizeof(Tile) * std::max<size_t>(1, h->tiles_h.size()));
+    h->d_xidx.alloc(sizeof(int) * std::max<size_t>(1, xidx.size()));
+    h->d_tidx.alloc(sizeof(int) * std::max<size_t>(1, tidx.size()));
+    h->d_gwork.alloc(sizeof(GWork) * std::max<size_t>(1, gwork.size()));
+    h->d_groups.alloc(sizeof(Group) * std::max<size_t>(1, h->groups_h.size()));
+    h2d(h->d_tiles.as<Tile>(), h->tiles_h, s);
+    h2d(h->d_xidx.as<int>(), xidx, s);
+    h2d(h->d_tidx.as<int>(), tidx, s);
+    h2d(h->d_gwork.as<GWork>(), gwork, s);
+    h2d(h->d_groups.as<Group>(), h->groups_h, s);
+}
+
+template <class S, class CT>
+static void launch_dense_fill(rad_htree* h, const std::vector<DenseWork>& work, cudaStream_t s) {
     if (work.empty()) return;
-    NearDesc* d_nd = ws.get_n<NearDesc>(h->near_h.size());
-    h2d(d_nd, h->near_h, s);
-    NearWork* d_work = ws.get_n<NearWork>(work.size());
+    Scratch ws(s);
+    DenseWork* d_work = ws.get_n<DenseWork>(work.size());
     h2d(d_work, work, s);
     const Geo g = geo_view(h->geo.as<double>(), h->geo32.as<float>(), h->n);
-    { ProfScope ps_("near_assemble", s); near_assemble_kernel<S, CT><<<(unsigned)work.size(), 256, 0, s>>>(g, d_nd, d_work, h->near_pool.as<S>()); }
+    { ProfScope ps_("near_assemble", s); dense_fill_kernel<S, CT><<<(unsigned)work.size(), 256, 0, s>>>(g, h->d_tiles.as<Tile>(), d_work, h->near_pool.as<S>()); }
     RAD_CHECK_LAUNCH();
 }
 
 template <class CT, class S>
-void launch_pack(rad_htree* h, const std::vector<PackJob>& jobs, const CT* Us, const CT* Vs, cudaStream_t s) {
-    if (jobs.empty()) return;
+static void launch_factor_fill(rad_htree* h, const std::vector<UWork>& uw, const std::vector<VWork>& vw,
+                               const CT* Us, const CT* Vs, cudaStream_t s) {
     Scratch ws(s);
-    PackJob* d_jobs = ws.get_n<PackJob>(jobs.size());
-    h2d(d_jobs, jobs, s);
-    { ProfScope ps_("aca_pack", s); pack_kernel<CT, S><<<(unsigned)jobs.size(), 256, 0, s>>>(d_jobs, Us, Vs, h->far_pool.as<S>()); }
-    RAD_CHECK_LAUNCH();
+    if (!uw.empty()) {
+        UWork* d = ws.get_n<UWork>(uw.size());
+        h2d(d, uw, s);
+        { ProfScope ps_("aca_pack", s); u_fill_kernel<CT, S><<<(unsigned)uw.size(), 256, 0, s>>>(h->d_tiles.as<Tile>(), d, Us, h->far_pool.as<S>()); }
+        RAD_CHECK_LAUNCH();
+    }
+    if (!vw.empty()) {
+        VWork* d = ws.get_n<VWork>(vw.size());
+        h2d(d, vw, s);
+        { ProfScope ps_("aca_pack", s); v_fill_kernel<CT, S><<<(unsigned)vw.size(), 256, 0, s>>>(h->d_groups.as<Group>(), d, Vs, h->far_pool.as<S>()); }
+        RAD_CHECK_LAUNCH();
+    }
 }
 
 template <class CT>
@@ -598,66 +690,120 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     CT* Us = nullptr;
     CT* Vs = nullptr;
     if (!jobs.empty()) launch_aca<CT>(h, p, jobs, ranks, evals, nullptr, ws, Us, Vs, s);
-
-    // storage plan
-    h->near_h.clear();
-    h->far_h.clear();
-    h->near_block.clear();
-    h->far_block.clear();
+    std::vector<int> job_of(h->blocks.size(), -1);
+    for (size_t a = 0; a < adm.size(); ++a) {
+        job_of[adm[a]] = (int)a;
+        h->blocks[adm[a]].rank = ranks[a];
+    }
     h->aca_entries = 0;
     for (auto e : evals) h->aca_entries += e;
-    const int ns = dtype_size(h->near_dtype);
-    const int fs = dtype_size(h->factor_dtype);
-    long long near_off = 0, far_off = 0;
-    std::vector<PackJob> pack;
-    int64_t fallback = 0;
+
+    // ---- storage plan: row tiles, column groups, panels
+    std::vector<int> tile_at;
+    make_tiles(h, h->tiles_h, tile_at);
+    std::vector<Tile>& tiles = h->tiles_h;
+    const size_t nt = tiles.size();
+    std::vector<std::vector<int>> xi(nt), ti(nt);
+    h->near_pieces.clear();
+    h->far_pieces.clear();
+    h->groups_h.clear();
+    int64_t fallback = 0, near_e = 0, far_u = 0, far_v = 0;
     int maxk = 0;
-    long long sum_far_entries = 0;
-    std::vector<int> rank_of(h->blocks.size(), -1);
-    for (size_t a = 0; a < adm.size(); ++a) rank_of[adm[a]] = ranks[a];
-    std::vector<int> job_of(h->blocks.size(), -1);
-    for (size_t a = 0; a < adm.size(); ++a) job_of[adm[a]] = (int)a;
+    // column groups of the low-rank blocks (k > 0), in order of first use
+    std::vector<int> group_of_node(h->nodes.size(), -1);
+    std::vector<std::vector<int>> group_blocks;
     for (int b = 0; b < (int)h->blocks.size(); ++b) {
         BlockH& bk = h->blocks[b];
+        bk.group = -1;
+        bk.grow = 0;
+        if (!bk.admissible) {
+            bk.rank = -1;
+            continue;
+        }
+        if (bk.rank < 0) {
+            ++fallback;
+            continue;
+        }
+        if (bk.rank == 0) continue;
+        int& gid = group_of_node[bk.col_node];
+        if (gid < 0) {
+            gid = (int)h->groups_h.size();
+            h->groups_h.push_back(Group{bk.c0, bk.c1 - bk.c0, 0, 0, 0, 0, 0});
+            group_blocks.emplace_back();
+        }
+        bk.group = gid;
+        bk.grow = h->groups_h[gid].M;
+        h->groups_h[gid].M += bk.rank;
+        group_blocks[gid].push_back(b);
+    }
+    int toff = 0;
+    for (auto& gr : h->groups_h) {
+        gr.ld = (int)round_up(gr.M, 4);
+        gr.toff = toff;
+        toff += gr.M;
+    }
+    h->sum_rank = toff;
+    std::vector<DenseWork> dwork;
+    std::vector<UWork> uwork;
+    std::vector<VWork> vwork;
+    for (int b = 0; b < (int)h->blocks.size(); ++b) {
+        const BlockH& bk = h->blocks[b];
         const int m = bk.r1 - bk.r0, n = bk.c1 - bk.c0;
-        const int rk = bk.admissible ? rank_of[b] : -1;
-        bk.rank = rk;
-        if (rk < 0) {
-            if (bk.admissible) ++fallback;
-            bk.store_idx = (int)h->near_h.size();
-            h->near_h.push_back(NearDesc{bk.r0, bk.c0, m, n, near_off});
-            h->near_block.push_back(b);
-            near_off += round_up((long long)m * n, 16);
-        } else {
-            bk.store_idx = (int)h->far_h.size();
-            FarDesc fd{bk.r0, bk.c0, m, n, rk, 0, far_off, 0};
-            far_off += round_up((long long)m * rk, 16);
-            fd.offV = far_off;
-            far_off += round_up((long long)n * rk, 16);
-            h->far_h.push_back(fd);
-            h->far_block.push_back(b);
-            maxk = std::max(maxk, rk);
-            sum_far_entries += (long long)rk * (m + n);
-            if (rk > 0) {
-                const AcaJob& j = jobs[job_of[b]];
-                pack.push_back(PackJob{j.offU, j.offV, fd.offU, fd.offV, m, n, rk, 0});
-            }
+        if (bk.rank < 0) {
+            near_e += (long long)m * n;
+            for_tiles(tiles, tile_at, bk.r0, bk.r1, [&](int t) {
+                h->near_pieces.push_back(Piece{b, t, tiles[t].kn});
+                for (int c0 = 0; c0 < n; c0 += 64)
+                    dwork.push_back(DenseWork{t, bk.c0 + c0, std::min(64, n - c0), tiles[t].kn + c0});
+                for (int c = 0; c < n; ++c) xi[t].push_back(bk.c0 + c);
+                tiles[t].kn += n;
+            });
+        } else if (bk.rank > 0) {
+            const int k = bk.rank;
+            const AcaJob& jb = jobs[job_of[b]];
+            const Group& gr = h->groups_h[bk.group];
+            maxk = std::max(maxk, k);
+            far_u += (long long)k * m;
+            far_v += (long long)k * n;
+            for_tiles(tiles, tile_at, bk.r0, bk.r1, [&](int t) {
+                h->far_pieces.push_back(Piece{b, t, tiles[t].kf});
+                uwork.push_back(UWork{t, tiles[t].r0 - bk.r0, m, k, tiles[t].kf, 0, jb.offU});
+                for (int l = 0; l < k; ++l) ti[t].push_back(gr.toff + bk.grow + l);
+                tiles[t].kf += k;
+            });
+            vwork.push_back(VWork{bk.group, bk.grow, n, k, jb.offV});
         }
     }
-    h->near_pool.alloc((size_t)std::max<long long>(near_off, 16) * ns);
-    h->far_pool.alloc((size_t)std::max<long long>(far_off, 16) * fs);
-    if (h->near_dtype == RAD_F64) launch_near<double, double>(h, s);
-    else launch_near<float, float>(h, s);
-    if (h->factor_dtype == RAD_F64) launch_pack<CT, double>(h, pack, Us, Vs, s);
-    else if (h->factor_dtype == RAD_F32) launch_pack<CT, float>(h, pack, Us, Vs, s);
-    else launch_pack<CT, __nv_bfloat16>(h, pack, Us, Vs, s);
+    long long noff = 0, foff = 0;
+    for (auto& t : tiles) {
+        t.noff = noff;
+        noff += round_up((long long)t.ld * t.kn, 16);
+        t.foff = foff;
+        foff += round_up((long long)t.ld * t.kf, 16);
+    }
+    for (auto& gr : h->groups_h) {
+        gr.voff = foff;
+        foff += round_up((long long)gr.ld * gr.n, 16);
+    }
+    h->stored_near = noff;
+    h->stored_far = foff;
+    const int ns = dtype_size(h->near_dtype);
+    const int fs = dtype_size(h->factor_dtype);
+    h->near_pool.alloc((size_t)std::max<long long>(noff, 16) * ns);
+    h->far_pool.alloc((size_t)std::max<long long>(foff, 16) * fs);
+    RAD_CUDA(cudaMemsetAsync(h->far_pool.p, 0, h->far_pool.bytes, s));
+    upload_operator(h, xi, ti, s);
+    if (h->near_dtype == RAD_F64) launch_dense_fill<double, double>(h, dwork, s);
+    else launch_dense_fill<float, float>(h, dwork, s);
+    if (h->factor_dtype == RAD_F64) launch_factor_fill<CT, double>(h, uwork, vwork, Us, Vs, s);
+    else if (h->factor_dtype == RAD_F32) launch_factor_fill<CT, float>(h, uwork, vwork, Us, Vs, s);
+    else launch_factor_fill<CT, __nv_bfloat16>(h, uwork, vwork, Us, Vs, s);
     h->n_dense_fallback = fallback;
     h->max_rank_used = maxk;
-    h->far_entries = sum_far_entries;
-    long long ne = 0;
-    for (auto& d : h->near_h) ne += (long long)d.m * d.n;
-    h->near_entries = ne;
-    finalize_operator(h, s);
+    h->near_entries = near_e;
+    h->far_u_entries = far_u;
+    h->far_v_entries = far_v;
+    h->far_entries = far_u + far_v;
     RAD_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -686,94 +832,38 @@ void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     h->compressed = true;
 }
 
-void finalize_operator(rad_htree* h, cudaStream_t s) {
-    const int n = (int)h->n;
-    // row tiles: leaf clusters in tree order, cut into <= 64-row pieces
-    std::vector<std::pair<int, int>> leaves;
-    if (h->from_dense) {
-        leaves.push_back({0, n});
-    } else {
-        for (auto& nd : h->nodes)
-            if (nd.leaf) leaves.push_back({nd.begin, nd.end});
-        std::sort(leaves.begin(), leaves.end());
-    }
-    std::vector<TileDesc> tiles;
-    std::vector<int> tile_at(n + 1, -1);
-    for (auto& lf : leaves)
-        for (int r = lf.first; r < lf.second; r += kTileRows) {
-            tile_at[r] = (int)tiles.size();
-            tiles.push_back(TileDesc{r, std::min(kTileRows, lf.second - r), 0, 0});
-        }
-    std::vector<std::vector<int2>> per(tiles.size());
-    for (int d = 0; d < (int)h->near_h.size(); ++d) {
-        const NearDesc& nd = h->near_h[d];
-        int r = nd.r0;
-        while (r < nd.r0 + nd.m) {
-            const int t = tile_at[r];
-            RAD_REQUIRE(t >= 0, RAD_ECUDA, "internal: block rows do not align with tiles");
-            per[t].push_back(make_int2(d, r - nd.r0));
-            r += tiles[t].rows;
-        }
-    }
-    std::vector<int> trow;
-    int toff = 0;
-    std::vector<int> nz;
-    for (int d = 0; d < (int)h->far_h.size(); ++d) {
-        FarDesc& fd = h->far_h[d];
-        fd.toff = toff;
-        for (int l = 0; l < fd.k; ++l) trow.push_back(d);
-        toff += fd.k;
-        if (fd.k == 0) continue;
-        nz.push_back(d);
-        int r = fd.r0;
-        while (r < fd.r0 + fd.m) {
-            const int t = tile_at[r];
-            RAD_REQUIRE(t >= 0, RAD_ECUDA, "internal: block rows do not align with tiles");
-            per[t].push_back(make_int2(d | kFarBit, r - fd.r0));
-            r += tiles[t].rows;
-        }
-    }
-    std::stable_sort(nz.begin(), nz.end(), [&](int a, int b) { return h->far_h[a].n > h->far_h[b].n; });
-    std::vector<int2> entries;
-    for (size_t t = 0; t < tiles.size(); ++t) {
-        tiles[t].e0 = (int)entries.size();
-        entries.insert(entries.end(), per[t].begin(), per[t].end());
-        tiles[t].e1 = (int)entries.size();
-    }
-    h->n_tiles = (int)tiles.size();
-    h->sum_rank = toff;
-    h->n_far_nz = (int)nz.size();
-    h->d_tiles.alloc(sizeof(TileDesc) * std::max<size_t>(1, tiles.size()));
-    h->d_entries.alloc(sizeof(int2) * std::max<size_t>(1, entries.size()));
-    h->d_near.alloc(sizeof(NearDesc) * std::max<size_t>(1, h->near_h.size()));
-    h->d_far.alloc(sizeof(FarDesc) * std::max<size_t>(1, h->far_h.size()));
-    h->d_trow.alloc(sizeof(int) * std::max<size_t>(1, trow.size()));
-    h->d_far_nz.alloc(sizeof(int) * std::max<size_t>(1, nz.size()));
-    h2d(h->d_tiles.as<TileDesc>(), tiles, s);
-    h2d(h->d_entries.as<int2>(), entries, s);
-    h2d(h->d_near.as<NearDesc>(), h->near_h, s);
-    h2d(h->d_far.as<FarDesc>(), h->far_h, s);
-    h2d(h->d_trow.as<int>(), trow, s);
-    h2d(h->d_far_nz.as<int>(), nz, s);
-}
-
 void load_dense_operator(rad_htree* h, const double* F_dev, cudaStream_t s) {
     const int n = (int)h->n;
     h->near_dtype = RAD_F64;
     h->factor_dtype = RAD_F64;
-    h->near_h.assign(1, NearDesc{0, 0, n, n, 0});
-    h->far_h.clear();
-    h->near_block.assign(1, 0);
-    h->far_block.clear();
-    h->near_pool.alloc(sizeof(double) * (size_t)n * n);
+    h->blocks.assign(1, BlockH{0, 0, 0, n, 0, n, 0, -1, -1, 0});
+    std::vector<int> tile_at;
+    make_tiles(h, h->tiles_h, tile_at);
+    std::vector<std::vector<int>> xi(h->tiles_h.size()), ti(h->tiles_h.size());
+    h->near_pieces.clear();
+    h->far_pieces.clear();
+    h->groups_h.clear();
+    long long noff = 0;
+    for (size_t t = 0; t < h->tiles_h.size(); ++t) {
+        Tile& tl = h->tiles_h[t];
+        tl.kn = n;
+        tl.noff = noff;
+        tl.foff = 0;
+        noff += round_up((long long)tl.ld * n, 16);
+        h->near_pieces.push_back(Piece{0, (int)t, 0});
+        for (int c = 0; c < n; ++c) xi[t].push_back(c);
+    }
+    h->sum_rank = 0;
+    h->stored_near = noff;
+    h->stored_far = 0;
+    h->near_pool.alloc(sizeof(double) * (size_t)std::max<long long>(noff, 16));
     h->far_pool.alloc(16 * sizeof(double));
-    const long long nn = (long long)n * n;
-    { ProfScope ps_("dense_load", s); transpose_dense_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(n, F_dev, h->near_pool.as<double>()); }
+    upload_operator(h, xi, ti, s);
+    dim3 grid((unsigned)std::min<long long>(1024, ((long long)n * 64 + 255) / 256), (unsigned)h->tiles_h.size());
+    { ProfScope ps_("dense_load", s); dense_from_matrix_kernel<<<grid, 256, 0, s>>>(n, h->d_tiles.as<Tile>(), F_dev, h->near_pool.as<double>()); }
     RAD_CHECK_LAUNCH();
-    h->near_entries = nn;
-    h->far_entries = 0;
-    h->blocks.assign(1, BlockH{0, 0, 0, n, 0, n, 0, -1, 0});
-    finalize_operator(h, s);
+    h->near_entries = (long long)n * n;
+    h->far_entries = h->far_u_entries = h->far_v_entries = 0;
     RAD_CUDA(cudaStreamSynchronize(s));
     h->compressed = true;
 }
@@ -803,36 +893,39 @@ void export_block(const rad_htree* h, int64_t b, double* D, double* U, double* V
     const int m = bk.r1 - bk.r0, n = bk.c1 - bk.c0;
     std::vector<unsigned char> raw;
     std::vector<double> cm;
-    if (bk.rank < 0) {
-        const NearDesc& d = h->near_h[bk.store_idx];
-        const int sz = dtype_size(h->near_dtype);
-        raw.resize((size_t)m * n * sz);
-        RAD_CUDA(cudaMemcpy(raw.data(), static_cast<const char*>(h->near_pool.p) + d.off * sz, raw.size(),
+    auto fetch = [&](const void* pool, int dt, long long off, size_t cnt) {
+        const int sz = dtype_size(dt);
+        raw.resize(cnt * sz);
+        RAD_CUDA(cudaMemcpy(raw.data(), static_cast<const char*>(pool) + off * sz, raw.size(),
                             cudaMemcpyDeviceToHost));
-        to_double(raw.data(), h->near_dtype, (size_t)m * n, cm);
-        if (D)
-            for (int i = 0; i < m; ++i)
-                for (int j = 0; j < n; ++j) D[(size_t)i * n + j] = cm[(size_t)j * m + i];
-    } else {
-        const FarDesc& f = h->far_h[bk.store_idx];
-        const int sz = dtype_size(h->factor_dtype);
-        const int k = f.k;
-        if (U && k) {
-            raw.resize((size_t)m * k * sz);
-            RAD_CUDA(cudaMemcpy(raw.data(), static_cast<const char*>(h->far_pool.p) + f.offU * sz, raw.size(),
-                                cudaMemcpyDeviceToHost));
-            to_double(raw.data(), h->factor_dtype, (size_t)m * k, cm);
-            for (int i = 0; i < m; ++i)
-                for (int l = 0; l < k; ++l) U[(size_t)i * k + l] = cm[(size_t)l * m + i];
+        to_double(raw.data(), dt, cnt, cm);
+    };
+    if (bk.rank < 0) {
+        if (!D) return;
+        for (const Piece& pc : h->near_pieces) {
+            if (pc.block != b) continue;
+            const Tile& t = h->tiles_h[pc.tile];
+            fetch(h->near_pool.p, h->near_dtype, t.noff + (long long)pc.col * t.ld, (size_t)n * t.ld);
+            for (int i = 0; i < t.rows; ++i)
+                for (int c = 0; c < n; ++c) D[(size_t)(t.r0 - bk.r0 + i) * n + c] = cm[(size_t)c * t.ld + i];
         }
-        if (V && k) {
-            raw.resize((size_t)n * k * sz);
-            RAD_CUDA(cudaMemcpy(raw.data(), static_cast<const char*>(h->far_pool.p) + f.offV * sz, raw.size(),
-                                cudaMemcpyDeviceToHost));
-            to_double(raw.data(), h->factor_dtype, (size_t)n * k, cm);
-            for (int j = 0; j < n; ++j)
-                for (int l = 0; l < k; ++l) V[(size_t)j * k + l] = cm[(size_t)l * n + j];
+        return;
+    }
+    const int k = bk.rank;
+    if (k == 0) return;
+    if (U)
+        for (const Piece& pc : h->far_pieces) {
+            if (pc.block != b) continue;
+            const Tile& t = h->tiles_h[pc.tile];
+            fetch(h->far_pool.p, h->factor_dtype, t.foff + (long long)pc.col * t.ld, (size_t)k * t.ld);
+            for (int i = 0; i < t.rows; ++i)
+                for (int l = 0; l < k; ++l) U[(size_t)(t.r0 - bk.r0 + i) * k + l] = cm[(size_t)l * t.ld + i];
         }
+    if (V) {
+        const Group& gr = h->groups_h[bk.group];
+        fetch(h->far_pool.p, h->factor_dtype, gr.voff, (size_t)gr.ld * gr.n);
+        for (int j = 0; j < n; ++j)
+            for (int l = 0; l < k; ++l) V[(size_t)j * k + l] = cm[(size_t)j * gr.ld + bk.grow + l];
     }
 }
 

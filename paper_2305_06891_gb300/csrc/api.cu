@@ -413,10 +413,8 @@ int rad_htree_get_stats(const rad_htree* h, rad_htree_stats* st) {
         st->aca_entries = h->aca_entries;
         st->bytes_near = h->near_entries * dtype_size(h->near_dtype);
         st->bytes_far = h->far_entries * dtype_size(h->factor_dtype);
-        for (auto& f : h->far_h) {
-            st->far_u_entries += (int64_t)f.k * f.m;
-            st->far_v_entries += (int64_t)f.k * f.n;
-        }
+        st->far_u_entries = h->far_u_entries;
+        st->far_v_entries = h->far_v_entries;
         st->n_tiles = h->n_tiles;
     });
 }

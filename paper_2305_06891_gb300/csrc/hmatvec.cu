@@ -1,21 +1,20 @@
 // A6: the block low-rank matrix-vector product y = F x of §5.2, in tree
-// order, in two phases:
-//   phase 1  t_b = V_b^T x_tau           for every low-rank block b
-//   phase 2  y_rho = sum_near D x_tau + sum_far U t_b   per row tile rho
-// Phase 2 gives every row tile (a leaf cluster, <= 64 rows) to one CTA, which
-// owns its output rows: no atomics, a fixed summation order, deterministic.
+// order, in two phases over the panel storage:
+//   phase 1  T = V^T X      one column group (a column cluster's low-rank
+//                           blocks, V^T rows stacked) at a time
+//   phase 2  Y = [D | U] [X(xidx); T(tidx)]   one row tile at a time
+// Every row tile is owned by one CTA: no atomics, a fixed summation order,
+// deterministic results.  Panels are contiguous and column-major, so a CTA
+// streams each of them front to back with fully coalesced loads.
 //
-// Dense blocks and U, V are stored column-major, so a tile's rows of a block
-// are one contiguous run per column: with one thread per row, each warp
-// load is 32 consecutive elements (fully coalesced streaming from HBM).
-//
-// One right-hand side: phase 1 is one warp per row of V^T (lanes over the
-// block's columns, shuffle reduction); phase 2 spreads a tile's blocks over
-// the CTA's warps and reduces the partial rows through shared memory in a
+// One right-hand side: thread (r, g) of a CTA takes row r of the panel and
+// every G-th column starting at g, so one CTA-wide step reads G * ld
+// consecutive elements; partial rows are summed over g in shared memory in a
 // fixed order.
-// Many right-hand sides: both phases are small gathered GEMMs; A (block
-// rows) and B (rows of X or T) are staged through shared memory in K-chunks
-// and every thread accumulates a 4 x RN register tile (FP32 or FP64 FFMA).
+// Many right-hand sides: a panel GEMM.  Chunks of KC panel columns (A) and
+// the KC gathered rows of X or T they multiply (B) are staged in shared
+// memory, double buffered through registers; each thread accumulates a
+// 4-row x RN-column tile (FP32 or FP64 FFMA).
 //
 // Epilogues fuse the reflection operator of Eq. (11):
 //   kReflect: w = xin - (1 - eps) o (F x)
@@ -40,217 +39,349 @@ __device__ __forceinline__ void epilogue(const Epi& epi, void* Y, int ldy, int r
 }
 
 // ---------------------------------------------------------------- 1 RHS
-template <class FS, class AT>
-__global__ void __launch_bounds__(256) phase1_single(OpView op, const AT* __restrict__ X, AT* __restrict__ T) {
-    const int w = blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (w >= op.sum_rank) return;
-    const int b = op.trow_block[w];
-    const FarDesc f = op.fd[b];
-    const int l = w - f.toff;
-    const FS* v = static_cast<const FS*>(op.far_pool) + f.offV + (long long)l * f.n;
-    const AT* x = X + f.c0;
-    AT a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    int j = lane;
-    for (; j + 96 < f.n; j += 128) {
-        a0 += (AT)Store<FS>::get(v[j]) * x[j];
-        a1 += (AT)Store<FS>::get(v[j + 32]) * x[j + 32];
-        a2 += (AT)Store<FS>::get(v[j + 64]) * x[j + 64];
-        a3 += (AT)Store<FS>::get(v[j + 96]) * x[j + 96];
+// Four consecutive stored elements (16-byte aligned for FP32, 8 for BF16,
+// 32 for FP64) converted to the accumulation type.
+template <class S, class AT> struct Vec4;
+template <> struct Vec4<float, float> {
+    static __device__ __forceinline__ void load(const float* p, float v[4]) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     }
-    for (; j < f.n; j += 32) a0 += (AT)Store<FS>::get(v[j]) * x[j];
-    AT acc = warp_sum((a0 + a1) + (a2 + a3));
-    if (lane == 0) T[w] = acc;
+};
+template <> struct Vec4<double, double> {
+    static __device__ __forceinline__ void load(const double* p, double v[4]) {
+        const double2 a = reinterpret_cast<const double2*>(p)[0];
+        const double2 b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+template <> struct Vec4<__nv_bfloat16, float> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16* p, float v[4]) {
+        const uint2 q = *reinterpret_cast<const uint2*>(p);
+        v[0] = __uint_as_float(q.x << 16); v[1] = __uint_as_float(q.x & 0xffff0000u);
+        v[2] = __uint_as_float(q.y << 16); v[3] = __uint_as_float(q.y & 0xffff0000u);
+    }
+};
+
+template <class FS, class AT>
+__global__ void __launch_bounds__(256) far_vt_single(OpView op, const AT* __restrict__ x, AT* __restrict__ T) {
+    __shared__ AT part[1024];
+    const Group gr = op.groups[blockIdx.x];
+    // each thread owns 4 consecutive rows of a column (one vector load);
+    // rq row quads per pass, G = 256 / rq column phases
+    const int quads = gr.ld / 4;
+    const int rq = min(256, quads);
+    const int G = 256 / rq;
+    const int q = threadIdx.x % rq, jg = threadIdx.x / rq;
+    const long long ld = gr.ld;
+    const AT* xv = x + gr.c0;
+    for (int q0 = 0; q0 < quads; q0 += rq) {
+        AT acc[4] = {0, 0, 0, 0};
+        if (q0 + q < quads && jg < G) {
+            const FS* P = static_cast<const FS*>(op.far_pool) + gr.voff + 4 * (q0 + q);
+            int j = jg;
+            for (; j + G < gr.n; j += 2 * G) {
+                AT v0[4], v1[4];
+                Vec4<FS, AT>::load(P + j * ld, v0);
+                Vec4<FS, AT>::load(P + (j + G) * ld, v1);
+                const AT x0 = xv[j], x1 = xv[j + G];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[r] += v0[r] * x0 + v1[r] * x1;
+            }
+            if (j < gr.n) {
+                AT v0[4];
+                Vec4<FS, AT>::load(P + j * ld, v0);
+                const AT x0 = xv[j];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[r] += v0[r] * x0;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) part[4 * threadIdx.x + r] = acc[r];
+        __syncthreads();
+        for (int rr = threadIdx.x; rr < 4 * rq; rr += 256) {
+            const int row = 4 * q0 + rr;
+            if (row < gr.M) {
+                AT s = 0;
+                for (int g = 0; g < G; ++g) s += part[4 * (g * rq) + rr];
+                T[gr.toff + row] = s;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// acc[0..3] += sum over panel columns c = g, g + G, ... of the 4 rows at P
+// of column c times v[idx[c]]
+template <class S, class AT>
+__device__ __forceinline__ void stream_panel4(const S* __restrict__ P, long long ld, int kcols, int g, int G,
+                                              const int* __restrict__ idx, const AT* __restrict__ v, AT acc[4]) {
+    int c = g;
+    for (; c + 3 * G < kcols; c += 4 * G) {
+        AT a0[4], a1[4], a2[4], a3[4];
+        Vec4<S, AT>::load(P + c * ld, a0);
+        Vec4<S, AT>::load(P + (c + G) * ld, a1);
+        Vec4<S, AT>::load(P + (c + 2 * G) * ld, a2);
+        Vec4<S, AT>::load(P + (c + 3 * G) * ld, a3);
+        const AT x0 = v[idx[c]], x1 = v[idx[c + G]], x2 = v[idx[c + 2 * G]], x3 = v[idx[c + 3 * G]];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r] += (a0[r] * x0 + a1[r] * x1) + (a2[r] * x2 + a3[r] * x3);
+    }
+    for (; c < kcols; c += G) {
+        AT a0[4];
+        Vec4<S, AT>::load(P + c * ld, a0);
+        const AT x0 = v[idx[c]];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r] += a0[r] * x0;
+    }
 }
 
 template <class NS, class FS, class AT>
 __global__ void __launch_bounds__(256)
-phase2_single(OpView op, const AT* __restrict__ X, const AT* __restrict__ T, void* Y, Epi epi) {
-    __shared__ AT part[8][kTileRows];
-    const TileDesc t = op.tiles[blockIdx.x];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nh = (t.rows + 31) >> 5;
-    const int hh = warp % nh, g = warp / nh, ng = 8 / nh;
-    const int row = hh * 32 + lane;
-    const bool active = row < t.rows;
-    AT acc = 0;
-    for (int e = t.e0 + g; e < t.e1; e += ng) {
-        const int2 en = op.entries[e];
-        if (en.x & kFarBit) {
-            const FarDesc f = op.fd[en.x & 0x7fffffff];
-            if (active) {
-                const FS* U = static_cast<const FS*>(op.far_pool) + f.offU + en.y + row;
-                const AT* tb = T + f.toff;
-                AT s0 = 0, s1 = 0;
-                int l = 0;
-                for (; l + 1 < f.k; l += 2) {
-                    s0 += (AT)Store<FS>::get(U[(long long)l * f.m]) * tb[l];
-                    s1 += (AT)Store<FS>::get(U[(long long)(l + 1) * f.m]) * tb[l + 1];
-                }
-                if (l < f.k) s0 += (AT)Store<FS>::get(U[(long long)l * f.m]) * tb[l];
-                acc += s0 + s1;
-            }
-        } else {
-            const NearDesc d = op.nd[en.x];
-            if (active) {
-                const NS* D = static_cast<const NS*>(op.near_pool) + d.off + en.y + row;
-                const AT* x = X + d.c0;
-                const long long m = d.m;
-                AT s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-                int j = 0;
-                for (; j + 3 < d.n; j += 4) {
-                    s0 += (AT)Store<NS>::get(D[(long long)j * m]) * x[j];
-                    s1 += (AT)Store<NS>::get(D[(long long)(j + 1) * m]) * x[j + 1];
-                    s2 += (AT)Store<NS>::get(D[(long long)(j + 2) * m]) * x[j + 2];
-                    s3 += (AT)Store<NS>::get(D[(long long)(j + 3) * m]) * x[j + 3];
-                }
-                for (; j < d.n; ++j) s0 += (AT)Store<NS>::get(D[(long long)j * m]) * x[j];
-                acc += (s0 + s1) + (s2 + s3);
-            }
-        }
+rows_single(OpView op, const AT* __restrict__ x, const AT* __restrict__ T, void* Y, Epi epi) {
+    __shared__ AT part[1024];
+    const Tile t = op.tiles[blockIdx.x];
+    // thread (q, g): rows 4q .. 4q+3, panel columns g, g + G, ...
+    const int quads = t.ld / 4;
+    const int G = 256 / quads;
+    const int q = threadIdx.x % quads, g = threadIdx.x / quads;
+    AT acc[4] = {0, 0, 0, 0};
+    if (g < G) {
+        stream_panel4<NS, AT>(static_cast<const NS*>(op.near_pool) + t.noff + 4 * q, t.ld, t.kn, g, G,
+                              op.xidx + t.ixn, x, acc);
+        stream_panel4<FS, AT>(static_cast<const FS*>(op.far_pool) + t.foff + 4 * q, t.ld, t.kf, g, G,
+                              op.tidx + t.ixf, T, acc);
     }
-    if (active) part[g][row] = acc;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) part[4 * threadIdx.x + r] = acc[r];
     __syncthreads();
     if ((int)threadIdx.x < t.rows) {
-        const int r = threadIdx.x;
+        const int row = threadIdx.x;
         AT s = 0;
-        for (int q = 0; q < ng; ++q) s += part[q][r];
-        epilogue<AT>(epi, Y, 1, t.r0 + r, 0, s);
+        for (int gg = 0; gg < G; ++gg) s += part[4 * (gg * quads) + row];
+        epilogue<AT>(epi, Y, 1, t.r0 + row, 0, s);
     }
 }
 
 // ---------------------------------------------------------------- many RHS
-constexpr int kKC = 16;
+template <class AT> struct Chunk;
+template <> struct Chunk<float> { static constexpr int KC = 32; };
+template <> struct Chunk<double> { static constexpr int KC = 16; };
+constexpr int kMaxCols = 96;    // right-hand sides per launch
+constexpr int kNCS = kMaxCols + 4;
+constexpr int kStages = 3;
 
-template <class AT, int RN>
-struct MicroTile {
-    AT acc[4][RN];
-    __device__ void zero() {
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int q = 0; q < RN; ++q) acc[r][q] = 0;
-    }
+// Dynamic shared memory of the panel GEMM: kStages x (A chunk, B chunk).
+template <class AS, class AT>
+struct GemmLayout {
+    static constexpr int KC = Chunk<AT>::KC;
+    static constexpr size_t a_bytes = sizeof(AS) * KC * kTileRows;
+    static constexpr size_t b_bytes = sizeof(AT) * KC * kNCS;
+    static constexpr size_t stage = (a_bytes + b_bytes + 127) / 128 * 128;
+    static constexpr size_t bytes = kStages * stage;
 };
 
-// Accumulate C(64 x NC) += A(rows x K) B(K x nc) through shared memory.
-//   A(i, k) = Aptr[k * a_ld + i]  (a_colmajor) or Aptr[i * a_ld + k]
-//   B(k, c) = Bptr[k * ldb + c]
-template <class AS, class AT, int RN>
-__device__ __forceinline__ void gemm_tile(MicroTile<AT, RN>& mt, AT (*As)[kTileRows + 4], AT (*Bs)[16 * RN + 4],
-                                          const AS* Aptr, long long a_ld, bool a_colmajor, int rows, int K,
-                                          const AT* Bptr, long long ldb, int nc) {
-    constexpr int NC = 16 * RN;
-    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
-    for (int k0 = 0; k0 < K; k0 += kKC) {
-        if (a_colmajor) {
-            for (int q = threadIdx.x; q < kKC * kTileRows; q += 256) {
-                const int kk = q / kTileRows, i = q - kk * kTileRows;
-                AT v = 0;
-                if (i < rows && k0 + kk < K) v = (AT)Store<AS>::get(Aptr[(long long)(k0 + kk) * a_ld + i]);
-                As[kk][i] = v;
+// 4-byte / 8-byte asynchronous global -> shared copies; a false predicate
+// copies nothing and fills the destination with zeros.
+__device__ __forceinline__ void cp_async_4(void* sdst, const void* gsrc, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(pred ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async_8(void* sdst, const void* gsrc, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gsrc), "r"(pred ? 8 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <class AT>
+__device__ __forceinline__ void cp_async_elem(AT* sdst, const AT* gsrc, bool pred);
+template <>
+__device__ __forceinline__ void cp_async_elem<float>(float* d, const float* g, bool p) { cp_async_4(d, g, p); }
+template <>
+__device__ __forceinline__ void cp_async_elem<double>(double* d, const double* g, bool p) { cp_async_8(d, g, p); }
+
+// acc(4 x RN per thread) += A(rows x K) B(K x nc): A column-major panel with
+// leading dimension lda (a chunk of <= 64 rows, rows_pad = 4 RG), B(k, :) =
+// row bsel(k) of the vector block Bv (leading dimension ldb).  Chunks of KC
+// columns of A (copied as raw 4-byte words) and the KC rows of B go through
+// a kStages-deep cp.async ring.  Thread (rg, cg) = (tid / CG, tid % CG) owns
+// rows 4 rg .. 4 rg + 3 and columns cg + CG q.
+template <class AS, class AT, int RN, class BSel>
+__device__ __forceinline__ void panel_gemm(AT (&acc)[4][RN], unsigned char* smem, const AS* __restrict__ A,
+                                           long long lda, int rows_pad, int K, BSel bsel,
+                                           const AT* __restrict__ Bv, int ldb, int nc, int RG, int CG) {
+    using L = GemmLayout<AS, AT>;
+    constexpr int KC = L::KC;
+    constexpr int WPE = sizeof(AS) >= 4 ? (int)(sizeof(AS) / 4) : 1;   // words per element (>= 1)
+    constexpr int EPW = sizeof(AS) >= 4 ? 1 : (int)(4 / sizeof(AS));   // elements per word
+    const int nchunks = (K + KC - 1) / KC;
+    if (nchunks == 0) return;
+    const int tid = threadIdx.x;
+    const int rg = tid / CG, cg = tid - rg * CG;
+    const bool active = rg < RG;
+    int boff[RN];
+#pragma unroll
+    for (int q = 0; q < RN; ++q) boff[q] = min(cg + CG * q, nc - 1);
+    // staging assignment: thread t copies word a_w of chunk columns a_kk0,
+    // a_kk0 + a_step, ... and element b_c of chunk rows b_kk0, b_kk0 + b_step
+    const int wpc = rows_pad * WPE / EPW;             // A words per column
+    const int a_step = 256 / wpc, a_kk0 = tid / wpc, a_w = tid - a_kk0 * wpc;
+    const int b_step = 256 / nc, b_kk0 = tid / nc, b_c = tid - b_kk0 * nc;
+    const unsigned* Aw = reinterpret_cast<const unsigned*>(A);
+    const long long ldaw = lda * WPE / EPW;           // A words per panel column
+    auto issue = [&](int ch) {
+        unsigned char* st = smem + (size_t)(ch % kStages) * L::stage;
+        unsigned* As = reinterpret_cast<unsigned*>(st);
+        AT* Bs = reinterpret_cast<AT*>(st + L::a_bytes);
+        const int k0 = ch * KC;
+        if (a_kk0 < a_step)
+            for (int kk = a_kk0; kk < KC; kk += a_step) {
+                const bool ok = k0 + kk < K;
+                const unsigned* src = ok ? Aw + (long long)(k0 + kk) * ldaw + a_w : Aw;
+                cp_async_4(As + kk * (kTileRows * WPE / EPW) + a_w, src, ok);
             }
-        } else {
-            for (int q = threadIdx.x; q < kKC * kTileRows; q += 256) {
-                const int i = q / kKC, kk = q - i * kKC;
-                AT v = 0;
-                if (i < rows && k0 + kk < K) v = (AT)Store<AS>::get(Aptr[(long long)i * a_ld + k0 + kk]);
-                As[kk][i] = v;
+        if (b_kk0 < b_step)
+            for (int kk = b_kk0; kk < KC; kk += b_step) {
+                const bool ok = k0 + kk < K;
+                const AT* src = ok ? Bv + (long long)bsel(k0 + kk) * ldb + b_c : Bv;
+                cp_async_elem<AT>(Bs + kk * kNCS + b_c, src, ok);
+            }
+        cp_async_commit();
+    };
+    issue(0);
+    if (nchunks > 1) issue(1);
+    else cp_async_commit();
+    for (int ch = 0; ch < nchunks; ++ch) {
+        cp_async_wait<kStages - 2>();
+        __syncthreads();
+        if (ch + 2 < nchunks) issue(ch + 2);
+        else cp_async_commit();
+        if (active) {
+            const unsigned char* st = smem + (size_t)(ch % kStages) * L::stage;
+            const AS* As = reinterpret_cast<const AS*>(st);
+            const AT* Bs = reinterpret_cast<const AT*>(st + L::a_bytes);
+            // chunk entries past K were filled with zeros
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) {
+                AT a[4], b[RN];
+                Vec4<AS, AT>::load(As + kk * kTileRows + rg * 4, a);
+#pragma unroll
+                for (int q = 0; q < RN; ++q) b[q] = Bs[kk * kNCS + boff[q]];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < RN; ++q) acc[r][q] += a[r] * b[q];
             }
         }
-        for (int q = threadIdx.x; q < kKC * NC; q += 256) {
-            const int kk = q / NC, c = q - kk * NC;
-            AT v = 0;
-            if (c < nc && k0 + kk < K) v = Bptr[(long long)(k0 + kk) * ldb + c];
-            Bs[kk][c] = v;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+}
+
+struct AffineRows {
+    int base;
+    __device__ __forceinline__ int operator()(int k) const { return base + k; }
+};
+struct IndexRows {
+    const int* idx;
+    __device__ __forceinline__ int operator()(int k) const { return idx[k]; }
+};
+
+template <class FS, class AT, int RN>
+__global__ void __launch_bounds__(256, 3)
+far_vt_multi(OpView op, const AT* __restrict__ X, int ldx, AT* __restrict__ T, int ldt, int nc) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const GWork w = op.gwork[blockIdx.x];
+    const Group gr = op.groups[w.g];
+    const int rows_pad = (w.rows + 3) / 4 * 4;
+    const int RG = rows_pad / 4, CG = 256 / RG;
+    AT acc[4][RN];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < RN; ++q) acc[r][q] = 0;
+    panel_gemm<FS, AT, RN>(acc, dsm, static_cast<const FS*>(op.far_pool) + gr.voff + w.r0, gr.ld, rows_pad, gr.n,
+                           AffineRows{gr.c0}, X, ldx, nc, RG, CG);
+    const int rg = threadIdx.x / CG, cg = threadIdx.x - rg * CG;
+    if (rg >= RG) return;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int row = rg * 4 + r;
+        if (row >= w.rows) continue;
+#pragma unroll
+        for (int q = 0; q < RN; ++q) {
+            const int c = cg + CG * q;
+            if (c < nc) T[(long long)(gr.toff + w.r0 + row) * ldt + c] = acc[r][q];
         }
-        __syncthreads();
+    }
+}
+
+template <class NS, class FS, class AT, int RN>
+__global__ void __launch_bounds__(256, 3)
+rows_multi(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ T, int ldt, void* Y, int ldy, int nc,
+           Epi epi) {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const Tile t = op.tiles[blockIdx.x];
+    const int RG = t.ld / 4, CG = 256 / RG;
+    AT acc[4][RN];
 #pragma unroll
-        for (int kk = 0; kk < kKC; ++kk) {
-            AT a[4], b[RN];
+    for (int r = 0; r < 4; ++r)
 #pragma unroll
-            for (int r = 0; r < 4; ++r) a[r] = As[kk][tr * 4 + r];
+        for (int q = 0; q < RN; ++q) acc[r][q] = 0;
+    panel_gemm<NS, AT, RN>(acc, dsm, static_cast<const NS*>(op.near_pool) + t.noff, t.ld, t.ld, t.kn,
+                           IndexRows{op.xidx + t.ixn}, X, ldx, nc, RG, CG);
+    panel_gemm<FS, AT, RN>(acc, dsm, static_cast<const FS*>(op.far_pool) + t.foff, t.ld, t.ld, t.kf,
+                           IndexRows{op.tidx + t.ixf}, T, ldt, nc, RG, CG);
+    const int rg = threadIdx.x / CG, cg = threadIdx.x - rg * CG;
+    if (rg >= RG) return;
 #pragma unroll
-            for (int q = 0; q < RN; ++q) b[q] = Bs[kk][tc + 16 * q];
+    for (int r = 0; r < 4; ++r) {
+        const int row = rg * 4 + r;
+        if (row >= t.rows) continue;
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int q = 0; q < RN; ++q) mt.acc[r][q] += a[r] * b[q];
+        for (int q = 0; q < RN; ++q) {
+            const int c = cg + CG * q;
+            if (c < nc) epilogue<AT>(epi, Y, ldy, t.r0 + row, c, acc[r][q]);
         }
-        __syncthreads();
     }
 }
 
 template <class FS, class AT, int RN>
-__global__ void __launch_bounds__(256)
-phase1_multi(OpView op, const AT* __restrict__ X, int ldx, AT* __restrict__ T, int ldt, int nc) {
-    __shared__ AT As[kKC][kTileRows + 4];
-    __shared__ AT Bs[kKC][16 * RN + 4];
-    const FarDesc f = op.fd[op.far_nz[blockIdx.x]];
-    const FS* V = static_cast<const FS*>(op.far_pool) + f.offV;
-    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
-    for (int l0 = 0; l0 < f.k; l0 += kTileRows) {
-        MicroTile<AT, RN> mt;
-        mt.zero();
-        gemm_tile<FS, AT, RN>(mt, As, Bs, V + (long long)l0 * f.n, f.n, false, min(kTileRows, f.k - l0), f.n,
-                              X + (long long)f.c0 * ldx, ldx, nc);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int l = l0 + tr * 4 + r;
-            if (l >= f.k) continue;
-#pragma unroll
-            for (int q = 0; q < RN; ++q) {
-                const int c = tc + 16 * q;
-                if (c < nc) T[(long long)(f.toff + l) * ldt + c] = mt.acc[r][q];
-            }
-        }
-    }
-}
-
-template <class NS, class FS, class AT, int RN>
-__global__ void __launch_bounds__(256)
-phase2_multi(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ T, int ldt, void* Y, int ldy,
-             int nc, Epi epi) {
-    __shared__ AT As[kKC][kTileRows + 4];
-    __shared__ AT Bs[kKC][16 * RN + 4];
-    const TileDesc t = op.tiles[blockIdx.x];
-    MicroTile<AT, RN> mt;
-    mt.zero();
-    for (int e = t.e0; e < t.e1; ++e) {
-        const int2 en = op.entries[e];
-        if (en.x & kFarBit) {
-            const FarDesc f = op.fd[en.x & 0x7fffffff];
-            const FS* U = static_cast<const FS*>(op.far_pool) + f.offU + en.y;
-            gemm_tile<FS, AT, RN>(mt, As, Bs, U, f.m, true, t.rows, f.k, T + (long long)f.toff * ldt, ldt, nc);
-        } else {
-            const NearDesc d = op.nd[en.x];
-            const NS* D = static_cast<const NS*>(op.near_pool) + d.off + en.y;
-            gemm_tile<NS, AT, RN>(mt, As, Bs, D, d.m, true, t.rows, d.n, X + (long long)d.c0 * ldx, ldx, nc);
-        }
-    }
-    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int row = tr * 4 + r;
-        if (row >= t.rows) continue;
-#pragma unroll
-        for (int q = 0; q < RN; ++q) {
-            const int c = tc + 16 * q;
-            if (c < nc) epilogue<AT>(epi, Y, ldy, t.r0 + row, c, mt.acc[r][q]);
-        }
-    }
-}
-
-template <class NS, class FS, class AT, int RN>
-void launch_multi(const rad_htree* h, const AT* X, int ldx, AT* T, int ldt, void* Y, int ldy, int nc,
-                  const Epi& epi, cudaStream_t s) {
+void launch_far_vt(const rad_htree* h, const AT* X, int ldx, AT* T, int ldt, int nc, cudaStream_t s) {
     const OpView op = h->view();
-    if (op.n_far_nz > 0) {
-        { ProfScope ps_("hmm_far_vt", s); phase1_multi<FS, AT, RN><<<op.n_far_nz, 256, 0, s>>>(op, X, ldx, T, ldt, nc); }
-        RAD_CHECK_LAUNCH();
+    const size_t bytes = GemmLayout<FS, AT>::bytes > GemmLayout<float, AT>::bytes ? GemmLayout<FS, AT>::bytes
+                                                                                  : GemmLayout<float, AT>::bytes;
+    static bool configured = false;
+    if (!configured) {
+        RAD_CUDA(cudaFuncSetAttribute(far_vt_multi<FS, AT, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        configured = true;
     }
-    { ProfScope ps_("hmm_rows", s); phase2_multi<NS, FS, AT, RN><<<op.n_tiles, 256, 0, s>>>(op, X, ldx, T, ldt, Y, ldy, nc, epi); }
+    { ProfScope ps_("hmm_far_vt", s); far_vt_multi<FS, AT, RN><<<op.n_gwork, 256, bytes, s>>>(op, X, ldx, T, ldt, nc); }
     RAD_CHECK_LAUNCH();
+}
+template <class NS, class FS, class AT, int RN>
+void launch_rows(const rad_htree* h, const AT* X, int ldx, const AT* T, int ldt, void* Y, int ldy, int nc,
+                 const Epi& epi, cudaStream_t s) {
+    const OpView op = h->view();
+    const size_t bytes = GemmLayout<NS, AT>::bytes > GemmLayout<FS, AT>::bytes ? GemmLayout<NS, AT>::bytes
+                                                                                : GemmLayout<FS, AT>::bytes;
+    static bool configured = false;
+    if (!configured) {
+        RAD_CUDA(cudaFuncSetAttribute(rows_multi<NS, FS, AT, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        configured = true;
+    }
+    { ProfScope ps_("hmm_rows", s); rows_multi<NS, FS, AT, RN><<<op.n_tiles, 256, bytes, s>>>(op, X, ldx, T, ldt, Y, ldy, nc, epi); }
+    RAD_CHECK_LAUNCH();
+}
+
+// Register-tile width RN for nc columns when the panel with the most row
+// groups has leading dimension max_ld: CG = 256 / (max_ld / 4) >= 16 column
+// slots, so RN = ceil(nc / CG) <= 8 for nc <= 128.
+inline int rn_for(int max_ld, int nc) {
+    const int cg = 256 / (max_ld / 4);
+    return std::max(1, std::min(8, (nc + cg - 1) / cg));
 }
 
 template <class NS, class FS, class AT>
@@ -258,17 +389,21 @@ void apply_t(const rad_htree* h, const AT* X, int ldx, void* Y, int ldy, int nrh
              cudaStream_t s) {
     const OpView op = h->view();
     if (nrhs == 1) {
-        if (op.sum_rank > 0) {
-            { ProfScope ps_("hmv_far_vt", s); phase1_single<FS, AT><<<(op.sum_rank + 7) / 8, 256, 0, s>>>(op, X, T); }
+        if (op.n_gwork > 0) {
+            { ProfScope ps_("hmv_far_vt", s); far_vt_single<FS, AT><<<(unsigned)h->groups_h.size(), 256, 0, s>>>(op, X, T); }
             RAD_CHECK_LAUNCH();
         }
-        { ProfScope ps_("hmv_rows", s); phase2_single<NS, FS, AT><<<op.n_tiles, 256, 0, s>>>(op, X, T, Y, epi); }
+        { ProfScope ps_("hmv_rows", s); rows_single<NS, FS, AT><<<op.n_tiles, 256, 0, s>>>(op, X, T, Y, epi); }
         RAD_CHECK_LAUNCH();
         return;
     }
+    int tile_ld = 4, group_ld = 4;
+    for (auto& t : h->tiles_h) tile_ld = std::max(tile_ld, t.ld);
+    for (auto& g : h->groups_h) group_ld = std::max(group_ld, (int)std::min<long long>(kTileRows, round_up(g.M, 4)));
+    const int ldt = tree_ld(nrhs);
     const int esz = epi.mode == kStore ? (int)sizeof(AT) : 8;
-    for (int c0 = 0; c0 < nrhs; c0 += 128) {
-        const int nc = std::min(128, nrhs - c0);
+    for (int c0 = 0; c0 < nrhs; c0 += kMaxCols) {
+        const int nc = std::min(kMaxCols, nrhs - c0);
         Epi e2 = epi;
         if (epi.mode != kStore) {
             e2.xin = epi.xin + c0;
@@ -277,16 +412,27 @@ void apply_t(const rad_htree* h, const AT* X, int ldx, void* Y, int ldy, int nrh
         const AT* Xc = X + c0;
         AT* Tc = T + c0;
         void* Yc = static_cast<char*>(Y) + (size_t)c0 * esz;
-        const int rn = (nc + 15) / 16;
-        switch (rn) {
-            case 1: launch_multi<NS, FS, AT, 1>(h, Xc, ldx, Tc, nrhs, Yc, ldy, nc, e2, s); break;
-            case 2: launch_multi<NS, FS, AT, 2>(h, Xc, ldx, Tc, nrhs, Yc, ldy, nc, e2, s); break;
-            case 3: launch_multi<NS, FS, AT, 3>(h, Xc, ldx, Tc, nrhs, Yc, ldy, nc, e2, s); break;
-            case 4: launch_multi<NS, FS, AT, 4>(h, Xc, ldx, Tc, nrhs, Yc, ldy, nc, e2, s); break;
-            case 5: launch_multi<NS, FS, AT, 5>(h, Xc, ldx, Tc, nrhs, Yc, ldy, nc, e2, s); break;
-            case 6: launch_multi<NS, FS, AT, 6>(h, Xc, ldx, Tc, nrhs, Yc, ldy, nc, e2, s); break;
-            case 7: launch_multi<NS, FS, AT, 7>(h, Xc, ldx, Tc, nrhs, Yc, ldy, nc, e2, s); break;
-            default: launch_multi<NS, FS, AT, 8>(h, Xc, ldx, Tc, nrhs, Yc, ldy, nc, e2, s); break;
+        if (op.n_gwork > 0) {
+            switch (rn_for(group_ld, nc)) {
+                case 1: launch_far_vt<FS, AT, 1>(h, Xc, ldx, Tc, ldt, nc, s); break;
+                case 2: launch_far_vt<FS, AT, 2>(h, Xc, ldx, Tc, ldt, nc, s); break;
+                case 3: launch_far_vt<FS, AT, 3>(h, Xc, ldx, Tc, ldt, nc, s); break;
+                case 4: launch_far_vt<FS, AT, 4>(h, Xc, ldx, Tc, ldt, nc, s); break;
+                case 5: launch_far_vt<FS, AT, 5>(h, Xc, ldx, Tc, ldt, nc, s); break;
+                case 6: launch_far_vt<FS, AT, 6>(h, Xc, ldx, Tc, ldt, nc, s); break;
+                case 7: launch_far_vt<FS, AT, 7>(h, Xc, ldx, Tc, ldt, nc, s); break;
+                default: launch_far_vt<FS, AT, 8>(h, Xc, ldx, Tc, ldt, nc, s); break;
+            }
+        }
+        switch (rn_for(tile_ld, nc)) {
+            case 1: launch_rows<NS, FS, AT, 1>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 2: launch_rows<NS, FS, AT, 2>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 3: launch_rows<NS, FS, AT, 3>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 4: launch_rows<NS, FS, AT, 4>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 5: launch_rows<NS, FS, AT, 5>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 6: launch_rows<NS, FS, AT, 6>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 7: launch_rows<NS, FS, AT, 7>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            default: launch_rows<NS, FS, AT, 8>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
         }
     }
 }
@@ -313,7 +459,7 @@ __global__ void scatter_kernel(int n, int nrhs, const TI* __restrict__ Y, int ld
 
 size_t apply_workspace_bytes(const rad_htree* h, int nrhs) {
     const size_t esz = h->op_is_f64() ? 8 : 4;
-    return esz * (size_t)std::max(1, h->sum_rank) * (size_t)nrhs;
+    return esz * (size_t)std::max(1, h->sum_rank) * (size_t)tree_ld(nrhs);
 }
 
 void apply_tree(const rad_htree* h, const void* X, int ldx, void* Y, int ldy, int nrhs, const Epi& epi,

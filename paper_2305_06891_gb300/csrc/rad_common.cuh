@@ -136,27 +136,39 @@ struct NodeBox {
     double lo[3], hi[3];
 };
 
-// Dense block: rows [r0, r0+m), cols [c0, c0+n), column-major m x n at off.
-struct NearDesc {
-    int r0, c0, m, n;
-    long long off;
+// Operator storage ("panels").
+//
+// Row tile: rows [r0, r0 + rows) of the matrix (a leaf cluster cut into
+// pieces of at most 64 rows), leading dimension ld = round_up(rows, 4).  Its
+// dense panel (near storage type) holds the tile's rows of every dense block
+// that covers it, side by side: kn columns, column-major, at noff; column c
+// multiplies row xidx[ixn + c] of X.  Its low-rank panel (factor storage
+// type) holds the tile's rows of U for every low-rank block covering it: kf
+// columns at foff; column c multiplies row tidx[ixf + c] of T = V^T X.
+struct Tile {
+    int r0, rows, ld, kn, kf, ixn, ixf, pad;
+    long long noff, foff;
 };
-// Low-rank block: U column-major m x k at offU, V column-major n x k at offV;
-// its V^T x lives at rows [toff, toff+k) of the T workspace.
-struct FarDesc {
-    int r0, c0, m, n, k, toff;
-    long long offU, offV;
+// Column group: the low-rank blocks whose column cluster is [c0, c0 + n).
+// Its V panel stacks their V^T rows: M rows (block b, column l of V_b),
+// ld = round_up(M, 4), n columns, column-major at voff (factor storage
+// type).  Its rows of T are [toff, toff + M).
+struct Group {
+    int c0, n, M, ld, toff, pad;
+    long long voff;
 };
-// Row tile: rows [r0, r0+rows) (rows <= 64) and its entries [e0, e1).
-struct TileDesc {
-    int r0, rows, e0, e1;
+// Phase-1 work item: rows [r0, r0 + rows) (rows <= 64) of group g.
+struct GWork {
+    int g, r0, rows, pad;
 };
-// Tile entry: x = block id (bit 31 set for a low-rank block), y = row offset
-// of the tile inside the block.
-constexpr int kFarBit = int(0x80000000u);
 
 constexpr int kTileRows = 64;
 constexpr int kMaxRank = 128;
+
+// Leading dimension of the tree-order vector blocks (X, T, Y) used by the
+// product for nrhs right-hand sides: 1 for one, else a multiple of 4 so that
+// every row starts on a 16-byte boundary.
+inline int tree_ld(int nrhs) { return nrhs == 1 ? 1 : (int)((nrhs + 3) / 4 * 4); }
 
 // Canonical leaf block (export order = sorted by (r0, c0)).
 struct BlockH {
@@ -164,22 +176,26 @@ struct BlockH {
     int r0, r1, c0, c1;
     int admissible;
     int rank;        // -1: stored dense
-    int store_idx;   // index into near or far descriptor arrays
+    int group;       // low-rank: column group holding V^T (else -1)
+    int grow;        // low-rank: first row of its V^T in that group
+};
+// One piece of a block stored in a row tile: tile t, first panel column.
+struct Piece {
+    int block, tile, col;
 };
 
 // Device view of a compressed operator, passed by value to the kernels.
 struct OpView {
     int n_tiles;
-    const TileDesc* tiles;
-    const int2* entries;
-    const NearDesc* nd;
+    const Tile* tiles;
     const void* near_pool;
-    const FarDesc* fd;
     const void* far_pool;
+    const int* xidx;
+    const int* tidx;
+    int n_gwork;
+    const GWork* gwork;
+    const Group* groups;
     int sum_rank;
-    const int* trow_block;   // T row -> far block
-    int n_far_nz;
-    const int* far_nz;       // far blocks with k > 0, largest n first
 };
 
 }  // namespace rad
@@ -211,32 +227,32 @@ struct rad_htree {
     int near_dtype = RAD_F64;
     double tol = 0.0;
     int pivoting = RAD_ACA_PARTIAL;
-    std::vector<rad::NearDesc> near_h;
-    std::vector<rad::FarDesc> far_h;
-    std::vector<int> near_block;      // near desc -> canonical block
-    std::vector<int> far_block;       // far desc -> canonical block
+    std::vector<rad::Tile> tiles_h;
+    std::vector<rad::Group> groups_h;
+    std::vector<rad::Piece> near_pieces, far_pieces;   // per tile, in panel order
     rad::DevBuf near_pool, far_pool;
-    rad::DevBuf d_near, d_far, d_tiles, d_entries, d_trow, d_far_nz;
+    rad::DevBuf d_tiles, d_xidx, d_tidx, d_gwork, d_groups;
     int n_tiles = 0;
+    int n_gwork = 0;
     int sum_rank = 0;
-    int n_far_nz = 0;
     int max_rank_used = 0;
     int64_t n_dense_fallback = 0;
     int64_t near_entries = 0, far_entries = 0, aca_entries = 0;
+    int64_t far_u_entries = 0, far_v_entries = 0;
+    int64_t stored_near = 0, stored_far = 0;   // elements incl. padding
 
     rad::OpView view() const {
         rad::OpView v;
         v.n_tiles = n_tiles;
-        v.tiles = d_tiles.as<rad::TileDesc>();
-        v.entries = d_entries.as<int2>();
-        v.nd = d_near.as<rad::NearDesc>();
+        v.tiles = d_tiles.as<rad::Tile>();
         v.near_pool = near_pool.p;
-        v.fd = d_far.as<rad::FarDesc>();
         v.far_pool = far_pool.p;
+        v.xidx = d_xidx.as<int>();
+        v.tidx = d_tidx.as<int>();
+        v.n_gwork = n_gwork;
+        v.gwork = d_gwork.as<rad::GWork>();
+        v.groups = d_groups.as<rad::Group>();
         v.sum_rank = sum_rank;
-        v.trow_block = d_trow.as<int>();
-        v.n_far_nz = n_far_nz;
-        v.far_nz = d_far_nz.as<int>();
         return v;
     }
     bool op_is_f64() const { return near_dtype == RAD_F64; }
@@ -250,7 +266,6 @@ void build_geometry_from_facets(rad_htree* h, const double* c, const double* nrm
 void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s);
 // aca.cu
 void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s);
-void finalize_operator(rad_htree* h, cudaStream_t s);
 void load_dense_operator(rad_htree* h, const double* F_dev_rowmajor, cudaStream_t s);
 void export_block(const rad_htree* h, int64_t b, double* D, double* U, double* V);
 // hmatvec.cu

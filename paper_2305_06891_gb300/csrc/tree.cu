@@ -484,7 +484,7 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     auto add = [&](int2 pr, int adm) {
         const NodeShape& a = nodes[pr.x];
         const NodeShape& b = nodes[pr.y];
-        blocks.push_back(BlockH{pr.x, pr.y, a.begin, a.end, b.begin, b.end, adm, adm ? 0 : -1, -1});
+        blocks.push_back(BlockH{pr.x, pr.y, a.begin, a.end, b.begin, b.end, adm, adm ? 0 : -1, -1, 0});
     };
     for (auto pr : far_pairs) add(pr, 1);
     for (auto pr : near_pairs) add(pr, 0);
