@@ -110,6 +110,23 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# ---------------------------------------------------------------- ranks
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of `value` over all ranks of the default process group (replicas
+    are timed independently; the job takes as long as its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank solves FIELDS fields per step."""
+    return world * FIELDS * steps / (total_ms * 1e-3)
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, rank: int, world: int):
     import torch
@@ -166,12 +183,7 @@ def run_ours(args, rank: int, world: int):
     rad.rad_profile_enable(False)
     launches = rad.rad_launch_count() - launches0
     clk = clocks.stop()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    total_ms = max_over_ranks(sum(times), dev) if world > 1 else sum(times)
 
     # ---- one-off measurements (not in the timed region)
     extra = {}
@@ -387,7 +399,7 @@ def main():
     st = r["stats"]
     times = r["times"]
     ms_per_step = r["total_ms"] / args.steps
-    value = world * FIELDS * args.steps / (r["total_ms"] * 1e-3)
+    value = job_value(world, args.steps, r["total_ms"])
     nc = FIELDS + 1
     steps = args.steps
     prof = {k: (v[0], v[1]) for k, v in r["prof"].items()}

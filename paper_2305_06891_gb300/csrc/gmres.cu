@@ -76,14 +76,19 @@ mdot_kernel(const double* __restrict__ A, long long strideA, int L, const double
     }
 }
 
-// out[l * nc + c] (+)= sum_chunk partial[chunk][l][c]   (fixed order)
+// out[l * nc + c] (+)= sum_chunk partial[chunk][l][c]: one warp per output,
+// lanes take chunks lane, lane + 32, ..., then a fixed butterfly (the same
+// summation order on every call).
 __global__ void reduce_chunks_kernel(const double* __restrict__ partial, int chunks, int L, int nc, double* out,
                                      int accumulate) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (e >= L * nc) return;
     double s = 0.0;
-    for (int k = 0; k < chunks; ++k) s += partial[(long long)k * L * nc + e];
-    out[e] = accumulate ? out[e] + s : s;
+    for (int k = lane; k < chunks; k += 32) s += partial[(long long)k * L * nc + e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[e] = accumulate ? out[e] + s : s;
 }
 
 // W[i][c] -= sum_{l<L} V_l[i][c] h[l][c]   for active columns
@@ -227,7 +232,7 @@ struct ColReducer {
         dim3 grid(chunks, (nc + 31) / 32);
         { ProfScope ps_("gmres_dots", s); mdot_kernel<<<grid, 256, 0, s>>>(A, strideA, L, Bv, n, nc, partial); }
         RAD_CHECK_LAUNCH();
-        { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<grid_for((long long)L * nc), 256, 0, s>>>(partial, chunks, L, nc, out,
+        { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<grid_for((long long)L * nc, 8), 256, 0, s>>>(partial, chunks, L, nc, out,
                                                                           accumulate ? 1 : 0); }
         RAD_CHECK_LAUNCH();
     }
@@ -317,7 +322,7 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
                 { ProfScope ps_("gmres_cgs_update", s); cgs_update_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, j + 1, hbuf, active, W, n, nc); }
                 RAD_CHECK_LAUNCH();
                 if (pass == 1) {
-                    { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<grid_for((long long)(j + 1) * nc), 256, 0, s>>>(ycoef, 1, j + 1, nc,
+                    { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<grid_for((long long)(j + 1) * nc, 8), 256, 0, s>>>(ycoef, 1, j + 1, nc,
                                                                                             hcol, 1); }
                     RAD_CHECK_LAUNCH();
                 }

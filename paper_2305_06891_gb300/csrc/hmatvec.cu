@@ -80,15 +80,17 @@ __global__ void __launch_bounds__(256) far_vt_single(OpView op, const AT* __rest
         if (q0 + q < quads && jg < G) {
             const FS* P = static_cast<const FS*>(op.far_pool) + gr.voff + 4 * (q0 + q);
             int j = jg;
-            for (; j + G < gr.n; j += 2 * G) {
-                AT v0[4], v1[4];
+            for (; j + 3 * G < gr.n; j += 4 * G) {
+                AT v0[4], v1[4], v2[4], v3[4];
                 Vec4<FS, AT>::load(P + j * ld, v0);
                 Vec4<FS, AT>::load(P + (j + G) * ld, v1);
-                const AT x0 = xv[j], x1 = xv[j + G];
+                Vec4<FS, AT>::load(P + (j + 2 * G) * ld, v2);
+                Vec4<FS, AT>::load(P + (j + 3 * G) * ld, v3);
+                const AT x0 = xv[j], x1 = xv[j + G], x2 = xv[j + 2 * G], x3 = xv[j + 3 * G];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) acc[r] += v0[r] * x0 + v1[r] * x1;
+                for (int r = 0; r < 4; ++r) acc[r] += (v0[r] * x0 + v1[r] * x1) + (v2[r] * x2 + v3[r] * x3);
             }
-            if (j < gr.n) {
+            for (; j < gr.n; j += G) {
                 AT v0[4];
                 Vec4<FS, AT>::load(P + j * ld, v0);
                 const AT x0 = xv[j];
