@@ -45,6 +45,35 @@ constexpr int kAcaNT = 256;
 constexpr int kSamples = kAcaNT;   // one sampled residual entry per thread
 constexpr int kMaxChecks = 4;
 
+// Running sum of the stopping rule's ||S_k||^2.  With FP32 arithmetic it is
+// kept as an unevaluated hi + lo pair updated by the error-free two-sum, so
+// the accumulation keeps about twice FP32's precision without touching the
+// narrow FP64 pipe; with FP64 arithmetic it is a plain double.
+template <class CT> struct RunSum;
+template <> struct RunSum<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ double value() const { return v; }
+};
+template <> struct RunSum<float> {
+    float h = 0.0f, l = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = __fadd_rn(h, x);
+        const float bp = __fsub_rn(s, h);
+        const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+        const float t = __fadd_rn(l, e);
+        h = __fadd_rn(s, t);
+        l = __fsub_rn(t, __fsub_rn(h, s));
+    }
+    __device__ __forceinline__ float value() const { return h; }
+};
+// Zero-row threshold floor (1e-300 in FP64; in FP32 only an exact zero
+// is below it).
+template <class CT> struct Tiny;
+template <> struct Tiny<double> { static constexpr double v = 1e-300; };
+template <> struct Tiny<float> { static constexpr float v = 0.0f; };
+
+
 // lowest index i < m with used[i] == 0, or -1; all threads receive it
 __device__ int lowest_unused(const unsigned char* used, int m, int* sm) {
     int best = 0x7fffffff;
@@ -68,19 +97,19 @@ __device__ int lowest_unused(const unsigned char* used, int m, int* sm) {
 // For l < k: out[l] = sum_j a_j * B[l*ld + j] over this thread's j; plus
 // out[k] = sum_j a_j^2.  Results (FP64) land in red[0..k] for every thread.
 template <class CT>
-__device__ void cross_dots(const CT* a, const CT* B, int len, long long ld, int k, double (*part)[kMaxRank + 1],
-                           double* red) {
+__device__ void cross_dots(const CT* a, const CT* B, int len, long long ld, int k, CT (*part)[kMaxRank + 1],
+                           CT* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int l = 0; l <= k; ++l) {
         CT s = 0;
         const CT* bl = (l < k) ? B + (long long)l * ld : a;
         for (int j = threadIdx.x; j < len; j += kAcaNT) s += a[j] * bl[j];
         s = warp_sum(s);
-        if (lane == 0) part[warp][l] = (double)s;
+        if (lane == 0) part[warp][l] = s;
     }
     __syncthreads();
     if ((int)threadIdx.x <= k) {
-        double s = 0.0;
+        CT s = 0;
         for (int w = 0; w < kAcaNT / 32; ++w) s += part[w][threadIdx.x];
         red[threadIdx.x] = s;
     }
@@ -88,19 +117,18 @@ __device__ void cross_dots(const CT* a, const CT* B, int len, long long ld, int 
 }
 
 // Shared memory of one ACA CTA: the CTA-wide path and the per-warp path.
-// Per-element arithmetic runs in CT; only per-step scalars (cross terms,
-// the running ||S_k||^2) are FP64.
+// All arithmetic runs in CT; the running ||S_k||^2 is a RunSum<CT>.
 template <class CT>
 struct AcaSmem {
     CT s_row[kMaxRank];
-    double part[kAcaNT / 32][kMaxRank + 1];
-    double s_cv[kMaxRank + 1];
-    double s_cu[kMaxRank + 1];
+    CT part[kAcaNT / 32][kMaxRank + 1];
+    CT s_cv[kMaxRank + 1];
+    CT s_cu[kMaxRank + 1];
     ArgMaxT<CT> am_sm[kAcaNT / 32 + 1];
     int i_sm[kAcaNT / 32 + 1];
     CT red_sm[kAcaNT / 32 + 1];
     CT w_a[kAcaNT / 32][kMaxRank];       // per warp: pivot row/column of U, V
-    double w_c[kAcaNT / 32][kMaxRank];   // per warp: (v_k . v_l)
+    CT w_c[kAcaNT / 32][kMaxRank];       // per warp: (v_k . v_l)
 };
 
 // One admissible block on a whole CTA (blocks with more than 1024 rows or
@@ -110,9 +138,9 @@ __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upoo
                               unsigned char* used_pool, int* __restrict__ rank_out,
                               long long* __restrict__ evals_out, double tol, AcaSmem<CT>& sm) {
     CT* s_row = sm.s_row;
-    double (*part)[kMaxRank + 1] = sm.part;
-    double* s_cv = sm.s_cv;
-    double* s_cu = sm.s_cu;
+    CT (*part)[kMaxRank + 1] = sm.part;
+    CT* s_cv = sm.s_cv;
+    CT* s_cu = sm.s_cu;
     ArgMaxT<CT>* am_sm = sm.am_sm;
     int* i_sm = sm.i_sm;
     CT* red_sm = sm.red_sm;
@@ -122,7 +150,9 @@ __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upoo
     unsigned char* used = used_pool + jb.offUsed;
 
     int i = 0, k = 0, status = 0, checks = 0;  // status: 1 converged, 2 rank cap
-    double norm2 = 0.0, scale = 0.0;
+    RunSum<CT> norm2;
+    CT scale = 0;
+    const CT tolsq = (CT)(tol * tol);
     long long evals = 0;
     for (int guard = 0; guard <= m + kmax + kMaxChecks + 2; ++guard) {
         if (k >= kmax) { status = 2; break; }
@@ -141,13 +171,13 @@ __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upoo
         evals += n;
         if (threadIdx.x == 0) used[i] = 1;
         __syncthreads();
-        if (!((double)best.v > fmax(1e-300, 1e-14 * scale))) {
+        if (!(best.v > fmax(Tiny<CT>::v, CT(1e-14) * scale))) {
             const int nxt = lowest_unused(used, m, i_sm);
             if (nxt < 0) { status = 1; break; }
             i = nxt;
             continue;
         }
-        scale = fmax(scale, (double)best.v);
+        scale = fmax(scale, best.v);
         const int jp = best.i;
         const CT piv = vk[jp];
         __syncthreads();
@@ -168,12 +198,13 @@ __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upoo
         evals += m;
         cross_dots<CT>(uk, U, m, m, k, part, s_cu);
         bu = block_argmax<kAcaNT>(bu, am_sm);
-        double cross = 0.0;
+        CT cross = 0;
         for (int l = 0; l < k; ++l) cross += s_cu[l] * s_cv[l];
-        const double uu = s_cu[k], vv = s_cv[k];
-        norm2 = norm2 + 2.0 * cross + uu * vv;
+        const CT uu = s_cu[k], vv = s_cv[k];
+        norm2.add(CT(2) * cross + uu * vv);
         ++k;
-        if (sqrt(uu) * sqrt(vv) <= tol * sqrt(fmax(norm2, 0.0))) {
+        // |u_k| |v_k| <= tol ||S_k||_F, compared squared
+        if (uu * vv <= tolsq * fmax(norm2.value(), CT(0))) {
             if (checks >= kMaxChecks) { status = 1; break; }
             // verify the candidate stop on sampled residual entries
             const int sidx = threadIdx.x;
@@ -182,11 +213,11 @@ __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upoo
                                  (unsigned long long)n);
             CT x = Entry<CT>::eval(g, jb.r0 + si, jb.c0 + sj);
             for (int l = 0; l < k; ++l) x -= U[(long long)l * m + si] * V[(long long)l * n + sj];
-            const double r2 = (double)block_sum<kAcaNT, CT>(x * x, red_sm);
+            const CT r2 = block_sum<kAcaNT, CT>(x * x, red_sm);
             const ArgMaxT<CT> bs = block_argmax<kAcaNT>(ArgMaxT<CT>{fabs(x), sidx}, am_sm);
             ++checks;
             evals += kSamples;
-            if (((double)m * (double)n / kSamples) * r2 <= tol * tol * fmax(norm2, 0.0)) { status = 1; break; }
+            if ((CT)m * (CT)n / CT(kSamples) * r2 <= tolsq * fmax(norm2.value(), CT(0))) { status = 1; break; }
             int wi = (int)(((long long)bs.i * m) / kSamples);
             if (used[wi]) {
                 wi = lowest_unused(used, m, i_sm);
@@ -209,7 +240,7 @@ __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upoo
 // with the four shuffle reductions interleaved.
 template <class CT>
 __device__ __forceinline__ void warp_dots4(const CT* a, const CT* B, int len, long long ld, int l0, int k,
-                                           double p[4]) {
+                                           CT p[4]) {
     const int lane = threadIdx.x & 31;
     const int nq = min(4, k - l0);
     CT t[4] = {CT(0), CT(0), CT(0), CT(0)};
@@ -224,7 +255,7 @@ __device__ __forceinline__ void warp_dots4(const CT* a, const CT* B, int len, lo
 #pragma unroll
         for (int q = 0; q < 4; ++q) t[q] += __shfl_xor_sync(0xffffffffu, t[q], o);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) p[q] = (double)t[q];
+    for (int q = 0; q < 4; ++q) p[q] = t[q];
 }
 
 // One admissible block (m <= 1024 rows) on a single warp: no block
@@ -234,14 +265,16 @@ __device__ __forceinline__ void warp_dots4(const CT* a, const CT* B, int len, lo
 template <class CT>
 __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upool, CT* Vpool,
                                int* __restrict__ rank_out, long long* __restrict__ evals_out, double tol,
-                               CT* s_a, double* s_c) {
+                               CT* s_a, CT* s_c) {
     const int lane = threadIdx.x & 31;
     const int m = jb.m, n = jb.n, kmax = jb.kmax;
     CT* U = Upool + jb.offU;
     CT* V = Vpool + jb.offV;
     unsigned used = 0u;
     int i = 0, k = 0, status = 0, checks = 0;
-    double norm2 = 0.0, scale = 0.0;
+    RunSum<CT> norm2;
+    CT scale = 0;
+    const CT tolsq = (CT)(tol * tol);
     long long evals = 0;
     for (int guard = 0; guard <= m + kmax + kMaxChecks + 2; ++guard) {
         if (k >= kmax) { status = 2; break; }
@@ -258,7 +291,7 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
         best = warp_argmax(best);
         evals += n;
         if ((i & 31) == lane) used |= 1u << (i >> 5);
-        if (!((double)best.v > fmax(1e-300, 1e-14 * scale))) {
+        if (!(best.v > fmax(Tiny<CT>::v, CT(1e-14) * scale))) {
             int cand = 0x7fffffff;
             for (int t = 0; t < 32 && lane + 32 * t < m; ++t)
                 if (!((used >> t) & 1u)) { cand = lane + 32 * t; break; }
@@ -268,7 +301,7 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
             __syncwarp();
             continue;
         }
-        scale = fmax(scale, (double)best.v);
+        scale = fmax(scale, best.v);
         const int jp = best.i;
         __syncwarp();
         const CT piv = vk[jp];
@@ -279,9 +312,9 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
             vk[j] = v;
             vvp += v * v;
         }
-        const double vv = (double)warp_sum(vvp);
+        const CT vv = warp_sum(vvp);
         for (int l0 = 0; l0 < k; l0 += 4) {
-            double p[4];
+            CT p[4];
             warp_dots4<CT>(vk, V, n, n, l0, k, p);
             if (lane == 0)
                 for (int q = 0; q < 4 && l0 + q < k; ++q) s_c[l0 + q] = p[q];
@@ -299,18 +332,19 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
             uup += u * u;
             if (!((used >> (r >> 5)) & 1u)) bu = am_better(bu, ArgMaxT<CT>{fabs(u), r});
         }
-        const double uu = (double)warp_sum(uup);
-        double cross = 0.0;
+        const CT uu = warp_sum(uup);
+        CT cross = 0;
         for (int l0 = 0; l0 < k; l0 += 4) {
-            double p[4];
+            CT p[4];
             warp_dots4<CT>(uk, U, m, m, l0, k, p);
             for (int q = 0; q < 4 && l0 + q < k; ++q) cross += p[q] * s_c[l0 + q];
         }
         bu = warp_argmax(bu);
         evals += m;
-        norm2 = norm2 + 2.0 * cross + uu * vv;
+        norm2.add(CT(2) * cross + uu * vv);
         ++k;
-        if (sqrt(uu) * sqrt(vv) <= tol * sqrt(fmax(norm2, 0.0))) {
+        // |u_k| |v_k| <= tol ||S_k||_F, compared squared
+        if (uu * vv <= tolsq * fmax(norm2.value(), CT(0))) {
             if (checks >= kMaxChecks) { status = 1; break; }
             CT r2p = 0;
             ArgMaxT<CT> bs{CT(-1), 0x7fffffff};
@@ -324,11 +358,11 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
                 r2p += x * x;
                 bs = am_better(bs, ArgMaxT<CT>{fabs(x), sidx});
             }
-            const double r2 = (double)warp_sum(r2p);
+            const CT r2 = warp_sum(r2p);
             bs = warp_argmax(bs);
             ++checks;
             evals += kSamples;
-            if (((double)m * (double)n / kSamples) * r2 <= tol * tol * fmax(norm2, 0.0)) { status = 1; break; }
+            if ((CT)m * (CT)n / CT(kSamples) * r2 <= tolsq * fmax(norm2.value(), CT(0))) { status = 1; break; }
             int wi = (int)(((long long)bs.i * m) / kSamples);
             const unsigned wused = __shfl_sync(0xffffffffu, (used >> (wi >> 5)) & 1u, wi & 31);
             if (wused) {

@@ -20,6 +20,8 @@
 //   kReflect: w = xin - (1 - eps) o (F x)
 //   kResid:   r = b - (xin - (1 - eps) o (F x))
 
+#include <mutex>
+
 #include "rad_device.cuh"
 
 namespace rad {
@@ -355,11 +357,10 @@ void launch_far_vt(const rad_htree* h, const AT* X, int ldx, AT* T, int ldt, int
     const OpView op = h->view();
     const size_t bytes = GemmLayout<FS, AT>::bytes > GemmLayout<float, AT>::bytes ? GemmLayout<FS, AT>::bytes
                                                                                   : GemmLayout<float, AT>::bytes;
-    static bool configured = false;
-    if (!configured) {
+    static std::once_flag configured;
+    std::call_once(configured, [&] {
         RAD_CUDA(cudaFuncSetAttribute(far_vt_multi<FS, AT, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-        configured = true;
-    }
+    });
     { ProfScope ps_("hmm_far_vt", s); far_vt_multi<FS, AT, RN><<<op.n_gwork, 256, bytes, s>>>(op, X, ldx, T, ldt, nc); }
     RAD_CHECK_LAUNCH();
 }
@@ -369,11 +370,10 @@ void launch_rows(const rad_htree* h, const AT* X, int ldx, const AT* T, int ldt,
     const OpView op = h->view();
     const size_t bytes = GemmLayout<NS, AT>::bytes > GemmLayout<FS, AT>::bytes ? GemmLayout<NS, AT>::bytes
                                                                                 : GemmLayout<FS, AT>::bytes;
-    static bool configured = false;
-    if (!configured) {
+    static std::once_flag configured;
+    std::call_once(configured, [&] {
         RAD_CUDA(cudaFuncSetAttribute(rows_multi<NS, FS, AT, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-        configured = true;
-    }
+    });
     { ProfScope ps_("hmm_rows", s); rows_multi<NS, FS, AT, RN><<<op.n_tiles, 256, bytes, s>>>(op, X, ldx, T, ldt, Y, ldy, nc, epi); }
     RAD_CHECK_LAUNCH();
 }
