@@ -45,9 +45,40 @@ import cavities as cv  # noqa: E402
 
 METRIC = "flux solves/s"
 UNIT = "solves/s"
-FIELDS = 64
-LEAF, ETA, ACA_TOL, SOLVE_TOL, RESTART = 64, 1.0, 1e-5, 1e-7, 30
 SIGMA = 5.670374419e-8
+RESTART = 30
+
+# Workloads.  "cylinder" (the default line): closed cylinder, 19,936 facets,
+# 64 fields, FP32 storage.  "sphere-mixed": level-6 icosphere, 81,920 facets,
+# one field, BF16 low-rank factors + FP32 dense blocks, refinement with an
+# FP32 accurate operator and FP64 residuals to 1e-8.
+WORKLOADS = {
+    "cylinder": dict(make=lambda: cv.config2(m=64), fields=64, leaf=64, eta=1.0, aca_tol=1e-5, solve_tol=1e-7,
+                     factor="f32", near="f32", accurate=None, refine=False,
+                     name="closed_cylinder_19936_64fields_fp32"),
+    "sphere-mixed": dict(make=cv.config3, fields=1, leaf=64, eta=1.0, aca_tol=1e-7, solve_tol=1e-8,
+                         factor="bf16", near="f32", accurate="f32", refine=True,
+                         name="icosphere6_81920_1field_bf16_refined"),
+}
+W = WORKLOADS["cylinder"]
+FIELDS = W["fields"]
+LEAF, ETA, ACA_TOL, SOLVE_TOL = W["leaf"], W["eta"], W["aca_tol"], W["solve_tol"]
+
+
+def select_workload(name: str):
+    global W, FIELDS, LEAF, ETA, ACA_TOL, SOLVE_TOL
+    W = WORKLOADS[name]
+    FIELDS = W["fields"]
+    LEAF, ETA, ACA_TOL, SOLVE_TOL = W["leaf"], W["eta"], W["aca_tol"], W["solve_tol"]
+
+
+def compress(rad, h):
+    rad.rad_compress_aca(h, ACA_TOL, 64, "partial", W["factor"], W["near"], accurate_dtype=W["accurate"])
+
+
+def solve(rad, h, eps, T, q=None):
+    return rad.rad_solve_flux(h, eps, T, SIGMA, tol=SOLVE_TOL, restart=RESTART, max_iter=600, q=q,
+                              refine=W["refine"], inner_tol=1e-4)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -134,7 +165,7 @@ def run_ours(args, rank: int, world: int):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    cav = cv.config2(m=FIELDS)
+    cav = W["make"]()
     n = cav.n
     verts_h, eps_h = cav.verts, cav.eps
     T_h = np.asfortranarray(cav.T)
@@ -145,10 +176,10 @@ def run_ours(args, rank: int, world: int):
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step(storage="f32", verts=verts_d, eps=eps_d, T=T_d, q=q_d):
+    def step(verts=verts_d, eps=eps_d, T=T_d, q=q_d):
         h = rad.rad_build_htree(verts, LEAF, ETA)
-        rad.rad_compress_aca(h, ACA_TOL, 64, "partial", storage, storage)
-        q, info = rad.rad_solve_flux(h, eps, T, SIGMA, tol=SOLVE_TOL, restart=RESTART, max_iter=600, q=q)
+        compress(rad, h)
+        q, info = solve(rad, h, eps, T, q=q)
         return h, info
 
     for _ in range(args.warmup):
@@ -198,7 +229,7 @@ def measure_extras(args, rad, torch, dev, cav, verts_d, eps_d, T_d, flush, strea
     n = cav.n
     # single-RHS block matvec on the bench operator (HBM bound)
     h = rad.rad_build_htree(verts_d, LEAF, ETA)
-    rad.rad_compress_aca(h, ACA_TOL, 64, "partial", "f32", "f32")
+    compress(rad, h)
     st = rad.rad_htree_get_stats(h)
     x = torch.as_tensor(SIGMA * cav.T[:, 0] ** 4, device=dev, dtype=torch.float32)
     y = torch.empty(n, dtype=torch.float32, device=dev)
@@ -218,7 +249,7 @@ def measure_extras(args, rad, torch, dev, cav, verts_d, eps_d, T_d, flush, strea
         ts.append(e0.elapsed_time(e1))
     prof = rad.rad_profile_read()
     rad.rad_profile_enable(False)
-    op_bytes = st["bytes_near"] + st["bytes_far"]
+    op_bytes = st["bytes_near"] + st["bytes_far"]   # the operator the product streams
     vec_bytes = 4 * (2 * n + 2 * st["sum_rank"])
     kern_ms = (prof.get("hmv_rows", (1, 0.0))[1] + prof.get("hmv_far_vt", (1, 0.0))[1]) / reps
     hbm, _, src = load_peaks()
@@ -258,8 +289,8 @@ def measure_extras(args, rad, torch, dev, cav, verts_d, eps_d, T_d, flush, strea
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = rad.rad_build_htree(verts_h, LEAF, ETA)
-        rad.rad_compress_aca(h, ACA_TOL, 64, "partial", "f32", "f32")
-        rad.rad_solve_flux(h, cav.eps, T_h, SIGMA, tol=SOLVE_TOL, restart=RESTART, max_iter=600, q=q_h)
+        compress(rad, h)
+        solve(rad, h, cav.eps, T_h, q=q_h)
         t1 = time.perf_counter()
         h.free()
         if it:
@@ -305,6 +336,11 @@ def roofline(prof: dict, st: dict, steps: int, clocks: dict, nc: int):
 
 # ---------------------------------------------------------------- oracle arm
 def oracle_step(cav, rows_sample=1024, lu_n=3072, seed=0):
+    """(see below)"""
+    return _oracle_step(cav, rows_sample, lu_n, seed)
+
+
+def _oracle_step(cav, rows_sample, lu_n, seed):
     """Time the FP64 oracle on a bounded sample and extrapolate to the full
     cavity.  Returns (extrapolated seconds per full flux solve of 64 fields,
     description)."""
@@ -338,7 +374,7 @@ def oracle_step(cav, rows_sample=1024, lu_n=3072, seed=0):
 
 
 def run_reference(args):
-    cav = cv.config2(m=FIELDS)
+    cav = W["make"]()
     cores = os.cpu_count()
     for _ in range(args.warmup):
         oracle_step(cav)
@@ -361,11 +397,14 @@ def run_reference(args):
 
 
 def config_dict():
-    return {"workload": "closed_cylinder_19936_64fields_fp32", "n_facets": 19936, "fields": FIELDS,
-            "leaf_size": LEAF, "eta_adm": ETA, "aca_tol": ACA_TOL, "aca_pivoting": "partial+sampled check",
-            "solve_tol": SOLVE_TOL, "gmres_restart": RESTART, "storage": "f32 near + f32 factors",
-            "accumulation": "f32 (operator), f64 (Krylov, inner products, residuals)",
-            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+    d = {"workload": W["name"], "fields": FIELDS, "leaf_size": LEAF, "eta_adm": ETA, "aca_tol": ACA_TOL,
+         "aca_pivoting": "partial+sampled check", "solve_tol": SOLVE_TOL, "gmres_restart": RESTART,
+         "storage": f"{W['near']} near + {W['factor']} factors",
+         "accumulation": "f32 (operator), f64 (Krylov, inner products, residuals)",
+         "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+    if W["refine"]:
+        d["refinement"] = f"{W['accurate']} accurate operator, f64 accumulation, inner GMRES tol 1e-4"
+    return d
 
 
 def main():
@@ -376,7 +415,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--workload", default="cylinder", choices=sorted(WORKLOADS))
     args = ap.parse_args()
+    select_workload(args.workload)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
 

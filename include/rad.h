@@ -73,22 +73,36 @@ typedef struct {
  * or RAD_BF16) is the storage type of the U, V factors and near_dtype
  * (RAD_F64 or RAD_F32) that of the dense blocks.  near_dtype = RAD_F64
  * requires factor_dtype = RAD_F64 (the FP64 path); the other combinations
- * compute in FP32 with FP32 accumulation. */
+ * compute in FP32 with FP32 accumulation.
+ * accurate_dtype = RAD_F32 with factor_dtype = RAD_BF16 also keeps the
+ * factors in FP32: the "accurate operator" that mixed-precision iterative
+ * refinement (rad_solve_params.refine) uses for its residuals; -1 keeps no
+ * second copy. */
 typedef struct {
     double  tol;
     int32_t max_rank;
     int32_t pivoting;
     int32_t factor_dtype;
     int32_t near_dtype;
+    int32_t accurate_dtype;
+    int32_t reserved;
 } rad_aca_params;
 
 /* GMRES on C y = b, C = I - diag(1 - eps) F (Eq. 11).  Stops when every
  * column's relative residual ||b - C y|| / ||b|| <= tol; restart = Krylov
- * dimension per cycle (1..64); max_iter = total Arnoldi steps per column. */
+ * dimension per cycle (1..64); max_iter = total Arnoldi steps per column.
+ * refine = 1 (needs a handle compressed with accurate_dtype = RAD_F32):
+ * mixed-precision iterative refinement - the residual r = b - C y is
+ * computed with the accurate operator (FP32 factors) accumulated in FP64,
+ * the correction solves C d = r by GMRES on the fast operator (BF16 factors)
+ * to inner_tol, y += d, until the accurate relative residual <= tol. */
 typedef struct {
     double  tol;
     int32_t restart;
     int32_t max_iter;
+    int32_t refine;
+    int32_t max_refine;          /* outer refinement steps (refine = 1)       */
+    double  inner_tol;           /* relative tolerance of each correction     */
 } rad_solve_params;
 
 typedef struct {
@@ -97,7 +111,10 @@ typedef struct {
     int32_t restarts;            /* restart cycles                             */
     int32_t matvecs;             /* block matrix products applied             */
     double  max_rel_residual;    /* max over columns of ||b - C y|| / ||b||,
-                                    recomputed with the stored operator       */
+                                    recomputed with the stored operator (the
+                                    accurate one when refining)               */
+    int32_t refinements;         /* outer refinement steps taken              */
+    int32_t reserved;
 } rad_solve_info;
 
 typedef struct {
@@ -122,6 +139,7 @@ typedef struct {
     int64_t far_u_entries;       /* sum k m over low-rank blocks (U factors)   */
     int64_t far_v_entries;       /* sum k n over low-rank blocks (V factors)   */
     int64_t n_tiles;             /* row tiles of the product (<= 64 rows)      */
+    int64_t bytes_accurate;      /* FP32 factor copy kept for refinement (0 if none) */
 } rad_htree_stats;
 
 /* -------------------------------------------------------------------------

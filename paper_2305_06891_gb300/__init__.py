@@ -43,16 +43,19 @@ class _TreeParams(C.Structure):
 
 class _AcaParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_rank", C.c_int32), ("pivoting", C.c_int32),
-                ("factor_dtype", C.c_int32), ("near_dtype", C.c_int32)]
+                ("factor_dtype", C.c_int32), ("near_dtype", C.c_int32), ("accurate_dtype", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class _SolveParams(C.Structure):
-    _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("max_iter", C.c_int32)]
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("max_iter", C.c_int32), ("refine", C.c_int32),
+                ("max_refine", C.c_int32), ("inner_tol", C.c_double)]
 
 
 class _SolveInfo(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("restarts", C.c_int32),
-                ("matvecs", C.c_int32), ("max_rel_residual", C.c_double)]
+                ("matvecs", C.c_int32), ("max_rel_residual", C.c_double), ("refinements", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class _Stats(C.Structure):
@@ -62,7 +65,8 @@ class _Stats(C.Structure):
                 ("near_dtype", C.c_int32), ("max_rank_used", C.c_int32), ("n_dense_fallback", C.c_int64),
                 ("near_entries", C.c_int64), ("far_entries", C.c_int64), ("sum_rank", C.c_int64),
                 ("aca_entries", C.c_int64), ("bytes_near", C.c_int64), ("bytes_far", C.c_int64),
-                ("far_u_entries", C.c_int64), ("far_v_entries", C.c_int64), ("n_tiles", C.c_int64)]
+                ("far_u_entries", C.c_int64), ("far_v_entries", C.c_int64), ("n_tiles", C.c_int64),
+                ("bytes_accurate", C.c_int64)]
 
 
 def _load():
@@ -249,8 +253,10 @@ def rad_htree_from_dense(F, stream=None) -> HTree:
 
 
 def rad_compress_aca(h: HTree, tol: float, max_rank: int = 64, pivoting: str = "partial",
-                     factor_dtype: str = "f32", near_dtype: str = "f32", stream=None) -> None:
-    p = _AcaParams(float(tol), int(max_rank), _PIV[pivoting], _DT[factor_dtype], _DT[near_dtype])
+                     factor_dtype: str = "f32", near_dtype: str = "f32", accurate_dtype: str | None = None,
+                     stream=None) -> None:
+    acc = -1 if accurate_dtype is None else _DT[accurate_dtype]
+    p = _AcaParams(float(tol), int(max_rank), _PIV[pivoting], _DT[factor_dtype], _DT[near_dtype], acc, 0)
     _check(_lib.rad_compress_aca(h.ptr, C.byref(p), _stream(stream)))
 
 
@@ -281,7 +287,8 @@ def rad_hmatvec(h: HTree, x, y=None, stream=None):
 
 
 def rad_solve_flux(h: HTree, eps, T, sigma: float = SIGMA_SB, tol: float = 1e-10, restart: int = 30,
-                   max_iter: int = 1000, q=None, stream=None, raise_on_notconv: bool = False):
+                   max_iter: int = 1000, q=None, stream=None, raise_on_notconv: bool = False,
+                   refine: bool = False, inner_tol: float = 1e-4, max_refine: int = 10):
     """A7-A8: flux q (N, m) for temperature fields T (N,) or (N, m).
 
     Returns ``(q, info)``; ``info`` is a dict with status, iters, restarts,
@@ -296,7 +303,7 @@ def rad_solve_flux(h: HTree, eps, T, sigma: float = SIGMA_SB, tol: float = 1e-10
         else:
             q = np.empty((n, m), dtype=np.float64, order="F")
     ldq = n
-    p = _SolveParams(float(tol), int(restart), int(max_iter))
+    p = _SolveParams(float(tol), int(restart), int(max_iter), 1 if refine else 0, int(max_refine), float(inner_tol))
     info = _SolveInfo()
     rc = _lib.rad_solve_flux(h.ptr, _ptr(e), _ptr(Tc), ldT, m, float(sigma), C.byref(p), _ptr(q), ldq,
                              C.byref(info), _stream(stream, e, Tc, q))
@@ -326,7 +333,8 @@ def rad_hmatvec_noalloc(h: HTree, x, y, stream=None):
 
 
 def rad_solve_reflection(h: HTree, eps, B, tol: float = 1e-10, restart: int = 30, max_iter: int = 1000,
-                         Y=None, stream=None, raise_on_notconv: bool = False):
+                         Y=None, stream=None, raise_on_notconv: bool = False, refine: bool = False,
+                         inner_tol: float = 1e-4, max_refine: int = 10):
     """A7: Y solving C Y = B (Eq. 11) for B (N,) or (N, nrhs).  Returns (Y, info)."""
     Bc, n, nrhs, ldB = _colmajor(B, np.float64)
     e = _f64_rowmajor(eps)
@@ -336,7 +344,7 @@ def rad_solve_reflection(h: HTree, eps, B, tol: float = 1e-10, restart: int = 30
             Y = t.empty((nrhs, n), dtype=t.float64, device=Bc.device).t()
         else:
             Y = np.empty((n, nrhs), dtype=np.float64, order="F")
-    p = _SolveParams(float(tol), int(restart), int(max_iter))
+    p = _SolveParams(float(tol), int(restart), int(max_iter), 1 if refine else 0, int(max_refine), float(inner_tol))
     info = _SolveInfo()
     rc = _lib.rad_solve_reflection(h.ptr, _ptr(e), _ptr(Bc), ldB, nrhs, C.byref(p), _ptr(Y), n, C.byref(info),
                                    _stream(stream, e, Bc, Y))

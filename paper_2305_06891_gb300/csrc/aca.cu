@@ -682,18 +682,19 @@ static void launch_dense_fill(rad_htree* h, const std::vector<DenseWork>& work, 
 
 template <class CT, class S>
 static void launch_factor_fill(rad_htree* h, const std::vector<UWork>& uw, const std::vector<VWork>& vw,
-                               const CT* Us, const CT* Vs, cudaStream_t s) {
+                               const CT* Us, const CT* Vs, cudaStream_t s, void* pool = nullptr) {
+    S* dst = static_cast<S*>(pool ? pool : h->far_pool.p);
     Scratch ws(s);
     if (!uw.empty()) {
         UWork* d = ws.get_n<UWork>(uw.size());
         h2d(d, uw, s);
-        { ProfScope ps_("aca_pack", s); u_fill_kernel<CT, S><<<(unsigned)uw.size(), 256, 0, s>>>(h->d_tiles.as<Tile>(), d, Us, h->far_pool.as<S>()); }
+        { ProfScope ps_("aca_pack", s); u_fill_kernel<CT, S><<<(unsigned)uw.size(), 256, 0, s>>>(h->d_tiles.as<Tile>(), d, Us, dst); }
         RAD_CHECK_LAUNCH();
     }
     if (!vw.empty()) {
         VWork* d = ws.get_n<VWork>(vw.size());
         h2d(d, vw, s);
-        { ProfScope ps_("aca_pack", s); v_fill_kernel<CT, S><<<(unsigned)vw.size(), 256, 0, s>>>(h->d_groups.as<Group>(), d, Vs, h->far_pool.as<S>()); }
+        { ProfScope ps_("aca_pack", s); v_fill_kernel<CT, S><<<(unsigned)vw.size(), 256, 0, s>>>(h->d_groups.as<Group>(), d, Vs, dst); }
         RAD_CHECK_LAUNCH();
     }
 }
@@ -832,6 +833,18 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     if (h->factor_dtype == RAD_F64) launch_factor_fill<CT, double>(h, uwork, vwork, Us, Vs, s);
     else if (h->factor_dtype == RAD_F32) launch_factor_fill<CT, float>(h, uwork, vwork, Us, Vs, s);
     else launch_factor_fill<CT, __nv_bfloat16>(h, uwork, vwork, Us, Vs, s);
+    // accurate operator for mixed-precision refinement: FP32 factors
+    h->far_pool_acc.release();
+    h->has_accurate = false;
+    if (p->accurate_dtype == RAD_F32) {
+        if (h->factor_dtype == RAD_BF16) {
+            h->far_pool_acc.alloc((size_t)std::max<long long>(foff, 16) * sizeof(float));
+            RAD_CUDA(cudaMemsetAsync(h->far_pool_acc.p, 0, h->far_pool_acc.bytes, s));
+            launch_factor_fill<CT, float>(h, uwork, vwork, Us, Vs, s, h->far_pool_acc.p);
+        }
+        h->has_accurate = true;
+    }
+    if (h->factor_dtype == RAD_F64) h->has_accurate = true;
     h->n_dense_fallback = fallback;
     h->max_rank_used = maxk;
     h->near_entries = near_e;
@@ -853,6 +866,8 @@ void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
                 RAD_EINVAL, "bad factor_dtype");
     RAD_REQUIRE((p->near_dtype == RAD_F64) == (p->factor_dtype == RAD_F64), RAD_EINVAL,
                 "near_dtype F64 requires factor_dtype F64 and vice versa");
+    RAD_REQUIRE(p->accurate_dtype == -1 || p->accurate_dtype == RAD_F32, RAD_EINVAL,
+                "accurate_dtype must be -1 or RAD_F32");
     RAD_REQUIRE(!h->from_dense, RAD_EINVAL, "a dense-wrapped handle cannot be recompressed");
     h->compressed = false;
     h->factor_dtype = p->factor_dtype;
@@ -898,6 +913,7 @@ void load_dense_operator(rad_htree* h, const double* F_dev, cudaStream_t s) {
     RAD_CHECK_LAUNCH();
     h->near_entries = (long long)n * n;
     h->far_entries = h->far_u_entries = h->far_v_entries = 0;
+    h->has_accurate = true;
     RAD_CUDA(cudaStreamSynchronize(s));
     h->compressed = true;
 }

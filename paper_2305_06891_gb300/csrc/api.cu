@@ -336,6 +336,10 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
         RAD_REQUIRE(p->max_iter >= 1, RAD_EINVAL, "max_iter must be >= 1");
         RAD_REQUIRE(p->tol > 0.0 && std::isfinite(p->tol), RAD_EINVAL, "tol must be > 0");
         RAD_REQUIRE(std::isfinite(sigma), RAD_EINVAL, "sigma must be finite");
+        RAD_REQUIRE(!p->refine || h->has_accurate, RAD_EINVAL,
+                    "refinement needs an accurate operator (compress with accurate_dtype = RAD_F32)");
+        RAD_REQUIRE(!p->refine || (p->max_refine >= 1 && p->inner_tol > 0.0 && p->inner_tol < 1.0), RAD_EINVAL,
+                    "refinement needs max_refine >= 1 and 0 < inner_tol < 1");
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const int n = (int)h->n;
         Scratch ws(s);
@@ -368,6 +372,10 @@ int rad_solve_reflection(const rad_htree* h, const double* eps, const double* B,
         RAD_REQUIRE(p->restart >= 1 && p->restart <= 64, RAD_EINVAL, "restart must be in [1, 64]");
         RAD_REQUIRE(p->max_iter >= 1, RAD_EINVAL, "max_iter must be >= 1");
         RAD_REQUIRE(p->tol > 0.0 && std::isfinite(p->tol), RAD_EINVAL, "tol must be > 0");
+        RAD_REQUIRE(!p->refine || h->has_accurate, RAD_EINVAL,
+                    "refinement needs an accurate operator (compress with accurate_dtype = RAD_F32)");
+        RAD_REQUIRE(!p->refine || (p->max_refine >= 1 && p->inner_tol > 0.0 && p->inner_tol < 1.0), RAD_EINVAL,
+                    "refinement needs max_refine >= 1 and 0 < inner_tol < 1");
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const int n = (int)h->n;
         Scratch ws(s);
@@ -416,6 +424,7 @@ int rad_htree_get_stats(const rad_htree* h, rad_htree_stats* st) {
         st->far_u_entries = h->far_u_entries;
         st->far_v_entries = h->far_v_entries;
         st->n_tiles = h->n_tiles;
+        st->bytes_accurate = h->far_pool_acc.p ? h->far_entries * 4 : 0;
     });
 }
 

@@ -221,6 +221,11 @@ __global__ void flux_kernel(int n, int m, const FT* __restrict__ FY, const int* 
         sigma * eps[u] * ((double)FY[(long long)p * nc + c] - eta * (double)FY[(long long)p * nc + m]);
 }
 
+__global__ void axpy_kernel(double* __restrict__ X, const double* __restrict__ D, long long cnt) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < cnt) X[e] += D[e];
+}
+
 inline unsigned grid_for(long long cnt, int bs = 256) { return (unsigned)((cnt + bs - 1) / bs); }
 
 struct ColReducer {
@@ -366,6 +371,73 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
     }
 }
 
+// Mixed-precision iterative refinement: r = b - C y with the accurate
+// operator (FP32 storage, FP64 accumulation), correction C d = r by GMRES on
+// the fast operator to inner_tol, y += d; stops when every column's
+// accurate relative residual is <= tol.
+static void refine_tree(const rad_htree* h, const double* eps_t, const double* B, int nc, const rad_solve_params* p,
+                        double* X, rad_solve_info* info, Scratch& ws, cudaStream_t s) {
+    const int n = (int)h->n;
+    const long long nv = (long long)n * nc;
+    double* R = ws.get_n<double>(nv);
+    double* D = ws.get_n<double>(nv);
+    double* Tacc = static_cast<double*>(ws.get(apply_workspace_bytes_acc(h, nc)));
+    double* bn2 = ws.get_n<double>(nc);
+    double* r2 = ws.get_n<double>(nc);
+    const int chunks = (n + kChunkRows - 1) / kChunkRows;
+    ColReducer red{n, nc, chunks, ws.get_n<double>((long long)chunks * nc), s};
+    red.dots(B, 0, 1, B, bn2, false);
+    std::vector<double> hb(nc), hr(nc);
+    RAD_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    RAD_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * nv, s));
+    RAD_CUDA(cudaStreamSynchronize(s));
+    rad_solve_params inner = *p;
+    inner.tol = p->inner_tol;
+    inner.refine = 0;
+    int iters = 0, matvecs = 0, restarts = 0, step = 0, status = RAD_ENOTCONV;
+    double max_rel = 0.0;
+    for (;; ++step) {
+        Epi epi{kResid, eps_t, X, B, nc};
+        apply_tree_acc(h, X, nc, R, nc, nc, epi, Tacc, s);
+        ++matvecs;
+        red.dots(R, 0, 1, R, r2, false);
+        RAD_CUDA(cudaMemcpyAsync(hr.data(), r2, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+        RAD_CUDA(cudaStreamSynchronize(s));
+        max_rel = 0.0;
+        for (int c = 0; c < nc; ++c)
+            max_rel = std::max(max_rel, std::sqrt(std::max(hr[c], 0.0)) / (hb[c] > 0.0 ? std::sqrt(hb[c]) : 1.0));
+        if (max_rel <= p->tol) {
+            status = RAD_OK;
+            break;
+        }
+        if (step >= p->max_refine || iters >= p->max_iter) break;
+        rad_solve_info ii{};
+        {
+            Scratch inner_ws(s);
+            gmres_tree(h, eps_t, R, nc, &inner, D, &ii, inner_ws, s);
+        }
+        iters += ii.iters;
+        matvecs += ii.matvecs;
+        restarts += ii.restarts;
+        { ProfScope ps_("gmres_update_x", s); axpy_kernel<<<grid_for(nv), 256, 0, s>>>(X, D, nv); }
+        RAD_CHECK_LAUNCH();
+    }
+    if (info) {
+        info->status = status;
+        info->iters = iters;
+        info->restarts = restarts;
+        info->matvecs = matvecs;
+        info->max_rel_residual = max_rel;
+        info->refinements = step;
+    }
+}
+
+static void solve_tree(const rad_htree* h, const double* eps_t, const double* B, int nc, const rad_solve_params* p,
+                       double* X, rad_solve_info* info, Scratch& ws, cudaStream_t s) {
+    if (p->refine) refine_tree(h, eps_t, B, nc, p, X, info, ws, s);
+    else gmres_tree(h, eps_t, B, nc, p, X, info, ws, s);
+}
+
 void solve_flux(const rad_htree* h, const double* eps_dev, const double* T_dev, int64_t ldT, int m, double sigma,
                 const rad_solve_params* p, double* q_dev, int64_t ldq, rad_solve_info* info, cudaStream_t s) {
     const int n = (int)h->n;
@@ -379,7 +451,7 @@ void solve_flux(const rad_htree* h, const double* eps_dev, const double* T_dev, 
     { ProfScope ps_("gmres_rhs", s); rhs_kernel<<<grid_for(nv), 256, 0, s>>>(n, m, eps_dev, T_dev, ldT, h->perm.as<int>(), eps_t, B); }
     RAD_CHECK_LAUNCH();
     rad_solve_info local{};
-    gmres_tree(h, eps_t, B, nc, p, X, &local, ws, s);
+    solve_tree(h, eps_t, B, nc, p, X, &local, ws, s);
     // flux, Eq. (12): FY = F [Y z]
     void* Tws = ws.get(apply_workspace_bytes(h, nc));
     if (op64) {
@@ -413,7 +485,7 @@ void solve_reflection(const rad_htree* h, const double* eps_dev, const double* B
     gather_user_to_tree(h, RAD_F64, eps_dev, n, 1, eps_t, 1, true, s);
     gather_user_to_tree(h, RAD_F64, B_dev, ldB, nrhs, B, nrhs, true, s);
     rad_solve_info local{};
-    gmres_tree(h, eps_t, B, nrhs, p, X, &local, ws, s);
+    solve_tree(h, eps_t, B, nrhs, p, X, &local, ws, s);
     scatter_tree_to_user(h, X, nrhs, nrhs, true, RAD_F64, Y_dev, ldY, s);
     RAD_CUDA(cudaStreamSynchronize(s));
     if (info) *info = local;

@@ -57,6 +57,12 @@ template <> struct Vec4<double, double> {
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
 };
+template <> struct Vec4<float, double> {
+    static __device__ __forceinline__ void load(const float* p, double v[4]) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+};
 template <> struct Vec4<__nv_bfloat16, float> {
     static __device__ __forceinline__ void load(const __nv_bfloat16* p, float v[4]) {
         const uint2 q = *reinterpret_cast<const uint2*>(p);
@@ -353,8 +359,7 @@ rows_multi(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ 
 }
 
 template <class FS, class AT, int RN>
-void launch_far_vt(const rad_htree* h, const AT* X, int ldx, AT* T, int ldt, int nc, cudaStream_t s) {
-    const OpView op = h->view();
+void launch_far_vt(const OpView& op, const AT* X, int ldx, AT* T, int ldt, int nc, cudaStream_t s) {
     const size_t bytes = GemmLayout<FS, AT>::bytes > GemmLayout<float, AT>::bytes ? GemmLayout<FS, AT>::bytes
                                                                                   : GemmLayout<float, AT>::bytes;
     static std::once_flag configured;
@@ -365,9 +370,8 @@ void launch_far_vt(const rad_htree* h, const AT* X, int ldx, AT* T, int ldt, int
     RAD_CHECK_LAUNCH();
 }
 template <class NS, class FS, class AT, int RN>
-void launch_rows(const rad_htree* h, const AT* X, int ldx, const AT* T, int ldt, void* Y, int ldy, int nc,
+void launch_rows(const OpView& op, const AT* X, int ldx, const AT* T, int ldt, void* Y, int ldy, int nc,
                  const Epi& epi, cudaStream_t s) {
-    const OpView op = h->view();
     const size_t bytes = GemmLayout<NS, AT>::bytes > GemmLayout<FS, AT>::bytes ? GemmLayout<NS, AT>::bytes
                                                                                 : GemmLayout<FS, AT>::bytes;
     static std::once_flag configured;
@@ -387,9 +391,8 @@ inline int rn_for(int max_ld, int nc) {
 }
 
 template <class NS, class FS, class AT>
-void apply_t(const rad_htree* h, const AT* X, int ldx, void* Y, int ldy, int nrhs, const Epi& epi, AT* T,
-             cudaStream_t s) {
-    const OpView op = h->view();
+void apply_t(const rad_htree* h, const OpView& op, const AT* X, int ldx, void* Y, int ldy, int nrhs, const Epi& epi,
+             AT* T, cudaStream_t s) {
     if (nrhs == 1) {
         if (op.n_gwork > 0) {
             { ProfScope ps_("hmv_far_vt", s); far_vt_single<FS, AT><<<(unsigned)h->groups_h.size(), 256, 0, s>>>(op, X, T); }
@@ -416,25 +419,25 @@ void apply_t(const rad_htree* h, const AT* X, int ldx, void* Y, int ldy, int nrh
         void* Yc = static_cast<char*>(Y) + (size_t)c0 * esz;
         if (op.n_gwork > 0) {
             switch (rn_for(group_ld, nc)) {
-                case 1: launch_far_vt<FS, AT, 1>(h, Xc, ldx, Tc, ldt, nc, s); break;
-                case 2: launch_far_vt<FS, AT, 2>(h, Xc, ldx, Tc, ldt, nc, s); break;
-                case 3: launch_far_vt<FS, AT, 3>(h, Xc, ldx, Tc, ldt, nc, s); break;
-                case 4: launch_far_vt<FS, AT, 4>(h, Xc, ldx, Tc, ldt, nc, s); break;
-                case 5: launch_far_vt<FS, AT, 5>(h, Xc, ldx, Tc, ldt, nc, s); break;
-                case 6: launch_far_vt<FS, AT, 6>(h, Xc, ldx, Tc, ldt, nc, s); break;
-                case 7: launch_far_vt<FS, AT, 7>(h, Xc, ldx, Tc, ldt, nc, s); break;
-                default: launch_far_vt<FS, AT, 8>(h, Xc, ldx, Tc, ldt, nc, s); break;
+                case 1: launch_far_vt<FS, AT, 1>(op, Xc, ldx, Tc, ldt, nc, s); break;
+                case 2: launch_far_vt<FS, AT, 2>(op, Xc, ldx, Tc, ldt, nc, s); break;
+                case 3: launch_far_vt<FS, AT, 3>(op, Xc, ldx, Tc, ldt, nc, s); break;
+                case 4: launch_far_vt<FS, AT, 4>(op, Xc, ldx, Tc, ldt, nc, s); break;
+                case 5: launch_far_vt<FS, AT, 5>(op, Xc, ldx, Tc, ldt, nc, s); break;
+                case 6: launch_far_vt<FS, AT, 6>(op, Xc, ldx, Tc, ldt, nc, s); break;
+                case 7: launch_far_vt<FS, AT, 7>(op, Xc, ldx, Tc, ldt, nc, s); break;
+                default: launch_far_vt<FS, AT, 8>(op, Xc, ldx, Tc, ldt, nc, s); break;
             }
         }
         switch (rn_for(tile_ld, nc)) {
-            case 1: launch_rows<NS, FS, AT, 1>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            case 2: launch_rows<NS, FS, AT, 2>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            case 3: launch_rows<NS, FS, AT, 3>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            case 4: launch_rows<NS, FS, AT, 4>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            case 5: launch_rows<NS, FS, AT, 5>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            case 6: launch_rows<NS, FS, AT, 6>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            case 7: launch_rows<NS, FS, AT, 7>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            default: launch_rows<NS, FS, AT, 8>(h, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 1: launch_rows<NS, FS, AT, 1>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 2: launch_rows<NS, FS, AT, 2>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 3: launch_rows<NS, FS, AT, 3>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 4: launch_rows<NS, FS, AT, 4>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 5: launch_rows<NS, FS, AT, 5>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 6: launch_rows<NS, FS, AT, 6>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            case 7: launch_rows<NS, FS, AT, 7>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+            default: launch_rows<NS, FS, AT, 8>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
         }
     }
 }
@@ -466,16 +469,33 @@ size_t apply_workspace_bytes(const rad_htree* h, int nrhs) {
 
 void apply_tree(const rad_htree* h, const void* X, int ldx, void* Y, int ldy, int nrhs, const Epi& epi,
                 void* T_ws, cudaStream_t s) {
+    const OpView op = h->view();
     if (h->op_is_f64()) {
-        apply_t<double, double, double>(h, static_cast<const double*>(X), ldx, Y, ldy, nrhs, epi,
+        apply_t<double, double, double>(h, op, static_cast<const double*>(X), ldx, Y, ldy, nrhs, epi,
                                         static_cast<double*>(T_ws), s);
     } else if (h->factor_dtype == RAD_F32) {
-        apply_t<float, float, float>(h, static_cast<const float*>(X), ldx, Y, ldy, nrhs, epi,
+        apply_t<float, float, float>(h, op, static_cast<const float*>(X), ldx, Y, ldy, nrhs, epi,
                                      static_cast<float*>(T_ws), s);
     } else {
-        apply_t<float, __nv_bfloat16, float>(h, static_cast<const float*>(X), ldx, Y, ldy, nrhs, epi,
+        apply_t<float, __nv_bfloat16, float>(h, op, static_cast<const float*>(X), ldx, Y, ldy, nrhs, epi,
                                              static_cast<float*>(T_ws), s);
     }
+}
+
+size_t apply_workspace_bytes_acc(const rad_htree* h, int nrhs) {
+    return sizeof(double) * (size_t)std::max(1, h->sum_rank) * (size_t)tree_ld(nrhs);
+}
+
+void apply_tree_acc(const rad_htree* h, const double* X, int ldx, double* Y, int ldy, int nrhs, const Epi& epi,
+                    double* T_ws, cudaStream_t s) {
+    RAD_REQUIRE(h->has_accurate, RAD_EINVAL, "no accurate operator (compress with accurate_dtype = RAD_F32)");
+    if (h->op_is_f64()) {
+        apply_t<double, double, double>(h, h->view(), X, ldx, Y, ldy, nrhs, epi, T_ws, s);
+        return;
+    }
+    OpView op = h->view();
+    op.far_pool = h->accurate_far_pool();
+    apply_t<float, float, double>(h, op, X, ldx, Y, ldy, nrhs, epi, T_ws, s);
 }
 
 void gather_user_to_tree(const rad_htree* h, int dtype_in, const void* x, int64_t ldx, int nrhs, void* X, int ldX,

@@ -231,6 +231,8 @@ struct rad_htree {
     std::vector<rad::Group> groups_h;
     std::vector<rad::Piece> near_pieces, far_pieces;   // per tile, in panel order
     rad::DevBuf near_pool, far_pool;
+    rad::DevBuf far_pool_acc;          // FP32 factors kept for refinement
+    bool has_accurate = false;         // an accurate operator exists
     rad::DevBuf d_tiles, d_xidx, d_tidx, d_gwork, d_groups;
     int n_tiles = 0;
     int n_gwork = 0;
@@ -256,6 +258,9 @@ struct rad_htree {
         return v;
     }
     bool op_is_f64() const { return near_dtype == RAD_F64; }
+    // the accurate operator: FP32 factors (the BF16 path's second copy, or
+    // the FP32 factors themselves)
+    const void* accurate_far_pool() const { return far_pool_acc.p ? far_pool_acc.p : far_pool.p; }
 };
 
 namespace rad {
@@ -283,6 +288,11 @@ struct Epi {
 };
 void apply_tree(const rad_htree* h, const void* X, int ldx, void* Y, int ldy, int nrhs,
                 const Epi& epi, void* T_ws, cudaStream_t s);
+// The accurate operator (FP32 storage) with FP64 vectors and FP64
+// accumulation; T_ws holds apply_workspace_bytes_acc(h, nrhs) bytes.
+void apply_tree_acc(const rad_htree* h, const double* X, int ldx, double* Y, int ldy, int nrhs, const Epi& epi,
+                    double* T_ws, cudaStream_t s);
+size_t apply_workspace_bytes_acc(const rad_htree* h, int nrhs);
 size_t apply_workspace_bytes(const rad_htree* h, int nrhs);
 void gather_user_to_tree(const rad_htree* h, int dtype_in, const void* x, int64_t ldx, int nrhs,
                          void* X, int ldX, bool op64, cudaStream_t s);
