@@ -874,9 +874,10 @@ void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     h->near_dtype = p->near_dtype;
     h->tol = p->tol;
     h->pivoting = p->pivoting;
-    // ACA arithmetic: FP64 for the FP64 path and for tolerances near FP32
-    // resolution; FP32 (FP64 centroid differences, FP64 norms) otherwise.
-    if (p->near_dtype == RAD_F64 || p->tol < 2e-6) compress_t<double>(h, p, s);
+    // ACA arithmetic: FP64 for the FP64 path and for tolerances below 1e-6
+    // (near FP32 resolution); FP32 otherwise (hi/lo centroid differences,
+    // two-sum running norm).
+    if (p->near_dtype == RAD_F64 || p->tol < 1e-6) compress_t<double>(h, p, s);
     else compress_t<float>(h, p, s);
     h->compressed = true;
 }

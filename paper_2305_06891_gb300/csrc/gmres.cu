@@ -452,9 +452,14 @@ void solve_flux(const rad_htree* h, const double* eps_dev, const double* T_dev, 
     RAD_CHECK_LAUNCH();
     rad_solve_info local{};
     solve_tree(h, eps_t, B, nc, p, X, &local, ws, s);
-    // flux, Eq. (12): FY = F [Y z]
-    void* Tws = ws.get(apply_workspace_bytes(h, nc));
-    if (op64) {
+    // flux, Eq. (12): FY = F [Y z] (with the accurate operator when refining)
+    void* Tws = ws.get(std::max(apply_workspace_bytes(h, nc), apply_workspace_bytes_acc(h, nc)));
+    if (p->refine && !op64) {
+        double* FY = ws.get_n<double>(nv);
+        apply_tree_acc(h, X, nc, FY, nc, nc, Epi{kStore, nullptr, nullptr, nullptr, 0}, static_cast<double*>(Tws), s);
+        { ProfScope ps_("flux", s); flux_kernel<double><<<grid_for((long long)n * m), 256, 0, s>>>(n, m, FY, h->perm.as<int>(), eps_dev, T_dev,
+                                                                      ldT, sigma, q_dev, ldq); }
+    } else if (op64) {
         double* FY = ws.get_n<double>(nv);
         apply_tree(h, X, nc, FY, nc, nc, Epi{kStore, nullptr, nullptr, nullptr, 0}, Tws, s);
         { ProfScope ps_("flux", s); flux_kernel<double><<<grid_for((long long)n * m), 256, 0, s>>>(n, m, FY, h->perm.as<int>(), eps_dev, T_dev,

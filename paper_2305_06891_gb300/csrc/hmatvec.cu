@@ -173,6 +173,241 @@ rows_single(OpView op, const AT* __restrict__ x, const AT* __restrict__ T, void*
     }
 }
 
+// ---------------------------------------------------------------- 2-4 RHS
+// Streaming kernels for a few right-hand sides: one pass over every panel,
+// thread (q, g) owns rows 4q .. 4q+3 for all NCOL columns.
+template <class FS, class AT, int NCOL>
+__global__ void __launch_bounds__(256) far_vt_stream(OpView op, const AT* __restrict__ X, int ldx,
+                                                     AT* __restrict__ T, int ldt) {
+    __shared__ AT part[NCOL][1024];
+    const Group gr = op.groups[blockIdx.x];
+    const int quads = gr.ld / 4;
+    const int rq = min(256, quads);
+    const int G = 256 / rq;
+    const int q = threadIdx.x % rq, jg = threadIdx.x / rq;
+    const long long ld = gr.ld;
+    for (int q0 = 0; q0 < quads; q0 += rq) {
+        AT acc[NCOL][4] = {};
+        if (q0 + q < quads && jg < G) {
+            const FS* P = static_cast<const FS*>(op.far_pool) + gr.voff + 4 * (q0 + q);
+            for (int j = jg; j < gr.n; j += G) {
+                AT v[4];
+                Vec4<FS, AT>::load(P + j * ld, v);
+                const AT* xr = X + (long long)(gr.c0 + j) * ldx;
+#pragma unroll
+                for (int c = 0; c < NCOL; ++c) {
+                    const AT xc = xr[c];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[c][r] += v[r] * xc;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) part[c][4 * threadIdx.x + r] = acc[c][r];
+        __syncthreads();
+        for (int rr = threadIdx.x; rr < 4 * rq; rr += 256) {
+            const int row = 4 * q0 + rr;
+            if (row < gr.M)
+#pragma unroll
+                for (int c = 0; c < NCOL; ++c) {
+                    AT sum = 0;
+                    for (int g = 0; g < G; ++g) sum += part[c][4 * (g * rq) + rr];
+                    T[(long long)(gr.toff + row) * ldt + c] = sum;
+                }
+        }
+        __syncthreads();
+    }
+}
+
+template <class S, class AT, int NCOL>
+__device__ __forceinline__ void stream_cols(const S* __restrict__ P, long long ld, int kcols, int g, int G,
+                                            const int* __restrict__ idx, const AT* __restrict__ V, int ldv,
+                                            AT (&acc)[NCOL][4]) {
+    for (int c = g; c < kcols; c += G) {
+        AT a[4];
+        Vec4<S, AT>::load(P + c * ld, a);
+        const AT* vr = V + (long long)idx[c] * ldv;
+#pragma unroll
+        for (int k = 0; k < NCOL; ++k) {
+            const AT xv = vr[k];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[k][r] += a[r] * xv;
+        }
+    }
+}
+
+template <class NS, class FS, class AT, int NCOL>
+__global__ void __launch_bounds__(256)
+rows_stream(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ T, int ldt, void* Y, int ldy,
+            Epi epi) {
+    __shared__ AT part[NCOL][1024];
+    const Tile t = op.tiles[blockIdx.x];
+    const int quads = t.ld / 4;
+    const int G = 256 / quads;
+    const int q = threadIdx.x % quads, g = threadIdx.x / quads;
+    AT acc[NCOL][4] = {};
+    if (g < G) {
+        stream_cols<NS, AT, NCOL>(static_cast<const NS*>(op.near_pool) + t.noff + 4 * q, t.ld, t.kn, g, G,
+                                  op.xidx + t.ixn, X, ldx, acc);
+        stream_cols<FS, AT, NCOL>(static_cast<const FS*>(op.far_pool) + t.foff + 4 * q, t.ld, t.kf, g, G,
+                                  op.tidx + t.ixf, T, ldt, acc);
+    }
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) part[c][4 * threadIdx.x + r] = acc[c][r];
+    __syncthreads();
+    if ((int)threadIdx.x < t.rows) {
+        const int row = threadIdx.x;
+#pragma unroll
+        for (int c = 0; c < NCOL; ++c) {
+            AT sum = 0;
+            for (int gg = 0; gg < G; ++gg) sum += part[c][4 * (gg * quads) + row];
+            epilogue<AT>(epi, Y, ldy, t.r0 + row, c, sum);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- double-float
+// FP64-grade sums on the FP32 pipe (GB300's FP64 pipe is narrow): a value is
+// an unevaluated pair hi + lo of floats; products of a stored FP32 entry with
+// a pair use the exact FMA product error, sums the error-free two-sum.
+struct DF {
+    float h, l;
+};
+__device__ __forceinline__ void df_fma(DF& acc, float a, const DF& x) {
+    const float p = __fmul_rn(a, x.h);
+    const float pe = __fmaf_rn(a, x.h, -p);                 // a*x.h - p, exactly
+    const float s = __fadd_rn(acc.h, p);
+    const float bp = __fsub_rn(s, acc.h);
+    const float se = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    acc.h = s;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(__fadd_rn(se, pe), __fmul_rn(a, x.l)));
+}
+__device__ __forceinline__ DF df_norm(DF v) {
+    const float s = __fadd_rn(v.h, v.l);
+    return DF{s, __fsub_rn(v.l, __fsub_rn(s, v.h))};
+}
+
+__global__ void to_df_kernel(const double* __restrict__ X, int ldx, int n, int nc, DF* __restrict__ out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)n * nc) return;
+    const int p = (int)(e / nc), c = (int)(e - (long long)p * nc);
+    const double x = X[(long long)p * ldx + c];
+    const float h = __double2float_rn(x);
+    out[e] = DF{h, __double2float_rn(x - (double)h)};
+}
+
+template <int NCOL>
+__global__ void __launch_bounds__(256) far_vt_df(OpView op, const DF* __restrict__ X, DF* __restrict__ T) {
+    __shared__ DF part[NCOL][1024];
+    const Group gr = op.groups[blockIdx.x];
+    const int quads = gr.ld / 4;
+    const int rq = min(128, quads);
+    const int G = 256 / rq;
+    const int q = threadIdx.x % rq, jg = threadIdx.x / rq;
+    const long long ld = gr.ld;
+    for (int q0 = 0; q0 < quads; q0 += rq) {
+        DF acc[NCOL][4];
+#pragma unroll
+        for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[c][r] = DF{0.0f, 0.0f};
+        if (q0 + q < quads && jg < G) {
+            const float* P = static_cast<const float*>(op.far_pool) + gr.voff + 4 * (q0 + q);
+            for (int j = jg; j < gr.n; j += G) {
+                float v[4];
+                Vec4<float, float>::load(P + j * ld, v);
+                const DF* xr = X + (long long)(gr.c0 + j) * NCOL;
+#pragma unroll
+                for (int c = 0; c < NCOL; ++c) {
+                    const DF xc = xr[c];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) df_fma(acc[c][r], v[r], xc);
+                }
+            }
+        }
+        if (jg < G)
+#pragma unroll
+            for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) part[c][4 * threadIdx.x + r] = df_norm(acc[c][r]);
+        __syncthreads();
+        for (int rr = threadIdx.x; rr < 4 * rq; rr += 256) {
+            const int row = 4 * q0 + rr;
+            if (row < gr.M)
+#pragma unroll
+                for (int c = 0; c < NCOL; ++c) {
+                    double sum = 0.0;
+                    for (int g = 0; g < G; ++g) {
+                        const DF d = part[c][4 * (g * rq) + rr];
+                        sum += (double)d.h + (double)d.l;
+                    }
+                    const float h = __double2float_rn(sum);
+                    T[(long long)(gr.toff + row) * NCOL + c] = DF{h, __double2float_rn(sum - (double)h)};
+                }
+        }
+        __syncthreads();
+    }
+}
+
+template <int NCOL>
+__device__ __forceinline__ void stream_cols_df(const float* __restrict__ P, long long ld, int kcols, int g, int G,
+                                               const int* __restrict__ idx, const DF* __restrict__ V,
+                                               DF (&acc)[NCOL][4]) {
+    for (int c = g; c < kcols; c += G) {
+        float a[4];
+        Vec4<float, float>::load(P + c * ld, a);
+        const DF* vr = V + (long long)idx[c] * NCOL;
+#pragma unroll
+        for (int k = 0; k < NCOL; ++k) {
+            const DF xv = vr[k];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) df_fma(acc[k][r], a[r], xv);
+        }
+    }
+}
+
+template <int NCOL>
+__global__ void __launch_bounds__(256)
+rows_df(OpView op, const DF* __restrict__ X, const DF* __restrict__ T, double* Y, int ldy, Epi epi) {
+    __shared__ DF part[NCOL][1024];
+    const Tile t = op.tiles[blockIdx.x];
+    const int quads = t.ld / 4;
+    const int G = 256 / quads;
+    const int q = threadIdx.x % quads, g = threadIdx.x / quads;
+    DF acc[NCOL][4];
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[c][r] = DF{0.0f, 0.0f};
+    if (g < G) {
+        stream_cols_df<NCOL>(static_cast<const float*>(op.near_pool) + t.noff + 4 * q, t.ld, t.kn, g, G,
+                             op.xidx + t.ixn, X, acc);
+        stream_cols_df<NCOL>(static_cast<const float*>(op.far_pool) + t.foff + 4 * q, t.ld, t.kf, g, G,
+                             op.tidx + t.ixf, T, acc);
+    }
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) part[c][4 * threadIdx.x + r] = df_norm(acc[c][r]);
+    __syncthreads();
+    if ((int)threadIdx.x < t.rows) {
+        const int row = threadIdx.x;
+#pragma unroll
+        for (int c = 0; c < NCOL; ++c) {
+            double sum = 0.0;
+            for (int gg = 0; gg < G; ++gg) {
+                const DF d = part[c][4 * (gg * quads) + row];
+                sum += (double)d.h + (double)d.l;
+            }
+            epilogue<double>(epi, Y, ldy, t.r0 + row, c, sum);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- many RHS
 template <class AT> struct Chunk;
 template <> struct Chunk<float> { static constexpr int KC = 32; };
@@ -390,6 +625,35 @@ inline int rn_for(int max_ld, int nc) {
     return std::max(1, std::min(8, (nc + cg - 1) / cg));
 }
 
+template <class NS, class FS, class AT, int NCOL>
+void launch_stream(const rad_htree* h, const OpView& op, const AT* X, int ldx, AT* T, int ldt, void* Y, int ldy,
+                   const Epi& epi, cudaStream_t s) {
+    if (op.n_gwork > 0) {
+        { ProfScope ps_("hmv_far_vt", s); far_vt_stream<FS, AT, NCOL><<<(unsigned)h->groups_h.size(), 256, 0, s>>>(op, X, ldx, T, ldt); }
+        RAD_CHECK_LAUNCH();
+    }
+    { ProfScope ps_("hmv_rows", s); rows_stream<NS, FS, AT, NCOL><<<op.n_tiles, 256, 0, s>>>(op, X, ldx, T, ldt, Y, ldy, epi); }
+    RAD_CHECK_LAUNCH();
+}
+
+template <int NCOL>
+void launch_df(const rad_htree* h, const OpView& op, const double* X, int ldx, double* Y, int ldy, int nrhs,
+               const Epi& epi, double* T_ws, cudaStream_t s) {
+    // the double-float copies of X and T share the T workspace
+    const int n = (int)h->n;
+    DF* Xd = reinterpret_cast<DF*>(T_ws);
+    DF* Td = Xd + (size_t)n * NCOL;
+    const long long cnt = (long long)n * nrhs;
+    { ProfScope ps_("permute", s); to_df_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(X, ldx, n, NCOL, Xd); }
+    RAD_CHECK_LAUNCH();
+    if (op.n_gwork > 0) {
+        { ProfScope ps_("hmv_far_vt", s); far_vt_df<NCOL><<<(unsigned)h->groups_h.size(), 256, 0, s>>>(op, Xd, Td); }
+        RAD_CHECK_LAUNCH();
+    }
+    { ProfScope ps_("hmv_rows", s); rows_df<NCOL><<<op.n_tiles, 256, 0, s>>>(op, Xd, Td, Y, ldy, epi); }
+    RAD_CHECK_LAUNCH();
+}
+
 template <class NS, class FS, class AT>
 void apply_t(const rad_htree* h, const OpView& op, const AT* X, int ldx, void* Y, int ldy, int nrhs, const Epi& epi,
              AT* T, cudaStream_t s) {
@@ -400,6 +664,15 @@ void apply_t(const rad_htree* h, const OpView& op, const AT* X, int ldx, void* Y
         }
         { ProfScope ps_("hmv_rows", s); rows_single<NS, FS, AT><<<op.n_tiles, 256, 0, s>>>(op, X, T, Y, epi); }
         RAD_CHECK_LAUNCH();
+        return;
+    }
+    if (nrhs <= 4) {
+        const int ldt = tree_ld(nrhs);
+        switch (nrhs) {
+            case 2: launch_stream<NS, FS, AT, 2>(h, op, X, ldx, T, ldt, Y, ldy, epi, s); break;
+            case 3: launch_stream<NS, FS, AT, 3>(h, op, X, ldx, T, ldt, Y, ldy, epi, s); break;
+            default: launch_stream<NS, FS, AT, 4>(h, op, X, ldx, T, ldt, Y, ldy, epi, s); break;
+        }
         return;
     }
     int tile_ld = 4, group_ld = 4;
@@ -483,7 +756,9 @@ void apply_tree(const rad_htree* h, const void* X, int ldx, void* Y, int ldy, in
 }
 
 size_t apply_workspace_bytes_acc(const rad_htree* h, int nrhs) {
-    return sizeof(double) * (size_t)std::max(1, h->sum_rank) * (size_t)tree_ld(nrhs);
+    const size_t gemm = sizeof(double) * (size_t)std::max(1, h->sum_rank) * (size_t)tree_ld(nrhs);
+    const size_t df = sizeof(DF) * (size_t)4 * ((size_t)h->n + (size_t)std::max(1, h->sum_rank));
+    return std::max(gemm, df);
 }
 
 void apply_tree_acc(const rad_htree* h, const double* X, int ldx, double* Y, int ldy, int nrhs, const Epi& epi,
@@ -495,6 +770,16 @@ void apply_tree_acc(const rad_htree* h, const double* X, int ldx, double* Y, int
     }
     OpView op = h->view();
     op.far_pool = h->accurate_far_pool();
+    if (nrhs <= 4) {
+        // FP64-grade accumulation on the FP32 pipe
+        switch (nrhs) {
+            case 1: launch_df<1>(h, op, X, ldx, Y, ldy, nrhs, epi, T_ws, s); break;
+            case 2: launch_df<2>(h, op, X, ldx, Y, ldy, nrhs, epi, T_ws, s); break;
+            case 3: launch_df<3>(h, op, X, ldx, Y, ldy, nrhs, epi, T_ws, s); break;
+            default: launch_df<4>(h, op, X, ldx, Y, ldy, nrhs, epi, T_ws, s); break;
+        }
+        return;
+    }
     apply_t<float, float, double>(h, op, X, ldx, Y, ldy, nrhs, epi, T_ws, s);
 }
 

@@ -42,7 +42,7 @@ def test_fp64_exact_when_tolerance_vanishes(cyl):
     assert rel(r.rad_hmatvec(h, x), F @ x) <= 1e-12
 
 
-@pytest.mark.parametrize("nrhs", [1, 2, 3, 17, 65, 130])
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 4, 17, 65, 130])
 def test_multi_rhs_fp64_and_fp32(cyl, nrhs):
     verts, F = cyl
     r = rad()
