@@ -27,6 +27,8 @@
 // stored dense.
 
 #include <algorithm>
+#include <climits>
+#include <memory>
 #include <cstring>
 #include <numeric>
 
@@ -538,6 +540,28 @@ dense_from_matrix_kernel(int n, const Tile* __restrict__ tiles, const double* __
     }
 }
 
+// Indices 0..key.size()-1 ordered by descending key, ties in index order
+// (two stable 16-bit counting passes; keys are clamped to 32 bits).
+static std::vector<int> order_desc(const std::vector<long long>& key) {
+    const size_t m = key.size();
+    std::vector<int> a(m), b(m);
+    std::vector<uint32_t> k(m);
+    for (size_t i = 0; i < m; ++i) {
+        a[i] = (int)i;
+        k[i] = 0xffffffffu - (uint32_t)std::min<long long>(std::max<long long>(key[i], 0), 0xffffffffll);
+    }
+    std::vector<int> cnt(65537);
+    for (int pass = 0; pass < 2; ++pass) {
+        const int sh = 16 * pass;
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (size_t i = 0; i < m; ++i) ++cnt[((k[a[i]] >> sh) & 0xffff) + 1];
+        for (int d = 0; d < 65536; ++d) cnt[d + 1] += cnt[d];
+        for (size_t i = 0; i < m; ++i) b[cnt[(k[a[i]] >> sh) & 0xffff]++] = a[i];
+        a.swap(b);
+    }
+    return a;
+}
+
 template <class CT>
 void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>& jobs, std::vector<int>& ranks,
                 std::vector<long long>& evals, std::vector<std::vector<double>>* unused, Scratch& ws,
@@ -555,13 +579,9 @@ void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>
     AcaJob* d_jobs = ws.get_n<AcaJob>(nj);
     h2d(d_jobs, jobs, s);
     // schedule the largest blocks first
-    std::vector<int> order(nj);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        const long long wa = (long long)(jobs[a].m + jobs[a].n) * std::max(1, jobs[a].kmax);
-        const long long wb = (long long)(jobs[b].m + jobs[b].n) * std::max(1, jobs[b].kmax);
-        return wa > wb;
-    });
+    std::vector<long long> wkey(nj);
+    for (int b = 0; b < nj; ++b) wkey[b] = (long long)(jobs[b].m + jobs[b].n) * std::max(1, jobs[b].kmax);
+    const std::vector<int> order = order_desc(wkey);
     int* d_order = ws.get_n<int>(nj);
     h2d(d_order, order, s);
     int* d_rank = ws.get_n<int>(nj);
@@ -642,31 +662,83 @@ static void for_tiles(const std::vector<Tile>& tiles, const std::vector<int>& ti
     }
 }
 
-static void upload_operator(rad_htree* h, const std::vector<std::vector<int>>& xi,
-                            const std::vector<std::vector<int>>& ti, cudaStream_t s) {
-    std::vector<int> xidx, tidx;
-    for (size_t t = 0; t < h->tiles_h.size(); ++t) {
-        h->tiles_h[t].ixn = (int)xidx.size();
-        h->tiles_h[t].ixf = (int)tidx.size();
-        xidx.insert(xidx.end(), xi[t].begin(), xi[t].end());
-        tidx.insert(tidx.end(), ti[t].begin(), ti[t].end());
+// A run of consecutive gather indices: out[dst + i] = start + i, i < count.
+// Every tile's gather list (near: X rows of its dense blocks; far: T rows of
+// its low-rank blocks) is a concatenation of such runs.
+struct IdxRun {
+    int tile, col, start, count;
+};
+__global__ void __launch_bounds__(256)
+fill_runs_kernel(const IdxRun* __restrict__ runs, int nruns, const Tile* __restrict__ tiles, int far, int* out) {
+    const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (r >= nruns) return;
+    const IdxRun u = runs[r];
+    const Tile t = tiles[u.tile];
+    int* o = out + (far ? t.ixf : t.ixn) + u.col;
+    for (int i = threadIdx.x & 31; i < u.count; i += 32) o[i] = u.start + i;
+}
+
+static void upload_operator(rad_htree* h, const std::vector<IdxRun>& near_runs, const std::vector<IdxRun>& far_runs,
+                            cudaStream_t s) {
+    long long nx = 0, nf = 0;
+    for (auto& t : h->tiles_h) {
+        t.ixn = (int)nx;
+        t.ixf = (int)nf;
+        nx += t.kn;
+        nf += t.kf;
     }
-    std::vector<GWork> gwork;
-    for (int g = 0; g < (int)h->groups_h.size(); ++g)
-        for (int r = 0; r < h->groups_h[g].M; r += kTileRows)
-            gwork.push_back(GWork{g, r, std::min(kTileRows, h->groups_h[g].M - r), 0});
+    RAD_REQUIRE(nx < INT_MAX && nf < INT_MAX, RAD_ELIMIT, "gather lists exceed 2^31 entries");
+    // Work lists, heaviest item first so that the long items start in the
+    // first wave and the short ones fill the tail (longest-processing-time
+    // order); ties keep the natural order.
+    const auto& G = h->groups_h;
+    auto split_groups = [&](int rows_per_item) {
+        std::vector<GWork> w;
+        for (int g = 0; g < (int)G.size(); ++g)
+            for (int r = 0; r < G[g].M; r += rows_per_item)
+                w.push_back(GWork{g, r, std::min(rows_per_item, G[g].M - r), 0});
+        std::vector<long long> key(w.size());
+        for (size_t i = 0; i < w.size(); ++i) key[i] = (long long)w[i].rows * G[w[i].g].n;
+        std::vector<GWork> sorted(w.size());
+        const std::vector<int> ord = order_desc(key);
+        for (size_t i = 0; i < w.size(); ++i) sorted[i] = w[ord[i]];
+        w.swap(sorted);
+        return w;
+    };
+    std::vector<GWork> gwork = split_groups(kTileRows);
+    std::vector<GWork> sitems = split_groups(kStreamRows);
+    std::vector<long long> tkey(h->tiles_h.size());
+    for (size_t t = 0; t < tkey.size(); ++t) {
+        const Tile& tl = h->tiles_h[t];
+        tkey[t] = (long long)tl.ld * (tl.kn + tl.kf);
+    }
+    const std::vector<int> torder = order_desc(tkey);
     h->n_tiles = (int)h->tiles_h.size();
     h->n_gwork = (int)gwork.size();
-    h->d_tiles.alloc(sizeof(Tile) * std::max<size_t>(1, h->tiles_h.size()));
-    h->d_xidx.alloc(sizeof(int) * std::max<size_t>(1, xidx.size()));
-    h->d_tidx.alloc(sizeof(int) * std::max<size_t>(1, tidx.size()));
-    h->d_gwork.alloc(sizeof(GWork) * std::max<size_t>(1, gwork.size()));
-    h->d_groups.alloc(sizeof(Group) * std::max<size_t>(1, h->groups_h.size()));
+    h->n_sitems = (int)sitems.size();
+    h->d_sitems.alloc(sizeof(GWork) * std::max<size_t>(1, sitems.size()), s);
+    h->d_torder.alloc(sizeof(int) * std::max<size_t>(1, torder.size()), s);
+    h2d(h->d_sitems.as<GWork>(), sitems, s);
+    h2d(h->d_torder.as<int>(), torder, s);
+    h->d_tiles.alloc(sizeof(Tile) * std::max<size_t>(1, h->tiles_h.size()), s);
+    h->d_xidx.alloc(sizeof(int) * std::max<long long>(1, nx), s);
+    h->d_tidx.alloc(sizeof(int) * std::max<long long>(1, nf), s);
+    h->d_gwork.alloc(sizeof(GWork) * std::max<size_t>(1, gwork.size()), s);
+    h->d_groups.alloc(sizeof(Group) * std::max<size_t>(1, h->groups_h.size()), s);
     h2d(h->d_tiles.as<Tile>(), h->tiles_h, s);
-    h2d(h->d_xidx.as<int>(), xidx, s);
-    h2d(h->d_tidx.as<int>(), tidx, s);
     h2d(h->d_gwork.as<GWork>(), gwork, s);
     h2d(h->d_groups.as<Group>(), h->groups_h, s);
+    Scratch ws(s);
+    const std::vector<IdxRun>* lists[2] = {&near_runs, &far_runs};
+    int* outs[2] = {h->d_xidx.as<int>(), h->d_tidx.as<int>()};
+    for (int f = 0; f < 2; ++f) {
+        const std::vector<IdxRun>& rl = *lists[f];
+        if (rl.empty()) continue;
+        IdxRun* d = ws.get_n<IdxRun>(rl.size());
+        h2d(d, rl, s);
+        { ProfScope ps_("gather_lists", s); fill_runs_kernel<<<(unsigned)((rl.size() + 7) / 8), 256, 0, s>>>(d, (int)rl.size(), h->d_tiles.as<Tile>(), f, outs[f]); }
+        RAD_CHECK_LAUNCH();
+    }
 }
 
 template <class S, class CT>
@@ -703,6 +775,7 @@ template <class CT>
 void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     Scratch ws(s);
     // admissible blocks -> ACA jobs
+    auto hs_jobs = std::make_unique<HostScope>("host_aca_jobs");
     std::vector<int> adm;
     for (int b = 0; b < (int)h->blocks.size(); ++b)
         if (h->blocks[b].admissible) adm.push_back(b);
@@ -724,7 +797,12 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     std::vector<long long> evals;
     CT* Us = nullptr;
     CT* Vs = nullptr;
-    if (!jobs.empty()) launch_aca<CT>(h, p, jobs, ranks, evals, nullptr, ws, Us, Vs, s);
+    hs_jobs.reset();
+    if (!jobs.empty()) {
+        HostScope hs_("host_aca_launch_wait");
+        launch_aca<CT>(h, p, jobs, ranks, evals, nullptr, ws, Us, Vs, s);
+    }
+    auto hs_plan = std::make_unique<HostScope>("host_plan");
     std::vector<int> job_of(h->blocks.size(), -1);
     for (size_t a = 0; a < adm.size(); ++a) {
         job_of[adm[a]] = (int)a;
@@ -737,11 +815,14 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     std::vector<int> tile_at;
     make_tiles(h, h->tiles_h, tile_at);
     std::vector<Tile>& tiles = h->tiles_h;
-    const size_t nt = tiles.size();
-    std::vector<std::vector<int>> xi(nt), ti(nt);
+    std::vector<IdxRun> near_runs, far_runs;
     h->near_pieces.clear();
     h->far_pieces.clear();
     h->groups_h.clear();
+    near_runs.reserve(h->blocks.size());
+    far_runs.reserve(2 * h->blocks.size());
+    h->near_pieces.reserve(h->blocks.size());
+    h->far_pieces.reserve(2 * h->blocks.size());
     int64_t fallback = 0, near_e = 0, far_u = 0, far_v = 0;
     int maxk = 0;
     // column groups of the low-rank blocks (k > 0), in order of first use
@@ -781,6 +862,9 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     std::vector<DenseWork> dwork;
     std::vector<UWork> uwork;
     std::vector<VWork> vwork;
+    dwork.reserve(h->blocks.size());
+    uwork.reserve(2 * h->blocks.size());
+    vwork.reserve(h->blocks.size());
     for (int b = 0; b < (int)h->blocks.size(); ++b) {
         const BlockH& bk = h->blocks[b];
         const int m = bk.r1 - bk.r0, n = bk.c1 - bk.c0;
@@ -790,7 +874,7 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
                 h->near_pieces.push_back(Piece{b, t, tiles[t].kn});
                 for (int c0 = 0; c0 < n; c0 += 64)
                     dwork.push_back(DenseWork{t, bk.c0 + c0, std::min(64, n - c0), tiles[t].kn + c0});
-                for (int c = 0; c < n; ++c) xi[t].push_back(bk.c0 + c);
+                near_runs.push_back(IdxRun{t, tiles[t].kn, bk.c0, n});
                 tiles[t].kn += n;
             });
         } else if (bk.rank > 0) {
@@ -803,7 +887,7 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
             for_tiles(tiles, tile_at, bk.r0, bk.r1, [&](int t) {
                 h->far_pieces.push_back(Piece{b, t, tiles[t].kf});
                 uwork.push_back(UWork{t, tiles[t].r0 - bk.r0, m, k, tiles[t].kf, 0, jb.offU});
-                for (int l = 0; l < k; ++l) ti[t].push_back(gr.toff + bk.grow + l);
+                far_runs.push_back(IdxRun{t, tiles[t].kf, gr.toff + bk.grow, k});
                 tiles[t].kf += k;
             });
             vwork.push_back(VWork{bk.group, bk.grow, n, k, jb.offV});
@@ -822,23 +906,25 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     }
     h->stored_near = noff;
     h->stored_far = foff;
+    hs_plan.reset();
+    auto hs_up = std::make_unique<HostScope>("host_alloc_upload_fill");
     const int ns = dtype_size(h->near_dtype);
     const int fs = dtype_size(h->factor_dtype);
-    h->near_pool.alloc((size_t)std::max<long long>(noff, 16) * ns);
-    h->far_pool.alloc((size_t)std::max<long long>(foff, 16) * fs);
+    h->near_pool.alloc((size_t)std::max<long long>(noff, 16) * ns, s);
+    h->far_pool.alloc((size_t)std::max<long long>(foff, 16) * fs, s);
     RAD_CUDA(cudaMemsetAsync(h->far_pool.p, 0, h->far_pool.bytes, s));
-    upload_operator(h, xi, ti, s);
+    upload_operator(h, near_runs, far_runs, s);
     if (h->near_dtype == RAD_F64) launch_dense_fill<double, double>(h, dwork, s);
     else launch_dense_fill<float, float>(h, dwork, s);
     if (h->factor_dtype == RAD_F64) launch_factor_fill<CT, double>(h, uwork, vwork, Us, Vs, s);
     else if (h->factor_dtype == RAD_F32) launch_factor_fill<CT, float>(h, uwork, vwork, Us, Vs, s);
     else launch_factor_fill<CT, __nv_bfloat16>(h, uwork, vwork, Us, Vs, s);
     // accurate operator for mixed-precision refinement: FP32 factors
-    h->far_pool_acc.release();
+    h->far_pool_acc.release(s);
     h->has_accurate = false;
     if (p->accurate_dtype == RAD_F32) {
         if (h->factor_dtype == RAD_BF16) {
-            h->far_pool_acc.alloc((size_t)std::max<long long>(foff, 16) * sizeof(float));
+            h->far_pool_acc.alloc((size_t)std::max<long long>(foff, 16) * sizeof(float), s);
             RAD_CUDA(cudaMemsetAsync(h->far_pool_acc.p, 0, h->far_pool_acc.bytes, s));
             launch_factor_fill<CT, float>(h, uwork, vwork, Us, Vs, s, h->far_pool_acc.p);
         }
@@ -851,6 +937,8 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     h->far_u_entries = far_u;
     h->far_v_entries = far_v;
     h->far_entries = far_u + far_v;
+    hs_up.reset();
+    HostScope hs_sync("host_compress_final_wait");
     RAD_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -877,6 +965,7 @@ void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     // ACA arithmetic: FP64 for the FP64 path and for tolerances below 1e-6
     // (near FP32 resolution); FP32 otherwise (hi/lo centroid differences,
     // two-sum running norm).
+    StageScope stage;
     if (p->near_dtype == RAD_F64 || p->tol < 1e-6) compress_t<double>(h, p, s);
     else compress_t<float>(h, p, s);
     h->compressed = true;
@@ -889,7 +978,7 @@ void load_dense_operator(rad_htree* h, const double* F_dev, cudaStream_t s) {
     h->blocks.assign(1, BlockH{0, 0, 0, n, 0, n, 0, -1, -1, 0});
     std::vector<int> tile_at;
     make_tiles(h, h->tiles_h, tile_at);
-    std::vector<std::vector<int>> xi(h->tiles_h.size()), ti(h->tiles_h.size());
+    std::vector<IdxRun> near_runs, far_runs;
     h->near_pieces.clear();
     h->far_pieces.clear();
     h->groups_h.clear();
@@ -901,14 +990,14 @@ void load_dense_operator(rad_htree* h, const double* F_dev, cudaStream_t s) {
         tl.foff = 0;
         noff += round_up((long long)tl.ld * n, 16);
         h->near_pieces.push_back(Piece{0, (int)t, 0});
-        for (int c = 0; c < n; ++c) xi[t].push_back(c);
+        near_runs.push_back(IdxRun{(int)t, 0, 0, n});
     }
     h->sum_rank = 0;
     h->stored_near = noff;
     h->stored_far = 0;
-    h->near_pool.alloc(sizeof(double) * (size_t)std::max<long long>(noff, 16));
-    h->far_pool.alloc(16 * sizeof(double));
-    upload_operator(h, xi, ti, s);
+    h->near_pool.alloc(sizeof(double) * (size_t)std::max<long long>(noff, 16), s);
+    h->far_pool.alloc(16 * sizeof(double), s);
+    upload_operator(h, near_runs, far_runs, s);
     dim3 grid((unsigned)std::min<long long>(1024, ((long long)n * 64 + 255) / 256), (unsigned)h->tiles_h.size());
     { ProfScope ps_("dense_load", s); dense_from_matrix_kernel<<<grid, 256, 0, s>>>(n, h->d_tiles.as<Tile>(), F_dev, h->near_pool.as<double>()); }
     RAD_CHECK_LAUNCH();

@@ -1,3 +1,6 @@
+#include <algorithm>
+#include <exception>
+#include <chrono>
 // C ABI entry points of librad (declared in include/rad.h).  Every entry
 // point catches all C++ exceptions and turns them into status codes.
 
@@ -27,7 +30,8 @@ namespace {
 std::atomic<long long> g_launches{0};
 struct ProfRec {
     const char* name;
-    cudaEvent_t a, b;
+    cudaEvent_t a, b;    // null for a host phase
+    double host_ms;
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
@@ -44,7 +48,7 @@ bool profiling_enabled() {
 ProfScope::ProfScope(const char* name, cudaStream_t st) : s(st) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on) return;
-    ProfRec r{name, nullptr, nullptr};
+    ProfRec r{name, nullptr, nullptr, 0.0};
     if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
         (void)cudaGetLastError();
         return;
@@ -59,10 +63,58 @@ ProfScope::~ProfScope() {
     if (idx < (int)g_prof.size()) cudaEventRecord(g_prof[idx].b, s);
 }
 
+HostScope::HostScope(const char* n) : name(n), t0(std::chrono::steady_clock::now()) {}
+HostScope::~HostScope() {
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (g_prof_on) g_prof.push_back(ProfRec{name, nullptr, nullptr, ms});
+}
+
+// ------------------------------------------------------------ staging
+namespace {
+struct StageState {
+    int depth = 0;
+    char* cur = nullptr;
+    size_t cap = 0, off = 0;
+    std::vector<char*> retired;   // outgrown blocks, freed when the scope ends
+};
+thread_local StageState g_stage;
+}  // namespace
+
+StageScope::StageScope() { ++g_stage.depth; }
+StageScope::~StageScope() {
+    if (--g_stage.depth > 0) return;
+    // unwinding from an error: copies may still be in flight
+    if (std::uncaught_exceptions() > 0) (void)cudaDeviceSynchronize();
+    for (char* p : g_stage.retired) cudaFreeHost(p);
+    g_stage.retired.clear();
+    g_stage.off = 0;
+}
+void* stage_alloc(size_t bytes) {
+    StageState& st = g_stage;
+    if (st.depth == 0) return nullptr;
+    const size_t need = (bytes + 255) / 256 * 256;
+    if (st.off + need > st.cap) {
+        const size_t cap = std::max<size_t>({need, 2 * st.cap, 16u << 20});
+        char* p = nullptr;
+        if (cudaMallocHost(&p, cap) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;   // fall back to a pageable copy
+        }
+        if (st.cur) st.retired.push_back(st.cur);
+        st.cur = p;
+        st.cap = cap;
+        st.off = 0;
+    }
+    void* r = st.cur + st.off;
+    st.off += need;
+    return r;
+}
+
 static void clear_profile() {
     for (auto& r : g_prof) {
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
+        if (r.a) cudaEventDestroy(r.a);
+        if (r.b) cudaEventDestroy(r.b);
     }
     g_prof.clear();
 }
@@ -90,14 +142,14 @@ static void keep_pool_warm() {
     done.push_back(dev);
 }
 
-void DevBuf::alloc(size_t b) {
-    release();
+void DevBuf::alloc(size_t b, cudaStream_t s) {
+    release(s);
     if (b == 0) return;
-    RAD_CUDA(cudaMalloc(&p, b));
+    RAD_CUDA(cudaMallocAsync(&p, b, s));
     bytes = b;
 }
-void DevBuf::release() {
-    if (p) cudaFree(p);
+void DevBuf::release(cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
     bytes = 0;
 }
@@ -186,8 +238,8 @@ int rad_profile_read(int32_t max_kernels, char* names, int64_t* counts, double* 
     std::lock_guard<std::mutex> lk(g_prof_mu);
     std::map<std::string, std::pair<int64_t, double>> agg;
     for (auto& r : g_prof) {
-        float ms = 0.0f;
-        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+        float ms = (float)r.host_ms;
+        if (r.a && (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)) {
             (void)cudaGetLastError();
             continue;
         }
@@ -273,8 +325,8 @@ int rad_htree_from_dense(int64_t n, const double* F, void* stream, rad_htree** o
         h->depth = 1;
         h->perm_h.resize(n);
         for (int i = 0; i < (int)n; ++i) h->perm_h[i] = i;
-        h->perm.alloc(sizeof(int) * n);
-        h->iperm.alloc(sizeof(int) * n);
+        h->perm.alloc(sizeof(int) * n, s);
+        h->iperm.alloc(sizeof(int) * n, s);
         h2d(h->perm.as<int>(), h->perm_h, s);
         h2d(h->iperm.as<int>(), h->perm_h, s);
         Scratch ws(s);

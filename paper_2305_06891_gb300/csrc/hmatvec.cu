@@ -74,50 +74,45 @@ template <> struct Vec4<__nv_bfloat16, float> {
 template <class FS, class AT>
 __global__ void __launch_bounds__(256) far_vt_single(OpView op, const AT* __restrict__ x, AT* __restrict__ T) {
     __shared__ AT part[1024];
-    const Group gr = op.groups[blockIdx.x];
-    // each thread owns 4 consecutive rows of a column (one vector load);
-    // rq row quads per pass, G = 256 / rq column phases
-    const int quads = gr.ld / 4;
-    const int rq = min(256, quads);
-    const int G = 256 / rq;
-    const int q = threadIdx.x % rq, jg = threadIdx.x / rq;
+    const GWork w = op.sitems[blockIdx.x];
+    const Group gr = op.groups[w.g];
+    // each thread owns 4 consecutive rows of the item (one vector load) and
+    // every G-th column of the group
+    const int quads = (w.rows + 3) / 4;
+    const int G = 256 / quads;
+    const int q = threadIdx.x % quads, jg = threadIdx.x / quads;
     const long long ld = gr.ld;
     const AT* xv = x + gr.c0;
-    for (int q0 = 0; q0 < quads; q0 += rq) {
-        AT acc[4] = {0, 0, 0, 0};
-        if (q0 + q < quads && jg < G) {
-            const FS* P = static_cast<const FS*>(op.far_pool) + gr.voff + 4 * (q0 + q);
-            int j = jg;
-            for (; j + 3 * G < gr.n; j += 4 * G) {
-                AT v0[4], v1[4], v2[4], v3[4];
-                Vec4<FS, AT>::load(P + j * ld, v0);
-                Vec4<FS, AT>::load(P + (j + G) * ld, v1);
-                Vec4<FS, AT>::load(P + (j + 2 * G) * ld, v2);
-                Vec4<FS, AT>::load(P + (j + 3 * G) * ld, v3);
-                const AT x0 = xv[j], x1 = xv[j + G], x2 = xv[j + 2 * G], x3 = xv[j + 3 * G];
+    AT acc[4] = {0, 0, 0, 0};
+    if (jg < G) {
+        const FS* P = static_cast<const FS*>(op.far_pool) + gr.voff + w.r0 + 4 * q;
+        int j = jg;
+        for (; j + 3 * G < gr.n; j += 4 * G) {
+            AT v0[4], v1[4], v2[4], v3[4];
+            Vec4<FS, AT>::load(P + j * ld, v0);
+            Vec4<FS, AT>::load(P + (j + G) * ld, v1);
+            Vec4<FS, AT>::load(P + (j + 2 * G) * ld, v2);
+            Vec4<FS, AT>::load(P + (j + 3 * G) * ld, v3);
+            const AT x0 = xv[j], x1 = xv[j + G], x2 = xv[j + 2 * G], x3 = xv[j + 3 * G];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) acc[r] += (v0[r] * x0 + v1[r] * x1) + (v2[r] * x2 + v3[r] * x3);
-            }
-            for (; j < gr.n; j += G) {
-                AT v0[4];
-                Vec4<FS, AT>::load(P + j * ld, v0);
-                const AT x0 = xv[j];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) acc[r] += v0[r] * x0;
-            }
+            for (int r = 0; r < 4; ++r) acc[r] += (v0[r] * x0 + v1[r] * x1) + (v2[r] * x2 + v3[r] * x3);
         }
+        for (; j < gr.n; j += G) {
+            AT v0[4];
+            Vec4<FS, AT>::load(P + j * ld, v0);
+            const AT x0 = xv[j];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) part[4 * threadIdx.x + r] = acc[r];
-        __syncthreads();
-        for (int rr = threadIdx.x; rr < 4 * rq; rr += 256) {
-            const int row = 4 * q0 + rr;
-            if (row < gr.M) {
-                AT s = 0;
-                for (int g = 0; g < G; ++g) s += part[4 * (g * rq) + rr];
-                T[gr.toff + row] = s;
-            }
+            for (int r = 0; r < 4; ++r) acc[r] += v0[r] * x0;
         }
-        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) part[4 * threadIdx.x + r] = acc[r];
+    __syncthreads();
+    if ((int)threadIdx.x < w.rows) {
+        const int rr = threadIdx.x;
+        AT sum = 0;
+        for (int g = 0; g < G; ++g) sum += part[4 * (g * quads) + rr];
+        T[gr.toff + w.r0 + rr] = sum;
     }
 }
 
@@ -150,7 +145,7 @@ template <class NS, class FS, class AT>
 __global__ void __launch_bounds__(256)
 rows_single(OpView op, const AT* __restrict__ x, const AT* __restrict__ T, void* Y, Epi epi) {
     __shared__ AT part[1024];
-    const Tile t = op.tiles[blockIdx.x];
+    const Tile t = op.tiles[op.torder[blockIdx.x]];
     // thread (q, g): rows 4q .. 4q+3, panel columns g, g + G, ...
     const int quads = t.ld / 4;
     const int G = 256 / quads;
@@ -180,44 +175,40 @@ template <class FS, class AT, int NCOL>
 __global__ void __launch_bounds__(256) far_vt_stream(OpView op, const AT* __restrict__ X, int ldx,
                                                      AT* __restrict__ T, int ldt) {
     __shared__ AT part[NCOL][1024];
-    const Group gr = op.groups[blockIdx.x];
-    const int quads = gr.ld / 4;
-    const int rq = min(256, quads);
-    const int G = 256 / rq;
-    const int q = threadIdx.x % rq, jg = threadIdx.x / rq;
+    const GWork w = op.sitems[blockIdx.x];
+    const Group gr = op.groups[w.g];
+    const int quads = (w.rows + 3) / 4;
+    const int G = 256 / quads;
+    const int q = threadIdx.x % quads, jg = threadIdx.x / quads;
     const long long ld = gr.ld;
-    for (int q0 = 0; q0 < quads; q0 += rq) {
-        AT acc[NCOL][4] = {};
-        if (q0 + q < quads && jg < G) {
-            const FS* P = static_cast<const FS*>(op.far_pool) + gr.voff + 4 * (q0 + q);
-            for (int j = jg; j < gr.n; j += G) {
-                AT v[4];
-                Vec4<FS, AT>::load(P + j * ld, v);
-                const AT* xr = X + (long long)(gr.c0 + j) * ldx;
+    AT acc[NCOL][4] = {};
+    if (jg < G) {
+        const FS* P = static_cast<const FS*>(op.far_pool) + gr.voff + w.r0 + 4 * q;
+        for (int j = jg; j < gr.n; j += G) {
+            AT v[4];
+            Vec4<FS, AT>::load(P + j * ld, v);
+            const AT* xr = X + (long long)(gr.c0 + j) * ldx;
 #pragma unroll
-                for (int c = 0; c < NCOL; ++c) {
-                    const AT xc = xr[c];
+            for (int c = 0; c < NCOL; ++c) {
+                const AT xc = xr[c];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) acc[c][r] += v[r] * xc;
-                }
+                for (int r = 0; r < 4; ++r) acc[c][r] += v[r] * xc;
             }
         }
+    }
 #pragma unroll
-        for (int c = 0; c < NCOL; ++c)
+    for (int c = 0; c < NCOL; ++c)
 #pragma unroll
-            for (int r = 0; r < 4; ++r) part[c][4 * threadIdx.x + r] = acc[c][r];
-        __syncthreads();
-        for (int rr = threadIdx.x; rr < 4 * rq; rr += 256) {
-            const int row = 4 * q0 + rr;
-            if (row < gr.M)
+        for (int r = 0; r < 4; ++r) part[c][4 * threadIdx.x + r] = acc[c][r];
+    __syncthreads();
+    if ((int)threadIdx.x < w.rows) {
+        const int rr = threadIdx.x;
 #pragma unroll
-                for (int c = 0; c < NCOL; ++c) {
-                    AT sum = 0;
-                    for (int g = 0; g < G; ++g) sum += part[c][4 * (g * rq) + rr];
-                    T[(long long)(gr.toff + row) * ldt + c] = sum;
-                }
+        for (int c = 0; c < NCOL; ++c) {
+            AT sum = 0;
+            for (int g = 0; g < G; ++g) sum += part[c][4 * (g * quads) + rr];
+            T[(long long)(gr.toff + w.r0 + rr) * ldt + c] = sum;
         }
-        __syncthreads();
     }
 }
 
@@ -243,7 +234,7 @@ __global__ void __launch_bounds__(256)
 rows_stream(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ T, int ldt, void* Y, int ldy,
             Epi epi) {
     __shared__ AT part[NCOL][1024];
-    const Tile t = op.tiles[blockIdx.x];
+    const Tile t = op.tiles[op.torder[blockIdx.x]];
     const int quads = t.ld / 4;
     const int G = 256 / quads;
     const int q = threadIdx.x % quads, g = threadIdx.x / quads;
@@ -303,53 +294,48 @@ __global__ void to_df_kernel(const double* __restrict__ X, int ldx, int n, int n
 template <int NCOL>
 __global__ void __launch_bounds__(256) far_vt_df(OpView op, const DF* __restrict__ X, DF* __restrict__ T) {
     __shared__ DF part[NCOL][1024];
-    const Group gr = op.groups[blockIdx.x];
-    const int quads = gr.ld / 4;
-    const int rq = min(128, quads);
-    const int G = 256 / rq;
-    const int q = threadIdx.x % rq, jg = threadIdx.x / rq;
+    const GWork w = op.sitems[blockIdx.x];
+    const Group gr = op.groups[w.g];
+    const int quads = (w.rows + 3) / 4;
+    const int G = 256 / quads;
+    const int q = threadIdx.x % quads, jg = threadIdx.x / quads;
     const long long ld = gr.ld;
-    for (int q0 = 0; q0 < quads; q0 += rq) {
-        DF acc[NCOL][4];
+    DF acc[NCOL][4];
 #pragma unroll
-        for (int c = 0; c < NCOL; ++c)
+    for (int c = 0; c < NCOL; ++c)
 #pragma unroll
-            for (int r = 0; r < 4; ++r) acc[c][r] = DF{0.0f, 0.0f};
-        if (q0 + q < quads && jg < G) {
-            const float* P = static_cast<const float*>(op.far_pool) + gr.voff + 4 * (q0 + q);
-            for (int j = jg; j < gr.n; j += G) {
-                float v[4];
-                Vec4<float, float>::load(P + j * ld, v);
-                const DF* xr = X + (long long)(gr.c0 + j) * NCOL;
+        for (int r = 0; r < 4; ++r) acc[c][r] = DF{0.0f, 0.0f};
+    if (jg < G) {
+        const float* P = static_cast<const float*>(op.far_pool) + gr.voff + w.r0 + 4 * q;
+        for (int j = jg; j < gr.n; j += G) {
+            float v[4];
+            Vec4<float, float>::load(P + j * ld, v);
+            const DF* xr = X + (long long)(gr.c0 + j) * NCOL;
 #pragma unroll
-                for (int c = 0; c < NCOL; ++c) {
-                    const DF xc = xr[c];
+            for (int c = 0; c < NCOL; ++c) {
+                const DF xc = xr[c];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) df_fma(acc[c][r], v[r], xc);
-                }
+                for (int r = 0; r < 4; ++r) df_fma(acc[c][r], v[r], xc);
             }
         }
-        if (jg < G)
+    }
 #pragma unroll
-            for (int c = 0; c < NCOL; ++c)
+    for (int c = 0; c < NCOL; ++c)
 #pragma unroll
-                for (int r = 0; r < 4; ++r) part[c][4 * threadIdx.x + r] = df_norm(acc[c][r]);
-        __syncthreads();
-        for (int rr = threadIdx.x; rr < 4 * rq; rr += 256) {
-            const int row = 4 * q0 + rr;
-            if (row < gr.M)
+        for (int r = 0; r < 4; ++r) part[c][4 * threadIdx.x + r] = df_norm(acc[c][r]);
+    __syncthreads();
+    if ((int)threadIdx.x < w.rows) {
+        const int rr = threadIdx.x;
 #pragma unroll
-                for (int c = 0; c < NCOL; ++c) {
-                    double sum = 0.0;
-                    for (int g = 0; g < G; ++g) {
-                        const DF d = part[c][4 * (g * rq) + rr];
-                        sum += (double)d.h + (double)d.l;
-                    }
-                    const float h = __double2float_rn(sum);
-                    T[(long long)(gr.toff + row) * NCOL + c] = DF{h, __double2float_rn(sum - (double)h)};
-                }
+        for (int c = 0; c < NCOL; ++c) {
+            double sum = 0.0;
+            for (int g = 0; g < G; ++g) {
+                const DF d = part[c][4 * (g * quads) + rr];
+                sum += (double)d.h + (double)d.l;
+            }
+            const float hi = __double2float_rn(sum);
+            T[(long long)(gr.toff + w.r0 + rr) * NCOL + c] = DF{hi, __double2float_rn(sum - (double)hi)};
         }
-        __syncthreads();
     }
 }
 
@@ -374,7 +360,7 @@ template <int NCOL>
 __global__ void __launch_bounds__(256)
 rows_df(OpView op, const DF* __restrict__ X, const DF* __restrict__ T, double* Y, int ldy, Epi epi) {
     __shared__ DF part[NCOL][1024];
-    const Tile t = op.tiles[blockIdx.x];
+    const Tile t = op.tiles[op.torder[blockIdx.x]];
     const int quads = t.ld / 4;
     const int G = 256 / quads;
     const int q = threadIdx.x % quads, g = threadIdx.x / quads;
@@ -568,7 +554,7 @@ __global__ void __launch_bounds__(256, 3)
 rows_multi(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ T, int ldt, void* Y, int ldy, int nc,
            Epi epi) {
     extern __shared__ __align__(128) unsigned char dsm[];
-    const Tile t = op.tiles[blockIdx.x];
+    const Tile t = op.tiles[op.torder[blockIdx.x]];
     const int RG = t.ld / 4, CG = 256 / RG;
     AT acc[4][RN];
 #pragma unroll
@@ -629,7 +615,7 @@ template <class NS, class FS, class AT, int NCOL>
 void launch_stream(const rad_htree* h, const OpView& op, const AT* X, int ldx, AT* T, int ldt, void* Y, int ldy,
                    const Epi& epi, cudaStream_t s) {
     if (op.n_gwork > 0) {
-        { ProfScope ps_("hmv_far_vt", s); far_vt_stream<FS, AT, NCOL><<<(unsigned)h->groups_h.size(), 256, 0, s>>>(op, X, ldx, T, ldt); }
+        { ProfScope ps_("hmv_far_vt", s); far_vt_stream<FS, AT, NCOL><<<(unsigned)op.n_sitems, 256, 0, s>>>(op, X, ldx, T, ldt); }
         RAD_CHECK_LAUNCH();
     }
     { ProfScope ps_("hmv_rows", s); rows_stream<NS, FS, AT, NCOL><<<op.n_tiles, 256, 0, s>>>(op, X, ldx, T, ldt, Y, ldy, epi); }
@@ -647,7 +633,7 @@ void launch_df(const rad_htree* h, const OpView& op, const double* X, int ldx, d
     { ProfScope ps_("permute", s); to_df_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(X, ldx, n, NCOL, Xd); }
     RAD_CHECK_LAUNCH();
     if (op.n_gwork > 0) {
-        { ProfScope ps_("hmv_far_vt", s); far_vt_df<NCOL><<<(unsigned)h->groups_h.size(), 256, 0, s>>>(op, Xd, Td); }
+        { ProfScope ps_("hmv_far_vt", s); far_vt_df<NCOL><<<(unsigned)op.n_sitems, 256, 0, s>>>(op, Xd, Td); }
         RAD_CHECK_LAUNCH();
     }
     { ProfScope ps_("hmv_rows", s); rows_df<NCOL><<<op.n_tiles, 256, 0, s>>>(op, Xd, Td, Y, ldy, epi); }
@@ -659,7 +645,7 @@ void apply_t(const rad_htree* h, const OpView& op, const AT* X, int ldx, void* Y
              AT* T, cudaStream_t s) {
     if (nrhs == 1) {
         if (op.n_gwork > 0) {
-            { ProfScope ps_("hmv_far_vt", s); far_vt_single<FS, AT><<<(unsigned)h->groups_h.size(), 256, 0, s>>>(op, X, T); }
+            { ProfScope ps_("hmv_far_vt", s); far_vt_single<FS, AT><<<(unsigned)op.n_sitems, 256, 0, s>>>(op, X, T); }
             RAD_CHECK_LAUNCH();
         }
         { ProfScope ps_("hmv_rows", s); rows_single<NS, FS, AT><<<op.n_tiles, 256, 0, s>>>(op, X, T, Y, epi); }

@@ -1,10 +1,13 @@
 // Internal declarations shared by the librad translation units.
 #pragma once
 
+#include <chrono>
+
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -50,22 +53,36 @@ struct ProfScope {
     ProfScope& operator=(const ProfScope&) = delete;
 };
 
+// Host wall time of a phase (names start with "host_"), recorded beside the
+// kernel times while profiling is on.
+struct HostScope {
+    const char* name;
+    std::chrono::steady_clock::time_point t0;
+    explicit HostScope(const char* n);
+    ~HostScope();
+    HostScope(const HostScope&) = delete;
+    HostScope& operator=(const HostScope&) = delete;
+};
+
 #define RAD_REQUIRE(cond, code, msg)          \
     do {                                      \
         if (!(cond)) ::rad::fail(code, msg);  \
     } while (0)
 
 // ------------------------------------------------------------ memory helpers
-// A device buffer owned by a handle; released with cudaFree.
+// A device buffer owned by a handle, from the stream-ordered memory pool.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
-    ~DevBuf() { release(); }
-    void alloc(size_t b);
-    void release();
+    ~DevBuf() { release(nullptr); }
+    // Stream-ordered allocation from the device's default memory pool (kept
+    // warm, so a repeated build/compress does not map new pages); release
+    // frees in the order of stream `s`.
+    void alloc(size_t b, cudaStream_t s);
+    void release(cudaStream_t s);
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
@@ -88,9 +105,31 @@ template <class T>
 const T* to_device_t(const T* p, size_t n, Scratch& ws) {
     return static_cast<const T*>(to_device(p, n * sizeof(T), ws));
 }
+// Page-locked staging for the host-to-device uploads of one call (per host
+// thread).  While a StageScope is alive, h2d() copies through page-locked
+// memory, so the copies are asynchronous DMA instead of staged pageable
+// copies.  The code holding the scope synchronises its stream before the
+// scope ends (tree build and compression do), so the staging memory is free
+// for the next call.
+struct StageScope {
+    StageScope();
+    ~StageScope();
+    StageScope(const StageScope&) = delete;
+    StageScope& operator=(const StageScope&) = delete;
+};
+void* stage_alloc(size_t bytes);   // nullptr when no scope is active
+
 template <class T>
 void h2d(T* dst, const std::vector<T>& v, cudaStream_t s) {
-    if (!v.empty()) RAD_CUDA(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    if (v.empty()) return;
+    const size_t bytes = v.size() * sizeof(T);
+    void* st = bytes >= 4096 ? stage_alloc(bytes) : nullptr;
+    if (st) {
+        std::memcpy(st, v.data(), bytes);
+        RAD_CUDA(cudaMemcpyAsync(dst, st, bytes, cudaMemcpyHostToDevice, s));
+    } else {
+        RAD_CUDA(cudaMemcpyAsync(dst, v.data(), bytes, cudaMemcpyHostToDevice, s));
+    }
 }
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -196,12 +235,22 @@ struct OpView {
     const GWork* gwork;
     const Group* groups;
     int sum_rank;
+    int n_sitems;           // far-field items of <= kStreamRows rows for 1-4 columns
+    const GWork* sitems;
+    const int* torder;      // launch order of the row tiles (heaviest first)
 };
+
+// Rows per far-field item of the streaming (1-4 column) products.
+constexpr int kStreamRows = 128;
 
 }  // namespace rad
 
 // The opaque handle (global namespace: it is the C type rad_htree).
 struct rad_htree {
+    // The arrays below may still be read by work queued on any stream when
+    // the handle goes away (rad_htree_free, or a call that failed half way):
+    // wait for the device before they return to the pool.
+    ~rad_htree() { (void)cudaDeviceSynchronize(); }
     int64_t n = 0;
     int leaf_size = 0;
     double eta = 0.0;
@@ -233,7 +282,8 @@ struct rad_htree {
     rad::DevBuf near_pool, far_pool;
     rad::DevBuf far_pool_acc;          // FP32 factors kept for refinement
     bool has_accurate = false;         // an accurate operator exists
-    rad::DevBuf d_tiles, d_xidx, d_tidx, d_gwork, d_groups;
+    rad::DevBuf d_tiles, d_xidx, d_tidx, d_gwork, d_groups, d_sitems, d_torder;
+    int n_sitems = 0;
     int n_tiles = 0;
     int n_gwork = 0;
     int sum_rank = 0;
@@ -255,6 +305,9 @@ struct rad_htree {
         v.gwork = d_gwork.as<rad::GWork>();
         v.groups = d_groups.as<rad::Group>();
         v.sum_rank = sum_rank;
+        v.n_sitems = n_sitems;
+        v.sitems = d_sitems.as<rad::GWork>();
+        v.torder = d_torder.as<int>();
         return v;
     }
     bool op_is_f64() const { return near_dtype == RAD_F64; }

@@ -381,6 +381,8 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     const int leaf = h->leaf_size;
     // cluster shapes, breadth first: Algorithm 1's recursion on sizes only
     std::vector<NodeShape>& nodes = h->nodes;
+    HostScope hs_shapes("host_tree_shapes");
+    StageScope stage;
     nodes.clear();
     nodes.push_back(NodeShape{0, n, 0, -1, -1, n <= leaf ? 1 : 0});
     for (size_t q = 0; q < nodes.size(); ++q) {
@@ -426,18 +428,19 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     }
     int* perm_final = idx[depth & 1];
 
-    h->perm.alloc(sizeof(int) * n);
-    h->iperm.alloc(sizeof(int) * n);
-    h->geo.alloc(sizeof(double) * 7 * (size_t)n);
+    h->perm.alloc(sizeof(int) * n, s);
+    h->iperm.alloc(sizeof(int) * n, s);
+    h->geo.alloc(sizeof(double) * 7 * (size_t)n, s);
     RAD_CUDA(cudaMemcpyAsync(h->perm.p, perm_final, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
     { ProfScope ps_("geometry", s); gather_geo_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, geo_user, perm_final, h->geo.as<double>(),
                                                       h->iperm.as<int>()); }
     RAD_CHECK_LAUNCH();
-    h->geo32.alloc(sizeof(float) * 10 * (size_t)n);
+    h->geo32.alloc(sizeof(float) * 10 * (size_t)n, s);
     { ProfScope ps_("geometry", s); geo32_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, h->geo.as<double>(), h->geo32.as<float>()); }
     RAD_CHECK_LAUNCH();
 
     // block tree: single CTA, retry with larger buffers on overflow
+    HostScope hs_blocks("host_block_tree_wait");
     const int base_cap = (int)std::min<int64_t>(1 << 28, 160ll * (n / std::max(1, leaf) + 1) + 4096);
     int cap = base_cap;
     std::vector<int2> far_pairs, near_pairs;
@@ -478,6 +481,7 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     RAD_CUDA(cudaStreamSynchronize(s));
     RAD_REQUIRE(herr == 0, RAD_ECUDA, "internal error in the cluster-tree partition");
 
+    HostScope hs_sort("host_block_list");
     std::vector<BlockH>& blocks = h->blocks;
     blocks.clear();
     blocks.reserve(far_pairs.size() + near_pairs.size());
@@ -488,9 +492,17 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     };
     for (auto pr : far_pairs) add(pr, 1);
     for (auto pr : near_pairs) add(pr, 0);
-    std::sort(blocks.begin(), blocks.end(), [](const BlockH& x, const BlockH& y) {
-        return x.r0 != y.r0 ? x.r0 < y.r0 : x.c0 < y.c0;
-    });
+    // order by (r0, c0): two stable counting passes over the cluster starts
+    // (c0 first, then r0); (r0, c0) identifies a block uniquely
+    std::vector<int> cnt(n + 2);
+    std::vector<BlockH> tmp(blocks.size());
+    for (int pass = 0; pass < 2; ++pass) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (auto& b : blocks) ++cnt[(pass ? b.r0 : b.c0) + 1];
+        for (int i = 0; i <= n; ++i) cnt[i + 1] += cnt[i];
+        for (auto& b : blocks) tmp[cnt[pass ? b.r0 : b.c0]++] = b;
+        blocks.swap(tmp);
+    }
     h->n_admissible = (int64_t)far_pairs.size();
 }
 
