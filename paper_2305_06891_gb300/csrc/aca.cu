@@ -713,6 +713,30 @@ static void upload_operator(rad_htree* h, const std::vector<IdxRun>& near_runs, 
         tkey[t] = (long long)tl.ld * (tl.kn + tl.kf);
     }
     const std::vector<int> torder = order_desc(tkey);
+    // phase A / phase B orders of the one-column product
+    std::vector<long long> akey;
+    std::vector<int> acode;
+    for (size_t i = 0; i < sitems.size(); ++i) {
+        akey.push_back((long long)sitems[i].rows * G[sitems[i].g].n);
+        acode.push_back((int)i);
+    }
+    for (size_t t = 0; t < h->tiles_h.size(); ++t) {
+        akey.push_back((long long)h->tiles_h[t].ld * h->tiles_h[t].kn);
+        acode.push_back(-(int)t - 1);
+    }
+    std::vector<int> aorder(acode.size());
+    {
+        const std::vector<int> o = order_desc(akey);
+        for (size_t i = 0; i < o.size(); ++i) aorder[i] = acode[o[i]];
+    }
+    std::vector<long long> fkey(h->tiles_h.size());
+    for (size_t t = 0; t < fkey.size(); ++t) fkey[t] = (long long)h->tiles_h[t].ld * h->tiles_h[t].kf;
+    const std::vector<int> forder = order_desc(fkey);
+    h->n_aitems = (int)aorder.size();
+    h->d_aorder.alloc(sizeof(int) * std::max<size_t>(1, aorder.size()), s);
+    h->d_forder.alloc(sizeof(int) * std::max<size_t>(1, forder.size()), s);
+    h2d(h->d_aorder.as<int>(), aorder, s);
+    h2d(h->d_forder.as<int>(), forder, s);
     h->n_tiles = (int)h->tiles_h.size();
     h->n_gwork = (int)gwork.size();
     h->n_sitems = (int)sitems.size();

@@ -71,51 +71,6 @@ template <> struct Vec4<__nv_bfloat16, float> {
     }
 };
 
-template <class FS, class AT>
-__global__ void __launch_bounds__(256) far_vt_single(OpView op, const AT* __restrict__ x, AT* __restrict__ T) {
-    __shared__ AT part[1024];
-    const GWork w = op.sitems[blockIdx.x];
-    const Group gr = op.groups[w.g];
-    // each thread owns 4 consecutive rows of the item (one vector load) and
-    // every G-th column of the group
-    const int quads = (w.rows + 3) / 4;
-    const int G = 256 / quads;
-    const int q = threadIdx.x % quads, jg = threadIdx.x / quads;
-    const long long ld = gr.ld;
-    const AT* xv = x + gr.c0;
-    AT acc[4] = {0, 0, 0, 0};
-    if (jg < G) {
-        const FS* P = static_cast<const FS*>(op.far_pool) + gr.voff + w.r0 + 4 * q;
-        int j = jg;
-        for (; j + 3 * G < gr.n; j += 4 * G) {
-            AT v0[4], v1[4], v2[4], v3[4];
-            Vec4<FS, AT>::load(P + j * ld, v0);
-            Vec4<FS, AT>::load(P + (j + G) * ld, v1);
-            Vec4<FS, AT>::load(P + (j + 2 * G) * ld, v2);
-            Vec4<FS, AT>::load(P + (j + 3 * G) * ld, v3);
-            const AT x0 = xv[j], x1 = xv[j + G], x2 = xv[j + 2 * G], x3 = xv[j + 3 * G];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[r] += (v0[r] * x0 + v1[r] * x1) + (v2[r] * x2 + v3[r] * x3);
-        }
-        for (; j < gr.n; j += G) {
-            AT v0[4];
-            Vec4<FS, AT>::load(P + j * ld, v0);
-            const AT x0 = xv[j];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[r] += v0[r] * x0;
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) part[4 * threadIdx.x + r] = acc[r];
-    __syncthreads();
-    if ((int)threadIdx.x < w.rows) {
-        const int rr = threadIdx.x;
-        AT sum = 0;
-        for (int g = 0; g < G; ++g) sum += part[4 * (g * quads) + rr];
-        T[gr.toff + w.r0 + rr] = sum;
-    }
-}
-
 // acc[0..3] += sum over panel columns c = g, g + G, ... of the 4 rows at P
 // of column c times v[idx[c]]
 template <class S, class AT>
@@ -138,33 +93,6 @@ __device__ __forceinline__ void stream_panel4(const S* __restrict__ P, long long
         const AT x0 = v[idx[c]];
 #pragma unroll
         for (int r = 0; r < 4; ++r) acc[r] += a0[r] * x0;
-    }
-}
-
-template <class NS, class FS, class AT>
-__global__ void __launch_bounds__(256)
-rows_single(OpView op, const AT* __restrict__ x, const AT* __restrict__ T, void* Y, Epi epi) {
-    __shared__ AT part[1024];
-    const Tile t = op.tiles[op.torder[blockIdx.x]];
-    // thread (q, g): rows 4q .. 4q+3, panel columns g, g + G, ...
-    const int quads = t.ld / 4;
-    const int G = 256 / quads;
-    const int q = threadIdx.x % quads, g = threadIdx.x / quads;
-    AT acc[4] = {0, 0, 0, 0};
-    if (g < G) {
-        stream_panel4<NS, AT>(static_cast<const NS*>(op.near_pool) + t.noff + 4 * q, t.ld, t.kn, g, G,
-                              op.xidx + t.ixn, x, acc);
-        stream_panel4<FS, AT>(static_cast<const FS*>(op.far_pool) + t.foff + 4 * q, t.ld, t.kf, g, G,
-                              op.tidx + t.ixf, T, acc);
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) part[4 * threadIdx.x + r] = acc[r];
-    __syncthreads();
-    if ((int)threadIdx.x < t.rows) {
-        const int row = threadIdx.x;
-        AT s = 0;
-        for (int gg = 0; gg < G; ++gg) s += part[4 * (gg * quads) + row];
-        epilogue<AT>(epi, Y, 1, t.r0 + row, 0, s);
     }
 }
 
@@ -209,6 +137,97 @@ __global__ void __launch_bounds__(256) far_vt_stream(OpView op, const AT* __rest
             for (int g = 0; g < G; ++g) sum += part[c][4 * (g * quads) + rr];
             T[(long long)(gr.toff + w.r0 + rr) * ldt + c] = sum;
         }
+    }
+}
+
+// ---------------------------------------------------------------- 1 RHS, two phases
+// Phase A: far-field items (T = V^T x, at most 128 rows of a column group)
+// and the tiles' dense panels (Yn = near x) in one launch, heaviest first, so
+// that the short items fill the tail of the long ones.  Phase B: the tiles'
+// low-rank panels, Y = epilogue(Yn + U T).
+template <class NS, class FS, class AT>
+__global__ void __launch_bounds__(256)
+single_phase_a(OpView op, const AT* __restrict__ x, AT* __restrict__ T, AT* __restrict__ Yn) {
+    __shared__ AT part[1024];
+    const int code = op.aorder[blockIdx.x];
+    AT acc[4] = {0, 0, 0, 0};
+    int quads, G, rows;
+    if (code >= 0) {
+        const GWork w = op.sitems[code];
+        const Group gr = op.groups[w.g];
+        quads = (w.rows + 3) / 4;
+        G = 256 / quads;
+        rows = w.rows;
+        const int q = threadIdx.x % quads, jg = threadIdx.x / quads;
+        if (jg < G) {
+            const FS* P = static_cast<const FS*>(op.far_pool) + gr.voff + w.r0 + 4 * q;
+            const long long ld = gr.ld;
+            const AT* xv = x + gr.c0;
+            int j = jg;
+            for (; j + 3 * G < gr.n; j += 4 * G) {
+                AT v0[4], v1[4], v2[4], v3[4];
+                Vec4<FS, AT>::load(P + j * ld, v0);
+                Vec4<FS, AT>::load(P + (j + G) * ld, v1);
+                Vec4<FS, AT>::load(P + (j + 2 * G) * ld, v2);
+                Vec4<FS, AT>::load(P + (j + 3 * G) * ld, v3);
+                const AT x0 = xv[j], x1 = xv[j + G], x2 = xv[j + 2 * G], x3 = xv[j + 3 * G];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[r] += (v0[r] * x0 + v1[r] * x1) + (v2[r] * x2 + v3[r] * x3);
+            }
+            for (; j < gr.n; j += G) {
+                AT v0[4];
+                Vec4<FS, AT>::load(P + j * ld, v0);
+                const AT x0 = xv[j];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) acc[r] += v0[r] * x0;
+            }
+        }
+    } else {
+        const Tile t = op.tiles[-code - 1];
+        quads = t.ld / 4;
+        G = 256 / quads;
+        rows = t.rows;
+        const int q = threadIdx.x % quads, g = threadIdx.x / quads;
+        if (g < G)
+            stream_panel4<NS, AT>(static_cast<const NS*>(op.near_pool) + t.noff + 4 * q, t.ld, t.kn, g, G,
+                                  op.xidx + t.ixn, x, acc);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) part[4 * threadIdx.x + r] = acc[r];
+    __syncthreads();
+    if ((int)threadIdx.x < rows) {
+        const int rr = threadIdx.x;
+        AT sum = 0;
+        for (int g = 0; g < G; ++g) sum += part[4 * (g * quads) + rr];
+        if (code >= 0) {
+            const GWork w = op.sitems[code];
+            T[op.groups[w.g].toff + w.r0 + rr] = sum;
+        } else {
+            Yn[op.tiles[-code - 1].r0 + rr] = sum;
+        }
+    }
+}
+
+template <class FS, class AT>
+__global__ void __launch_bounds__(256)
+single_phase_b(OpView op, const AT* __restrict__ T, const AT* __restrict__ Yn, void* Y, Epi epi) {
+    __shared__ AT part[1024];
+    const Tile t = op.tiles[op.forder[blockIdx.x]];
+    const int quads = t.ld / 4;
+    const int G = 256 / quads;
+    const int q = threadIdx.x % quads, g = threadIdx.x / quads;
+    AT acc[4] = {0, 0, 0, 0};
+    if (g < G && t.kf > 0)
+        stream_panel4<FS, AT>(static_cast<const FS*>(op.far_pool) + t.foff + 4 * q, t.ld, t.kf, g, G,
+                              op.tidx + t.ixf, T, acc);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) part[4 * threadIdx.x + r] = acc[r];
+    __syncthreads();
+    if ((int)threadIdx.x < t.rows) {
+        const int row = threadIdx.x;
+        AT s = Yn[t.r0 + row];
+        for (int gg = 0; gg < G; ++gg) s += part[4 * (gg * quads) + row];
+        epilogue<AT>(epi, Y, 1, t.r0 + row, 0, s);
     }
 }
 
@@ -644,11 +663,10 @@ template <class NS, class FS, class AT>
 void apply_t(const rad_htree* h, const OpView& op, const AT* X, int ldx, void* Y, int ldy, int nrhs, const Epi& epi,
              AT* T, cudaStream_t s) {
     if (nrhs == 1) {
-        if (op.n_gwork > 0) {
-            { ProfScope ps_("hmv_far_vt", s); far_vt_single<FS, AT><<<(unsigned)op.n_sitems, 256, 0, s>>>(op, X, T); }
-            RAD_CHECK_LAUNCH();
-        }
-        { ProfScope ps_("hmv_rows", s); rows_single<NS, FS, AT><<<op.n_tiles, 256, 0, s>>>(op, X, T, Y, epi); }
+        AT* Yn = T + std::max(1, op.sum_rank);
+        { ProfScope ps_("hmv_phase_a", s); single_phase_a<NS, FS, AT><<<(unsigned)op.n_aitems, 256, 0, s>>>(op, X, T, Yn); }
+        RAD_CHECK_LAUNCH();
+        { ProfScope ps_("hmv_phase_b", s); single_phase_b<FS, AT><<<op.n_tiles, 256, 0, s>>>(op, T, Yn, Y, epi); }
         RAD_CHECK_LAUNCH();
         return;
     }
@@ -723,7 +741,8 @@ __global__ void scatter_kernel(int n, int nrhs, const TI* __restrict__ Y, int ld
 
 size_t apply_workspace_bytes(const rad_htree* h, int nrhs) {
     const size_t esz = h->op_is_f64() ? 8 : 4;
-    return esz * (size_t)std::max(1, h->sum_rank) * (size_t)tree_ld(nrhs);
+    // T = V^T X, plus the dense-panel partial sums of a one-column product
+    return esz * ((size_t)std::max(1, h->sum_rank) * (size_t)tree_ld(nrhs) + (nrhs == 1 ? (size_t)h->n : 0));
 }
 
 void apply_tree(const rad_htree* h, const void* X, int ldx, void* Y, int ldy, int nrhs, const Epi& epi,

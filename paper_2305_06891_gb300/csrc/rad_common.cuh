@@ -238,6 +238,13 @@ struct OpView {
     int n_sitems;           // far-field items of <= kStreamRows rows for 1-4 columns
     const GWork* sitems;
     const int* torder;      // launch order of the row tiles (heaviest first)
+    // one-column product in two launches: phase A runs the far-field items
+    // (code >= 0: sitems[code]) and the dense panels of the tiles (code < 0:
+    // tile -code-1) together, heaviest first; phase B the low-rank panels of
+    // the tiles in forder
+    int n_aitems;
+    const int* aorder;
+    const int* forder;
 };
 
 // Rows per far-field item of the streaming (1-4 column) products.
@@ -282,8 +289,9 @@ struct rad_htree {
     rad::DevBuf near_pool, far_pool;
     rad::DevBuf far_pool_acc;          // FP32 factors kept for refinement
     bool has_accurate = false;         // an accurate operator exists
-    rad::DevBuf d_tiles, d_xidx, d_tidx, d_gwork, d_groups, d_sitems, d_torder;
+    rad::DevBuf d_tiles, d_xidx, d_tidx, d_gwork, d_groups, d_sitems, d_torder, d_aorder, d_forder;
     int n_sitems = 0;
+    int n_aitems = 0;
     int n_tiles = 0;
     int n_gwork = 0;
     int sum_rank = 0;
@@ -308,6 +316,9 @@ struct rad_htree {
         v.n_sitems = n_sitems;
         v.sitems = d_sitems.as<rad::GWork>();
         v.torder = d_torder.as<int>();
+        v.n_aitems = n_aitems;
+        v.aorder = d_aorder.as<int>();
+        v.forder = d_forder.as<int>();
         return v;
     }
     bool op_is_f64() const { return near_dtype == RAD_F64; }
