@@ -163,6 +163,23 @@ int rad_build_htree_facets(int64_t n, const double* centroid, const double* norm
                            const double* area, const rad_tree_params* p,
                            void* stream, rad_htree** out);
 
+/* Batch of independent cavities in one handle (no counterpart in the
+ * paper, which treats one cavity): cavity c owns the next counts[c]
+ * triangles of verts (the cavities' triangles concatenated, 9 doubles each,
+ * host or device).  The cluster tree is a forest with one root per cavity
+ * (Algorithm 1 applied to each cavity) and the block tree (Algorithm 2)
+ * never pairs clusters of different cavities, whose mutual view factors
+ * are not part of any cavity's problem.  Every other call works on the
+ * batch as on one cavity: one ACA launch compresses all cavities' blocks,
+ * one product applies all of them, and the solvers (rad_solve_reflection,
+ * rad_solve_flux) keep Krylov subspaces, inner products and convergence
+ * tests per cavity and per right-hand side, so that each cavity's result
+ * is the one it would get alone up to rounding.  Vectors are the
+ * concatenation of the cavities' vectors (length sum(counts)).
+ *   n_cavities >= 1, counts[c] >= 1 (host array); RAD_EINVAL otherwise. */
+int rad_build_htree_batch(int32_t n_cavities, const int64_t* counts, const double* verts,
+                          const rad_tree_params* p, void* stream, rad_htree** out);
+
 /* Test hook: wraps a caller's dense n x n view-factor matrix F (row-major,
  * F[i*n + j] = F_ij, §3.2) as a single dense block stored in FP64, already
  * "compressed".  Lets closed-form pins (e.g. Eq. 5) drive rad_solve_flux. */

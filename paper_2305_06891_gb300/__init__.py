@@ -81,6 +81,7 @@ def _load():
         "rad_last_error": (C.c_char_p, []),
         "rad_build_htree": (C.c_int, [i64, vp, C.POINTER(_TreeParams), vp, C.POINTER(H)]),
         "rad_build_htree_facets": (C.c_int, [i64, vp, vp, vp, C.POINTER(_TreeParams), vp, C.POINTER(H)]),
+        "rad_build_htree_batch": (C.c_int, [i32, vp, vp, C.POINTER(_TreeParams), vp, C.POINTER(H)]),
         "rad_htree_from_dense": (C.c_int, [i64, vp, vp, C.POINTER(H)]),
         "rad_compress_aca": (C.c_int, [H, C.POINTER(_AcaParams), vp]),
         "rad_hmatvec": (C.c_int, [H, i32, vp, i64, vp, i64, i64, vp]),
@@ -230,6 +231,21 @@ def rad_build_htree(verts, leaf_size: int = 32, eta_adm: float = 1.0, stream=Non
     out = C.c_void_p()
     p = _TreeParams(int(leaf_size), 0, float(eta_adm))
     _check(_lib.rad_build_htree(n, _ptr(v), C.byref(p), _stream(stream, v), C.byref(out)))
+    return HTree(out.value, n)
+
+
+def rad_build_htree_batch(verts, counts, leaf_size: int = 32, eta_adm: float = 1.0, stream=None) -> HTree:
+    """A batch of cavities in one handle: ``verts`` (sum(counts), 3, 3) holds the
+    cavities' triangles one cavity after the other, ``counts`` their numbers."""
+    v = _f64_rowmajor(verts)
+    cnt = np.ascontiguousarray(np.asarray(counts, dtype=np.int64))
+    n = int(v.shape[0])
+    if int(cnt.sum()) != n:
+        raise ValueError("sum(counts) must equal the number of triangles")
+    out = C.c_void_p()
+    p = _TreeParams(int(leaf_size), 0, float(eta_adm))
+    _check(_lib.rad_build_htree_batch(int(cnt.size), cnt.ctypes.data, _ptr(v), C.byref(p), _stream(stream, v),
+                                      C.byref(out)))
     return HTree(out.value, n)
 
 

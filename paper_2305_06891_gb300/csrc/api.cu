@@ -284,6 +284,43 @@ int rad_build_htree(int64_t n, const double* verts, const rad_tree_params* p, vo
     });
 }
 
+int rad_build_htree_batch(int32_t n_cavities, const int64_t* counts, const double* verts, const rad_tree_params* p,
+                          void* stream, rad_htree** out) {
+    return guarded([&] {
+        RAD_REQUIRE(out != nullptr && verts != nullptr && counts != nullptr, RAD_EINVAL, "null argument");
+        *out = nullptr;
+        RAD_REQUIRE(n_cavities >= 1, RAD_EINVAL, "n_cavities must be >= 1");
+        std::vector<int64_t> seg(n_cavities + 1, 0);
+        for (int c = 0; c < n_cavities; ++c) {
+            RAD_REQUIRE(counts[c] >= 1, RAD_EINVAL, "every cavity needs at least one triangle");
+            seg[c + 1] = seg[c] + counts[c];
+        }
+        const int64_t n = seg[n_cavities];
+        check_tree_params(n, p);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        auto h = std::make_unique<rad_htree>();
+        h->n = n;
+        h->seg = seg;
+        h->leaf_size = p->leaf_size;
+        h->eta = p->eta_adm;
+        RAD_CUDA(cudaGetDevice(&h->device));
+        Scratch ws(s);
+        const double* v = to_device_t(verts, 9 * (size_t)n, ws);
+        double* geo_user = ws.get_n<double>(7 * (size_t)n);
+        build_geometry_from_tris(h.get(), v, geo_user, s);
+        build_trees(h.get(), geo_user, s);
+        if (n_cavities > 1) {
+            std::vector<int> segrow(n);
+            for (int c = 0; c < n_cavities; ++c)
+                for (int64_t i = seg[c]; i < seg[c + 1]; ++i) segrow[i] = c;
+            h->d_segrow.alloc(sizeof(int) * (size_t)n, s);
+            RAD_CUDA(cudaMemcpyAsync(h->d_segrow.p, segrow.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s));
+        }
+        RAD_CUDA(cudaStreamSynchronize(s));
+        *out = h.release();
+    });
+}
+
 int rad_build_htree_facets(int64_t n, const double* centroid, const double* normal, const double* area,
                            const rad_tree_params* p, void* stream, rad_htree** out) {
     return guarded([&] {

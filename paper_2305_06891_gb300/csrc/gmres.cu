@@ -45,13 +45,13 @@ __global__ void rhs_kernel(int n, int m, const double* __restrict__ eps, const d
 // partial[(chunk * L + l) * nc + c] = sum over the chunk's rows of
 // A_l[i][c] * Bv[i][c],  A_l = A + l * strideA.
 __global__ void __launch_bounds__(256)
-mdot_kernel(const double* __restrict__ A, long long strideA, int L, const double* __restrict__ Bv, int n, int nc,
-            double* __restrict__ partial) {
+mdot_kernel(const double* __restrict__ A, long long strideA, int L, const double* __restrict__ Bv,
+            const int2* __restrict__ chunk, int nc, double* __restrict__ partial) {
     __shared__ double red[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int c = blockIdx.y * 32 + tx;
-    const int r0 = blockIdx.x * kChunkRows;
-    const int r1 = min(n, r0 + kChunkRows);
+    const int r0 = chunk[blockIdx.x].x;
+    const int r1 = chunk[blockIdx.x].y;
     for (int l0 = 0; l0 < L; l0 += 4) {
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
         if (c < nc) {
@@ -76,40 +76,59 @@ mdot_kernel(const double* __restrict__ A, long long strideA, int L, const double
     }
 }
 
-// out[l * nc + c] (+)= sum_chunk partial[chunk][l][c]: one warp per output,
-// lanes take chunks lane, lane + 32, ..., then a fixed butterfly (the same
-// summation order on every call).
-__global__ void reduce_chunks_kernel(const double* __restrict__ partial, int chunks, int L, int nc, double* out,
-                                     int accumulate) {
+// Virtual columns: a batch handle holds several cavities (segments of the
+// rows); every (segment, column) pair is its own Krylov problem, with index
+// vc = segment * nc + c.  seg == nullptr means one segment.
+__device__ __forceinline__ int vcol(const int* seg, long long e, int nc) {
+    const long long row = e / nc;
+    const int c = (int)(e - row * nc);
+    return seg ? seg[row] * nc + c : c;
+}
+
+// out[l * nvc + vc] = sum over the chunks of vc's segment of
+// partial[chunk][l][c]: one warp per output, lanes take chunks lane,
+// lane + 32, ..., then a fixed butterfly (the same summation order on every
+// call).  Chunks never straddle segments.
+__global__ void reduce_chunks_kernel(const double* __restrict__ partial, const int* __restrict__ seg_chunk0, int L,
+                                     int nc, int nvc, double* out) {
     const int e = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (e >= L * nc) return;
+    if (e >= L * nvc) return;
+    const int l = e / nvc, vc = e - l * nvc;
+    const int sg = vc / nc, c = vc - sg * nc;
+    const int k0 = seg_chunk0[sg], k1 = seg_chunk0[sg + 1];
     double s = 0.0;
-    for (int k = lane; k < chunks; k += 32) s += partial[(long long)k * L * nc + e];
+    for (int k = k0 + lane; k < k1; k += 32) s += partial[((long long)k * L + l) * nc + c];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[e] = accumulate ? out[e] + s : s;
+    if (lane == 0) out[e] = s;
+}
+
+__global__ void add_kernel(double* __restrict__ a, const double* __restrict__ b, long long cnt) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < cnt) a[e] += b[e];
 }
 
 // W[i][c] -= sum_{l<L} V_l[i][c] h[l][c]   for active columns
 __global__ void cgs_update_kernel(const double* __restrict__ V, long long strideV, int L, const double* __restrict__ h,
-                                  const int* __restrict__ active, double* __restrict__ W, int n, int nc) {
+                                  const int* __restrict__ active, double* __restrict__ W, int n, int nc,
+                                  const int* __restrict__ seg, int nvc) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)n * nc) return;
-    const int c = (int)(e % nc);
+    const int c = vcol(seg, e, nc);
     if (!active[c]) return;
     double w = W[e];
-    for (int l = 0; l < L; ++l) w -= V[l * strideV + e] * h[l * nc + c];
+    for (int l = 0; l < L; ++l) w -= V[l * strideV + e] * h[l * nvc + c];
     W[e] = w;
 }
 
 // V_next = W / hn (active columns with hn > 0), else 0; optional FP32 copy.
 __global__ void normalize_kernel(const double* __restrict__ W, const double* __restrict__ hn2,
                                  const int* __restrict__ active, double* __restrict__ Vn, float* __restrict__ X32,
-                                 int n, int nc) {
+                                 int n, int nc, const int* __restrict__ seg) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)n * nc) return;
-    const int c = (int)(e % nc);
+    const int c = vcol(seg, e, nc);
     const double hn = sqrt(hn2[c]);
     const double v = (active[c] && hn > 0.0) ? W[e] / hn : 0.0;
     Vn[e] = v;
@@ -174,23 +193,23 @@ __global__ void trisolve_kernel(int R, int nc, const double* __restrict__ Hm, co
 // X[i][c] += sum_{l < jc[c]} V_l[i][c] y[l][c]
 __global__ void update_x_kernel(const double* __restrict__ V, long long strideV, int Lmax,
                                 const double* __restrict__ ycoef, const int* __restrict__ jc, double* __restrict__ X,
-                                int n, int nc) {
+                                int n, int nc, const int* __restrict__ seg, int nvc) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)n * nc) return;
-    const int c = (int)(e % nc);
+    const int c = vcol(seg, e, nc);
     const int J = min(jc[c], Lmax);
     double x = X[e];
-    for (int l = 0; l < J; ++l) x += V[l * strideV + e] * ycoef[l * nc + c];
+    for (int l = 0; l < J; ++l) x += V[l * strideV + e] * ycoef[l * nvc + c];
     X[e] = x;
 }
 
 // start a cycle: V_0 = R / beta for active columns, g = beta e_1
 __global__ void start_cycle_kernel(const double* __restrict__ Rv, const double* __restrict__ beta2,
                                    const int* __restrict__ active, double* __restrict__ V0, float* __restrict__ X32,
-                                   int n, int nc) {
+                                   int n, int nc, const int* __restrict__ seg) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)n * nc) return;
-    const int c = (int)(e % nc);
+    const int c = vcol(seg, e, nc);
     const double b = sqrt(beta2[c]);
     const double v = (active[c] && b > 0.0) ? Rv[e] / b : 0.0;
     V0[e] = v;
@@ -228,17 +247,43 @@ __global__ void axpy_kernel(double* __restrict__ X, const double* __restrict__ D
 
 inline unsigned grid_for(long long cnt, int bs = 256) { return (unsigned)((cnt + bs - 1) / bs); }
 
+// Inner products per virtual column (segment, column) over chunks of at most
+// 64 rows that never straddle a segment.
 struct ColReducer {
-    int n, nc, chunks;
+    int n, nc, nseg, nvc, nchunks;
+    const int2* chunk;       // [r0, r1) per chunk
+    const int* seg_chunk0;   // first chunk of each segment, nseg + 1 entries
     double* partial;
     cudaStream_t s;
-    // out[l][c] (+)= sum_i A_l[i][c] Bv[i][c]
-    void dots(const double* A, long long strideA, int L, const double* Bv, double* out, bool accumulate) {
-        dim3 grid(chunks, (nc + 31) / 32);
-        { ProfScope ps_("gmres_dots", s); mdot_kernel<<<grid, 256, 0, s>>>(A, strideA, L, Bv, n, nc, partial); }
+    ColReducer(const rad_htree* h, int nc_, int Lmax, Scratch& ws, cudaStream_t st) : n((int)h->n), nc(nc_), s(st) {
+        const std::vector<int64_t> one{0, h->n};
+        const std::vector<int64_t>& sg = h->seg.size() >= 2 ? h->seg : one;
+        nseg = (int)sg.size() - 1;
+        nvc = nseg * nc;
+        std::vector<int2> ch;
+        std::vector<int> c0(nseg + 1);
+        for (int g = 0; g < nseg; ++g) {
+            c0[g] = (int)ch.size();
+            for (int64_t r = sg[g]; r < sg[g + 1]; r += kChunkRows)
+                ch.push_back(make_int2((int)r, (int)std::min<int64_t>(r + kChunkRows, sg[g + 1])));
+        }
+        c0[nseg] = (int)ch.size();
+        nchunks = (int)ch.size();
+        int2* dch = ws.get_n<int2>(ch.size());
+        int* dc0 = ws.get_n<int>(c0.size());
+        h2d(dch, ch, s);
+        h2d(dc0, c0, s);
+        chunk = dch;
+        seg_chunk0 = dc0;
+        partial = ws.get_n<double>((long long)nchunks * Lmax * nc);
+    }
+    // out[l][vc] = sum over vc's rows of A_l[i][c] Bv[i][c]
+    void dots(const double* A, long long strideA, int L, const double* Bv, double* out) {
+        dim3 grid(nchunks, (nc + 31) / 32);
+        { ProfScope ps_("gmres_dots", s); mdot_kernel<<<grid, 256, 0, s>>>(A, strideA, L, Bv, chunk, nc, partial); }
         RAD_CHECK_LAUNCH();
-        { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<grid_for((long long)L * nc, 8), 256, 0, s>>>(partial, chunks, L, nc, out,
-                                                                          accumulate ? 1 : 0); }
+        { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<grid_for((long long)L * nvc, 8), 256, 0, s>>>(partial, seg_chunk0, L, nc, nvc,
+                                                                          out); }
         RAD_CHECK_LAUNCH();
     }
 };
@@ -246,6 +291,9 @@ struct ColReducer {
 }  // namespace
 
 // GMRES on C X = B in tree order (row-major N x nc).  X receives the solution.
+// Each virtual column (segment of a batch, column) runs its own restarted
+// GMRES: own Krylov vectors (the column's rows in that segment), Hessenberg
+// matrix, rotations and stopping test; they share the operator products.
 static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B, int nc, const rad_solve_params* p,
                        double* X, rad_solve_info* info, Scratch& ws, cudaStream_t s) {
     const int n = (int)h->n;
@@ -253,36 +301,37 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
     const double tol = p->tol;
     const bool op64 = h->op_is_f64();
     const long long nv = (long long)n * nc;
+    ColReducer red(h, nc, R + 1, ws, s);
+    const int nvc = red.nvc;
+    const int* seg = red.nseg > 1 ? h->d_segrow.as<int>() : nullptr;
     double* W = ws.get_n<double>(nv);
     double* V = ws.get_n<double>(nv * (R + 1));
     float* X32 = op64 ? nullptr : ws.get_n<float>(nv);
     void* Tws = ws.get(apply_workspace_bytes(h, nc));
-    double* Hm = ws.get_n<double>((long long)R * (R + 1) * nc);
-    double* cs = ws.get_n<double>((long long)R * nc);
-    double* sn = ws.get_n<double>((long long)R * nc);
-    double* g = ws.get_n<double>((long long)(R + 1) * nc);
-    double* ycoef = ws.get_n<double>((long long)R * nc);
-    double* bnorm2 = ws.get_n<double>(nc);
-    double* bnorm = ws.get_n<double>(nc);
-    double* beta2 = ws.get_n<double>(nc);
-    double* hn2 = ws.get_n<double>(nc);
-    double* resid = ws.get_n<double>(nc);
-    int* active = ws.get_n<int>(nc);
-    int* jc = ws.get_n<int>(nc);
-    const int chunks = (n + kChunkRows - 1) / kChunkRows;
-    ColReducer red{n, nc, chunks, ws.get_n<double>((long long)chunks * (R + 1) * nc), s};
+    double* Hm = ws.get_n<double>((long long)R * (R + 1) * nvc);
+    double* cs = ws.get_n<double>((long long)R * nvc);
+    double* sn = ws.get_n<double>((long long)R * nvc);
+    double* g = ws.get_n<double>((long long)(R + 1) * nvc);
+    double* ycoef = ws.get_n<double>((long long)(R + 1) * nvc);
+    double* bnorm2 = ws.get_n<double>(nvc);
+    double* bnorm = ws.get_n<double>(nvc);
+    double* beta2 = ws.get_n<double>(nvc);
+    double* hn2 = ws.get_n<double>(nvc);
+    double* resid = ws.get_n<double>(nvc);
+    int* active = ws.get_n<int>(nvc);
+    int* jc = ws.get_n<int>(nvc);
 
     RAD_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * nv, s));
-    red.dots(B, 0, 1, B, bnorm2, false);
-    std::vector<double> hb2(nc), hbeta(nc);
-    RAD_CUDA(cudaMemcpyAsync(hb2.data(), bnorm2, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    red.dots(B, 0, 1, B, bnorm2);
+    std::vector<double> hb2(nvc), hbeta(nvc);
+    RAD_CUDA(cudaMemcpyAsync(hb2.data(), bnorm2, sizeof(double) * nvc, cudaMemcpyDeviceToHost, s));
     RAD_CUDA(cudaStreamSynchronize(s));
-    std::vector<double> hbn(nc);
-    for (int c = 0; c < nc; ++c) hbn[c] = hb2[c] > 0.0 ? std::sqrt(hb2[c]) : 1.0;
-    RAD_CUDA(cudaMemcpyAsync(bnorm, hbn.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, s));
+    std::vector<double> hbn(nvc);
+    for (int c = 0; c < nvc; ++c) hbn[c] = hb2[c] > 0.0 ? std::sqrt(hb2[c]) : 1.0;
+    RAD_CUDA(cudaMemcpyAsync(bnorm, hbn.data(), sizeof(double) * nvc, cudaMemcpyHostToDevice, s));
     // initial residual = B (x0 = 0)
     RAD_CUDA(cudaMemcpyAsync(W, B, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
-    RAD_CUDA(cudaMemcpyAsync(beta2, bnorm2, sizeof(double) * nc, cudaMemcpyDeviceToDevice, s));
+    RAD_CUDA(cudaMemcpyAsync(beta2, bnorm2, sizeof(double) * nvc, cudaMemcpyDeviceToDevice, s));
     hbeta = hb2;
 
     auto apply_C = [&](const double* vin, const float* vin32, double* out, int mode) {
@@ -292,12 +341,12 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
 
     int total_iters = 0, restarts = 0, matvecs = 0, status = RAD_OK;
     double prev_max = INFINITY, max_rel = 0.0;
-    std::vector<int> hact(nc);
+    std::vector<int> hact(nvc);
     for (;;) {
-        // columns still above tolerance take part in this cycle
+        // virtual columns still above tolerance take part in this cycle
         max_rel = 0.0;
         int n_act = 0;
-        for (int c = 0; c < nc; ++c) {
+        for (int c = 0; c < nvc; ++c) {
             const double rel = std::sqrt(std::max(hbeta[c], 0.0)) / hbn[c];
             max_rel = std::max(max_rel, rel);
             hact[c] = rel > tol ? 1 : 0;
@@ -309,46 +358,45 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
             break;
         }
         prev_max = max_rel;
-        RAD_CUDA(cudaMemcpyAsync(active, hact.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, s));
-        { ProfScope ps_("gmres_small", s); start_cycle_kernel<<<grid_for(nv), 256, 0, s>>>(W, beta2, active, V, X32, n, nc); }
+        RAD_CUDA(cudaMemcpyAsync(active, hact.data(), sizeof(int) * nvc, cudaMemcpyHostToDevice, s));
+        { ProfScope ps_("gmres_small", s); start_cycle_kernel<<<grid_for(nv), 256, 0, s>>>(W, beta2, active, V, X32, n, nc, seg); }
         RAD_CHECK_LAUNCH();
-        { ProfScope ps_("gmres_small", s); init_g_kernel<<<grid_for(nc), 128, 0, s>>>(R, nc, beta2, g, jc); }
+        { ProfScope ps_("gmres_small", s); init_g_kernel<<<grid_for(nvc), 128, 0, s>>>(R, nvc, beta2, g, jc); }
         RAD_CHECK_LAUNCH();
         for (int j = 0; j < R && total_iters < p->max_iter; ++j) {
             double* Vj = V + (long long)j * nv;
-            double* hcol = Hm + (long long)j * (R + 1) * nc;
+            double* hcol = Hm + (long long)j * (R + 1) * nvc;
             // w = C v_j
             apply_C(Vj, X32, W, kReflect);
             ++matvecs;
             // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2
             for (int pass = 0; pass < 2; ++pass) {
                 double* hbuf = pass == 0 ? hcol : ycoef;  // ycoef doubles as scratch here
-                red.dots(V, nv, j + 1, W, hbuf, false);
-                { ProfScope ps_("gmres_cgs_update", s); cgs_update_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, j + 1, hbuf, active, W, n, nc); }
+                red.dots(V, nv, j + 1, W, hbuf);
+                { ProfScope ps_("gmres_cgs_update", s); cgs_update_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, j + 1, hbuf, active, W, n, nc, seg, nvc); }
                 RAD_CHECK_LAUNCH();
                 if (pass == 1) {
-                    { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<grid_for((long long)(j + 1) * nc, 8), 256, 0, s>>>(ycoef, 1, j + 1, nc,
-                                                                                            hcol, 1); }
+                    { ProfScope ps_("gmres_small", s); add_kernel<<<grid_for((long long)(j + 1) * nvc), 256, 0, s>>>(hcol, ycoef, (long long)(j + 1) * nvc); }
                     RAD_CHECK_LAUNCH();
                 }
             }
-            red.dots(W, 0, 1, W, hn2, false);
-            { ProfScope ps_("gmres_normalize", s); normalize_kernel<<<grid_for(nv), 256, 0, s>>>(W, hn2, active, V + (long long)(j + 1) * nv, X32, n, nc); }
+            red.dots(W, 0, 1, W, hn2);
+            { ProfScope ps_("gmres_normalize", s); normalize_kernel<<<grid_for(nv), 256, 0, s>>>(W, hn2, active, V + (long long)(j + 1) * nv, X32, n, nc, seg); }
             RAD_CHECK_LAUNCH();
-            { ProfScope ps_("gmres_small", s); givens_kernel<<<grid_for(nc, 128), 128, 0, s>>>(j, R, nc, Hm, hn2, cs, sn, g, bnorm, resid, active, jc,
+            { ProfScope ps_("gmres_small", s); givens_kernel<<<grid_for(nvc, 128), 128, 0, s>>>(j, R, nvc, Hm, hn2, cs, sn, g, bnorm, resid, active, jc,
                                                             tol); }
             RAD_CHECK_LAUNCH();
             ++total_iters;
-            RAD_CUDA(cudaMemcpyAsync(hact.data(), active, sizeof(int) * nc, cudaMemcpyDeviceToHost, s));
+            RAD_CUDA(cudaMemcpyAsync(hact.data(), active, sizeof(int) * nvc, cudaMemcpyDeviceToHost, s));
             RAD_CUDA(cudaStreamSynchronize(s));
             int still = 0;
-            for (int c = 0; c < nc; ++c) still += hact[c];
+            for (int c = 0; c < nvc; ++c) still += hact[c];
             if (still == 0) break;
         }
         // x += V y
-        { ProfScope ps_("gmres_small", s); trisolve_kernel<<<grid_for(nc, 128), 128, 0, s>>>(R, nc, Hm, g, jc, ycoef); }
+        { ProfScope ps_("gmres_small", s); trisolve_kernel<<<grid_for(nvc, 128), 128, 0, s>>>(R, nvc, Hm, g, jc, ycoef); }
         RAD_CHECK_LAUNCH();
-        { ProfScope ps_("gmres_update_x", s); update_x_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, R, ycoef, jc, X, n, nc); }
+        { ProfScope ps_("gmres_update_x", s); update_x_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, R, ycoef, jc, X, n, nc, seg, nvc); }
         RAD_CHECK_LAUNCH();
         // true residual r = b - C x
         if (X32) {
@@ -357,8 +405,8 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
         }
         apply_C(X, X32, W, kResid);
         ++matvecs;
-        red.dots(W, 0, 1, W, beta2, false);
-        RAD_CUDA(cudaMemcpyAsync(hbeta.data(), beta2, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+        red.dots(W, 0, 1, W, beta2);
+        RAD_CUDA(cudaMemcpyAsync(hbeta.data(), beta2, sizeof(double) * nvc, cudaMemcpyDeviceToHost, s));
         RAD_CUDA(cudaStreamSynchronize(s));
         ++restarts;
     }
@@ -382,13 +430,13 @@ static void refine_tree(const rad_htree* h, const double* eps_t, const double* B
     double* R = ws.get_n<double>(nv);
     double* D = ws.get_n<double>(nv);
     double* Tacc = static_cast<double*>(ws.get(apply_workspace_bytes_acc(h, nc)));
-    double* bn2 = ws.get_n<double>(nc);
-    double* r2 = ws.get_n<double>(nc);
-    const int chunks = (n + kChunkRows - 1) / kChunkRows;
-    ColReducer red{n, nc, chunks, ws.get_n<double>((long long)chunks * nc), s};
-    red.dots(B, 0, 1, B, bn2, false);
-    std::vector<double> hb(nc), hr(nc);
-    RAD_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    ColReducer red(h, nc, 1, ws, s);
+    const int nvc = red.nvc;
+    double* bn2 = ws.get_n<double>(nvc);
+    double* r2 = ws.get_n<double>(nvc);
+    red.dots(B, 0, 1, B, bn2);
+    std::vector<double> hb(nvc), hr(nvc);
+    RAD_CUDA(cudaMemcpyAsync(hb.data(), bn2, sizeof(double) * nvc, cudaMemcpyDeviceToHost, s));
     RAD_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * nv, s));
     RAD_CUDA(cudaStreamSynchronize(s));
     rad_solve_params inner = *p;
@@ -400,11 +448,11 @@ static void refine_tree(const rad_htree* h, const double* eps_t, const double* B
         Epi epi{kResid, eps_t, X, B, nc};
         apply_tree_acc(h, X, nc, R, nc, nc, epi, Tacc, s);
         ++matvecs;
-        red.dots(R, 0, 1, R, r2, false);
-        RAD_CUDA(cudaMemcpyAsync(hr.data(), r2, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+        red.dots(R, 0, 1, R, r2);
+        RAD_CUDA(cudaMemcpyAsync(hr.data(), r2, sizeof(double) * nvc, cudaMemcpyDeviceToHost, s));
         RAD_CUDA(cudaStreamSynchronize(s));
         max_rel = 0.0;
-        for (int c = 0; c < nc; ++c)
+        for (int c = 0; c < nvc; ++c)
             max_rel = std::max(max_rel, std::sqrt(std::max(hr[c], 0.0)) / (hb[c] > 0.0 ? std::sqrt(hb[c]) : 1.0));
         if (max_rel <= p->tol) {
             status = RAD_OK;

@@ -259,6 +259,10 @@ struct rad_htree {
     // wait for the device before they return to the pool.
     ~rad_htree() { (void)cudaDeviceSynchronize(); }
     int64_t n = 0;
+    // segment (cavity) boundaries of a batch handle: cavity c holds facets
+    // [seg[c], seg[c+1]) in user order and in tree order; {0, n} otherwise
+    std::vector<int64_t> seg;
+    rad::DevBuf d_segrow;   // segment of every tree-order row (batches only)
     int leaf_size = 0;
     double eta = 0.0;
     int device = 0;

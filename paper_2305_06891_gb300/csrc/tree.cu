@@ -278,14 +278,23 @@ __device__ __forceinline__ bool admissible(const NodeBox& s, const NodeBox& t, d
 
 __global__ void __launch_bounds__(kTreeNT)
 block_tree_kernel(const NodeShape* __restrict__ shapes, const NodeBox* __restrict__ boxes, double eta,
-                  int2* candA, int2* candB, int cap_cand, int2* __restrict__ far_out, int cap_far,
-                  int2* __restrict__ near_out, int cap_near, int* __restrict__ counters) {
+                  const int* __restrict__ roots, const long long* __restrict__ slice_off,
+                  const int* __restrict__ slice_cap, int2* candA_all, int2* candB_all, int2* __restrict__ far_all,
+                  int2* __restrict__ near_all, int* __restrict__ counters_all) {
+    // one CTA per tree of the forest (one cavity), each with its own slice
+    // of the candidate and output buffers
     constexpr int NT = kTreeNT;
     constexpr unsigned long long M21 = (1ull << 21) - 1ull;
     __shared__ unsigned long long scan_sm[NT / 32 + 1];
-    int2* cur = candA;
-    int2* nxt = candB;
-    if (threadIdx.x == 0) cur[0] = make_int2(0, 0);
+    const long long off = slice_off[blockIdx.x];
+    const int cap_cand = slice_cap[blockIdx.x], cap_far = cap_cand, cap_near = cap_cand;
+    int2* cur = candA_all + off;
+    int2* nxt = candB_all + off;
+    int2* far_out = far_all + off;
+    int2* near_out = near_all + off;
+    int* counters = counters_all + 4 * blockIdx.x;
+    const int root = roots[blockIdx.x];
+    if (threadIdx.x == 0) cur[0] = make_int2(root, root);
     __syncthreads();
     int ncur = 1, nfar = 0, nnear = 0, overflow = 0, max_cand = 1;
     for (int level = 0; level < 64 && ncur > 0; ++level) {
@@ -384,7 +393,16 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     HostScope hs_shapes("host_tree_shapes");
     StageScope stage;
     nodes.clear();
-    nodes.push_back(NodeShape{0, n, 0, -1, -1, n <= leaf ? 1 : 0});
+    // one root per segment (cavity): a batch is a forest whose trees never
+    // meet, so no block couples two cavities
+    if (h->seg.empty()) h->seg = {0, (int64_t)n};
+    const int nseg = (int)h->seg.size() - 1;
+    std::vector<int> roots(nseg);
+    for (int c = 0; c < nseg; ++c) {
+        const int b0 = (int)h->seg[c], b1 = (int)h->seg[c + 1];
+        roots[c] = (int)nodes.size();
+        nodes.push_back(NodeShape{b0, b1, 0, -1, -1, b1 - b0 <= leaf ? 1 : 0});
+    }
     for (size_t q = 0; q < nodes.size(); ++q) {
         NodeShape nd = nodes[q];
         if (nd.leaf) continue;
@@ -439,37 +457,67 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     { ProfScope ps_("geometry", s); geo32_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, h->geo.as<double>(), h->geo32.as<float>()); }
     RAD_CHECK_LAUNCH();
 
-    // block tree: single CTA, retry with larger buffers on overflow
+    // block tree: one CTA per tree, retry with larger buffers on overflow
     HostScope hs_blocks("host_block_tree_wait");
-    const int base_cap = (int)std::min<int64_t>(1 << 28, 160ll * (n / std::max(1, leaf) + 1) + 4096);
-    int cap = base_cap;
-    std::vector<int2> far_pairs, near_pairs;
-    for (int attempt = 0; attempt < 6; ++attempt) {
-        Scratch bw(s);
-        int2* candA = bw.get_n<int2>(cap);
-        int2* candB = bw.get_n<int2>(cap);
-        int2* far_out = bw.get_n<int2>(cap);
-        int2* near_out = bw.get_n<int2>(cap);
-        int* counters = bw.get_n<int>(4);
-        { ProfScope ps_("block_tree", s); block_tree_kernel<<<1, kTreeNT, 0, s>>>(d_shapes, d_boxes, h->eta, candA, candB, cap, far_out, cap,
-                                                near_out, cap, counters); }
-        RAD_CHECK_LAUNCH();
-        int hc[4];
-        RAD_CUDA(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
-        RAD_CUDA(cudaStreamSynchronize(s));
-        if (hc[2]) {
-            const int64_t need = std::max<int64_t>({(int64_t)hc[0], (int64_t)hc[1], (int64_t)hc[3]});
-            RAD_REQUIRE(cap < (1 << 28), RAD_ELIMIT, "block tree too large");
-            cap = (int)std::min<int64_t>(1 << 28, std::max<int64_t>(4ll * cap, need + 1024));
-            continue;
-        }
-        far_pairs.resize(hc[0]);
-        near_pairs.resize(hc[1]);
-        if (hc[0]) RAD_CUDA(cudaMemcpyAsync(far_pairs.data(), far_out, sizeof(int2) * hc[0], cudaMemcpyDeviceToHost, s));
-        if (hc[1]) RAD_CUDA(cudaMemcpyAsync(near_pairs.data(), near_out, sizeof(int2) * hc[1], cudaMemcpyDeviceToHost, s));
-        RAD_CUDA(cudaStreamSynchronize(s));
-        break;
+    std::vector<int> caps(nseg);
+    for (int c = 0; c < nseg; ++c) {
+        const int64_t nc_ = h->seg[c + 1] - h->seg[c];
+        caps[c] = (int)std::min<int64_t>(1 << 28, 160ll * (nc_ / std::max(1, leaf) + 1) + 4096);
     }
+    std::vector<int2> far_pairs, near_pairs;
+    int* d_roots = ws.get_n<int>(nseg);
+    h2d(d_roots, roots, s);
+    bool done = false;
+    for (int attempt = 0; attempt < 6 && !done; ++attempt) {
+        std::vector<long long> off(nseg + 1, 0);
+        for (int c = 0; c < nseg; ++c) off[c + 1] = off[c] + caps[c];
+        Scratch bw(s);
+        int2* candA = bw.get_n<int2>(off[nseg]);
+        int2* candB = bw.get_n<int2>(off[nseg]);
+        int2* far_out = bw.get_n<int2>(off[nseg]);
+        int2* near_out = bw.get_n<int2>(off[nseg]);
+        int* counters = bw.get_n<int>(4 * (size_t)nseg);
+        long long* d_off = bw.get_n<long long>(nseg);
+        int* d_caps = bw.get_n<int>(nseg);
+        h2d(d_off, std::vector<long long>(off.begin(), off.end() - 1), s);
+        h2d(d_caps, caps, s);
+        { ProfScope ps_("block_tree", s); block_tree_kernel<<<nseg, kTreeNT, 0, s>>>(d_shapes, d_boxes, h->eta, d_roots, d_off, d_caps,
+                                                candA, candB, far_out, near_out, counters); }
+        RAD_CHECK_LAUNCH();
+        std::vector<int> hc(4 * (size_t)nseg);
+        RAD_CUDA(cudaMemcpyAsync(hc.data(), counters, sizeof(int) * hc.size(), cudaMemcpyDeviceToHost, s));
+        RAD_CUDA(cudaStreamSynchronize(s));
+        bool over = false;
+        for (int c = 0; c < nseg; ++c) {
+            if (!hc[4 * c + 2]) continue;
+            over = true;
+            const int64_t need = std::max<int64_t>({(int64_t)hc[4 * c], (int64_t)hc[4 * c + 1], (int64_t)hc[4 * c + 3]});
+            RAD_REQUIRE(caps[c] < (1 << 28), RAD_ELIMIT, "block tree too large");
+            caps[c] = (int)std::min<int64_t>(1 << 28, std::max<int64_t>(4ll * caps[c], need + 1024));
+        }
+        if (over) continue;
+        long long nf = 0, nn = 0;
+        for (int c = 0; c < nseg; ++c) {
+            nf += hc[4 * c];
+            nn += hc[4 * c + 1];
+        }
+        far_pairs.resize(nf);
+        near_pairs.resize(nn);
+        nf = nn = 0;
+        for (int c = 0; c < nseg; ++c) {
+            if (hc[4 * c])
+                RAD_CUDA(cudaMemcpyAsync(far_pairs.data() + nf, far_out + off[c], sizeof(int2) * hc[4 * c],
+                                         cudaMemcpyDeviceToHost, s));
+            if (hc[4 * c + 1])
+                RAD_CUDA(cudaMemcpyAsync(near_pairs.data() + nn, near_out + off[c], sizeof(int2) * hc[4 * c + 1],
+                                         cudaMemcpyDeviceToHost, s));
+            nf += hc[4 * c];
+            nn += hc[4 * c + 1];
+        }
+        RAD_CUDA(cudaStreamSynchronize(s));
+        done = true;
+    }
+    RAD_REQUIRE(done, RAD_ELIMIT, "block tree did not fit");
     RAD_REQUIRE(!(far_pairs.empty() && near_pairs.empty()), RAD_ELIMIT, "block tree did not fit");
 
     h->boxes.resize(n_nodes);
