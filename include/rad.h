@@ -77,7 +77,13 @@ typedef struct {
  * accurate_dtype = RAD_F32 with factor_dtype = RAD_BF16 also keeps the
  * factors in FP32: the "accurate operator" that mixed-precision iterative
  * refinement (rad_solve_params.refine) uses for its residuals; -1 keeps no
- * second copy. */
+ * second copy.
+ * scratch_mib bounds the device scratch of partial-pivot ACA (max_rank
+ * columns of U and V per admissible block, before the ranks are known):
+ * 0 = 30% of the free device memory, at most 24 GiB, at least 1 GiB; > 0 =
+ * that many MiB.  Blocks beyond the bound are compressed in further chunks,
+ * each compacted to its ranks before the next starts; the result does not
+ * depend on the chunking. */
 typedef struct {
     double  tol;
     int32_t max_rank;
@@ -85,7 +91,7 @@ typedef struct {
     int32_t factor_dtype;
     int32_t near_dtype;
     int32_t accurate_dtype;
-    int32_t reserved;
+    int32_t scratch_mib;
 } rad_aca_params;
 
 /* GMRES on C y = b, C = I - diag(1 - eps) F (Eq. 11).  Stops when every
@@ -140,6 +146,10 @@ typedef struct {
     int64_t far_v_entries;       /* sum k n over low-rank blocks (V factors)   */
     int64_t n_tiles;             /* row tiles of the product (<= 64 rows)      */
     int64_t bytes_accurate;      /* FP32 factor copy kept for refinement (0 if none) */
+    int32_t tuned;               /* 1 after rad_htree_autotune                  */
+    int32_t stream_rows;         /* rows per far-field item (1-4 columns)       */
+    int32_t grid_a1, grid_b1;    /* grids of the 1-column phases (0: per item)  */
+    int32_t grid_a2, grid_b2;    /* grids of the 2-4 column launches            */
 } rad_htree_stats;
 
 /* -------------------------------------------------------------------------
@@ -202,9 +212,29 @@ int rad_compress_aca(rad_htree* h, const rad_aca_params* p, void* stream);
  *   y      column-major n x nrhs, column c at y + c*ldy (ldy >= n)
  *   nrhs   1 .. 4096
  * Requires a compressed handle.  Device arrays: asynchronous on `stream`.
+ * Graph replay (no counterpart in the paper): with device arrays, the
+ * second call with the same x, y, leading dimensions, nrhs, dtype and stream
+ * captures the gather, the product and the scatter into a CUDA graph kept by
+ * the handle, and later identical calls replay it (one graph launch; x and
+ * y are read and written in place, so their contents may change between
+ * calls).  Not while profiling, not when `stream` is itself being captured
+ * (the kernels are then recorded into the caller's graph), and not for
+ * overlapping calls on other streams.  Recompression or autotuning drops the
+ * graph.
  * ------------------------------------------------------------------------- */
 int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx,
                 void* y, int64_t ldy, int64_t nrhs, void* stream);
+
+/* Autotuner for the streaming products (1-4 columns; no counterpart in the
+ * paper): times, on this handle's compressed operator, every combination of
+ * far-field item rows (64, 128, 256) and grid policy (one CTA per work item,
+ * or a persistent grid of 2, 4 or 8 CTAs per SM) for each launch, and keeps
+ * the fastest (reported in rad_htree_stats).  The grid policy does not
+ * change results (each work item is computed by one CTA in a fixed order);
+ * the item rows change the order of the sums over a column group (results
+ * agree to rounding).  Synchronous; takes a fraction of a second.
+ * Recompression resets the choice. */
+int rad_htree_autotune(rad_htree* h, void* stream);
 
 /* -------------------------------------------------------------------------
  * rad_solve_flux — A7-A8: for each of the m temperature fields T(:, c)

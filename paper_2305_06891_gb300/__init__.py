@@ -44,7 +44,7 @@ class _TreeParams(C.Structure):
 class _AcaParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_rank", C.c_int32), ("pivoting", C.c_int32),
                 ("factor_dtype", C.c_int32), ("near_dtype", C.c_int32), ("accurate_dtype", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("scratch_mib", C.c_int32)]
 
 
 class _SolveParams(C.Structure):
@@ -66,7 +66,8 @@ class _Stats(C.Structure):
                 ("near_entries", C.c_int64), ("far_entries", C.c_int64), ("sum_rank", C.c_int64),
                 ("aca_entries", C.c_int64), ("bytes_near", C.c_int64), ("bytes_far", C.c_int64),
                 ("far_u_entries", C.c_int64), ("far_v_entries", C.c_int64), ("n_tiles", C.c_int64),
-                ("bytes_accurate", C.c_int64)]
+                ("bytes_accurate", C.c_int64), ("tuned", C.c_int32), ("stream_rows", C.c_int32),
+                ("grid_a1", C.c_int32), ("grid_b1", C.c_int32), ("grid_a2", C.c_int32), ("grid_b2", C.c_int32)]
 
 
 def _load():
@@ -95,6 +96,7 @@ def _load():
         "rad_htree_export_blocks": (C.c_int, [H, vp, vp, vp, vp]),
         "rad_htree_export_block": (C.c_int, [H, i64, vp, vp, vp]),
         "rad_htree_free": (C.c_int, [H]),
+        "rad_htree_autotune": (C.c_int, [H, vp]),
         "rad_launch_count": (C.c_int64, []),
         "rad_profile_enable": (C.c_int, [i32]),
         "rad_profile_read": (C.c_int, [i32, vp, vp, vp]),
@@ -270,9 +272,10 @@ def rad_htree_from_dense(F, stream=None) -> HTree:
 
 def rad_compress_aca(h: HTree, tol: float, max_rank: int = 64, pivoting: str = "partial",
                      factor_dtype: str = "f32", near_dtype: str = "f32", accurate_dtype: str | None = None,
-                     stream=None) -> None:
+                     stream=None, scratch_mib: int = 0) -> None:
     acc = -1 if accurate_dtype is None else _DT[accurate_dtype]
-    p = _AcaParams(float(tol), int(max_rank), _PIV[pivoting], _DT[factor_dtype], _DT[near_dtype], acc, 0)
+    p = _AcaParams(float(tol), int(max_rank), _PIV[pivoting], _DT[factor_dtype], _DT[near_dtype], acc,
+                   int(scratch_mib))
     _check(_lib.rad_compress_aca(h.ptr, C.byref(p), _stream(stream)))
 
 
@@ -370,6 +373,14 @@ def rad_solve_reflection(h: HTree, eps, B, tol: float = 1e-10, restart: int = 30
     if (_is_tensor(B) and B.dim() == 1) or (not _is_tensor(B) and np.ndim(B) == 1):
         Y = Y[:, 0]
     return Y, d
+
+
+def rad_htree_autotune(h: HTree, stream=None) -> dict:
+    """Choose the streaming products' item rows and grids by timing them on
+    this handle's operator; returns the chosen configuration."""
+    _check(_lib.rad_htree_autotune(h.ptr, _stream(stream)))
+    st = rad_htree_get_stats(h)
+    return {k: st[k] for k in ("stream_rows", "grid_a1", "grid_b1", "grid_a2", "grid_b2")}
 
 
 def rad_htree_get_stats(h: HTree) -> dict:

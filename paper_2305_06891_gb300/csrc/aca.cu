@@ -492,13 +492,15 @@ dense_fill_kernel(Geo g, const Tile* __restrict__ tiles, const DenseWork* __rest
 // Low-rank pieces: rows [ro, ro + tile rows) of U_b (ACA scratch, m x k
 // column-major) go to low-rank panel columns [col, col + k).
 struct UWork {
-    int tile, ro, m, k, col, pad;
+    int tile, ro, m, k, col, chunk;
     long long src;
 };
 template <class CT, class S>
 __global__ void __launch_bounds__(256)
-u_fill_kernel(const Tile* __restrict__ tiles, const UWork* __restrict__ work, const CT* __restrict__ Us, S* pool) {
+u_fill_kernel(const Tile* __restrict__ tiles, const UWork* __restrict__ work, const CT* const* __restrict__ Ubase,
+              S* pool) {
     const UWork w = work[blockIdx.x];
+    const CT* __restrict__ Us = Ubase[w.chunk];
     const Tile t = tiles[w.tile];
     S* P = pool + t.foff + (long long)w.col * t.ld;
     const int cnt = w.k * t.ld;
@@ -511,13 +513,15 @@ u_fill_kernel(const Tile* __restrict__ tiles, const UWork* __restrict__ work, co
 // V^T rows of block b (ACA scratch V_b, n x k column-major) go to rows
 // [grow, grow + k) of its group's V panel.
 struct VWork {
-    int group, grow, n, k;
+    int group, grow, n, k, chunk, pad;
     long long src;
 };
 template <class CT, class S>
 __global__ void __launch_bounds__(256)
-v_fill_kernel(const Group* __restrict__ groups, const VWork* __restrict__ work, const CT* __restrict__ Vs, S* pool) {
+v_fill_kernel(const Group* __restrict__ groups, const VWork* __restrict__ work, const CT* const* __restrict__ Vbase,
+              S* pool) {
     const VWork w = work[blockIdx.x];
+    const CT* __restrict__ Vs = Vbase[w.chunk];
     const Group gr = groups[w.group];
     S* P = pool + gr.voff;
     const int cnt = w.n * w.k;
@@ -538,6 +542,20 @@ dense_from_matrix_kernel(int n, const Tile* __restrict__ tiles, const double* __
         const int c = (int)(e / t.ld), i = (int)(e - (long long)c * t.ld);
         P[e] = i < t.rows ? F[(long long)(t.r0 + i) * n + c] : 0.0;
     }
+}
+
+// Copies the first rank columns of every job's U and V scratch slots (column
+// major, so m*k and n*k contiguous elements) to compact offsets.
+template <class CT>
+__global__ void __launch_bounds__(256)
+compact_kernel(const AcaJob* __restrict__ jobs, const int* __restrict__ rank, const long long* __restrict__ cu,
+               const long long* __restrict__ cv, const CT* __restrict__ Us, const CT* __restrict__ Vs, CT* Uc, CT* Vc) {
+    const AcaJob j = jobs[blockIdx.x];
+    const int k = rank[blockIdx.x];
+    if (k <= 0) return;
+    const long long nu = (long long)j.m * k, nv = (long long)j.n * k;
+    for (long long e = threadIdx.x; e < nu; e += 256) Uc[cu[blockIdx.x] + e] = Us[j.offU + e];
+    for (long long e = threadIdx.x; e < nv; e += 256) Vc[cv[blockIdx.x] + e] = Vs[j.offV + e];
 }
 
 // Indices 0..key.size()-1 ordered by descending key, ties in index order
@@ -678,6 +696,49 @@ fill_runs_kernel(const IdxRun* __restrict__ runs, int nruns, const Tile* __restr
     for (int i = threadIdx.x & 31; i < u.count; i += 32) o[i] = u.start + i;
 }
 
+}  // namespace
+
+// Work lists of the streaming (1-4 column) products for far-field items of
+// at most `rows` rows: sitems (heaviest first) and the phase-A order that
+// mixes them with the tiles' dense panels.
+void build_stream_lists(rad_htree* h, int rows, cudaStream_t s) {
+    const auto& G = h->groups_h;
+    std::vector<GWork> w;
+    for (int g = 0; g < (int)G.size(); ++g)
+        for (int r = 0; r < G[g].M; r += rows) w.push_back(GWork{g, r, std::min(rows, G[g].M - r), 0});
+    std::vector<long long> key(w.size());
+    for (size_t i = 0; i < w.size(); ++i) key[i] = (long long)w[i].rows * G[w[i].g].n;
+    std::vector<GWork> sitems(w.size());
+    {
+        const std::vector<int> ord = order_desc(key);
+        for (size_t i = 0; i < w.size(); ++i) sitems[i] = w[ord[i]];
+    }
+    std::vector<long long> akey;
+    std::vector<int> acode;
+    for (size_t i = 0; i < sitems.size(); ++i) {
+        akey.push_back((long long)sitems[i].rows * G[sitems[i].g].n);
+        acode.push_back((int)i);
+    }
+    for (size_t t = 0; t < h->tiles_h.size(); ++t) {
+        akey.push_back((long long)h->tiles_h[t].ld * h->tiles_h[t].kn);
+        acode.push_back(-(int)t - 1);
+    }
+    std::vector<int> aorder(acode.size());
+    {
+        const std::vector<int> o = order_desc(akey);
+        for (size_t i = 0; i < o.size(); ++i) aorder[i] = acode[o[i]];
+    }
+    h->stream_rows = rows;
+    h->n_sitems = (int)sitems.size();
+    h->n_aitems = (int)aorder.size();
+    h->d_sitems.alloc(sizeof(GWork) * std::max<size_t>(1, sitems.size()), s);
+    h->d_aorder.alloc(sizeof(int) * std::max<size_t>(1, aorder.size()), s);
+    h2d(h->d_sitems.as<GWork>(), sitems, s);
+    h2d(h->d_aorder.as<int>(), aorder, s);
+}
+
+namespace {
+
 static void upload_operator(rad_htree* h, const std::vector<IdxRun>& near_runs, const std::vector<IdxRun>& far_runs,
                             cudaStream_t s) {
     long long nx = 0, nf = 0;
@@ -706,44 +767,22 @@ static void upload_operator(rad_htree* h, const std::vector<IdxRun>& near_runs, 
         return w;
     };
     std::vector<GWork> gwork = split_groups(kTileRows);
-    std::vector<GWork> sitems = split_groups(kStreamRows);
     std::vector<long long> tkey(h->tiles_h.size());
     for (size_t t = 0; t < tkey.size(); ++t) {
         const Tile& tl = h->tiles_h[t];
         tkey[t] = (long long)tl.ld * (tl.kn + tl.kf);
     }
     const std::vector<int> torder = order_desc(tkey);
-    // phase A / phase B orders of the one-column product
-    std::vector<long long> akey;
-    std::vector<int> acode;
-    for (size_t i = 0; i < sitems.size(); ++i) {
-        akey.push_back((long long)sitems[i].rows * G[sitems[i].g].n);
-        acode.push_back((int)i);
-    }
-    for (size_t t = 0; t < h->tiles_h.size(); ++t) {
-        akey.push_back((long long)h->tiles_h[t].ld * h->tiles_h[t].kn);
-        acode.push_back(-(int)t - 1);
-    }
-    std::vector<int> aorder(acode.size());
-    {
-        const std::vector<int> o = order_desc(akey);
-        for (size_t i = 0; i < o.size(); ++i) aorder[i] = acode[o[i]];
-    }
     std::vector<long long> fkey(h->tiles_h.size());
     for (size_t t = 0; t < fkey.size(); ++t) fkey[t] = (long long)h->tiles_h[t].ld * h->tiles_h[t].kf;
     const std::vector<int> forder = order_desc(fkey);
-    h->n_aitems = (int)aorder.size();
-    h->d_aorder.alloc(sizeof(int) * std::max<size_t>(1, aorder.size()), s);
-    h->d_forder.alloc(sizeof(int) * std::max<size_t>(1, forder.size()), s);
-    h2d(h->d_aorder.as<int>(), aorder, s);
-    h2d(h->d_forder.as<int>(), forder, s);
     h->n_tiles = (int)h->tiles_h.size();
     h->n_gwork = (int)gwork.size();
-    h->n_sitems = (int)sitems.size();
-    h->d_sitems.alloc(sizeof(GWork) * std::max<size_t>(1, sitems.size()), s);
     h->d_torder.alloc(sizeof(int) * std::max<size_t>(1, torder.size()), s);
-    h2d(h->d_sitems.as<GWork>(), sitems, s);
+    h->d_forder.alloc(sizeof(int) * std::max<size_t>(1, forder.size()), s);
     h2d(h->d_torder.as<int>(), torder, s);
+    h2d(h->d_forder.as<int>(), forder, s);
+    build_stream_lists(h, h->stream_rows, s);
     h->d_tiles.alloc(sizeof(Tile) * std::max<size_t>(1, h->tiles_h.size()), s);
     h->d_xidx.alloc(sizeof(int) * std::max<long long>(1, nx), s);
     h->d_tidx.alloc(sizeof(int) * std::max<long long>(1, nf), s);
@@ -778,19 +817,19 @@ static void launch_dense_fill(rad_htree* h, const std::vector<DenseWork>& work, 
 
 template <class CT, class S>
 static void launch_factor_fill(rad_htree* h, const std::vector<UWork>& uw, const std::vector<VWork>& vw,
-                               const CT* Us, const CT* Vs, cudaStream_t s, void* pool = nullptr) {
+                               const CT* const* Ubase, const CT* const* Vbase, cudaStream_t s, void* pool = nullptr) {
     S* dst = static_cast<S*>(pool ? pool : h->far_pool.p);
     Scratch ws(s);
     if (!uw.empty()) {
         UWork* d = ws.get_n<UWork>(uw.size());
         h2d(d, uw, s);
-        { ProfScope ps_("aca_pack", s); u_fill_kernel<CT, S><<<(unsigned)uw.size(), 256, 0, s>>>(h->d_tiles.as<Tile>(), d, Us, dst); }
+        { ProfScope ps_("aca_pack", s); u_fill_kernel<CT, S><<<(unsigned)uw.size(), 256, 0, s>>>(h->d_tiles.as<Tile>(), d, Ubase, dst); }
         RAD_CHECK_LAUNCH();
     }
     if (!vw.empty()) {
         VWork* d = ws.get_n<VWork>(vw.size());
         h2d(d, vw, s);
-        { ProfScope ps_("aca_pack", s); v_fill_kernel<CT, S><<<(unsigned)vw.size(), 256, 0, s>>>(h->d_groups.as<Group>(), d, Vs, dst); }
+        { ProfScope ps_("aca_pack", s); v_fill_kernel<CT, S><<<(unsigned)vw.size(), 256, 0, s>>>(h->d_groups.as<Group>(), d, Vbase, dst); }
         RAD_CHECK_LAUNCH();
     }
 }
@@ -816,15 +855,96 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
         ov += round_up((long long)n * kmax, 8);
         oused += round_up(m, 16);
     }
-    RAD_REQUIRE((ou + ov) * (long long)sizeof(CT) <= (64ll << 30), RAD_ELIMIT, "ACA scratch exceeds 64 GiB");
-    std::vector<int> ranks;
-    std::vector<long long> evals;
-    CT* Us = nullptr;
-    CT* Vs = nullptr;
     hs_jobs.reset();
+    // ACA scratch holds kmax columns per block.  When that exceeds the
+    // budget (large batches), the jobs run in chunks, and after each chunk
+    // the first rank columns are compacted and the scratch is released.
+    size_t free_b = 0, total_b = 0;
+    RAD_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const long long budget =
+        p->scratch_mib > 0 ? (long long)p->scratch_mib << 20
+                           : std::max<long long>(1ll << 30, std::min<long long>((long long)(0.3 * (double)free_b), 24ll << 30));
+    std::vector<int> ranks(jobs.size(), 0);
+    std::vector<long long> evals(jobs.size(), 0);
+    std::vector<long long> src_u(jobs.size(), 0), src_v(jobs.size(), 0);
+    std::vector<int> job_chunk(jobs.size(), 0);
+    std::vector<const CT*> ubase, vbase;
     if (!jobs.empty()) {
         HostScope hs_("host_aca_launch_wait");
-        launch_aca<CT>(h, p, jobs, ranks, evals, nullptr, ws, Us, Vs, s);
+        if ((ou + ov) * (long long)sizeof(CT) <= budget) {
+            CT* Us = nullptr;
+            CT* Vs = nullptr;
+            launch_aca<CT>(h, p, jobs, ranks, evals, nullptr, ws, Us, Vs, s);
+            for (size_t j = 0; j < jobs.size(); ++j) {
+                src_u[j] = jobs[j].offU;
+                src_v[j] = jobs[j].offV;
+            }
+            ubase.push_back(Us);
+            vbase.push_back(Vs);
+        } else {
+            size_t j0 = 0;
+            while (j0 < jobs.size()) {
+                // jobs [j0, j1): scratch within the budget (at least one job)
+                size_t j1 = j0;
+                long long sz = 0;
+                while (j1 < jobs.size()) {
+                    const long long add = round_up((long long)jobs[j1].m * jobs[j1].kmax, 8) +
+                                          round_up((long long)jobs[j1].n * jobs[j1].kmax, 8);
+                    if (j1 > j0 && (sz + add) * (long long)sizeof(CT) > budget) break;
+                    sz += add;
+                    ++j1;
+                }
+                std::vector<AcaJob> cj(jobs.begin() + j0, jobs.begin() + j1);
+                const long long bu = cj.front().offU, bv = cj.front().offV, bs = cj.front().offUsed;
+                for (auto& j : cj) {
+                    j.offU -= bu;
+                    j.offV -= bv;
+                    j.offUsed -= bs;
+                }
+                std::vector<int> cr;
+                std::vector<long long> ce, cu(cj.size()), cv(cj.size());
+                Scratch cws(s);
+                CT* Us = nullptr;
+                CT* Vs = nullptr;
+                launch_aca<CT>(h, p, cj, cr, ce, nullptr, cws, Us, Vs, s);
+                long long tu = 0, tv = 0;
+                for (size_t q = 0; q < cj.size(); ++q) {
+                    cu[q] = tu;
+                    cv[q] = tv;
+                    const int k = std::max(cr[q], 0);
+                    tu += (long long)cj[q].m * k;
+                    tv += (long long)cj[q].n * k;
+                }
+                CT* Uc = ws.get_n<CT>(std::max<long long>(tu, 1));
+                CT* Vc = ws.get_n<CT>(std::max<long long>(tv, 1));
+                AcaJob* d_cj = cws.get_n<AcaJob>(cj.size());
+                int* d_cr = cws.get_n<int>(cj.size());
+                long long* d_cu = cws.get_n<long long>(cj.size());
+                long long* d_cv = cws.get_n<long long>(cj.size());
+                h2d(d_cj, cj, s);
+                h2d(d_cr, cr, s);
+                h2d(d_cu, cu, s);
+                h2d(d_cv, cv, s);
+                { ProfScope ps_("aca_compact", s); compact_kernel<CT><<<(unsigned)cj.size(), 256, 0, s>>>(d_cj, d_cr, d_cu, d_cv, Us, Vs, Uc, Vc); }
+                RAD_CHECK_LAUNCH();
+                for (size_t q = 0; q < cj.size(); ++q) {
+                    ranks[j0 + q] = cr[q];
+                    evals[j0 + q] = ce[q];
+                    src_u[j0 + q] = cu[q];
+                    src_v[j0 + q] = cv[q];
+                    job_chunk[j0 + q] = (int)ubase.size();
+                }
+                ubase.push_back(Uc);
+                vbase.push_back(Vc);
+                j0 = j1;
+            }
+        }
+    }
+    const CT** d_ubase = ws.get_n<const CT*>(std::max<size_t>(1, ubase.size()));
+    const CT** d_vbase = ws.get_n<const CT*>(std::max<size_t>(1, vbase.size()));
+    if (!ubase.empty()) {
+        RAD_CUDA(cudaMemcpyAsync(d_ubase, ubase.data(), sizeof(CT*) * ubase.size(), cudaMemcpyHostToDevice, s));
+        RAD_CUDA(cudaMemcpyAsync(d_vbase, vbase.data(), sizeof(CT*) * vbase.size(), cudaMemcpyHostToDevice, s));
     }
     auto hs_plan = std::make_unique<HostScope>("host_plan");
     std::vector<int> job_of(h->blocks.size(), -1);
@@ -903,18 +1023,18 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
             });
         } else if (bk.rank > 0) {
             const int k = bk.rank;
-            const AcaJob& jb = jobs[job_of[b]];
+            const int jb = job_of[b];
             const Group& gr = h->groups_h[bk.group];
             maxk = std::max(maxk, k);
             far_u += (long long)k * m;
             far_v += (long long)k * n;
             for_tiles(tiles, tile_at, bk.r0, bk.r1, [&](int t) {
                 h->far_pieces.push_back(Piece{b, t, tiles[t].kf});
-                uwork.push_back(UWork{t, tiles[t].r0 - bk.r0, m, k, tiles[t].kf, 0, jb.offU});
+                uwork.push_back(UWork{t, tiles[t].r0 - bk.r0, m, k, tiles[t].kf, job_chunk[jb], src_u[jb]});
                 far_runs.push_back(IdxRun{t, tiles[t].kf, gr.toff + bk.grow, k});
                 tiles[t].kf += k;
             });
-            vwork.push_back(VWork{bk.group, bk.grow, n, k, jb.offV});
+            vwork.push_back(VWork{bk.group, bk.grow, n, k, job_chunk[jb], 0, src_v[jb]});
         }
     }
     long long noff = 0, foff = 0;
@@ -940,9 +1060,9 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     upload_operator(h, near_runs, far_runs, s);
     if (h->near_dtype == RAD_F64) launch_dense_fill<double, double>(h, dwork, s);
     else launch_dense_fill<float, float>(h, dwork, s);
-    if (h->factor_dtype == RAD_F64) launch_factor_fill<CT, double>(h, uwork, vwork, Us, Vs, s);
-    else if (h->factor_dtype == RAD_F32) launch_factor_fill<CT, float>(h, uwork, vwork, Us, Vs, s);
-    else launch_factor_fill<CT, __nv_bfloat16>(h, uwork, vwork, Us, Vs, s);
+    if (h->factor_dtype == RAD_F64) launch_factor_fill<CT, double>(h, uwork, vwork, d_ubase, d_vbase, s);
+    else if (h->factor_dtype == RAD_F32) launch_factor_fill<CT, float>(h, uwork, vwork, d_ubase, d_vbase, s);
+    else launch_factor_fill<CT, __nv_bfloat16>(h, uwork, vwork, d_ubase, d_vbase, s);
     // accurate operator for mixed-precision refinement: FP32 factors
     h->far_pool_acc.release(s);
     h->has_accurate = false;
@@ -950,7 +1070,7 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
         if (h->factor_dtype == RAD_BF16) {
             h->far_pool_acc.alloc((size_t)std::max<long long>(foff, 16) * sizeof(float), s);
             RAD_CUDA(cudaMemsetAsync(h->far_pool_acc.p, 0, h->far_pool_acc.bytes, s));
-            launch_factor_fill<CT, float>(h, uwork, vwork, Us, Vs, s, h->far_pool_acc.p);
+            launch_factor_fill<CT, float>(h, uwork, vwork, d_ubase, d_vbase, s, h->far_pool_acc.p);
         }
         h->has_accurate = true;
     }
@@ -980,7 +1100,12 @@ void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
                 "near_dtype F64 requires factor_dtype F64 and vice versa");
     RAD_REQUIRE(p->accurate_dtype == -1 || p->accurate_dtype == RAD_F32, RAD_EINVAL,
                 "accurate_dtype must be -1 or RAD_F32");
+    RAD_REQUIRE(p->scratch_mib >= 0, RAD_EINVAL, "scratch_mib must be >= 0");
     RAD_REQUIRE(!h->from_dense, RAD_EINVAL, "a dense-wrapped handle cannot be recompressed");
+    drop_product_graph(h);
+    h->stream_rows = kStreamRows;
+    h->grid_a1 = h->grid_b1 = h->grid_a2 = h->grid_b2 = 0;
+    h->tuned = 0;
     h->compressed = false;
     h->factor_dtype = p->factor_dtype;
     h->near_dtype = p->near_dtype;

@@ -39,6 +39,8 @@ std::vector<ProfRec> g_prof;
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(); }
 
 bool profiling_enabled() {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -221,6 +223,81 @@ static void check_tree_params(int64_t n, const rad_tree_params* p) {
 
 using namespace rad;
 
+namespace rad {
+
+void drop_product_graph(const rad_htree* h) {
+    if (!h->graph) return;
+    if (h->graph->exec) RAD_CUDA(cudaStreamSynchronize(h->graph->stream));
+    h->graph.reset();
+}
+
+// The graph path of rad_hmatvec (device arrays only).  Returns false when the
+// call must take the ordinary path.
+static bool product_via_graph(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx, void* y, int64_t ldy,
+                              int64_t nrhs, cudaStream_t s) {
+    if (profiling_enabled()) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    RAD_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return false;   // the caller is capturing: plain launches
+    if (!h->graph) h->graph = std::make_unique<ProductGraph>();
+    ProductGraph& g = *h->graph;
+    std::lock_guard<std::mutex> lk(g.mu);
+    const bool same = g.x == x && g.y == y && g.ldx == ldx && g.ldy == ldy && g.nrhs == nrhs && g.dtype == dtype &&
+                      g.stream == s;
+    if (same && g.exec) {
+        RAD_CUDA(cudaGraphLaunch(g.exec, s));
+        note_launches(g.kernels);
+        return true;
+    }
+    if (!same) {
+        if (g.exec) {
+            RAD_CUDA(cudaStreamSynchronize(g.stream));
+            RAD_CUDA(cudaGraphExecDestroy(g.exec));
+            g.exec = nullptr;
+        }
+        g.x = x;
+        g.y = y;
+        g.ldx = ldx;
+        g.ldy = ldy;
+        g.nrhs = nrhs;
+        g.dtype = dtype;
+        g.stream = s;
+        g.hits = 1;
+        return false;
+    }
+    // second identical call: capture gather + product + scatter once
+    const int n = (int)h->n;
+    const int nr = (int)nrhs;
+    const bool op64 = h->op_is_f64();
+    const size_t osz = op64 ? 8 : 4;
+    g.X.alloc(osz * n * nr, s);
+    g.Y.alloc(osz * n * nr, s);
+    g.T.alloc(apply_workspace_bytes(h, nr), s);
+    if (!g.capture) RAD_CUDA(cudaStreamCreateWithFlags(&g.capture, cudaStreamNonBlocking));
+    const long long k0 = launch_count();
+    RAD_CUDA(cudaStreamBeginCapture(g.capture, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t graph = nullptr;
+    try {
+        gather_user_to_tree(h, dtype, x, ldx, nr, g.X.p, nr, op64, g.capture);
+        apply_tree(h, g.X.p, nr, g.Y.p, nr, nr, Epi{kStore, nullptr, nullptr, nullptr, 0}, g.T.p, g.capture);
+        scatter_tree_to_user(h, g.Y.p, nr, nr, op64, dtype, y, ldy, g.capture);
+    } catch (...) {
+        cudaStreamEndCapture(g.capture, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        (void)cudaGetLastError();
+        throw;
+    }
+    RAD_CUDA(cudaStreamEndCapture(g.capture, &graph));
+    g.kernels = launch_count() - k0;
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    RAD_CUDA(ie);
+    RAD_CUDA(cudaGraphLaunch(g.exec, s));
+    return true;
+}
+
+}  // namespace rad
+
 extern "C" {
 
 int rad_version(void) { return 10000; }
@@ -380,6 +457,7 @@ int rad_compress_aca(rad_htree* h, const rad_aca_params* p, void* stream) {
     });
 }
 
+
 int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx, void* y, int64_t ldy, int64_t nrhs,
                 void* stream) {
     return guarded([&] {
@@ -389,6 +467,7 @@ int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx, v
         RAD_REQUIRE(nrhs >= 1 && nrhs <= 4096, RAD_EINVAL, "nrhs must be in [1, 4096]");
         RAD_REQUIRE(ldx >= h->n && ldy >= h->n, RAD_EINVAL, "leading dimension smaller than n");
         cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (is_device_ptr(x) && is_device_ptr(y) && product_via_graph(h, dtype, x, ldx, y, ldy, nrhs, s)) return;
         const int n = (int)h->n;
         const int nr = (int)nrhs;
         const size_t esz = dtype == RAD_F64 ? 8 : 4;
@@ -514,6 +593,12 @@ int rad_htree_get_stats(const rad_htree* h, rad_htree_stats* st) {
         st->far_v_entries = h->far_v_entries;
         st->n_tiles = h->n_tiles;
         st->bytes_accurate = h->far_pool_acc.p ? h->far_entries * 4 : 0;
+        st->tuned = h->tuned;
+        st->stream_rows = h->stream_rows;
+        st->grid_a1 = h->grid_a1;
+        st->grid_b1 = h->grid_b1;
+        st->grid_a2 = h->grid_a2;
+        st->grid_b2 = h->grid_b2;
     });
 }
 
@@ -558,6 +643,13 @@ int rad_htree_export_block(const rad_htree* h, int64_t block, double* D, double*
     return guarded([&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null handle");
         export_block(h, block, D, U, V);
+    });
+}
+
+int rad_htree_autotune(rad_htree* h, void* stream) {
+    return guarded([&] {
+        RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null argument");
+        autotune(h, static_cast<cudaStream_t>(stream));
     });
 }
 

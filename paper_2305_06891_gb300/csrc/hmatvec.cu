@@ -100,10 +100,10 @@ __device__ __forceinline__ void stream_panel4(const S* __restrict__ P, long long
 // Streaming kernels for a few right-hand sides: one pass over every panel,
 // thread (q, g) owns rows 4q .. 4q+3 for all NCOL columns.
 template <class FS, class AT, int NCOL>
-__global__ void __launch_bounds__(256) far_vt_stream(OpView op, const AT* __restrict__ X, int ldx,
+__device__ __forceinline__ void far_vt_stream_item(int it_, OpView op, const AT* __restrict__ X, int ldx,
                                                      AT* __restrict__ T, int ldt) {
     __shared__ AT part[NCOL][1024];
-    const GWork w = op.sitems[blockIdx.x];
+    const GWork w = op.sitems[it_];
     const Group gr = op.groups[w.g];
     const int quads = (w.rows + 3) / 4;
     const int G = 256 / quads;
@@ -140,16 +140,26 @@ __global__ void __launch_bounds__(256) far_vt_stream(OpView op, const AT* __rest
     }
 }
 
+template <class FS, class AT, int NCOL>
+__global__ void __launch_bounds__(256) far_vt_stream(OpView op, const AT* __restrict__ X, int ldx, AT* __restrict__ T, int ldt) {
+    // grid-stride over the work items: one CTA per item, or a persistent grid
+    for (int it = blockIdx.x; it < op.n_sitems; it += gridDim.x) {
+        far_vt_stream_item<FS, AT, NCOL>(it, op, X, ldx, T, ldt);
+        __syncthreads();
+    }
+}
+
+
 // ---------------------------------------------------------------- 1 RHS, two phases
 // Phase A: far-field items (T = V^T x, at most 128 rows of a column group)
 // and the tiles' dense panels (Yn = near x) in one launch, heaviest first, so
 // that the short items fill the tail of the long ones.  Phase B: the tiles'
 // low-rank panels, Y = epilogue(Yn + U T).
 template <class NS, class FS, class AT>
-__global__ void __launch_bounds__(256)
-single_phase_a(OpView op, const AT* __restrict__ x, AT* __restrict__ T, AT* __restrict__ Yn) {
+__device__ __forceinline__ void
+single_phase_a_item(int it_, OpView op, const AT* __restrict__ x, AT* __restrict__ T, AT* __restrict__ Yn) {
     __shared__ AT part[1024];
-    const int code = op.aorder[blockIdx.x];
+    const int code = op.aorder[it_];
     AT acc[4] = {0, 0, 0, 0};
     int quads, G, rows;
     if (code >= 0) {
@@ -208,11 +218,21 @@ single_phase_a(OpView op, const AT* __restrict__ x, AT* __restrict__ T, AT* __re
     }
 }
 
+template <class NS, class FS, class AT>
+__global__ void __launch_bounds__(256) single_phase_a(OpView op, const AT* __restrict__ x, AT* __restrict__ T, AT* __restrict__ Yn) {
+    // grid-stride over the work items: one CTA per item, or a persistent grid
+    for (int it = blockIdx.x; it < op.n_aitems; it += gridDim.x) {
+        single_phase_a_item<NS, FS, AT>(it, op, x, T, Yn);
+        __syncthreads();
+    }
+}
+
+
 template <class FS, class AT>
-__global__ void __launch_bounds__(256)
-single_phase_b(OpView op, const AT* __restrict__ T, const AT* __restrict__ Yn, void* Y, Epi epi) {
+__device__ __forceinline__ void
+single_phase_b_item(int it_, OpView op, const AT* __restrict__ T, const AT* __restrict__ Yn, void* Y, Epi epi) {
     __shared__ AT part[1024];
-    const Tile t = op.tiles[op.forder[blockIdx.x]];
+    const Tile t = op.tiles[op.forder[it_]];
     const int quads = t.ld / 4;
     const int G = 256 / quads;
     const int q = threadIdx.x % quads, g = threadIdx.x / quads;
@@ -230,6 +250,16 @@ single_phase_b(OpView op, const AT* __restrict__ T, const AT* __restrict__ Yn, v
         epilogue<AT>(epi, Y, 1, t.r0 + row, 0, s);
     }
 }
+
+template <class FS, class AT>
+__global__ void __launch_bounds__(256) single_phase_b(OpView op, const AT* __restrict__ T, const AT* __restrict__ Yn, void* Y, Epi epi) {
+    // grid-stride over the work items: one CTA per item, or a persistent grid
+    for (int it = blockIdx.x; it < op.n_tiles; it += gridDim.x) {
+        single_phase_b_item<FS, AT>(it, op, T, Yn, Y, epi);
+        __syncthreads();
+    }
+}
+
 
 template <class S, class AT, int NCOL>
 __device__ __forceinline__ void stream_cols(const S* __restrict__ P, long long ld, int kcols, int g, int G,
@@ -249,11 +279,11 @@ __device__ __forceinline__ void stream_cols(const S* __restrict__ P, long long l
 }
 
 template <class NS, class FS, class AT, int NCOL>
-__global__ void __launch_bounds__(256)
-rows_stream(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ T, int ldt, void* Y, int ldy,
+__device__ __forceinline__ void
+rows_stream_item(int it_, OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ T, int ldt, void* Y, int ldy,
             Epi epi) {
     __shared__ AT part[NCOL][1024];
-    const Tile t = op.tiles[op.torder[blockIdx.x]];
+    const Tile t = op.tiles[op.torder[it_]];
     const int quads = t.ld / 4;
     const int G = 256 / quads;
     const int q = threadIdx.x % quads, g = threadIdx.x / quads;
@@ -279,6 +309,16 @@ rows_stream(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__
         }
     }
 }
+
+template <class NS, class FS, class AT, int NCOL>
+__global__ void __launch_bounds__(256) rows_stream(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ T, int ldt, void* Y, int ldy, Epi epi) {
+    // grid-stride over the work items: one CTA per item, or a persistent grid
+    for (int it = blockIdx.x; it < op.n_tiles; it += gridDim.x) {
+        rows_stream_item<NS, FS, AT, NCOL>(it, op, X, ldx, T, ldt, Y, ldy, epi);
+        __syncthreads();
+    }
+}
+
 
 // ---------------------------------------------------------------- double-float
 // FP64-grade sums on the FP32 pipe (GB300's FP64 pipe is narrow): a value is
@@ -630,14 +670,20 @@ inline int rn_for(int max_ld, int nc) {
     return std::max(1, std::min(8, (nc + cg - 1) / cg));
 }
 
+// Grid of a grid-stride launch over `items` work items: one CTA per item, or
+// the tuned persistent size.
+inline unsigned grid_of(int tuned, int items) {
+    return (unsigned)std::max(1, tuned > 0 ? std::min(tuned, items) : items);
+}
+
 template <class NS, class FS, class AT, int NCOL>
 void launch_stream(const rad_htree* h, const OpView& op, const AT* X, int ldx, AT* T, int ldt, void* Y, int ldy,
                    const Epi& epi, cudaStream_t s) {
     if (op.n_gwork > 0) {
-        { ProfScope ps_("hmv_far_vt", s); far_vt_stream<FS, AT, NCOL><<<(unsigned)op.n_sitems, 256, 0, s>>>(op, X, ldx, T, ldt); }
+        { ProfScope ps_("hmv_far_vt", s); far_vt_stream<FS, AT, NCOL><<<grid_of(h->grid_a2, op.n_sitems), 256, 0, s>>>(op, X, ldx, T, ldt); }
         RAD_CHECK_LAUNCH();
     }
-    { ProfScope ps_("hmv_rows", s); rows_stream<NS, FS, AT, NCOL><<<op.n_tiles, 256, 0, s>>>(op, X, ldx, T, ldt, Y, ldy, epi); }
+    { ProfScope ps_("hmv_rows", s); rows_stream<NS, FS, AT, NCOL><<<grid_of(h->grid_b2, op.n_tiles), 256, 0, s>>>(op, X, ldx, T, ldt, Y, ldy, epi); }
     RAD_CHECK_LAUNCH();
 }
 
@@ -664,9 +710,9 @@ void apply_t(const rad_htree* h, const OpView& op, const AT* X, int ldx, void* Y
              AT* T, cudaStream_t s) {
     if (nrhs == 1) {
         AT* Yn = T + std::max(1, op.sum_rank);
-        { ProfScope ps_("hmv_phase_a", s); single_phase_a<NS, FS, AT><<<(unsigned)op.n_aitems, 256, 0, s>>>(op, X, T, Yn); }
+        { ProfScope ps_("hmv_phase_a", s); single_phase_a<NS, FS, AT><<<grid_of(h->grid_a1, op.n_aitems), 256, 0, s>>>(op, X, T, Yn); }
         RAD_CHECK_LAUNCH();
-        { ProfScope ps_("hmv_phase_b", s); single_phase_b<FS, AT><<<op.n_tiles, 256, 0, s>>>(op, T, Yn, Y, epi); }
+        { ProfScope ps_("hmv_phase_b", s); single_phase_b<FS, AT><<<grid_of(h->grid_b1, op.n_tiles), 256, 0, s>>>(op, T, Yn, Y, epi); }
         RAD_CHECK_LAUNCH();
         return;
     }
@@ -818,6 +864,123 @@ void scatter_tree_to_user(const rad_htree* h, const void* Y, int ldY, int nrhs, 
         else { ProfScope ps_("permute", s); scatter_kernel<float, float><<<grid, 256, 0, s>>>(n, nrhs, (const float*)Y, ldY, perm, (float*)y, ldy); }
     }
     RAD_CHECK_LAUNCH();
+}
+
+
+// ---------------------------------------------------------------- autotuner
+// Times the streaming products on this handle's operator for every
+// candidate (far-field item rows x grid policy of each launch) and keeps the
+// fastest.  The grid policy does not change results (every item is computed
+// by one CTA in the same order); the item rows change the order of the sums
+// over a column group's columns.
+namespace {
+
+template <class NS, class FS, class AT>
+struct Tuner {
+    rad_htree* h;
+    cudaStream_t s;
+    AT *X, *T, *Yn;
+    void* Y;
+    cudaEvent_t e0, e1;
+    template <class F>
+    float time(F&& launch) {
+        launch();
+        RAD_CHECK_LAUNCH();
+        float best = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            RAD_CUDA(cudaEventRecord(e0, s));
+            launch();
+            RAD_CHECK_LAUNCH();
+            RAD_CUDA(cudaEventRecord(e1, s));
+            RAD_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            RAD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            best = std::min(best, ms);
+        }
+        return best;
+    }
+    // best grid (0 = one CTA per item) and its time for one launch kind
+    std::pair<int, float> pick(int kind, const std::vector<int>& grids) {
+        const OpView op = h->view();
+        const Epi epi{kStore, nullptr, nullptr, nullptr, 0};
+        std::pair<int, float> best{0, 1e30f};
+        for (int g : grids) {
+            float t = 0.0f;
+            if (kind == 0) t = time([&] { single_phase_a<NS, FS, AT><<<grid_of(g, op.n_aitems), 256, 0, s>>>(op, X, T, Yn); });
+            if (kind == 1) t = time([&] { single_phase_b<FS, AT><<<grid_of(g, op.n_tiles), 256, 0, s>>>(op, T, Yn, Y, epi); });
+            if (kind == 2 && op.n_sitems > 0)
+                t = time([&] { far_vt_stream<FS, AT, 2><<<grid_of(g, op.n_sitems), 256, 0, s>>>(op, X, 2, T, 4); });
+            if (kind == 3)
+                t = time([&] { rows_stream<NS, FS, AT, 2><<<grid_of(g, op.n_tiles), 256, 0, s>>>(op, X, 2, T, 4, Y, 2, epi); });
+            if (t < best.second) best = {g, t};
+        }
+        return best;
+    }
+    void run() {
+        int sms = 0, dev = 0;
+        RAD_CUDA(cudaGetDevice(&dev));
+        RAD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const std::vector<int> grids{0, 2 * sms, 4 * sms, 8 * sms};
+        const int rows_cand[3] = {64, 128, 256};
+        float best_total = 1e30f;
+        int best_rows = h->stream_rows, ga1 = 0, gb1 = 0, ga2 = 0, gb2 = 0;
+        for (int rows : rows_cand) {
+            build_stream_lists(h, rows, s);
+            const auto a1 = pick(0, grids), b1 = pick(1, grids), a2 = pick(2, grids), b2 = pick(3, grids);
+            const float total = a1.second + b1.second + a2.second + b2.second;
+            if (total < best_total) {
+                best_total = total;
+                best_rows = rows;
+                ga1 = a1.first;
+                gb1 = b1.first;
+                ga2 = a2.first;
+                gb2 = b2.first;
+            }
+        }
+        build_stream_lists(h, best_rows, s);
+        h->grid_a1 = ga1;
+        h->grid_b1 = gb1;
+        h->grid_a2 = ga2;
+        h->grid_b2 = gb2;
+        h->tuned = 1;
+    }
+};
+
+}  // namespace
+
+void autotune(rad_htree* h, cudaStream_t s) {
+    RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed (call rad_compress_aca)");
+    drop_product_graph(h);
+    Scratch ws(s);
+    const int n = (int)h->n;
+    const size_t esz = h->op_is_f64() ? 8 : 4;
+    cudaEvent_t e0, e1;
+    RAD_CUDA(cudaEventCreate(&e0));
+    RAD_CUDA(cudaEventCreate(&e1));
+    void* X = ws.get(esz * 2 * (size_t)n);
+    void* Y = ws.get(8 * 2 * (size_t)n);
+    void* T = ws.get(apply_workspace_bytes(h, 4) + esz * (size_t)n);
+    RAD_CUDA(cudaMemsetAsync(X, 0, esz * 2 * (size_t)n, s));
+    RAD_CUDA(cudaMemsetAsync(T, 0, apply_workspace_bytes(h, 4) + esz * (size_t)n, s));
+    try {
+        if (h->op_is_f64()) {
+            Tuner<double, double, double> t{h, s, (double*)X, (double*)T, (double*)T + std::max(1, h->sum_rank) * 4, Y, e0, e1};
+            t.run();
+        } else if (h->factor_dtype == RAD_F32) {
+            Tuner<float, float, float> t{h, s, (float*)X, (float*)T, (float*)T + std::max(1, h->sum_rank) * 4, Y, e0, e1};
+            t.run();
+        } else {
+            Tuner<float, __nv_bfloat16, float> t{h, s, (float*)X, (float*)T, (float*)T + std::max(1, h->sum_rank) * 4, Y, e0, e1};
+            t.run();
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    RAD_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace rad

@@ -8,6 +8,8 @@
 
 #include <cstdint>
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -35,6 +37,8 @@ void set_last_error(const std::string& msg);
     } while (0)
 
 void note_launch();
+void note_launches(long long k);
+long long launch_count();
 #define RAD_CHECK_LAUNCH()                \
     do {                                  \
         ::rad::note_launch();             \
@@ -253,11 +257,41 @@ constexpr int kStreamRows = 128;
 }  // namespace rad
 
 // The opaque handle (global namespace: it is the C type rad_htree).
+// A one-product CUDA graph kept by a handle: rad_hmatvec on device arrays
+// captures (gather, product, scatter) on the second identical call (same
+// arrays, leading dimensions, columns, dtype and stream) and replays it
+// afterwards; its tree-order vectors and workspace belong to the cache.
+struct ProductGraph {
+    std::mutex mu;
+    const void* x = nullptr;
+    void* y = nullptr;
+    int64_t ldx = 0, ldy = 0, nrhs = 0;
+    int dtype = -1;
+    cudaStream_t stream = nullptr;
+    int hits = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t capture = nullptr;
+    long long kernels = 0;
+    rad::DevBuf X, Y, T;
+    ~ProductGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (capture) cudaStreamDestroy(capture);
+    }
+};
+
 struct rad_htree {
     // The arrays below may still be read by work queued on any stream when
     // the handle goes away (rad_htree_free, or a call that failed half way):
     // wait for the device before they return to the pool.
     ~rad_htree() { (void)cudaDeviceSynchronize(); }
+    mutable std::unique_ptr<ProductGraph> graph;
+    // launch configuration of the streaming products, chosen by
+    // rad_htree_autotune: rows per far-field item, and grid sizes (0 = one
+    // CTA per work item, else a persistent grid-stride launch) of phase A /
+    // phase B for one column (a1, b1) and for 2-4 columns (a2, b2)
+    int stream_rows = rad::kStreamRows;
+    int grid_a1 = 0, grid_b1 = 0, grid_a2 = 0, grid_b2 = 0;
+    int tuned = 0;
     int64_t n = 0;
     // segment (cavity) boundaries of a batch handle: cavity c holds facets
     // [seg[c], seg[c+1]) in user order and in tree order; {0, n} otherwise
@@ -362,6 +396,9 @@ void apply_tree_acc(const rad_htree* h, const double* X, int ldx, double* Y, int
                     double* T_ws, cudaStream_t s);
 size_t apply_workspace_bytes_acc(const rad_htree* h, int nrhs);
 size_t apply_workspace_bytes(const rad_htree* h, int nrhs);
+void build_stream_lists(rad_htree* h, int rows, cudaStream_t s);
+void autotune(rad_htree* h, cudaStream_t s);
+void drop_product_graph(const rad_htree* h);
 void gather_user_to_tree(const rad_htree* h, int dtype_in, const void* x, int64_t ldx, int nrhs,
                          void* X, int ldX, bool op64, cudaStream_t s);
 void scatter_tree_to_user(const rad_htree* h, const void* Y, int ldY, int nrhs, bool op64,

@@ -101,3 +101,18 @@ def test_batch_rejects_bad_counts():
         r.rad_build_htree_batch(v, [v.shape[0], 0])
     with pytest.raises(Exception):
         r.rad_build_htree_batch(v, [v.shape[0] + 1])
+
+
+def test_chunked_aca_equals_one_pass(batch):
+    """A scratch bound of 1 MiB forces the ACA into many chunks (each
+    compacted before the next); ranks and products are unchanged."""
+    r, cavs, counts, hb, singles = batch
+    n = int(sum(counts))
+    x = np.random.default_rng(5).uniform(0.5, 1.5, (n, 2))
+    r.rad_compress_aca(hb, 1e-6, 64, "partial", "f32", "f32")
+    st1, y1 = r.rad_htree_get_stats(hb), r.rad_hmatvec(hb, x)
+    r.rad_compress_aca(hb, 1e-6, 64, "partial", "f32", "f32", scratch_mib=1)
+    st2, y2 = r.rad_htree_get_stats(hb), r.rad_hmatvec(hb, x)
+    for k in ("sum_rank", "far_entries", "near_entries", "aca_entries", "n_dense_fallback"):
+        assert st1[k] == st2[k], k
+    np.testing.assert_array_equal(y1, y2)
