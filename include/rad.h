@@ -80,7 +80,7 @@ typedef struct {
  * second copy.
  * scratch_mib bounds the device scratch of partial-pivot ACA (max_rank
  * columns of U and V per admissible block, before the ranks are known):
- * 0 = 30% of the free device memory, at most 24 GiB, at least 1 GiB; > 0 =
+ * 0 = 30% of the free device memory, at most 48 GiB, at least 1 GiB; > 0 =
  * that many MiB.  Blocks beyond the bound are compressed in further chunks,
  * each compacted to its ranks before the next starts; the result does not
  * depend on the chunking. */

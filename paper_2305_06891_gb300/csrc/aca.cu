@@ -863,7 +863,7 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     RAD_CUDA(cudaMemGetInfo(&free_b, &total_b));
     const long long budget =
         p->scratch_mib > 0 ? (long long)p->scratch_mib << 20
-                           : std::max<long long>(1ll << 30, std::min<long long>((long long)(0.3 * (double)free_b), 24ll << 30));
+                           : std::max<long long>(1ll << 30, std::min<long long>((long long)(0.3 * (double)free_b), 48ll << 30));
     std::vector<int> ranks(jobs.size(), 0);
     std::vector<long long> evals(jobs.size(), 0);
     std::vector<long long> src_u(jobs.size(), 0), src_v(jobs.size(), 0);

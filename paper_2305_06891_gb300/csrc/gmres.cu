@@ -361,7 +361,7 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
         RAD_CUDA(cudaMemcpyAsync(active, hact.data(), sizeof(int) * nvc, cudaMemcpyHostToDevice, s));
         { ProfScope ps_("gmres_small", s); start_cycle_kernel<<<grid_for(nv), 256, 0, s>>>(W, beta2, active, V, X32, n, nc, seg); }
         RAD_CHECK_LAUNCH();
-        { ProfScope ps_("gmres_small", s); init_g_kernel<<<grid_for(nvc), 128, 0, s>>>(R, nvc, beta2, g, jc); }
+        { ProfScope ps_("gmres_small", s); init_g_kernel<<<grid_for(nvc, 128), 128, 0, s>>>(R, nvc, beta2, g, jc); }
         RAD_CHECK_LAUNCH();
         for (int j = 0; j < R && total_iters < p->max_iter; ++j) {
             double* Vj = V + (long long)j * nv;

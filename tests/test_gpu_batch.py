@@ -116,3 +116,32 @@ def test_chunked_aca_equals_one_pass(batch):
     for k in ("sum_rank", "far_entries", "near_entries", "aca_entries", "n_dense_fallback"):
         assert st1[k] == st2[k], k
     np.testing.assert_array_equal(y1, y2)
+
+
+def test_many_cavities_each_converge_like_alone():
+    """More virtual columns (cavity x right-hand side) than one CTA of the
+    per-column kernels covers: every cavity still solves as it would alone."""
+    r = rad()
+    rng = cv.rng_for(91)
+    cavs = []
+    for k in range(90):
+        a, b = rng.uniform(1.0, 3.0, 2)
+        verts = cv.box(1.0, float(a), float(b), 2, 3, 3)
+        n = verts.shape[0]
+        cavs.append((verts, rng.uniform(0.3, 0.9, n), rng.uniform(300.0, 1200.0, (n, 1))))
+    verts = np.concatenate([c[0] for c in cavs])
+    counts = [c[0].shape[0] for c in cavs]
+    off = np.concatenate([[0], np.cumsum(counts)])
+    hb = r.rad_build_htree_batch(verts, counts, leaf_size=16, eta_adm=1.0)
+    r.rad_compress_aca(hb, 1e-10, 64, "partial", "f64", "f64")
+    eps = np.concatenate([c[1] for c in cavs])
+    T = np.concatenate([c[2] for c in cavs])
+    qb, info = r.rad_solve_flux(hb, eps, T, SIGMA_SB, tol=1e-10)
+    assert info["status"] == 0 and info["max_rel_residual"] <= 1e-10
+    for k in (0, 41, 89):
+        h = r.rad_build_htree(cavs[k][0], leaf_size=16, eta_adm=1.0)
+        r.rad_compress_aca(h, 1e-10, 64, "partial", "f64", "f64")
+        qs, _ = r.rad_solve_flux(h, cavs[k][1], cavs[k][2], SIGMA_SB, tol=1e-10)
+        h.free()
+        assert rel(qb[off[k]:off[k + 1]], qs) <= 1e-12
+    hb.free()
