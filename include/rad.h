@@ -324,6 +324,75 @@ int64_t rad_launch_count(void);
 int rad_profile_enable(int32_t on);
 int rad_profile_read(int32_t max_kernels, char* names, int64_t* counts, double* total_ms);
 
+/* ------------------------------------------------------------ serving
+ * A flux-solve server (no counterpart in the paper; a runtime around the
+ * calls above).  Cavities are registered once; each request is a flux solve
+ * (rad_solve_flux) on a registered cavity with its own emissivities and
+ * temperature fields, e.g. one time step of a transient computation.
+ *
+ * Continuous batching: `slots` worker threads, each with its own CUDA
+ * stream, take requests as they arrive; the requests in flight run
+ * concurrently on the device.  A cavity's compressed operator is built on
+ * its first request and stays resident in device memory for later ones.
+ * Admission is by a device-memory budget: a request whose cavity is not
+ * resident waits until its operator fits (estimated from the facet count,
+ * corrected to the actual size once built) next to the resident ones; idle
+ * resident operators are evicted least recently used first.  Requests
+ * whose cavity is resident are admitted ahead of waiting ones.  Every
+ * request's arithmetic is the same alone and in any mix: each runs on one
+ * stream with deterministic kernels on the same operator bits.
+ *
+ * Requests take host arrays; the caller keeps eps, T and q alive until
+ * rad_server_wait returns for the ticket. */
+typedef struct rad_server rad_server;
+
+typedef struct {
+    int32_t slots;               /* concurrent requests (worker threads), >= 1 */
+    int32_t reserved;
+    int64_t hbm_budget_bytes;    /* resident operators + request workspaces   */
+    rad_tree_params tree;        /* cluster/block tree of a new cavity         */
+    rad_aca_params aca;          /* its compression                            */
+    rad_solve_params solve;      /* every request's solve                      */
+} rad_server_params;
+
+typedef struct {
+    int32_t status;              /* RAD_OK, RAD_ENOTCONV or the failing code   */
+    int32_t built;               /* 1 if this request built its operator      */
+    int32_t iters;               /* GMRES iterations                           */
+    int32_t refinements;         /* refinement steps                           */
+    double  max_rel_residual;    /* as in rad_solve_info                       */
+    double  queue_ms;            /* submit -> start on a worker               */
+    double  service_ms;          /* start -> done (build, compress, solve)    */
+    double  latency_ms;          /* submit -> done                             */
+    int32_t slot;                /* worker that ran it                         */
+    int32_t reserved;
+} rad_request_info;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t builds, evictions;
+    int64_t resident_bytes;      /* operators resident now                     */
+    int64_t peak_bytes;          /* peak of resident + reserved                */
+    int32_t resident_cavities, in_flight;
+    double  p50_latency_ms, p99_latency_ms, max_latency_ms;
+    double  mean_service_ms;
+} rad_server_stats;
+
+int rad_server_create(const rad_server_params* p, rad_server** out);
+/* Registers a cavity (verts copied from host or device; n triangles as in
+ * rad_build_htree); nothing is built until a request needs it. */
+int rad_server_add_cavity(rad_server* s, int64_t n, const double* verts, int64_t* cavity_id);
+/* Queues a flux solve of m fields on a registered cavity (arguments as in
+ * rad_solve_flux, host arrays); returns at once with a ticket. */
+int rad_server_submit(rad_server* s, int64_t cavity_id, const double* eps, const double* T, int64_t ldT,
+                      int64_t m, double sigma, double* q, int64_t ldq, int64_t* ticket);
+/* Blocks until the ticket's request is done; its q is written.  Returns the
+ * request's status (info may be NULL). */
+int rad_server_wait(rad_server* s, int64_t ticket, rad_request_info* info);
+int rad_server_get_stats(rad_server* s, rad_server_stats* st);
+/* Waits for every queued request, stops the workers, frees the operators. */
+int rad_server_destroy(rad_server* s);
+
 /* Library version: major * 10000 + minor * 100 + patch. */
 int rad_version(void);
 

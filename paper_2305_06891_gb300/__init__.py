@@ -58,6 +58,25 @@ class _SolveInfo(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class _ServerParams(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("reserved", C.c_int32), ("hbm_budget_bytes", C.c_int64),
+                ("tree", _TreeParams), ("aca", _AcaParams), ("solve", _SolveParams)]
+
+
+class _RequestInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("built", C.c_int32), ("iters", C.c_int32), ("refinements", C.c_int32),
+                ("max_rel_residual", C.c_double), ("queue_ms", C.c_double), ("service_ms", C.c_double),
+                ("latency_ms", C.c_double), ("slot", C.c_int32), ("reserved", C.c_int32)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("builds", C.c_int64), ("evictions", C.c_int64), ("resident_bytes", C.c_int64),
+                ("peak_bytes", C.c_int64), ("resident_cavities", C.c_int32), ("in_flight", C.c_int32),
+                ("p50_latency_ms", C.c_double), ("p99_latency_ms", C.c_double), ("max_latency_ms", C.c_double),
+                ("mean_service_ms", C.c_double)]
+
+
 class _Stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("leaf_size", C.c_int32), ("n_nodes", C.c_int32),
                 ("n_leaf_clusters", C.c_int32), ("depth", C.c_int32), ("n_blocks", C.c_int64),
@@ -97,6 +116,12 @@ def _load():
         "rad_htree_export_block": (C.c_int, [H, i64, vp, vp, vp]),
         "rad_htree_free": (C.c_int, [H]),
         "rad_htree_autotune": (C.c_int, [H, vp]),
+        "rad_server_create": (C.c_int, [C.POINTER(_ServerParams), C.POINTER(vp)]),
+        "rad_server_add_cavity": (C.c_int, [vp, i64, vp, C.POINTER(i64)]),
+        "rad_server_submit": (C.c_int, [vp, i64, vp, vp, i64, i64, dbl, vp, i64, C.POINTER(i64)]),
+        "rad_server_wait": (C.c_int, [vp, i64, C.POINTER(_RequestInfo)]),
+        "rad_server_get_stats": (C.c_int, [vp, C.POINTER(_ServerStats)]),
+        "rad_server_destroy": (C.c_int, [vp]),
         "rad_launch_count": (C.c_int64, []),
         "rad_profile_enable": (C.c_int, [i32]),
         "rad_profile_read": (C.c_int, [i32, vp, vp, vp]),
@@ -375,6 +400,97 @@ def rad_solve_reflection(h: HTree, eps, B, tol: float = 1e-10, restart: int = 30
     return Y, d
 
 
+class Server:
+    """Flux-solve server (continuous batching over resident operators; see
+    ``rad_server_create``).  Host arrays only; ``submit`` keeps references to
+    its arrays until ``wait`` returns the flux."""
+
+    def __init__(self, slots: int = 4, hbm_budget_bytes: int = 64 << 30, leaf_size: int = 64,
+                 eta_adm: float = 1.0, aca_tol: float = 1e-6, max_rank: int = 64, factor_dtype: str = "bf16",
+                 near_dtype: str = "f32", accurate_dtype: str | None = "f32", tol: float = 1e-8,
+                 restart: int = 30, max_iter: int = 1000, refine: bool = True, inner_tol: float = 1e-4,
+                 max_refine: int = 10, aca_scratch_mib: int = 0):
+        acc = -1 if accurate_dtype is None else _DT[accurate_dtype]
+        p = _ServerParams(int(slots), 0, int(hbm_budget_bytes), _TreeParams(int(leaf_size), 0, float(eta_adm)),
+                          _AcaParams(float(aca_tol), int(max_rank), RAD_ACA_PARTIAL, _DT[factor_dtype],
+                                     _DT[near_dtype], acc, int(aca_scratch_mib)),
+                          _SolveParams(float(tol), int(restart), int(max_iter), 1 if refine else 0,
+                                       int(max_refine), float(inner_tol)))
+        out = C.c_void_p()
+        _check(_lib.rad_server_create(C.byref(p), C.byref(out)))
+        self._p = out
+        self._keep = {}
+        self._n = []
+
+    def add_cavity(self, verts) -> int:
+        v = _f64_rowmajor(verts)
+        cid = C.c_int64()
+        _check(_lib.rad_server_add_cavity(self._p, int(v.shape[0]), _ptr(v), C.byref(cid)))
+        self._n.append(int(v.shape[0]))
+        return int(cid.value)
+
+    def submit(self, cavity_id: int, eps, T, sigma: float = SIGMA_SB) -> int:
+        n = self._n[cavity_id]
+        e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+        Tm = np.asfortranarray(np.asarray(T, dtype=np.float64).reshape(n, -1))
+        q = np.empty(Tm.shape, dtype=np.float64, order="F")
+        t = C.c_int64()
+        _check(_lib.rad_server_submit(self._p, int(cavity_id), _ptr(e), _ptr(Tm), n, int(Tm.shape[1]),
+                                      float(sigma), _ptr(q), n, C.byref(t)))
+        self._keep[int(t.value)] = (e, Tm, q)
+        return int(t.value)
+
+    def wait(self, ticket: int):
+        info = _RequestInfo()
+        rc = _lib.rad_server_wait(self._p, int(ticket), C.byref(info))
+        e, Tm, q = self._keep.pop(int(ticket))
+        d = {k: getattr(info, k) for k, _ in _RequestInfo._fields_}
+        if rc not in (RAD_OK, RAD_ENOTCONV):
+            raise RadError(rc, f"request {ticket} failed: status {rc}")
+        return q, d
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(_lib.rad_server_get_stats(self._p, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
+
+    def close(self):
+        if self._p:
+            _lib.rad_server_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rad_server_create(**kw) -> Server:
+    """Same-name wrapper of the C entry point: a new :class:`Server`."""
+    return Server(**kw)
+
+
+def rad_server_add_cavity(server: Server, verts) -> int:
+    return server.add_cavity(verts)
+
+
+def rad_server_submit(server: Server, cavity_id: int, eps, T, sigma: float = SIGMA_SB) -> int:
+    return server.submit(cavity_id, eps, T, sigma)
+
+
+def rad_server_wait(server: Server, ticket: int):
+    return server.wait(ticket)
+
+
+def rad_server_get_stats(server: Server) -> dict:
+    return server.stats()
+
+
+def rad_server_destroy(server: Server) -> None:
+    server.close()
+
+
 def rad_htree_autotune(h: HTree, stream=None) -> dict:
     """Choose the streaming products' item rows and grids by timing them on
     this handle's operator; returns the chosen configuration."""
@@ -447,4 +563,5 @@ def rad_profile_read(max_kernels: int = 64) -> dict:
     return out
 
 
-__all__ = [n for n in dir() if n.startswith("rad_")] + ["HTree", "RadError", "SIGMA_SB", "header_functions"]
+__all__ = [n for n in dir() if n.startswith("rad_")] + ["HTree", "Server", "RadError", "SIGMA_SB",
+                                                          "header_functions"]

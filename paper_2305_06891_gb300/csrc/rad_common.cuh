@@ -283,7 +283,11 @@ struct rad_htree {
     // The arrays below may still be read by work queued on any stream when
     // the handle goes away (rad_htree_free, or a call that failed half way):
     // wait for the device before they return to the pool.
-    ~rad_htree() { (void)cudaDeviceSynchronize(); }
+    ~rad_htree() {
+        if (sync_on_destroy) (void)cudaDeviceSynchronize();
+    }
+    // false only when the owner knows no queued work reads the handle
+    bool sync_on_destroy = true;
     mutable std::unique_ptr<ProductGraph> graph;
     // launch configuration of the streaming products, chosen by
     // rad_htree_autotune: rows per far-field item, and grid sizes (0 = one

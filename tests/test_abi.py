@@ -46,3 +46,12 @@ def test_null_arguments_are_rejected_without_touching_the_gpu(lib):
     assert lib.rad_build_htree(8, None, None, None, None) == 1   # RAD_EINVAL
     lib.rad_last_error.restype = ctypes.c_char_p
     assert b"null" in lib.rad_last_error()
+
+
+def test_server_parameters_are_checked_before_any_cuda_call(lib):
+    import paper_2305_06891_gb300 as rad
+    with pytest.raises(rad.RadError) as e:
+        rad.Server(slots=0)
+    assert e.value.code == 1
+    with pytest.raises(rad.RadError):
+        rad.Server(slots=2, hbm_budget_bytes=0)
