@@ -327,3 +327,36 @@ def config5(n_requests: int = 64, rate: float = 200.0, n_lo: float = 5000.0,
         out.append((t, Cavity(f"req_{r}", verts, eps, T,
                               dict(leaf_size=64, eta_adm=1.0, aca_tol=1e-7))))
     return out
+
+
+def config5_stream(n_cavities: int = 12, n_requests: int = 96, rate: float = 200.0, n_lo: float = 5000.0,
+                   n_hi: float = 200000.0):
+    """Served stream of transient-step flux solves on a pool of cavities.
+
+    The pool holds ``n_cavities`` cavities drawn like :func:`config5`
+    (cube, cylinder or sphere, log-uniform target size in [n_lo, n_hi]); each
+    of the ``n_requests`` requests arrives after an exponential gap (mean
+    1/rate), picks a pool cavity uniformly and carries its own emissivity and
+    temperature field.  Returns ``(pool, requests)`` with ``pool`` a list of
+    vertex arrays and ``requests`` a list of ``(arrival_s, cavity, eps, T)``.
+    """
+    rng = rng_for(5)
+    pool = []
+    for _ in range(n_cavities):
+        kind = int(rng.integers(0, 3))
+        n_target = math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))
+        if kind == 0:
+            verts = unit_cube(max(1, int(round(math.sqrt(n_target / 12.0)))))
+        elif kind == 1:
+            verts = cylinder_for_n(n_target)
+        else:
+            verts = icosphere(max(1, int(round(math.log(n_target / 20.0, 4.0)))))
+        pool.append(verts)
+    t = 0.0
+    reqs = []
+    for _ in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        c = int(rng.integers(0, n_cavities))
+        eps, T = _fields(rng, pool[c].shape[0], 1, 0.3, 0.9)
+        reqs.append((t, c, eps, T))
+    return pool, reqs
