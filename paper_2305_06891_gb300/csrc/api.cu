@@ -270,7 +270,8 @@ static bool product_via_graph(const rad_htree* h, int32_t dtype, const void* x, 
     const int nr = (int)nrhs;
     const bool op64 = h->op_is_f64();
     const size_t osz = op64 ? 8 : 4;
-    g.X.alloc(osz * n * nr, s);
+    const int ldp = nr == 1 ? 1 : (nr + 3) / 4 * 4;
+    g.X.alloc(osz * n * ldp, s);
     g.Y.alloc(osz * n * nr, s);
     g.T.alloc(apply_workspace_bytes(h, nr), s);
     if (!g.capture) RAD_CUDA(cudaStreamCreateWithFlags(&g.capture, cudaStreamNonBlocking));
@@ -278,8 +279,8 @@ static bool product_via_graph(const rad_htree* h, int32_t dtype, const void* x, 
     RAD_CUDA(cudaStreamBeginCapture(g.capture, cudaStreamCaptureModeThreadLocal));
     cudaGraph_t graph = nullptr;
     try {
-        gather_user_to_tree(h, dtype, x, ldx, nr, g.X.p, nr, op64, g.capture);
-        apply_tree(h, g.X.p, nr, g.Y.p, nr, nr, Epi{kStore, nullptr, nullptr, nullptr, 0}, g.T.p, g.capture);
+        gather_user_to_tree(h, dtype, x, ldx, nr, g.X.p, ldp, op64, g.capture);
+        apply_tree(h, g.X.p, ldp, g.Y.p, nr, nr, Epi{kStore, nullptr, nullptr, nullptr, 0}, g.T.p, g.capture);
         scatter_tree_to_user(h, g.Y.p, nr, nr, op64, dtype, y, ldy, g.capture);
     } catch (...) {
         cudaStreamEndCapture(g.capture, &graph);
@@ -476,11 +477,12 @@ int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx, v
         Scratch ws(s);
         const void* xd = stage_in_2d(x, n, nr, ldx, esz, ws);
         const int64_t ldxd = is_device_ptr(x) ? ldx : n;
-        void* X = ws.get(osz * n * nr);
+        const int ldp = nr == 1 ? 1 : (nr + 3) / 4 * 4;   // padded rows: 16-byte quads in the product
+        void* X = ws.get(osz * n * ldp);
         void* Y = ws.get(osz * n * nr);
         void* T = ws.get(apply_workspace_bytes(h, nr));
-        gather_user_to_tree(h, dtype, xd, ldxd, nr, X, nr, op64, s);
-        apply_tree(h, X, nr, Y, nr, nr, Epi{kStore, nullptr, nullptr, nullptr, 0}, T, s);
+        gather_user_to_tree(h, dtype, xd, ldxd, nr, X, ldp, op64, s);
+        apply_tree(h, X, ldp, Y, nr, nr, Epi{kStore, nullptr, nullptr, nullptr, 0}, T, s);
         if (is_device_ptr(y)) {
             scatter_tree_to_user(h, Y, nr, nr, op64, dtype, y, ldy, s);
         } else {

@@ -125,19 +125,21 @@ __global__ void cgs_update_kernel(const double* __restrict__ V, long long stride
 // V_next = W / hn (active columns with hn > 0), else 0; optional FP32 copy.
 __global__ void normalize_kernel(const double* __restrict__ W, const double* __restrict__ hn2,
                                  const int* __restrict__ active, double* __restrict__ Vn, float* __restrict__ X32,
-                                 int n, int nc, const int* __restrict__ seg) {
+                                 int n, int nc, const int* __restrict__ seg, int ldp) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)n * nc) return;
     const int c = vcol(seg, e, nc);
     const double hn = sqrt(hn2[c]);
     const double v = (active[c] && hn > 0.0) ? W[e] / hn : 0.0;
     Vn[e] = v;
-    if (X32) X32[e] = (float)v;
+    if (X32) X32[(e / nc) * ldp + e % nc] = (float)v;
 }
 
-__global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, long long cnt) {
+// FP32 copy of an n x nc row-major FP64 block, rows padded to ldp columns
+// (so that the product can move them as 16-byte quads).
+__global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, long long cnt, int nc, int ldp) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < cnt) b[e] = (float)a[e];
+    if (e < cnt) b[(e / nc) * ldp + e % nc] = (float)a[e];
 }
 
 // Per column: apply the previous Givens rotations to the new Hessenberg
@@ -206,14 +208,14 @@ __global__ void update_x_kernel(const double* __restrict__ V, long long strideV,
 // start a cycle: V_0 = R / beta for active columns, g = beta e_1
 __global__ void start_cycle_kernel(const double* __restrict__ Rv, const double* __restrict__ beta2,
                                    const int* __restrict__ active, double* __restrict__ V0, float* __restrict__ X32,
-                                   int n, int nc, const int* __restrict__ seg) {
+                                   int n, int nc, const int* __restrict__ seg, int ldp) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)n * nc) return;
     const int c = vcol(seg, e, nc);
     const double b = sqrt(beta2[c]);
     const double v = (active[c] && b > 0.0) ? Rv[e] / b : 0.0;
     V0[e] = v;
-    if (X32) X32[e] = (float)v;
+    if (X32) X32[(e / nc) * ldp + e % nc] = (float)v;
 }
 
 __global__ void init_g_kernel(int R, int nc, const double* __restrict__ beta2, double* __restrict__ g,
@@ -306,7 +308,8 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
     const int* seg = red.nseg > 1 ? h->d_segrow.as<int>() : nullptr;
     double* W = ws.get_n<double>(nv);
     double* V = ws.get_n<double>(nv * (R + 1));
-    float* X32 = op64 ? nullptr : ws.get_n<float>(nv);
+    const int ldp = (nc + 3) / 4 * 4;                  // padded row stride of the FP32 copy
+    float* X32 = op64 ? nullptr : ws.get_n<float>((long long)n * ldp);
     void* Tws = ws.get(apply_workspace_bytes(h, nc));
     double* Hm = ws.get_n<double>((long long)R * (R + 1) * nvc);
     double* cs = ws.get_n<double>((long long)R * nvc);
@@ -336,7 +339,7 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
 
     auto apply_C = [&](const double* vin, const float* vin32, double* out, int mode) {
         Epi epi{mode, eps_t, vin, mode == kResid ? B : nullptr, nc};
-        apply_tree(h, op64 ? (const void*)vin : (const void*)vin32, nc, out, nc, nc, epi, Tws, s);
+        apply_tree(h, op64 ? (const void*)vin : (const void*)vin32, op64 ? nc : ldp, out, nc, nc, epi, Tws, s);
     };
 
     int total_iters = 0, restarts = 0, matvecs = 0, status = RAD_OK;
@@ -359,7 +362,7 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
         }
         prev_max = max_rel;
         RAD_CUDA(cudaMemcpyAsync(active, hact.data(), sizeof(int) * nvc, cudaMemcpyHostToDevice, s));
-        { ProfScope ps_("gmres_small", s); start_cycle_kernel<<<grid_for(nv), 256, 0, s>>>(W, beta2, active, V, X32, n, nc, seg); }
+        { ProfScope ps_("gmres_small", s); start_cycle_kernel<<<grid_for(nv), 256, 0, s>>>(W, beta2, active, V, X32, n, nc, seg, ldp); }
         RAD_CHECK_LAUNCH();
         { ProfScope ps_("gmres_small", s); init_g_kernel<<<grid_for(nvc, 128), 128, 0, s>>>(R, nvc, beta2, g, jc); }
         RAD_CHECK_LAUNCH();
@@ -381,7 +384,7 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
                 }
             }
             red.dots(W, 0, 1, W, hn2);
-            { ProfScope ps_("gmres_normalize", s); normalize_kernel<<<grid_for(nv), 256, 0, s>>>(W, hn2, active, V + (long long)(j + 1) * nv, X32, n, nc, seg); }
+            { ProfScope ps_("gmres_normalize", s); normalize_kernel<<<grid_for(nv), 256, 0, s>>>(W, hn2, active, V + (long long)(j + 1) * nv, X32, n, nc, seg, ldp); }
             RAD_CHECK_LAUNCH();
             { ProfScope ps_("gmres_small", s); givens_kernel<<<grid_for(nvc, 128), 128, 0, s>>>(j, R, nvc, Hm, hn2, cs, sn, g, bnorm, resid, active, jc,
                                                             tol); }
@@ -400,7 +403,7 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
         RAD_CHECK_LAUNCH();
         // true residual r = b - C x
         if (X32) {
-            { ProfScope ps_("gmres_convert", s); to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(X, X32, nv); }
+            { ProfScope ps_("gmres_convert", s); to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(X, X32, nv, nc, ldp); }
             RAD_CHECK_LAUNCH();
         }
         apply_C(X, X32, W, kResid);
@@ -513,11 +516,12 @@ void solve_flux(const rad_htree* h, const double* eps_dev, const double* T_dev, 
         { ProfScope ps_("flux", s); flux_kernel<double><<<grid_for((long long)n * m), 256, 0, s>>>(n, m, FY, h->perm.as<int>(), eps_dev, T_dev,
                                                                       ldT, sigma, q_dev, ldq); }
     } else {
-        float* X32 = ws.get_n<float>(nv);
+        const int ldp = (nc + 3) / 4 * 4;
+        float* X32 = ws.get_n<float>((long long)n * ldp);
         float* FY = ws.get_n<float>(nv);
-        { ProfScope ps_("gmres_convert", s); to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(X, X32, nv); }
+        { ProfScope ps_("gmres_convert", s); to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(X, X32, nv, nc, ldp); }
         RAD_CHECK_LAUNCH();
-        apply_tree(h, X32, nc, FY, nc, nc, Epi{kStore, nullptr, nullptr, nullptr, 0}, Tws, s);
+        apply_tree(h, X32, ldp, FY, nc, nc, Epi{kStore, nullptr, nullptr, nullptr, 0}, Tws, s);
         { ProfScope ps_("flux", s); flux_kernel<float><<<grid_for((long long)n * m), 256, 0, s>>>(n, m, FY, h->perm.as<int>(), eps_dev, T_dev,
                                                                      ldT, sigma, q_dev, ldq); }
     }

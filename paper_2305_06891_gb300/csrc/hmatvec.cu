@@ -22,6 +22,8 @@
 
 #include <mutex>
 
+#include <type_traits>
+
 #include "rad_device.cuh"
 
 namespace rad {
@@ -457,87 +459,116 @@ rows_df(OpView op, const DF* __restrict__ X, const DF* __restrict__ T, double* Y
 template <class AT> struct Chunk;
 template <> struct Chunk<float> { static constexpr int KC = 32; };
 template <> struct Chunk<double> { static constexpr int KC = 16; };
-constexpr int kMaxCols = 96;    // right-hand sides per launch
-constexpr int kNCS = kMaxCols + 4;
+constexpr int kMaxCols = 96;    // right-hand sides per launch (multiple of 4)
 constexpr int kStages = 3;
 
-// Dynamic shared memory of the panel GEMM: kStages x (A chunk, B chunk).
+// Copy unit of the panel operand: 16 bytes (FP32, FP64) or 8 bytes (BF16,
+// whose panel columns are only 8-byte aligned).
+template <class S> struct AUnit { static constexpr int bytes = 16; };
+template <> struct AUnit<__nv_bfloat16> { static constexpr int bytes = 8; };
+
+// Dynamic shared memory of the panel GEMM: kStages x (A chunk: KC panel
+// columns of up to 64 rows; B chunk: KC rows of 4 CQ columns).
 template <class AS, class AT>
 struct GemmLayout {
     static constexpr int KC = Chunk<AT>::KC;
     static constexpr size_t a_bytes = sizeof(AS) * KC * kTileRows;
-    static constexpr size_t b_bytes = sizeof(AT) * KC * kNCS;
-    static constexpr size_t stage = (a_bytes + b_bytes + 127) / 128 * 128;
-    static constexpr size_t bytes = kStages * stage;
+    static __host__ __device__ size_t stage(int cq) { return (a_bytes + sizeof(AT) * KC * 4 * cq + 127) / 128 * 128; }
+    static __host__ __device__ size_t bytes(int cq) { return kStages * stage(cq); }
 };
 
-// 4-byte / 8-byte asynchronous global -> shared copies; a false predicate
-// copies nothing and fills the destination with zeros.
-__device__ __forceinline__ void cp_async_4(void* sdst, const void* gsrc, bool pred) {
+// asynchronous global -> shared copies; a false predicate copies nothing and
+// fills the destination with zeros
+__device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc, bool pred) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(pred ? 4 : 0));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc), "r"(pred ? 16 : 0));
 }
 __device__ __forceinline__ void cp_async_8(void* sdst, const void* gsrc, bool pred) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gsrc), "r"(pred ? 8 : 0));
 }
+__device__ __forceinline__ void cp_async_4(void* sdst, const void* gsrc, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gsrc), "r"(pred ? 4 : 0));
+}
+template <int B>
+__device__ __forceinline__ void cp_async_n(void* d, const void* g, bool p) {
+    if constexpr (B == 16) cp_async_16(d, g, p);
+    else if constexpr (B == 8) cp_async_8(d, g, p);
+    else cp_async_4(d, g, p);
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-template <class AT>
-__device__ __forceinline__ void cp_async_elem(AT* sdst, const AT* gsrc, bool pred);
-template <>
-__device__ __forceinline__ void cp_async_elem<float>(float* d, const float* g, bool p) { cp_async_4(d, g, p); }
-template <>
-__device__ __forceinline__ void cp_async_elem<double>(double* d, const double* g, bool p) { cp_async_8(d, g, p); }
+// Four consecutive accumulation-type values from shared memory.
+template <class AT> struct Quad;
+template <> struct Quad<float> {
+    static __device__ __forceinline__ void load(const float* p, float v[4]) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+};
+template <> struct Quad<double> {
+    static __device__ __forceinline__ void load(const double* p, double v[4]) {
+        const double2 a = reinterpret_cast<const double2*>(p)[0];
+        const double2 b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
 
-// acc(4 x RN per thread) += A(rows x K) B(K x nc): A column-major panel with
-// leading dimension lda (a chunk of <= 64 rows, rows_pad = 4 RG), B(k, :) =
-// row bsel(k) of the vector block Bv (leading dimension ldb).  Chunks of KC
-// columns of A (copied as raw 4-byte words) and the KC rows of B go through
-// a kStages-deep cp.async ring.  Thread (rg, cg) = (tid / CG, tid % CG) owns
-// rows 4 rg .. 4 rg + 3 and columns cg + CG q.
-template <class AS, class AT, int RN, class BSel>
-__device__ __forceinline__ void panel_gemm(AT (&acc)[4][RN], unsigned char* smem, const AS* __restrict__ A,
+// acc(4 x 4 per thread) += A(rows x K) B(K x nc).  A: column-major panel
+// (leading dimension lda, a chunk of <= 64 rows padded to rows_pad = 4 RG);
+// B(k, :) = row bsel(k) of the vector block Bv (leading dimension ldb).
+// Thread (rg, cq) = (tid / CQ, tid % CQ) owns rows 4 rg .. 4 rg + 3 and
+// columns 4 cq .. 4 cq + 3; per k it reads one quad of A and one quad of B
+// from shared memory (lanes of a row group share the A quad) for 16 FMAs.
+// Chunks of KC panel columns and the KC matching rows of B go through a
+// kStages-deep cp.async ring; B rows move as 16-byte quads when VB (rows
+// 16-byte aligned, padded to 4 CQ columns), else element by element with
+// zero fill past nc.
+template <class AS, class AT, bool VB, class BSel>
+__device__ __forceinline__ void panel_gemm(AT (&acc)[4][4], unsigned char* smem, const AS* __restrict__ A,
                                            long long lda, int rows_pad, int K, BSel bsel,
-                                           const AT* __restrict__ Bv, int ldb, int nc, int RG, int CG) {
+                                           const AT* __restrict__ Bv, int ldb, int nc, int CQ) {
     using L = GemmLayout<AS, AT>;
     constexpr int KC = L::KC;
-    constexpr int WPE = sizeof(AS) >= 4 ? (int)(sizeof(AS) / 4) : 1;   // words per element (>= 1)
-    constexpr int EPW = sizeof(AS) >= 4 ? 1 : (int)(4 / sizeof(AS));   // elements per word
+    constexpr int AU = AUnit<AS>::bytes;
+    constexpr int EPU = AU / (int)sizeof(AS);            // A elements per copy unit
     const int nchunks = (K + KC - 1) / KC;
     if (nchunks == 0) return;
-    const int tid = threadIdx.x;
-    const int rg = tid / CG, cg = tid - rg * CG;
-    const bool active = rg < RG;
-    int boff[RN];
-#pragma unroll
-    for (int q = 0; q < RN; ++q) boff[q] = min(cg + CG * q, nc - 1);
-    // staging assignment: thread t copies word a_w of chunk columns a_kk0,
-    // a_kk0 + a_step, ... and element b_c of chunk rows b_kk0, b_kk0 + b_step
-    const int wpc = rows_pad * WPE / EPW;             // A words per column
-    const int a_step = 256 / wpc, a_kk0 = tid / wpc, a_w = tid - a_kk0 * wpc;
-    const int b_step = 256 / nc, b_kk0 = tid / nc, b_c = tid - b_kk0 * nc;
-    const unsigned* Aw = reinterpret_cast<const unsigned*>(A);
-    const long long ldaw = lda * WPE / EPW;           // A words per panel column
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int rg = tid / CQ, cq = tid - rg * CQ;
+    const bool active = rg < rows_pad / 4;
+    const int BS = 4 * CQ;                               // B row stride in shared memory
+    const size_t stage = L::stage(CQ);
+    const int upc = rows_pad / EPU;                      // A copy units per panel column
     auto issue = [&](int ch) {
-        unsigned char* st = smem + (size_t)(ch % kStages) * L::stage;
-        unsigned* As = reinterpret_cast<unsigned*>(st);
+        unsigned char* st = smem + (size_t)(ch % kStages) * stage;
+        AS* As = reinterpret_cast<AS*>(st);
         AT* Bs = reinterpret_cast<AT*>(st + L::a_bytes);
         const int k0 = ch * KC;
-        if (a_kk0 < a_step)
-            for (int kk = a_kk0; kk < KC; kk += a_step) {
+        for (int u = tid; u < KC * upc; u += nt) {
+            const int kk = u / upc, w = u - kk * upc;
+            const bool ok = k0 + kk < K;
+            const AS* src = ok ? A + (long long)(k0 + kk) * lda + w * EPU : A;
+            cp_async_n<AU>(As + kk * kTileRows + w * EPU, src, ok);
+        }
+        if constexpr (VB) {
+            for (int u = tid; u < KC * CQ; u += nt) {
+                const int kk = u / CQ, q = u - kk * CQ;
                 const bool ok = k0 + kk < K;
-                const unsigned* src = ok ? Aw + (long long)(k0 + kk) * ldaw + a_w : Aw;
-                cp_async_4(As + kk * (kTileRows * WPE / EPW) + a_w, src, ok);
+                const AT* src = ok ? Bv + (long long)bsel(k0 + kk) * ldb + 4 * q : Bv;
+                cp_async_16(Bs + kk * BS + 4 * q, src, ok);
             }
-        if (b_kk0 < b_step)
-            for (int kk = b_kk0; kk < KC; kk += b_step) {
-                const bool ok = k0 + kk < K;
-                const AT* src = ok ? Bv + (long long)bsel(k0 + kk) * ldb + b_c : Bv;
-                cp_async_elem<AT>(Bs + kk * kNCS + b_c, src, ok);
+        } else {
+            for (int u = tid; u < KC * BS; u += nt) {
+                const int kk = u / BS, c = u - kk * BS;
+                const bool ok = k0 + kk < K && c < nc;
+                const AT* src = ok ? Bv + (long long)bsel(k0 + kk) * ldb + c : Bv;
+                cp_async_n<(int)sizeof(AT)>(Bs + kk * BS + c, src, ok);
             }
+        }
         cp_async_commit();
     };
     issue(0);
@@ -549,20 +580,19 @@ __device__ __forceinline__ void panel_gemm(AT (&acc)[4][RN], unsigned char* smem
         if (ch + 2 < nchunks) issue(ch + 2);
         else cp_async_commit();
         if (active) {
-            const unsigned char* st = smem + (size_t)(ch % kStages) * L::stage;
+            const unsigned char* st = smem + (size_t)(ch % kStages) * stage;
             const AS* As = reinterpret_cast<const AS*>(st);
             const AT* Bs = reinterpret_cast<const AT*>(st + L::a_bytes);
             // chunk entries past K were filled with zeros
-#pragma unroll
+#pragma unroll 8
             for (int kk = 0; kk < KC; ++kk) {
-                AT a[4], b[RN];
+                AT a[4], b[4];
                 Vec4<AS, AT>::load(As + kk * kTileRows + rg * 4, a);
-#pragma unroll
-                for (int q = 0; q < RN; ++q) b[q] = Bs[kk * kNCS + boff[q]];
+                Quad<AT>::load(Bs + kk * BS + 4 * cq, b);
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
 #pragma unroll
-                    for (int q = 0; q < RN; ++q) acc[r][q] += a[r] * b[q];
+                    for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
             }
         }
     }
@@ -579,95 +609,82 @@ struct IndexRows {
     __device__ __forceinline__ int operator()(int k) const { return idx[k]; }
 };
 
-template <class FS, class AT, int RN>
-__global__ void __launch_bounds__(256, 3)
-far_vt_multi(OpView op, const AT* __restrict__ X, int ldx, AT* __restrict__ T, int ldt, int nc) {
+template <class FS, class AT, bool VB>
+__global__ void __launch_bounds__(384)
+far_vt_multi(OpView op, const AT* __restrict__ X, int ldx, AT* __restrict__ T, int ldt, int nc, int CQ) {
     extern __shared__ __align__(128) unsigned char dsm[];
     const GWork w = op.gwork[blockIdx.x];
     const Group gr = op.groups[w.g];
     const int rows_pad = (w.rows + 3) / 4 * 4;
-    const int RG = rows_pad / 4, CG = 256 / RG;
-    AT acc[4][RN];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int q = 0; q < RN; ++q) acc[r][q] = 0;
-    panel_gemm<FS, AT, RN>(acc, dsm, static_cast<const FS*>(op.far_pool) + gr.voff + w.r0, gr.ld, rows_pad, gr.n,
-                           AffineRows{gr.c0}, X, ldx, nc, RG, CG);
-    const int rg = threadIdx.x / CG, cg = threadIdx.x - rg * CG;
-    if (rg >= RG) return;
+    AT acc[4][4] = {};
+    panel_gemm<FS, AT, VB>(acc, dsm, static_cast<const FS*>(op.far_pool) + gr.voff + w.r0, gr.ld, rows_pad, gr.n,
+                           AffineRows{gr.c0}, X, ldx, nc, CQ);
+    const int rg = threadIdx.x / CQ, cq = threadIdx.x - rg * CQ;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int row = rg * 4 + r;
         if (row >= w.rows) continue;
 #pragma unroll
-        for (int q = 0; q < RN; ++q) {
-            const int c = cg + CG * q;
-            if (c < nc) T[(long long)(gr.toff + w.r0 + row) * ldt + c] = acc[r][q];
+        for (int c = 0; c < 4; ++c) {
+            const int col = 4 * cq + c;
+            if (col < nc) T[(long long)(gr.toff + w.r0 + row) * ldt + col] = acc[r][c];
         }
     }
 }
 
-template <class NS, class FS, class AT, int RN>
-__global__ void __launch_bounds__(256, 3)
+template <class NS, class FS, class AT, bool VB>
+__global__ void __launch_bounds__(384)
 rows_multi(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ T, int ldt, void* Y, int ldy, int nc,
-           Epi epi) {
+           int CQ, Epi epi) {
     extern __shared__ __align__(128) unsigned char dsm[];
     const Tile t = op.tiles[op.torder[blockIdx.x]];
-    const int RG = t.ld / 4, CG = 256 / RG;
-    AT acc[4][RN];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int q = 0; q < RN; ++q) acc[r][q] = 0;
-    panel_gemm<NS, AT, RN>(acc, dsm, static_cast<const NS*>(op.near_pool) + t.noff, t.ld, t.ld, t.kn,
-                           IndexRows{op.xidx + t.ixn}, X, ldx, nc, RG, CG);
-    panel_gemm<FS, AT, RN>(acc, dsm, static_cast<const FS*>(op.far_pool) + t.foff, t.ld, t.ld, t.kf,
-                           IndexRows{op.tidx + t.ixf}, T, ldt, nc, RG, CG);
-    const int rg = threadIdx.x / CG, cg = threadIdx.x - rg * CG;
-    if (rg >= RG) return;
+    AT acc[4][4] = {};
+    panel_gemm<NS, AT, VB>(acc, dsm, static_cast<const NS*>(op.near_pool) + t.noff, t.ld, t.ld, t.kn,
+                           IndexRows{op.xidx + t.ixn}, X, ldx, nc, CQ);
+    // T rows are always padded to a multiple of 4 columns and 16-byte aligned
+    panel_gemm<FS, AT, std::is_same<AT, float>::value>(acc, dsm, static_cast<const FS*>(op.far_pool) + t.foff, t.ld,
+                                                       t.ld, t.kf, IndexRows{op.tidx + t.ixf}, T, ldt, nc, CQ);
+    const int rg = threadIdx.x / CQ, cq = threadIdx.x - rg * CQ;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int row = rg * 4 + r;
         if (row >= t.rows) continue;
 #pragma unroll
-        for (int q = 0; q < RN; ++q) {
-            const int c = cg + CG * q;
-            if (c < nc) epilogue<AT>(epi, Y, ldy, t.r0 + row, c, acc[r][q]);
+        for (int c = 0; c < 4; ++c) {
+            const int col = 4 * cq + c;
+            if (col < nc) epilogue<AT>(epi, Y, ldy, t.r0 + row, col, acc[r][c]);
         }
     }
 }
 
-template <class FS, class AT, int RN>
+// Threads of the panel GEMM for nc columns: 16 row groups x ceil(nc / 4)
+// column quads, rounded up to whole warps.
+inline int gemm_threads(int cq) { return (16 * cq + 31) / 32 * 32; }
+
+template <class FS, class AT, bool VB>
 void launch_far_vt(const OpView& op, const AT* X, int ldx, AT* T, int ldt, int nc, cudaStream_t s) {
-    const size_t bytes = GemmLayout<FS, AT>::bytes > GemmLayout<float, AT>::bytes ? GemmLayout<FS, AT>::bytes
-                                                                                  : GemmLayout<float, AT>::bytes;
+    const int cq = (nc + 3) / 4;
+    const size_t bytes = GemmLayout<FS, AT>::bytes(cq);
     static std::once_flag configured;
     std::call_once(configured, [&] {
-        RAD_CUDA(cudaFuncSetAttribute(far_vt_multi<FS, AT, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        RAD_CUDA(cudaFuncSetAttribute(far_vt_multi<FS, AT, VB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)GemmLayout<FS, AT>::bytes(kMaxCols / 4)));
     });
-    { ProfScope ps_("hmm_far_vt", s); far_vt_multi<FS, AT, RN><<<op.n_gwork, 256, bytes, s>>>(op, X, ldx, T, ldt, nc); }
+    { ProfScope ps_("hmm_far_vt", s); far_vt_multi<FS, AT, VB><<<op.n_gwork, gemm_threads(cq), bytes, s>>>(op, X, ldx, T, ldt, nc, cq); }
     RAD_CHECK_LAUNCH();
 }
-template <class NS, class FS, class AT, int RN>
+template <class NS, class FS, class AT, bool VB>
 void launch_rows(const OpView& op, const AT* X, int ldx, const AT* T, int ldt, void* Y, int ldy, int nc,
                  const Epi& epi, cudaStream_t s) {
-    const size_t bytes = GemmLayout<NS, AT>::bytes > GemmLayout<FS, AT>::bytes ? GemmLayout<NS, AT>::bytes
-                                                                                : GemmLayout<FS, AT>::bytes;
+    const int cq = (nc + 3) / 4;
+    const size_t bytes = std::max(GemmLayout<NS, AT>::bytes(cq), GemmLayout<FS, AT>::bytes(cq));
     static std::once_flag configured;
     std::call_once(configured, [&] {
-        RAD_CUDA(cudaFuncSetAttribute(rows_multi<NS, FS, AT, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        const size_t mx = std::max(GemmLayout<NS, AT>::bytes(kMaxCols / 4), GemmLayout<FS, AT>::bytes(kMaxCols / 4));
+        RAD_CUDA(cudaFuncSetAttribute(rows_multi<NS, FS, AT, VB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx));
     });
-    { ProfScope ps_("hmm_rows", s); rows_multi<NS, FS, AT, RN><<<op.n_tiles, 256, bytes, s>>>(op, X, ldx, T, ldt, Y, ldy, nc, epi); }
+    { ProfScope ps_("hmm_rows", s); rows_multi<NS, FS, AT, VB><<<op.n_tiles, gemm_threads(cq), bytes, s>>>(op, X, ldx, T, ldt, Y, ldy, nc, cq, epi); }
     RAD_CHECK_LAUNCH();
-}
-
-// Register-tile width RN for nc columns when the panel with the most row
-// groups has leading dimension max_ld: CG = 256 / (max_ld / 4) >= 16 column
-// slots, so RN = ceil(nc / CG) <= 8 for nc <= 128.
-inline int rn_for(int max_ld, int nc) {
-    const int cg = 256 / (max_ld / 4);
-    return std::max(1, std::min(8, (nc + cg - 1) / cg));
 }
 
 // Grid of a grid-stride launch over `items` work items: one CTA per item, or
@@ -725,11 +742,11 @@ void apply_t(const rad_htree* h, const OpView& op, const AT* X, int ldx, void* Y
         }
         return;
     }
-    int tile_ld = 4, group_ld = 4;
-    for (auto& t : h->tiles_h) tile_ld = std::max(tile_ld, t.ld);
-    for (auto& g : h->groups_h) group_ld = std::max(group_ld, (int)std::min<long long>(kTileRows, round_up(g.M, 4)));
     const int ldt = tree_ld(nrhs);
     const int esz = epi.mode == kStore ? (int)sizeof(AT) : 8;
+    // X rows move as 16-byte quads when they are FP32, 16-byte aligned and
+    // padded to a multiple of 4 columns
+    const bool vx = std::is_same<AT, float>::value && ldx % 4 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
     for (int c0 = 0; c0 < nrhs; c0 += kMaxCols) {
         const int nc = std::min(kMaxCols, nrhs - c0);
         Epi e2 = epi;
@@ -740,27 +757,12 @@ void apply_t(const rad_htree* h, const OpView& op, const AT* X, int ldx, void* Y
         const AT* Xc = X + c0;
         AT* Tc = T + c0;
         void* Yc = static_cast<char*>(Y) + (size_t)c0 * esz;
-        if (op.n_gwork > 0) {
-            switch (rn_for(group_ld, nc)) {
-                case 1: launch_far_vt<FS, AT, 1>(op, Xc, ldx, Tc, ldt, nc, s); break;
-                case 2: launch_far_vt<FS, AT, 2>(op, Xc, ldx, Tc, ldt, nc, s); break;
-                case 3: launch_far_vt<FS, AT, 3>(op, Xc, ldx, Tc, ldt, nc, s); break;
-                case 4: launch_far_vt<FS, AT, 4>(op, Xc, ldx, Tc, ldt, nc, s); break;
-                case 5: launch_far_vt<FS, AT, 5>(op, Xc, ldx, Tc, ldt, nc, s); break;
-                case 6: launch_far_vt<FS, AT, 6>(op, Xc, ldx, Tc, ldt, nc, s); break;
-                case 7: launch_far_vt<FS, AT, 7>(op, Xc, ldx, Tc, ldt, nc, s); break;
-                default: launch_far_vt<FS, AT, 8>(op, Xc, ldx, Tc, ldt, nc, s); break;
-            }
-        }
-        switch (rn_for(tile_ld, nc)) {
-            case 1: launch_rows<NS, FS, AT, 1>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            case 2: launch_rows<NS, FS, AT, 2>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            case 3: launch_rows<NS, FS, AT, 3>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            case 4: launch_rows<NS, FS, AT, 4>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            case 5: launch_rows<NS, FS, AT, 5>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            case 6: launch_rows<NS, FS, AT, 6>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            case 7: launch_rows<NS, FS, AT, 7>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
-            default: launch_rows<NS, FS, AT, 8>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s); break;
+        if (vx) {
+            if (op.n_gwork > 0) launch_far_vt<FS, AT, true>(op, Xc, ldx, Tc, ldt, nc, s);
+            launch_rows<NS, FS, AT, true>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s);
+        } else {
+            if (op.n_gwork > 0) launch_far_vt<FS, AT, false>(op, Xc, ldx, Tc, ldt, nc, s);
+            launch_rows<NS, FS, AT, false>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s);
         }
     }
 }
