@@ -150,6 +150,8 @@ typedef struct {
     int32_t stream_rows;         /* rows per far-field item (1-4 columns)       */
     int32_t grid_a1, grid_b1;    /* grids of the 1-column phases (0: per item)  */
     int32_t grid_a2, grid_b2;    /* grids of the 2-4 column launches            */
+    int32_t product_path;        /* >= 5 FP32 columns: 0 CUDA cores, 1 tensor cores */
+    int32_t reserved2;
 } rad_htree_stats;
 
 /* -------------------------------------------------------------------------
@@ -235,6 +237,15 @@ int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx,
  * agree to rounding).  Synchronous; takes a fraction of a second.
  * Recompression resets the choice. */
 int rad_htree_autotune(rad_htree* h, void* stream);
+
+/* Kernel family of the product with 5 or more FP32 columns (no counterpart
+ * in the paper): 0 = CUDA-core register tiles (FP32 FFMA, the default),
+ * 1 = tensor cores (tcgen05, TF32 operands split into hi + lo with all four
+ * partial products, accumulated per 32-column chunk and summed in FP32, so
+ * results agree with path 0 to FP32 rounding).  rad_htree_autotune picks
+ * the faster one for the handle's operator; recompression resets it to 0.
+ * RAD_EINVAL for another value. */
+int rad_htree_set_product_path(rad_htree* h, int32_t path);
 
 /* -------------------------------------------------------------------------
  * rad_solve_flux — A7-A8: for each of the m temperature fields T(:, c)

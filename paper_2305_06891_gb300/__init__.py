@@ -86,7 +86,8 @@ class _Stats(C.Structure):
                 ("aca_entries", C.c_int64), ("bytes_near", C.c_int64), ("bytes_far", C.c_int64),
                 ("far_u_entries", C.c_int64), ("far_v_entries", C.c_int64), ("n_tiles", C.c_int64),
                 ("bytes_accurate", C.c_int64), ("tuned", C.c_int32), ("stream_rows", C.c_int32),
-                ("grid_a1", C.c_int32), ("grid_b1", C.c_int32), ("grid_a2", C.c_int32), ("grid_b2", C.c_int32)]
+                ("grid_a1", C.c_int32), ("grid_b1", C.c_int32), ("grid_a2", C.c_int32), ("grid_b2", C.c_int32),
+                ("product_path", C.c_int32), ("reserved2", C.c_int32)]
 
 
 def _load():
@@ -116,6 +117,7 @@ def _load():
         "rad_htree_export_block": (C.c_int, [H, i64, vp, vp, vp]),
         "rad_htree_free": (C.c_int, [H]),
         "rad_htree_autotune": (C.c_int, [H, vp]),
+        "rad_htree_set_product_path": (C.c_int, [H, i32]),
         "rad_server_create": (C.c_int, [C.POINTER(_ServerParams), C.POINTER(vp)]),
         "rad_server_add_cavity": (C.c_int, [vp, i64, vp, C.POINTER(i64)]),
         "rad_server_submit": (C.c_int, [vp, i64, vp, vp, i64, i64, dbl, vp, i64, C.POINTER(i64)]),
@@ -496,7 +498,12 @@ def rad_htree_autotune(h: HTree, stream=None) -> dict:
     this handle's operator; returns the chosen configuration."""
     _check(_lib.rad_htree_autotune(h.ptr, _stream(stream)))
     st = rad_htree_get_stats(h)
-    return {k: st[k] for k in ("stream_rows", "grid_a1", "grid_b1", "grid_a2", "grid_b2")}
+    return {k: st[k] for k in ("stream_rows", "grid_a1", "grid_b1", "grid_a2", "grid_b2", "product_path")}
+
+
+def rad_htree_set_product_path(h: HTree, path: int) -> None:
+    """0: CUDA-core tiles, 1: tensor cores (split TF32) for >= 5 FP32 columns."""
+    _check(_lib.rad_htree_set_product_path(h.ptr, int(path)))
 
 
 def rad_htree_get_stats(h: HTree) -> dict:

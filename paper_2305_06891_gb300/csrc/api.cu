@@ -601,6 +601,7 @@ int rad_htree_get_stats(const rad_htree* h, rad_htree_stats* st) {
         st->grid_b1 = h->grid_b1;
         st->grid_a2 = h->grid_a2;
         st->grid_b2 = h->grid_b2;
+        st->product_path = h->mm_path;
     });
 }
 
@@ -652,6 +653,15 @@ int rad_htree_autotune(rad_htree* h, void* stream) {
     return guarded([&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null argument");
         autotune(h, static_cast<cudaStream_t>(stream));
+    });
+}
+
+int rad_htree_set_product_path(rad_htree* h, int32_t path) {
+    return guarded([&] {
+        RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null argument");
+        RAD_REQUIRE(path == 0 || path == 1, RAD_EINVAL, "path must be 0 (CUDA cores) or 1 (tensor cores)");
+        drop_product_graph(h);
+        h->mm_path = path;
     });
 }
 

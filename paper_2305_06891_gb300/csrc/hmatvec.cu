@@ -757,6 +757,14 @@ void apply_t(const rad_htree* h, const OpView& op, const AT* X, int ldx, void* Y
         const AT* Xc = X + c0;
         AT* Tc = T + c0;
         void* Yc = static_cast<char*>(Y) + (size_t)c0 * esz;
+        if constexpr (std::is_same<AT, float>::value && std::is_same<NS, float>::value) {
+            if (vx && h->mm_path == 1) {
+                // tensor cores (split TF32) for FP32 vectors
+                if (op.n_gwork > 0) tc_far_vt<FS>(op, Xc, ldx, Tc, ldt, nc, s);
+                tc_rows<FS>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s);
+                continue;
+            }
+        }
         if (vx) {
             if (op.n_gwork > 0) launch_far_vt<FS, AT, true>(op, Xc, ldx, Tc, ldt, nc, s);
             launch_rows<NS, FS, AT, true>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s);
@@ -883,6 +891,7 @@ struct Tuner {
     cudaStream_t s;
     AT *X, *T, *Yn;
     void* Y;
+    AT* X64;   // n x 64 block for the many-column product
     cudaEvent_t e0, e1;
     template <class F>
     float time(F&& launch) {
@@ -944,6 +953,23 @@ struct Tuner {
         h->grid_b1 = gb1;
         h->grid_a2 = ga2;
         h->grid_b2 = gb2;
+        // many-column product: CUDA-core tiles or tensor cores, 64 columns
+        if constexpr (std::is_same<AT, float>::value && std::is_same<NS, float>::value) {
+            float best = 1e30f;
+            int pick = 0;
+            for (int path = 0; path < 2; ++path) {
+                h->mm_path = path;
+                const float t = time([&] {
+                    apply_t<NS, FS, AT>(h, h->view(), X64, 64, Y, 64, 64, Epi{kStore, nullptr, nullptr, nullptr, 0},
+                                        T, s);
+                });
+                if (t < best) {
+                    best = t;
+                    pick = path;
+                }
+            }
+            h->mm_path = pick;
+        }
         h->tuned = 1;
     }
 };
@@ -960,19 +986,25 @@ void autotune(rad_htree* h, cudaStream_t s) {
     RAD_CUDA(cudaEventCreate(&e0));
     RAD_CUDA(cudaEventCreate(&e1));
     void* X = ws.get(esz * 2 * (size_t)n);
-    void* Y = ws.get(8 * 2 * (size_t)n);
-    void* T = ws.get(apply_workspace_bytes(h, 4) + esz * (size_t)n);
+    void* Y = ws.get(8 * 64 * (size_t)n);
+    const size_t tb = std::max(apply_workspace_bytes(h, 4) + esz * (size_t)n, apply_workspace_bytes(h, 64));
+    void* T = ws.get(tb);
+    void* X64 = ws.get(esz * 64 * (size_t)n);
     RAD_CUDA(cudaMemsetAsync(X, 0, esz * 2 * (size_t)n, s));
-    RAD_CUDA(cudaMemsetAsync(T, 0, apply_workspace_bytes(h, 4) + esz * (size_t)n, s));
+    RAD_CUDA(cudaMemsetAsync(T, 0, tb, s));
+    RAD_CUDA(cudaMemsetAsync(X64, 0, esz * 64 * (size_t)n, s));
     try {
         if (h->op_is_f64()) {
-            Tuner<double, double, double> t{h, s, (double*)X, (double*)T, (double*)T + std::max(1, h->sum_rank) * 4, Y, e0, e1};
+            Tuner<double, double, double> t{h, s, (double*)X, (double*)T, (double*)T + std::max(1, h->sum_rank) * 4, Y,
+                                            (double*)X64, e0, e1};
             t.run();
         } else if (h->factor_dtype == RAD_F32) {
-            Tuner<float, float, float> t{h, s, (float*)X, (float*)T, (float*)T + std::max(1, h->sum_rank) * 4, Y, e0, e1};
+            Tuner<float, float, float> t{h, s, (float*)X, (float*)T, (float*)T + std::max(1, h->sum_rank) * 4, Y,
+                                         (float*)X64, e0, e1};
             t.run();
         } else {
-            Tuner<float, __nv_bfloat16, float> t{h, s, (float*)X, (float*)T, (float*)T + std::max(1, h->sum_rank) * 4, Y, e0, e1};
+            Tuner<float, __nv_bfloat16, float> t{h, s, (float*)X, (float*)T, (float*)T + std::max(1, h->sum_rank) * 4,
+                                                 Y, (float*)X64, e0, e1};
             t.run();
         }
     } catch (...) {

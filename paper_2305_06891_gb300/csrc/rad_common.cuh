@@ -296,6 +296,10 @@ struct rad_htree {
     int stream_rows = rad::kStreamRows;
     int grid_a1 = 0, grid_b1 = 0, grid_a2 = 0, grid_b2 = 0;
     int tuned = 0;
+    // many-column product of FP32 vectors: 0 = CUDA-core register tiles,
+    // 1 = tensor cores (split TF32); set by rad_htree_autotune or
+    // rad_htree_set_product_path
+    int mm_path = 0;
     int64_t n = 0;
     // segment (cavity) boundaries of a batch handle: cavity c holds facets
     // [seg[c], seg[c+1]) in user order and in tree order; {0, n} otherwise
@@ -400,6 +404,13 @@ void apply_tree_acc(const rad_htree* h, const double* X, int ldx, double* Y, int
                     double* T_ws, cudaStream_t s);
 size_t apply_workspace_bytes_acc(const rad_htree* h, int nrhs);
 size_t apply_workspace_bytes(const rad_htree* h, int nrhs);
+// tcgemm.cu: tensor-core panel GEMMs (FP32 vectors, 16-byte aligned rows)
+template <class FS>
+void tc_rows(const OpView& op, const float* X, int ldx, const float* T, int ldt, void* Y, int ldy, int nc,
+             const Epi& epi, cudaStream_t s);
+template <class FS>
+void tc_far_vt(const OpView& op, const float* X, int ldx, float* T, int ldt, int nc, cudaStream_t s);
+bool tc_take_timeout();
 void build_stream_lists(rad_htree* h, int rows, cudaStream_t s);
 void autotune(rad_htree* h, cudaStream_t s);
 void drop_product_graph(const rad_htree* h);

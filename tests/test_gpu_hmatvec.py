@@ -96,3 +96,25 @@ def test_caller_provided_outputs(c1):
     out = r.rad_hmatvec(h, x, y)
     assert out.data_ptr() == y.data_ptr()
     assert rel(y.cpu().numpy(), F @ c.T[:, 0]) <= 1e-6
+
+
+@pytest.mark.parametrize("factor", ["f32", "bf16"])
+@pytest.mark.parametrize("path", [0, 1])
+def test_many_column_paths_match_column_by_column(cyl, factor, path):
+    """The many-column product, on CUDA cores (path 0) and on tensor cores
+    (path 1, split TF32), equals the one-column streaming product column by
+    column to FP32 accuracy, for FP32 and BF16 factors (same stored
+    operator)."""
+    verts, F = cyl
+    r = rad()
+    h = r.rad_build_htree(verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-6, 64, "partial", factor, "f32")
+    r.rad_htree_set_product_path(h, path)
+    assert r.rad_htree_get_stats(h)["product_path"] == path
+    X = np.random.default_rng(7).uniform(-1.0, 1.5, size=(F.shape[0], 9)).astype(np.float32)
+    Y = r.rad_hmatvec(h, X)
+    for c in range(9):
+        y1 = r.rad_hmatvec(h, np.ascontiguousarray(X[:, c]))
+        # FP32 rounding of sums of |F| |x|: scale by the product with |x|
+        scale = np.abs(r.rad_hmatvec(h, np.ascontiguousarray(np.abs(X[:, c])))).max()
+        assert np.abs(Y[:, c] - y1).max() <= 2e-6 * scale, c
