@@ -65,7 +65,7 @@ WORKLOADS = {
                    factor="bf16", near="f32", accurate="f32", refine=True, slots=4, budget_gib=64,
                    name="served_poisson200_12cavities_bf16_refined"),
     # 256 boxes, 2k-40k facets each, one handle (forest), one field each
-    "batch": dict(make=cv.config4, batch=True, fields=1, leaf=64, eta=1.0, aca_tol=1e-6, solve_tol=1e-8,
+    "batch": dict(make=cv.config4, batch=True, fields=1, leaf=64, eta=1.0, aca_tol=1e-6, solve_tol=1e-7,
                   factor="f32", near="f32", accurate=None, refine=False,
                   name="batch_256_boxes_3.21M_facets_fp32"),
 }

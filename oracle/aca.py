@@ -23,11 +23,12 @@ pivoting as the faster, less reliable alternative):
   The paper warns that partial pivoting is less reliable; that candidate stop
   can fire while rows the pivots never visited are still poorly
   approximated.  So a candidate stop is verified (at most 4 times per block)
-  on S = 256 sampled residual entries at rows i_s = floor(s m / S) and columns
-  j_s = (s * 2654435761 + c * 40503) mod n (s < S, c = checks done so far):
-  ||R||_F^2 is estimated as (m n / S) sum_s r_s^2; if that exceeds
-  eps_rel^2 ||S_k||_F^2 the iteration continues from the row of the largest
-  |r_s| (ties: lowest s).
+  on m + n sampled residual entries, one in every row and one in every
+  column: (i, (i * 2654435761 + c * 40503 + 1) mod n) for each row i, then
+  ((j * 2246822519 + c * 40503 + 3) mod m, j) for each column j (c = checks
+  done so far).  ||R||_F^2 is estimated as (m n / (m + n)) sum_s r_s^2; if
+  that exceeds eps_rel^2 ||S_k||_F^2 the iteration continues from the row of
+  the largest |r_s| (ties: the first sample).
 
 Both return (U, V, converged) with U (m, k), V (n, k).  ``converged`` is
 False when the rank cap was reached first (the caller then stores the block
@@ -131,26 +132,39 @@ def aca_partial(get_row, get_col, m: int, n: int, tol: float, max_rank: int,
         i = int(np.argmax(cand))
 
 
-SAMPLES = 256
 MAX_CHECKS = 4
+# hash multipliers of the verification samples (odd 32-bit constants)
+ROW_MULT = 2654435761
+COL_MULT = 2246822519
+CHECK_MULT = 40503
 
 
 def sample_positions(m: int, n: int, check: int):
-    """Rows and columns of the S residual samples of verification ``check``."""
-    s = np.arange(SAMPLES, dtype=np.int64)
-    return (s * m) // SAMPLES, (s * 2654435761 + check * 40503) % n
+    """Rows and columns of the m + n residual samples of verification
+    ``check``: one column per row, (i * ROW_MULT + check * CHECK_MULT + 1)
+    mod n for row i, then one row per column, (j * COL_MULT + check *
+    CHECK_MULT + 3) mod m for column j, so that every row and every column of
+    the block is probed."""
+    i = np.arange(m, dtype=np.int64)
+    j = np.arange(n, dtype=np.int64)
+    cols_a = (i * ROW_MULT + check * CHECK_MULT + 1) % n
+    rows_b = (j * COL_MULT + check * CHECK_MULT + 3) % m
+    return np.concatenate([i, rows_b]), np.concatenate([cols_a, j])
 
 
 def _sampled_residual(get_row, us, vs, m, n, check):
+    """(m n / (m + n)) sum of squared residual samples (an unbiased estimate
+    of ||X - U V^T||_F^2 under uniform sampling) and the row of the largest
+    |residual| (ties: the first sample)."""
     rows, cols = sample_positions(m, n, check)
-    r = np.empty(SAMPLES)
-    for s in range(SAMPLES):
+    r = np.empty(len(rows))
+    for s in range(len(rows)):
         i, j = int(rows[s]), int(cols[s])
         x = float(np.asarray(get_row(i))[j])
         for u_l, v_l in zip(us, vs):
             x -= u_l[i] * v_l[j]
         r[s] = x
-    est2 = (m * n / SAMPLES) * float((r * r).sum())
+    est2 = (m * n / len(rows)) * float((r * r).sum())
     return est2, int(rows[int(np.argmax(np.abs(r)))])
 
 

@@ -17,10 +17,11 @@
 // ||S_k||^2 = ||S_{k-1}||^2 + 2 sum_{l<k} (u_k.u_l)(v_k.v_l) + |u_k|^2 |v_k|^2.
 // Partial pivoting is the less reliable rule (§1), and that candidate stop
 // can fire early, so it is verified (at most kMaxChecks times per block) on
-// kSamples residual entries at rows floor(s m / S) and columns
-// (s * 2654435761 + c * 40503) mod n, c = checks so far: if
-// (m n / S) sum r_s^2 > tol^2 ||S_k||^2 the iteration resumes from the row of
-// the largest |r_s| (ties: lowest s).
+// m + n residual entries, one in every row and one in every column: sample
+// s < m is (s, (s * 2654435761 + c * 40503 + 1) mod n), sample m + j is
+// ((j * 2246822519 + c * 40503 + 3) mod m, j), c = checks so far; if
+// (m n / (m + n)) sum r_s^2 > tol^2 ||S_k||^2 the iteration resumes from the
+// row of the largest |r_s| (ties: lowest s).
 // Full pivoting keeps the whole residual and stops when
 // ||R_k||_F <= tol ||X||_F (Eq. 31 exactly).
 // A block whose rank would exceed kmax = min(max_rank, m n / (m + n)) is
@@ -44,7 +45,19 @@ struct AcaJob {
 };
 
 constexpr int kAcaNT = 256;
-constexpr int kSamples = kAcaNT;   // one sampled residual entry per thread
+
+// position of verification sample s (< m + n) of check c
+__device__ __forceinline__ void sample_pos(int s, int m, int n, int c, int& si, int& sj) {
+    if (s < m) {
+        si = s;
+        sj = (int)(((unsigned long long)s * 2654435761ull + (unsigned long long)c * 40503ull + 1ull) %
+                   (unsigned long long)n);
+    } else {
+        sj = s - m;
+        si = (int)(((unsigned long long)sj * 2246822519ull + (unsigned long long)c * 40503ull + 3ull) %
+                   (unsigned long long)m);
+    }
+}
 constexpr int kMaxChecks = 4;
 
 // Running sum of the stopping rule's ||S_k||^2.  With FP32 arithmetic it is
@@ -208,19 +221,25 @@ __device__ void aca_cta_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upoo
         // |u_k| |v_k| <= tol ||S_k||_F, compared squared
         if (uu * vv <= tolsq * fmax(norm2.value(), CT(0))) {
             if (checks >= kMaxChecks) { status = 1; break; }
-            // verify the candidate stop on sampled residual entries
-            const int sidx = threadIdx.x;
-            const int si = (int)(((long long)sidx * m) / kSamples);
-            const int sj = (int)(((unsigned long long)sidx * 2654435761ull + (unsigned long long)checks * 40503ull) %
-                                 (unsigned long long)n);
-            CT x = Entry<CT>::eval(g, jb.r0 + si, jb.c0 + sj);
-            for (int l = 0; l < k; ++l) x -= U[(long long)l * m + si] * V[(long long)l * n + sj];
-            const CT r2 = block_sum<kAcaNT, CT>(x * x, red_sm);
-            const ArgMaxT<CT> bs = block_argmax<kAcaNT>(ArgMaxT<CT>{fabs(x), sidx}, am_sm);
+            // verify the candidate stop on one residual entry per row and
+            // one per column
+            CT r2p = 0;
+            ArgMaxT<CT> bsp{CT(-1), 0x7fffffff};
+            for (int sidx = threadIdx.x; sidx < m + n; sidx += kAcaNT) {
+                int si, sj;
+                sample_pos(sidx, m, n, checks, si, sj);
+                CT x = Entry<CT>::eval(g, jb.r0 + si, jb.c0 + sj);
+                for (int l = 0; l < k; ++l) x -= U[(long long)l * m + si] * V[(long long)l * n + sj];
+                r2p += x * x;
+                bsp = am_better(bsp, ArgMaxT<CT>{fabs(x), sidx});
+            }
+            const CT r2 = block_sum<kAcaNT, CT>(r2p, red_sm);
+            const ArgMaxT<CT> bs = block_argmax<kAcaNT>(bsp, am_sm);
+            int wi, wj;
+            sample_pos(bs.i, m, n, checks, wi, wj);
             ++checks;
-            evals += kSamples;
-            if ((CT)m * (CT)n / CT(kSamples) * r2 <= tolsq * fmax(norm2.value(), CT(0))) { status = 1; break; }
-            int wi = (int)(((long long)bs.i * m) / kSamples);
+            evals += m + n;
+            if ((CT)m * (CT)n / CT(m + n) * r2 <= tolsq * fmax(norm2.value(), CT(0))) { status = 1; break; }
             if (used[wi]) {
                 wi = lowest_unused(used, m, i_sm);
                 if (wi < 0) { status = 1; break; }
@@ -350,11 +369,9 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
             if (checks >= kMaxChecks) { status = 1; break; }
             CT r2p = 0;
             ArgMaxT<CT> bs{CT(-1), 0x7fffffff};
-            for (int t = 0; t < kSamples / 32; ++t) {
-                const int sidx = lane + 32 * t;
-                const int si = (int)(((long long)sidx * m) / kSamples);
-                const int sj = (int)(((unsigned long long)sidx * 2654435761ull +
-                                      (unsigned long long)checks * 40503ull) % (unsigned long long)n);
+            for (int sidx = lane; sidx < m + n; sidx += 32) {
+                int si, sj;
+                sample_pos(sidx, m, n, checks, si, sj);
                 CT x = Entry<CT>::eval(g, jb.r0 + si, jb.c0 + sj);
                 for (int l = 0; l < k; ++l) x -= U[(long long)l * m + si] * V[(long long)l * n + sj];
                 r2p += x * x;
@@ -362,10 +379,11 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
             }
             const CT r2 = warp_sum(r2p);
             bs = warp_argmax(bs);
+            int wi, wj;
+            sample_pos(bs.i, m, n, checks, wi, wj);
             ++checks;
-            evals += kSamples;
-            if ((CT)m * (CT)n / CT(kSamples) * r2 <= tolsq * fmax(norm2.value(), CT(0))) { status = 1; break; }
-            int wi = (int)(((long long)bs.i * m) / kSamples);
+            evals += m + n;
+            if ((CT)m * (CT)n / CT(m + n) * r2 <= tolsq * fmax(norm2.value(), CT(0))) { status = 1; break; }
             const unsigned wused = __shfl_sync(0xffffffffu, (used >> (wi >> 5)) & 1u, wi & 31);
             if (wused) {
                 int cand = 0x7fffffff;
