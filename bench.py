@@ -104,8 +104,13 @@ def build(rad, work, verts):
     return rad.rad_build_htree(verts, LEAF, ETA)
 
 
+PRODUCT_PATH = None   # --product-path: many-column product kernels (library default when None)
+
+
 def compress(rad, h):
     rad.rad_compress_aca(h, ACA_TOL, 64, "partial", W["factor"], W["near"], accurate_dtype=W["accurate"])
+    if PRODUCT_PATH is not None:
+        rad.rad_htree_set_product_path(h, PRODUCT_PATH)
 
 
 def solve(rad, h, eps, T, q=None):
@@ -359,20 +364,28 @@ def measure_extras(args, rad, torch, dev, cav, verts_d, eps_d, T_d, flush, strea
     return out
 
 
+# DRAM bytes (read + write) per launch of a workload's dominant kernel, from
+# the ncu capture summarised in profiles/ (kept only while the kernel is
+# unchanged since that capture).
+TRAFFIC = {("cylinder", "hmm_rows"): 284.72e6 + 6.27e6}
+
+
 def roofline(prof: dict, st: dict, steps: int, clocks: dict, nc: int):
     """Dominant kernel of the timed steps and its roofline."""
     hbm, smax, src = load_peaks()
     if not prof:
         return None
     name, (cnt, ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    wl = next(k for k, v in WORKLOADS.items() if v is W)
+    traffic = TRAFFIC.get((wl, name)) if PRODUCT_PATH in (None, 0) else None
     avg_s = ms / cnt * 1e-3
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
     if name == "hmm_rows":
         flops = 2.0 * nc * (st["near_entries"] + st["far_u_entries"])
         ach = flops / avg_s / 1e12
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None, "launches": cnt, "avg_ms": ms / cnt,
-                "peak_note": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz"}
+                "frac": ach / fp32_peak, "traffic": traffic, "launches": cnt, "avg_ms": ms / cnt,
+                "peak_note": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz (of derived)"}
     if name == "hmm_far_vt":
         flops = 2.0 * nc * st["far_v_entries"]
         ach = flops / avg_s / 1e12
@@ -514,7 +527,8 @@ def run_reference(args):
 
 def config_dict(work=None):
     d = {"workload": W["name"], "fields": FIELDS, "leaf_size": LEAF, "eta_adm": ETA, "aca_tol": ACA_TOL,
-         "aca_pivoting": "partial+sampled check", "solve_tol": SOLVE_TOL, "gmres_restart": RESTART,
+         "aca_pivoting": "partial, stop checked on a residual probe in every row and column",
+         "solve_tol": SOLVE_TOL, "gmres_restart": RESTART,
          "storage": f"{W['near']} near + {W['factor']} factors",
          "accumulation": "f32 (operator), f64 (Krylov, inner products, residuals)",
          "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
@@ -673,8 +687,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--workload", default="cylinder", choices=sorted(WORKLOADS))
+    ap.add_argument("--product-path", type=int, choices=[0, 1], default=None,
+                    help="many-column product: 0 CUDA-core tiles, 1 tensor cores (default: library choice)")
     args = ap.parse_args()
     select_workload(args.workload)
+    global PRODUCT_PATH
+    PRODUCT_PATH = args.product_path
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
 
