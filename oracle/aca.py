@@ -168,6 +168,29 @@ def _sampled_residual(get_row, us, vs, m, n, check):
     return est2, int(rows[int(np.argmax(np.abs(r)))])
 
 
+def truncate(U: np.ndarray, V: np.ndarray, tol: float):
+    """Rank truncation of a cross U V^T (§4.3 postprocessing into standard
+    form; §5.1 truncates ranks at the relative accuracy eps_rel from the
+    singular-value decay): with U = Q_U R_U, V = Q_V R_V and the SVD
+    R_U R_V^T = W diag(s) Z^T, keep the smallest r with
+    sqrt(sum_{i >= r} s_i^2) <= tol * sqrt(sum_i s_i^2) and return
+    (Q_U W_r diag(s_r), Q_V Z_r), r >= 1 unless U V^T = 0."""
+    U = np.asarray(U, dtype=np.float64)
+    V = np.asarray(V, dtype=np.float64)
+    k = U.shape[1]
+    if k == 0:
+        return U, V
+    Qu, Ru = np.linalg.qr(U)
+    Qv, Rv = np.linalg.qr(V)
+    W, s, Zt = np.linalg.svd(Ru @ Rv.T)
+    total = float((s * s).sum())
+    if total == 0.0:
+        return U[:, :0], V[:, :0]
+    tail = np.concatenate([np.cumsum((s * s)[::-1])[::-1], [0.0]])   # tail[r] = sum_{i >= r} s_i^2
+    r = next(r for r in range(1, k + 1) if tail[r] <= tol * tol * total)
+    return Qu @ W[:, :r] * s[:r], Qv @ Zt[:r].T
+
+
 def _stack(vecs, length):
     if not vecs:
         return np.zeros((length, 0))

@@ -171,3 +171,29 @@ def test_verification_catches_a_box_edge_block():
     verified = np.linalg.norm(X - U @ V.T) / np.linalg.norm(X)
     assert unverified > 1e-2
     assert ok and verified <= 2 * tol
+
+
+def test_truncation_keeps_the_product_within_tolerance_and_drops_redundant_rank():
+    """Rank truncation (§4.3 standard form, §5.1 relative accuracy): an
+    exact rank-3 product written with 7 redundant terms comes back at rank
+    3 to rounding; a numerically low-rank cross is cut to the rank the
+    singular-value decay allows, within tol."""
+    rng = np.random.default_rng(4)
+    A, B = rng.normal(size=(40, 3)), rng.normal(size=(30, 3))
+    C = rng.normal(size=(3, 7))
+    U, V = A @ C, B @ np.linalg.pinv(C).T          # U V^T = A B^T, 7 terms
+    Ut, Vt = aca.truncate(U, V, 1e-10)
+    assert Ut.shape[1] == 3
+    assert np.linalg.norm(Ut @ Vt.T - A @ B.T) <= 1e-12 * np.linalg.norm(A @ B.T)
+    x = np.linspace(0.0, 1.0, 60)
+    y = np.linspace(2.0, 3.0, 50)
+    X = 1.0 / (x[:, None] - y[None, :]) ** 2
+    U, V, ok = aca.aca_partial(lambda i: X[i], lambda j: X[:, j], 60, 50, 1e-12, 40)
+    for tol in (1e-4, 1e-7):
+        Ut, Vt = aca.truncate(U, V, tol)
+        s = np.linalg.svd(X, compute_uv=False)
+        # the exact optimal rank for tol, give or take the ACA error
+        r_opt = next(r for r in range(1, len(s) + 1) if np.sqrt((s[r:] ** 2).sum()) <= tol * np.linalg.norm(s))
+        assert abs(Ut.shape[1] - r_opt) <= 1
+        assert np.linalg.norm(X - Ut @ Vt.T) <= 1.01 * tol * np.linalg.norm(X) + 1e-11 * np.linalg.norm(X)
+    assert aca.truncate(np.zeros((5, 2)), np.zeros((4, 2)), 1e-6)[0].shape[1] == 0
