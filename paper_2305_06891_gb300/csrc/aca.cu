@@ -29,7 +29,9 @@
 
 #include <algorithm>
 #include <climits>
+#include <exception>
 #include <memory>
+#include <thread>
 #include <cstring>
 #include <numeric>
 
@@ -977,19 +979,12 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     std::vector<int> tile_at;
     make_tiles(h, h->tiles_h, tile_at);
     std::vector<Tile>& tiles = h->tiles_h;
-    std::vector<IdxRun> near_runs, far_runs;
     h->near_pieces.clear();
     h->far_pieces.clear();
     h->groups_h.clear();
-    near_runs.reserve(h->blocks.size());
-    far_runs.reserve(2 * h->blocks.size());
-    h->near_pieces.reserve(h->blocks.size());
-    h->far_pieces.reserve(2 * h->blocks.size());
-    int64_t fallback = 0, near_e = 0, far_u = 0, far_v = 0;
-    int maxk = 0;
+    int64_t fallback = 0;
     // column groups of the low-rank blocks (k > 0), in order of first use
     std::vector<int> group_of_node(h->nodes.size(), -1);
-    std::vector<std::vector<int>> group_blocks;
     for (int b = 0; b < (int)h->blocks.size(); ++b) {
         BlockH& bk = h->blocks[b];
         bk.group = -1;
@@ -1007,12 +1002,10 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
         if (gid < 0) {
             gid = (int)h->groups_h.size();
             h->groups_h.push_back(Group{bk.c0, bk.c1 - bk.c0, 0, 0, 0, 0, 0});
-            group_blocks.emplace_back();
         }
         bk.group = gid;
         bk.grow = h->groups_h[gid].M;
         h->groups_h[gid].M += bk.rank;
-        group_blocks[gid].push_back(b);
     }
     int toff = 0;
     for (auto& gr : h->groups_h) {
@@ -1021,38 +1014,109 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
         toff += gr.M;
     }
     h->sum_rank = toff;
-    std::vector<DenseWork> dwork;
-    std::vector<UWork> uwork;
-    std::vector<VWork> vwork;
-    dwork.reserve(h->blocks.size());
-    uwork.reserve(2 * h->blocks.size());
-    vwork.reserve(h->blocks.size());
-    for (int b = 0; b < (int)h->blocks.size(); ++b) {
+    // Per-tile panel columns, gather runs and fill work.  Large plans are
+    // split into kPlanParts row ranges cut at tile starts and built by
+    // threads (each range owns its tiles); blocks whose rows cross a cut go
+    // first, sequentially.  The layout is deterministic for a given block
+    // list (the part count does not depend on the machine).
+    struct PlanPart {
+        std::vector<DenseWork> dwork;
+        std::vector<UWork> uwork;
+        std::vector<VWork> vwork;
+        std::vector<IdxRun> near_runs, far_runs;
+        std::vector<Piece> near_pieces, far_pieces;
+        int64_t near_e = 0, far_u = 0, far_v = 0;
+        int maxk = 0;
+    };
+    auto plan_block = [&](int b, PlanPart& o) {
         const BlockH& bk = h->blocks[b];
         const int m = bk.r1 - bk.r0, n = bk.c1 - bk.c0;
         if (bk.rank < 0) {
-            near_e += (long long)m * n;
+            o.near_e += (long long)m * n;
             for_tiles(tiles, tile_at, bk.r0, bk.r1, [&](int t) {
-                h->near_pieces.push_back(Piece{b, t, tiles[t].kn});
+                o.near_pieces.push_back(Piece{b, t, tiles[t].kn});
                 for (int c0 = 0; c0 < n; c0 += 64)
-                    dwork.push_back(DenseWork{t, bk.c0 + c0, std::min(64, n - c0), tiles[t].kn + c0});
-                near_runs.push_back(IdxRun{t, tiles[t].kn, bk.c0, n});
+                    o.dwork.push_back(DenseWork{t, bk.c0 + c0, std::min(64, n - c0), tiles[t].kn + c0});
+                o.near_runs.push_back(IdxRun{t, tiles[t].kn, bk.c0, n});
                 tiles[t].kn += n;
             });
         } else if (bk.rank > 0) {
             const int k = bk.rank;
             const int jb = job_of[b];
             const Group& gr = h->groups_h[bk.group];
-            maxk = std::max(maxk, k);
-            far_u += (long long)k * m;
-            far_v += (long long)k * n;
+            o.maxk = std::max(o.maxk, k);
+            o.far_u += (long long)k * m;
+            o.far_v += (long long)k * n;
             for_tiles(tiles, tile_at, bk.r0, bk.r1, [&](int t) {
-                h->far_pieces.push_back(Piece{b, t, tiles[t].kf});
-                uwork.push_back(UWork{t, tiles[t].r0 - bk.r0, m, k, tiles[t].kf, job_chunk[jb], src_u[jb]});
-                far_runs.push_back(IdxRun{t, tiles[t].kf, gr.toff + bk.grow, k});
+                o.far_pieces.push_back(Piece{b, t, tiles[t].kf});
+                o.uwork.push_back(UWork{t, tiles[t].r0 - bk.r0, m, k, tiles[t].kf, job_chunk[jb], src_u[jb]});
+                o.far_runs.push_back(IdxRun{t, tiles[t].kf, gr.toff + bk.grow, k});
                 tiles[t].kf += k;
             });
-            vwork.push_back(VWork{bk.group, bk.grow, n, k, job_chunk[jb], 0, src_v[jb]});
+            o.vwork.push_back(VWork{bk.group, bk.grow, n, k, job_chunk[jb], 0, src_v[jb]});
+        }
+    };
+    constexpr int kPlanParts = 8;
+    const int nb = (int)h->blocks.size();
+    const int parts = nb >= 20000 ? kPlanParts : 1;
+    std::vector<int> cut(parts + 1, 0);   // row cuts at tile starts
+    cut[parts] = (int)h->n;
+    for (int q = 1; q < parts; ++q) {
+        int r = (int)((long long)h->n * q / parts);
+        while (r < (int)h->n && tile_at[r] < 0) ++r;
+        cut[q] = std::max(cut[q - 1], r);
+    }
+    std::vector<PlanPart> pp(parts + 1);  // pp[0]: crossing blocks, pp[q + 1]: range q
+    std::vector<std::vector<int>> part_blocks(parts);
+    for (int b = 0; b < nb; ++b) {
+        const BlockH& bk = h->blocks[b];
+        const int q = (int)(std::upper_bound(cut.begin(), cut.end(), bk.r0) - cut.begin()) - 1;
+        if (bk.r1 > cut[q + 1]) plan_block(b, pp[0]);
+        else part_blocks[q].push_back(b);
+    }
+    std::vector<std::exception_ptr> part_err(parts);
+    auto run_part = [&](int q) {
+        try {
+            for (int b : part_blocks[q]) plan_block(b, pp[q + 1]);
+        } catch (...) {
+            part_err[q] = std::current_exception();
+        }
+    };
+    if (parts == 1) {
+        run_part(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int q = 1; q < parts; ++q) th.emplace_back(run_part, q);
+        run_part(0);
+        for (auto& x : th) x.join();
+    }
+    for (auto& e : part_err)
+        if (e) std::rethrow_exception(e);
+    std::vector<DenseWork> dwork;
+    std::vector<UWork> uwork;
+    std::vector<VWork> vwork;
+    std::vector<IdxRun> near_runs, far_runs;
+    int64_t near_e = 0, far_u = 0, far_v = 0;
+    int maxk = 0;
+    {
+        size_t nd = 0, nu = 0, nv = 0, nn = 0, nf = 0, pn = 0, pf = 0;
+        for (auto& o : pp) {
+            nd += o.dwork.size(); nu += o.uwork.size(); nv += o.vwork.size(); nn += o.near_runs.size();
+            nf += o.far_runs.size(); pn += o.near_pieces.size(); pf += o.far_pieces.size();
+        }
+        dwork.reserve(nd); uwork.reserve(nu); vwork.reserve(nv); near_runs.reserve(nn); far_runs.reserve(nf);
+        h->near_pieces.reserve(pn);
+        h->far_pieces.reserve(pf);
+        for (auto& o : pp) {
+            dwork.insert(dwork.end(), o.dwork.begin(), o.dwork.end());
+            uwork.insert(uwork.end(), o.uwork.begin(), o.uwork.end());
+            vwork.insert(vwork.end(), o.vwork.begin(), o.vwork.end());
+            near_runs.insert(near_runs.end(), o.near_runs.begin(), o.near_runs.end());
+            far_runs.insert(far_runs.end(), o.far_runs.begin(), o.far_runs.end());
+            h->near_pieces.insert(h->near_pieces.end(), o.near_pieces.begin(), o.near_pieces.end());
+            h->far_pieces.insert(h->far_pieces.end(), o.far_pieces.begin(), o.far_pieces.end());
+            near_e += o.near_e; far_u += o.far_u; far_v += o.far_v;
+            maxk = std::max(maxk, o.maxk);
         }
     }
     long long noff = 0, foff = 0;
