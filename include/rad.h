@@ -151,7 +151,7 @@ typedef struct {
     int32_t grid_a1, grid_b1;    /* grids of the 1-column phases (0: per item)  */
     int32_t grid_a2, grid_b2;    /* grids of the 2-4 column launches            */
     int32_t product_path;        /* >= 5 FP32 columns: 0 CUDA cores, 1 tensor cores */
-    int32_t reserved2;
+    int32_t closed;              /* 1 after rad_htree_close_cavity               */
 } rad_htree_stats;
 
 /* -------------------------------------------------------------------------
@@ -246,6 +246,16 @@ int rad_htree_autotune(rad_htree* h, void* stream);
  * the faster one for the handle's operator; recompression resets it to 0.
  * RAD_EINVAL for another value. */
 int rad_htree_set_product_path(rad_htree* h, int32_t path);
+
+/* Closed-cavity treatment of the view factors (§6, Eqs. rowsum,
+ * clamped_rowsum and F_closed, with the textbook F): s_i = sum_j F_ij of
+ * the stored operator (the FP32 accurate copy when the factors are BF16),
+ * c_i = s_i clamped to [0, 1], and every row with c_i != 0 divided by c_i,
+ * in the stored dense blocks and U factors.  row_sums (may be NULL)
+ * receives s in facet order (n doubles, host or device).  Requires a
+ * compressed handle; call again after every rad_compress_aca (compression
+ * rebuilds the unscaled operator).  Calling it twice scales twice. */
+int rad_htree_close_cavity(rad_htree* h, double* row_sums, void* stream);
 
 /* -------------------------------------------------------------------------
  * rad_solve_flux — A7-A8: for each of the m temperature fields T(:, c)

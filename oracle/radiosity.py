@@ -23,6 +23,18 @@ from . import viewfactor
 from .geometry import Facets
 
 
+def close_cavity(F: np.ndarray):
+    """Closed-cavity treatment of §6 (Eqs. rowsum, clamped_rowsum, F_closed),
+    with the textbook F: s_i = sum_j F_ij (the paper's (1/A_i) sum_j of its
+    area-weighted entries), c_i = s_i clamped to [0, 1], and every row with
+    c_i != 0 divided by c_i.  Returns (F_closed, s, c)."""
+    F = np.asarray(F, dtype=np.float64)
+    s = F.sum(axis=1)
+    c = np.clip(s, 0.0, 1.0)
+    scale = np.where(c != 0.0, 1.0 / np.where(c != 0.0, c, 1.0), 1.0)
+    return F * scale[:, None], s, c
+
+
 def reflection_matrix(F: np.ndarray, eps: np.ndarray) -> np.ndarray:
     """C = I - diag(1 - eps) F, Eq. (11)."""
     N = F.shape[0]

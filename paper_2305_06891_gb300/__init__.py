@@ -87,7 +87,7 @@ class _Stats(C.Structure):
                 ("far_u_entries", C.c_int64), ("far_v_entries", C.c_int64), ("n_tiles", C.c_int64),
                 ("bytes_accurate", C.c_int64), ("tuned", C.c_int32), ("stream_rows", C.c_int32),
                 ("grid_a1", C.c_int32), ("grid_b1", C.c_int32), ("grid_a2", C.c_int32), ("grid_b2", C.c_int32),
-                ("product_path", C.c_int32), ("reserved2", C.c_int32)]
+                ("product_path", C.c_int32), ("closed", C.c_int32)]
 
 
 def _load():
@@ -118,6 +118,7 @@ def _load():
         "rad_htree_free": (C.c_int, [H]),
         "rad_htree_autotune": (C.c_int, [H, vp]),
         "rad_htree_set_product_path": (C.c_int, [H, i32]),
+        "rad_htree_close_cavity": (C.c_int, [H, vp, vp]),
         "rad_server_create": (C.c_int, [C.POINTER(_ServerParams), C.POINTER(vp)]),
         "rad_server_add_cavity": (C.c_int, [vp, i64, vp, C.POINTER(i64)]),
         "rad_server_submit": (C.c_int, [vp, i64, vp, vp, i64, i64, dbl, vp, i64, C.POINTER(i64)]),
@@ -499,6 +500,13 @@ def rad_htree_autotune(h: HTree, stream=None) -> dict:
     _check(_lib.rad_htree_autotune(h.ptr, _stream(stream)))
     st = rad_htree_get_stats(h)
     return {k: st[k] for k in ("stream_rows", "grid_a1", "grid_b1", "grid_a2", "grid_b2", "product_path")}
+
+
+def rad_htree_close_cavity(h: HTree, stream=None) -> np.ndarray:
+    """Closed-cavity row normalisation (§6); returns the row sums s (facet order)."""
+    s = np.empty(h.n, dtype=np.float64)
+    _check(_lib.rad_htree_close_cavity(h.ptr, s.ctypes.data, _stream(stream)))
+    return s
 
 
 def rad_htree_set_product_path(h: HTree, path: int) -> None:

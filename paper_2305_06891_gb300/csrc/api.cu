@@ -602,6 +602,7 @@ int rad_htree_get_stats(const rad_htree* h, rad_htree_stats* st) {
         st->grid_a2 = h->grid_a2;
         st->grid_b2 = h->grid_b2;
         st->product_path = h->mm_path;
+        st->closed = h->closed;
     });
 }
 
@@ -653,6 +654,24 @@ int rad_htree_autotune(rad_htree* h, void* stream) {
     return guarded([&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null argument");
         autotune(h, static_cast<cudaStream_t>(stream));
+    });
+}
+
+int rad_htree_close_cavity(rad_htree* h, double* row_sums, void* stream) {
+    return guarded([&] {
+        RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null argument");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        Scratch ws(s);
+        const int n = (int)h->n;
+        double* st = ws.get_n<double>(n);
+        close_cavity(h, st, s);
+        if (row_sums) {
+            double* ud = is_device_ptr(row_sums) ? row_sums : ws.get_n<double>(n);
+            scatter_tree_to_user(h, st, 1, 1, true, RAD_F64, ud, n, s);
+            if (ud != row_sums)
+                RAD_CUDA(cudaMemcpyAsync(row_sums, ud, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        }
+        RAD_CUDA(cudaStreamSynchronize(s));
     });
 }
 

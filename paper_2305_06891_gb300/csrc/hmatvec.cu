@@ -877,6 +877,88 @@ void scatter_tree_to_user(const rad_htree* h, const void* Y, int ldY, int nrhs, 
 }
 
 
+// ---------------------------------------------------------------- closed cavity
+// §6 closed-cavity rows: s = F 1 with the stored operator, c = clamp(s, 0, 1),
+// row i of F divided by c_i when c_i != 0.  The operator is stored by rows in
+// the tile panels (dense panel and U panel; V is shared by all rows of a
+// block), so the scaling multiplies the tile rows of both panels (and of the
+// FP32 accurate copy of U when kept).
+namespace {
+
+template <class T>
+__global__ void fill_kernel(T* x, long long cnt, T v) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < cnt) x[e] = v;
+}
+
+template <class T>
+__global__ void row_scale_kernel(const T* __restrict__ sums, int n, double* __restrict__ s64,
+                                 double* __restrict__ scale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double si = (double)sums[i];
+    const double c = si < 0.0 ? 0.0 : (si > 1.0 ? 1.0 : si);
+    s64[i] = si;
+    scale[i] = c != 0.0 ? 1.0 / c : 1.0;
+}
+
+template <class S>
+__global__ void __launch_bounds__(256)
+scale_panel_kernel(const Tile* __restrict__ tiles, int far, const double* __restrict__ scale, S* pool) {
+    const Tile t = tiles[blockIdx.x];
+    const int k = far ? t.kf : t.kn;
+    S* P = pool + (far ? t.foff : t.noff);
+    const long long cnt = (long long)k * t.ld;
+    for (long long e = threadIdx.x; e < cnt; e += 256) {
+        const int r = (int)(e % t.ld);
+        if (r < t.rows) P[e] = Store<S>::put((double)Store<S>::get(P[e]) * scale[t.r0 + r]);
+    }
+}
+
+template <class S>
+void scale_panels(const rad_htree* h, int far, const double* scale, void* pool, cudaStream_t s) {
+    if (h->n_tiles == 0) return;
+    { ProfScope ps_("close_cavity", s); scale_panel_kernel<S><<<h->n_tiles, 256, 0, s>>>(h->d_tiles.as<Tile>(), far, scale, static_cast<S*>(pool)); }
+    RAD_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+void close_cavity(rad_htree* h, double* s_tree_out, cudaStream_t s) {
+    RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed (call rad_compress_aca)");
+    Scratch ws(s);
+    const int n = (int)h->n;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    double* S64 = s_tree_out;
+    double* scale = ws.get_n<double>(n);
+    const Epi st{kStore, nullptr, nullptr, nullptr, 0};
+    if (h->op_is_f64() || h->has_accurate) {
+        // FP64 operator, or the FP32 accurate copy with FP64-grade sums
+        double* X = ws.get_n<double>(n);
+        double* Y = ws.get_n<double>(n);
+        fill_kernel<double><<<g, 256, 0, s>>>(X, n, 1.0);
+        RAD_CHECK_LAUNCH();
+        if (h->op_is_f64()) apply_tree(h, X, 1, Y, 1, 1, st, ws.get(apply_workspace_bytes(h, 1)), s);
+        else apply_tree_acc(h, X, 1, Y, 1, 1, st, static_cast<double*>(ws.get(apply_workspace_bytes_acc(h, 1))), s);
+        row_scale_kernel<double><<<g, 256, 0, s>>>(Y, n, S64, scale);
+    } else {
+        float* X = ws.get_n<float>(n);
+        float* Y = ws.get_n<float>(n);
+        fill_kernel<float><<<g, 256, 0, s>>>(X, n, 1.0f);
+        RAD_CHECK_LAUNCH();
+        apply_tree(h, X, 1, Y, 1, 1, st, ws.get(apply_workspace_bytes(h, 1)), s);
+        row_scale_kernel<float><<<g, 256, 0, s>>>(Y, n, S64, scale);
+    }
+    RAD_CHECK_LAUNCH();
+    if (h->near_dtype == RAD_F64) scale_panels<double>(h, 0, scale, h->near_pool.p, s);
+    else scale_panels<float>(h, 0, scale, h->near_pool.p, s);
+    if (h->factor_dtype == RAD_F64) scale_panels<double>(h, 1, scale, h->far_pool.p, s);
+    else if (h->factor_dtype == RAD_F32) scale_panels<float>(h, 1, scale, h->far_pool.p, s);
+    else scale_panels<__nv_bfloat16>(h, 1, scale, h->far_pool.p, s);
+    if (h->far_pool_acc.p) scale_panels<float>(h, 1, scale, h->far_pool_acc.p, s);
+    h->closed = 1;
+}
+
 // ---------------------------------------------------------------- autotuner
 // Times the streaming products on this handle's operator for every
 // candidate (far-field item rows x grid policy of each launch) and keeps the

@@ -300,6 +300,7 @@ struct rad_htree {
     // 1 = tensor cores (split TF32); set by rad_htree_autotune or
     // rad_htree_set_product_path
     int mm_path = 0;
+    int closed = 0;   // rows normalised for a closed cavity (rad_htree_close_cavity)
     int64_t n = 0;
     // segment (cavity) boundaries of a batch handle: cavity c holds facets
     // [seg[c], seg[c+1]) in user order and in tree order; {0, n} otherwise
@@ -413,6 +414,7 @@ void tc_far_vt(const OpView& op, const float* X, int ldx, float* T, int ldt, int
 bool tc_take_timeout();
 void build_stream_lists(rad_htree* h, int rows, cudaStream_t s);
 void autotune(rad_htree* h, cudaStream_t s);
+void close_cavity(rad_htree* h, double* s_tree_out, cudaStream_t s);
 void drop_product_graph(const rad_htree* h);
 void gather_user_to_tree(const rad_htree* h, int dtype_in, const void* x, int64_t ldx, int nrhs,
                          void* X, int ldX, bool op64, cudaStream_t s);

@@ -90,3 +90,37 @@ def test_device_buffers_equal_host_buffers():
     qd, _ = r.rad_solve_flux(h, torch.as_tensor(c.eps, device="cuda"), torch.as_tensor(c.T, device="cuda"),
                              SIGMA_SB, tol=1e-12)
     np.testing.assert_array_equal(qd.cpu().numpy(), qh)
+
+
+def _sphere_facets(n=400, seed=8, fill=0.8, R=1.5):
+    rng = np.random.default_rng(seed)
+    p = rng.normal(size=(n, 3))
+    p /= np.linalg.norm(p, axis=1, keepdims=True)
+    area = rng.uniform(0.5, 1.5, size=n)
+    area *= fill * 4.0 * np.pi * R * R / area.sum()
+    return geometry.Facets(R * p, -p, area)
+
+
+@pytest.mark.parametrize("dt", ["f64", "f32", "bf16"])
+def test_closed_cavity_rows_match_the_oracle(dt):
+    """§6 closed cavity: after rad_htree_close_cavity the stored operator is
+    the oracle's row-scaled F (facets on a sphere, where s_i is known in
+    closed form), and its rows sum to 1."""
+    f = _sphere_facets()
+    r = rad()
+    h = r.rad_build_htree_facets(f.c, f.n, f.area, leaf_size=16, eta_adm=1.0)
+    near = "f64" if dt == "f64" else "f32"
+    r.rad_compress_aca(h, 1e-10 if dt == "f64" else 1e-6, 64, "partial", dt, near,
+                       accurate_dtype=None if dt != "bf16" else "f32")
+    s = r.rad_htree_close_cavity(h)
+    F = viewfactor.dense(f)
+    Fc, s_ref, _ = radiosity.close_cavity(F)
+    assert r.rad_htree_get_stats(h)["closed"] == 1
+    assert np.abs(s - s_ref).max() <= (1e-9 if dt == "f64" else 2e-6)
+    x = np.random.default_rng(3).uniform(0.5, 1.5, f.c.shape[0])
+    xin = x if dt == "f64" else x.astype(np.float32)
+    tol = {"f64": 1e-9, "f32": 2e-6, "bf16": 1e-2}[dt]
+    assert rel(r.rad_hmatvec(h, xin), Fc @ x) <= tol
+    ones = np.ones(f.c.shape[0]) if dt == "f64" else np.ones(f.c.shape[0], np.float32)
+    assert np.abs(r.rad_hmatvec(h, ones) - 1.0).max() <= tol
+    h.free()

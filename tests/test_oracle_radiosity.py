@@ -102,3 +102,35 @@ def test_sampled_rows_agree_with_dense():
     x = c.T[:, 0] ** 4
     np.testing.assert_allclose(radiosity.matvec_rows(f, rows, x), (F @ x)[rows], rtol=1e-13)
     np.testing.assert_allclose(radiosity.rowsum_rows(f, rows), F.sum(axis=1)[rows], rtol=1e-13)
+
+
+def test_closed_cavity_rows_follow_the_clamp_rule():
+    """§6 closed cavity: rows with 0 < s_i <= 1 sum to 1 after the scaling,
+    rows with s_i > 1 or s_i = 0 are left alone (c_i = 1 or c_i = 0)."""
+    rng = np.random.default_rng(2)
+    F = rng.uniform(0.0, 0.2, (6, 6))
+    F[1] *= 10.0           # s > 1: c = 1, row kept
+    F[2] = 0.0             # s = 0: c = 0, row kept
+    Fc, s, c = radiosity.close_cavity(F)
+    assert s[1] > 1.0 and c[1] == 1.0 and np.array_equal(Fc[1], F[1])
+    assert s[2] == 0.0 and c[2] == 0.0 and np.array_equal(Fc[2], F[2])
+    for i in (0, 3, 4, 5):
+        assert 0.0 < s[i] <= 1.0
+        assert abs(Fc[i].sum() - 1.0) <= 1e-15
+        np.testing.assert_allclose(Fc[i], F[i] / s[i], rtol=1e-15)
+    # facets on a sphere with inward radial normals: F_ij = A_j / (4 pi R^2)
+    # (sphere identity), so s_i = (A - A_i) / (4 pi R^2) with A = sum of areas;
+    # with A below the sphere's area every row is scaled to sum 1, and row i
+    # becomes A_j / (A - A_i)
+    rng = np.random.default_rng(8)
+    R = 1.5
+    p = rng.normal(size=(60, 3))
+    p /= np.linalg.norm(p, axis=1, keepdims=True)
+    area = rng.uniform(0.5, 1.5, size=60)
+    area *= 0.8 * 4.0 * math.pi * R * R / area.sum()
+    f = geometry.Facets(R * p, -p, area)
+    Fc, s, c = radiosity.close_cavity(viewfactor.dense(f))
+    np.testing.assert_allclose(s, (area.sum() - area) / (4.0 * math.pi * R * R), rtol=1e-12)
+    expect = area[None, :] / (area.sum() - area)[:, None]
+    np.fill_diagonal(expect, 0.0)
+    np.testing.assert_allclose(Fc, expect, rtol=1e-12)
