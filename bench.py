@@ -105,10 +105,12 @@ def build(rad, work, verts):
 
 
 PRODUCT_PATH = None   # --product-path: many-column product kernels (library default when None)
+RECOMPRESS = 0.0      # --recompress-tol: truncation of the ACA crosses (0 = off)
 
 
 def compress(rad, h):
-    rad.rad_compress_aca(h, ACA_TOL, 64, "partial", W["factor"], W["near"], accurate_dtype=W["accurate"])
+    rad.rad_compress_aca(h, ACA_TOL, 64, "partial", W["factor"], W["near"], accurate_dtype=W["accurate"],
+                         recompress_tol=RECOMPRESS)
     if PRODUCT_PATH is not None:
         rad.rad_htree_set_product_path(h, PRODUCT_PATH)
 
@@ -481,7 +483,8 @@ def accuracy_vs_oracle(work, samples=512, cols=4, seed=7, no_fp64=False):
         exact[k] = (rows[cav_of == k], viewfactor.rows(geometry.facets_from_triangles(c.verts), loc))
     for label, (fac, near, acc, refine) in paths.items():
         h = build(rad, work, verts_d)
-        rad.rad_compress_aca(h, ACA_TOL, 64, "partial", fac, near, accurate_dtype=acc)
+        rad.rad_compress_aca(h, ACA_TOL, 64, "partial", fac, near, accurate_dtype=acc,
+                             recompress_tol=RECOMPRESS if label == "ours" else 0.0)
         Y, info = rad.rad_solve_reflection(h, work.eps, B, tol=SOLVE_TOL, restart=RESTART, max_iter=600,
                                            refine=refine, inner_tol=1e-4)
         h.free()
@@ -528,6 +531,7 @@ def run_reference(args):
 def config_dict(work=None):
     d = {"workload": W["name"], "fields": FIELDS, "leaf_size": LEAF, "eta_adm": ETA, "aca_tol": ACA_TOL,
          "aca_pivoting": "partial, stop checked on a residual probe in every row and column",
+         "recompress_tol": RECOMPRESS,
          "solve_tol": SOLVE_TOL, "gmres_restart": RESTART,
          "storage": f"{W['near']} near + {W['factor']} factors",
          "accumulation": "f32 (operator), f64 (Krylov, inner products, residuals)",
@@ -554,7 +558,7 @@ def run_served(args):
     srv = rad.Server(slots=W["slots"], hbm_budget_bytes=W["budget_gib"] << 30, leaf_size=LEAF, eta_adm=ETA,
                      aca_tol=ACA_TOL, factor_dtype=W["factor"], near_dtype=W["near"],
                      accurate_dtype=W["accurate"], tol=SOLVE_TOL, restart=RESTART, max_iter=600,
-                     refine=W["refine"], inner_tol=1e-4)
+                     refine=W["refine"], inner_tol=1e-4, recompress_tol=RECOMPRESS)
     ids = [srv.add_cavity(v) for v in pool]
 
     def stream():
@@ -594,7 +598,8 @@ def run_served(args):
     # the dominant kernel: one product on the largest pool operator
     big = int(np.argmax([v.shape[0] for v in pool]))
     h = rad.rad_build_htree(torch.as_tensor(pool[big], device=dev), LEAF, ETA)
-    rad.rad_compress_aca(h, ACA_TOL, 64, "partial", W["factor"], W["near"], accurate_dtype=W["accurate"])
+    rad.rad_compress_aca(h, ACA_TOL, 64, "partial", W["factor"], W["near"], accurate_dtype=W["accurate"],
+                         recompress_tol=RECOMPRESS)
     hst = rad.rad_htree_get_stats(h)
     n = pool[big].shape[0]
     x = torch.ones(n, dtype=torch.float32, device=dev)
@@ -689,10 +694,13 @@ def main():
     ap.add_argument("--workload", default="cylinder", choices=sorted(WORKLOADS))
     ap.add_argument("--product-path", type=int, choices=[0, 1], default=None,
                     help="many-column product: 0 CUDA-core tiles, 1 tensor cores (default: library choice)")
+    ap.add_argument("--recompress-tol", type=float, default=None,
+                    help="truncate every ACA cross at this relative accuracy (default: the workload's setting)")
     args = ap.parse_args()
     select_workload(args.workload)
-    global PRODUCT_PATH
+    global PRODUCT_PATH, RECOMPRESS
     PRODUCT_PATH = args.product_path
+    RECOMPRESS = W.get("recompress", 0.0) if args.recompress_tol is None else args.recompress_tol
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
 

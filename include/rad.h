@@ -83,7 +83,14 @@ typedef struct {
  * 0 = 30% of the free device memory, at most 48 GiB, at least 1 GiB; > 0 =
  * that many MiB.  Blocks beyond the bound are compressed in further chunks,
  * each compacted to its ranks before the next starts; the result does not
- * depend on the chunking. */
+ * depend on the chunking.
+ * recompress_tol (§4.3 postprocessing into standard form, ranks truncated
+ * by the singular-value decay as in §5.1): 0 = keep every ACA cross as it
+ * is; in (0, 1) = bring each cross of rank 2..64 to U = Q_U W_r diag(s_r),
+ * V = Q_V Z_r from the SVD of R_U R_V^T (U = Q_U R_U, V = Q_V R_V), with the
+ * smallest r >= 1 such that the dropped singular values have
+ * sqrt(sum s_i^2) <= recompress_tol * ||U V^T||_F.  The dropped part adds at
+ * most that relative error to each block (on top of tol). */
 typedef struct {
     double  tol;
     int32_t max_rank;
@@ -92,6 +99,7 @@ typedef struct {
     int32_t near_dtype;
     int32_t accurate_dtype;
     int32_t scratch_mib;
+    double  recompress_tol;
 } rad_aca_params;
 
 /* GMRES on C y = b, C = I - diag(1 - eps) F (Eq. 11).  Stops when every

@@ -44,7 +44,7 @@ class _TreeParams(C.Structure):
 class _AcaParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_rank", C.c_int32), ("pivoting", C.c_int32),
                 ("factor_dtype", C.c_int32), ("near_dtype", C.c_int32), ("accurate_dtype", C.c_int32),
-                ("scratch_mib", C.c_int32)]
+                ("scratch_mib", C.c_int32), ("recompress_tol", C.c_double)]
 
 
 class _SolveParams(C.Structure):
@@ -300,10 +300,13 @@ def rad_htree_from_dense(F, stream=None) -> HTree:
 
 def rad_compress_aca(h: HTree, tol: float, max_rank: int = 64, pivoting: str = "partial",
                      factor_dtype: str = "f32", near_dtype: str = "f32", accurate_dtype: str | None = None,
-                     stream=None, scratch_mib: int = 0) -> None:
+                     stream=None, scratch_mib: int = 0, recompress_tol: float = 0.0) -> None:
+    """ACA of the admissible blocks (dense entries for the others).
+    ``recompress_tol`` > 0 truncates every cross to standard form at that
+    relative accuracy (SVD of R_U R_V^T after QR of both factors)."""
     acc = -1 if accurate_dtype is None else _DT[accurate_dtype]
     p = _AcaParams(float(tol), int(max_rank), _PIV[pivoting], _DT[factor_dtype], _DT[near_dtype], acc,
-                   int(scratch_mib))
+                   int(scratch_mib), float(recompress_tol))
     _check(_lib.rad_compress_aca(h.ptr, C.byref(p), _stream(stream)))
 
 
@@ -412,11 +415,11 @@ class Server:
                  eta_adm: float = 1.0, aca_tol: float = 1e-6, max_rank: int = 64, factor_dtype: str = "bf16",
                  near_dtype: str = "f32", accurate_dtype: str | None = "f32", tol: float = 1e-8,
                  restart: int = 30, max_iter: int = 1000, refine: bool = True, inner_tol: float = 1e-4,
-                 max_refine: int = 10, aca_scratch_mib: int = 0):
+                 max_refine: int = 10, aca_scratch_mib: int = 0, recompress_tol: float = 0.0):
         acc = -1 if accurate_dtype is None else _DT[accurate_dtype]
         p = _ServerParams(int(slots), 0, int(hbm_budget_bytes), _TreeParams(int(leaf_size), 0, float(eta_adm)),
                           _AcaParams(float(aca_tol), int(max_rank), RAD_ACA_PARTIAL, _DT[factor_dtype],
-                                     _DT[near_dtype], acc, int(aca_scratch_mib)),
+                                     _DT[near_dtype], acc, int(aca_scratch_mib), float(recompress_tol)),
                           _SolveParams(float(tol), int(restart), int(max_iter), 1 if refine else 0,
                                        int(max_refine), float(inner_tol)))
         out = C.c_void_p()

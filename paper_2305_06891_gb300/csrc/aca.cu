@@ -578,6 +578,249 @@ compact_kernel(const AcaJob* __restrict__ jobs, const int* __restrict__ rank, co
     for (long long e = threadIdx.x; e < nv; e += 256) Vc[cv[blockIdx.x] + e] = Vs[j.offV + e];
 }
 
+// ------------------------------------------------------------ recompression
+// §4.3 postprocessing of an ACA cross into standard form, with the rank
+// truncated at a relative accuracy by the singular-value rule of §5.1:
+// U = Q_U R_U and V = Q_V R_V (classical Gram-Schmidt applied twice),
+// M = R_U R_V^T, one-sided Jacobi rotations on the columns of M accumulated
+// in an orthogonal Z (M Z = W diag(s) at convergence), and the smallest r
+// with sum_{i >= r} s_i^2 <= tol^2 sum_i s_i^2 is kept (s_i = norms of the
+// columns of M Z in decreasing order, r >= 1):
+// U <- Q_U (M Z)_r, V <- Q_V Z_r, in place in the ACA scratch.  Because Z is
+// orthogonal, the dropped part has Frobenius norm exactly the norm of the
+// dropped columns of M Z, converged or not.
+constexpr int kRcMax = 64;     // crosses of higher rank keep their ACA form
+constexpr int kRcRows = 64;    // row chunk of the final in-place product
+constexpr int kRcSweeps = 16;
+
+// shared memory of one cross of rank <= KM (leading dimension KM + 1)
+template <class CT, int KM, int NT>
+struct RcSmem {
+    static constexpr int LD = KM + 1;
+    CT R[2][KM * LD];          // R_U, R_V ([row][col], upper triangular)
+    CT M[KM * LD];             // R_U R_V^T, rotated in place to M Z
+    CT Z[KM * LD];             // accumulated rotations
+    CT Qc[kRcRows * LD];       // row chunk of Q in the final product
+    CT coef[KM];
+    CT red[NT / 32 + 1];
+    CT s2[KM];
+    int pos[KM];               // column of M Z holding the r-th largest norm
+    int keep;
+    int rotated;
+};
+
+template <class CT> struct RcTol;
+template <> struct RcTol<float> {
+    static constexpr float eps = 1.1920929e-7f;
+    static constexpr float orth = 1e-5f;     // Jacobi: columns count as orthogonal
+};
+template <> struct RcTol<double> {
+    static constexpr double eps = 2.220446049250313e-16;
+    static constexpr double orth = 1e-10;
+};
+
+// In-place QR of the len x k column-major A: A <- Q, R (row-major) upper
+// triangular.  Each column loses its components along the previous ones
+// twice (coefficients accumulated in R); what is left is normalised, or
+// zeroed with R_cc = 0 when it is below 16 eps of the column.
+template <class CT, int KM, int NT>
+__device__ void rc_qr(CT* A, int len, int k, CT* R, RcSmem<CT, KM, NT>& S) {
+    constexpr int LD = KM + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = threadIdx.x; e < KM * LD; e += NT) R[e] = CT(0);
+    __syncthreads();
+    for (int c = 0; c < k; ++c) {
+        CT* a = A + (long long)c * len;
+        for (int pass = 0; pass < 2 && c > 0; ++pass) {
+            for (int q = warp; q < c; q += NT / 32) {
+                const CT* aq = A + (long long)q * len;
+                CT s = CT(0);
+                for (int i = lane; i < len; i += 32) s += aq[i] * a[i];
+                s = warp_sum(s);
+                if (lane == 0) S.coef[q] = s;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < len; i += NT) {
+                CT v = a[i];
+                for (int q = 0; q < c; ++q) v -= A[(long long)q * len + i] * S.coef[q];
+                a[i] = v;
+            }
+            if (threadIdx.x < c) R[threadIdx.x * LD + c] += S.coef[threadIdx.x];
+            __syncthreads();
+        }
+        CT s = CT(0);
+        for (int i = threadIdx.x; i < len; i += NT) s += a[i] * a[i];
+        s = block_sum<NT>(s, S.red);
+        CT orig = s;
+        for (int q = 0; q < c; ++q) orig += R[q * LD + c] * R[q * LD + c];
+        const bool dir = s > CT(0) && s > CT(256) * RcTol<CT>::eps * RcTol<CT>::eps * orig;
+        const CT nrm = sqrt(s);
+        const CT inv = dir ? CT(1) / nrm : CT(0);
+        for (int i = threadIdx.x; i < len; i += NT) a[i] *= inv;
+        if (threadIdx.x == 0) R[c * LD + c] = dir ? nrm : CT(0);
+        __syncthreads();
+    }
+}
+
+// One-sided Jacobi on the k x k matrix S.M, rotations accumulated in S.Z.
+// Each sweep visits every column pair once in k - 1 rounds of disjoint pairs
+// (round-robin: player 0 fixed, players 1 .. K-1 on a circle; an odd k adds
+// an idle player); one warp per pair.  A pair is left alone when its
+// coupling is below orth of its columns' norms or below `floor` (a
+// thousandth of the truncation threshold tol^2 ||M||_F^2: it cannot move
+// the truncation).
+template <class CT, int KM, int NT>
+__device__ void rc_jacobi(int k, CT floor, RcSmem<CT, KM, NT>& S) {
+    constexpr int LD = KM + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int K = k + (k & 1);
+    for (int sweep = 0; sweep < kRcSweeps; ++sweep) {
+        if (threadIdx.x == 0) S.rotated = 0;
+        __syncthreads();
+        for (int r = 0; r < K - 1; ++r) {
+            for (int pr = warp; pr < K / 2; pr += NT / 32) {
+                int p, q;
+                if (pr == 0) {
+                    p = 0;
+                    q = r + 1;
+                } else {
+                    p = (r + pr) % (K - 1) + 1;
+                    q = (r - pr + K - 1) % (K - 1) + 1;
+                }
+                if (p >= k || q >= k) continue;
+                CT al = CT(0), be = CT(0), ga = CT(0);
+                for (int i = lane; i < k; i += 32) {
+                    const CT x = S.M[i * LD + p], y = S.M[i * LD + q];
+                    al += x * x;
+                    be += y * y;
+                    ga += x * y;
+                }
+                // butterfly sums: every lane holds the same totals
+                al = warp_sum(al);
+                be = warp_sum(be);
+                ga = warp_sum(ga);
+                if (fabs(ga) <= floor || fabs(ga) <= RcTol<CT>::orth * sqrt(al * be)) continue;
+                const CT zeta = (be - al) / (CT(2) * ga);
+                const CT t = (zeta >= CT(0) ? CT(1) : CT(-1)) / (fabs(zeta) + sqrt(CT(1) + zeta * zeta));
+                const CT cs = CT(1) / sqrt(CT(1) + t * t), sn = cs * t;
+                for (int i = lane; i < k; i += 32) {
+                    const CT x = S.M[i * LD + p], y = S.M[i * LD + q];
+                    S.M[i * LD + p] = cs * x - sn * y;
+                    S.M[i * LD + q] = sn * x + cs * y;
+                    const CT zx = S.Z[i * LD + p], zy = S.Z[i * LD + q];
+                    S.Z[i * LD + p] = cs * zx - sn * zy;
+                    S.Z[i * LD + q] = sn * zx + cs * zy;
+                }
+                if (lane == 0) S.rotated = 1;
+            }
+            __syncthreads();
+        }
+        const int any = S.rotated;
+        __syncthreads();
+        if (!any) break;
+    }
+}
+
+// A (len x k, column-major) <- A B_sel, B_sel = columns pos[0 .. keep) of the
+// k x k matrix B, row chunk by row chunk (each chunk is read into shared
+// memory before its rows are overwritten).
+template <class CT, int KM, int NT>
+__device__ void rc_apply(CT* A, int len, int k, int keep, const CT* B, RcSmem<CT, KM, NT>& S) {
+    constexpr int LD = KM + 1;
+    for (int i0 = 0; i0 < len; i0 += kRcRows) {
+        const int rows = min(kRcRows, len - i0);
+        for (int e = threadIdx.x; e < rows * k; e += NT) {
+            const int c = e / rows, i = e - c * rows;
+            S.Qc[i * LD + c] = A[(long long)c * len + i0 + i];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * keep; e += NT) {
+            const int r = e / rows, i = e - r * rows;
+            const int col = S.pos[r];
+            CT acc = CT(0);
+            for (int c = 0; c < k; ++c) acc += S.Qc[i * LD + c] * B[c * LD + col];
+            A[(long long)r * len + i0 + i] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA per listed ACA job (crosses of rank 2 .. KM); the rank is
+// rewritten with the truncated one.
+template <class CT, int KM, int NT>
+__global__ void __launch_bounds__(NT)
+recompress_kernel(const AcaJob* __restrict__ jobs, const int* __restrict__ list, int* rank, CT* Us, CT* Vs,
+                  double tol) {
+    constexpr int LD = KM + 1;
+    extern __shared__ __align__(16) unsigned char rc_smem[];
+    RcSmem<CT, KM, NT>& S = *reinterpret_cast<RcSmem<CT, KM, NT>*>(rc_smem);
+    const int b = list[blockIdx.x];
+    const int k = rank[b];
+    if (k < 2 || k > KM) return;
+    const AcaJob j = jobs[b];
+    CT* U = Us + j.offU;
+    CT* V = Vs + j.offV;
+    rc_qr(U, j.m, k, S.R[0], S);
+    rc_qr(V, j.n, k, S.R[1], S);
+    CT fro = CT(0);
+    for (int e = threadIdx.x; e < k * k; e += NT) {
+        const int a = e / k, c2 = e - a * k;
+        CT s = CT(0);
+        for (int c = 0; c < k; ++c) s += S.R[0][a * LD + c] * S.R[1][c2 * LD + c];
+        S.M[a * LD + c2] = s;
+        S.Z[a * LD + c2] = a == c2 ? CT(1) : CT(0);
+        fro += s * s;
+    }
+    fro = block_sum<NT>(fro, S.red);
+    rc_jacobi(k, CT(1e-3) * CT(tol) * CT(tol) * fro, S);
+    for (int c = threadIdx.x; c < k; c += NT) {
+        CT s = CT(0);
+        for (int i = 0; i < k; ++i) s += S.M[i * LD + c] * S.M[i * LD + c];
+        S.s2[c] = s;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += NT) {
+        int at = 0;
+        for (int d = 0; d < k; ++d) at += (S.s2[d] > S.s2[c]) || (S.s2[d] == S.s2[c] && d < c);
+        S.pos[at] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        CT total = CT(0);
+        for (int r = 0; r < k; ++r) total += S.s2[S.pos[r]];
+        int keep = 0;
+        if (total > CT(0)) {
+            const CT lim = CT(tol) * CT(tol) * total;
+            CT tail = CT(0);
+            keep = k;
+            for (int r = k - 1; r >= 1; --r) {
+                tail += S.s2[S.pos[r]];
+                if (tail > lim) break;
+                keep = r;
+            }
+        }
+        S.keep = keep;
+    }
+    __syncthreads();
+    const int keep = S.keep;
+    rc_apply(U, j.m, k, keep, S.M, S);
+    rc_apply(V, j.n, k, keep, S.Z, S);
+    if (threadIdx.x == 0) rank[b] = keep;
+}
+
+template <class CT, int KM, int NT>
+void launch_recompress(const std::vector<int>& list, const AcaJob* d_jobs, int* d_rank, CT* Us, CT* Vs,
+                       double tol, Scratch& ws, cudaStream_t s) {
+    if (list.empty()) return;
+    int* d_list = ws.get_n<int>(list.size());
+    h2d(d_list, list, s);
+    const size_t bytes = sizeof(RcSmem<CT, KM, NT>);
+    RAD_CUDA(cudaFuncSetAttribute(recompress_kernel<CT, KM, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)bytes));
+    recompress_kernel<CT, KM, NT><<<(unsigned)list.size(), NT, bytes, s>>>(d_jobs, d_list, d_rank, Us, Vs, tol);
+    RAD_CHECK_LAUNCH();
+}
+
 // Indices 0..key.size()-1 ordered by descending key, ties in index order
 // (two stable 16-bit counting passes; keys are clamped to 32 bits).
 static std::vector<int> order_desc(const std::vector<long long>& key) {
@@ -660,6 +903,25 @@ void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>
     RAD_CUDA(cudaMemcpyAsync(ranks.data(), d_rank, sizeof(int) * nj, cudaMemcpyDeviceToHost, s));
     RAD_CUDA(cudaMemcpyAsync(evals.data(), d_evals, sizeof(long long) * nj, cudaMemcpyDeviceToHost, s));
     RAD_CUDA(cudaStreamSynchronize(s));
+    if (p->recompress_tol > 0.0) {
+        // crosses of rank 2..64 by rank class, largest work first
+        std::vector<long long> wk(nj);
+        for (int b = 0; b < nj; ++b) wk[b] = (long long)(jobs[b].m + jobs[b].n) * ranks[b] * ranks[b];
+        std::vector<int> l16, l32, l64;
+        for (int b : order_desc(wk)) {
+            const int k = ranks[b];
+            if (k < 2 || k > kRcMax) continue;
+            (k <= 16 ? l16 : k <= 32 ? l32 : l64).push_back(b);
+        }
+        {
+            ProfScope ps_("aca_recompress", s);
+            launch_recompress<CT, 64, 256>(l64, d_jobs, d_rank, Us, Vs, p->recompress_tol, ws, s);
+            launch_recompress<CT, 32, 256>(l32, d_jobs, d_rank, Us, Vs, p->recompress_tol, ws, s);
+            launch_recompress<CT, 16, 128>(l16, d_jobs, d_rank, Us, Vs, p->recompress_tol, ws, s);
+        }
+        RAD_CUDA(cudaMemcpyAsync(ranks.data(), d_rank, sizeof(int) * nj, cudaMemcpyDeviceToHost, s));
+        RAD_CUDA(cudaStreamSynchronize(s));
+    }
 }
 
 // Row tiles: leaf clusters (or [0, n) for a dense-wrapped matrix) cut into
@@ -1183,6 +1445,8 @@ void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     RAD_REQUIRE(p->accurate_dtype == -1 || p->accurate_dtype == RAD_F32, RAD_EINVAL,
                 "accurate_dtype must be -1 or RAD_F32");
     RAD_REQUIRE(p->scratch_mib >= 0, RAD_EINVAL, "scratch_mib must be >= 0");
+    RAD_REQUIRE(p->recompress_tol >= 0.0 && p->recompress_tol < 1.0, RAD_EINVAL,
+                "recompress_tol must be in [0, 1)");
     RAD_REQUIRE(!h->from_dense, RAD_EINVAL, "a dense-wrapped handle cannot be recompressed");
     drop_product_graph(h);
     h->stream_rows = kStreamRows;
