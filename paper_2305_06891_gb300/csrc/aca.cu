@@ -578,6 +578,28 @@ compact_kernel(const AcaJob* __restrict__ jobs, const int* __restrict__ rank, co
     for (long long e = threadIdx.x; e < nv; e += 256) Vc[cv[blockIdx.x] + e] = Vs[j.offV + e];
 }
 
+// Indices 0..key.size()-1 ordered by descending key, ties in index order
+// (two stable 16-bit counting passes; keys are clamped to 32 bits).
+static std::vector<int> order_desc(const std::vector<long long>& key) {
+    const size_t m = key.size();
+    std::vector<int> a(m), b(m);
+    std::vector<uint32_t> k(m);
+    for (size_t i = 0; i < m; ++i) {
+        a[i] = (int)i;
+        k[i] = 0xffffffffu - (uint32_t)std::min<long long>(std::max<long long>(key[i], 0), 0xffffffffll);
+    }
+    std::vector<int> cnt(65537);
+    for (int pass = 0; pass < 2; ++pass) {
+        const int sh = 16 * pass;
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (size_t i = 0; i < m; ++i) ++cnt[((k[a[i]] >> sh) & 0xffff) + 1];
+        for (int d = 0; d < 65536; ++d) cnt[d + 1] += cnt[d];
+        for (size_t i = 0; i < m; ++i) b[cnt[(k[a[i]] >> sh) & 0xffff]++] = a[i];
+        a.swap(b);
+    }
+    return a;
+}
+
 // ------------------------------------------------------------ recompression
 // §4.3 postprocessing of an ACA cross into standard form, with the rank
 // truncated at a relative accuracy by the singular-value rule of §5.1:
@@ -591,7 +613,7 @@ compact_kernel(const AcaJob* __restrict__ jobs, const int* __restrict__ rank, co
 // dropped columns of M Z, converged or not.
 constexpr int kRcMax = 64;     // crosses of higher rank keep their ACA form
 constexpr int kRcRows = 64;    // row chunk of the final in-place product
-constexpr int kRcSweeps = 16;
+constexpr int kRcSweeps = 10;
 
 // shared memory of one cross of rank <= KM (leading dimension KM + 1)
 template <class CT, int KM, int NT>
@@ -665,10 +687,11 @@ __device__ void rc_qr(CT* A, int len, int k, CT* R, RcSmem<CT, KM, NT>& S) {
 // One-sided Jacobi on the k x k matrix S.M, rotations accumulated in S.Z.
 // Each sweep visits every column pair once in k - 1 rounds of disjoint pairs
 // (round-robin: player 0 fixed, players 1 .. K-1 on a circle; an odd k adds
-// an idle player); one warp per pair.  A pair is left alone when its
-// coupling is below orth of its columns' norms or below `floor` (a
-// thousandth of the truncation threshold tol^2 ||M||_F^2: it cannot move
-// the truncation).
+// an idle player); one warp per pair.  A pair (column norms^2 a, b,
+// coupling g) is left alone when g is below orth sqrt(a b), or when
+// rotating it would move a or b by less than `floor` (a thousandth of the
+// truncation threshold tol^2 ||M||_F^2, divided by k): |g| <= floor or
+// g^2 <= floor |a - b|.
 template <class CT, int KM, int NT>
 __device__ void rc_jacobi(int k, CT floor, RcSmem<CT, KM, NT>& S) {
     constexpr int LD = KM + 1;
@@ -699,7 +722,9 @@ __device__ void rc_jacobi(int k, CT floor, RcSmem<CT, KM, NT>& S) {
                 al = warp_sum(al);
                 be = warp_sum(be);
                 ga = warp_sum(ga);
-                if (fabs(ga) <= floor || fabs(ga) <= RcTol<CT>::orth * sqrt(al * be)) continue;
+                if (fabs(ga) <= floor || ga * ga <= floor * fabs(al - be) ||
+                    fabs(ga) <= RcTol<CT>::orth * sqrt(al * be))
+                    continue;
                 const CT zeta = (be - al) / (CT(2) * ga);
                 const CT t = (zeta >= CT(0) ? CT(1) : CT(-1)) / (fabs(zeta) + sqrt(CT(1) + zeta * zeta));
                 const CT cs = CT(1) / sqrt(CT(1) + t * t), sn = cs * t;
@@ -721,17 +746,18 @@ __device__ void rc_jacobi(int k, CT floor, RcSmem<CT, KM, NT>& S) {
     }
 }
 
-// A (len x k, column-major) <- A B_sel, B_sel = columns pos[0 .. keep) of the
-// k x k matrix B, row chunk by row chunk (each chunk is read into shared
-// memory before its rows are overwritten).
+// dst (len x keep, column-major) <- Q B_sel with Q = src (len x k,
+// column-major) and B_sel = columns pos[0 .. keep) of the k x k matrix B,
+// row chunk by row chunk (each chunk of Q is read into shared memory before
+// any of its rows is written, so dst may be src).
 template <class CT, int KM, int NT>
-__device__ void rc_apply(CT* A, int len, int k, int keep, const CT* B, RcSmem<CT, KM, NT>& S) {
+__device__ void rc_apply(const CT* src, CT* dst, int len, int k, int keep, const CT* B, RcSmem<CT, KM, NT>& S) {
     constexpr int LD = KM + 1;
     for (int i0 = 0; i0 < len; i0 += kRcRows) {
         const int rows = min(kRcRows, len - i0);
         for (int e = threadIdx.x; e < rows * k; e += NT) {
             const int c = e / rows, i = e - c * rows;
-            S.Qc[i * LD + c] = A[(long long)c * len + i0 + i];
+            S.Qc[i * LD + c] = src[(long long)c * len + i0 + i];
         }
         __syncthreads();
         for (int e = threadIdx.x; e < rows * keep; e += NT) {
@@ -739,15 +765,17 @@ __device__ void rc_apply(CT* A, int len, int k, int keep, const CT* B, RcSmem<CT
             const int col = S.pos[r];
             CT acc = CT(0);
             for (int c = 0; c < k; ++c) acc += S.Qc[i * LD + c] * B[c * LD + col];
-            A[(long long)r * len + i0 + i] = acc;
+            dst[(long long)r * len + i0 + i] = acc;
         }
         __syncthreads();
     }
 }
 
 // One CTA per listed ACA job (crosses of rank 2 .. KM); the rank is
-// rewritten with the truncated one.
-template <class CT, int KM, int NT>
+// rewritten with the truncated one.  RES: the cross (m + n) x k is first
+// copied into shared memory behind RcSmem and factorised there (one read
+// and one write of global memory); otherwise it is factorised in place.
+template <class CT, int KM, int NT, bool RES>
 __global__ void __launch_bounds__(NT)
 recompress_kernel(const AcaJob* __restrict__ jobs, const int* __restrict__ list, int* rank, CT* Us, CT* Vs,
                   double tol) {
@@ -760,8 +788,17 @@ recompress_kernel(const AcaJob* __restrict__ jobs, const int* __restrict__ list,
     const AcaJob j = jobs[b];
     CT* U = Us + j.offU;
     CT* V = Vs + j.offV;
-    rc_qr(U, j.m, k, S.R[0], S);
-    rc_qr(V, j.n, k, S.R[1], S);
+    CT* qU = U;
+    CT* qV = V;
+    if constexpr (RES) {
+        qU = reinterpret_cast<CT*>(rc_smem + sizeof(RcSmem<CT, KM, NT>));
+        qV = qU + (long long)j.m * k;
+        for (int e = threadIdx.x; e < j.m * k; e += NT) qU[e] = U[e];
+        for (int e = threadIdx.x; e < j.n * k; e += NT) qV[e] = V[e];
+        __syncthreads();
+    }
+    rc_qr(qU, j.m, k, S.R[0], S);
+    rc_qr(qV, j.n, k, S.R[1], S);
     CT fro = CT(0);
     for (int e = threadIdx.x; e < k * k; e += NT) {
         const int a = e / k, c2 = e - a * k;
@@ -772,7 +809,7 @@ recompress_kernel(const AcaJob* __restrict__ jobs, const int* __restrict__ list,
         fro += s * s;
     }
     fro = block_sum<NT>(fro, S.red);
-    rc_jacobi(k, CT(1e-3) * CT(tol) * CT(tol) * fro, S);
+    rc_jacobi(k, CT(1e-3) * CT(tol) * CT(tol) * fro / CT(k), S);
     for (int c = threadIdx.x; c < k; c += NT) {
         CT s = CT(0);
         for (int i = 0; i < k; ++i) s += S.M[i * LD + c] * S.M[i * LD + c];
@@ -803,44 +840,63 @@ recompress_kernel(const AcaJob* __restrict__ jobs, const int* __restrict__ list,
     }
     __syncthreads();
     const int keep = S.keep;
-    rc_apply(U, j.m, k, keep, S.M, S);
-    rc_apply(V, j.n, k, keep, S.Z, S);
+    rc_apply(qU, U, j.m, k, keep, S.M, S);
+    rc_apply(qV, V, j.n, k, keep, S.Z, S);
     if (threadIdx.x == 0) rank[b] = keep;
 }
 
-template <class CT, int KM, int NT>
-void launch_recompress(const std::vector<int>& list, const AcaJob* d_jobs, int* d_rank, CT* Us, CT* Vs,
-                       double tol, Scratch& ws, cudaStream_t s) {
+// res_elems > 0: resident variant with room for that many cross elements
+template <class CT, int KM, int NT, bool RES>
+void launch_recompress(const std::vector<int>& list, long long res_elems, const AcaJob* d_jobs, int* d_rank,
+                       CT* Us, CT* Vs, double tol, Scratch& ws, cudaStream_t s) {
     if (list.empty()) return;
     int* d_list = ws.get_n<int>(list.size());
     h2d(d_list, list, s);
-    const size_t bytes = sizeof(RcSmem<CT, KM, NT>);
-    RAD_CUDA(cudaFuncSetAttribute(recompress_kernel<CT, KM, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)bytes));
-    recompress_kernel<CT, KM, NT><<<(unsigned)list.size(), NT, bytes, s>>>(d_jobs, d_list, d_rank, Us, Vs, tol);
+    const size_t bytes = sizeof(RcSmem<CT, KM, NT>) + (RES ? (size_t)res_elems * sizeof(CT) : 0);
+    RAD_CUDA(cudaFuncSetAttribute(recompress_kernel<CT, KM, NT, RES>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    recompress_kernel<CT, KM, NT, RES><<<(unsigned)list.size(), NT, bytes, s>>>(d_jobs, d_list, d_rank, Us, Vs,
+                                                                                 tol);
     RAD_CHECK_LAUNCH();
 }
 
-// Indices 0..key.size()-1 ordered by descending key, ties in index order
-// (two stable 16-bit counting passes; keys are clamped to 32 bits).
-static std::vector<int> order_desc(const std::vector<long long>& key) {
-    const size_t m = key.size();
-    std::vector<int> a(m), b(m);
-    std::vector<uint32_t> k(m);
-    for (size_t i = 0; i < m; ++i) {
-        a[i] = (int)i;
-        k[i] = 0xffffffffu - (uint32_t)std::min<long long>(std::max<long long>(key[i], 0), 0xffffffffll);
+// Recompression of every cross of rank 2..64 (ranks on the host, updated
+// on return): by rank class (16 / 32 / 64) and by whether the cross fits
+// in shared memory (up to 16 KiB, up to 48 KiB, in place otherwise),
+// largest work first within a launch.
+template <class CT>
+void recompress_all(const std::vector<AcaJob>& jobs, std::vector<int>& ranks, const AcaJob* d_jobs, int* d_rank,
+                    CT* Us, CT* Vs, double tol, Scratch& ws, cudaStream_t s) {
+    const int nj = (int)jobs.size();
+    std::vector<long long> wk(nj);
+    for (int b = 0; b < nj; ++b) wk[b] = (long long)(jobs[b].m + jobs[b].n) * ranks[b] * ranks[b];
+    constexpr long long kTier[2] = {16 << 10, 48 << 10};
+    std::vector<int> lists[3][3];        // [rank class][tier 0, tier 1, in place]
+    long long need[3][2] = {};
+    for (int b : order_desc(wk)) {
+        const int k = ranks[b];
+        if (k < 2 || k > kRcMax) continue;
+        const int kc = k <= 16 ? 0 : k <= 32 ? 1 : 2;
+        const long long el = (long long)(jobs[b].m + jobs[b].n) * k;
+        const long long by = el * (long long)sizeof(CT);
+        const int t = by <= kTier[0] ? 0 : by <= kTier[1] ? 1 : 2;
+        lists[kc][t].push_back(b);
+        if (t < 2) need[kc][t] = std::max(need[kc][t], el);
     }
-    std::vector<int> cnt(65537);
-    for (int pass = 0; pass < 2; ++pass) {
-        const int sh = 16 * pass;
-        std::fill(cnt.begin(), cnt.end(), 0);
-        for (size_t i = 0; i < m; ++i) ++cnt[((k[a[i]] >> sh) & 0xffff) + 1];
-        for (int d = 0; d < 65536; ++d) cnt[d + 1] += cnt[d];
-        for (size_t i = 0; i < m; ++i) b[cnt[(k[a[i]] >> sh) & 0xffff]++] = a[i];
-        a.swap(b);
+    ProfScope ps_("aca_recompress", s);
+    for (int t = 2; t >= 0; --t) {
+        if (t == 2) {
+            launch_recompress<CT, 16, 256, false>(lists[0][2], 0, d_jobs, d_rank, Us, Vs, tol, ws, s);
+            launch_recompress<CT, 32, 256, false>(lists[1][2], 0, d_jobs, d_rank, Us, Vs, tol, ws, s);
+            launch_recompress<CT, 64, 256, false>(lists[2][2], 0, d_jobs, d_rank, Us, Vs, tol, ws, s);
+        } else {
+            launch_recompress<CT, 16, 128, true>(lists[0][t], need[0][t], d_jobs, d_rank, Us, Vs, tol, ws, s);
+            launch_recompress<CT, 32, 128, true>(lists[1][t], need[1][t], d_jobs, d_rank, Us, Vs, tol, ws, s);
+            launch_recompress<CT, 64, 128, true>(lists[2][t], need[2][t], d_jobs, d_rank, Us, Vs, tol, ws, s);
+        }
     }
-    return a;
+    RAD_CUDA(cudaMemcpyAsync(ranks.data(), d_rank, sizeof(int) * nj, cudaMemcpyDeviceToHost, s));
+    RAD_CUDA(cudaStreamSynchronize(s));
 }
 
 template <class CT>
@@ -903,25 +959,7 @@ void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>
     RAD_CUDA(cudaMemcpyAsync(ranks.data(), d_rank, sizeof(int) * nj, cudaMemcpyDeviceToHost, s));
     RAD_CUDA(cudaMemcpyAsync(evals.data(), d_evals, sizeof(long long) * nj, cudaMemcpyDeviceToHost, s));
     RAD_CUDA(cudaStreamSynchronize(s));
-    if (p->recompress_tol > 0.0) {
-        // crosses of rank 2..64 by rank class, largest work first
-        std::vector<long long> wk(nj);
-        for (int b = 0; b < nj; ++b) wk[b] = (long long)(jobs[b].m + jobs[b].n) * ranks[b] * ranks[b];
-        std::vector<int> l16, l32, l64;
-        for (int b : order_desc(wk)) {
-            const int k = ranks[b];
-            if (k < 2 || k > kRcMax) continue;
-            (k <= 16 ? l16 : k <= 32 ? l32 : l64).push_back(b);
-        }
-        {
-            ProfScope ps_("aca_recompress", s);
-            launch_recompress<CT, 64, 256>(l64, d_jobs, d_rank, Us, Vs, p->recompress_tol, ws, s);
-            launch_recompress<CT, 32, 256>(l32, d_jobs, d_rank, Us, Vs, p->recompress_tol, ws, s);
-            launch_recompress<CT, 16, 128>(l16, d_jobs, d_rank, Us, Vs, p->recompress_tol, ws, s);
-        }
-        RAD_CUDA(cudaMemcpyAsync(ranks.data(), d_rank, sizeof(int) * nj, cudaMemcpyDeviceToHost, s));
-        RAD_CUDA(cudaStreamSynchronize(s));
-    }
+    if (p->recompress_tol > 0.0) recompress_all<CT>(jobs, ranks, d_jobs, d_rank, Us, Vs, p->recompress_tol, ws, s);
 }
 
 // Row tiles: leaf clusters (or [0, n) for a dense-wrapped matrix) cut into

@@ -72,7 +72,7 @@ def test_recompression_matches_oracle_truncation(cyl, factor, aca_tol, rc_tol, n
         ko = Uo.shape[1]
         tail, total = _oracle_tail(U0, V0)
         lim = rc_tol * rc_tol * total
-        band = 4 * noise * total + 1e-3 * lim
+        band = 0.05 * lim + 4 * noise * rc_tol * total
         if k1 != ko:
             assert abs(k1 - ko) == 1, (key, k0, k1, ko)
             assert abs(tail[min(k1, ko)] - lim) <= band, (key, k1, ko, tail[min(k1, ko)] / total, rc_tol ** 2)
