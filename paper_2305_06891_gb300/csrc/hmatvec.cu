@@ -116,6 +116,45 @@ __device__ __forceinline__ void stream_panel4(const S* __restrict__ P, long long
     }
 }
 
+// acc[k][0..3] += sum over panel columns c = g, g + G, ... of the 4 rows at
+// P of column c times V[idx[c]][k] (V[base + c][k] when idx is null), for
+// the NCOL columns k of V's rows; four panel columns in flight per step.
+template <class S, class AT, int NCOL>
+__device__ __forceinline__ void stream_cols(const S* __restrict__ P, long long ld, int kcols, int g, int G,
+                                            const int* __restrict__ idx, const AT* __restrict__ V, int ldv,
+                                            AT (&acc)[NCOL][4], int base = 0) {
+    constexpr int U = 4;
+    int c = g;
+    for (; c + (U - 1) * G < kcols; c += U * G) {
+        AT a[U][4];
+        const AT* vr[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            Vec4<S, AT>::load(P + (long long)(c + u * G) * ld, a[u]);
+            vr[u] = V + (long long)(idx ? idx[c + u * G] : base + c + u * G) * ldv;
+        }
+#pragma unroll
+        for (int k = 0; k < NCOL; ++k) {
+            AT xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[u] = vr[u][k];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[k][r] += (a[0][r] * xv[0] + a[1][r] * xv[1]) + (a[2][r] * xv[2] + a[3][r] * xv[3]);
+        }
+    }
+    for (; c < kcols; c += G) {
+        AT a[4];
+        Vec4<S, AT>::load(P + (long long)c * ld, a);
+        const AT* vr = V + (long long)(idx ? idx[c] : base + c) * ldv;
+#pragma unroll
+        for (int k = 0; k < NCOL; ++k) {
+            const AT xv = vr[k];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[k][r] += a[r] * xv;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- 2-4 RHS
 // Streaming kernels for a few right-hand sides: one pass over every panel,
 // thread (q, g) owns rows 4q .. 4q+3 for all NCOL columns.
@@ -130,20 +169,9 @@ __device__ __forceinline__ void far_vt_stream_item(int it_, OpView op, const AT*
     const int q = threadIdx.x % quads, jg = threadIdx.x / quads;
     const long long ld = gr.ld;
     AT acc[NCOL][4] = {};
-    if (jg < G) {
-        const FS* P = static_cast<const FS*>(op.far_pool) + gr.voff + w.r0 + 4 * q;
-        for (int j = jg; j < gr.n; j += G) {
-            AT v[4];
-            Vec4<FS, AT>::load(P + j * ld, v);
-            const AT* xr = X + (long long)(gr.c0 + j) * ldx;
-#pragma unroll
-            for (int c = 0; c < NCOL; ++c) {
-                const AT xc = xr[c];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) acc[c][r] += v[r] * xc;
-            }
-        }
-    }
+    if (jg < G)
+        stream_cols<FS, AT, NCOL>(static_cast<const FS*>(op.far_pool) + gr.voff + w.r0 + 4 * q, ld, gr.n, jg, G,
+                                  nullptr, X, ldx, acc, gr.c0);
 #pragma unroll
     for (int c = 0; c < NCOL; ++c)
 #pragma unroll
@@ -260,23 +288,6 @@ __global__ void __launch_bounds__(256) single_phase_b(OpView op, const AT* __res
     }
 }
 
-
-template <class S, class AT, int NCOL>
-__device__ __forceinline__ void stream_cols(const S* __restrict__ P, long long ld, int kcols, int g, int G,
-                                            const int* __restrict__ idx, const AT* __restrict__ V, int ldv,
-                                            AT (&acc)[NCOL][4]) {
-    for (int c = g; c < kcols; c += G) {
-        AT a[4];
-        Vec4<S, AT>::load(P + c * ld, a);
-        const AT* vr = V + (long long)idx[c] * ldv;
-#pragma unroll
-        for (int k = 0; k < NCOL; ++k) {
-            const AT xv = vr[k];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) acc[k][r] += a[r] * xv;
-        }
-    }
-}
 
 template <class NS, class FS, class AT, int NCOL>
 __device__ __forceinline__ void
