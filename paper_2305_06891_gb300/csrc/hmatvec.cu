@@ -361,6 +361,45 @@ __global__ void to_df_kernel(const double* __restrict__ X, int ldx, int n, int n
     out[e] = DF{h, __double2float_rn(x - (double)h)};
 }
 
+// Double-float counterpart of stream_cols (idx null: rows base + c): the
+// loads of four panel columns are issued together, the double-float updates
+// then run in column order (the same arithmetic as one column at a time).
+template <int NCOL>
+__device__ __forceinline__ void stream_cols_df(const float* __restrict__ P, long long ld, int kcols, int g, int G,
+                                               const int* __restrict__ idx, const DF* __restrict__ V,
+                                               DF (&acc)[NCOL][4], int base = 0) {
+    constexpr int U = 4;
+    int c = g;
+    for (; c + (U - 1) * G < kcols; c += U * G) {
+        float a[U][4];
+        const DF* vr[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            Vec4<float, float>::load(P + (long long)(c + u * G) * ld, a[u]);
+            vr[u] = V + (long long)(idx ? idx[c + u * G] : base + c + u * G) * NCOL;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int k = 0; k < NCOL; ++k) {
+                const DF xv = vr[u][k];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) df_fma(acc[k][r], a[u][r], xv);
+            }
+    }
+    for (; c < kcols; c += G) {
+        float a[4];
+        Vec4<float, float>::load(P + (long long)c * ld, a);
+        const DF* vr = V + (long long)(idx ? idx[c] : base + c) * NCOL;
+#pragma unroll
+        for (int k = 0; k < NCOL; ++k) {
+            const DF xv = vr[k];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) df_fma(acc[k][r], a[r], xv);
+        }
+    }
+}
+
 template <int NCOL>
 __global__ void __launch_bounds__(256) far_vt_df(OpView op, const DF* __restrict__ X, DF* __restrict__ T) {
     __shared__ DF part[NCOL][1024];
@@ -375,20 +414,9 @@ __global__ void __launch_bounds__(256) far_vt_df(OpView op, const DF* __restrict
     for (int c = 0; c < NCOL; ++c)
 #pragma unroll
         for (int r = 0; r < 4; ++r) acc[c][r] = DF{0.0f, 0.0f};
-    if (jg < G) {
-        const float* P = static_cast<const float*>(op.far_pool) + gr.voff + w.r0 + 4 * q;
-        for (int j = jg; j < gr.n; j += G) {
-            float v[4];
-            Vec4<float, float>::load(P + j * ld, v);
-            const DF* xr = X + (long long)(gr.c0 + j) * NCOL;
-#pragma unroll
-            for (int c = 0; c < NCOL; ++c) {
-                const DF xc = xr[c];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) df_fma(acc[c][r], v[r], xc);
-            }
-        }
-    }
+    if (jg < G)
+        stream_cols_df<NCOL>(static_cast<const float*>(op.far_pool) + gr.voff + w.r0 + 4 * q, ld, gr.n, jg, G,
+                             nullptr, X, acc, gr.c0);
 #pragma unroll
     for (int c = 0; c < NCOL; ++c)
 #pragma unroll
@@ -405,23 +433,6 @@ __global__ void __launch_bounds__(256) far_vt_df(OpView op, const DF* __restrict
             }
             const float hi = __double2float_rn(sum);
             T[(long long)(gr.toff + w.r0 + rr) * NCOL + c] = DF{hi, __double2float_rn(sum - (double)hi)};
-        }
-    }
-}
-
-template <int NCOL>
-__device__ __forceinline__ void stream_cols_df(const float* __restrict__ P, long long ld, int kcols, int g, int G,
-                                               const int* __restrict__ idx, const DF* __restrict__ V,
-                                               DF (&acc)[NCOL][4]) {
-    for (int c = g; c < kcols; c += G) {
-        float a[4];
-        Vec4<float, float>::load(P + c * ld, a);
-        const DF* vr = V + (long long)idx[c] * NCOL;
-#pragma unroll
-        for (int k = 0; k < NCOL; ++k) {
-            const DF xv = vr[k];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) df_fma(acc[k][r], a[r], xv);
         }
     }
 }

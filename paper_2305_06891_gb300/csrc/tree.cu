@@ -276,83 +276,61 @@ __device__ __forceinline__ bool admissible(const NodeBox& s, const NodeBox& t, d
     return fmin(ds, dt) <= __dmul_rn(__dmul_rn(eta, eta), dist2);
 }
 
-__global__ void __launch_bounds__(kTreeNT)
-block_tree_kernel(const NodeShape* __restrict__ shapes, const NodeBox* __restrict__ boxes, double eta,
-                  const int* __restrict__ roots, const long long* __restrict__ slice_off,
-                  const int* __restrict__ slice_cap, int2* candA_all, int2* candB_all, int2* __restrict__ far_all,
-                  int2* __restrict__ near_all, int* __restrict__ counters_all) {
-    // one CTA per tree of the forest (one cavity), each with its own slice
-    // of the candidate and output buffers
-    constexpr int NT = kTreeNT;
-    constexpr unsigned long long M21 = (1ull << 21) - 1ull;
-    __shared__ unsigned long long scan_sm[NT / 32 + 1];
-    const long long off = slice_off[blockIdx.x];
-    const int cap_cand = slice_cap[blockIdx.x], cap_far = cap_cand, cap_near = cap_cand;
-    int2* cur = candA_all + off;
-    int2* nxt = candB_all + off;
-    int2* far_out = far_all + off;
-    int2* near_out = near_all + off;
-    int* counters = counters_all + 4 * blockIdx.x;
-    const int root = roots[blockIdx.x];
-    if (threadIdx.x == 0) cur[0] = make_int2(root, root);
-    __syncthreads();
-    int ncur = 1, nfar = 0, nnear = 0, overflow = 0, max_cand = 1;
-    for (int level = 0; level < 64 && ncur > 0; ++level) {
-        int nnext = 0;
-        for (int s = 0; s < ncur; s += NT) {
-            const int t = s + (int)threadIdx.x;
-            const bool valid = t < ncur;
-            int cls = -1;
-            int2 pr = make_int2(0, 0);
-            if (valid) {
-                pr = cur[t];
-                const NodeShape ns = shapes[pr.x], nt = shapes[pr.y];
-                if (admissible(boxes[pr.x], boxes[pr.y], eta)) cls = 1;
-                else if (ns.leaf || nt.leaf) cls = 2;
-                else cls = 0;
-            }
-            const unsigned long long packed =
-                !valid ? 0ull : cls == 1 ? 1ull : cls == 2 ? (1ull << 21) : (1ull << 42);
-            unsigned long long tot;
-            const unsigned long long ex = block_excl_scan<NT, unsigned long long>(packed, scan_sm, tot);
-            if (valid) {
-                if (cls == 1) {
-                    const int pos = nfar + (int)(ex & M21);
-                    if (pos < cap_far) far_out[pos] = pr;
-                } else if (cls == 2) {
-                    const int pos = nnear + (int)((ex >> 21) & M21);
-                    if (pos < cap_near) near_out[pos] = pr;
-                } else {
-                    const NodeShape ns = shapes[pr.x], nt = shapes[pr.y];
-                    const int base = nnext + 4 * (int)(ex >> 42);
-                    const int cs[2] = {ns.child0, ns.child1};
-                    const int ct[2] = {nt.child0, nt.child1};
+// One level of Algorithm 2 for every tree of the forest at once: each
+// candidate pair (sigma, tau) becomes a far block (Eq. 28 holds), a near
+// block (a leaf on either side) or its four child pairs for the next level.
+// Outputs are appended with warp-aggregated atomics, so their order is not
+// fixed; the host orders the blocks by (row start, column start) afterwards.
+// lv[0] = candidates of this level (read), lv[1] = next level's count,
+// tot[0 / 1] = far / near blocks so far.  Writes past a capacity are
+// dropped; the counts keep growing so the host can retry with room.
+constexpr int kLevelNT = 256;
+__global__ void __launch_bounds__(kLevelNT)
+block_level_kernel(const NodeShape* __restrict__ shapes, const NodeBox* __restrict__ boxes, double eta,
+                   const int2* __restrict__ cur, int2* __restrict__ nxt, int cap_cand, int2* __restrict__ far_out,
+                   int2* __restrict__ near_out, int cap_out, int* lv, int* tot) {
+    const int ncur = min(lv[0], cap_cand);
+    const int lane = threadIdx.x & 31;
+    for (int base = blockIdx.x * kLevelNT; base < ncur; base += gridDim.x * kLevelNT) {
+        const int t = base + (int)threadIdx.x;
+        int cls = -1;
+        int2 pr = make_int2(0, 0);
+        NodeShape ns{}, nt{};
+        if (t < ncur) {
+            pr = cur[t];
+            ns = shapes[pr.x];
+            nt = shapes[pr.y];
+            if (admissible(boxes[pr.x], boxes[pr.y], eta)) cls = 1;
+            else if (ns.leaf || nt.leaf) cls = 2;
+            else cls = 0;
+        }
+        const unsigned mf = __ballot_sync(0xffffffffu, cls == 1);
+        const unsigned mn = __ballot_sync(0xffffffffu, cls == 2);
+        const unsigned mc = __ballot_sync(0xffffffffu, cls == 0);
+        const unsigned below = (1u << lane) - 1u;
+        int bf = 0, bn = 0, bc = 0;
+        if (lane == 0) {
+            if (mf) bf = atomicAdd(&tot[0], __popc(mf));
+            if (mn) bn = atomicAdd(&tot[1], __popc(mn));
+            if (mc) bc = atomicAdd(&lv[1], 4 * __popc(mc));
+        }
+        bf = __shfl_sync(0xffffffffu, bf, 0);
+        bn = __shfl_sync(0xffffffffu, bn, 0);
+        bc = __shfl_sync(0xffffffffu, bc, 0);
+        if (cls == 1) {
+            const int pos = bf + __popc(mf & below);
+            if (pos < cap_out) far_out[pos] = pr;
+        } else if (cls == 2) {
+            const int pos = bn + __popc(mn & below);
+            if (pos < cap_out) near_out[pos] = pr;
+        } else if (cls == 0) {
+            const int pos = bc + 4 * __popc(mc & below);
+            const int cs[2] = {ns.child0, ns.child1};
+            const int ct[2] = {nt.child0, nt.child1};
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (base + q < cap_cand) nxt[base + q] = make_int2(cs[q >> 1], ct[q & 1]);
-                }
-            }
-            nfar += (int)(tot & M21);
-            nnear += (int)((tot >> 21) & M21);
-            nnext += 4 * (int)(tot >> 42);
+            for (int q = 0; q < 4; ++q)
+                if (pos + q < cap_cand) nxt[pos + q] = make_int2(cs[q >> 1], ct[q & 1]);
         }
-        __syncthreads();
-        if (nnext > cap_cand) {
-            overflow = 1;
-            max_cand = max(max_cand, nnext);
-            break;
-        }
-        max_cand = max(max_cand, nnext);
-        int2* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-        ncur = nnext;
-    }
-    if (threadIdx.x == 0) {
-        counters[0] = nfar;
-        counters[1] = nnear;
-        counters[2] = overflow || nfar > cap_far || nnear > cap_near || ncur > 0 && overflow;
-        counters[3] = max_cand;
     }
 }
 
@@ -457,63 +435,58 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     { ProfScope ps_("geometry", s); geo32_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, h->geo.as<double>(), h->geo32.as<float>()); }
     RAD_CHECK_LAUNCH();
 
-    // block tree: one CTA per tree, retry with larger buffers on overflow
+    // block tree: one launch per level over the candidates of every tree,
+    // retry with larger buffers on overflow
     HostScope hs_blocks("host_block_tree_wait");
-    std::vector<int> caps(nseg);
+    int64_t cap64 = 0;
     for (int c = 0; c < nseg; ++c) {
         const int64_t nc_ = h->seg[c + 1] - h->seg[c];
-        caps[c] = (int)std::min<int64_t>(1 << 28, 160ll * (nc_ / std::max(1, leaf) + 1) + 4096);
+        cap64 += 160ll * (nc_ / std::max(1, leaf) + 1) + 4096;
     }
+    int cap = (int)std::min<int64_t>(1 << 28, cap64);
     std::vector<int2> far_pairs, near_pairs;
-    int* d_roots = ws.get_n<int>(nseg);
-    h2d(d_roots, roots, s);
+    std::vector<int2> root_pairs(nseg);
+    for (int c = 0; c < nseg; ++c) root_pairs[c] = make_int2(roots[c], roots[c]);
+    const int levels = depth + 1;
     bool done = false;
     for (int attempt = 0; attempt < 6 && !done; ++attempt) {
-        std::vector<long long> off(nseg + 1, 0);
-        for (int c = 0; c < nseg; ++c) off[c + 1] = off[c] + caps[c];
         Scratch bw(s);
-        int2* candA = bw.get_n<int2>(off[nseg]);
-        int2* candB = bw.get_n<int2>(off[nseg]);
-        int2* far_out = bw.get_n<int2>(off[nseg]);
-        int2* near_out = bw.get_n<int2>(off[nseg]);
-        int* counters = bw.get_n<int>(4 * (size_t)nseg);
-        long long* d_off = bw.get_n<long long>(nseg);
-        int* d_caps = bw.get_n<int>(nseg);
-        h2d(d_off, std::vector<long long>(off.begin(), off.end() - 1), s);
-        h2d(d_caps, caps, s);
-        { ProfScope ps_("block_tree", s); block_tree_kernel<<<nseg, kTreeNT, 0, s>>>(d_shapes, d_boxes, h->eta, d_roots, d_off, d_caps,
-                                                candA, candB, far_out, near_out, counters); }
-        RAD_CHECK_LAUNCH();
-        std::vector<int> hc(4 * (size_t)nseg);
-        RAD_CUDA(cudaMemcpyAsync(hc.data(), counters, sizeof(int) * hc.size(), cudaMemcpyDeviceToHost, s));
+        int2* candA = bw.get_n<int2>(cap);
+        int2* candB = bw.get_n<int2>(cap);
+        int2* far_out = bw.get_n<int2>(cap);
+        int2* near_out = bw.get_n<int2>(cap);
+        int* lv = bw.get_n<int>(levels + 2);      // candidates per level
+        int* tot = bw.get_n<int>(2);
+        RAD_CUDA(cudaMemsetAsync(lv, 0, sizeof(int) * (levels + 2), s));
+        RAD_CUDA(cudaMemsetAsync(tot, 0, sizeof(int) * 2, s));
+        h2d(candA, root_pairs, s);
+        const int one[1] = {nseg};
+        RAD_CUDA(cudaMemcpyAsync(lv, one, sizeof(int), cudaMemcpyHostToDevice, s));
+        {
+            ProfScope ps_("block_tree", s);
+            for (int l = 0; l < levels; ++l) {
+                block_level_kernel<<<152 * 8, kLevelNT, 0, s>>>(d_shapes, d_boxes, h->eta, (l & 1) ? candB : candA,
+                                                                (l & 1) ? candA : candB, cap, far_out, near_out, cap,
+                                                                lv + l, tot);
+                RAD_CHECK_LAUNCH();
+            }
+        }
+        std::vector<int> hl(levels + 2), ht(2);
+        RAD_CUDA(cudaMemcpyAsync(hl.data(), lv, sizeof(int) * hl.size(), cudaMemcpyDeviceToHost, s));
+        RAD_CUDA(cudaMemcpyAsync(ht.data(), tot, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
         RAD_CUDA(cudaStreamSynchronize(s));
-        bool over = false;
-        for (int c = 0; c < nseg; ++c) {
-            if (!hc[4 * c + 2]) continue;
-            over = true;
-            const int64_t need = std::max<int64_t>({(int64_t)hc[4 * c], (int64_t)hc[4 * c + 1], (int64_t)hc[4 * c + 3]});
-            RAD_REQUIRE(caps[c] < (1 << 28), RAD_ELIMIT, "block tree too large");
-            caps[c] = (int)std::min<int64_t>(1 << 28, std::max<int64_t>(4ll * caps[c], need + 1024));
+        int64_t need = std::max<int64_t>(ht[0], ht[1]);
+        for (int l = 0; l <= levels; ++l) need = std::max<int64_t>(need, hl[l]);
+        RAD_REQUIRE(hl[levels] == 0, RAD_ECUDA, "internal error: block tree deeper than the cluster tree");
+        if (need > cap) {
+            RAD_REQUIRE(cap < (1 << 28), RAD_ELIMIT, "block tree too large");
+            cap = (int)std::min<int64_t>(1 << 28, std::max<int64_t>(4ll * cap, need + 1024));
+            continue;
         }
-        if (over) continue;
-        long long nf = 0, nn = 0;
-        for (int c = 0; c < nseg; ++c) {
-            nf += hc[4 * c];
-            nn += hc[4 * c + 1];
-        }
-        far_pairs.resize(nf);
-        near_pairs.resize(nn);
-        nf = nn = 0;
-        for (int c = 0; c < nseg; ++c) {
-            if (hc[4 * c])
-                RAD_CUDA(cudaMemcpyAsync(far_pairs.data() + nf, far_out + off[c], sizeof(int2) * hc[4 * c],
-                                         cudaMemcpyDeviceToHost, s));
-            if (hc[4 * c + 1])
-                RAD_CUDA(cudaMemcpyAsync(near_pairs.data() + nn, near_out + off[c], sizeof(int2) * hc[4 * c + 1],
-                                         cudaMemcpyDeviceToHost, s));
-            nf += hc[4 * c];
-            nn += hc[4 * c + 1];
-        }
+        far_pairs.resize(ht[0]);
+        near_pairs.resize(ht[1]);
+        if (ht[0]) RAD_CUDA(cudaMemcpyAsync(far_pairs.data(), far_out, sizeof(int2) * ht[0], cudaMemcpyDeviceToHost, s));
+        if (ht[1]) RAD_CUDA(cudaMemcpyAsync(near_pairs.data(), near_out, sizeof(int2) * ht[1], cudaMemcpyDeviceToHost, s));
         RAD_CUDA(cudaStreamSynchronize(s));
         done = true;
     }
