@@ -1162,18 +1162,46 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     std::vector<int> adm;
     for (int b = 0; b < (int)h->blocks.size(); ++b)
         if (h->blocks[b].admissible) adm.push_back(b);
-    std::vector<AcaJob> jobs;
-    jobs.reserve(adm.size());
+    // jobs with their scratch offsets (running sums over the admissible
+    // blocks in order), in parallel parts for large lists
+    std::vector<AcaJob> jobs(adm.size());
     long long ou = 0, ov = 0, oused = 0;
-    for (int b : adm) {
-        const BlockH& bk = h->blocks[b];
-        const int m = bk.r1 - bk.r0, n = bk.c1 - bk.c0;
-        const long long brk = (long long)m * n / (m + n);
-        const int kmax = (int)std::min<long long>({(long long)p->max_rank, brk, (long long)kMaxRank});
-        jobs.push_back(AcaJob{bk.r0, bk.c0, m, n, kmax, 0, ou, ov, oused});
-        ou += round_up((long long)m * kmax, 8);
-        ov += round_up((long long)n * kmax, 8);
-        oused += round_up(m, 16);
+    {
+        const int64_t na = (int64_t)adm.size();
+        const int P = na >= 1000000 ? 16 : 1;
+        std::vector<long long> su(P + 1, 0), sv(P + 1, 0), ss(P + 1, 0);
+        auto kmax_of = [&](int m, int n) {
+            const long long brk = (long long)m * n / (m + n);
+            return (int)std::min<long long>({(long long)p->max_rank, brk, (long long)kMaxRank});
+        };
+        parallel_parts(P, [&](int q) {
+            for (int64_t a = na * q / P, e = na * (q + 1) / P; a < e; ++a) {
+                const BlockH& bk = h->blocks[adm[a]];
+                const int m = bk.r1 - bk.r0, n = bk.c1 - bk.c0, kmax = kmax_of(m, n);
+                su[q + 1] += round_up((long long)m * kmax, 8);
+                sv[q + 1] += round_up((long long)n * kmax, 8);
+                ss[q + 1] += round_up(m, 16);
+            }
+        });
+        for (int q = 0; q < P; ++q) {
+            su[q + 1] += su[q];
+            sv[q + 1] += sv[q];
+            ss[q + 1] += ss[q];
+        }
+        parallel_parts(P, [&](int q) {
+            long long u = su[q], v = sv[q], us = ss[q];
+            for (int64_t a = na * q / P, e = na * (q + 1) / P; a < e; ++a) {
+                const BlockH& bk = h->blocks[adm[a]];
+                const int m = bk.r1 - bk.r0, n = bk.c1 - bk.c0, kmax = kmax_of(m, n);
+                jobs[a] = AcaJob{bk.r0, bk.c0, m, n, kmax, 0, u, v, us};
+                u += round_up((long long)m * kmax, 8);
+                v += round_up((long long)n * kmax, 8);
+                us += round_up(m, 16);
+            }
+        });
+        ou = su[P];
+        ov = sv[P];
+        oused = ss[P];
     }
     hs_jobs.reset();
     // ACA scratch holds kmax columns per block.  When that exceeds the
@@ -1315,10 +1343,11 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     }
     h->sum_rank = toff;
     // Per-tile panel columns, gather runs and fill work.  Large plans are
-    // split into kPlanParts row ranges cut at tile starts and built by
-    // threads (each range owns its tiles); blocks whose rows cross a cut go
-    // first, sequentially.  The layout is deterministic for a given block
-    // list (the part count does not depend on the machine).
+    // split into row ranges (8 from 20,000 blocks, 16 from a million) cut at
+    // tile starts and built by threads (each range owns its tiles); blocks
+    // whose rows cross a cut go first, sequentially.  The layout is
+    // deterministic for a given block list (the part count depends only on
+    // the block count, not on the machine).
     struct PlanPart {
         std::vector<DenseWork> dwork;
         std::vector<UWork> uwork;
@@ -1356,9 +1385,8 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
             o.vwork.push_back(VWork{bk.group, bk.grow, n, k, job_chunk[jb], 0, src_v[jb]});
         }
     };
-    constexpr int kPlanParts = 8;
     const int nb = (int)h->blocks.size();
-    const int parts = nb >= 20000 ? kPlanParts : 1;
+    const int parts = nb >= 1000000 ? 16 : nb >= 20000 ? 8 : 1;
     std::vector<int> cut(parts + 1, 0);   // row cuts at tile starts
     cut[parts] = (int)h->n;
     for (int q = 1; q < parts; ++q) {
@@ -1374,24 +1402,10 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
         if (bk.r1 > cut[q + 1]) plan_block(b, pp[0]);
         else part_blocks[q].push_back(b);
     }
-    std::vector<std::exception_ptr> part_err(parts);
-    auto run_part = [&](int q) {
-        try {
-            for (int b : part_blocks[q]) plan_block(b, pp[q + 1]);
-        } catch (...) {
-            part_err[q] = std::current_exception();
-        }
-    };
-    if (parts == 1) {
-        run_part(0);
-    } else {
-        std::vector<std::thread> th;
-        for (int q = 1; q < parts; ++q) th.emplace_back(run_part, q);
-        run_part(0);
-        for (auto& x : th) x.join();
-    }
-    for (auto& e : part_err)
-        if (e) std::rethrow_exception(e);
+    parallel_parts(parts, [&](int q) {
+        for (int b : part_blocks[q]) plan_block(b, pp[q + 1]);
+    });
+    // concatenation of the parts' lists in part order (copies in parallel)
     std::vector<DenseWork> dwork;
     std::vector<UWork> uwork;
     std::vector<VWork> vwork;
@@ -1399,25 +1413,38 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     int64_t near_e = 0, far_u = 0, far_v = 0;
     int maxk = 0;
     {
-        size_t nd = 0, nu = 0, nv = 0, nn = 0, nf = 0, pn = 0, pf = 0;
-        for (auto& o : pp) {
-            nd += o.dwork.size(); nu += o.uwork.size(); nv += o.vwork.size(); nn += o.near_runs.size();
-            nf += o.far_runs.size(); pn += o.near_pieces.size(); pf += o.far_pieces.size();
-        }
-        dwork.reserve(nd); uwork.reserve(nu); vwork.reserve(nv); near_runs.reserve(nn); far_runs.reserve(nf);
-        h->near_pieces.reserve(pn);
-        h->far_pieces.reserve(pf);
-        for (auto& o : pp) {
-            dwork.insert(dwork.end(), o.dwork.begin(), o.dwork.end());
-            uwork.insert(uwork.end(), o.uwork.begin(), o.uwork.end());
-            vwork.insert(vwork.end(), o.vwork.begin(), o.vwork.end());
-            near_runs.insert(near_runs.end(), o.near_runs.begin(), o.near_runs.end());
-            far_runs.insert(far_runs.end(), o.far_runs.begin(), o.far_runs.end());
-            h->near_pieces.insert(h->near_pieces.end(), o.near_pieces.begin(), o.near_pieces.end());
-            h->far_pieces.insert(h->far_pieces.end(), o.far_pieces.begin(), o.far_pieces.end());
+        const int np = (int)pp.size();
+        std::vector<size_t> od(np + 1, 0), ou_(np + 1, 0), ov_(np + 1, 0), onr(np + 1, 0), ofr(np + 1, 0),
+            opn(np + 1, 0), opf(np + 1, 0);
+        for (int q = 0; q < np; ++q) {
+            const PlanPart& o = pp[q];
+            od[q + 1] = od[q] + o.dwork.size();
+            ou_[q + 1] = ou_[q] + o.uwork.size();
+            ov_[q + 1] = ov_[q] + o.vwork.size();
+            onr[q + 1] = onr[q] + o.near_runs.size();
+            ofr[q + 1] = ofr[q] + o.far_runs.size();
+            opn[q + 1] = opn[q] + o.near_pieces.size();
+            opf[q + 1] = opf[q] + o.far_pieces.size();
             near_e += o.near_e; far_u += o.far_u; far_v += o.far_v;
             maxk = std::max(maxk, o.maxk);
         }
+        dwork.resize(od[np]); uwork.resize(ou_[np]); vwork.resize(ov_[np]);
+        near_runs.resize(onr[np]); far_runs.resize(ofr[np]);
+        h->near_pieces.resize(opn[np]);
+        h->far_pieces.resize(opf[np]);
+        const bool par = nb >= 1000000;
+        parallel_parts(par ? np : 1, [&](int q0) {
+            for (int q = (par ? q0 : 0); q < (par ? q0 + 1 : np); ++q) {
+                const PlanPart& o = pp[q];
+                std::copy(o.dwork.begin(), o.dwork.end(), dwork.begin() + od[q]);
+                std::copy(o.uwork.begin(), o.uwork.end(), uwork.begin() + ou_[q]);
+                std::copy(o.vwork.begin(), o.vwork.end(), vwork.begin() + ov_[q]);
+                std::copy(o.near_runs.begin(), o.near_runs.end(), near_runs.begin() + onr[q]);
+                std::copy(o.far_runs.begin(), o.far_runs.end(), far_runs.begin() + ofr[q]);
+                std::copy(o.near_pieces.begin(), o.near_pieces.end(), h->near_pieces.begin() + opn[q]);
+                std::copy(o.far_pieces.begin(), o.far_pieces.end(), h->far_pieces.begin() + opf[q]);
+            }
+        });
     }
     long long noff = 0, foff = 0;
     for (auto& t : tiles) {

@@ -8,9 +8,11 @@
 
 #include <cstdint>
 #include <cstring>
+#include <exception>
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "rad.h"
@@ -137,6 +139,31 @@ void h2d(T* dst, const std::vector<T>& v, cudaStream_t s) {
 }
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// Runs f(q) for q = 0 .. parts-1, parts > 1 on host threads (q = 0 on the
+// calling thread); the first exception thrown by any part is rethrown.
+template <class F>
+void parallel_parts(int parts, F&& f) {
+    if (parts <= 1) {
+        f(0);
+        return;
+    }
+    std::vector<std::exception_ptr> err(parts);
+    auto run = [&](int q) {
+        try {
+            f(q);
+        } catch (...) {
+            err[q] = std::current_exception();
+        }
+    };
+    std::vector<std::thread> th;
+    th.reserve(parts - 1);
+    for (int q = 1; q < parts; ++q) th.emplace_back(run, q);
+    run(0);
+    for (auto& t : th) t.join();
+    for (auto& e : err)
+        if (e) std::rethrow_exception(e);
+}
 inline int dtype_size(int dt) { return dt == RAD_F64 ? 8 : dt == RAD_F32 ? 4 : 2; }
 
 // ------------------------------------------------------------ data layout

@@ -19,6 +19,7 @@
 // deterministic compaction.
 
 #include <algorithm>
+#include <climits>
 #include <cfloat>
 
 #include "rad_device.cuh"
@@ -503,27 +504,93 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     RAD_REQUIRE(herr == 0, RAD_ECUDA, "internal error in the cluster-tree partition");
 
     HostScope hs_sort("host_block_list");
+    // Blocks ordered by (row start, column start), which identifies a block
+    // uniquely.  Lists of a million blocks or more: the pairs are bucketed by
+    // row range (counts per input chunk and range, then a scatter) and each
+    // range is ordered by row start (counting) and, within a row start, by
+    // column start, on kListParts host threads; the order does not depend on
+    // the part count.
     std::vector<BlockH>& blocks = h->blocks;
-    blocks.clear();
-    blocks.reserve(far_pairs.size() + near_pairs.size());
-    auto add = [&](int2 pr, int adm) {
-        const NodeShape& a = nodes[pr.x];
-        const NodeShape& b = nodes[pr.y];
-        blocks.push_back(BlockH{pr.x, pr.y, a.begin, a.end, b.begin, b.end, adm, adm ? 0 : -1, -1, 0});
-    };
-    for (auto pr : far_pairs) add(pr, 1);
-    for (auto pr : near_pairs) add(pr, 0);
-    // order by (r0, c0): two stable counting passes over the cluster starts
-    // (c0 first, then r0); (r0, c0) identifies a block uniquely
-    std::vector<int> cnt(n + 2);
-    std::vector<BlockH> tmp(blocks.size());
-    for (int pass = 0; pass < 2; ++pass) {
-        std::fill(cnt.begin(), cnt.end(), 0);
-        for (auto& b : blocks) ++cnt[(pass ? b.r0 : b.c0) + 1];
-        for (int i = 0; i <= n; ++i) cnt[i + 1] += cnt[i];
-        for (auto& b : blocks) tmp[cnt[pass ? b.r0 : b.c0]++] = b;
-        blocks.swap(tmp);
+    const int64_t nfp = (int64_t)far_pairs.size(), nb = nfp + (int64_t)near_pairs.size();
+    RAD_REQUIRE(nb < INT32_MAX, RAD_ELIMIT, "too many blocks");
+    auto pair_at = [&](int64_t i) { return i < nfp ? far_pairs[i] : near_pairs[i - nfp]; };
+    constexpr int kListParts = 16;
+    if (nb < 1000000) {
+        // small lists: build in input order, then two stable counting
+        // passes (column start, then row start) over the block array
+        blocks.clear();
+        blocks.reserve(nb);
+        for (int64_t i = 0; i < nb; ++i) {
+            const int2 pr = pair_at(i);
+            const NodeShape& a = nodes[pr.x];
+            const NodeShape& bn = nodes[pr.y];
+            const int adm = i < nfp ? 1 : 0;
+            blocks.push_back(BlockH{pr.x, pr.y, a.begin, a.end, bn.begin, bn.end, adm, adm ? 0 : -1, -1, 0});
+        }
+        std::vector<int> cn(n + 2);
+        std::vector<BlockH> tmp(blocks.size());
+        for (int pass = 0; pass < 2; ++pass) {
+            std::fill(cn.begin(), cn.end(), 0);
+            for (auto& b : blocks) ++cn[(pass ? b.r0 : b.c0) + 1];
+            for (int i = 0; i <= n; ++i) cn[i + 1] += cn[i];
+            for (auto& b : blocks) tmp[cn[pass ? b.r0 : b.c0]++] = b;
+            blocks.swap(tmp);
+        }
+        h->n_admissible = (int64_t)far_pairs.size();
+        return;
     }
+    const int P = kListParts;
+    std::vector<int> rcut(P + 1);
+    for (int q = 0; q <= P; ++q) rcut[q] = (int)((int64_t)n * q / P);
+    auto range_of = [&](int r0) { return (int)(std::upper_bound(rcut.begin() + 1, rcut.end() - 1, r0) - rcut.begin()) - 1; };
+    std::vector<int64_t> cnt((size_t)P * P, 0);
+    parallel_parts(P, [&](int t) {
+        int64_t* c = &cnt[(size_t)t * P];
+        for (int64_t i = nb * t / P, e = nb * (t + 1) / P; i < e; ++i) ++c[range_of(nodes[pair_at(i).x].begin)];
+    });
+    std::vector<int64_t> off((size_t)P * P), rstart(P + 1, 0);
+    {
+        int64_t acc = 0;
+        for (int q = 0; q < P; ++q) {
+            rstart[q] = acc;
+            for (int t = 0; t < P; ++t) {
+                off[(size_t)t * P + q] = acc;
+                acc += cnt[(size_t)t * P + q];
+            }
+        }
+        rstart[P] = acc;
+    }
+    std::vector<int> bucket(nb);
+    parallel_parts(P, [&](int t) {
+        int64_t* o = &off[(size_t)t * P];
+        for (int64_t i = nb * t / P, e = nb * (t + 1) / P; i < e; ++i)
+            bucket[o[range_of(nodes[pair_at(i).x].begin)]++] = (int)i;
+    });
+    blocks.resize(nb);
+    parallel_parts(P, [&](int q) {
+        const int lo = rcut[q], hi = rcut[q + 1];
+        const int64_t b0 = rstart[q], b1 = rstart[q + 1];
+        std::vector<int> c(hi - lo + 1, 0), ord(b1 - b0);
+        for (int64_t k = b0; k < b1; ++k) ++c[nodes[pair_at(bucket[k]).x].begin - lo + 1];
+        for (int r = 0; r < hi - lo; ++r) c[r + 1] += c[r];
+        for (int64_t k = b0; k < b1; ++k) ord[c[nodes[pair_at(bucket[k]).x].begin - lo]++] = bucket[k];
+        auto c0_of = [&](int i) { return nodes[pair_at(i).y].begin; };
+        for (int64_t g0 = 0; g0 < b1 - b0;) {
+            const int r0 = nodes[pair_at(ord[g0]).x].begin;
+            int64_t g1 = g0 + 1;
+            while (g1 < b1 - b0 && nodes[pair_at(ord[g1]).x].begin == r0) ++g1;
+            std::sort(ord.begin() + g0, ord.begin() + g1, [&](int x, int y) { return c0_of(x) < c0_of(y); });
+            g0 = g1;
+        }
+        for (int64_t k = 0; k < b1 - b0; ++k) {
+            const int i = ord[k];
+            const int2 pr = pair_at(i);
+            const NodeShape& a = nodes[pr.x];
+            const NodeShape& bn = nodes[pr.y];
+            const int adm = i < nfp ? 1 : 0;
+            blocks[b0 + k] = BlockH{pr.x, pr.y, a.begin, a.end, bn.begin, bn.end, adm, adm ? 0 : -1, -1, 0};
+        }
+    });
     h->n_admissible = (int64_t)far_pairs.size();
 }
 
