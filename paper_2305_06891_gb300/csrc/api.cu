@@ -92,6 +92,19 @@ StageScope::~StageScope() {
     g_stage.retired.clear();
     g_stage.off = 0;
 }
+void stage_copy(void* dst, const void* src, size_t bytes) {
+    constexpr size_t kPar = 32u << 20;
+    if (bytes < kPar) {
+        std::memcpy(dst, src, bytes);
+        return;
+    }
+    constexpr int P = 8;
+    parallel_parts(P, [&](int q) {
+        const size_t b0 = bytes * q / P, b1 = bytes * (q + 1) / P;
+        std::memcpy(static_cast<char*>(dst) + b0, static_cast<const char*>(src) + b0, b1 - b0);
+    });
+}
+
 void* stage_alloc(size_t bytes) {
     StageState& st = g_stage;
     if (st.depth == 0) return nullptr;

@@ -23,7 +23,9 @@ namespace rad {
 
 namespace {
 
-constexpr int kChunkRows = 64;
+constexpr int kChunkRows = 64;        // rows per inner-product chunk of wide blocks
+constexpr int kChunkElems = 8192;     // elements per chunk for narrow blocks
+constexpr int kNarrowCols = 128;      // flattened inner products up to this many columns
 
 __global__ void rhs_kernel(int n, int m, const double* __restrict__ eps, const double* __restrict__ T, long long ldT,
                            const int* __restrict__ perm, double* __restrict__ eps_t, double* __restrict__ B) {
@@ -43,9 +45,47 @@ __global__ void rhs_kernel(int n, int m, const double* __restrict__ eps, const d
 }
 
 // partial[(chunk * L + l) * nc + c] = sum over the chunk's rows of
-// A_l[i][c] * Bv[i][c],  A_l = A + l * strideA.
+// A_l[i][c] * Bv[i][c],  A_l = A + l * strideA.  The chunk's rows are one
+// contiguous range of row-major elements; thread t (< per * nc, per =
+// blockDim / nc) reads elements t, t + per*nc, ... (all of column t % nc),
+// four A_l at a time, and the per threads of a column are summed in a
+// fixed order through shared memory.
 __global__ void __launch_bounds__(256)
 mdot_kernel(const double* __restrict__ A, long long strideA, int L, const double* __restrict__ Bv,
+            const int2* __restrict__ chunk, int nc, double* __restrict__ partial) {
+    __shared__ double red[4][256];
+    const int per = blockDim.x / nc, T = per * nc;
+    const int t = threadIdx.x;
+    const long long e0 = (long long)chunk[blockIdx.x].x * nc, e1 = (long long)chunk[blockIdx.x].y * nc;
+    for (int l0 = 0; l0 < L; l0 += 4) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        if (t < T) {
+            for (long long e = e0 + t; e < e1; e += T) {
+                const double bv = Bv[e];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (l0 + q < L) acc[q] += A[(l0 + q) * strideA + e] * bv;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[q][t] = acc[q];
+        __syncthreads();
+        for (int o = t; o < 4 * nc; o += blockDim.x) {
+            const int q = o / nc, c = o - q * nc;
+            if (l0 + q < L) {
+                double sum = 0.0;
+                for (int k = 0; k < per; ++k) sum += red[q][k * nc + c];
+                partial[((long long)blockIdx.x * L + l0 + q) * nc + c] = sum;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Same sums for wide blocks (nc > 128): a warp takes 32 consecutive columns
+// (grid y = column slab), the eight warps of a CTA take rows ty, ty + 8, ...
+__global__ void __launch_bounds__(256)
+mdot_wide_kernel(const double* __restrict__ A, long long strideA, int L, const double* __restrict__ Bv,
             const int2* __restrict__ chunk, int nc, double* __restrict__ partial) {
     __shared__ double red[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -249,8 +289,10 @@ __global__ void axpy_kernel(double* __restrict__ X, const double* __restrict__ D
 
 inline unsigned grid_for(long long cnt, int bs = 256) { return (unsigned)((cnt + bs - 1) / bs); }
 
-// Inner products per virtual column (segment, column) over chunks of at most
-// 64 rows that never straddle a segment.
+// Inner products per virtual column (segment, column) over chunks of rows
+// that never straddle a segment (for blocks of up to 128 columns about
+// eight chunks per SM of 1,024 to 8,192 elements each; 64 rows for wider
+// blocks).
 struct ColReducer {
     int n, nc, nseg, nvc, nchunks;
     const int2* chunk;       // [r0, r1) per chunk
@@ -264,10 +306,13 @@ struct ColReducer {
         nvc = nseg * nc;
         std::vector<int2> ch;
         std::vector<int> c0(nseg + 1);
+        // narrow blocks: about eight chunks per SM, 1,024 to 8,192 elements each
+        const int64_t chunk_elems = std::min<int64_t>(kChunkElems, std::max<int64_t>(1024, (int64_t)n * nc / 1216));
         for (int g = 0; g < nseg; ++g) {
             c0[g] = (int)ch.size();
-            for (int64_t r = sg[g]; r < sg[g + 1]; r += kChunkRows)
-                ch.push_back(make_int2((int)r, (int)std::min<int64_t>(r + kChunkRows, sg[g + 1])));
+            const int64_t rows = nc <= kNarrowCols ? std::max<int64_t>(1, chunk_elems / nc) : kChunkRows;
+            for (int64_t r = sg[g]; r < sg[g + 1]; r += rows)
+                ch.push_back(make_int2((int)r, (int)std::min<int64_t>(r + rows, sg[g + 1])));
         }
         c0[nseg] = (int)ch.size();
         nchunks = (int)ch.size();
@@ -281,8 +326,13 @@ struct ColReducer {
     }
     // out[l][vc] = sum over vc's rows of A_l[i][c] Bv[i][c]
     void dots(const double* A, long long strideA, int L, const double* Bv, double* out) {
-        dim3 grid(nchunks, (nc + 31) / 32);
-        { ProfScope ps_("gmres_dots", s); mdot_kernel<<<grid, 256, 0, s>>>(A, strideA, L, Bv, chunk, nc, partial); }
+        if (nc <= kNarrowCols) {
+            ProfScope ps_("gmres_dots", s);
+            mdot_kernel<<<nchunks, 256, 0, s>>>(A, strideA, L, Bv, chunk, nc, partial);
+        } else {
+            ProfScope ps_("gmres_dots", s);
+            mdot_wide_kernel<<<dim3(nchunks, (nc + 31) / 32), 256, 0, s>>>(A, strideA, L, Bv, chunk, nc, partial);
+        }
         RAD_CHECK_LAUNCH();
         { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<grid_for((long long)L * nvc, 8), 256, 0, s>>>(partial, seg_chunk0, L, nc, nvc,
                                                                           out); }

@@ -125,13 +125,16 @@ struct StageScope {
 };
 void* stage_alloc(size_t bytes);   // nullptr when no scope is active
 
+// Host copy into page-locked staging; 8 threads from 32 MiB.
+void stage_copy(void* dst, const void* src, size_t bytes);
+
 template <class T>
 void h2d(T* dst, const std::vector<T>& v, cudaStream_t s) {
     if (v.empty()) return;
     const size_t bytes = v.size() * sizeof(T);
     void* st = bytes >= 4096 ? stage_alloc(bytes) : nullptr;
     if (st) {
-        std::memcpy(st, v.data(), bytes);
+        stage_copy(st, v.data(), bytes);
         RAD_CUDA(cudaMemcpyAsync(dst, st, bytes, cudaMemcpyHostToDevice, s));
     } else {
         RAD_CUDA(cudaMemcpyAsync(dst, v.data(), bytes, cudaMemcpyHostToDevice, s));
