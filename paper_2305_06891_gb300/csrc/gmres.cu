@@ -44,7 +44,7 @@ __global__ void rhs_kernel(int n, int m, const double* __restrict__ eps, const d
     }
 }
 
-// partial[(chunk * L + l) * nc + c] = sum over the chunk's rows of
+// partial[(l * nc + c) * nchunks + chunk] = sum over the chunk's rows of
 // A_l[i][c] * Bv[i][c],  A_l = A + l * strideA.  The chunk's rows are one
 // contiguous range of row-major elements; thread t (< per * nc, per =
 // blockDim / nc) reads elements t, t + per*nc, ... (all of column t % nc),
@@ -75,7 +75,7 @@ mdot_kernel(const double* __restrict__ A, long long strideA, int L, const double
             if (l0 + q < L) {
                 double sum = 0.0;
                 for (int k = 0; k < per; ++k) sum += red[q][k * nc + c];
-                partial[((long long)blockIdx.x * L + l0 + q) * nc + c] = sum;
+                partial[((long long)(l0 + q) * nc + c) * gridDim.x + blockIdx.x] = sum;
             }
         }
         __syncthreads();
@@ -109,7 +109,7 @@ mdot_wide_kernel(const double* __restrict__ A, long long strideA, int L, const d
             if (ty == 0 && l0 + q < L && c < nc) {
                 double s = 0.0;
                 for (int w = 0; w < 8; ++w) s += red[w][tx];
-                partial[((long long)blockIdx.x * L + l0 + q) * nc + c] = s;
+                partial[((long long)(l0 + q) * nc + c) * gridDim.x + blockIdx.x] = s;
             }
             __syncthreads();
         }
@@ -126,11 +126,11 @@ __device__ __forceinline__ int vcol(const int* seg, long long e, int nc) {
 }
 
 // out[l * nvc + vc] = sum over the chunks of vc's segment of
-// partial[chunk][l][c]: one warp per output, lanes take chunks lane,
+// partial[l][c][chunk]: one warp per output, lanes take chunks lane,
 // lane + 32, ..., then a fixed butterfly (the same summation order on every
 // call).  Chunks never straddle segments.
 __global__ void reduce_chunks_kernel(const double* __restrict__ partial, const int* __restrict__ seg_chunk0, int L,
-                                     int nc, int nvc, double* out) {
+                                     int nc, int nvc, int nchunks, double* out) {
     const int e = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (e >= L * nvc) return;
@@ -138,7 +138,8 @@ __global__ void reduce_chunks_kernel(const double* __restrict__ partial, const i
     const int sg = vc / nc, c = vc - sg * nc;
     const int k0 = seg_chunk0[sg], k1 = seg_chunk0[sg + 1];
     double s = 0.0;
-    for (int k = k0 + lane; k < k1; k += 32) s += partial[((long long)k * L + l) * nc + c];
+    const double* pc = partial + ((long long)l * nc + c) * nchunks;
+    for (int k = k0 + lane; k < k1; k += 32) s += pc[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[e] = s;
@@ -335,7 +336,7 @@ struct ColReducer {
         }
         RAD_CHECK_LAUNCH();
         { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<grid_for((long long)L * nvc, 8), 256, 0, s>>>(partial, seg_chunk0, L, nc, nvc,
-                                                                          out); }
+                                                                          nchunks, out); }
         RAD_CHECK_LAUNCH();
     }
 };
