@@ -119,10 +119,32 @@ mdot_wide_kernel(const double* __restrict__ A, long long strideA, int L, const d
 // Virtual columns: a batch handle holds several cavities (segments of the
 // rows); every (segment, column) pair is its own Krylov problem, with index
 // vc = segment * nc + c.  seg == nullptr means one segment.
+// row and column of element e of a row-major block with nc columns (32-bit
+// division while e fits, the FP64-free fast path of every vector kernel)
+__device__ __forceinline__ void row_col(long long e, int nc, long long& row, int& c) {
+    if (e <= 0xffffffffll) {
+        const unsigned r = (unsigned)e / (unsigned)nc;
+        row = r;
+        c = (int)((unsigned)e - r * (unsigned)nc);
+    } else {
+        row = e / nc;
+        c = (int)(e - row * nc);
+    }
+}
 __device__ __forceinline__ int vcol(const int* seg, long long e, int nc) {
-    const long long row = e / nc;
-    const int c = (int)(e - row * nc);
+    long long row;
+    int c;
+    row_col(e, nc, row, c);
     return seg ? seg[row] * nc + c : c;
+}
+
+// rs[vc] = 1 / sqrt(ss[vc]) for active columns with ss > 0, else 0 (the
+// scale of a normalisation, computed once per column)
+__global__ void col_scale_kernel(int nvc, const double* __restrict__ ss, const int* __restrict__ active,
+                                 double* __restrict__ rs) {
+    const int vc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (vc >= nvc) return;
+    rs[vc] = (active[vc] && ss[vc] > 0.0) ? 1.0 / sqrt(ss[vc]) : 0.0;
 }
 
 // out[l * nvc + vc] = sum over the chunks of vc's segment of
@@ -163,24 +185,31 @@ __global__ void cgs_update_kernel(const double* __restrict__ V, long long stride
     W[e] = w;
 }
 
-// V_next = W / hn (active columns with hn > 0), else 0; optional FP32 copy.
-__global__ void normalize_kernel(const double* __restrict__ W, const double* __restrict__ hn2,
-                                 const int* __restrict__ active, double* __restrict__ Vn, float* __restrict__ X32,
-                                 int n, int nc, const int* __restrict__ seg, int ldp) {
+// Vn = W * rs (rs from col_scale_kernel: 1 / ||W|| per active column, else
+// 0); optional FP32 copy with rows padded to ldp.  Also starts a cycle
+// (W = residual, rs = 1 / beta).
+__global__ void normalize_kernel(const double* __restrict__ W, const double* __restrict__ rs,
+                                 double* __restrict__ Vn, float* __restrict__ X32, int n, int nc,
+                                 const int* __restrict__ seg, int ldp) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)n * nc) return;
-    const int c = vcol(seg, e, nc);
-    const double hn = sqrt(hn2[c]);
-    const double v = (active[c] && hn > 0.0) ? W[e] / hn : 0.0;
+    long long row;
+    int c;
+    row_col(e, nc, row, c);
+    const double v = W[e] * rs[seg ? seg[row] * nc + c : c];
     Vn[e] = v;
-    if (X32) X32[(e / nc) * ldp + e % nc] = (float)v;
+    if (X32) X32[row * ldp + c] = (float)v;
 }
 
 // FP32 copy of an n x nc row-major FP64 block, rows padded to ldp columns
 // (so that the product can move them as 16-byte quads).
 __global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, long long cnt, int nc, int ldp) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < cnt) b[(e / nc) * ldp + e % nc] = (float)a[e];
+    if (e >= cnt) return;
+    long long row;
+    int c;
+    row_col(e, nc, row, c);
+    b[row * ldp + c] = (float)a[e];
 }
 
 // Per column: apply the previous Givens rotations to the new Hessenberg
@@ -244,19 +273,6 @@ __global__ void update_x_kernel(const double* __restrict__ V, long long strideV,
     double x = X[e];
     for (int l = 0; l < J; ++l) x += V[l * strideV + e] * ycoef[l * nvc + c];
     X[e] = x;
-}
-
-// start a cycle: V_0 = R / beta for active columns, g = beta e_1
-__global__ void start_cycle_kernel(const double* __restrict__ Rv, const double* __restrict__ beta2,
-                                   const int* __restrict__ active, double* __restrict__ V0, float* __restrict__ X32,
-                                   int n, int nc, const int* __restrict__ seg, int ldp) {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (long long)n * nc) return;
-    const int c = vcol(seg, e, nc);
-    const double b = sqrt(beta2[c]);
-    const double v = (active[c] && b > 0.0) ? Rv[e] / b : 0.0;
-    V0[e] = v;
-    if (X32) X32[(e / nc) * ldp + e % nc] = (float)v;
 }
 
 __global__ void init_g_kernel(int R, int nc, const double* __restrict__ beta2, double* __restrict__ g,
@@ -371,6 +387,7 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
     double* bnorm = ws.get_n<double>(nvc);
     double* beta2 = ws.get_n<double>(nvc);
     double* hn2 = ws.get_n<double>(nvc);
+    double* rscale = ws.get_n<double>(nvc);
     double* resid = ws.get_n<double>(nvc);
     int* active = ws.get_n<int>(nvc);
     int* jc = ws.get_n<int>(nvc);
@@ -413,7 +430,10 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
         }
         prev_max = max_rel;
         RAD_CUDA(cudaMemcpyAsync(active, hact.data(), sizeof(int) * nvc, cudaMemcpyHostToDevice, s));
-        { ProfScope ps_("gmres_small", s); start_cycle_kernel<<<grid_for(nv), 256, 0, s>>>(W, beta2, active, V, X32, n, nc, seg, ldp); }
+        // start a cycle: V_0 = R / beta for active columns, g = beta e_1
+        { ProfScope ps_("gmres_small", s); col_scale_kernel<<<grid_for(nvc, 128), 128, 0, s>>>(nvc, beta2, active, rscale); }
+        RAD_CHECK_LAUNCH();
+        { ProfScope ps_("gmres_small", s); normalize_kernel<<<grid_for(nv), 256, 0, s>>>(W, rscale, V, X32, n, nc, seg, ldp); }
         RAD_CHECK_LAUNCH();
         { ProfScope ps_("gmres_small", s); init_g_kernel<<<grid_for(nvc, 128), 128, 0, s>>>(R, nvc, beta2, g, jc); }
         RAD_CHECK_LAUNCH();
@@ -435,7 +455,9 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
                 }
             }
             red.dots(W, 0, 1, W, hn2);
-            { ProfScope ps_("gmres_normalize", s); normalize_kernel<<<grid_for(nv), 256, 0, s>>>(W, hn2, active, V + (long long)(j + 1) * nv, X32, n, nc, seg, ldp); }
+            { ProfScope ps_("gmres_normalize", s); col_scale_kernel<<<grid_for(nvc, 128), 128, 0, s>>>(nvc, hn2, active, rscale); }
+            RAD_CHECK_LAUNCH();
+            { ProfScope ps_("gmres_normalize", s); normalize_kernel<<<grid_for(nv), 256, 0, s>>>(W, rscale, V + (long long)(j + 1) * nv, X32, n, nc, seg, ldp); }
             RAD_CHECK_LAUNCH();
             { ProfScope ps_("gmres_small", s); givens_kernel<<<grid_for(nvc, 128), 128, 0, s>>>(j, R, nvc, Hm, hn2, cs, sn, g, bnorm, resid, active, jc,
                                                             tol); }
