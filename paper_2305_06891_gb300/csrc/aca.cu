@@ -853,8 +853,14 @@ void launch_recompress(const std::vector<int>& list, long long res_elems, const 
     int* d_list = ws.get_n<int>(list.size());
     h2d(d_list, list, s);
     const size_t bytes = sizeof(RcSmem<CT, KM, NT>) + (RES ? (size_t)res_elems * sizeof(CT) : 0);
-    RAD_CUDA(cudaFuncSetAttribute(recompress_kernel<CT, KM, NT, RES>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    // the attribute is set once, to the largest size a launch can ask for
+    // (the 48 KiB tier), so that concurrent compressions on other host
+    // threads never see it lowered between their setting and their launch
+    static std::once_flag configured;
+    std::call_once(configured, [] {
+        RAD_CUDA(cudaFuncSetAttribute(recompress_kernel<CT, KM, NT, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(RcSmem<CT, KM, NT>) + (RES ? (size_t)(48 << 10) : 0))));
+    });
     recompress_kernel<CT, KM, NT, RES><<<(unsigned)list.size(), NT, bytes, s>>>(d_jobs, d_list, d_rank, Us, Vs,
                                                                                  tol);
     RAD_CHECK_LAUNCH();

@@ -118,13 +118,17 @@ __device__ __forceinline__ void stream_panel4(const S* __restrict__ P, long long
 
 // acc[k][0..3] += sum over panel columns c = g, g + G, ... of the 4 rows at
 // P of column c times V[idx[c]][k] (V[base + c][k] when idx is null), for
-// the NCOL columns k of V's rows; four panel columns in flight per step.
+// the NCOL columns k of V's rows; four panel columns in flight per step
+// (FP32 / BF16 panels).
 template <class S, class AT, int NCOL>
 __device__ __forceinline__ void stream_cols(const S* __restrict__ P, long long ld, int kcols, int g, int G,
                                             const int* __restrict__ idx, const AT* __restrict__ V, int ldv,
                                             AT (&acc)[NCOL][4], int base = 0) {
     constexpr int U = 4;
     int c = g;
+    // FP64 panels (the plain FP64 path) keep one column per step: their
+    // wider registers cost more occupancy than the extra loads in flight gain
+    if constexpr (sizeof(S) != 8)
     for (; c + (U - 1) * G < kcols; c += U * G) {
         AT a[U][4];
         const AT* vr[U];

@@ -84,3 +84,20 @@ def test_request_larger_than_budget_fails_cleanly():
         srv.wait(t)
     assert srv.stats()["failed"] == 1
     srv.close()
+
+
+def test_concurrent_builds_with_recompression():
+    # four slots build four operators at once, each with recompressed
+    # crosses (kernels whose shared-memory size depends on the cavity)
+    r = rad()
+    cavs = _cavities()
+    reqs = [(c, e, T) for c, e, T in _requests(cavs, count=8)]
+    srv = r.Server(slots=4, hbm_budget_bytes=64 << 30, aca_scratch_mib=64, recompress_tol=1e-6, **SETTINGS)
+    ids = [srv.add_cavity(v) for v in cavs]
+    tickets = [srv.submit(ids[c], e, T) for c, e, T in reqs]
+    out = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    for q, info in out:
+        assert info["status"] == 0 and info["max_rel_residual"] <= 1e-9 and np.isfinite(q).all()
