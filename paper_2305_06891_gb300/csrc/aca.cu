@@ -1065,6 +1065,34 @@ void build_stream_lists(rad_htree* h, int rows, cudaStream_t s) {
 
 namespace {
 
+// SMs of the current device (one query per process)
+static int sm_count() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return 1;
+        }
+        return std::max(1, v);
+    }();
+    return n;
+}
+
+// Heaviest-first order re-dealt in snake order over L slots (the SMs that
+// the first wave of one-CTA-per-item launches spreads over): positions
+// 0..L-1 take items 0..L-1, positions L..2L-1 take items 2L-1..L, and so on,
+// so that every slot's items add up to about the same work.
+static std::vector<int> snake_order(const std::vector<int>& heavy_first, int L) {
+    const size_t n = heavy_first.size();
+    std::vector<int> out(n);
+    for (size_t i = 0; i < n; ++i) {
+        const size_t round = i / L, pos = i % L;
+        const size_t src = round * L + ((round & 1) ? std::min<size_t>(L, n - round * L) - 1 - pos : pos);
+        out[i] = heavy_first[src];
+    }
+    return out;
+}
+
 static void upload_operator(rad_htree* h, const std::vector<IdxRun>& near_runs, const std::vector<IdxRun>& far_runs,
                             cudaStream_t s) {
     long long nx = 0, nf = 0;
@@ -1093,12 +1121,24 @@ static void upload_operator(rad_htree* h, const std::vector<IdxRun>& near_runs, 
         return w;
     };
     std::vector<GWork> gwork = split_groups(kTileRows);
+    {
+        // one CTA per item, dealt across the SMs in snake order
+        const std::vector<int> ident_order = [&] {
+            std::vector<int> v(gwork.size());
+            std::iota(v.begin(), v.end(), 0);
+            return v;
+        }();
+        const std::vector<int> so = snake_order(ident_order, sm_count());
+        std::vector<GWork> g2(gwork.size());
+        for (size_t i = 0; i < so.size(); ++i) g2[i] = gwork[so[i]];
+        gwork.swap(g2);
+    }
     std::vector<long long> tkey(h->tiles_h.size());
     for (size_t t = 0; t < tkey.size(); ++t) {
         const Tile& tl = h->tiles_h[t];
         tkey[t] = (long long)tl.ld * (tl.kn + tl.kf);
     }
-    const std::vector<int> torder = order_desc(tkey);
+    const std::vector<int> torder = snake_order(order_desc(tkey), sm_count());
     std::vector<long long> fkey(h->tiles_h.size());
     for (size_t t = 0; t < fkey.size(); ++t) fkey[t] = (long long)h->tiles_h[t].ld * h->tiles_h[t].kf;
     const std::vector<int> forder = order_desc(fkey);
