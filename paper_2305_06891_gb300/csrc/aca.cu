@@ -515,18 +515,22 @@ struct UWork {
     int tile, ro, m, k, col, chunk;
     long long src;
 };
+// One warp per piece (eight per CTA): column l of the piece is rows
+// ro .. ro + ld of U_b's column l (zeros past the tile's rows).
 template <class CT, class S>
 __global__ void __launch_bounds__(256)
-u_fill_kernel(const Tile* __restrict__ tiles, const UWork* __restrict__ work, const CT* const* __restrict__ Ubase,
-              S* pool) {
-    const UWork w = work[blockIdx.x];
+u_fill_kernel(const Tile* __restrict__ tiles, const UWork* __restrict__ work, int nwork,
+              const CT* const* __restrict__ Ubase, S* pool) {
+    const int wi = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (wi >= nwork) return;
+    const UWork w = work[wi];
     const CT* __restrict__ Us = Ubase[w.chunk];
     const Tile t = tiles[w.tile];
     S* P = pool + t.foff + (long long)w.col * t.ld;
-    const int cnt = w.k * t.ld;
-    for (int e = threadIdx.x; e < cnt; e += 256) {
-        const int l = e / t.ld, i = e - l * t.ld;
-        P[e] = i < t.rows ? Store<S>::put(Us[w.src + (long long)l * w.m + w.ro + i]) : Store<S>::put(CT(0));
+    for (int l = 0; l < w.k; ++l) {
+        const CT* src = Us + w.src + (long long)l * w.m + w.ro;
+        S* dst = P + (long long)l * t.ld;
+        for (int i = lane; i < t.ld; i += 32) dst[i] = i < t.rows ? Store<S>::put(src[i]) : Store<S>::put(CT(0));
     }
 }
 
@@ -1189,7 +1193,7 @@ static void launch_factor_fill(rad_htree* h, const std::vector<UWork>& uw, const
     if (!uw.empty()) {
         UWork* d = ws.get_n<UWork>(uw.size());
         h2d(d, uw, s);
-        { ProfScope ps_("aca_pack", s); u_fill_kernel<CT, S><<<(unsigned)uw.size(), 256, 0, s>>>(h->d_tiles.as<Tile>(), d, Ubase, dst); }
+        { ProfScope ps_("aca_pack", s); u_fill_kernel<CT, S><<<(unsigned)((uw.size() + 7) / 8), 256, 0, s>>>(h->d_tiles.as<Tile>(), d, (int)uw.size(), Ubase, dst); }
         RAD_CHECK_LAUNCH();
     }
     if (!vw.empty()) {
