@@ -181,14 +181,32 @@ tree_level_kernel(const NodeShape* __restrict__ shapes, NodeBox* __restrict__ bo
             if ((k & mask) == prefix) atomicAdd(&hist[(k >> shift) & 0xffull], 1u);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            int cum = 0, d = 0;
-            for (; d < 255; ++d) {
-                if (want < cum + (int)hist[d]) break;
-                cum += (int)hist[d];
+        if (warp == 0) {
+            // digit d holding rank `want`: lane q scans bins 8q .. 8q + 7
+            unsigned loc[8], sum = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                loc[j] = hist[8 * lane + j];
+                sum += loc[j];
             }
-            sel_digit = d;
-            sel_want = want - cum;
+            unsigned incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const int excl = (int)(incl - sum);
+            if (want >= excl && want < (int)incl) {
+                int cum = excl, d = 8 * lane;
+#pragma unroll
+                for (int j = 0; j < 7; ++j) {
+                    if (want < cum + (int)loc[j]) break;
+                    cum += (int)loc[j];
+                    ++d;
+                }
+                sel_digit = d;
+                sel_want = want - cum;
+            }
         }
         __syncthreads();
         prefix |= (unsigned long long)sel_digit << shift;
@@ -200,32 +218,34 @@ tree_level_kernel(const NodeShape* __restrict__ shapes, NodeBox* __restrict__ bo
     const int n_eq_left = want + 1;  // equal keys that go left, in index order
 
     // 4. stable partition (left: key < pivot, or key == pivot among the
-    //    first n_eq_left equal keys in list order)
-    int lbase = 0, rbase = 0, eqbase = 0;
-    for (int s = b; s < e; s += NT) {
-        const int p = s + threadIdx.x;
-        const bool valid = p < e;
-        const unsigned long long k = valid ? keys[p] : 0ull;
-        const int isless = (valid && k < pkey) ? 1 : 0;
-        const int iseq = (valid && k == pkey) ? 1 : 0;
-        int eqtot;
-        const int eqr = block_excl_scan<NT, int>(iseq, scan_sm, eqtot);
-        const int goleft = (isless || (iseq && eqbase + eqr < n_eq_left)) ? 1 : 0;
-        int ltot;
-        const int lp = block_excl_scan<NT, int>(goleft, scan_sm, ltot);
-        const int cnt = min(NT, e - s);
-        if (valid) {
-            const int f = idx_in[p];
-            const int dst = goleft ? b + lbase + lp : b + h + rbase + ((int)threadIdx.x - lp);
-            const bool ok = goleft ? dst < b + h : (dst >= b + h && dst < e);
-            if (ok) idx_out[dst] = f;
-            else atomicOr(err, 4);
-        }
-        lbase += ltot;
-        rbase += cnt - ltot;
-        eqbase += eqtot;
+    //    first n_eq_left equal keys in list order): each thread takes a
+    //    contiguous segment of the node, counts, two block scans give the
+    //    offsets, and the thread writes its segment in order
+    const int per = (n + NT - 1) / NT;
+    const int s0 = min(e, b + (int)threadIdx.x * per), s1 = min(e, s0 + per);
+    int cl = 0, ce = 0;
+    for (int p = s0; p < s1; ++p) {
+        const unsigned long long k = keys[p];
+        cl += k < pkey ? 1 : 0;
+        ce += k == pkey ? 1 : 0;
     }
-    if (threadIdx.x == 0 && lbase != h) atomicOr(err, 2);
+    int eqtot;
+    const int eq_before = block_excl_scan<NT, int>(ce, scan_sm, eqtot);
+    const int gl = cl + min(ce, max(0, n_eq_left - eq_before));
+    int ltot;
+    const int l_before = block_excl_scan<NT, int>(gl, scan_sm, ltot);
+    int li = 0, ri = 0, eqi = 0;
+    const int r_before = (s0 - b) - l_before;
+    for (int p = s0; p < s1; ++p) {
+        const unsigned long long k = keys[p];
+        bool left = k < pkey;
+        if (k == pkey) left = eq_before + eqi++ < n_eq_left;
+        const int dst = left ? b + l_before + li++ : b + h + r_before + ri++;
+        const bool ok = left ? dst < b + h : (dst >= b + h && dst < e);
+        if (ok) idx_out[dst] = idx_in[p];
+        else atomicOr(err, 4);
+    }
+    if (threadIdx.x == 0 && ltot != h) atomicOr(err, 2);
 }
 
 __global__ void gather_geo_kernel(int n, const double* __restrict__ geo_user, const int* __restrict__ perm,
