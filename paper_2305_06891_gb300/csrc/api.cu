@@ -1,10 +1,10 @@
-#include <algorithm>
-#include <exception>
-#include <chrono>
 // C ABI entry points of librad (declared in include/rad.h).  Every entry
 // point catches all C++ exceptions and turns them into status codes.
 
+#include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <exception>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -92,8 +92,93 @@ StageScope::~StageScope() {
     g_stage.retired.clear();
     g_stage.off = 0;
 }
+// Host worker pool: kPoolThreads threads started on first use and kept for
+// the life of the process.  One job at a time (try_lock on job_mu).  Parts
+// are handed out under the pool mutex together with a check of the job's
+// epoch, so a worker that wakes late never touches a finished job; the
+// caller runs parts as well and returns once every part has finished.
+namespace {
+constexpr int kPoolThreads = 15;
+struct HostPool {
+    std::mutex job_mu;                     // held by the caller for one job
+    std::mutex mu;                         // guards everything below
+    std::condition_variable cv, done_cv;
+    void (*job)(void*, int) = nullptr;
+    void* ctx = nullptr;
+    int parts = 0, next_part = 0, remaining = 0;
+    unsigned long long epoch = 0;
+    bool stop = false;
+    std::vector<std::thread> th;
+    void drain(unsigned long long ep) {
+        for (;;) {
+            int q;
+            void (*j)(void*, int);
+            void* c;
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                if (epoch != ep || next_part >= parts) return;
+                q = next_part++;
+                j = job;
+                c = ctx;
+            }
+            j(c, q);
+            std::lock_guard<std::mutex> lk(mu);
+            if (--remaining == 0) done_cv.notify_all();
+        }
+    }
+    void worker() {
+        unsigned long long seen = 0;
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return stop || epoch != seen; });
+                if (stop) return;
+                seen = epoch;
+            }
+            drain(seen);
+        }
+    }
+    HostPool() {
+        for (int i = 0; i < kPoolThreads; ++i) th.emplace_back([this] { worker(); });
+    }
+    ~HostPool() {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        for (auto& t : th) t.join();
+    }
+};
+HostPool& host_pool() {
+    static HostPool p;
+    return p;
+}
+}  // namespace
+
+bool pool_run(int parts, void (*job)(void*, int), void* ctx) {
+    HostPool& p = host_pool();
+    std::unique_lock<std::mutex> busy(p.job_mu, std::try_to_lock);
+    if (!busy.owns_lock()) return false;
+    unsigned long long ep;
+    {
+        std::lock_guard<std::mutex> lk(p.mu);
+        p.job = job;
+        p.ctx = ctx;
+        p.parts = parts;
+        p.next_part = 0;
+        p.remaining = parts;
+        ep = ++p.epoch;
+    }
+    p.cv.notify_all();
+    p.drain(ep);
+    std::unique_lock<std::mutex> lk(p.mu);
+    p.done_cv.wait(lk, [&] { return p.remaining == 0; });
+    return true;
+}
+
 void stage_copy(void* dst, const void* src, size_t bytes) {
-    constexpr size_t kPar = 32u << 20;
+    constexpr size_t kPar = 8u << 20;
     if (bytes < kPar) {
         std::memcpy(dst, src, bytes);
         return;

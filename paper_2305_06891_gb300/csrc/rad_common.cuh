@@ -2,6 +2,7 @@
 #pragma once
 
 #include <chrono>
+#include <condition_variable>
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -125,7 +126,7 @@ struct StageScope {
 };
 void* stage_alloc(size_t bytes);   // nullptr when no scope is active
 
-// Host copy into page-locked staging; 8 threads from 32 MiB.
+// Host copy into page-locked staging; 8 threads from 8 MiB.
 void stage_copy(void* dst, const void* src, size_t bytes);
 
 template <class T>
@@ -143,8 +144,15 @@ void h2d(T* dst, const std::vector<T>& v, cudaStream_t s) {
 
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// Runs job(q) for q = 0 .. parts-1 on the library's host worker pool (the
+// caller takes part too); returns false without running anything when the
+// pool is busy with another caller's job (e.g. another server thread).
+bool pool_run(int parts, void (*job)(void*, int), void* ctx);
+
 // Runs f(q) for q = 0 .. parts-1, parts > 1 on host threads (q = 0 on the
-// calling thread); the first exception thrown by any part is rethrown.
+// calling thread): the persistent worker pool, or freshly started threads
+// while the pool serves another caller; the first exception thrown by any
+// part is rethrown.
 template <class F>
 void parallel_parts(int parts, F&& f) {
     if (parts <= 1) {
@@ -159,11 +167,14 @@ void parallel_parts(int parts, F&& f) {
             err[q] = std::current_exception();
         }
     };
-    std::vector<std::thread> th;
-    th.reserve(parts - 1);
-    for (int q = 1; q < parts; ++q) th.emplace_back(run, q);
-    run(0);
-    for (auto& t : th) t.join();
+    using Run = decltype(run);
+    if (!pool_run(parts, [](void* c, int q) { (*static_cast<Run*>(c))(q); }, &run)) {
+        std::vector<std::thread> th;
+        th.reserve(parts - 1);
+        for (int q = 1; q < parts; ++q) th.emplace_back(run, q);
+        run(0);
+        for (auto& t : th) t.join();
+    }
     for (auto& e : err)
         if (e) std::rethrow_exception(e);
 }
