@@ -1394,10 +1394,10 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     h->sum_rank = toff;
     // Per-tile panel columns, gather runs and fill work.  Large plans are
     // split into row ranges (8 from 20,000 blocks, 16 from 100,000) cut at
-    // tile starts and built by threads (each range owns its tiles); blocks
-    // whose rows cross a cut go first, sequentially.  The layout is
-    // deterministic for a given block list (the part count depends only on
-    // the block count, not on the machine).
+    // tile starts and built by threads (each range owns its tiles); the
+    // pieces of blocks whose rows cross a cut come first in each range.
+    // The layout is deterministic for a given block list (the part count
+    // depends only on the block count, not on the machine).
     struct PlanPart {
         std::vector<DenseWork> dwork;
         std::vector<UWork> uwork;
@@ -1407,12 +1407,15 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
         int64_t near_e = 0, far_u = 0, far_v = 0;
         int maxk = 0;
     };
-    auto plan_block = [&](int b, PlanPart& o) {
+    // block b's pieces in the tiles of rows [lo, hi); the per-block items
+    // (entry counts, the V^T fill) only for its owner part
+    auto plan_block = [&](int b, PlanPart& o, int lo, int hi, bool owner) {
         const BlockH& bk = h->blocks[b];
         const int m = bk.r1 - bk.r0, n = bk.c1 - bk.c0;
+        const int r0 = std::max(bk.r0, lo), r1 = std::min(bk.r1, hi);
         if (bk.rank < 0) {
-            o.near_e += (long long)m * n;
-            for_tiles(tiles, tile_at, bk.r0, bk.r1, [&](int t) {
+            if (owner) o.near_e += (long long)m * n;
+            for_tiles(tiles, tile_at, r0, r1, [&](int t) {
                 o.near_pieces.push_back(Piece{b, t, tiles[t].kn});
                 for (int c0 = 0; c0 < n; c0 += 64)
                     o.dwork.push_back(DenseWork{t, bk.c0 + c0, std::min(64, n - c0), tiles[t].kn + c0});
@@ -1423,16 +1426,18 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
             const int k = bk.rank;
             const int jb = job_of[b];
             const Group& gr = h->groups_h[bk.group];
-            o.maxk = std::max(o.maxk, k);
-            o.far_u += (long long)k * m;
-            o.far_v += (long long)k * n;
-            for_tiles(tiles, tile_at, bk.r0, bk.r1, [&](int t) {
+            if (owner) {
+                o.maxk = std::max(o.maxk, k);
+                o.far_u += (long long)k * m;
+                o.far_v += (long long)k * n;
+            }
+            for_tiles(tiles, tile_at, r0, r1, [&](int t) {
                 o.far_pieces.push_back(Piece{b, t, tiles[t].kf});
                 o.uwork.push_back(UWork{t, tiles[t].r0 - bk.r0, m, k, tiles[t].kf, job_chunk[jb], src_u[jb]});
                 o.far_runs.push_back(IdxRun{t, tiles[t].kf, gr.toff + bk.grow, k});
                 tiles[t].kf += k;
             });
-            o.vwork.push_back(VWork{bk.group, bk.grow, n, k, job_chunk[jb], 0, src_v[jb]});
+            if (owner) o.vwork.push_back(VWork{bk.group, bk.grow, n, k, job_chunk[jb], 0, src_v[jb]});
         }
     };
     const int nb = (int)h->blocks.size();
@@ -1444,16 +1449,26 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
         while (r < (int)h->n && tile_at[r] < 0) ++r;
         cut[q] = std::max(cut[q - 1], r);
     }
-    std::vector<PlanPart> pp(parts + 1);  // pp[0]: crossing blocks, pp[q + 1]: range q
-    std::vector<std::vector<int>> part_blocks(parts);
+    // range q plans first the pieces of the blocks that cross into it from
+    // other ranges (in block order), then its own blocks: per tile, the
+    // same column order as one sequential pass over crossing blocks first
+    std::vector<PlanPart> pp(parts);
+    std::vector<std::vector<int>> part_blocks(parts), part_cross(parts);
     for (int b = 0; b < nb; ++b) {
         const BlockH& bk = h->blocks[b];
         const int q = (int)(std::upper_bound(cut.begin(), cut.end(), bk.r0) - cut.begin()) - 1;
-        if (bk.r1 > cut[q + 1]) plan_block(b, pp[0]);
-        else part_blocks[q].push_back(b);
+        if (bk.r1 > cut[q + 1]) {
+            for (int q2 = q; q2 < parts && cut[q2] < bk.r1; ++q2) part_cross[q2].push_back(b);
+        } else {
+            part_blocks[q].push_back(b);
+        }
     }
     parallel_parts(parts, [&](int q) {
-        for (int b : part_blocks[q]) plan_block(b, pp[q + 1]);
+        for (int b : part_cross[q]) {
+            const BlockH& bk = h->blocks[b];
+            plan_block(b, pp[q], cut[q], cut[q + 1], bk.r0 >= cut[q] && bk.r0 < cut[q + 1]);
+        }
+        for (int b : part_blocks[q]) plan_block(b, pp[q], cut[q], cut[q + 1], true);
     });
     // concatenation of the parts' lists in part order (copies in parallel)
     std::vector<DenseWork> dwork;
