@@ -1097,7 +1097,7 @@ static std::vector<int> snake_order(const std::vector<int>& heavy_first, int L) 
     return out;
 }
 
-static void upload_operator(rad_htree* h, const std::vector<IdxRun>& near_runs, const std::vector<IdxRun>& far_runs,
+static void upload_operator(rad_htree* h, const HVec<IdxRun>& near_runs, const HVec<IdxRun>& far_runs,
                             cudaStream_t s) {
     long long nx = 0, nf = 0;
     for (auto& t : h->tiles_h) {
@@ -1162,10 +1162,10 @@ static void upload_operator(rad_htree* h, const std::vector<IdxRun>& near_runs, 
     h2d(h->d_gwork.as<GWork>(), gwork, s);
     h2d(h->d_groups.as<Group>(), h->groups_h, s);
     Scratch ws(s);
-    const std::vector<IdxRun>* lists[2] = {&near_runs, &far_runs};
+    const HVec<IdxRun>* lists[2] = {&near_runs, &far_runs};
     int* outs[2] = {h->d_xidx.as<int>(), h->d_tidx.as<int>()};
     for (int f = 0; f < 2; ++f) {
-        const std::vector<IdxRun>& rl = *lists[f];
+        const HVec<IdxRun>& rl = *lists[f];
         if (rl.empty()) continue;
         IdxRun* d = ws.get_n<IdxRun>(rl.size());
         h2d(d, rl, s);
@@ -1175,7 +1175,7 @@ static void upload_operator(rad_htree* h, const std::vector<IdxRun>& near_runs, 
 }
 
 template <class S, class CT>
-static void launch_dense_fill(rad_htree* h, const std::vector<DenseWork>& work, cudaStream_t s) {
+static void launch_dense_fill(rad_htree* h, const HVec<DenseWork>& work, cudaStream_t s) {
     if (work.empty()) return;
     Scratch ws(s);
     DenseWork* d_work = ws.get_n<DenseWork>(work.size());
@@ -1186,7 +1186,7 @@ static void launch_dense_fill(rad_htree* h, const std::vector<DenseWork>& work, 
 }
 
 template <class CT, class S>
-static void launch_factor_fill(rad_htree* h, const std::vector<UWork>& uw, const std::vector<VWork>& vw,
+static void launch_factor_fill(rad_htree* h, const HVec<UWork>& uw, const HVec<VWork>& vw,
                                const CT* const* Ubase, const CT* const* Vbase, cudaStream_t s, void* pool = nullptr) {
     S* dst = static_cast<S*>(pool ? pool : h->far_pool.p);
     Scratch ws(s);
@@ -1463,6 +1463,7 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
             part_blocks[q].push_back(b);
         }
     }
+    auto hs_parts = std::make_unique<HostScope>("host_plan_parts");
     parallel_parts(parts, [&](int q) {
         for (int b : part_cross[q]) {
             const BlockH& bk = h->blocks[b];
@@ -1470,11 +1471,13 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
         }
         for (int b : part_blocks[q]) plan_block(b, pp[q], cut[q], cut[q + 1], true);
     });
+    hs_parts.reset();
+    auto hs_merge = std::make_unique<HostScope>("host_plan_merge");
     // concatenation of the parts' lists in part order (copies in parallel)
-    std::vector<DenseWork> dwork;
-    std::vector<UWork> uwork;
-    std::vector<VWork> vwork;
-    std::vector<IdxRun> near_runs, far_runs;
+    HVec<DenseWork> dwork;
+    HVec<UWork> uwork;
+    HVec<VWork> vwork;
+    HVec<IdxRun> near_runs, far_runs;
     int64_t near_e = 0, far_u = 0, far_v = 0;
     int maxk = 0;
     {
@@ -1511,6 +1514,7 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
             }
         });
     }
+    hs_merge.reset();
     long long noff = 0, foff = 0;
     for (auto& t : tiles) {
         t.noff = noff;
@@ -1605,7 +1609,7 @@ void load_dense_operator(rad_htree* h, const double* F_dev, cudaStream_t s) {
     h->blocks.assign(1, BlockH{0, 0, 0, n, 0, n, 0, -1, -1, 0});
     std::vector<int> tile_at;
     make_tiles(h, h->tiles_h, tile_at);
-    std::vector<IdxRun> near_runs, far_runs;
+    HVec<IdxRun> near_runs, far_runs;
     h->near_pieces.clear();
     h->far_pieces.clear();
     h->groups_h.clear();

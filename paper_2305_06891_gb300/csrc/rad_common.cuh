@@ -126,11 +126,35 @@ struct StageScope {
 };
 void* stage_alloc(size_t bytes);   // nullptr when no scope is active
 
+// Allocator whose value construction without arguments leaves trivially
+// constructible elements uninitialised: host work lists that are filled
+// right after resize() skip the zeroing pass.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+    template <class U>
+    struct rebind {
+        using other = NoInitAlloc<U>;
+    };
+    NoInitAlloc() = default;
+    template <class U>
+    NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+    template <class U, class... A>
+    void construct(U* p, A&&... a) {
+        ::new ((void*)p) U(std::forward<A>(a)...);
+    }
+    template <class U>
+    void construct(U* p) {
+        ::new ((void*)p) U;
+    }
+};
+template <class T>
+using HVec = std::vector<T, NoInitAlloc<T>>;
+
 // Host copy into page-locked staging; 8 threads from 8 MiB.
 void stage_copy(void* dst, const void* src, size_t bytes);
 
-template <class T>
-void h2d(T* dst, const std::vector<T>& v, cudaStream_t s) {
+template <class T, class Al>
+void h2d(T* dst, const std::vector<T, Al>& v, cudaStream_t s) {
     if (v.empty()) return;
     const size_t bytes = v.size() * sizeof(T);
     void* st = bytes >= 4096 ? stage_alloc(bytes) : nullptr;
@@ -373,7 +397,7 @@ struct rad_htree {
     int pivoting = RAD_ACA_PARTIAL;
     std::vector<rad::Tile> tiles_h;
     std::vector<rad::Group> groups_h;
-    std::vector<rad::Piece> near_pieces, far_pieces;   // per tile, in panel order
+    rad::HVec<rad::Piece> near_pieces, far_pieces;     // per tile, in panel order
     rad::DevBuf near_pool, far_pool;
     rad::DevBuf far_pool_acc;          // FP32 factors kept for refinement
     bool has_accurate = false;         // an accurate operator exists
