@@ -74,3 +74,51 @@ def test_box_cavity_with_hard_partial_pivot_blocks():
     f = geometry.facets_from_triangles(verts)
     yr = viewfactor.rows(f, rows) @ x
     assert np.abs(y[rows] - yr).max() <= 1e-6 * np.abs(yr).max()
+
+
+def test_icosphere6_bench_configuration_sampled_rows():
+    # the sphere workload exactly as bench.py times it: ACA tol 1e-6, BF16
+    # factors, FP32 accurate copy, refinement to 1e-8
+    import torch
+    c = cv.config3()
+    r = rad()
+    h = r.rad_build_htree(torch.as_tensor(c.verts, device="cuda"), 64, 1.0)
+    r.rad_compress_aca(h, 1e-6, 64, "partial", "bf16", "f32", accurate_dtype="f32")
+    f = geometry.facets_from_triangles(c.verts)
+    rows = _sample(c.n, seed=5)
+    B = np.concatenate([c.eps[:, None] * c.T ** 4, c.eps[:, None]], axis=1)
+    Y, info = r.rad_solve_reflection(h, c.eps, B, tol=1e-8, refine=True, inner_tol=1e-4)
+    assert info["status"] == 0 and info["max_rel_residual"] <= 1e-8
+    res = radiosity.residual_rows(f, c.eps, rows, Y, B)
+    assert np.linalg.norm(res) / np.linalg.norm(B[rows]) <= 1e-6
+
+
+def test_batch_of_256_boxes_bench_configuration_sampled_rows():
+    # the batch workload as bench.py times it: 256 boxes (3.2 M facets) in
+    # one handle, FP32, ACA tol 1e-6, one field per cavity, solve tol 1e-7;
+    # 512 sampled rows spread over the cavities, each checked against its
+    # own cavity's exact rows of Eq. (11)
+    import torch
+    cavs = cv.config4()
+    counts = np.array([c.n for c in cavs], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    verts = np.concatenate([c.verts for c in cavs])
+    eps = np.concatenate([c.eps for c in cavs])
+    eta = np.concatenate([SIGMA_SB * c.T[:, 0] ** 4 for c in cavs])
+    B = np.asfortranarray(np.stack([eps * eta, eps], axis=1))
+    r = rad()
+    h = r.rad_build_htree_batch(torch.as_tensor(verts, device="cuda"), counts, 64, 1.0)
+    r.rad_compress_aca(h, 1e-6, 64, "partial", "f32", "f32")
+    Y, info = r.rad_solve_reflection(h, eps, B, tol=1e-7, restart=30, max_iter=600)
+    assert info["status"] == 0 and info["max_rel_residual"] <= 1e-7
+    rows = _sample(int(off[-1]), seed=11)
+    cav_of = np.searchsorted(off, rows, side="right") - 1
+    worst = 0.0
+    for k in np.unique(cav_of):
+        o0, o1 = off[k], off[k + 1]
+        loc = rows[cav_of == k] - o0
+        fk = geometry.facets_from_triangles(cavs[k].verts)
+        res = radiosity.residual_rows(fk, eps[o0:o1], loc, Y[o0:o1], B[o0:o1])
+        for j in range(B.shape[1]):
+            worst = max(worst, float(np.abs(res[:, j]).max() / np.abs(B[o0:o1, j]).max()))
+    assert worst <= 1e-6, worst
