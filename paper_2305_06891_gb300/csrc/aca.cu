@@ -1346,10 +1346,6 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     }
     auto hs_plan = std::make_unique<HostScope>("host_plan");
     std::vector<int> job_of(h->blocks.size(), -1);
-    for (size_t a = 0; a < adm.size(); ++a) {
-        job_of[adm[a]] = (int)a;
-        h->blocks[adm[a]].rank = ranks[a];
-    }
     h->aca_entries = 0;
     for (auto e : evals) h->aca_entries += e;
 
@@ -1361,10 +1357,36 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     h->far_pieces.clear();
     h->groups_h.clear();
     int64_t fallback = 0;
-    // column groups of the low-rank blocks (k > 0), in order of first use
+    // row ranges of the parallel plan (below): cut at tile starts
+    const int nb = (int)h->blocks.size();
+    const int parts = nb >= 100000 ? 16 : nb >= 20000 ? 8 : 1;
+    std::vector<int> cut(parts + 1, 0);
+    cut[parts] = (int)h->n;
+    for (int q = 1; q < parts; ++q) {
+        int r = (int)((long long)h->n * q / parts);
+        while (r < (int)h->n && tile_at[r] < 0) ++r;
+        cut[q] = std::max(cut[q - 1], r);
+    }
+    std::vector<std::vector<int>> part_blocks(parts), part_cross(parts);
+    // one pass over the blocks: ACA job and rank, column group of the
+    // low-rank blocks (k > 0, groups in order of first use), row range
     std::vector<int> group_of_node(h->nodes.size(), -1);
-    for (int b = 0; b < (int)h->blocks.size(); ++b) {
+    size_t next_adm = 0;
+    for (int b = 0; b < nb; ++b) {
         BlockH& bk = h->blocks[b];
+        if (next_adm < adm.size() && adm[next_adm] == b) {
+            job_of[b] = (int)next_adm;
+            bk.rank = ranks[next_adm];
+            ++next_adm;
+        }
+        {
+            const int q = (int)(std::upper_bound(cut.begin(), cut.end(), bk.r0) - cut.begin()) - 1;
+            if (bk.r1 > cut[q + 1]) {
+                for (int q2 = q; q2 < parts && cut[q2] < bk.r1; ++q2) part_cross[q2].push_back(b);
+            } else {
+                part_blocks[q].push_back(b);
+            }
+        }
         bk.group = -1;
         bk.grow = 0;
         if (!bk.admissible) {
@@ -1440,29 +1462,10 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
             if (owner) o.vwork.push_back(VWork{bk.group, bk.grow, n, k, job_chunk[jb], 0, src_v[jb]});
         }
     };
-    const int nb = (int)h->blocks.size();
-    const int parts = nb >= 100000 ? 16 : nb >= 20000 ? 8 : 1;
-    std::vector<int> cut(parts + 1, 0);   // row cuts at tile starts
-    cut[parts] = (int)h->n;
-    for (int q = 1; q < parts; ++q) {
-        int r = (int)((long long)h->n * q / parts);
-        while (r < (int)h->n && tile_at[r] < 0) ++r;
-        cut[q] = std::max(cut[q - 1], r);
-    }
     // range q plans first the pieces of the blocks that cross into it from
     // other ranges (in block order), then its own blocks: per tile, the
     // same column order as one sequential pass over crossing blocks first
     std::vector<PlanPart> pp(parts);
-    std::vector<std::vector<int>> part_blocks(parts), part_cross(parts);
-    for (int b = 0; b < nb; ++b) {
-        const BlockH& bk = h->blocks[b];
-        const int q = (int)(std::upper_bound(cut.begin(), cut.end(), bk.r0) - cut.begin()) - 1;
-        if (bk.r1 > cut[q + 1]) {
-            for (int q2 = q; q2 < parts && cut[q2] < bk.r1; ++q2) part_cross[q2].push_back(b);
-        } else {
-            part_blocks[q].push_back(b);
-        }
-    }
     auto hs_parts = std::make_unique<HostScope>("host_plan_parts");
     parallel_parts(parts, [&](int q) {
         for (int b : part_cross[q]) {
