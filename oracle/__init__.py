@@ -19,12 +19,15 @@ aca         cross approximation, Eq. (30), with full and partial pivoting and
             the stopping rule of Eq. (31)
 hmatrix     block low-rank matrix built from the above, its matvec (§5.2)
 radiosity   reflection matrix Eq. (11), direct solve, facet flux Eq. (12)
+hlu         hierarchical LU of the reflection matrix with rank truncation
+            (§5.1) and its forward / backward substitution (§5.2)
 
 Pins (see ``tests/test_oracle_*.py``): closed-form parallel and perpendicular
 plate view factors, the sphere identity, the two-grey-planes flux Eq. (5),
 closed-cavity and uniform-temperature identities, energy conservation,
 brute-force tree invariants and a hand-derived 1-D block structure, exact
-rank-r ACA recovery and the cross identity of Eq. (30).
+rank-r ACA recovery and the cross identity of Eq. (30), the H-LU as the
+unique LU of C without truncation, its error following eps_rel with it.
 """
 
 SIGMA_SB = 5.670374419e-8
