@@ -592,6 +592,35 @@ static std::vector<int> order_desc(const std::vector<long long>& key) {
         a[i] = (int)i;
         k[i] = 0xffffffffu - (uint32_t)std::min<long long>(std::max<long long>(key[i], 0), 0xffffffffll);
     }
+    // Large inputs: each pass counts per chunk of the current order on host
+    // threads, takes offsets digit by digit and chunk by chunk (so equal
+    // digits keep their order), and scatters per chunk: the same stable
+    // passes as the sequential loop.
+    const int P = m >= 200000 ? 16 : 1;
+    if (P > 1) {
+        std::vector<uint32_t> cnt((size_t)P * 65536);
+        for (int pass = 0; pass < 2; ++pass) {
+            const int sh = 16 * pass;
+            std::fill(cnt.begin(), cnt.end(), 0u);
+            parallel_parts(P, [&](int t) {
+                uint32_t* c = &cnt[(size_t)t * 65536];
+                for (size_t i = m * t / P, e = m * (t + 1) / P; i < e; ++i) ++c[(k[a[i]] >> sh) & 0xffff];
+            });
+            uint32_t run = 0;
+            for (int d = 0; d < 65536; ++d)
+                for (int t = 0; t < P; ++t) {
+                    const uint32_t v = cnt[(size_t)t * 65536 + d];
+                    cnt[(size_t)t * 65536 + d] = run;
+                    run += v;
+                }
+            parallel_parts(P, [&](int t) {
+                uint32_t* c = &cnt[(size_t)t * 65536];
+                for (size_t i = m * t / P, e = m * (t + 1) / P; i < e; ++i) b[c[(k[a[i]] >> sh) & 0xffff]++] = a[i];
+            });
+            a.swap(b);
+        }
+        return a;
+    }
     std::vector<int> cnt(65537);
     for (int pass = 0; pass < 2; ++pass) {
         const int sh = 16 * pass;
@@ -914,6 +943,7 @@ void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>
                 std::vector<long long>& evals, std::vector<std::vector<double>>* unused, Scratch& ws,
                 CT*& Us, CT*& Vs, cudaStream_t s) {
     (void)unused;
+    auto hs_prep = std::make_unique<HostScope>("host_aca_prep");
     const int nj = (int)jobs.size();
     long long su = 0, sv = 0, sused = 0;
     for (auto& j : jobs) {
@@ -934,6 +964,7 @@ void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>
     int* d_rank = ws.get_n<int>(nj);
     long long* d_evals = ws.get_n<long long>(nj);
     const Geo g = geo_view(h->geo.as<double>(), h->geo32.as<float>(), h->n);
+    hs_prep.reset();
     if (p->pivoting == RAD_ACA_FULL) {
         std::vector<long long> offR(nj);
         long long sr = 0;
@@ -1305,6 +1336,7 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
                 CT* Us = nullptr;
                 CT* Vs = nullptr;
                 launch_aca<CT>(h, p, cj, cr, ce, nullptr, cws, Us, Vs, s);
+                HostScope hs_cp("host_aca_compact_prep");
                 long long tu = 0, tv = 0;
                 for (size_t q = 0; q < cj.size(); ++q) {
                     cu[q] = tu;
