@@ -151,6 +151,39 @@ def hlu(node: HNode, tol: float) -> None:
     hlu(A22, tol)
 
 
+def matvec(node: HNode, x: np.ndarray) -> np.ndarray:
+    """Block times vector following the block structure: U (V^T x) in a
+    low-rank leaf, D x in a dense one."""
+    if node.is_leaf:
+        return node.U @ (node.V.T @ x) if node.low_rank else node.D @ x
+    n1 = node.children[0][0].c1 - node.c0
+    top = matvec(node.children[0][0], x[:n1]) + matvec(node.children[0][1], x[n1:])
+    bot = matvec(node.children[1][0], x[:n1]) + matvec(node.children[1][1], x[n1:])
+    return np.concatenate([top, bot])
+
+
+def forward(node: HNode, b: np.ndarray) -> np.ndarray:
+    """L y = b on a factored diagonal pair (unit lower L): y1 from L11,
+    then L22 y2 = b2 - L21 y1 (§5.2, recursively)."""
+    if node.is_leaf:
+        return solve_triangular(_lower_unit(node.D), b, lower=True, unit_diagonal=True)
+    m1 = node.children[0][0].r1 - node.r0
+    y1 = forward(node.children[0][0], b[:m1])
+    y2 = forward(node.children[1][1], b[m1:] - matvec(node.children[1][0], y1))
+    return np.concatenate([y1, y2])
+
+
+def backward(node: HNode, y: np.ndarray) -> np.ndarray:
+    """U x = y on a factored diagonal pair: x2 from U22, then
+    U11 x1 = y1 - U12 x2 (§5.2, recursively)."""
+    if node.is_leaf:
+        return solve_triangular(np.triu(node.D), y, lower=False)
+    m1 = node.children[0][0].r1 - node.r0
+    x2 = backward(node.children[1][1], y[m1:])
+    x1 = backward(node.children[0][0], y[:m1] - matvec(node.children[0][1], x2))
+    return np.concatenate([x1, x2])
+
+
 @dataclass
 class HLU:
     """L U ~ C in tree order (perm: tree position -> facet)."""
@@ -168,6 +201,15 @@ class HLU:
         bt = np.asarray(b, dtype=np.float64)[self.perm]
         y = solve_triangular(L, bt, lower=True, unit_diagonal=True)
         xt = solve_triangular(U, y, lower=False)
+        x = np.empty_like(xt)
+        x[self.perm] = xt
+        return x
+
+    def solve_blocks(self, b: np.ndarray) -> np.ndarray:
+        """The same solve through the block structure: forward and backward
+        substitution by pairs, low-rank blocks applied as U (V^T x)."""
+        bt = np.asarray(b, dtype=np.float64)[self.perm]
+        xt = backward(self.root, forward(self.root, bt))
         x = np.empty_like(xt)
         x[self.perm] = xt
         return x

@@ -91,3 +91,16 @@ def test_truncation_keeps_the_smallest_admissible_rank():
         U, V = hlu.truncate_dense(M, tol)
         assert U.shape[1] == r, (tol, U.shape[1])
         assert np.linalg.norm(M - U @ V.T) <= tol * total * (1 + 1e-9) + 1e-14
+
+
+@pytest.mark.parametrize("tol", [0.0, 1e-5])
+def test_block_substitution_equals_dense_substitution(cube, tol):
+    """§5.2: forward and backward substitution through the block structure
+    (low-rank blocks applied as U (V^T x)) add no approximation: they equal
+    the dense triangular solves with the same factors."""
+    f, F, eps, C = cube
+    h = hlu.factor(F, eps, f.c, n_min=16, eta=1.0, tol=tol)
+    b = np.random.default_rng(6).uniform(size=f.size)
+    x_dense = h.solve(b)
+    x_blocks = h.solve_blocks(b)
+    assert np.linalg.norm(x_blocks - x_dense) <= 1e-12 * np.linalg.norm(x_dense)
