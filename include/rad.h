@@ -294,8 +294,10 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
  * the library's load until the process exits) instead of allocations:
  *   - x and y must be device arrays (host arrays are rejected: staging them
  *     would allocate);
- *   - it needs 2 * round256(s * n * nrhs) + round256(s * sum_rank * nrhs)
- *     bytes, s = 8 for an FP64 operator and 4 otherwise (sum_rank from
+ *   - it needs round256(s * n * p) + round256(s * n * nrhs)
+ *     + round256(s * (max(sum_rank, 1) * p + (nrhs == 1 ? n : 0))) bytes,
+ *     s = 8 for an FP64 operator and 4 otherwise, p = 1 for one column and
+ *     nrhs rounded up to a multiple of 4 otherwise (sum_rank from
  *     rad_htree_get_stats); larger calls return RAD_ELIMIT;
  *   - the first call on each device looks up the array's device address
  *     (make that first call before any stream capture);

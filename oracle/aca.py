@@ -4,7 +4,7 @@ The method builds row and column pivot sets R, C and the cross
 X ~ X(:,C) X(R,C)^-1 X(R,:)  (Eq. 30), written as rank-one terms
 X ~ U V^T = sum_k u_k v_k^T, until the block satisfies
 ||X - U V^T|| / ||X|| <= eps_rel  (Eq. 31; Frobenius norm, which is the norm
-of the paper's Table 1).
+of the paper's Table 2, §6.3).
 
 Two pivoting rules (§1: the paper uses full pivoting and names partial
 pivoting as the faster, less reliable alternative):
@@ -17,18 +17,12 @@ pivoting as the faster, less reliable alternative):
   row 0.  Column pivot: argmax |residual row| (ties: lowest).  A residual row
   whose largest modulus is <= max(1e-300, 1e-14 * largest pivot so far) is
   marked used and the lowest unused row is tried instead.  Next row: argmax
-  |u_k| over unused rows.  Candidate stop when |u_k| |v_k| <= eps_rel ||S_k||_F,
-  with ||S_k||_F^2 = ||S_{k-1}||_F^2 + 2 sum_{l<k} (u_k.u_l)(v_k.v_l)
-  + |u_k|^2 |v_k|^2.
-  The paper warns that partial pivoting is less reliable; that candidate stop
-  can fire while rows the pivots never visited are still poorly
-  approximated.  So a candidate stop is verified (at most 4 times per block)
-  on m + n sampled residual entries, one in every row and one in every
-  column: (i, (i * 2654435761 + c * 40503 + 1) mod n) for each row i, then
-  ((j * 2246822519 + c * 40503 + 3) mod m, j) for each column j (c = checks
-  done so far).  ||R||_F^2 is estimated as (m n / (m + n)) sum_s r_s^2; if
-  that exceeds eps_rel^2 ||S_k||_F^2 the iteration continues from the row of
-  the largest |r_s| (ties: the first sample).
+  |u_k| over unused rows.  Stop when |u_k| |v_k| <= eps_rel ||S_k||_F, with
+  ||S_k||_F^2 = ||S_{k-1}||_F^2 + 2 sum_{l<k} (u_k.u_l)(v_k.v_l)
+  + |u_k|^2 |v_k|^2, the Frobenius norm of the current cross.  This is the
+  plain rule and nothing more: the stop is an estimate, and (as the paper
+  warns) it can fire while rows the pivots never visited are still poorly
+  approximated, so only full pivoting meets Eq. (31) exactly.
 
 Both return (U, V, converged) with U (m, k), V (n, k).  ``converged`` is
 False when the rank cap was reached first (the caller then stores the block
@@ -78,7 +72,6 @@ def aca_partial(get_row, get_col, m: int, n: int, tol: float, max_rank: int,
     used = np.zeros(m, dtype=bool)
     norm2_S = 0.0
     scale = 0.0
-    checks = 0
     i = 0
     while True:
         if len(us) >= max_rank:
@@ -111,61 +104,11 @@ def aca_partial(get_row, get_col, m: int, n: int, tol: float, max_rank: int,
         us.append(u)
         vs.append(v)
         if math.sqrt(uu) * math.sqrt(vv) <= tol * math.sqrt(max(norm2_S, 0.0)):
-            if checks >= MAX_CHECKS:
-                return _stack(us, m), _stack(vs, n), True
-            est2, worst_row = _sampled_residual(get_row, us, vs, m, n, checks)
-            checks += 1
-            if est2 <= tol * tol * norm2_S:
-                return _stack(us, m), _stack(vs, n), True
-            if stats is not None:
-                stats["rejected_stops"] = stats.get("rejected_stops", 0) + 1
-            if used[worst_row]:
-                free = np.flatnonzero(~used)
-                if free.size == 0:
-                    return _stack(us, m), _stack(vs, n), True
-                worst_row = int(free[0])
-            i = worst_row
-            continue
+            return _stack(us, m), _stack(vs, n), True
         cand = np.where(used, -1.0, np.abs(u))
         if not (cand >= 0).any():
             return _stack(us, m), _stack(vs, n), True
         i = int(np.argmax(cand))
-
-
-MAX_CHECKS = 4
-# hash multipliers of the verification samples (odd 32-bit constants)
-ROW_MULT = 2654435761
-COL_MULT = 2246822519
-CHECK_MULT = 40503
-
-
-def sample_positions(m: int, n: int, check: int):
-    """Rows and columns of the m + n residual samples of verification
-    ``check``: one column per row, (i * ROW_MULT + check * CHECK_MULT + 1)
-    mod n for row i, then one row per column, (j * COL_MULT + check *
-    CHECK_MULT + 3) mod m for column j, so that every row and every column of
-    the block is probed."""
-    i = np.arange(m, dtype=np.int64)
-    j = np.arange(n, dtype=np.int64)
-    cols_a = (i * ROW_MULT + check * CHECK_MULT + 1) % n
-    rows_b = (j * COL_MULT + check * CHECK_MULT + 3) % m
-    return np.concatenate([i, rows_b]), np.concatenate([cols_a, j])
-
-
-def _sampled_residual(get_row, us, vs, m, n, check):
-    """(m n / (m + n)) sum of squared residual samples (an unbiased estimate
-    of ||X - U V^T||_F^2 under uniform sampling) and the row of the largest
-    |residual| (ties: the first sample)."""
-    rows, cols = sample_positions(m, n, check)
-    r = np.empty(len(rows))
-    for s in range(len(rows)):
-        i, j = int(rows[s]), int(cols[s])
-        x = float(np.asarray(get_row(i))[j])
-        for u_l, v_l in zip(us, vs):
-            x -= u_l[i] * v_l[j]
-        r[s] = x
-    est2 = (m * n / len(rows)) * float((r * r).sum())
-    return est2, int(rows[int(np.argmax(np.abs(r)))])
 
 
 def truncate(U: np.ndarray, V: np.ndarray, tol: float):

@@ -7,22 +7,25 @@ U V^T for an admissible pair) or splits into the four pairs of its
 children.  The identity only touches the dense diagonal leaves, and Lambda
 scales the rows of every block (§5 opening paragraphs).
 
-The factorisation C ~ L U follows the four steps of §5.1 on every diagonal
-pair (tau, tau) with children tau1, tau2:
-  1. L11 U11 = C11                    (recursively; dense LU in a leaf)
-  2. U12 = L11^-1 C12                 (forward substitution)
-  3. L21 = C21 U11^-1                 (backward substitution)
-  4. L22 U22 = C22 - L21 U12          (recursively)
-Each block computed in steps 2-4 is brought back into the format of its
-pair, with the ranks of its low-rank leaves truncated at the relative
-accuracy eps_rel by the singular-value decay (§5.1, last paragraph).  This
-oracle forms the block products and substitutions of steps 2-4 exactly (as
-dense arrays) and then truncates them leaf by leaf, which is the defined
-result of "product, then truncation into the block format"; it is slow and
-meant for small N.  The dense leaf LU has no pivoting (C is strictly
-diagonally dominant by rows whenever max(1 - eps_i) * max_i sum_j F_ij < 1,
-which holds for the cavities of the tests).  L is unit lower triangular; L
-and U are stored together, LAPACK style, in the same block structure.
+The factorisation C ~ L U (§5.1) recurses on the diagonal cluster pairs.
+A diagonal pair that is a leaf gets a dense LU.  A diagonal pair with
+children tau1, tau2 is treated as a 2 x 2 block matrix: its upper-left
+diagonal block is factorised first (recursively); the off-diagonal blocks
+then become the off-diagonal factors by one triangular solve each (the
+upper-right block against the unit lower factor of the upper-left block,
+the lower-left block against its upper factor from the right); finally the
+lower-right block is replaced by its Schur complement (the lower-left
+factor times the upper-right factor subtracted from it) and factorised
+recursively.  Every block produced this way is brought back into the block
+format of its pair, the ranks of its low-rank leaves truncated at the
+relative accuracy eps_rel by the singular-value decay (§5.1).  This
+oracle forms those products and substitutions exactly (as dense arrays)
+and then truncates them leaf by leaf, which is the defined result of
+"product, then truncation into the block format"; it is slow and meant
+for small N.  The dense leaf LU has no pivoting (C is strictly diagonally
+dominant by rows whenever max(1 - eps_i) * max_i sum_j F_ij < 1, which
+holds for the cavities of the tests).  L is unit lower triangular; L and
+U are stored together, LAPACK style, in the same block structure.
 
 The solve x = U^-1 (L^-1 b) (§5.2) is the plain forward and backward
 substitution with those factors; like the product it adds no approximation.
@@ -136,18 +139,20 @@ def _dense_lu_nopivot(A: np.ndarray) -> np.ndarray:
 
 
 def hlu(node: HNode, tol: float) -> None:
-    """The four steps of §5.1 on a diagonal pair, in place (node ends up
-    holding L and U together)."""
+    """Block LU of a diagonal pair (§5.1), in place: node ends up holding
+    L and U together."""
     if node.is_leaf:
         node.D = _dense_lu_nopivot(node.D)
         return
     (A11, A12), (A21, A22) = node.children
-    hlu(A11, tol)                                              # step 1
+    hlu(A11, tol)
     LU11 = to_dense(A11)
     L11, U11 = _lower_unit(LU11), np.triu(LU11)
-    fill(A12, solve_triangular(L11, to_dense(A12), lower=True, unit_diagonal=True), tol)      # step 2
-    fill(A21, solve_triangular(U11.T, to_dense(A21).T, lower=True).T, tol)                    # step 3
-    fill(A22, to_dense(A22) - to_dense(A21) @ to_dense(A12), tol)                               # step 4
+    # off-diagonal factors: L11 U12 = C12 and L21 U11 = C21
+    fill(A12, solve_triangular(L11, to_dense(A12), lower=True, unit_diagonal=True), tol)
+    fill(A21, solve_triangular(U11.T, to_dense(A21).T, lower=True).T, tol)
+    # Schur complement of the upper-left block
+    fill(A22, to_dense(A22) - to_dense(A21) @ to_dense(A12), tol)
     hlu(A22, tol)
 
 

@@ -4,7 +4,9 @@ matrix-vector product (§5.2).
 Build: cluster tree (Algorithm 1), block tree (Algorithm 2); inadmissible
 leaf blocks are stored dense (entries by Eq. 10, centroid rule); admissible
 blocks are approximated by ACA (§4.3) to eps_rel, or stored dense when ACA
-hits its rank cap.
+hits its rank cap.  The default pivoting is full pivoting, the paper's
+choice (§1), which meets Eq. (31) exactly; the plain partial-pivot rule is
+available as ``pivoting="partial"``.
 
 Matvec: y = F x is the plain sum, over the leaf blocks sigma x tau, of
 D x_tau (dense) or U (V^T x_tau) (low rank), in tree order, followed by the
@@ -70,7 +72,7 @@ class HMatrix:
         return F
 
 
-def build(f: Facets, n_min: int, eta: float, tol: float, pivoting: str = "partial",
+def build(f: Facets, n_min: int, eta: float, tol: float, pivoting: str = "full",
           max_rank: int | None = None) -> HMatrix:
     tree = build_cluster_tree(f.c, n_min)
     perm = tree.perm

@@ -2,12 +2,15 @@
 // admissible blocks (§4.3, Eqs. 30-31), plus packing of the factors and the
 // row-tile tables used by the matrix-vector product.
 //
-// ACA runs one CTA per admissible block.  Rows and columns of the block are
-// evaluated on the fly from the tree-ordered facet geometry; the residual
-// row/column are written straight into the block's slot of the U/V scratch
-// (column-major, room for kmax columns); pivots come from block-wide
-// warp-shuffle argmax reductions (ties: lowest index); the Frobenius-norm
-// estimate of the cross and all dot products accumulate in FP64.
+// Partial-pivot ACA runs one warp per admissible block of at most 1024 rows
+// and 4096 columns and one 256-thread CTA per larger block, both in the same
+// launch.  Rows and columns of the block are evaluated on the fly from the
+// tree-ordered facet geometry; the residual row/column are written straight
+// into the block's slot of the U/V scratch (column-major, room for kmax
+// columns); pivots come from warp-shuffle (or block-wide) argmax reductions
+// (ties: lowest index); the Frobenius-norm estimate of the cross and the dot
+// products accumulate in FP64 (or a two-sum FP32 pair where the tolerance
+// allows FP32 arithmetic).
 //
 // Partial pivoting: first pivot row 0; column pivot = argmax |residual row|;
 // a residual row whose largest modulus is <= max(1e-300, 1e-14 x largest
@@ -16,7 +19,7 @@
 // |u_k| |v_k| <= tol ||S_k||_F with
 // ||S_k||^2 = ||S_{k-1}||^2 + 2 sum_{l<k} (u_k.u_l)(v_k.v_l) + |u_k|^2 |v_k|^2.
 // Partial pivoting is the less reliable rule (§1), and that candidate stop
-// can fire early, so it is verified (at most kMaxChecks times per block) on
+// can fire early, so this kernel (beyond the paper's plain rule) verifies it (at most kMaxChecks times per block) on
 // m + n residual entries, one in every row and one in every column: sample
 // s < m is (s, (s * 2654435761 + c * 40503 + 1) mod n), sample m + j is
 // ((j * 2246822519 + c * 40503 + 3) mod m, j), c = checks so far; if

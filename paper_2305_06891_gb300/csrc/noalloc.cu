@@ -78,9 +78,14 @@ extern "C" int rad_hmatvec_noalloc(const rad_htree* h, int32_t dtype, const void
         const int nr = (int)nrhs;
         const bool op64 = h->op_is_f64();
         const size_t osz = op64 ? 8 : 4;
-        const size_t bx = round256(osz * (size_t)n * nr);
+        // the same layout as rad_hmatvec: tree-order X rows padded to
+        // tree_ld(nrhs) columns (16-byte rows for the many-column kernels),
+        // Y compact, then the V^T X workspace
+        const int ldp = tree_ld(nr);
+        const size_t bx = round256(osz * (size_t)n * ldp);
+        const size_t by = round256(osz * (size_t)n * nr);
         const size_t bt = round256(apply_workspace_bytes(h, nr));
-        const size_t need = 2 * bx + bt;
+        const size_t need = bx + by + bt;
         if (need > kRadNoAllocScratchBytes) {
             char msg[256];
             std::snprintf(msg, sizeof msg,
@@ -92,9 +97,9 @@ extern "C" int rad_hmatvec_noalloc(const rad_htree* h, int32_t dtype, const void
         unsigned char* base = static_cast<unsigned char*>(noalloc_scratch());
         void* X = base;
         void* Y = base + bx;
-        void* T = base + 2 * bx;
-        gather_user_to_tree(h, dtype, x, ldx, nr, X, nr, op64, s);
-        apply_tree(h, X, nr, Y, nr, nr, Epi{kStore, nullptr, nullptr, nullptr, 0}, T, s);
+        void* T = base + bx + by;
+        gather_user_to_tree(h, dtype, x, ldx, nr, X, ldp, op64, s);
+        apply_tree(h, X, ldp, Y, nr, nr, Epi{kStore, nullptr, nullptr, nullptr, 0}, T, s);
         scatter_tree_to_user(h, Y, nr, nr, op64, dtype, y, ldy, s);
         return RAD_OK;
     } catch (const Error& e) {

@@ -41,7 +41,7 @@ def test_truncation_error_follows_eps_rel(cube, tol):
     L, U = h.factors()
     Ct = C[np.ix_(h.perm, h.perm)]
     rel = np.linalg.norm(L @ U - Ct) / np.linalg.norm(Ct)
-    # every block of steps 2-4 and every admissible block of C is truncated
+    # every block the factorisation produces and every admissible block of C is truncated
     # at tol relative to itself; over the few levels of this tree the
     # factorisation error stays within a small multiple of tol
     assert rel <= 10 * tol, rel

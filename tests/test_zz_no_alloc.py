@@ -3,8 +3,9 @@
 It exists for callers that cannot let this library allocate device memory
 (for example a serving engine that has reserved the GPU's memory for its own
 pool).  Here it is called through the C ABI and compared with rad_hmatvec,
-the allocating entry point, on two calls in a row (the second call reuses the
-fixed scratch the first one left behind).  This file is collected last on
+the allocating entry point, on several calls in a row (each call reuses the
+fixed scratch the one before left behind), with 1, 3, 6 and 65 columns so
+that every kernel family of the product runs through the fixed scratch.  This file is collected last on
 purpose.
 """
 import ctypes
@@ -39,7 +40,9 @@ def test_noalloc_matches_allocating_product_on_two_calls(dtype):
     n = h.n
     stream = torch.cuda.current_stream().cuda_stream
     gen = torch.Generator(device="cuda").manual_seed(5)
-    for call, nrhs in enumerate((1, 3)):
+    # one column, the 2-4 column streaming kernels, and the panel GEMMs of
+    # 5 or more columns (6 and 65: padded rows, more than one column chunk)
+    for call, nrhs in enumerate((1, 3, 6, 65)):
         X = torch.rand((nrhs, n), device="cuda", dtype=tdt, generator=gen).t()    # column-major
         ref = rad.rad_hmatvec(h, X)
         Y = torch.full((nrhs, n), float("nan"), device="cuda", dtype=tdt).t()
