@@ -2,22 +2,35 @@
 """Benchmark: flux solves per second of the block low-rank cavity-radiation
 hot path on one GB300 (or N independent replicas, one per GPU).
 
-Workload (the closed-cylinder cavity): 19,936 inward-facing triangles
-(R = 1, H = 4), emissivity U[0.3, 0.9], 64 temperature fields U[300, 1200] K,
-leaf size 64, eta = 1, ACA tol 1e-5 (partial pivoting with sampled
-verification), FP32 storage with FP32 accumulation, GMRES (restart 30) on the
-reflection system to a relative residual of 1e-7 with FP64 Krylov vectors.
+Headline workload (the closed-cylinder cavity): 19,936 inward-facing
+triangles (R = 1, H = 4), emissivity U[0.3, 0.9], 64 temperature fields
+U[300, 1200] K, leaf size 64, eta = 1, ACA tol 1e-5 (partial pivoting, stop
+checked on a residual probe in every row and column), FP32 storage with FP32
+accumulation, GMRES (restart 30) on the reflection system to a relative
+residual of 1e-7 with FP64 Krylov vectors.
 
-One step = the whole hot path on freshly uploaded inputs: facet geometry,
-cluster tree, block tree, dense blocks, ACA, then the flux solve for all 64
-fields (GMRES on 65 right-hand sides: 64 fields + the shared z = C^-1 eps,
-and the flux epilogue).  value = fields solved per second.
+One step = the whole hot path on inputs resident in device memory: facet
+geometry, cluster tree, block tree, dense blocks, ACA, then the flux solve
+for all 64 fields (GMRES on 65 right-hand sides: 64 fields + the shared
+z = C^-1 eps, and the flux epilogue).  value = fields solved per second.
 
 Timing: W warm-up steps, then K steps between a barrier + synchronize; each
 step is bracketed by CUDA events on the launching stream, and a 256 MiB
-buffer is written between steps to flush L2 (129 MB).  The per-kernel
-profile (CUDA events inside librad) gives the dominant kernel's duration for
-the roofline; nvidia-smi samples clocks during the timed steps.
+buffer is written between steps to flush L2 (129 MB).  The timed steps run
+without instrumentation; a separate profiled pass of the same steps (CUDA
+events around every library kernel, on its launch stream) gives the kernel
+table and the dominant kernel's roofline.  nvidia-smi samples clocks during
+the timed steps.
+
+Accuracy: the GPU flux and product against the full dense FP64 oracle (all
+19,936^2 entries, LAPACK LU), whose timed phases are also the CPU baseline.
+
+The default run adds the other workloads as keys of the same line:
+``workloads.sphere_mixed`` (level-6 icosphere, 81,920 facets, BF16 factors +
+refinement), ``workloads.batch`` (256 boxes, 3.21 M facets, one handle) and
+``workloads.served`` (Poisson stream of 200 requests/s on 12 resident
+cavities, continuous batching, p50/p99 latency), each with its plain FP64 GPU
+path and its accuracy against exact oracle rows.
 
 --impl reference times the FP64 CPU oracle (dense assembly, LU, flux) on the
 host cores on a bounded sample of the same workload, extrapolated to the
@@ -29,6 +42,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -81,6 +95,10 @@ def select_workload(name: str):
     LEAF, ETA, ACA_TOL, SOLVE_TOL = W["leaf"], W["eta"], W["aca_tol"], W["solve_tol"]
 
 
+def workload_key() -> str:
+    return next(k for k, v in WORKLOADS.items() if v is W)
+
+
 class Work:
     """The workload's inputs: one cavity, or a batch concatenated facet-wise."""
 
@@ -118,7 +136,8 @@ def compress(rad, h):
 def solve(rad, h, eps, T, q=None):
     return rad.rad_solve_flux(h, eps, T, SIGMA, tol=SOLVE_TOL, restart=RESTART, max_iter=600, q=q,
                               refine=W["refine"], inner_tol=1e-4)
-SM_COUNT = 152
+
+
 FP32_LANES_PER_SM = 128
 
 
@@ -130,6 +149,28 @@ def load_peaks():
         return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
     except Exception:
         return 6800.0, 2070.0, "fallback"
+
+
+def sm_count(dev=None) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(dev if dev is not None else 0).multi_processor_count)
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip() + f" ({platform.machine()})"
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
 
 
 # ---------------------------------------------------------------- clocks
@@ -199,8 +240,29 @@ def job_value(world: int, steps: int, total_ms: float, solves_per_step: int | No
     return world * per * steps / (total_ms * 1e-3)
 
 
+def timed_steps(step, steps, stream, flush):
+    """CUDA-event time of each of `steps` calls of step(); L2 flushed before
+    each.  Returns (times_ms, last result)."""
+    import torch
+    times, res = [], None
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        if res is not None and hasattr(res[0], "free"):
+            res[0].free()
+    return times, res
+
+
 # ---------------------------------------------------------------- our arm
-def run_ours(args, rank: int, world: int):
+def run_ours(args, rank: int, world: int, profile_steps: int | None = None, e2e: bool = True):
+    """The timed steps (uninstrumented), then a profiled pass of the same
+    steps on rank 0.  Returns the measurements."""
     import torch
     import paper_2305_06891_gb300 as rad
 
@@ -208,26 +270,22 @@ def run_ours(args, rank: int, world: int):
     torch.cuda.set_device(dev)
     cav = Work(W)
     n = cav.n
-    T_h = np.asfortranarray(cav.T)
     verts_d = torch.as_tensor(cav.verts, device=dev)
     eps_d = torch.as_tensor(cav.eps, device=dev)
     T_d = torch.as_tensor(cav.T, device=dev).t().contiguous().t()
     q_d = torch.empty((FIELDS, n), dtype=torch.float64, device=dev).t()
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    stats = {}
 
-    def step(verts=verts_d, eps=eps_d, T=T_d, q=q_d):
-        h = build(rad, cav, verts)
+    def step():
+        h = build(rad, cav, verts_d)
         compress(rad, h)
-        q, info = solve(rad, h, eps, T, q=q)
+        q, info = solve(rad, h, eps_d, T_d, q=q_d)
+        stats.update(rad.rad_htree_get_stats(h))
         return h, info
 
-    for _ in range(args.warmup):
-        h, info = step()
-        h.free()
-    torch.cuda.synchronize()
-
-    dist = None
+    timed_steps(step, args.warmup, stream, flush)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -235,36 +293,28 @@ def run_ours(args, rank: int, world: int):
     clocks = ClockSampler(dev.index)
     clocks.start()
     launches0 = rad.rad_launch_count()
-    rad.rad_profile_enable(True)
-    times, infos = [], []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        h, info = step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        infos.append(info)
-        st = rad.rad_htree_get_stats(h)
-        h.free()
-    torch.cuda.synchronize()
-    prof = rad.rad_profile_read()
-    rad.rad_profile_enable(False)
+    times, (_, info) = timed_steps(step, args.steps, stream, flush)
     launches = rad.rad_launch_count() - launches0
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(times), dev) if world > 1 else sum(times)
 
-    # ---- one-off measurements (not in the timed region)
+    # ---- profiled pass (not timed for the value): per-kernel CUDA events
+    prof, prof_times = {}, []
+    if rank == 0:
+        k = profile_steps or min(args.steps, 5)
+        rad.rad_profile_enable(True)
+        prof_times, _ = timed_steps(step, k, stream, flush)
+        torch.cuda.synchronize()
+        prof = rad.rad_profile_read()
+        rad.rad_profile_enable(False)
     extra = {}
     if rank == 0:
-        extra = measure_extras(args, rad, torch, dev, cav, verts_d, eps_d, T_d, flush, stream)
-    return dict(times=times, total_ms=total_ms, infos=infos, stats=st, prof=prof, launches=launches, clocks=clk,
-                extra=extra, n=n, cav=cav, T_h=T_h)
+        extra = measure_extras(args, rad, torch, dev, cav, verts_d, flush, stream, e2e=e2e)
+    return dict(times=times, total_ms=total_ms, info=info, stats=stats, prof=prof, prof_times=prof_times,
+                launches=launches, clocks=clk, extra=extra, n=n, cav=cav, dev=dev)
 
 
-def measure_extras(args, rad, torch, dev, cav, verts_d, eps_d, T_d, flush, stream):
+def measure_extras(args, rad, torch, dev, cav, verts_d, flush, stream, e2e=True):
     out = {}
     n = cav.n
     # single-RHS block matvec on the bench operator (HBM bound): plain
@@ -272,8 +322,9 @@ def measure_extras(args, rad, torch, dev, cav, verts_d, eps_d, T_d, flush, strea
     h = build(rad, cav, verts_d)
     compress(rad, h)
     st = rad.rad_htree_get_stats(h)
-    x = torch.as_tensor(SIGMA * cav.T[:, 0] ** 4, device=dev, dtype=torch.float32)
-    y = torch.empty(n, dtype=torch.float32, device=dev)
+    fdt = torch.float64 if W["near"] == "f64" else torch.float32
+    x = torch.as_tensor(SIGMA * cav.T[:, 0] ** 4, device=dev, dtype=fdt)
+    y = torch.empty(n, dtype=fdt, device=dev)
     op_bytes = st["bytes_near"] + st["bytes_far"]   # the operator the product streams
     vec_bytes = 4 * (2 * n + 2 * st["sum_rank"])
     hbm, _, src = load_peaks()
@@ -323,6 +374,7 @@ def measure_extras(args, rad, torch, dev, cav, verts_d, eps_d, T_d, flush, strea
     if not args.no_fp64:
         sample = cav.cavs[:16] if cav.batch else cav.cavs
         ts64 = []
+        info = None
         for it in range(2):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -345,24 +397,25 @@ def measure_extras(args, rad, torch, dev, cav, verts_d, eps_d, T_d, flush, strea
                             "cavities": len(sample), "gmres_iters": info["iters"],
                             "max_rel_residual": info["max_rel_residual"]}
     # end to end through the C ABI with host buffers (copies inside)
-    verts_h = np.ascontiguousarray(cav.verts)
-    T_h = np.asfortranarray(cav.T)
-    q_h = np.empty((n, FIELDS), order="F")
-    e2e = []
-    for it in range(max(2, min(args.steps, 5)) + 1):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        h = build(rad, cav, verts_h)
-        compress(rad, h)
-        solve(rad, h, cav.eps, T_h, q=q_h)
-        t1 = time.perf_counter()
-        h.free()
-        if it:
-            e2e.append(t1 - t0)
-    out["e2e"] = {"value": cav.solves / statistics.median(e2e), "unit": UNIT,
-                  "h2d_bytes_per_step": int(verts_h.nbytes + cav.eps.nbytes + T_h.nbytes),
-                  "d2h_bytes_per_step": int(q_h.nbytes), "ms_per_step": 1e3 * statistics.median(e2e)}
+    if e2e:
+        verts_h = np.ascontiguousarray(cav.verts)
+        T_h = np.asfortranarray(cav.T)
+        q_h = np.empty((n, FIELDS), order="F")
+        ts = []
+        for it in range(max(2, min(args.steps, 5)) + 1):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = build(rad, cav, verts_h)
+            compress(rad, h)
+            solve(rad, h, cav.eps, T_h, q=q_h)
+            t1 = time.perf_counter()
+            h.free()
+            if it:
+                ts.append(t1 - t0)
+        out["e2e"] = {"value": cav.solves / statistics.median(ts), "unit": UNIT,
+                      "h2d_bytes_per_step": int(verts_h.nbytes + cav.eps.nbytes + T_h.nbytes),
+                      "d2h_bytes_per_step": int(q_h.nbytes), "ms_per_step": 1e3 * statistics.median(ts)}
     return out
 
 
@@ -372,42 +425,39 @@ def measure_extras(args, rad, torch, dev, cav, verts_d, eps_d, T_d, flush, strea
 TRAFFIC = {("cylinder", "hmm_rows"): 284.72e6 + 6.27e6}
 
 
-def roofline(prof: dict, st: dict, steps: int, clocks: dict, nc: int):
-    """Dominant kernel of the timed steps and its roofline."""
+def roofline(prof: dict, st: dict, steps: int, nc: int, sms: int):
+    """Dominant kernel of the profiled steps and its roofline."""
     hbm, smax, src = load_peaks()
     if not prof:
         return None
     name, (cnt, ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    wl = next(k for k, v in WORKLOADS.items() if v is W)
-    traffic = TRAFFIC.get((wl, name)) if PRODUCT_PATH in (None, 0) else None
+    traffic = TRAFFIC.get((workload_key(), name)) if PRODUCT_PATH in (None, 0) else None
     avg_s = ms / cnt * 1e-3
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
+    fp32_peak = sms * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
+    note = f"FP32 FFMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz (of derived)"
+    base = {"kernel": name, "launches": cnt, "avg_ms": ms / cnt,
+            "measured": f"CUDA events around every launch on its stream, profiled pass of {steps} steps"}
     if name == "hmm_rows":
         flops = 2.0 * nc * (st["near_entries"] + st["far_u_entries"])
         ach = flops / avg_s / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": traffic, "launches": cnt, "avg_ms": ms / cnt,
-                "peak_note": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz (of derived)"}
+        return dict(base, bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
+                    traffic=traffic, peak_note=note)
     if name == "hmm_far_vt":
         flops = 2.0 * nc * st["far_v_entries"]
         ach = flops / avg_s / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None, "launches": cnt, "avg_ms": ms / cnt,
-                "peak_note": f"FP32 FFMA: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz"}
+        return dict(base, bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
+                    traffic=traffic, peak_note=note)
     if name in ("aca_partial", "near_assemble"):
         # view-factor entry evaluations: ~ 24 FP32 + 3 FP64 operations each
         ents = st["aca_entries"] if name == "aca_partial" else st["near_entries"]
-        flops = 27.0 * ents / steps * steps
-        ach = flops / avg_s / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None, "launches": cnt, "avg_ms": ms / cnt,
-                "peak_note": "entry evaluations x 27 flops vs FP32 issue peak"}
+        ach = 27.0 * ents / avg_s / 1e12
+        return dict(base, bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
+                    traffic=None, peak_note="entry evaluations x 27 flops vs " + note)
     # vector-bound GMRES kernels and the rest: HBM
-    return {"kernel": name, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
-            "traffic": None, "launches": cnt, "avg_ms": ms / cnt}
+    return dict(base, bound="hbm", achieved=None, peak=hbm, unit="GB/s", frac=None, traffic=None)
 
 
-# ---------------------------------------------------------------- oracle arm
+# ---------------------------------------------------------------- oracle
 def oracle_step(work, rows_sample=1024, lu_n=3072, seed=0):
     """Seconds the FP64 oracle needs for one step of the workload (all its
     cavities and fields), measured on a bounded sample and extrapolated:
@@ -421,12 +471,13 @@ def oracle_step(work, rows_sample=1024, lu_n=3072, seed=0):
     return total, desc
 
 
-def _oracle_coeffs(cav, rows_sample, lu_n, seed):
+def _oracle_coeffs(cav, rows_sample, lu_n, seed, fields=None):
     """Time the oracle on one cavity: F assembly on `rows_sample` rows, and the
     direct solve + flux on its first `lu_n` facets.  Returns per-unit costs
     (seconds per F entry, per n^3 of the LU, per n^2 and column of a product)
     and a description."""
     from oracle import geometry, radiosity, viewfactor
+    fields = FIELDS if fields is None else fields
     n = cav.n
     f = geometry.facets_from_triangles(cav.verts)
     rng = np.random.default_rng(seed)
@@ -436,7 +487,7 @@ def _oracle_coeffs(cav, rows_sample, lu_n, seed):
     a = (time.perf_counter() - t0) / (rows_sample * n)
     sub = np.arange(lu_n)
     Fs = viewfactor.dense(f.subset(sub))
-    T = cav.T[sub, :FIELDS]
+    T = cav.T[sub, :fields]
     t0 = time.perf_counter()
     q, Y, z = radiosity.solve_flux(Fs, cav.eps[sub], T, SIGMA)
     t_solve = time.perf_counter() - t0
@@ -447,20 +498,130 @@ def _oracle_coeffs(cav, rows_sample, lu_n, seed):
     t_mm = time.perf_counter() - t0
     t_lu = max(t_solve - 2 * t_mm, 1e-9)
     b = t_lu / lu_n ** 3
-    c = t_mm / (lu_n ** 2 * (FIELDS + 1))
+    c = t_mm / (lu_n ** 2 * (fields + 1))
     desc = (f"F rows {rows_sample}/{n} of a {n}-facet cavity (assembly x n^2); direct solve + flux on its "
-            f"leading {lu_n} facets (LU x n^3, F@[Y z] x n^2); {FIELDS} field(s) per cavity")
+            f"leading {lu_n} facets (LU x n^3, F@[Y z] x n^2); {fields} field(s) per cavity")
     return a, b, c, desc
 
 
+def dense_oracle(work):
+    """The whole step by the FP64 oracle on the full cavity, timed by phase:
+    dense assembly of every F entry, the direct LU solve of C [Y z] = [eps
+    eta, eps] with the flux of Eq. (12), and the flux products F [Y z] alone
+    (timed again to split the LU from the products).  Also the exact
+    products F X (X = sigma T^4) for the accuracy check."""
+    from oracle import geometry, radiosity, viewfactor
+    c = work.cavs[0]
+    f = geometry.facets_from_triangles(c.verts)
+    t0 = time.perf_counter()
+    F = viewfactor.dense(f)
+    t_asm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    q, Y, z = radiosity.solve_flux(F, c.eps, c.T[:, :FIELDS], SIGMA)
+    t_solve = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _ = F @ np.concatenate([Y, z[:, None]], axis=1)
+    t_mm = time.perf_counter() - t0
+    Yx = F @ (SIGMA * c.T[:, :FIELDS] ** 4)
+    del F
+    phases = {"assembly_s": t_asm, "lu_solve_s": max(t_solve - t_mm, 0.0), "flux_products_s": t_mm}
+    return q, Yx, phases
+
+
+def single_thread_sample(n_sub=3072):
+    """The oracle phases on the leading `n_sub` facets of the workload's
+    (first) cavity in a child process limited to one BLAS thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(n_sub), "--workload", workload_key()]
+    try:
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:
+        return {"error": str(e)[:200]}
+
+
+def oracle_sample_main(n_sub):
+    from oracle import geometry, radiosity, viewfactor
+    c = Work(W).cavs[0]
+    sub = np.arange(min(n_sub, c.n))
+    f = geometry.facets_from_triangles(c.verts[sub])
+    t0 = time.perf_counter()
+    F = viewfactor.dense(f)
+    t_asm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    q, Y, z = radiosity.solve_flux(F, c.eps[sub], c.T[sub, :FIELDS], SIGMA)
+    t_solve = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _ = F @ np.concatenate([Y, z[:, None]], axis=1)
+    t_mm = time.perf_counter() - t0
+    m = len(sub)
+    N = c.n
+    # extrapolation to the full cavity: assembly and products x (N/m)^2, LU x (N/m)^3
+    full = t_asm * (N / m) ** 2 + max(t_solve - t_mm, 0.0) * (N / m) ** 3 + t_mm * (N / m) ** 2
+    print(json.dumps({"facets": m, "threads": 1, "assembly_s": t_asm, "lu_solve_s": max(t_solve - t_mm, 0.0),
+                      "flux_products_s": t_mm, "full_step_s_extrapolated": full,
+                      "value_extrapolated": FIELDS / full, "unit": UNIT}))
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def max_field_err(a, b):
+    return float(max(np.linalg.norm(a[:, j] - b[:, j]) / np.linalg.norm(b[:, j]) for j in range(b.shape[1])))
+
+
+def gpu_solutions(work, fac, near, acc, refine, recompress):
+    """Flux of all fields and the product F X (X = sigma T^4) from the GPU
+    with the given storage, as host arrays."""
+    import torch
+    import paper_2305_06891_gb300 as rad
+    dev = torch.device("cuda", torch.cuda.current_device())
+    h = build(rad, work, torch.as_tensor(work.verts, device=dev))
+    rad.rad_compress_aca(h, ACA_TOL, 64, "partial", fac, near, accurate_dtype=acc, recompress_tol=recompress)
+    q, info = rad.rad_solve_flux(h, work.eps, np.asfortranarray(work.T), SIGMA, tol=SOLVE_TOL, restart=RESTART,
+                                 max_iter=600, refine=refine, inner_tol=1e-4)
+    X = SIGMA * work.T ** 4
+    xdt = torch.float64 if near == "f64" else torch.float32
+    Y = rad.rad_hmatvec(h, torch.as_tensor(np.ascontiguousarray(X), device=dev, dtype=xdt)).cpu().numpy()
+    h.free()
+    return np.asarray(q), Y, info
+
+
+def dense_accuracy_and_baseline(work, args):
+    """Accuracy of the GPU flux and product against the full dense FP64
+    oracle, and the oracle's own timed phases (the CPU baseline)."""
+    cores = os.cpu_count()
+    q_ref, Y_ref, phases = dense_oracle(work)
+    step_s = sum(phases.values())
+    paths = {"ours": (W["factor"], W["near"], W["accurate"], W["refine"], RECOMPRESS)}
+    if not args.no_fp64:
+        paths["fp64_path"] = ("f64", "f64", None, False, 0.0)
+    acc = {"oracle": f"full dense FP64: all {work.n}^2 entries of F (centroid rule), LAPACK LU of C, Eq. (12)",
+           "error": "||v - v_ref||_2 / ||v_ref||_2 over all facets and fields; max over fields of the same per field"}
+    for label, (fac, near, a, refine, rc) in paths.items():
+        q, Y, info = gpu_solutions(work, fac, near, a, refine, rc)
+        acc[label] = {"flux_rel_err": rel_err(q, q_ref), "flux_rel_err_max_field": max_field_err(q, q_ref),
+                      "product_rel_err": rel_err(Y, Y_ref), "product_rel_err_max_field": max_field_err(Y, Y_ref),
+                      "solver_rel_residual": info["max_rel_residual"]}
+    st1 = single_thread_sample()
+    base = {"value": work.solves / step_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"the whole step on the full cavity, measured (not extrapolated): dense assembly of "
+                       f"{work.n}^2 entries, LU solve of {FIELDS + 1} right-hand sides, flux products; "
+                       f"numpy/LAPACK with {cores} threads"),
+            "cpu_model": cpu_model(), "phases_s": phases, "step_s": step_s, "single_thread": st1}
+    return acc, base
+
+
 def accuracy_vs_oracle(work, samples=512, cols=4, seed=7, no_fp64=False):
-    """Error of the GPU solves against the FP64 oracle, stated per result:
-    the reflection system C Y = B (Eq. 11) is solved on the GPU with the
-    workload's settings (and with the plain FP64 path), and the residual
-    B - C Y is evaluated on `samples` random rows with exact FP64 rows of F
-    from the oracle.  Reported as max over rows and columns of |r_i| / max|b|
-    per column (per cavity for a batch).  Runs on the host beside the CPU
-    baseline, outside the timed region."""
+    """Error of the GPU solves against the FP64 oracle on cavities too large
+    to assemble densely: the reflection system C Y = B (Eq. 11) is solved on
+    the GPU with the workload's settings (and with the plain FP64 path), and
+    the residual B - C Y is evaluated on `samples` random rows with exact
+    FP64 rows of F.  Reported as max over rows and columns of |r_i| / max|b|
+    per column (per cavity for a batch), with the error bound
+    ||e||_inf <= ||r||_inf / (1 - max(1 - eps) max_i sum_j F_ij) from the
+    exact row sums of the sampled rows."""
     import torch
     import paper_2305_06891_gb300 as rad
     from oracle import geometry, viewfactor
@@ -477,10 +638,14 @@ def accuracy_vs_oracle(work, samples=512, cols=4, seed=7, no_fp64=False):
     out = {"check": f"residual of C Y = B on {len(rows)} random rows with exact FP64 oracle rows of F; "
                     f"B = [eps*sigma*T^4 for {B.shape[1] - 1} field(s), eps]", "rows": int(len(rows))}
     exact = {}
+    smax = 0.0
     for k in np.unique(cav_of):
         c = work.cavs[k]
         loc = rows[cav_of == k] - work.off[k]
-        exact[k] = (rows[cav_of == k], viewfactor.rows(geometry.facets_from_triangles(c.verts), loc))
+        Fr = viewfactor.rows(geometry.facets_from_triangles(c.verts), loc)
+        exact[k] = (rows[cav_of == k], Fr)
+        smax = max(smax, float(Fr.sum(axis=1).max()))
+    rho = float((1.0 - work.eps).max())
     for label, (fac, near, acc, refine) in paths.items():
         h = build(rad, work, verts_d)
         rad.rad_compress_aca(h, ACA_TOL, 64, "partial", fac, near, accurate_dtype=acc,
@@ -493,7 +658,9 @@ def accuracy_vs_oracle(work, samples=512, cols=4, seed=7, no_fp64=False):
             o0, o1 = work.off[k], work.off[k + 1]
             R = B[glob] - (Y[glob] - (1.0 - work.eps[glob])[:, None] * (Fr @ Y[o0:o1]))
             worst = max(worst, float((np.abs(R).max(axis=0) / np.abs(B[o0:o1]).max(axis=0)).max()))
-        out[label] = {"max_rel_residual_exact_rows": worst, "solver_rel_residual": info["max_rel_residual"]}
+        out[label] = {"max_rel_residual_exact_rows": worst, "solver_rel_residual": info["max_rel_residual"],
+                      "error_bound": worst / max(1e-300, 1.0 - rho * smax)}
+    out["bound_terms"] = {"max_one_minus_eps": rho, "max_exact_row_sum": smax}
     return out
 
 
@@ -511,6 +678,7 @@ def run_reference(args):
     for _ in range(args.warmup):
         est(0)
     vals = []
+    desc = ""
     t0 = time.perf_counter()
     for s in range(args.steps):
         t, desc = est(s)
@@ -523,7 +691,9 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(work),
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores, "sample": desc,
-                             "wall_s": elapsed},
+                             "wall_s": elapsed, "cpu_model": cpu_model(),
+                             "note": "ms_per_step is the oracle's time for one whole step, extrapolated from the "
+                                     "bounded sample each step times"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -534,7 +704,8 @@ def config_dict(work=None):
          "recompress_tol": RECOMPRESS,
          "solve_tol": SOLVE_TOL, "gmres_restart": RESTART,
          "storage": f"{W['near']} near + {W['factor']} factors",
-         "accumulation": "f32 (operator), f64 (Krylov, inner products, residuals)",
+         "accumulation": ("f64 (operator, Krylov, inner products)" if W["near"] == "f64" else
+                          "f32 (operator), f64 (Krylov, inner products, residuals)"),
          "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
     if work is not None and work.batch:
         d["cavities"] = len(work.counts)
@@ -546,12 +717,53 @@ def config_dict(work=None):
     return d
 
 
-def run_served(args):
+def kernel_tables(prof, steps):
+    kern = {k: v for k, v in prof.items() if not k.startswith("host_")}
+    host = {k: v[1] / steps for k, v in prof.items() if k.startswith("host_")}
+    return ({k: v[1] / steps for k, v in sorted(kern.items(), key=lambda kv: -kv[1][1])},
+            dict(sorted(host.items(), key=lambda kv: -kv[1])), kern)
+
+
+def solver_workload_summary(name, args):
+    """A secondary solver workload (sphere-mixed or batch), measured like the
+    headline: timed steps, the plain FP64 GPU path, accuracy on exact oracle
+    rows, the oracle's bounded-sample time."""
+    import torch
+    select_workload(name)
+    steps = max(3, min(args.steps, 5 if name == "batch" else 10))
+    r = run_ours(argparse.Namespace(**dict(vars(args), steps=steps, warmup=2)), 0, 1, profile_steps=1,
+                 e2e=name != "batch")
+    ms = r["total_ms"] / steps
+    value = r["cav"].solves / (ms * 1e-3)
+    kern, host, _ = kernel_tables(r["prof"], 1)
+    d = {"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": 2,
+         "dtype": "f32" if W["factor"] == "f32" else "bf16+f32", "config": config_dict(r["cav"]),
+         "gpu_launches": int(r["launches"]), "clocks": r["clocks"],
+         "gmres": {k: r["info"][k] for k in ("iters", "restarts", "matvecs", "max_rel_residual", "refinements")},
+         "kernels_ms_per_step": dict(list(kern.items())[:8]),
+         "hmatvec": r["extra"].get("hmatvec")}
+    if "fp64_path" in r["extra"]:
+        d["fp64_path"] = r["extra"]["fp64_path"]
+        d["speedup_vs_fp64_gpu"] = value / r["extra"]["fp64_path"]["value"]
+    if "e2e" in r["extra"]:
+        d["e2e"] = r["extra"]["e2e"]
+    if not args.no_cpu_baseline:
+        t, desc = oracle_step(r["cav"])
+        d["cpu_baseline"] = {"value": r["cav"].solves / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": desc + " (extrapolated)"}
+        d["accuracy"] = accuracy_vs_oracle(r["cav"], no_fp64=args.no_fp64 or r["cav"].batch)
+    torch.cuda.empty_cache()
+    return d
+
+
+def served_summary(args, steps=None):
     """The served workload: one pass of the request stream warms the server
-    (builds every operator); each timed step replays the stream with its
+    (builds every operator); each timed pass replays the stream with its
     arrival times through the public server API (host arrays in and out)."""
     import torch
     import paper_2305_06891_gb300 as rad
+    select_workload("served")
+    steps = steps or args.steps
     pool, reqs = cv.config5_stream()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
@@ -578,7 +790,7 @@ def run_served(args):
     clocks.start()
     l0 = rad.rad_launch_count()
     walls, infos = [], []
-    for _ in range(args.steps):
+    for _ in range(steps):
         w, inf = stream()
         walls.append(w)
         infos += inf
@@ -636,11 +848,11 @@ def run_served(args):
             hh.free()
         fp64 = {"value": len(reqs) / t64, "unit": UNIT, "ms_per_request": 1e3 * t64 / len(reqs),
                 "note": "FP64 storage and arithmetic, operators resident, requests one after another"}
-    h2d = sum(e.nbytes + T.nbytes for _, _, e, T in reqs) * args.steps
+    h2d = sum(e.nbytes + T.nbytes for _, _, e, T in reqs) * steps
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16+f32", "data": "synthetic",
         "config": dict(config_dict(), requests_per_step=len(reqs), rate_per_s=200.0, cavities=len(pool),
                        facets=[int(v.shape[0]) for v in pool], slots=W["slots"], hbm_budget_gib=W["budget_gib"]),
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -653,7 +865,7 @@ def run_served(args):
         "roofline": {"kernel": "single_phase_a + single_phase_b (one product, largest pool operator)",
                      "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                      "traffic": None, "peak_kind": src, "avg_ms": kms},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d // args.steps),
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d // steps),
                 "d2h_bytes_per_step": int(sum(T.nbytes for _, _, _, T in reqs)),
                 "note": "the served value itself is end to end: host arrays through rad_server_submit/wait"},
         "max_rel_residual": float(max(i["max_rel_residual"] for i in infos)),
@@ -661,11 +873,13 @@ def run_served(args):
     if fp64:
         line["fp64_path"] = fp64
         line["speedup_vs_fp64_gpu"] = value / fp64["value"]
+        line["speedup_vs_fp64_gpu_at_capacity"] = (len(reqs) / burst) / fp64["value"]
     if not args.no_cpu_baseline:
         t, desc = served_oracle_estimate(pool, reqs)
         line["cpu_baseline"] = {"value": len(reqs) / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": desc}
-    print(json.dumps(line), flush=True)
+    torch.cuda.empty_cache()
+    return line
 
 
 def served_oracle_estimate(pool, reqs, seed=0):
@@ -677,10 +891,43 @@ def served_oracle_estimate(pool, reqs, seed=0):
     probe_v = next(v for v in pool if v.shape[0] == probe_n)
     rng = np.random.default_rng(seed)
     probe = cv.Cavity("probe", probe_v, rng.uniform(0.3, 0.9, probe_n), rng.uniform(300, 1200, (probe_n, 1)), {})
-    a, b, c, desc = _oracle_coeffs(probe, min(1024, probe_n), min(3072, probe_n), seed)
+    a, b, c, desc = _oracle_coeffs(probe, min(1024, probe_n), min(3072, probe_n), seed, fields=1)
     t = sum(a * pool[k].shape[0] ** 2 + b * pool[k].shape[0] ** 3 + 4.0 * c * pool[k].shape[0] ** 2
             for _, k, _, _ in reqs)
     return t, desc + f"; extrapolated to each of the {len(reqs)} requests' cavities"
+
+
+def headline_line(args, world, r):
+    st = r["stats"]
+    ms_per_step = r["total_ms"] / args.steps
+    value = job_value(world, args.steps, r["total_ms"], r["cav"].solves)
+    nc = FIELDS + 1
+    ksteps = max(1, len(r["prof_times"]))
+    kern, host, kern_raw = kernel_tables(r["prof"], ksteps)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if W["near"] == "f64" else "f32", "data": "synthetic",
+        "config": config_dict(r["cav"]),
+        "latency_ms": {"p50": float(np.percentile(r["times"], 50)), "p99": float(np.percentile(r["times"], 99))},
+        "gpu_launches": int(r["launches"]),
+        "clocks": r["clocks"],
+        "roofline": roofline(kern_raw, st, ksteps, nc, sm_count(r["dev"])),
+        "profiled_pass": {"steps": ksteps, "ms_per_step": statistics.mean(r["prof_times"]) if r["prof_times"] else None,
+                          "note": "kernel and host-phase tables come from this separate, instrumented pass"},
+        "kernels_ms_per_step": kern,
+        "host_phases_ms_per_step": host,
+        "gmres": {k: r["info"][k] for k in ("iters", "restarts", "matvecs", "max_rel_residual")},
+        "operator": {k: st[k] for k in ("n_blocks", "n_admissible", "near_entries", "far_entries", "sum_rank",
+                                         "max_rank_used", "n_dense_fallback", "bytes_near", "bytes_far")},
+    }
+    ex = r["extra"]
+    line["e2e"] = ex.get("e2e")
+    line["hmatvec"] = ex.get("hmatvec")
+    if "fp64_path" in ex:
+        line["fp64_path"] = ex["fp64_path"]
+        line["speedup_vs_fp64_gpu"] = value / world / ex["fp64_path"]["value"]
+    return line
 
 
 def main():
@@ -691,16 +938,22 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="headline line only (skip the sphere, batch and served keys)")
     ap.add_argument("--workload", default="cylinder", choices=sorted(WORKLOADS))
     ap.add_argument("--product-path", type=int, choices=[0, 1], default=None,
                     help="many-column product: 0 CUDA-core tiles, 1 tensor cores (default: library choice)")
     ap.add_argument("--recompress-tol", type=float, default=None,
                     help="truncate every ACA cross at this relative accuracy (default: the workload's setting)")
+    ap.add_argument("--oracle-sample", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     select_workload(args.workload)
     global PRODUCT_PATH, RECOMPRESS
     PRODUCT_PATH = args.product_path
     RECOMPRESS = W.get("recompress", 0.0) if args.recompress_tol is None else args.recompress_tol
+    if args.oracle_sample is not None:
+        oracle_sample_main(args.oracle_sample)
+        return 0
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
 
@@ -710,7 +963,7 @@ def main():
         return 0
     if W.get("served"):
         if rank == 0:
-            run_served(args)
+            print(json.dumps(served_summary(args)), flush=True)
         return 0
 
     if world > 1:
@@ -724,41 +977,30 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return 0
-    st = r["stats"]
-    times = r["times"]
-    ms_per_step = r["total_ms"] / args.steps
-    value = job_value(world, args.steps, r["total_ms"], r["cav"].solves)
-    nc = FIELDS + 1
-    steps = args.steps
-    prof = {k: (v[0], v[1]) for k, v in r["prof"].items() if not k.startswith("host_")}
-    host = {k: v[1] / args.steps for k, v in r["prof"].items() if k.startswith("host_")}
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": args.warmup,
-        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic", "config": config_dict(r["cav"]),
-        "latency_ms": {"p50": float(np.percentile(times, 50)), "p99": float(np.percentile(times, 99))},
-        "gpu_launches": int(r["launches"]),
-        "clocks": r["clocks"],
-        "roofline": roofline(prof, st, steps, r["clocks"], nc),
-        "kernels_ms_per_step": {k: v[1] / steps for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
-        "host_phases_ms_per_step": dict(sorted(host.items(), key=lambda kv: -kv[1])),
-        "gmres": {"iters": r["infos"][-1]["iters"], "restarts": r["infos"][-1]["restarts"],
-                  "matvecs": r["infos"][-1]["matvecs"], "max_rel_residual": r["infos"][-1]["max_rel_residual"]},
-        "operator": {k: st[k] for k in ("n_blocks", "n_admissible", "near_entries", "far_entries", "sum_rank",
-                                         "max_rank_used", "n_dense_fallback", "bytes_near", "bytes_far")},
-    }
-    ex = r["extra"]
-    line["e2e"] = ex.get("e2e")
-    line["hmatvec"] = ex.get("hmatvec")
-    if "fp64_path" in ex:
-        line["fp64_path"] = ex["fp64_path"]
-        line["speedup_vs_fp64_gpu"] = value / world / ex["fp64_path"]["value"]
+    line = headline_line(args, world, r)
     if not args.no_cpu_baseline:
-        t, desc = oracle_step(r["cav"])
-        line["cpu_baseline"] = {"value": r["cav"].solves / t, "unit": UNIT, "cores": os.cpu_count(),
-                                "kind": "oracle", "sample": desc}
-        # (a batch's FP64 path would hold a ~100 GB operator: ours only there)
-        line["accuracy"] = accuracy_vs_oracle(r["cav"], no_fp64=args.no_fp64 or r["cav"].batch)
+        if not r["cav"].batch and r["cav"].n <= 40000:
+            line["accuracy"], line["cpu_baseline"] = dense_accuracy_and_baseline(r["cav"], args)
+        else:
+            t, desc = oracle_step(r["cav"])
+            line["cpu_baseline"] = {"value": r["cav"].solves / t, "unit": UNIT, "cores": os.cpu_count(),
+                                    "kind": "oracle", "sample": desc + " (extrapolated)", "cpu_model": cpu_model()}
+            # (a batch's FP64 path would hold a ~100 GB operator: ours only there)
+            line["accuracy"] = accuracy_vs_oracle(r["cav"], no_fp64=args.no_fp64 or r["cav"].batch)
+    if world == 1 and args.workload == "cylinder" and not args.no_workloads:
+        head = args.workload
+        wl = {}
+        for name, key in (("sphere-mixed", "sphere_mixed"), ("batch", "batch")):
+            try:
+                wl[key] = solver_workload_summary(name, args)
+            except Exception as e:   # report, never hide: the key carries the failure
+                wl[key] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        try:
+            wl["served"] = served_summary(args, steps=3)
+        except Exception as e:
+            wl["served"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        select_workload(head)
+        line["workloads"] = wl
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -25,8 +25,10 @@
  *   build, compression, solve) synchronise that stream before returning;
  *   rad_hmatvec does not.
  * - The library owns the rad_htree handle and every device buffer inside it
- *   (rad_htree_free releases them).  A handle is used on the device that was
- *   current when it was built.  Calls on one handle must not overlap.
+ *   (rad_htree_free releases them).  Device memory comes from the handle's
+ *   allocator (rad_tree_params.allocator: the caller's callbacks, or the
+ *   library's own stream-ordered pool).  A handle is used on the device that
+ *   was current when it was built.  Calls on one handle must not overlap.
  * - Floating-point facet data is double precision.  Facets must be
  *   non-degenerate (positive area) and finite, else RAD_EINVAL.
  */
@@ -58,12 +60,42 @@ extern "C" {
 
 typedef struct rad_htree rad_htree;
 
+/* Device-memory callbacks (no counterpart in the paper; an interface of this
+ * library).  A handle takes every device buffer it owns, and every per-call
+ * workspace of the calls made on it, from its allocator, so that a caller
+ * with its own memory manager (e.g. PyTorch's caching allocator) owns and
+ * accounts for all of the library's device memory:
+ *   alloc(ctx, bytes, stream) returns device memory of at least `bytes`
+ *     bytes, 256-byte aligned, usable in the order of `stream` (a
+ *     cudaStream_t; NULL = legacy default stream), or NULL on failure (the
+ *     call then returns RAD_ENOMEM after returning what it already took);
+ *   free(ctx, ptr, bytes, stream) takes back a pointer alloc returned, with
+ *     the same byte count; work queued on `stream` before the call may still
+ *     read it, so a stream-ordered allocator reuses it only after that work.
+ *     Buffers owned by a handle are freed after a device synchronisation
+ *     (rad_htree_free), per-call workspaces in the order of the call's stream.
+ *   ctx is passed through unchanged.
+ * The callbacks are called from the thread that makes the library call (for a
+ * server: its worker threads) and must stay valid until the handle is freed.
+ * Without an allocator (NULL), the library allocates stream-ordered
+ * (cudaMallocFromPoolAsync on the call's stream) from a memory pool of its own
+ * per device that keeps freed memory cached; it does not change the device's
+ * default memory pool. */
+typedef struct {
+    void* (*alloc)(void* ctx, uint64_t bytes, void* stream);
+    void  (*free)(void* ctx, void* ptr, uint64_t bytes, void* stream);
+    void*  ctx;
+} rad_allocator;
+
 /* §4.1-4.2.  leaf_size = n_min of Algorithm 1 (a cluster with at most
- * leaf_size facets is a leaf, >= 1); eta_adm = c of Eq. (28), > 0. */
+ * leaf_size facets is a leaf, >= 1); eta_adm = c of Eq. (28), > 0.
+ * allocator: device memory of the new handle (see rad_allocator; NULL = the
+ * library's own pool); the struct is copied, the callbacks are not. */
 typedef struct {
     int32_t leaf_size;
     int32_t reserved;
     double  eta_adm;
+    const rad_allocator* allocator;
 } rad_tree_params;
 
 /* §4.3.  tol = eps_rel of Eq. (31) (>= 0); max_rank caps the rank of every
@@ -279,6 +311,8 @@ int rad_htree_close_cavity(rad_htree* h, double* row_sums, void* stream);
  *   sigma  Stefan-Boltzmann constant (the caller's value; 5.670374419e-8)
  *   info   optional (may be NULL)
  * Returns RAD_ENOTCONV (q still written) if a column misses the tolerance.
+ * RAD_EINVAL, before any solver work, if an emissivity is not finite or not
+ * in (0, 1], or a temperature is not finite or negative.
  * ------------------------------------------------------------------------- */
 int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64_t ldT,
                    int64_t m, double sigma, const rad_solve_params* p,
@@ -315,7 +349,9 @@ int rad_hmatvec_noalloc(const rad_htree* h, int32_t dtype, const void* x, int64_
  * GMRES as rad_solve_flux (the paper applies C^-1 through its LU factors,
  * §5.2; this library iterates with the stored F instead).
  *   B, Y   column-major n x nrhs (ldB, ldY >= n); nrhs 1 .. 1024
- * Returns RAD_ENOTCONV (Y still written) if a column misses the tolerance.
+ * Returns RAD_ENOTCONV (Y still written) if a column misses the tolerance;
+ * RAD_EINVAL, before any solver work, for an emissivity that is not finite
+ * or not in (0, 1], or a value of B that is not finite.
  * ------------------------------------------------------------------------- */
 int rad_solve_reflection(const rad_htree* h, const double* eps, const double* B, int64_t ldB, int64_t nrhs,
                          const rad_solve_params* p, double* Y, int64_t ldY, rad_solve_info* info, void* stream);
@@ -381,7 +417,9 @@ typedef struct {
     int32_t slots;               /* concurrent requests (worker threads), >= 1 */
     int32_t reserved;
     int64_t hbm_budget_bytes;    /* resident operators + request workspaces   */
-    rad_tree_params tree;        /* cluster/block tree of a new cavity         */
+    rad_tree_params tree;        /* cluster/block tree of a new cavity; its
+                                    allocator (copied at creation) serves every
+                                    operator and request of the server          */
     rad_aca_params aca;          /* its compression                            */
     rad_solve_params solve;      /* every request's solve                      */
 } rad_server_params;

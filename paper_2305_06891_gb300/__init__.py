@@ -37,8 +37,82 @@ class RadError(RuntimeError):
         self.code = code
 
 
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p)
+
+
+class _Allocator(C.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", C.c_void_p)]
+
+
 class _TreeParams(C.Structure):
-    _fields_ = [("leaf_size", C.c_int32), ("reserved", C.c_int32), ("eta_adm", C.c_double)]
+    _fields_ = [("leaf_size", C.c_int32), ("reserved", C.c_int32), ("eta_adm", C.c_double),
+                ("allocator", C.POINTER(_Allocator))]
+
+
+class Allocator:
+    """Device memory of a handle through the caller's callbacks
+    (``rad_allocator``): ``alloc(nbytes, stream) -> int`` returns a device
+    pointer (0 or an exception: allocation failure, the library call returns
+    RAD_ENOMEM) and ``free(ptr, nbytes, stream)`` takes it back; ``stream`` is
+    the cudaStream_t of the library call as an int.  Counts what is live.
+    ``fail_after`` makes every allocation after the first ``fail_after`` fail
+    (fault injection for tests)."""
+
+    def __init__(self, alloc, free, fail_after: int | None = None):
+        self.n_alloc = self.n_free = 0
+        self.live_bytes = self.peak_bytes = 0
+        self.live: dict[int, int] = {}
+        self.fail_after = fail_after
+
+        def _a(ctx, nbytes, stream):
+            try:
+                if self.fail_after is not None and self.n_alloc >= self.fail_after:
+                    return None
+                ptr = int(alloc(int(nbytes), int(stream or 0)))
+            except Exception:
+                return None
+            if ptr:
+                self.n_alloc += 1
+                self.live[ptr] = int(nbytes)
+                self.live_bytes += int(nbytes)
+                self.peak_bytes = max(self.peak_bytes, self.live_bytes)
+            return ptr or None
+
+        def _f(ctx, ptr, nbytes, stream):
+            try:
+                self.n_free += 1
+                self.live_bytes -= self.live.pop(int(ptr), 0)
+                free(int(ptr), int(nbytes), int(stream or 0))
+            except Exception:
+                pass
+
+        self._cb = (_ALLOC_FN(_a), _FREE_FN(_f))
+        self.struct = _Allocator(self._cb[0], self._cb[1], None)
+
+
+def torch_allocator(device=None, fail_after: int | None = None) -> Allocator:
+    """The PyTorch caching allocator as a handle's device memory: every
+    buffer of the handle and every workspace of calls on it is a block of
+    torch's pool (``torch.cuda.memory_allocated`` counts it), allocated for
+    the library call's stream."""
+    t = _torch()
+    dev = t.cuda.current_device() if device is None else t.device(device).index
+
+    def alloc(nbytes, stream):
+        return t.cuda.caching_allocator_alloc(nbytes, device=dev, stream=stream)
+
+    def free(ptr, nbytes, stream):
+        t.cuda.caching_allocator_delete(ptr)
+
+    return Allocator(alloc, free, fail_after)
+
+
+def _tree_params(leaf_size, eta_adm, allocator):
+    p = _TreeParams(int(leaf_size), 0, float(eta_adm), None)
+    if allocator is not None:
+        p.allocator = C.pointer(allocator.struct)
+    return p
 
 
 class _AcaParams(C.Structure):
@@ -222,11 +296,13 @@ def _colmajor(a, dtype):
 
 
 class HTree:
-    """Owns one ``rad_htree*``; freed with :func:`rad_htree_free` or on GC."""
+    """Owns one ``rad_htree*``; freed with :func:`rad_htree_free` or on GC.
+    Keeps the handle's :class:`Allocator` (if any) alive with it."""
 
-    def __init__(self, ptr: int, n: int):
+    def __init__(self, ptr: int, n: int, allocator: Allocator | None = None):
         self._p = C.c_void_p(ptr)
         self.n = n
+        self.allocator = allocator
 
     @property
     def ptr(self) -> C.c_void_p:
@@ -254,17 +330,20 @@ def rad_last_error() -> str:
     return _lib.rad_last_error().decode()
 
 
-def rad_build_htree(verts, leaf_size: int = 32, eta_adm: float = 1.0, stream=None) -> HTree:
-    """A1-A3 on the GPU: facets of the triangles ``verts`` (N, 3, 3)."""
+def rad_build_htree(verts, leaf_size: int = 32, eta_adm: float = 1.0, stream=None,
+                    allocator: Allocator | None = None) -> HTree:
+    """A1-A3 on the GPU: facets of the triangles ``verts`` (N, 3, 3).
+    ``allocator``: device memory of the handle (default: the library's pool)."""
     v = _f64_rowmajor(verts)
     n = int(v.shape[0])
     out = C.c_void_p()
-    p = _TreeParams(int(leaf_size), 0, float(eta_adm))
+    p = _tree_params(leaf_size, eta_adm, allocator)
     _check(_lib.rad_build_htree(n, _ptr(v), C.byref(p), _stream(stream, v), C.byref(out)))
-    return HTree(out.value, n)
+    return HTree(out.value, n, allocator)
 
 
-def rad_build_htree_batch(verts, counts, leaf_size: int = 32, eta_adm: float = 1.0, stream=None) -> HTree:
+def rad_build_htree_batch(verts, counts, leaf_size: int = 32, eta_adm: float = 1.0, stream=None,
+                          allocator: Allocator | None = None) -> HTree:
     """A batch of cavities in one handle: ``verts`` (sum(counts), 3, 3) holds the
     cavities' triangles one cavity after the other, ``counts`` their numbers."""
     v = _f64_rowmajor(verts)
@@ -273,21 +352,21 @@ def rad_build_htree_batch(verts, counts, leaf_size: int = 32, eta_adm: float = 1
     if int(cnt.sum()) != n:
         raise ValueError("sum(counts) must equal the number of triangles")
     out = C.c_void_p()
-    p = _TreeParams(int(leaf_size), 0, float(eta_adm))
+    p = _tree_params(leaf_size, eta_adm, allocator)
     _check(_lib.rad_build_htree_batch(int(cnt.size), cnt.ctypes.data, _ptr(v), C.byref(p), _stream(stream, v),
                                       C.byref(out)))
-    return HTree(out.value, n)
+    return HTree(out.value, n, allocator)
 
 
 def rad_build_htree_facets(centroid, normal, area, leaf_size: int = 32, eta_adm: float = 1.0,
-                           stream=None) -> HTree:
+                           stream=None, allocator: Allocator | None = None) -> HTree:
     c, nr, a = _f64_rowmajor(centroid), _f64_rowmajor(normal), _f64_rowmajor(area)
     n = int(a.shape[0])
     out = C.c_void_p()
-    p = _TreeParams(int(leaf_size), 0, float(eta_adm))
+    p = _tree_params(leaf_size, eta_adm, allocator)
     _check(_lib.rad_build_htree_facets(n, _ptr(c), _ptr(nr), _ptr(a), C.byref(p), _stream(stream, c),
                                        C.byref(out)))
-    return HTree(out.value, n)
+    return HTree(out.value, n, allocator)
 
 
 def rad_htree_from_dense(F, stream=None) -> HTree:
@@ -415,9 +494,11 @@ class Server:
                  eta_adm: float = 1.0, aca_tol: float = 1e-6, max_rank: int = 64, factor_dtype: str = "bf16",
                  near_dtype: str = "f32", accurate_dtype: str | None = "f32", tol: float = 1e-8,
                  restart: int = 30, max_iter: int = 1000, refine: bool = True, inner_tol: float = 1e-4,
-                 max_refine: int = 10, aca_scratch_mib: int = 0, recompress_tol: float = 0.0):
+                 max_refine: int = 10, aca_scratch_mib: int = 0, recompress_tol: float = 0.0,
+                 allocator: Allocator | None = None):
         acc = -1 if accurate_dtype is None else _DT[accurate_dtype]
-        p = _ServerParams(int(slots), 0, int(hbm_budget_bytes), _TreeParams(int(leaf_size), 0, float(eta_adm)),
+        self.allocator = allocator
+        p = _ServerParams(int(slots), 0, int(hbm_budget_bytes), _tree_params(leaf_size, eta_adm, allocator),
                           _AcaParams(float(aca_tol), int(max_rank), RAD_ACA_PARTIAL, _DT[factor_dtype],
                                      _DT[near_dtype], acc, int(aca_scratch_mib), float(recompress_tol)),
                           _SolveParams(float(tol), int(restart), int(max_iter), 1 if refine else 0,

@@ -219,48 +219,79 @@ static void clear_profile() {
     g_prof.clear();
 }
 
-// Keep freed stream-ordered allocations cached in the device's default pool
-// (process-local setting), so that repeated calls do not return memory to
-// the driver and allocate it again.
-static void keep_pool_warm() {
+// The library's own memory pool of a device (created on first use): a
+// stream-ordered pool whose release threshold is raised so that freed memory
+// stays cached and repeated builds do not map new pages.  It is separate from
+// the device's default pool, whose settings belong to the caller's process.
+static cudaMemPool_t library_pool() {
     static std::mutex mu;
-    static std::vector<int> done;
+    static std::vector<std::pair<int, cudaMemPool_t>> pools;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        (void)cudaGetLastError();
+    RAD_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& e : pools)
+        if (e.first == dev) return e.second;
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    RAD_CUDA(cudaMemPoolCreate(&pool, &props));
+    uint64_t thr = UINT64_MAX;
+    RAD_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    pools.push_back({dev, pool});
+    return pool;
+}
+
+namespace {
+thread_local Allocator g_cur_alloc;   // default: the library's pool
+}
+const Allocator& current_allocator() { return g_cur_alloc; }
+AllocScope::AllocScope(const Allocator& a) : prev(g_cur_alloc) { g_cur_alloc = a; }
+AllocScope::~AllocScope() { g_cur_alloc = prev; }
+
+void* Allocator::get(size_t bytes, cudaStream_t s) const {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (cb.alloc) {
+        p = cb.alloc(cb.ctx, (uint64_t)bytes, s);
+        if (!p) fail(RAD_ENOMEM, "the caller's allocator returned NULL for " + std::to_string(bytes) + " bytes");
+        return p;
+    }
+    RAD_CUDA(cudaMallocFromPoolAsync(&p, bytes, library_pool(), s));
+    return p;
+}
+void Allocator::put(void* p, size_t bytes, cudaStream_t s) const {
+    if (!p) return;
+    if (cb.alloc) {
+        if (cb.free) cb.free(cb.ctx, p, (uint64_t)(bytes ? bytes : 16), s);
         return;
     }
-    std::lock_guard<std::mutex> lk(mu);
-    for (int d : done)
-        if (d == dev) return;
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-        uint64_t thr = UINT64_MAX;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-    }
-    (void)cudaGetLastError();
-    done.push_back(dev);
+    if (cudaFreeAsync(p, s) != cudaSuccess) (void)cudaGetLastError();
 }
 
 void DevBuf::alloc(size_t b, cudaStream_t s) {
     release(s);
     if (b == 0) return;
-    RAD_CUDA(cudaMallocAsync(&p, b, s));
+    al = current_allocator();
+    p = al.get(b, s);
     bytes = b;
 }
 void DevBuf::release(cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
+    if (p) al.put(p, bytes, s);
     p = nullptr;
     bytes = 0;
 }
 
 Scratch::~Scratch() {
-    for (void* q : ptrs) cudaFreeAsync(q, s);
+    for (auto& q : ptrs) al.put(q.first, q.second, s);
 }
 void* Scratch::get(size_t bytes) {
-    void* q = nullptr;
-    RAD_CUDA(cudaMallocAsync(&q, bytes ? bytes : 16, s));
-    ptrs.push_back(q);
+    ptrs.reserve(ptrs.size() + 1);
+    void* q = al.get(bytes ? bytes : 16, s);
+    ptrs.push_back({q, bytes ? bytes : 16});
     return q;
 }
 
@@ -292,7 +323,6 @@ static const void* stage_in_2d(const void* p, int64_t rows, int64_t cols, int64_
 template <class F>
 static int guarded(F&& f) {
     try {
-        keep_pool_warm();
         f();
         return RAD_OK;
     } catch (const Error& e) {
@@ -315,6 +345,15 @@ static void check_tree_params(int64_t n, const rad_tree_params* p) {
     RAD_REQUIRE(n >= 1 && n < (int64_t)(INT_MAX / 8), RAD_EINVAL, "n must be in [1, 2^28)");
     RAD_REQUIRE(p->leaf_size >= 1, RAD_EINVAL, "leaf_size must be >= 1");
     RAD_REQUIRE(std::isfinite(p->eta_adm) && p->eta_adm > 0.0, RAD_EINVAL, "eta_adm must be > 0");
+    RAD_REQUIRE(!p->allocator || (p->allocator->alloc && p->allocator->free), RAD_EINVAL,
+                "an allocator needs both alloc and free");
+}
+
+// The allocator a new handle keeps (the caller's callbacks, or the pool).
+static Allocator handle_allocator(const rad_tree_params* p) {
+    Allocator a;
+    if (p->allocator) a.cb = *p->allocator;
+    return a;
 }
 
 }  // namespace rad
@@ -449,6 +488,8 @@ int rad_build_htree(int64_t n, const double* verts, const rad_tree_params* p, vo
         h->n = n;
         h->leaf_size = p->leaf_size;
         h->eta = p->eta_adm;
+        h->alloc = handle_allocator(p);
+        AllocScope as(h->alloc);
         RAD_CUDA(cudaGetDevice(&h->device));
         Scratch ws(s);
         const double* v = to_device_t(verts, 9 * (size_t)n, ws);
@@ -479,6 +520,8 @@ int rad_build_htree_batch(int32_t n_cavities, const int64_t* counts, const doubl
         h->seg = seg;
         h->leaf_size = p->leaf_size;
         h->eta = p->eta_adm;
+        h->alloc = handle_allocator(p);
+        AllocScope as(h->alloc);
         RAD_CUDA(cudaGetDevice(&h->device));
         Scratch ws(s);
         const double* v = to_device_t(verts, 9 * (size_t)n, ws);
@@ -508,6 +551,8 @@ int rad_build_htree_facets(int64_t n, const double* centroid, const double* norm
         h->n = n;
         h->leaf_size = p->leaf_size;
         h->eta = p->eta_adm;
+        h->alloc = handle_allocator(p);
+        AllocScope as(h->alloc);
         RAD_CUDA(cudaGetDevice(&h->device));
         Scratch ws(s);
         const double* c = to_device_t(centroid, 3 * (size_t)n, ws);
@@ -552,6 +597,7 @@ int rad_htree_from_dense(int64_t n, const double* F, void* stream, rad_htree** o
 int rad_compress_aca(rad_htree* h, const rad_aca_params* p, void* stream) {
     return guarded([&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null handle");
+        AllocScope as(h->alloc);
         compress(h, p, static_cast<cudaStream_t>(stream));
     });
 }
@@ -561,6 +607,7 @@ int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx, v
                 void* stream) {
     return guarded([&] {
         RAD_REQUIRE(h != nullptr && x != nullptr && y != nullptr, RAD_EINVAL, "null argument");
+        AllocScope as(h->alloc);
         RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed (call rad_compress_aca)");
         RAD_REQUIRE(dtype == RAD_F64 || dtype == RAD_F32, RAD_EINVAL, "dtype must be RAD_F64 or RAD_F32");
         RAD_REQUIRE(nrhs >= 1 && nrhs <= 4096, RAD_EINVAL, "nrhs must be in [1, 4096]");
@@ -597,6 +644,7 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
     int solve_status = RAD_OK;
     const int rc = guarded([&] {
         RAD_REQUIRE(h != nullptr && eps && T && q && p, RAD_EINVAL, "null argument");
+        AllocScope as(h->alloc);
         RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed (call rad_compress_aca)");
         RAD_REQUIRE(m >= 1 && m <= 1024, RAD_EINVAL, "m must be in [1, 1024]");
         RAD_REQUIRE(ldT >= h->n && ldq >= h->n, RAD_EINVAL, "leading dimension smaller than n");
@@ -634,6 +682,7 @@ int rad_solve_reflection(const rad_htree* h, const double* eps, const double* B,
     int solve_status = RAD_OK;
     const int rc = guarded([&] {
         RAD_REQUIRE(h != nullptr && eps && B && Y && p, RAD_EINVAL, "null argument");
+        AllocScope as(h->alloc);
         RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed (call rad_compress_aca)");
         RAD_REQUIRE(nrhs >= 1 && nrhs <= 1024, RAD_EINVAL, "nrhs must be in [1, 1024]");
         RAD_REQUIRE(ldB >= h->n && ldY >= h->n, RAD_EINVAL, "leading dimension smaller than n");
@@ -744,6 +793,7 @@ int rad_htree_export_blocks(const rad_htree* h, int32_t* row_node, int32_t* col_
 int rad_htree_export_block(const rad_htree* h, int64_t block, double* D, double* U, double* V) {
     return guarded([&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null handle");
+        AllocScope as(h->alloc);
         export_block(h, block, D, U, V);
     });
 }
@@ -751,6 +801,7 @@ int rad_htree_export_block(const rad_htree* h, int64_t block, double* D, double*
 int rad_htree_autotune(rad_htree* h, void* stream) {
     return guarded([&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null argument");
+        AllocScope as(h->alloc);
         autotune(h, static_cast<cudaStream_t>(stream));
     });
 }
@@ -758,6 +809,7 @@ int rad_htree_autotune(rad_htree* h, void* stream) {
 int rad_htree_close_cavity(rad_htree* h, double* row_sums, void* stream) {
     return guarded([&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null argument");
+        AllocScope as(h->alloc);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         Scratch ws(s);
         const int n = (int)h->n;

@@ -299,6 +299,29 @@ __global__ void flux_kernel(int n, int m, const FT* __restrict__ FY, const int* 
         sigma * eps[u] * ((double)FY[(long long)p * nc + c] - eta * (double)FY[(long long)p * nc + m]);
 }
 
+// Inputs of a solve, checked before any solver launch: every emissivity
+// finite and in (0, 1] (bit 1 of *flags), every value of the n x cols
+// column-major array X finite (and >= 0 when nonneg: temperatures) (bit 2).
+__global__ void check_inputs_kernel(int n, const double* __restrict__ eps, const double* __restrict__ X,
+                                    long long ldX, int cols, int nonneg, int* __restrict__ flags) {
+    int bad = 0;
+    const long long total = (long long)n * (cols + 1);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e % n);
+        const long long c = e / n;
+        if (c == 0) {
+            const double v = eps[i];
+            if (!(isfinite(v) && v > 0.0 && v <= 1.0)) bad |= 1;
+        } else {
+            const double v = X[(c - 1) * ldX + i];
+            if (!isfinite(v) || (nonneg && v < 0.0)) bad |= 2;
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (bad && (threadIdx.x & 31) == 0) atomicOr(flags, bad);
+}
+
 __global__ void axpy_kernel(double* __restrict__ X, const double* __restrict__ D, long long cnt) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < cnt) X[e] += D[e];
@@ -356,6 +379,23 @@ struct ColReducer {
         RAD_CHECK_LAUNCH();
     }
 };
+
+// Runs check_inputs_kernel and fails with RAD_EINVAL naming what is wrong.
+static void check_solve_inputs(int n, const double* eps, const double* X, long long ldX, int cols, bool temps,
+                               Scratch& ws, cudaStream_t s) {
+    int* d_flags = ws.get_n<int>(1);
+    RAD_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int), s));
+    const long long total = (long long)n * (cols + 1);
+    const unsigned grid = (unsigned)std::min<long long>(1216, (total + 255) / 256);
+    { ProfScope ps_("check_inputs", s); check_inputs_kernel<<<grid, 256, 0, s>>>(n, eps, X, ldX, cols, temps ? 1 : 0, d_flags); }
+    RAD_CHECK_LAUNCH();
+    int flags = 0;
+    RAD_CUDA(cudaMemcpyAsync(&flags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RAD_CUDA(cudaStreamSynchronize(s));
+    RAD_REQUIRE(!(flags & 1), RAD_EINVAL, "every emissivity must be finite and in (0, 1]");
+    RAD_REQUIRE(!(flags & 2), RAD_EINVAL,
+                temps ? "every temperature must be finite and >= 0" : "every right-hand side value must be finite");
+}
 
 }  // namespace
 
@@ -569,6 +609,7 @@ void solve_flux(const rad_htree* h, const double* eps_dev, const double* T_dev, 
     const bool op64 = h->op_is_f64();
     const long long nv = (long long)n * nc;
     Scratch ws(s);
+    check_solve_inputs(n, eps_dev, T_dev, ldT, m, true, ws, s);
     double* eps_t = ws.get_n<double>(n);
     double* B = ws.get_n<double>(nv);
     double* X = ws.get_n<double>(nv);
@@ -609,6 +650,7 @@ void solve_reflection(const rad_htree* h, const double* eps_dev, const double* B
     const int n = (int)h->n;
     const long long nv = (long long)n * nrhs;
     Scratch ws(s);
+    check_solve_inputs(n, eps_dev, B_dev, ldB, nrhs, false, ws, s);
     double* eps_t = ws.get_n<double>(n);
     double* B = ws.get_n<double>(nv);
     double* X = ws.get_n<double>(nv);

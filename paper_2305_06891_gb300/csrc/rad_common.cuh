@@ -77,28 +77,50 @@ struct HostScope {
     } while (0)
 
 // ------------------------------------------------------------ memory helpers
-// A device buffer owned by a handle, from the stream-ordered memory pool.
+// Where device memory comes from: the caller's rad_allocator callbacks, or
+// (cb.alloc == nullptr) the library's own stream-ordered pool of the current
+// device, which keeps freed memory cached.
+struct Allocator {
+    rad_allocator cb{nullptr, nullptr, nullptr};
+    void* get(size_t bytes, cudaStream_t s) const;          // fails with RAD_ENOMEM
+    void put(void* p, size_t bytes, cudaStream_t s) const;  // never throws
+};
+// The allocator of the library call running on this thread: entry points
+// that work on a handle install the handle's allocator for their duration
+// (AllocScope); elsewhere it is the library's pool.
+const Allocator& current_allocator();
+struct AllocScope {
+    Allocator prev;
+    explicit AllocScope(const Allocator& a);
+    ~AllocScope();
+    AllocScope(const AllocScope&) = delete;
+    AllocScope& operator=(const AllocScope&) = delete;
+};
+
+// A device buffer owned by a handle, from the allocator current at alloc();
+// it remembers that allocator and returns the memory to it.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    Allocator al;
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
     ~DevBuf() { release(nullptr); }
-    // Stream-ordered allocation from the device's default memory pool (kept
-    // warm, so a repeated build/compress does not map new pages); release
-    // frees in the order of stream `s`.
+    // Stream-ordered allocation on stream `s`; release frees in the order of
+    // stream `s`.
     void alloc(size_t b, cudaStream_t s);
     void release(cudaStream_t s);
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
-// Per-call stream-ordered workspace; everything is freed (stream-ordered)
-// when the object goes out of scope.
+// Per-call stream-ordered workspace from the current allocator; everything
+// is freed (stream-ordered) when the object goes out of scope.
 struct Scratch {
     cudaStream_t s;
-    std::vector<void*> ptrs;
-    explicit Scratch(cudaStream_t st) : s(st) {}
+    Allocator al;
+    std::vector<std::pair<void*, size_t>> ptrs;
+    explicit Scratch(cudaStream_t st) : s(st), al(current_allocator()) {}
     Scratch(const Scratch&) = delete;
     ~Scratch();
     void* get(size_t bytes);
@@ -367,6 +389,7 @@ struct rad_htree {
     int mm_path = 0;
     int closed = 0;   // rows normalised for a closed cavity (rad_htree_close_cavity)
     int64_t n = 0;
+    rad::Allocator alloc;   // device memory of the handle and of calls on it
     // segment (cavity) boundaries of a batch handle: cavity c holds facets
     // [seg[c], seg[c+1]) in user order and in tree order; {0, n} otherwise
     std::vector<int64_t> seg;

@@ -56,6 +56,7 @@ struct Request {
 
 struct rad_server {
     rad_server_params p{};
+    rad_allocator alloc{};   // copy of the caller's allocator (p.tree.allocator points here)
     int device = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -242,8 +243,14 @@ int rad_server_create(const rad_server_params* p, rad_server** out) {
                     "bad solve parameters");
         RAD_REQUIRE(!p->solve.refine || (p->aca.accurate_dtype == RAD_F32 || p->aca.factor_dtype == RAD_F64),
                     RAD_EINVAL, "refinement needs aca.accurate_dtype = RAD_F32 (or the FP64 path)");
+        RAD_REQUIRE(!p->tree.allocator || (p->tree.allocator->alloc && p->tree.allocator->free), RAD_EINVAL,
+                    "an allocator needs both alloc and free");
         auto s = std::make_unique<rad_server>();
         s->p = *p;
+        if (p->tree.allocator) {
+            s->alloc = *p->tree.allocator;
+            s->p.tree.allocator = &s->alloc;
+        }
         RAD_CUDA(cudaGetDevice(&s->device));
         rad_server* raw = s.get();
         for (int k = 0; k < p->slots; ++k) s->workers.emplace_back([raw, k] { raw->run(k); });

@@ -55,3 +55,39 @@ def test_server_parameters_are_checked_before_any_cuda_call(lib):
     assert e.value.code == 1
     with pytest.raises(rad.RadError):
         rad.Server(slots=2, hbm_budget_bytes=0)
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Size and field offsets of every struct the binding passes across the
+    C ABI, against a C program compiled with the header (gcc)."""
+    import ctypes as C
+    import shutil
+    import subprocess
+
+    import paper_2305_06891_gb300 as rad
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"rad_allocator": rad._Allocator, "rad_tree_params": rad._TreeParams,
+               "rad_aca_params": rad._AcaParams, "rad_solve_params": rad._SolveParams,
+               "rad_solve_info": rad._SolveInfo, "rad_htree_stats": rad._Stats,
+               "rad_server_params": rad._ServerParams, "rad_request_info": rad._RequestInfo,
+               "rad_server_stats": rad._ServerStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rad.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0; }"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, val = line.split()
+        got[(cname, field)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
