@@ -141,7 +141,11 @@ typedef struct {
  * mixed-precision iterative refinement - the residual r = b - C y is
  * computed with the accurate operator (FP32 factors) accumulated in FP64,
  * the correction solves C d = r by GMRES on the fast operator (BF16 factors)
- * to inner_tol, y += d, until the accurate relative residual <= tol. */
+ * to inner_tol, y += d, until the accurate relative residual <= tol.
+ * precond: see rad_hlu_factor; factors built for other emissivities remain a
+ * valid (weaker) preconditioner, the stopping test is always on C itself. */
+typedef struct rad_hlu rad_hlu;
+
 typedef struct {
     double  tol;
     int32_t restart;
@@ -149,6 +153,10 @@ typedef struct {
     int32_t refine;
     int32_t max_refine;          /* outer refinement steps (refine = 1)       */
     double  inner_tol;           /* relative tolerance of each correction     */
+    const rad_hlu* precond;      /* optional right preconditioner: the block LU
+                                    factors of C (rad_hlu_factor on the same
+                                    handle); GMRES then iterates on C (LU)^-1
+                                    and returns x = (LU)^-1 u.  NULL = none.  */
 } rad_solve_params;
 
 typedef struct {
@@ -342,6 +350,66 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
  * ------------------------------------------------------------------------- */
 int rad_hmatvec_noalloc(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx,
                         void* y, int64_t ldy, int64_t nrhs, void* stream);
+
+/* -------------------------------------------------------------------------
+ * Hierarchical block LU of the reflection matrix (§5.1) and the forward and
+ * backward substitution with its factors (§5.2).
+ *
+ * rad_hlu_factor: C = I - diag(1 - eps) F~, F~ the handle's stored operator
+ * (dense blocks and U V^T of the low-rank blocks; the FP32 accurate copy
+ * when the factors are BF16), is factorised C ~ L U in the block structure of
+ * the handle's block tree: L unit lower and U upper triangular, each leaf
+ * block dense or low rank.  The recursion runs over the diagonal cluster
+ * pairs: a leaf pair gets a dense LU without pivoting; a pair with children
+ * is factorised as a 2 x 2 block matrix (upper-left block recursively, the
+ * off-diagonal blocks by triangular solves, the Schur complement of the
+ * lower-right block recursively).  Every block the recursion produces is
+ * brought back into the block format, the ranks of its admissible leaves
+ * truncated at the relative accuracy tol by the singular-value decay; a leaf
+ * whose truncation would need more than min(64, m n / (m + n)) terms stays
+ * dense.  tol = 0 keeps every block exact (the unique LU of C without
+ * pivoting, every leaf dense).
+ *   eps     n emissivities in (0, 1] (facet order, host or device)
+ *   out     receives the factors; they refer to h, which must outlive them
+ * Works on one dense n x n matrix while factorising (n <= 46340; leaf
+ * clusters of at most 128 facets, else RAD_ELIMIT).  Arithmetic is FP64 for
+ * an FP64 operator (near_dtype RAD_F64), FP32 otherwise.  RAD_EINVAL for an
+ * emissivity outside (0, 1] or a zero pivot.  Synchronous.
+ *
+ * rad_hlu_solve: X = U^-1 L^-1 B for nrhs right-hand sides (column-major,
+ * facet order, host or device), by forward and backward substitution through
+ * the block structure (a triangular solve per diagonal leaf, D x or U (V^T x)
+ * per off-diagonal leaf).  Synchronous.
+ * rad_hlu_export: the factors as one dense n x n row-major host array in
+ * TREE order (rad_htree_export_tree gives the permutation), L strictly below
+ * the diagonal (unit diagonal implied) and U on and above it.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double  tol;                 /* eps_rel of the truncation, in [0, 1)      */
+    int32_t reserved0, reserved1;
+} rad_hlu_params;
+
+typedef struct {
+    int64_t n;
+    int64_t dense_entries;       /* entries of the dense leaves               */
+    int64_t lowrank_entries;     /* sum k (m + n) over the low-rank leaves     */
+    int32_t max_rank;
+    int32_t n_lowrank;           /* low-rank leaves                            */
+    int32_t n_dense_fallback;    /* admissible leaves kept dense               */
+    int32_t precision;           /* RAD_F64 or RAD_F32                         */
+    double  tol;
+    double  factor_ms;           /* host wall time of rad_hlu_factor           */
+    int32_t solve_launches;      /* steps of one substitution (leaf solves and
+                                    region products)                           */
+    int32_t reserved;
+} rad_hlu_stats;
+
+int rad_hlu_factor(const rad_htree* h, const double* eps, const rad_hlu_params* p, void* stream, rad_hlu** out);
+int rad_hlu_solve(const rad_hlu* lu, const double* B, int64_t ldB, int64_t nrhs, double* X, int64_t ldX,
+                  void* stream);
+int rad_hlu_get_stats(const rad_hlu* lu, rad_hlu_stats* st);
+int rad_hlu_export(const rad_hlu* lu, double* LU);
+int rad_hlu_free(rad_hlu* lu);
 
 /* -------------------------------------------------------------------------
  * rad_solve_reflection — A7 alone: solves C Y = B (Eq. 11, C = I -

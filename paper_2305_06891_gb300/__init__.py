@@ -123,7 +123,18 @@ class _AcaParams(C.Structure):
 
 class _SolveParams(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("max_iter", C.c_int32), ("refine", C.c_int32),
-                ("max_refine", C.c_int32), ("inner_tol", C.c_double)]
+                ("max_refine", C.c_int32), ("inner_tol", C.c_double), ("precond", C.c_void_p)]
+
+
+class _HluParams(C.Structure):
+    _fields_ = [("tol", C.c_double), ("reserved0", C.c_int32), ("reserved1", C.c_int32)]
+
+
+class _HluStats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("dense_entries", C.c_int64), ("lowrank_entries", C.c_int64),
+                ("max_rank", C.c_int32), ("n_lowrank", C.c_int32), ("n_dense_fallback", C.c_int32),
+                ("precision", C.c_int32), ("tol", C.c_double), ("factor_ms", C.c_double),
+                ("solve_launches", C.c_int32), ("reserved", C.c_int32)]
 
 
 class _SolveInfo(C.Structure):
@@ -199,6 +210,11 @@ def _load():
         "rad_server_wait": (C.c_int, [vp, i64, C.POINTER(_RequestInfo)]),
         "rad_server_get_stats": (C.c_int, [vp, C.POINTER(_ServerStats)]),
         "rad_server_destroy": (C.c_int, [vp]),
+        "rad_hlu_factor": (C.c_int, [H, vp, C.POINTER(_HluParams), vp, C.POINTER(vp)]),
+        "rad_hlu_solve": (C.c_int, [vp, vp, i64, i64, vp, i64, vp]),
+        "rad_hlu_get_stats": (C.c_int, [vp, C.POINTER(_HluStats)]),
+        "rad_hlu_export": (C.c_int, [vp, vp]),
+        "rad_hlu_free": (C.c_int, [vp]),
         "rad_launch_count": (C.c_int64, []),
         "rad_profile_enable": (C.c_int, [i32]),
         "rad_profile_read": (C.c_int, [i32, vp, vp, vp]),
@@ -417,7 +433,7 @@ def rad_hmatvec(h: HTree, x, y=None, stream=None):
 
 def rad_solve_flux(h: HTree, eps, T, sigma: float = SIGMA_SB, tol: float = 1e-10, restart: int = 30,
                    max_iter: int = 1000, q=None, stream=None, raise_on_notconv: bool = False,
-                   refine: bool = False, inner_tol: float = 1e-4, max_refine: int = 10):
+                   refine: bool = False, inner_tol: float = 1e-4, max_refine: int = 10, precond=None):
     """A7-A8: flux q (N, m) for temperature fields T (N,) or (N, m).
 
     Returns ``(q, info)``; ``info`` is a dict with status, iters, restarts,
@@ -432,7 +448,8 @@ def rad_solve_flux(h: HTree, eps, T, sigma: float = SIGMA_SB, tol: float = 1e-10
         else:
             q = np.empty((n, m), dtype=np.float64, order="F")
     ldq = n
-    p = _SolveParams(float(tol), int(restart), int(max_iter), 1 if refine else 0, int(max_refine), float(inner_tol))
+    p = _SolveParams(float(tol), int(restart), int(max_iter), 1 if refine else 0, int(max_refine), float(inner_tol),
+                     precond.ptr if precond is not None else None)
     info = _SolveInfo()
     rc = _lib.rad_solve_flux(h.ptr, _ptr(e), _ptr(Tc), ldT, m, float(sigma), C.byref(p), _ptr(q), ldq,
                              C.byref(info), _stream(stream, e, Tc, q))
@@ -463,7 +480,7 @@ def rad_hmatvec_noalloc(h: HTree, x, y, stream=None):
 
 def rad_solve_reflection(h: HTree, eps, B, tol: float = 1e-10, restart: int = 30, max_iter: int = 1000,
                          Y=None, stream=None, raise_on_notconv: bool = False, refine: bool = False,
-                         inner_tol: float = 1e-4, max_refine: int = 10):
+                         inner_tol: float = 1e-4, max_refine: int = 10, precond=None):
     """A7: Y solving C Y = B (Eq. 11) for B (N,) or (N, nrhs).  Returns (Y, info)."""
     Bc, n, nrhs, ldB = _colmajor(B, np.float64)
     e = _f64_rowmajor(eps)
@@ -473,7 +490,8 @@ def rad_solve_reflection(h: HTree, eps, B, tol: float = 1e-10, restart: int = 30
             Y = t.empty((nrhs, n), dtype=t.float64, device=Bc.device).t()
         else:
             Y = np.empty((n, nrhs), dtype=np.float64, order="F")
-    p = _SolveParams(float(tol), int(restart), int(max_iter), 1 if refine else 0, int(max_refine), float(inner_tol))
+    p = _SolveParams(float(tol), int(restart), int(max_iter), 1 if refine else 0, int(max_refine), float(inner_tol),
+                     precond.ptr if precond is not None else None)
     info = _SolveInfo()
     rc = _lib.rad_solve_reflection(h.ptr, _ptr(e), _ptr(Bc), ldB, nrhs, C.byref(p), _ptr(Y), n, C.byref(info),
                                    _stream(stream, e, Bc, Y))
@@ -483,6 +501,77 @@ def rad_solve_reflection(h: HTree, eps, B, tol: float = 1e-10, restart: int = 30
     if (_is_tensor(B) and B.dim() == 1) or (not _is_tensor(B) and np.ndim(B) == 1):
         Y = Y[:, 0]
     return Y, d
+
+
+class HLU:
+    """Owns one ``rad_hlu*`` (block LU factors of the reflection matrix);
+    keeps its handle alive, freed with :func:`rad_hlu_free` or on GC."""
+
+    def __init__(self, ptr: int, h: HTree):
+        self._p = C.c_void_p(ptr)
+        self.h = h
+        self.n = h.n
+
+    @property
+    def ptr(self) -> C.c_void_p:
+        if not self._p:
+            raise RadError(RAD_EINVAL, "factors already freed")
+        return self._p
+
+    def free(self):
+        if self._p:
+            _lib.rad_hlu_free(self._p)
+            self._p = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def rad_hlu_factor(h: HTree, eps, tol: float, stream=None) -> HLU:
+    """§5.1: block LU of C = I - diag(1 - eps) F (the handle's stored F) with
+    the ranks of the admissible leaves truncated at ``tol``."""
+    e = _f64_rowmajor(eps)
+    p = _HluParams(float(tol), 0, 0)
+    out = C.c_void_p()
+    _check(_lib.rad_hlu_factor(h.ptr, _ptr(e), C.byref(p), _stream(stream, e), C.byref(out)))
+    return HLU(out.value, h)
+
+
+def rad_hlu_solve(lu: HLU, B, X=None, stream=None):
+    """§5.2: X = U^-1 L^-1 B by forward and backward substitution through the
+    block structure.  ``B`` (N,) or (N, nrhs), host or device."""
+    Bc, n, nrhs, ldB = _colmajor(B, np.float64)
+    if X is None:
+        if _is_tensor(Bc):
+            t = _torch()
+            X = t.empty((nrhs, n), dtype=t.float64, device=Bc.device).t()
+        else:
+            X = np.empty((n, nrhs), dtype=np.float64, order="F")
+    _check(_lib.rad_hlu_solve(lu.ptr, _ptr(Bc), ldB, nrhs, _ptr(X), n, _stream(stream, Bc, X)))
+    if (_is_tensor(B) and B.dim() == 1) or (not _is_tensor(B) and np.ndim(B) == 1):
+        X = X[:, 0]
+    return X
+
+
+def rad_hlu_get_stats(lu: HLU) -> dict:
+    st = _HluStats()
+    _check(_lib.rad_hlu_get_stats(lu.ptr, C.byref(st)))
+    return {k: getattr(st, k) for k, _ in _HluStats._fields_}
+
+
+def rad_hlu_export(lu: HLU) -> np.ndarray:
+    """The factors as one dense (N, N) array in tree order: L strictly below
+    the diagonal (unit diagonal), U on and above it."""
+    out = np.empty((lu.n, lu.n), dtype=np.float64)
+    _check(_lib.rad_hlu_export(lu.ptr, out.ctypes.data))
+    return out
+
+
+def rad_hlu_free(lu: HLU) -> None:
+    lu.free()
 
 
 class Server:

@@ -650,6 +650,8 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
         RAD_REQUIRE(ldT >= h->n && ldq >= h->n, RAD_EINVAL, "leading dimension smaller than n");
         RAD_REQUIRE(p->restart >= 1 && p->restart <= 64, RAD_EINVAL, "restart must be in [1, 64]");
         RAD_REQUIRE(p->max_iter >= 1, RAD_EINVAL, "max_iter must be >= 1");
+        RAD_REQUIRE(!p->precond || hlu_handle(p->precond) == h, RAD_EINVAL,
+                    "the preconditioner's factors belong to another handle");
         RAD_REQUIRE(p->tol > 0.0 && std::isfinite(p->tol), RAD_EINVAL, "tol must be > 0");
         RAD_REQUIRE(std::isfinite(sigma), RAD_EINVAL, "sigma must be finite");
         RAD_REQUIRE(!p->refine || h->has_accurate, RAD_EINVAL,
@@ -688,6 +690,8 @@ int rad_solve_reflection(const rad_htree* h, const double* eps, const double* B,
         RAD_REQUIRE(ldB >= h->n && ldY >= h->n, RAD_EINVAL, "leading dimension smaller than n");
         RAD_REQUIRE(p->restart >= 1 && p->restart <= 64, RAD_EINVAL, "restart must be in [1, 64]");
         RAD_REQUIRE(p->max_iter >= 1, RAD_EINVAL, "max_iter must be >= 1");
+        RAD_REQUIRE(!p->precond || hlu_handle(p->precond) == h, RAD_EINVAL,
+                    "the preconditioner's factors belong to another handle");
         RAD_REQUIRE(p->tol > 0.0 && std::isfinite(p->tol), RAD_EINVAL, "tol must be > 0");
         RAD_REQUIRE(!p->refine || h->has_accurate, RAD_EINVAL,
                     "refinement needs an accurate operator (compress with accurate_dtype = RAD_F32)");

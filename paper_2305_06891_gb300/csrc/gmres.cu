@@ -449,6 +449,18 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
         Epi epi{mode, eps_t, vin, mode == kResid ? B : nullptr, nc};
         apply_tree(h, op64 ? (const void*)vin : (const void*)vin32, op64 ? nc : ldp, out, nc, nc, epi, Tws, s);
     };
+    // right preconditioning with the block LU factors: the Krylov space is
+    // built on C (LU)^-1 and the update is x += (LU)^-1 V y
+    const rad_hlu* pre = p->precond;
+    double* Zp = pre ? ws.get_n<double>(nv) : nullptr;
+    auto precondition = [&](const double* vin, double* out) {
+        RAD_CUDA(cudaMemcpyAsync(out, vin, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+        hlu_apply_tree(pre, out, nc, s);
+        if (X32) {
+            { ProfScope ps_("gmres_convert", s); to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(out, X32, nv, nc, ldp); }
+            RAD_CHECK_LAUNCH();
+        }
+    };
 
     int total_iters = 0, restarts = 0, matvecs = 0, status = RAD_OK;
     double prev_max = INFINITY, max_rel = 0.0;
@@ -480,8 +492,13 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
         for (int j = 0; j < R && total_iters < p->max_iter; ++j) {
             double* Vj = V + (long long)j * nv;
             double* hcol = Hm + (long long)j * (R + 1) * nvc;
-            // w = C v_j
-            apply_C(Vj, X32, W, kReflect);
+            // w = C v_j  (C (LU)^-1 v_j when preconditioned)
+            if (pre) {
+                precondition(Vj, Zp);
+                apply_C(Zp, X32, W, kReflect);
+            } else {
+                apply_C(Vj, X32, W, kReflect);
+            }
             ++matvecs;
             // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2
             for (int pass = 0; pass < 2; ++pass) {
@@ -512,8 +529,18 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
         // x += V y
         { ProfScope ps_("gmres_small", s); trisolve_kernel<<<grid_for(nvc, 128), 128, 0, s>>>(R, nvc, Hm, g, jc, ycoef); }
         RAD_CHECK_LAUNCH();
-        { ProfScope ps_("gmres_update_x", s); update_x_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, R, ycoef, jc, X, n, nc, seg, nvc); }
-        RAD_CHECK_LAUNCH();
+        if (pre) {
+            // x += (LU)^-1 (V y)
+            RAD_CUDA(cudaMemsetAsync(W, 0, sizeof(double) * nv, s));
+            { ProfScope ps_("gmres_update_x", s); update_x_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, R, ycoef, jc, W, n, nc, seg, nvc); }
+            RAD_CHECK_LAUNCH();
+            hlu_apply_tree(pre, W, nc, s);
+            { ProfScope ps_("gmres_update_x", s); axpy_kernel<<<grid_for(nv), 256, 0, s>>>(X, W, nv); }
+            RAD_CHECK_LAUNCH();
+        } else {
+            { ProfScope ps_("gmres_update_x", s); update_x_kernel<<<grid_for(nv), 256, 0, s>>>(V, nv, R, ycoef, jc, X, n, nc, seg, nvc); }
+            RAD_CHECK_LAUNCH();
+        }
         // true residual r = b - C x
         if (X32) {
             { ProfScope ps_("gmres_convert", s); to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(X, X32, nv, nc, ldp); }

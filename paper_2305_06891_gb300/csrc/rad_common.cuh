@@ -508,6 +508,9 @@ void gather_user_to_tree(const rad_htree* h, int dtype_in, const void* x, int64_
                          void* X, int ldX, bool op64, cudaStream_t s);
 void scatter_tree_to_user(const rad_htree* h, const void* Y, int ldY, int nrhs, bool op64,
                           int dtype_out, void* y, int64_t ldy, cudaStream_t s);
+// hlu.cu: x = U^-1 L^-1 x on tree-order FP64 row-major vectors (n x nc)
+void hlu_apply_tree(const rad_hlu* lu, double* X, int nc, cudaStream_t s);
+const rad_htree* hlu_handle(const rad_hlu* lu);
 // gmres.cu
 void solve_flux(const rad_htree* h, const double* eps_dev, const double* T_dev, int64_t ldT,
                 int m, double sigma, const rad_solve_params* p, double* q_dev, int64_t ldq,

@@ -72,7 +72,8 @@ def test_binding_structs_match_the_header_layout(tmp_path):
                "rad_aca_params": rad._AcaParams, "rad_solve_params": rad._SolveParams,
                "rad_solve_info": rad._SolveInfo, "rad_htree_stats": rad._Stats,
                "rad_server_params": rad._ServerParams, "rad_request_info": rad._RequestInfo,
-               "rad_server_stats": rad._ServerStats}
+               "rad_server_stats": rad._ServerStats, "rad_hlu_params": rad._HluParams,
+               "rad_hlu_stats": rad._HluStats}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rad.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

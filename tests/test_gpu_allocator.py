@@ -2,6 +2,8 @@
 and host-side fault injection: an allocator that fails, and invalid solve
 inputs, each give an error status with nothing leaked and the GPU context
 still usable."""
+import gc
+
 import numpy as np
 import pytest
 
@@ -25,7 +27,8 @@ def _run(r, verts, eps, T, allocator=None):
     x = torch.as_tensor(SIGMA_SB * T ** 4, device="cuda", dtype=torch.float32)
     y = r.rad_hmatvec(h, x).cpu().numpy()
     q, info = r.rad_solve_flux(h, torch.as_tensor(eps, device="cuda"), torch.as_tensor(T, device="cuda"),
-                               SIGMA_SB, tol=1e-10)
+                               SIGMA_SB, tol=1e-6)
+    assert info["status"] == 0
     return h, y, q.cpu().numpy()
 
 
@@ -34,6 +37,7 @@ def test_every_handle_buffer_comes_from_torch_caching_allocator():
     r = rad()
     verts, eps, T = _cavity()
     _, y0, q0 = _run(r, verts, eps, T)
+    gc.collect()
     torch.cuda.synchronize()
     base = torch.cuda.memory_allocated()
     al = r.torch_allocator()
@@ -48,6 +52,7 @@ def test_every_handle_buffer_comes_from_torch_caching_allocator():
     # same kernels on the same bits: identical results
     assert np.array_equal(y0, y1) and np.array_equal(q0, q1)
     r.rad_htree_free(h)
+    gc.collect()
     torch.cuda.synchronize()
     assert al.live_bytes == 0 and not al.live and al.n_alloc == al.n_free
     assert torch.cuda.memory_allocated() == base
@@ -60,17 +65,20 @@ def test_failing_allocator_gives_enomem_and_leaks_nothing(fail_after):
     verts, eps, T = _cavity()
     al = r.torch_allocator(fail_after=fail_after)
     vd = torch.as_tensor(verts, device="cuda")
+    gc.collect()          # tensors other tests left to the collector
     torch.cuda.synchronize()
     base = torch.cuda.memory_allocated()
     h = None
     with pytest.raises(r.RadError) as e:
         h = r.rad_build_htree(vd, 32, 1.0, allocator=al)
         r.rad_compress_aca(h, 1e-6, 64, "partial", "f32", "f32")
-        r.rad_solve_flux(h, eps, T, SIGMA_SB, tol=1e-10)
+        r.rad_solve_flux(h, eps, T, SIGMA_SB, tol=1e-6)
     assert e.value.code == r.RAD_ENOMEM
     assert "allocator" in r.rad_last_error()
     if h is not None:
         r.rad_htree_free(h)
+    del e
+    gc.collect()
     torch.cuda.synchronize()
     assert al.live_bytes == 0 and al.n_alloc == al.n_free
     assert torch.cuda.memory_allocated() == base
@@ -95,7 +103,7 @@ def test_invalid_solve_inputs_are_rejected_before_solving():
             ea = torch.as_tensor(e2, device="cuda") if dev else e2
             Ta = torch.as_tensor(np.asfortranarray(T2), device="cuda") if dev else T2
             with pytest.raises(r.RadError) as ex:
-                r.rad_solve_flux(h, ea, Ta, SIGMA_SB, tol=1e-10)
+                r.rad_solve_flux(h, ea, Ta, SIGMA_SB, tol=1e-6)
             assert ex.value.code == r.RAD_EINVAL
     # only the input checks ran (one launch each), no solver kernel
     assert r.rad_launch_count() - l0 == 10
@@ -105,7 +113,7 @@ def test_invalid_solve_inputs_are_rejected_before_solving():
         r.rad_solve_reflection(h, eps, B, tol=1e-8)
     assert ex.value.code == r.RAD_EINVAL
     # the handle still solves correctly afterwards
-    q, info = r.rad_solve_flux(h, eps, T, SIGMA_SB, tol=1e-10)
+    q, info = r.rad_solve_flux(h, eps, T, SIGMA_SB, tol=1e-6)
     assert info["status"] == 0 and np.array_equal(q, q_ok)
     r.rad_htree_free(h)
 
@@ -116,8 +124,9 @@ def test_server_takes_every_operator_and_workspace_from_the_allocator():
     verts, eps, T = _cavity()
     results = []
     for al in (None, r.torch_allocator()):
-        srv = r.Server(slots=2, hbm_budget_bytes=1 << 30, leaf_size=32, aca_tol=1e-6, factor_dtype="f32",
-                       near_dtype="f32", accurate_dtype=None, tol=1e-10, refine=False, allocator=al)
+        srv = r.Server(slots=2, hbm_budget_bytes=8 << 30, leaf_size=32, aca_tol=1e-6, factor_dtype="f32",
+                       near_dtype="f32", accurate_dtype=None, tol=1e-6, refine=False, aca_scratch_mib=256,
+                       allocator=al)
         cid = srv.add_cavity(verts)
         tickets = [srv.submit(cid, eps, T[:, k:k + 1], SIGMA_SB) for k in range(3)]
         results.append([srv.wait(t)[0] for t in tickets])
