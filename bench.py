@@ -882,6 +882,67 @@ def served_summary(args, steps=None):
     return line
 
 
+def hlu_summary(args):
+    """The block LU of C (paper §5.1-5.2) on two operators: the unit cube
+    (768 facets, FP64, eps_rel 1e-4) and the headline cylinder (19,936
+    facets, FP32, eps_rel 1e-3): factor time and storage, one substitution,
+    and the flux solve with and without the factors as GMRES preconditioner.
+    The cube's direct apply is checked against the oracle's dense solve."""
+    import torch
+    import paper_2305_06891_gb300 as rad
+    from oracle import geometry, radiosity, viewfactor
+    dev = torch.device("cuda", 0)
+    out = {}
+    cases = (("cube_768_f64", cv.config1(), 32, 1e-8, "f64", 1e-4, 1e-10, 1),
+             ("cylinder_19936_f32", cv.config2(m=64), 64, 1e-5, "f32", 1e-3, 1e-7, 64))
+    for name, c, leaf, acatol, dt, lutol, stol, fields in cases:
+        h = rad.rad_build_htree(torch.as_tensor(c.verts, device=dev), leaf, 1.0)
+        rad.rad_compress_aca(h, acatol, 64, "partial", dt, dt)
+        ed = torch.as_tensor(c.eps, device=dev)
+        Td = torch.as_tensor(np.asfortranarray(c.T[:, :fields]), device=dev)
+        fms = []
+        lu = None
+        for _ in range(3):
+            if lu is not None:
+                lu.free()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lu = rad.rad_hlu_factor(h, ed, lutol)
+            fms.append(1e3 * (time.perf_counter() - t0))
+        st = rad.rad_hlu_get_stats(lu)
+        b = torch.as_tensor(np.random.default_rng(0).uniform(size=(c.n, fields + 1)), device=dev)
+        sms = []
+        for _ in range(4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x = rad.rad_hlu_solve(lu, b)
+            torch.cuda.synchronize()
+            sms.append(1e3 * (time.perf_counter() - t0))
+        d = {"facets": c.n, "precision": dt, "eps_rel": lutol, "factor_ms": statistics.median(fms),
+             "stored_entries": st["dense_entries"] + st["lowrank_entries"], "dense_lu_entries": c.n * c.n,
+             "lowrank_leaves": st["n_lowrank"], "max_rank": st["max_rank"],
+             "substitution_ms": statistics.median(sms[1:]), "substitution_steps": st["solve_launches"],
+             "substitution_columns": fields + 1}
+        for label, pre in (("gmres", None), ("gmres_hlu_preconditioned", lu)):
+            rad.rad_solve_flux(h, ed, Td, SIGMA, tol=stol, restart=RESTART, max_iter=600, precond=pre)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q, info = rad.rad_solve_flux(h, ed, Td, SIGMA, tol=stol, restart=RESTART, max_iter=600, precond=pre)
+            torch.cuda.synchronize()
+            ms = 1e3 * (time.perf_counter() - t0)
+            d[label] = {"iters": info["iters"], "ms": ms, "solves_per_s": fields / (ms * 1e-3),
+                        "max_rel_residual": info["max_rel_residual"]}
+        if c.n <= 5000:
+            F = viewfactor.dense(geometry.facets_from_triangles(c.verts))
+            C = radiosity.reflection_matrix(F, c.eps)
+            xe = np.linalg.solve(C, b.cpu().numpy())
+            d["direct_apply_rel_err"] = rel_err(x.cpu().numpy(), xe)
+        out[name] = d
+        lu.free()
+        h.free()
+    return out
+
+
 def served_oracle_estimate(pool, reqs, seed=0):
     """The oracle factors each request's cavity (no reuse); per-unit costs
     measured on a bounded sample of the median pool cavity, extrapolated to
@@ -999,6 +1060,10 @@ def main():
             wl["served"] = served_summary(args, steps=3)
         except Exception as e:
             wl["served"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        try:
+            wl["hlu"] = hlu_summary(args)
+        except Exception as e:
+            wl["hlu"] = {"error": f"{type(e).__name__}: {e}"[:300]}
         select_workload(head)
         line["workloads"] = wl
     print(json.dumps(line), flush=True)

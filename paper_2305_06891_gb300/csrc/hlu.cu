@@ -58,7 +58,6 @@ namespace {
 
 constexpr int kHluMaxLeaf = 128;   // diagonal leaves factorised in shared memory
 constexpr int kHluMaxRank = 64;    // rank capacity of a truncated leaf
-constexpr int kTrsmCols = 32;      // right-hand sides per CTA of the triangular solves
 
 template <class T> __device__ __forceinline__ T eps_mach();
 template <> __device__ __forceinline__ double eps_mach<double>() { return 2.220446049250313e-16; }
@@ -150,69 +149,63 @@ __global__ void __launch_bounds__(256) hlu_lu_leaf_kernel(T* __restrict__ M, lon
 }
 
 // Triangular solves with an m x m triangle Tr (column-major, leading dim
-// ldt) on nc right-hand sides X(l, c) = X[l rs + c cs], l < m:
+// ldt, m <= 128) on nc right-hand sides X(l, c) = X[l rs + c cs], l < m:
 //   kLowerUnit: X := L^-1 X,   L the unit lower triangle of Tr
 //   kUpperT:    X := U^-T X,   U the upper triangle of Tr (so X^T := X^T U^-1)
 //   kUpper:     X := U^-1 X
-// One CTA per kTrsmCols right-hand sides; the triangle and the CTA's
-// columns are staged in shared memory, one barrier per eliminated row.
+// One warp per right-hand side: lane j holds rows j, j + 32, j + 64, j + 96
+// in registers; each eliminated value is broadcast by a shuffle, so there is
+// no barrier and no shared memory.
 enum TrsmMode { kLowerUnit = 0, kUpperT = 1, kUpper = 2 };
 template <class T, int MODE>
 __global__ void __launch_bounds__(256) hlu_trsm_kernel(const T* __restrict__ Tr, long long ldt, int m,
                                                        T* __restrict__ X, long long rs, long long cs, int nc) {
-    extern __shared__ unsigned char smem_raw[];
-    T* L = reinterpret_cast<T*>(smem_raw);            // m x m
-    T* Xs = L + m * m;                                // m x kTrsmCols, Xs[l + c m]
-    const int c0 = blockIdx.x * kTrsmCols;
-    const int cw = min(kTrsmCols, nc - c0);
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[e] = Tr[(e % m) + (long long)(e / m) * ldt];
-    if (rs == 1) {
-        for (int e = threadIdx.x; e < m * cw; e += blockDim.x) {
-            const int l = e % m, c = e / m;
-            Xs[l + c * m] = X[l + (long long)(c0 + c) * cs];
-        }
-    } else {
-        for (int e = threadIdx.x; e < m * cw; e += blockDim.x) {
-            const int c = e % cw, l = e / cw;
-            Xs[l + c * m] = X[(long long)l * rs + (long long)(c0 + c) * cs];
-        }
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= nc) return;                       // whole warps leave together
+    T* x = X + (long long)c * cs;
+    T v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int l = lane + 32 * q;
+        v[q] = l < m ? x[(long long)l * rs] : T(0);
     }
-    __syncthreads();
     if (MODE == kUpper) {
-        for (int k = m - 1; k >= 0; --k) {
-            for (int c = threadIdx.x; c < cw; c += blockDim.x) Xs[k + c * m] /= L[k + k * m];
-            __syncthreads();
-            for (int e = threadIdx.x; e < k * cw; e += blockDim.x) {
-                const int i = e % k, c = e / k;
-                Xs[i + c * m] -= L[i + k * m] * Xs[k + c * m];
+#pragma unroll
+        for (int q = 3; q >= 0; --q) {
+            for (int kk = 31; kk >= 0; --kk) {
+                const int k = 32 * q + kk;
+                if (k >= m) continue;
+                if (lane == kk) v[q] /= Tr[k + (long long)k * ldt];
+                const T xk = __shfl_sync(0xffffffffu, v[q], kk);
+#pragma unroll
+                for (int p = 0; p <= q; ++p) {
+                    const int i = lane + 32 * p;
+                    if (i < k) v[p] -= Tr[i + (long long)k * ldt] * xk;
+                }
             }
-            __syncthreads();
         }
     } else {
-        for (int k = 0; k < m; ++k) {
-            if (MODE == kUpperT) {
-                for (int c = threadIdx.x; c < cw; c += blockDim.x) Xs[k + c * m] /= L[k + k * m];
-                __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            for (int kk = 0; kk < 32; ++kk) {
+                const int k = 32 * q + kk;
+                if (k >= m) break;
+                if (MODE == kUpperT && lane == kk) v[q] /= Tr[k + (long long)k * ldt];
+                const T xk = __shfl_sync(0xffffffffu, v[q], kk);
+#pragma unroll
+                for (int p = q; p < 4; ++p) {
+                    const int i = lane + 32 * p;
+                    if (i > k && i < m)
+                        v[p] -= (MODE == kLowerUnit ? Tr[i + (long long)k * ldt] : Tr[k + (long long)i * ldt]) * xk;
+                }
             }
-            const int rem = m - k - 1;
-            for (int e = threadIdx.x; e < rem * cw; e += blockDim.x) {
-                const int i = k + 1 + e % rem, c = e / rem;
-                const T a = MODE == kLowerUnit ? L[i + k * m] : L[k + i * m];
-                Xs[i + c * m] -= a * Xs[k + c * m];
-            }
-            __syncthreads();
         }
     }
-    if (rs == 1) {
-        for (int e = threadIdx.x; e < m * cw; e += blockDim.x) {
-            const int l = e % m, c = e / m;
-            X[l + (long long)(c0 + c) * cs] = Xs[l + c * m];
-        }
-    } else {
-        for (int e = threadIdx.x; e < m * cw; e += blockDim.x) {
-            const int c = e % cw, l = e / cw;
-            X[(long long)l * rs + (long long)(c0 + c) * cs] = Xs[l + c * m];
-        }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int l = lane + 32 * q;
+        if (l < m) x[(long long)l * rs] = v[q];
     }
 }
 
@@ -550,12 +543,26 @@ template <class T>
 __global__ void __launch_bounds__(256) hlu_region_vt_kernel(const RegLR* __restrict__ jobs, const T* __restrict__ up,
                                                             const T* __restrict__ x, int nc, T* __restrict__ t) {
     const RegLR jb = jobs[blockIdx.x];
-    for (int e = threadIdx.x; e < jb.k * nc; e += blockDim.x) {
+    if (nc >= 32) {
+        // a thread per output (l, c), c fastest: coalesced reads of x rows
+        for (int e = threadIdx.x; e < jb.k * nc; e += blockDim.x) {
+            const int l = e / nc, c = e % nc;
+            const T* v = up + jb.voff + (long long)l * jb.n;
+            T s = 0;
+            for (int j = 0; j < jb.n; ++j) s += v[j] * x[(long long)(jb.c0 + j) * nc + c];
+            t[(long long)jb.toff * nc + e] = s;
+        }
+        return;
+    }
+    // few right-hand sides: a warp per output, lanes along the dot product
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int e = warp; e < jb.k * nc; e += 8) {
         const int l = e / nc, c = e % nc;
         const T* v = up + jb.voff + (long long)l * jb.n;
         T s = 0;
-        for (int j = 0; j < jb.n; ++j) s += v[j] * x[(long long)(jb.c0 + j) * nc + c];
-        t[(long long)jb.toff * nc + e] = s;
+        for (int j = lane; j < jb.n; j += 32) s += v[j] * x[(long long)(jb.c0 + j) * nc + c];
+        s = warp_sum(s);
+        if (lane == 0) t[(long long)jb.toff * nc + e] = s;
     }
 }
 // Phase 2: one CTA per row segment (a leaf cluster of the region's rows);
@@ -689,12 +696,11 @@ struct HluBuilder {
 
     void trsm(int mode, const T* Tr, long long ldt, int m, T* X, long long rs, long long cs, int nc) {
         if (nc <= 0 || m <= 0) return;
-        const size_t sm = ((size_t)m * m + (size_t)m * kTrsmCols) * sizeof(T);
-        const unsigned grid = (unsigned)((nc + kTrsmCols - 1) / kTrsmCols);
+        const unsigned grid = (unsigned)((nc + 7) / 8);
         ProfScope ps_("hlu_trsm", s);
-        if (mode == kLowerUnit) hlu_trsm_kernel<T, kLowerUnit><<<grid, 256, sm, s>>>(Tr, ldt, m, X, rs, cs, nc);
-        else if (mode == kUpperT) hlu_trsm_kernel<T, kUpperT><<<grid, 256, sm, s>>>(Tr, ldt, m, X, rs, cs, nc);
-        else hlu_trsm_kernel<T, kUpper><<<grid, 256, sm, s>>>(Tr, ldt, m, X, rs, cs, nc);
+        if (mode == kLowerUnit) hlu_trsm_kernel<T, kLowerUnit><<<grid, 256, 0, s>>>(Tr, ldt, m, X, rs, cs, nc);
+        else if (mode == kUpperT) hlu_trsm_kernel<T, kUpperT><<<grid, 256, 0, s>>>(Tr, ldt, m, X, rs, cs, nc);
+        else hlu_trsm_kernel<T, kUpper><<<grid, 256, 0, s>>>(Tr, ldt, m, X, rs, cs, nc);
         RAD_CHECK_LAUNCH();
     }
     void gemm(int m, int nn, int k, const T* A, long long lda, const T* B, long long ldb, T* C, long long ldc) {
@@ -847,9 +853,6 @@ void set_smem_limits() {
     if (done) return;
     const int big = 200 * 1024;
     RAD_CUDA(cudaFuncSetAttribute(hlu_lu_leaf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    RAD_CUDA(cudaFuncSetAttribute(hlu_trsm_kernel<T, kLowerUnit>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    RAD_CUDA(cudaFuncSetAttribute(hlu_trsm_kernel<T, kUpperT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    RAD_CUDA(cudaFuncSetAttribute(hlu_trsm_kernel<T, kUpper>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     RAD_CUDA(cudaFuncSetAttribute(hlu_truncate_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     done = true;
 }
@@ -1096,15 +1099,14 @@ void substitute_t(const rad_hlu* lu, T* X, int nc, T* tws, cudaStream_t s) {
         for (const rad_hlu::Op& op : ops) {
             if (op.kind == 0 || op.kind == 1) {
                 const int m = op.m;
-                const size_t sm = ((size_t)m * m + (size_t)m * kTrsmCols) * sizeof(T);
-                const unsigned grid = (unsigned)((nc + kTrsmCols - 1) / kTrsmCols);
+                const unsigned grid = (unsigned)((nc + 7) / 8);
                 ProfScope ps_("hlu_solve_leaf", s);
                 if (op.kind == 0)
-                    hlu_trsm_kernel<T, kLowerUnit><<<grid, 256, sm, s>>>(dp + op.doff, m, m, X + (long long)op.r0 * nc,
-                                                                         nc, 1, nc);
+                    hlu_trsm_kernel<T, kLowerUnit><<<grid, 256, 0, s>>>(dp + op.doff, m, m, X + (long long)op.r0 * nc,
+                                                                        nc, 1, nc);
                 else
-                    hlu_trsm_kernel<T, kUpper><<<grid, 256, sm, s>>>(dp + op.doff, m, m, X + (long long)op.r0 * nc, nc,
-                                                                     1, nc);
+                    hlu_trsm_kernel<T, kUpper><<<grid, 256, 0, s>>>(dp + op.doff, m, m, X + (long long)op.r0 * nc, nc,
+                                                                    1, nc);
                 RAD_CHECK_LAUNCH();
             } else {
                 if (op.lr1 > op.lr0) {
