@@ -446,6 +446,19 @@ int rad_htree_export_block(const rad_htree* h, int64_t block, double* D, double*
 
 int rad_htree_free(rad_htree* h);
 
+/* Checkpoint and resume (no counterpart in the paper): rad_htree_save writes
+ * everything the handle holds (trees, block partition, compressed operator,
+ * work lists, tuning) into buf.  With buf = NULL it only stores the size in
+ * *bytes; otherwise *bytes is the buffer's size on entry (RAD_ELIMIT if too
+ * small) and the bytes written on return.  Synchronises the device.
+ * rad_htree_load builds an identical handle on the current device from such
+ * a blob (p may be NULL; only p->allocator is used, as in rad_build_htree):
+ * products and solves on it give the same results bit for bit.  A blob that
+ * is truncated, from another format version or inconsistent gives RAD_EINVAL
+ * before any device work.  Synchronous on `stream`. */
+int rad_htree_save(const rad_htree* h, void* buf, uint64_t* bytes);
+int rad_htree_load(const void* buf, uint64_t bytes, const rad_tree_params* p, void* stream, rad_htree** out);
+
 const char* rad_last_error(void);
 
 /* ------------------------------------------------------------ tracing
@@ -532,6 +545,14 @@ int rad_server_destroy(rad_server* s);
 
 /* Library version: major * 10000 + minor * 100 + patch. */
 int rad_version(void);
+
+/* 1 in the bounds-checked build of this library (librad_checked.so, built
+ * with RAD_CHECK_BOUNDS), 0 otherwise.  In that build every device
+ * allocation carries 256 canary bytes on each side; they are verified when
+ * the memory is returned and before every call returns, and a call after
+ * which one was overwritten returns RAD_ECUDA ("bounds check: ...").  The
+ * checks synchronise the device and are meant for testing, not speed. */
+int rad_debug_bounds_checks(void);
 
 #ifdef __cplusplus
 }

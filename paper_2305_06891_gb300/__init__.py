@@ -19,7 +19,9 @@ import re
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "librad.so")
+# RAD_LIB=checked loads the bounds-checked build (librad_checked.so: canary
+# words around every device allocation, verified after every call)
+LIB_PATH = os.path.join(_HERE, "librad_checked.so" if os.environ.get("RAD_LIB") == "checked" else "librad.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "rad.h")
 
 SIGMA_SB = 5.670374419e-8
@@ -184,6 +186,7 @@ def _load():
     H = C.c_void_p
     sig = {
         "rad_version": (C.c_int, []),
+        "rad_debug_bounds_checks": (C.c_int, []),
         "rad_last_error": (C.c_char_p, []),
         "rad_build_htree": (C.c_int, [i64, vp, C.POINTER(_TreeParams), vp, C.POINTER(H)]),
         "rad_build_htree_facets": (C.c_int, [i64, vp, vp, vp, C.POINTER(_TreeParams), vp, C.POINTER(H)]),
@@ -210,6 +213,8 @@ def _load():
         "rad_server_wait": (C.c_int, [vp, i64, C.POINTER(_RequestInfo)]),
         "rad_server_get_stats": (C.c_int, [vp, C.POINTER(_ServerStats)]),
         "rad_server_destroy": (C.c_int, [vp]),
+        "rad_htree_save": (C.c_int, [H, vp, C.POINTER(C.c_uint64)]),
+        "rad_htree_load": (C.c_int, [vp, C.c_uint64, C.POINTER(_TreeParams), vp, C.POINTER(H)]),
         "rad_hlu_factor": (C.c_int, [H, vp, C.POINTER(_HluParams), vp, C.POINTER(vp)]),
         "rad_hlu_solve": (C.c_int, [vp, vp, i64, i64, vp, i64, vp]),
         "rad_hlu_get_stats": (C.c_int, [vp, C.POINTER(_HluStats)]),
@@ -340,6 +345,11 @@ class HTree:
 
 def rad_version() -> int:
     return _lib.rad_version()
+
+
+def rad_debug_bounds_checks() -> bool:
+    """True when the loaded library is the bounds-checked build."""
+    return bool(_lib.rad_debug_bounds_checks())
 
 
 def rad_last_error() -> str:
@@ -722,6 +732,25 @@ def rad_htree_export_block(h: HTree, b: int, m: int, n: int, rank: int):
     _check(_lib.rad_htree_export_block(h.ptr, int(b), None, C.c_void_p(U.ctypes.data) if rank else None,
                                        C.c_void_p(V.ctypes.data) if rank else None))
     return U, V
+
+
+def rad_htree_save(h: HTree) -> bytes:
+    """Checkpoint of the handle (trees, compressed operator, work lists)."""
+    size = C.c_uint64(0)
+    _check(_lib.rad_htree_save(h.ptr, None, C.byref(size)))
+    buf = C.create_string_buffer(size.value)
+    _check(_lib.rad_htree_save(h.ptr, buf, C.byref(size)))
+    return buf.raw[:size.value]
+
+
+def rad_htree_load(blob: bytes, stream=None, allocator: Allocator | None = None) -> HTree:
+    """A handle identical to the one ``blob`` was saved from, on the current device."""
+    data = bytes(blob)
+    out = C.c_void_p()
+    p = _tree_params(1, 1.0, allocator)
+    _check(_lib.rad_htree_load(data, len(data), C.byref(p), _stream(stream), C.byref(out)))
+    n = int(np.frombuffer(data[12 + 8:12 + 16], dtype=np.int64)[0])
+    return HTree(out.value, n, allocator)
 
 
 def rad_htree_free(h: HTree) -> None:

@@ -252,8 +252,7 @@ const Allocator& current_allocator() { return g_cur_alloc; }
 AllocScope::AllocScope(const Allocator& a) : prev(g_cur_alloc) { g_cur_alloc = a; }
 AllocScope::~AllocScope() { g_cur_alloc = prev; }
 
-void* Allocator::get(size_t bytes, cudaStream_t s) const {
-    if (bytes == 0) bytes = 16;
+static void* raw_get(const rad_allocator& cb, size_t bytes, cudaStream_t s) {
     void* p = nullptr;
     if (cb.alloc) {
         p = cb.alloc(cb.ctx, (uint64_t)bytes, s);
@@ -263,13 +262,97 @@ void* Allocator::get(size_t bytes, cudaStream_t s) const {
     RAD_CUDA(cudaMallocFromPoolAsync(&p, bytes, library_pool(), s));
     return p;
 }
-void Allocator::put(void* p, size_t bytes, cudaStream_t s) const {
-    if (!p) return;
+static void raw_put(const rad_allocator& cb, void* p, size_t bytes, cudaStream_t s) {
     if (cb.alloc) {
-        if (cb.free) cb.free(cb.ctx, p, (uint64_t)(bytes ? bytes : 16), s);
+        if (cb.free) cb.free(cb.ctx, p, (uint64_t)bytes, s);
         return;
     }
     if (cudaFreeAsync(p, s) != cudaSuccess) (void)cudaGetLastError();
+}
+
+#ifdef RAD_CHECK_BOUNDS
+// Bounds-checked build: every device allocation carries kGuard canary bytes
+// (value kCanary) before and after the bytes handed out.  The guards are
+// verified when the memory is returned and after every C-ABI call; a
+// changed canary byte means a kernel wrote outside its buffer, and the call
+// returns RAD_ECUDA naming the allocation.
+namespace {
+constexpr size_t kGuard = 256;
+constexpr unsigned char kCanary = 0xA5;
+std::mutex g_guard_mu;
+std::map<void*, size_t> g_guarded;   // handed-out pointer -> bytes
+std::string g_guard_error;
+bool guards_intact(void* user, size_t bytes) {
+    unsigned char g[2 * kGuard];
+    unsigned char* base = static_cast<unsigned char*>(user) - kGuard;
+    if (cudaMemcpy(g, base, kGuard, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(g + kGuard, static_cast<unsigned char*>(user) + bytes, kGuard, cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    for (unsigned char c : g)
+        if (c != kCanary) return false;
+    return true;
+}
+}  // namespace
+#endif
+
+void* Allocator::get(size_t bytes, cudaStream_t s) const {
+    if (bytes == 0) bytes = 16;
+#ifdef RAD_CHECK_BOUNDS
+    const size_t total = (bytes + 255) / 256 * 256 + 2 * kGuard;
+    unsigned char* base = static_cast<unsigned char*>(raw_get(cb, total, s));
+    RAD_CUDA(cudaMemsetAsync(base, kCanary, kGuard, s));
+    RAD_CUDA(cudaMemsetAsync(base + kGuard + bytes, kCanary, total - kGuard - bytes, s));
+    RAD_CUDA(cudaStreamSynchronize(s));   // canaries in place before anyone checks them
+    {
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        g_guarded[base + kGuard] = bytes;
+    }
+    return base + kGuard;
+#else
+    return raw_get(cb, bytes, s);
+#endif
+}
+void Allocator::put(void* p, size_t bytes, cudaStream_t s) const {
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+#ifdef RAD_CHECK_BOUNDS
+    (void)cudaStreamSynchronize(s);
+    {
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        if (!guards_intact(p, bytes) && g_guard_error.empty())
+            g_guard_error = "bounds check: canary overwritten around a device allocation of " +
+                            std::to_string(bytes) + " bytes";
+        g_guarded.erase(p);
+    }
+    raw_put(cb, static_cast<unsigned char*>(p) - kGuard, (bytes + 255) / 256 * 256 + 2 * kGuard, s);
+#else
+    raw_put(cb, p, bytes, s);
+#endif
+}
+
+// After a C-ABI call: in the bounds-checked build, waits for the device and
+// verifies every live allocation's canaries; fails with RAD_ECUDA if one was
+// overwritten (during this call or when memory was returned).  A no-op in
+// the ordinary build.
+void check_bounds_after_call() {
+#ifdef RAD_CHECK_BOUNDS
+    (void)cudaDeviceSynchronize();
+    std::string err;
+    {
+        // under the lock: no allocation is returned (and reused) while its
+        // canaries are read
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        for (auto& e : g_guarded)
+            if (!guards_intact(e.first, e.second) && g_guard_error.empty())
+                g_guard_error = "bounds check: canary overwritten around a device allocation of " +
+                                std::to_string(e.second) + " bytes";
+        err.swap(g_guard_error);
+    }
+    if (!err.empty()) fail(RAD_ECUDA, err);
+#endif
 }
 
 void DevBuf::alloc(size_t b, cudaStream_t s) {
@@ -321,9 +404,11 @@ static const void* stage_in_2d(const void* p, int64_t rows, int64_t cols, int64_
 }
 
 template <class F>
-static int guarded(F&& f) {
+static int guarded(const char* name, F&& f) {
+    NvtxRange nv_(name);
     try {
         f();
+        check_bounds_after_call();
         return RAD_OK;
     } catch (const Error& e) {
         g_last_error = e.msg;
@@ -438,7 +523,15 @@ static bool product_via_graph(const rad_htree* h, int32_t dtype, const void* x, 
 
 extern "C" {
 
-int rad_version(void) { return 10000; }
+int rad_version(void) { return 10100; }
+
+int rad_debug_bounds_checks(void) {
+#ifdef RAD_CHECK_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 int64_t rad_launch_count(void) { return g_launches.load(); }
 
@@ -479,7 +572,7 @@ int rad_profile_read(int32_t max_kernels, char* names, int64_t* counts, double* 
 const char* rad_last_error(void) { return g_last_error.c_str(); }
 
 int rad_build_htree(int64_t n, const double* verts, const rad_tree_params* p, void* stream, rad_htree** out) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(out != nullptr && verts != nullptr, RAD_EINVAL, "null argument");
         *out = nullptr;
         check_tree_params(n, p);
@@ -503,7 +596,7 @@ int rad_build_htree(int64_t n, const double* verts, const rad_tree_params* p, vo
 
 int rad_build_htree_batch(int32_t n_cavities, const int64_t* counts, const double* verts, const rad_tree_params* p,
                           void* stream, rad_htree** out) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(out != nullptr && verts != nullptr && counts != nullptr, RAD_EINVAL, "null argument");
         *out = nullptr;
         RAD_REQUIRE(n_cavities >= 1, RAD_EINVAL, "n_cavities must be >= 1");
@@ -542,7 +635,7 @@ int rad_build_htree_batch(int32_t n_cavities, const int64_t* counts, const doubl
 
 int rad_build_htree_facets(int64_t n, const double* centroid, const double* normal, const double* area,
                            const rad_tree_params* p, void* stream, rad_htree** out) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(out != nullptr && centroid && normal && area, RAD_EINVAL, "null argument");
         *out = nullptr;
         check_tree_params(n, p);
@@ -567,7 +660,7 @@ int rad_build_htree_facets(int64_t n, const double* centroid, const double* norm
 }
 
 int rad_htree_from_dense(int64_t n, const double* F, void* stream, rad_htree** out) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(out != nullptr && F != nullptr, RAD_EINVAL, "null argument");
         *out = nullptr;
         RAD_REQUIRE(n >= 1 && n <= 46340, RAD_EINVAL, "n must be in [1, 46340]");
@@ -595,7 +688,7 @@ int rad_htree_from_dense(int64_t n, const double* F, void* stream, rad_htree** o
 }
 
 int rad_compress_aca(rad_htree* h, const rad_aca_params* p, void* stream) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null handle");
         AllocScope as(h->alloc);
         compress(h, p, static_cast<cudaStream_t>(stream));
@@ -605,7 +698,7 @@ int rad_compress_aca(rad_htree* h, const rad_aca_params* p, void* stream) {
 
 int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx, void* y, int64_t ldy, int64_t nrhs,
                 void* stream) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(h != nullptr && x != nullptr && y != nullptr, RAD_EINVAL, "null argument");
         AllocScope as(h->alloc);
         RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed (call rad_compress_aca)");
@@ -642,7 +735,7 @@ int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx, v
 int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64_t ldT, int64_t m, double sigma,
                    const rad_solve_params* p, double* q, int64_t ldq, rad_solve_info* info, void* stream) {
     int solve_status = RAD_OK;
-    const int rc = guarded([&] {
+    const int rc = guarded(__func__, [&] {
         RAD_REQUIRE(h != nullptr && eps && T && q && p, RAD_EINVAL, "null argument");
         AllocScope as(h->alloc);
         RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed (call rad_compress_aca)");
@@ -682,7 +775,7 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
 int rad_solve_reflection(const rad_htree* h, const double* eps, const double* B, int64_t ldB, int64_t nrhs,
                          const rad_solve_params* p, double* Y, int64_t ldY, rad_solve_info* info, void* stream) {
     int solve_status = RAD_OK;
-    const int rc = guarded([&] {
+    const int rc = guarded(__func__, [&] {
         RAD_REQUIRE(h != nullptr && eps && B && Y && p, RAD_EINVAL, "null argument");
         AllocScope as(h->alloc);
         RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed (call rad_compress_aca)");
@@ -719,7 +812,7 @@ int rad_solve_reflection(const rad_htree* h, const double* eps, const double* B,
 }
 
 int rad_htree_get_stats(const rad_htree* h, rad_htree_stats* st) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(h != nullptr && st != nullptr, RAD_EINVAL, "null argument");
         std::memset(st, 0, sizeof(*st));
         st->n = h->n;
@@ -759,7 +852,7 @@ int rad_htree_get_stats(const rad_htree* h, rad_htree_stats* st) {
 
 int rad_htree_export_tree(const rad_htree* h, int32_t* perm, int32_t* begin, int32_t* end, int32_t* level,
                           int32_t* child, double* bbox) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null handle");
         if (perm) std::memcpy(perm, h->perm_h.data(), sizeof(int32_t) * h->perm_h.size());
         for (size_t q = 0; q < h->nodes.size(); ++q) {
@@ -782,7 +875,7 @@ int rad_htree_export_tree(const rad_htree* h, int32_t* perm, int32_t* begin, int
 
 int rad_htree_export_blocks(const rad_htree* h, int32_t* row_node, int32_t* col_node, int32_t* admissible,
                             int32_t* rank) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null handle");
         for (size_t b = 0; b < h->blocks.size(); ++b) {
             const BlockH& bk = h->blocks[b];
@@ -795,7 +888,7 @@ int rad_htree_export_blocks(const rad_htree* h, int32_t* row_node, int32_t* col_
 }
 
 int rad_htree_export_block(const rad_htree* h, int64_t block, double* D, double* U, double* V) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null handle");
         AllocScope as(h->alloc);
         export_block(h, block, D, U, V);
@@ -803,7 +896,7 @@ int rad_htree_export_block(const rad_htree* h, int64_t block, double* D, double*
 }
 
 int rad_htree_autotune(rad_htree* h, void* stream) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null argument");
         AllocScope as(h->alloc);
         autotune(h, static_cast<cudaStream_t>(stream));
@@ -811,7 +904,7 @@ int rad_htree_autotune(rad_htree* h, void* stream) {
 }
 
 int rad_htree_close_cavity(rad_htree* h, double* row_sums, void* stream) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null argument");
         AllocScope as(h->alloc);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -830,7 +923,7 @@ int rad_htree_close_cavity(rad_htree* h, double* row_sums, void* stream) {
 }
 
 int rad_htree_set_product_path(rad_htree* h, int32_t path) {
-    return guarded([&] {
+    return guarded(__func__, [&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null argument");
         RAD_REQUIRE(path == 0 || path == 1, RAD_EINVAL, "path must be 0 (CUDA cores) or 1 (tensor cores)");
         drop_product_graph(h);
@@ -839,7 +932,7 @@ int rad_htree_set_product_path(rad_htree* h, int32_t path) {
 }
 
 int rad_htree_free(rad_htree* h) {
-    return guarded([&] { delete h; });
+    return guarded(__func__, [&] { delete h; });
 }
 
 }  // extern "C"

@@ -1155,6 +1155,7 @@ using namespace rad;
 extern "C" {
 
 int rad_hlu_factor(const rad_htree* h, const double* eps, const rad_hlu_params* p, void* stream, rad_hlu** out) {
+    NvtxRange nv_(__func__);
     try {
         RAD_REQUIRE(h != nullptr && eps != nullptr && p != nullptr && out != nullptr, RAD_EINVAL, "null argument");
         *out = nullptr;
@@ -1186,6 +1187,7 @@ int rad_hlu_factor(const rad_htree* h, const double* eps, const rad_hlu_params* 
         if (lu->f64) factor_t<double>(lu.get(), epsd, s);
         else factor_t<float>(lu.get(), epsd, s);
         lu->factor_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        check_bounds_after_call();
         *out = lu.release();
         return RAD_OK;
     } catch (const Error& e) {
@@ -1199,6 +1201,7 @@ int rad_hlu_factor(const rad_htree* h, const double* eps, const rad_hlu_params* 
 
 int rad_hlu_solve(const rad_hlu* lu, const double* B, int64_t ldB, int64_t nrhs, double* X, int64_t ldX,
                   void* stream) {
+    NvtxRange nv_(__func__);
     try {
         RAD_REQUIRE(lu != nullptr && B != nullptr && X != nullptr, RAD_EINVAL, "null argument");
         RAD_REQUIRE(nrhs >= 1 && nrhs <= 4096, RAD_EINVAL, "nrhs must be in [1, 4096]");
@@ -1226,6 +1229,7 @@ int rad_hlu_solve(const rad_hlu* lu, const double* B, int64_t ldB, int64_t nrhs,
             RAD_CUDA(cudaMemcpy2DAsync(X, 8 * ldX, Xd, 8 * (size_t)n, 8 * (size_t)n, nr, cudaMemcpyDeviceToHost, s));
         }
         RAD_CUDA(cudaStreamSynchronize(s));
+        check_bounds_after_call();
         return RAD_OK;
     } catch (const Error& e) {
         set_last_error(e.msg);
@@ -1256,6 +1260,7 @@ int rad_hlu_get_stats(const rad_hlu* lu, rad_hlu_stats* st) {
 }
 
 int rad_hlu_export(const rad_hlu* lu, double* LU) {
+    NvtxRange nv_(__func__);
     try {
         RAD_REQUIRE(lu != nullptr && LU != nullptr, RAD_EINVAL, "null argument");
         const int n = lu->n;

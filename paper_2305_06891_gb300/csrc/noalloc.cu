@@ -63,6 +63,7 @@ using namespace rad;
 
 extern "C" int rad_hmatvec_noalloc(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx, void* y,
                                    int64_t ldy, int64_t nrhs, void* stream) {
+    NvtxRange nv_(__func__);
     try {
         RAD_REQUIRE(h != nullptr && x != nullptr && y != nullptr, RAD_EINVAL, "null argument");
         RAD_REQUIRE(h->compressed, RAD_EINVAL, "handle is not compressed (call rad_compress_aca)");
@@ -101,6 +102,7 @@ extern "C" int rad_hmatvec_noalloc(const rad_htree* h, int32_t dtype, const void
         gather_user_to_tree(h, dtype, x, ldx, nr, X, ldp, op64, s);
         apply_tree(h, X, ldp, Y, nr, nr, Epi{kStore, nullptr, nullptr, nullptr, 0}, T, s);
         scatter_tree_to_user(h, Y, nr, nr, op64, dtype, y, ldy, s);
+        check_bounds_after_call();
         return RAD_OK;
     } catch (const Error& e) {
         set_last_error(e.msg);

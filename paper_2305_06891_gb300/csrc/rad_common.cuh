@@ -16,9 +16,20 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rad.h"
 
 namespace rad {
+
+// NVTX range around one C-ABI call, named after it: visible on the timeline
+// of Nsight tools, a no-op when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ------------------------------------------------------------ error plumbing
 struct Error {
@@ -75,6 +86,11 @@ struct HostScope {
     do {                                      \
         if (!(cond)) ::rad::fail(code, msg);  \
     } while (0)
+
+// Bounds-checked build (-DRAD_CHECK_BOUNDS, librad_checked.so): verifies the
+// canary words around every device allocation; call before an entry point
+// returns RAD_OK.  A no-op in the ordinary build.
+void check_bounds_after_call();
 
 // ------------------------------------------------------------ memory helpers
 // Where device memory comes from: the caller's rad_allocator callbacks, or

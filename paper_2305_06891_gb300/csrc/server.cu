@@ -233,6 +233,7 @@ using namespace rad;
 extern "C" {
 
 int rad_server_create(const rad_server_params* p, rad_server** out) {
+    NvtxRange nv_(__func__);
     try {
         RAD_REQUIRE(p != nullptr && out != nullptr, RAD_EINVAL, "null argument");
         *out = nullptr;
@@ -266,6 +267,7 @@ int rad_server_create(const rad_server_params* p, rad_server** out) {
 }
 
 int rad_server_add_cavity(rad_server* s, int64_t n, const double* verts, int64_t* cavity_id) {
+    NvtxRange nv_(__func__);
     try {
         RAD_REQUIRE(s && verts && cavity_id, RAD_EINVAL, "null argument");
         RAD_REQUIRE(n >= 1 && n < (int64_t)1 << 28, RAD_EINVAL, "n must be in [1, 2^28)");
@@ -292,6 +294,7 @@ int rad_server_add_cavity(rad_server* s, int64_t n, const double* verts, int64_t
 
 int rad_server_submit(rad_server* s, int64_t cavity_id, const double* eps, const double* T, int64_t ldT, int64_t m,
                       double sigma, double* q, int64_t ldq, int64_t* ticket) {
+    NvtxRange nv_(__func__);
     try {
         RAD_REQUIRE(s && eps && T && q && ticket, RAD_EINVAL, "null argument");
         std::lock_guard<std::mutex> lk(s->mu);
@@ -324,6 +327,7 @@ int rad_server_submit(rad_server* s, int64_t cavity_id, const double* eps, const
 }
 
 int rad_server_wait(rad_server* s, int64_t ticket, rad_request_info* info) {
+    NvtxRange nv_(__func__);
     if (!s) {
         set_last_error("null argument");
         return RAD_EINVAL;
@@ -376,6 +380,7 @@ int rad_server_get_stats(rad_server* s, rad_server_stats* st) {
 }
 
 int rad_server_destroy(rad_server* s) {
+    NvtxRange nv_(__func__);
     if (!s) return RAD_OK;
     {
         std::lock_guard<std::mutex> lk(s->mu);

@@ -92,3 +92,12 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(cname, "size")] == C.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_checkpoint_blobs_are_validated_before_any_device_work(lib):
+    import paper_2305_06891_gb300 as rad
+    for blob in (b"", b"NOTRADHT" + bytes(64), b"RADHTREE" + (7).to_bytes(4, "little") + bytes(64),
+                 b"RADHTREE" + (1).to_bytes(4, "little") + (10 ** 9).to_bytes(8, "little")):
+        with pytest.raises(rad.RadError) as e:
+            rad.rad_htree_load(blob)
+        assert e.value.code == rad.RAD_EINVAL
