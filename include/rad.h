@@ -288,11 +288,15 @@ int rad_htree_autotune(rad_htree* h, void* stream);
 
 /* Kernel family of the product with 5 or more FP32 columns (no counterpart
  * in the paper): 0 = CUDA-core register tiles (FP32 FFMA, the default),
- * 1 = tensor cores (tcgen05, TF32 operands split into hi + lo with all four
- * partial products, accumulated per 32-column chunk and summed in FP32, so
- * results agree with path 0 to FP32 rounding).  rad_htree_autotune picks
- * the faster one for the handle's operator; recompression resets it to 0.
- * RAD_EINVAL for another value. */
+ * 1 = tensor cores (tcgen05 kind::f16: every FP32 operand split into three
+ * BF16 pieces carrying its 24 bits, six partial products per k-step, the
+ * leading and the correction terms in two accumulators restarted every 32
+ * panel columns and summed in FP32 registers, so results agree with path 0
+ * to FP32 rounding).  Selecting path 1 builds the split panel images once
+ * (1.5 times the FP32 operator's bytes; synchronous); path 0 releases them.
+ * rad_htree_autotune picks the faster path for the handle's operator;
+ * recompression resets it to 0.  RAD_EINVAL for another value, or for path 1
+ * on an FP64 operator. */
 int rad_htree_set_product_path(rad_htree* h, int32_t path);
 
 /* Closed-cavity treatment of the view factors (§6, Eqs. rowsum,
@@ -340,7 +344,10 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
  *     + round256(s * (max(sum_rank, 1) * p + (nrhs == 1 ? n : 0))) bytes,
  *     s = 8 for an FP64 operator and 4 otherwise, p = 1 for one column and
  *     nrhs rounded up to a multiple of 4 otherwise (sum_rank from
- *     rad_htree_get_stats); larger calls return RAD_ELIMIT;
+ *     rad_htree_get_stats), plus round256(6 (n + max(sum_rank, 1)) q) + 512
+ *     bytes for 5 or more columns on the tensor-core product path
+ *     (q = min(96, nrhs rounded up to a multiple of 8)); larger calls return
+ *     RAD_ELIMIT;
  *   - the first call on each device looks up the array's device address
  *     (make that first call before any stream capture);
  *   - all calls on a device share the array: calls that overlap on the GPU

@@ -1625,6 +1625,7 @@ void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     h->grid_a1 = h->grid_b1 = h->grid_a2 = h->grid_b2 = 0;
     h->tuned = 0;
     h->mm_path = 0;
+    tc_drop_images(h);
     h->closed = 0;
     h->compressed = false;
     h->factor_dtype = p->factor_dtype;

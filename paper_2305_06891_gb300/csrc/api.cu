@@ -765,6 +765,7 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
             RAD_CUDA(cudaMemcpy2DAsync(q, 8 * ldq, qd, 8 * (size_t)n, 8 * (size_t)n, m, cudaMemcpyDeviceToHost, s));
             RAD_CUDA(cudaStreamSynchronize(s));
         }
+        RAD_REQUIRE(!tc_take_timeout(), RAD_ECUDA, "a tensor-core wait timed out (results are incomplete)");
         if (info) *info = local;
         solve_status = local.status;
         if (solve_status != RAD_OK) set_last_error("GMRES did not reach the tolerance");
@@ -804,6 +805,7 @@ int rad_solve_reflection(const rad_htree* h, const double* eps, const double* B,
             RAD_CUDA(cudaMemcpy2DAsync(Y, 8 * ldY, Yd, 8 * (size_t)n, 8 * (size_t)n, nrhs, cudaMemcpyDeviceToHost, s));
             RAD_CUDA(cudaStreamSynchronize(s));
         }
+        RAD_REQUIRE(!tc_take_timeout(), RAD_ECUDA, "a tensor-core wait timed out (results are incomplete)");
         if (info) *info = local;
         solve_status = local.status;
         if (solve_status != RAD_OK) set_last_error("GMRES did not reach the tolerance");
@@ -926,7 +928,15 @@ int rad_htree_set_product_path(rad_htree* h, int32_t path) {
     return guarded(__func__, [&] {
         RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null argument");
         RAD_REQUIRE(path == 0 || path == 1, RAD_EINVAL, "path must be 0 (CUDA cores) or 1 (tensor cores)");
+        RAD_REQUIRE(path == 0 || tc_supported(h), RAD_EINVAL,
+                    "the tensor-core path needs a compressed FP32 or BF16 operator");
+        AllocScope as(h->alloc);
         drop_product_graph(h);
+        if (path == 1) {
+            tc_build_images(h, nullptr);
+        } else {
+            tc_drop_images(h);
+        }
         h->mm_path = path;
     });
 }

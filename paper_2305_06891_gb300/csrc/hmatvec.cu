@@ -782,10 +782,11 @@ void apply_t(const rad_htree* h, const OpView& op, const AT* X, int ldx, void* Y
         AT* Tc = T + c0;
         void* Yc = static_cast<char*>(Y) + (size_t)c0 * esz;
         if constexpr (std::is_same<AT, float>::value && std::is_same<NS, float>::value) {
-            if (vx && h->mm_path == 1) {
-                // tensor cores (split TF32) for FP32 vectors
-                if (op.n_gwork > 0) tc_far_vt<FS>(op, Xc, ldx, Tc, ldt, nc, s);
-                tc_rows<FS>(op, Xc, ldx, Tc, ldt, Yc, ldy, nc, e2, s);
+            if (h->mm_path == 1 && h->tc_ready) {
+                // tensor cores (BF16 x 3 split) for FP32 vectors; their
+                // workspace follows the FP32 T block
+                void* tws = reinterpret_cast<char*>(T) + sizeof(AT) * (size_t)std::max(1, op.sum_rank) * ldt;
+                tc_product(h, op, Xc, ldx, Yc, ldy, nc, e2, tws, s);
                 continue;
             }
         }
@@ -821,8 +822,10 @@ __global__ void scatter_kernel(int n, int nrhs, const TI* __restrict__ Y, int ld
 
 size_t apply_workspace_bytes(const rad_htree* h, int nrhs) {
     const size_t esz = h->op_is_f64() ? 8 : 4;
-    // T = V^T X, plus the dense-panel partial sums of a one-column product
-    return esz * ((size_t)std::max(1, h->sum_rank) * (size_t)tree_ld(nrhs) + (nrhs == 1 ? (size_t)h->n : 0));
+    // T = V^T X, plus the dense-panel partial sums of a one-column product,
+    // plus the split vector planes of the tensor-core path
+    const size_t tc = nrhs >= 5 && h->mm_path == 1 && !h->op_is_f64() ? tc_workspace_bytes(h, nrhs) : 0;
+    return esz * ((size_t)std::max(1, h->sum_rank) * (size_t)tree_ld(nrhs) + (nrhs == 1 ? (size_t)h->n : 0)) + tc;
 }
 
 void apply_tree(const rad_htree* h, const void* X, int ldx, void* Y, int ldy, int nrhs, const Epi& epi,
@@ -1063,6 +1066,7 @@ struct Tuner {
         if constexpr (std::is_same<AT, float>::value && std::is_same<NS, float>::value) {
             float best = 1e30f;
             int pick = 0;
+            tc_build_images(h, s);
             for (int path = 0; path < 2; ++path) {
                 h->mm_path = path;
                 const float t = time([&] {
@@ -1075,6 +1079,7 @@ struct Tuner {
                 }
             }
             h->mm_path = pick;
+            if (pick == 0) tc_drop_images(h);
         }
         h->tuned = 1;
     }
@@ -1093,7 +1098,8 @@ void autotune(rad_htree* h, cudaStream_t s) {
     RAD_CUDA(cudaEventCreate(&e1));
     void* X = ws.get(esz * 2 * (size_t)n);
     void* Y = ws.get(8 * 64 * (size_t)n);
-    const size_t tb = std::max(apply_workspace_bytes(h, 4) + esz * (size_t)n, apply_workspace_bytes(h, 64));
+    const size_t tb = std::max(apply_workspace_bytes(h, 4) + esz * (size_t)n, apply_workspace_bytes(h, 64)) +
+                      (h->op_is_f64() ? 0 : tc_workspace_bytes(h, 64));
     void* T = ws.get(tb);
     void* X64 = ws.get(esz * 64 * (size_t)n);
     RAD_CUDA(cudaMemsetAsync(X, 0, esz * 2 * (size_t)n, s));

@@ -400,9 +400,13 @@ struct rad_htree {
     int grid_a1 = 0, grid_b1 = 0, grid_a2 = 0, grid_b2 = 0;
     int tuned = 0;
     // many-column product of FP32 vectors: 0 = CUDA-core register tiles,
-    // 1 = tensor cores (split TF32); set by rad_htree_autotune or
+    // 1 = tensor cores (BF16 x 3 split); set by rad_htree_autotune or
     // rad_htree_set_product_path
     int mm_path = 0;
+    // tensor-core path: the three BF16 chunk images of every panel and the
+    // first chunk of every tile's dense / U panel and of every far item
+    rad::DevBuf tc_img, tc_tile_near0, tc_tile_far0, tc_item0;
+    bool tc_ready = false;
     int closed = 0;   // rows normalised for a closed cavity (rad_htree_close_cavity)
     int64_t n = 0;
     rad::Allocator alloc;   // device memory of the handle and of calls on it
@@ -509,12 +513,13 @@ void apply_tree_acc(const rad_htree* h, const double* X, int ldx, double* Y, int
                     double* T_ws, cudaStream_t s);
 size_t apply_workspace_bytes_acc(const rad_htree* h, int nrhs);
 size_t apply_workspace_bytes(const rad_htree* h, int nrhs);
-// tcgemm.cu: tensor-core panel GEMMs (FP32 vectors, 16-byte aligned rows)
-template <class FS>
-void tc_rows(const OpView& op, const float* X, int ldx, const float* T, int ldt, void* Y, int ldy, int nc,
-             const Epi& epi, cudaStream_t s);
-template <class FS>
-void tc_far_vt(const OpView& op, const float* X, int ldx, float* T, int ldt, int nc, cudaStream_t s);
+// tcgemm.cu: tensor-core panel GEMMs (BF16 x 3 split, FP32 vectors)
+bool tc_supported(const rad_htree* h);
+void tc_build_images(rad_htree* h, cudaStream_t s);
+void tc_drop_images(rad_htree* h);
+size_t tc_workspace_bytes(const rad_htree* h, int nrhs);
+void tc_product(const rad_htree* h, const OpView& op, const float* X, int ldx, void* Y, int ldy, int nc,
+                const Epi& epi, void* ws, cudaStream_t s);
 bool tc_take_timeout();
 void build_stream_lists(rad_htree* h, int rows, cudaStream_t s);
 void autotune(rad_htree* h, cudaStream_t s);

@@ -2,29 +2,41 @@
 // operands at FP32-level accuracy.
 //
 // A panel times gathered vector rows, D[64 x N] += A[64 x K] B[K x N], runs
-// on the 5th-generation tensor cores with the accumulator in tensor memory.
-// TF32 alone keeps 10 mantissa bits, far from the 1e-6 this product must
-// meet, so every operand is split into hi = tf32(x) (rounded to nearest) and
-// lo = tf32(x - hi) and the product takes all four terms hi*hi + hi*lo +
-// lo*hi + lo*lo: the inputs lose about 2^-23 relative and the accumulation
-// is FP32, as for an FP32 FFMA loop.
+// on the 5th-generation tensor cores (kind::f16 with BF16 operands, FP32
+// accumulators in tensor memory).  BF16 keeps 8 mantissa bits, so every
+// FP32 operand x is split into three BF16 pieces, x1 = bf16(x),
+// x2 = bf16(x - x1), x3 = bf16(x - x1 - x2), which together carry its 24
+// bits; the product takes the six terms a1 b1 (the "main" accumulator) and
+// a1 b2 + a2 b1 + a1 b3 + a2 b2 + a3 b1 (a second, "correction" accumulator),
+// dropping terms of order 2^-24 relative.  The tensor core's accumulation
+// truncates, so the accumulators start from zero every 128 panel columns
+// and are added into FP32 registers (round to nearest): the rounding stays
+// at the level of an FP32 FFMA loop (measured below it).
 //
-// Per CTA (256 threads, one work item): chunks of KC = 32 panel columns and
-// their 32 gathered rows are loaded from global memory into registers
-// (16-byte vectors), split, and stored into shared memory as K-major
-// 8 x 16-byte core matrices (no swizzle; the stride between 8-row groups is
-// padded by 16 bytes to spread shared-memory banks).  Two stages: while one
-// thread issues the 16 MMAs of chunk c (4 k-steps of 8 x 4 terms) and
-// commits them to the stage's mbarrier, the threads load chunk c + 1.  A
-// stage is rewritten only after its previous MMAs completed.  The M = 64
-// accumulator lives in tensor-memory lanes 0-15 of each 32-lane quarter
-// (rows 16 q .. 16 q + 15 in quarter q); warps w and w + 4 read quarter w for
-// the two halves of the columns.
-//
-// Every wait is bounded: after kWaitLimit polls a CTA records the timeout in
-// a device flag (checked by the host at its next synchronisation), skips the
-// rest of its work, waits (bounded) for its own MMAs and frees its tensor
-// memory.
+// The split is never done inside the kernel:
+//   - panels (dense blocks, U and V^T factors) are split once, when the path
+//     is selected, into three 64 x 32 BF16 images per chunk of 32 panel
+//     columns, laid out as the MMA reads them (K-major core matrices of
+//     8 rows x 16 bytes, no swizzle: 8-row groups 512 bytes apart, K-adjacent
+//     cores 128 bytes apart), zero-padded past the panel's rows and columns;
+//   - vector rows (X, and T = V^T X) are split once per product into three
+//     BF16 planes of N8 = 8 ceil(nc / 8) columns; a gathered row lands in
+//     shared memory by 16-byte copies as MN-major core matrices (8 columns x
+//     8 rows of 16 bytes; 8-column groups 512 bytes apart, K-adjacent cores
+//     128 bytes apart), which the MMA reads with the B-transpose bit set.
+// Persistent, warp-specialised kernel (one CTA of 256 threads per SM,
+// items taken round-robin, heaviest first): warps 0-2 copy chunks (12 KiB of
+// panel images by one bulk copy, 3 x N8 x 32 x 2 bytes of gathered vector
+// rows by 16-byte copies) into a ring of six shared-memory stages; one thread of warp 3 issues every chunk's 2
+// k-steps x 6 MMAs (M = 64, K = 16) into one of two accumulator pairs in
+// tensor memory; warps 4-7 (whose tensor-memory lane quarters hold rows
+// 16 q .. 16 q + 15 in lanes 0-15) add a pair into FP32 registers after
+// every 4 chunks of an item and write the item's rows at its end.  The roles
+// hand over through mbarriers (stage full / empty, accumulators full /
+// empty) and never wait for the whole CTA.  Every wait is bounded: after
+// a bounded number of tries a role raises an abort flag that the others see, the CTA
+// records the timeout in a device flag (checked by the host at its next
+// synchronisation) and frees its tensor memory.
 
 #include <cstdint>
 #include <mutex>
@@ -37,313 +49,218 @@ __device__ int g_tc_timeout = 0;
 
 namespace {
 
-constexpr int kKC = 32;                  // panel columns per chunk
-constexpr int kCoreBytes = 128;          // 8 rows x 16 bytes
-constexpr int kGroupStride = (kKC / 4) * kCoreBytes + 16;   // 8-row group stride (SBO)
-constexpr int kTmemCols = 256;           // main accumulator at 0, corrections at 128
-constexpr uint32_t kCorrCol = 128;
-constexpr long kWaitLimit = 1l << 26;     // polls (well beyond any real MMA latency)
+constexpr int kKC = 32;                          // panel columns per chunk
+constexpr int kImg = kTileRows * kKC * 2;        // one BF16 image of a chunk: 4 KiB
+constexpr int kChunkBytes = 3 * kImg;            // the three split images
+constexpr int kGrp = (kKC / 8) * 128;            // 512: 8-row / 8-column group stride
+constexpr uint32_t kCorrCol = 128;               // correction accumulator: 128 columns after the main one
+constexpr int kMaxN8 = 96;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: K-major, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+// shared-memory matrix descriptor, no swizzle: lbo = stride of K-adjacent
+// core matrices, sbo = stride of the 8-row (K-major) or 8-column (MN-major)
+// groups
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)((kCoreBytes >> 4) & 0x3FFF) << 16;        // K-adjacent cores
-    d |= (uint64_t)((kGroupStride >> 4) & 0x3FFF) << 32;      // 8-row groups
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;                                   // tcgen05 descriptor version
     return d;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
         "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 
-// non-blocking poll of an mbarrier phase (test_wait returns at once; the
-// blocking try_wait may suspend the thread for a time slice)
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred P;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, P;\n\t}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long it = 0; it < kWaitLimit; ++it)
-        if (mbar_try(bar, parity)) return true;
-    return false;
+// x = x1 + x2 + x3 in BF16 pieces (round to nearest; each difference is
+// exact in FP32)
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+    a = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(a);
+    b = __float2bfloat16_rn(r1);
+    c = __float2bfloat16_rn(r1 - __bfloat162float(b));
 }
 
-// split x into two TF32 values (round to nearest, ties away from zero):
-// hi = tf32(x), lo = tf32(x - hi)
-__device__ __forceinline__ float tf32_rn(float x) {
-    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
-}
-
-// A chunk element source: panel column k (FP32 or BF16 storage)
-__device__ __forceinline__ float4 load_quad(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ float4 load_quad(const __nv_bfloat16* p) {
-    const uint2 q = *reinterpret_cast<const uint2*>(p);
-    return make_float4(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xffff0000u), __uint_as_float(q.y << 16),
-                       __uint_as_float(q.y & 0xffff0000u));
-}
-
-// One K segment: panel A (column-major, leading dimension lda, rows_pad
-// rows used) times rows of B selected by idx (or base + k when idx is null).
-template <class AS>
-struct Seg {
-    const AS* A;
-    long long lda;
-    int rows_pad;
-    int K;
-    const float* B;
-    int ldb;
-    const int* idx;
-    int base;
+// ---------------------------------------------------------------- packing
+// One chunk of a panel: rows [0, rows) and columns [k0, k0 + 32) of the
+// column-major panel at pool + src (leading dimension ld, K columns in all).
+struct PackJob {
+    long long src;
+    int ld, rows, k0, K;
+    long long chunk;
 };
-
-// store element (r, k) of a K-major operand split into hi / lo
-__device__ __forceinline__ void put_split(unsigned char* hi, unsigned char* lo, int r, int k, float x) {
-    const int off = (r >> 3) * kGroupStride + (k >> 2) * kCoreBytes + (r & 7) * 16 + (k & 3) * 4;
-    const float h = tf32_rn(x);
-    *reinterpret_cast<float*>(hi + off) = h;
-    *reinterpret_cast<float*>(lo + off) = tf32_rn(x - h);
+template <class FS>
+__global__ void __launch_bounds__(256) tc_pack_kernel(const FS* __restrict__ pool, const PackJob* __restrict__ jobs,
+                                                      unsigned char* __restrict__ img) {
+    const PackJob j = jobs[blockIdx.x];
+    unsigned char* dst = img + j.chunk * kChunkBytes;
+    for (int e = threadIdx.x; e < kTileRows * kKC; e += blockDim.x) {
+        const int m = e % kTileRows, k = e / kTileRows;
+        float x = 0.0f;
+        if (m < j.rows && j.k0 + k < j.K) x = (float)Store<FS>::get(pool[j.src + m + (long long)(j.k0 + k) * j.ld]);
+        __nv_bfloat16 a, b, c;
+        split3(x, a, b, c);
+        const int off = (m >> 3) * kGrp + (k >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16*>(dst + off) = a;
+        *reinterpret_cast<__nv_bfloat16*>(dst + kImg + off) = b;
+        *reinterpret_cast<__nv_bfloat16*>(dst + 2 * kImg + off) = c;
+    }
 }
 
-// Raw chunk staging: the KC panel columns (64 rows each, storage type AS)
-// and the KC gathered vector rows (N8 floats each) land in shared memory by
-// cp.async, kRawStages chunks ahead of the split pass.
-constexpr int kRawStages = 3;
-// bytes of one raw stage (FP32 panel columns are the larger case)
-__host__ __device__ constexpr int raw_stage_bytes(int N8) { return kKC * kTileRows * 4 + kKC * N8 * 4; }
-template <class AS>
-__device__ __forceinline__ int raw_a_bytes() { return kKC * kTileRows * (int)sizeof(AS); }
+// vector rows -> three BF16 planes of N8 columns (zero past nc)
+__global__ void tc_split_rows_kernel(const float* __restrict__ X, int ldx, int rows, int nc, int N8,
+                                     __nv_bfloat16* __restrict__ P, long long plane) {
+    const long long total = (long long)rows * N8;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / N8;
+        const int c = (int)(e - i * N8);
+        const float x = c < nc ? X[i * ldx + c] : 0.0f;
+        __nv_bfloat16 a, b, d;
+        split3(x, a, b, d);
+        P[e] = a;
+        P[plane + e] = b;
+        P[2 * plane + e] = d;
+    }
+}
 
+// ---------------------------------------------------------------- GEMM
 __device__ __forceinline__ void cp16(void* sdst, const void* gsrc, bool pred) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(sdst)), "l"(gsrc),
                  "r"(pred ? 16 : 0));
 }
-__device__ __forceinline__ void cp8(void* sdst, const void* gsrc, bool pred) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(sdst)), "l"(gsrc),
-                 "r"(pred ? 8 : 0));
-}
 
-// issue the copies of chunk k0 .. k0 + KC of one segment into raw stage st
-// (entries past K or past the vector's columns are zero-filled)
-template <class AS>
-__device__ __forceinline__ void issue_chunk(const Seg<AS>& sg, int k0, int nq_load, int N8, unsigned char* st) {
-    AS* ra = reinterpret_cast<AS*>(st);
-    float* rb = reinterpret_cast<float*>(st + raw_a_bytes<AS>());
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int u = tid + 256 * i;            // u < 512 = 32 columns x 16 row quads
-        const int k = u >> 4, mq = u & 15;
-        const bool ok = k0 + k < sg.K && 4 * mq < sg.rows_pad;
-        const AS* src = ok ? sg.A + (long long)(k0 + k) * sg.lda + 4 * mq : sg.A;
-        if constexpr (sizeof(AS) == 4) cp16(ra + k * kTileRows + 4 * mq, src, ok);
-        else cp8(ra + k * kTileRows + 4 * mq, src, ok);
-    }
-    const int nq = N8 / 4;
-    for (int u = tid; u < kKC * nq; u += 256) {
-        const int k = u / nq, q = u - k * nq;
-        const bool ok = k0 + k < sg.K && q < nq_load;
-        const float* src = sg.B;
-        if (ok) src = sg.B + (long long)(sg.idx ? sg.idx[k0 + k] : sg.base + k0 + k) * sg.ldb + 4 * q;
-        cp16(rb + k * N8 + 4 * q, src, ok);
-    }
-}
+// One K segment of a work item: nch chunk images from img, and the vector
+// rows idx[k] (or base + k) of three BF16 planes (plane elements apart, N8
+// columns) for k < K.
+struct Seg {
+    const unsigned char* img;
+    int nch, K;
+    const __nv_bfloat16* B;
+    long long plane;
+    const int* idx;
+    int base;
+};
 
-__device__ __forceinline__ float4 raw_quad(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ float4 raw_quad(const __nv_bfloat16* p) { return load_quad(p); }
+__host__ __device__ constexpr int b_plane_bytes(int N8) { return (N8 / 8) * kGrp; }
+__host__ __device__ constexpr int stage_bytes(int N8) { return kChunkBytes + 3 * b_plane_bytes(N8); }
 
-// split pass: raw stage -> K-major hi / lo core matrices
-template <class AS>
-__device__ __forceinline__ void split_chunk(const unsigned char* raw, unsigned char* st, int a_bytes, int b_bytes,
-                                            int N8) {
-    const AS* ra = reinterpret_cast<const AS*>(raw);
-    const float* rb = reinterpret_cast<const float*>(raw + raw_a_bytes<AS>());
-    unsigned char* Ahi = st;
-    unsigned char* Alo = st + a_bytes;
-    unsigned char* Bhi = st + 2 * a_bytes;
-    unsigned char* Blo = st + 2 * a_bytes + b_bytes;
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int u = tid + 256 * i;
-        const int k = u >> 4, m = 4 * (u & 15);
-        const float4 v = raw_quad(ra + k * kTileRows + m);
-        put_split(Ahi, Alo, m, k, v.x);
-        put_split(Ahi, Alo, m + 1, k, v.y);
-        put_split(Ahi, Alo, m + 2, k, v.z);
-        put_split(Ahi, Alo, m + 3, k, v.w);
-    }
-    const int nq = N8 / 4;
-    for (int u = tid; u < kKC * nq; u += 256) {
-        const int k = u / nq, q = u - k * nq;
-        const float4 v = *reinterpret_cast<const float4*>(rb + k * N8 + 4 * q);
-        const int n = 4 * q;
-        put_split(Bhi, Blo, n, k, v.x);
-        put_split(Bhi, Blo, n + 1, k, v.y);
-        put_split(Bhi, Blo, n + 2, k, v.z);
-        put_split(Bhi, Blo, n + 3, k, v.w);
-    }
-}
+constexpr int kProducers = 96;     // warps 0-2 copy chunks into the stage ring
+constexpr int kMmaWarp = 3;        // lane 0 issues the MMAs
+constexpr int kDrainers = 128;     // warps 4-7 read the accumulators (lane quarters 0-3)
+constexpr int kDrain = 4;          // chunks accumulated in tensor memory between drains
+constexpr int kRingStages = 6;     // chunks in flight
+constexpr int kMaxBlkAll = kMaxN8 / 8;
 
-// tcgen05.ld of 8 accumulator columns of this thread's lane
-__device__ __forceinline__ void tmem_ld8(uint32_t addr, float v[8]) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(addr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-constexpr int kMaxBlk = 6;   // 8-column blocks per warp half (N <= 96)
-
-// Adds one chunk's accumulators (main hi*hi at column 0, corrections at
-// column kCorrCol) to this thread's FP32 registers: rows 16 (w % 4) + lane
-// of the accumulator (lanes 0-15), 8-column blocks [b0, b1) of its half.
-__device__ __forceinline__ void drain_add(uint32_t tmem, int b0, int b1, float (&racc)[kMaxBlk][8]) {
-    const int warp = threadIdx.x >> 5;
-    const uint32_t lane_addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-#pragma unroll
-    for (int i = 0; i < kMaxBlk; ++i) {
-        const int b = b0 + i;
-        if (b < b1) {
-            float v[8], w[8];
-            tmem_ld8(lane_addr + 8 * b, v);
-            tmem_ld8(lane_addr + kCorrCol + 8 * b, w);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) racc[i][j] += v[j] + w[j];
-        }
+// chunk c of a segment into a stage, by producer thread pt (0 .. 95): the
+// three panel images (12 KiB, contiguous) by one bulk copy that completes
+// on the stage's "full" mbarrier, the gathered vector rows by 16-byte
+// copies
+__device__ __forceinline__ void issue_chunk(const Seg& sg, int c, int N8, unsigned char* st, int pt, uint32_t full) {
+    if (pt == 0) {
+        const unsigned char* a = sg.img + (size_t)c * kChunkBytes;
+        asm volatile("{\n\t.reg .b64 tk;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 tk, [%0], %1;\n\t}\n" ::"r"(full),
+                     "r"(kChunkBytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                smem_u32(st)),
+            "l"(a), "r"(kChunkBytes), "r"(full)
+            : "memory");
     }
-}
-
-// racc = sum over the segments of A_s B_s for one 64-row item (rows and
-// blocks as in drain_add); returns false if a wait timed out.
-//
-// The tensor cores accumulate a chunk (32 k) at a time, starting from zero:
-// hi*hi into the main accumulator, the three correction terms into a
-// second one; each chunk is then added into FP32 registers.  Summing long
-// panels inside the tensor core would carry its accumulation rounding over
-// all K; per chunk it stays at FP32 level.
-template <class AS0, class AS1>
-__device__ bool tc_item(const Seg<AS0>& s0, const Seg<AS1>& s1, int nseg, int N8, int nc_load, unsigned char* smem,
-                        uint32_t tmem, uint32_t bar0, uint32_t bar1, int b0, int b1, float (&racc)[kMaxBlk][8]) {
-    (void)bar1;
-    const int a_bytes = 8 * kGroupStride;             // 64 rows
-    const int b_bytes = (N8 / 8) * kGroupStride;
-    const int raw_bytes = raw_stage_bytes(N8);
-    unsigned char* hilo = smem + kRawStages * raw_bytes;
-    const int nq_load = (nc_load + 3) / 4;            // quads read from memory
-    const int c0n = (s0.K + kKC - 1) / kKC;
-    const int c1n = nseg > 1 ? (s1.K + kKC - 1) / kKC : 0;
-    const int nch = c0n + c1n;
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N8 >> 3) << 17) | (4u << 24);
-#pragma unroll
-    for (int i = 0; i < kMaxBlk; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) racc[i][j] = 0.0f;
-    if (nch == 0) return true;
-    auto issue = [&](int c) {
-        if (c < nch) {
-            unsigned char* st = smem + (c % kRawStages) * raw_bytes;
-            if (c < c0n) issue_chunk<AS0>(s0, c * kKC, nq_load, N8, st);
-            else issue_chunk<AS1>(s1, (c - c0n) * kKC, nq_load, N8, st);
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    };
-    for (int c = 0; c < kRawStages; ++c) issue(c);
-    bool ok = true;
-    for (int c = 0; c < nch; ++c) {
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(kRawStages - 1) : "memory");   // chunk c landed
-        if (c >= 1) {
-            // MMAs of chunk c-1 done: accumulators readable, hi/lo free
-            ok = ok && mbar_wait(bar0, (c - 1) & 1);
-            ok = __syncthreads_and(ok);
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            drain_add(tmem, b0, b1, racc);
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        } else {
-            __syncthreads();
-        }
-        const unsigned char* raw = smem + (c % kRawStages) * raw_bytes;
-        if (c < c0n) split_chunk<AS0>(raw, hilo, a_bytes, b_bytes, N8);
-        else split_chunk<AS1>(raw, hilo, a_bytes, b_bytes, N8);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        issue(c + kRawStages);                         // refill the raw stage just split
-        if (threadIdx.x == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ahi = smem_u32(hilo), alo = ahi + a_bytes, bhi = ahi + 2 * a_bytes, blo = bhi + b_bytes;
-#pragma unroll
-            for (int k8 = 0; k8 < kKC / 8; ++k8) {
-                const uint32_t ko = k8 * 2 * kCoreBytes;
-                const uint32_t acc = k8 > 0 ? 1u : 0u;
-                mma_tf32(tmem, smem_desc(ahi + ko), smem_desc(bhi + ko), idesc, acc);
-                mma_tf32(tmem + kCorrCol, smem_desc(alo + ko), smem_desc(blo + ko), idesc, acc);
-                mma_tf32(tmem + kCorrCol, smem_desc(ahi + ko), smem_desc(blo + ko), idesc, 1u);
-                mma_tf32(tmem + kCorrCol, smem_desc(alo + ko), smem_desc(bhi + ko), idesc, 1u);
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar0)
-                         : "memory");
-        }
+    // warp w copies plane w: the chunk's 32 row indices are read once per
+    // warp (one coalesced load, lane k holding row k) and handed out by
+    // shuffles, so the copies do not wait on dependent index loads
+    unsigned char* b = st + kChunkBytes + (pt >> 5) * b_plane_bytes(N8);
+    const int lane = pt & 31, q = pt >> 5;
+    const int nj = N8 / 8;
+    const int k0 = c * kKC;
+    const bool okl = k0 + lane < sg.K;
+    const int myrow = okl ? (sg.idx ? sg.idx[k0 + lane] : sg.base + k0 + lane) : 0;
+    const __nv_bfloat16* plane = sg.B + q * sg.plane;
+    for (int it = 0; it < nj; ++it) {
+        const int r = it * 32 + lane;               // copy r of this plane: row k, 16-byte piece j
+        const int k = r / nj, j = r - k * nj;
+        const int row = __shfl_sync(0xffffffffu, myrow, k);
+        const bool ok = k0 + k < sg.K;
+        const __nv_bfloat16* src = ok ? plane + (long long)row * N8 + 8 * j : sg.B;
+        cp16(b + j * kGrp + (k >> 3) * 128 + (k & 7) * 16, src, ok);
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    if (ok) {
-        ok = mbar_wait(bar0, (nch - 1) & 1);
-        ok = __syncthreads_and(ok);
-        if (ok) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            drain_add(tmem, b0, b1, racc);
-        }
-    } else {
-        __syncthreads();
-    }
-    return ok;
 }
 
 struct TcShared {
-    unsigned long long bar[2];
+    unsigned long long full[kRingStages], empty[kRingStages], accf[2], acce[2];
     uint32_t tmem;
+    int abort;
 };
 
-__device__ __forceinline__ void tc_setup(TcShared& sh) {
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sh.bar[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sh.bar[1])), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+__device__ __forceinline__ uint32_t bar_addr(unsigned long long* b) { return smem_u32(b); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_addr(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(bar_addr(b)) : "memory");
+}
+// blocking test of an mbarrier phase: the thread may be suspended in hardware
+// for up to about 1 microsecond (the hint, in nanoseconds) instead of
+// spinning, which keeps shared memory free for the copies being waited for
+constexpr long kTryLimit = 1l << 22;   // tries (each returns within about a microsecond)
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(1000u)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait that also gives up once another role has aborted
+__device__ __forceinline__ bool role_wait(unsigned long long* b, uint32_t parity, volatile int* abort) {
+    const uint32_t a = bar_addr(b);
+    for (long it = 0; it < kTryLimit; ++it) {
+        if (mbar_try_wait(a, parity)) return true;
+        if ((it & 63) == 63 && *abort) return false;
     }
-    if (threadIdx.x < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem)),
-                     "r"(kTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    atomicExch((int*)abort, 1);
+    return false;
 }
 
-__device__ __forceinline__ void tc_teardown(TcShared& sh) {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x < 32)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sh.tmem), "r"(kTmemCols));
-}
+// The work items of one launch: tiles (rows) or far-field items (far_vt).
+struct Items {
+    bool rows;
+    OpView op;
+    const long long* first;    // rows: tile_near0; far_vt: item0
+    const long long* first2;   // rows: tile_far0
+    const unsigned char* img;
+    const __nv_bfloat16 *Xs, *Ts;
+    long long xplane, tplane;
+    __device__ __forceinline__ int count() const { return rows ? op.n_tiles : op.n_gwork; }
+    // the two segments of item i (the second is empty for far-field items)
+    __device__ __forceinline__ void segs(int i, Seg& s0, Seg& s1) const {
+        if (rows) {
+            const int ti = op.torder[i];
+            const Tile t = op.tiles[ti];
+            s0 = Seg{img + first[ti] * (long long)kChunkBytes, (t.kn + kKC - 1) / kKC, t.kn, Xs, xplane,
+                     op.xidx + t.ixn, 0};
+            s1 = Seg{img + first2[ti] * (long long)kChunkBytes, (t.kf + kKC - 1) / kKC, t.kf, Ts, tplane,
+                     op.tidx + t.ixf, 0};
+        } else {
+            const GWork w = op.gwork[i];
+            const Group gr = op.groups[w.g];
+            s0 = Seg{img + first[i] * (long long)kChunkBytes, (gr.n + kKC - 1) / kKC, gr.n, Xs, xplane, nullptr,
+                     gr.c0};
+            s1 = Seg{nullptr, 0, 0, nullptr, 0, nullptr, 0};
+        }
+    }
+};
 
 __device__ __forceinline__ void epilogue_tc(const Epi& epi, void* Y, int ldy, int row, int col, float acc) {
     if (epi.mode == kStore) {
@@ -356,121 +273,376 @@ __device__ __forceinline__ void epilogue_tc(const Epi& epi, void* Y, int ldy, in
     }
 }
 
-// 8-column blocks [b0, b1) of the accumulator read by this thread's warp half
-__device__ __forceinline__ void drain_blocks(int N8, int& b0, int& b1) {
-    const int nblk = N8 / 8, half = threadIdx.x >> 7;
-    b0 = half ? (nblk + 1) / 2 : 0;
-    b1 = half ? nblk : (nblk + 1) / 2;
-}
-
-// Y rows of every tile = epilogue([dense | U] [X gathered ; T gathered]).
-template <class FS>
-__global__ void __launch_bounds__(256, 2)
-tc_rows_kernel(OpView op, const float* __restrict__ X, int ldx, const float* __restrict__ T, int ldt, void* Y, int ldy,
-               int nc, int N8, Epi epi) {
+// Persistent, warp-specialised panel GEMM: CTA b takes items b, b + grid,
+// ... (heaviest first).  Producers fill a ring of kRingStages chunk stages
+// (cp.async, arriving on the stage's "full" mbarrier when the copies land);
+// the MMA thread waits "full", issues the chunk's 12 MMAs into one of two
+// tensor-memory accumulator pairs and commits them to the stage's "empty"
+// mbarrier (the producers' licence to refill it); after every kDrain chunks
+// of an item (and at its end) it commits the pair to "acc full"; the
+// drainers add the pair to FP32 registers, release it ("acc empty") and,
+// at the end of an item, write its rows.
+__global__ void __launch_bounds__(256, 1) tc_gemm_kernel(Items it, int nc, int N8, void* Y, int ldy, Epi epi,
+                                                          __nv_bfloat16* Tout, long long tplane_out) {
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ TcShared sh;
-    tc_setup(sh);
-    const uint32_t tmem = sh.tmem;
-    const Tile t = op.tiles[op.torder[blockIdx.x]];
-    const Seg<float> s0{static_cast<const float*>(op.near_pool) + t.noff, t.ld, t.ld, t.kn, X, ldx,
-                        op.xidx + t.ixn, 0};
-    const Seg<FS> s1{static_cast<const FS*>(op.far_pool) + t.foff, t.ld, t.ld, t.kf, T, ldt, op.tidx + t.ixf, 0};
-    int b0, b1;
-    drain_blocks(N8, b0, b1);
-    float racc[kMaxBlk][8];
-    const bool ok = tc_item<float, FS>(s0, s1, 2, N8, nc, dsm, tmem, smem_u32(&sh.bar[0]), smem_u32(&sh.bar[1]), b0,
-                                       b1, racc);
-    const int lane = threadIdx.x & 31, row = 16 * ((threadIdx.x >> 5) & 3) + lane;
-    if (ok) {
-        if (lane < 16 && row < t.rows)
-#pragma unroll
-            for (int i = 0; i < kMaxBlk; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int col = 8 * (b0 + i) + j;
-                    if (b0 + i < b1 && col < nc) epilogue_tc(epi, Y, ldy, t.r0 + row, col, racc[i][j]);
-                }
-    } else if (threadIdx.x == 0) {
-        atomicExch(&g_tc_timeout, 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int sb = stage_bytes(N8);
+    if (tid == 0) {
+        for (int i = 0; i < kRingStages; ++i) {
+            mbar_init(&sh.full[i], kProducers + 1);   // 96 copy arrivals + the bulk copy's expect_tx
+            mbar_init(&sh.empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&sh.accf[i], 1);
+            mbar_init(&sh.acce[i], kDrainers);
+        }
+        sh.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    tc_teardown(sh);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = sh.tmem;
+    volatile int* abort = &sh.abort;
+    const int n_items = it.count();
+
+    if (warp < kProducers / 32) {
+        // ------------------------------------------------ producers
+        int g = 0;   // global chunk counter of this CTA
+        for (int i = blockIdx.x; i < n_items && !*abort; i += gridDim.x) {
+            Seg s0, s1;
+            it.segs(i, s0, s1);
+            const int nch = s0.nch + s1.nch;
+            for (int c = 0; c < nch; ++c, ++g) {
+                const int st = g % kRingStages, use = g / kRingStages;
+                if (use > 0) {
+                    // warp-uniform outcome: the copies below shuffle across the warp
+                    const bool w = __all_sync(0xffffffffu, role_wait(&sh.empty[st], (uint32_t)((use - 1) & 1), abort));
+                    if (!w) break;
+                }
+                unsigned char* stage = dsm + (size_t)st * sb;
+                const uint32_t fb = bar_addr(&sh.full[st]);
+                if (c < s0.nch) issue_chunk(s0, c, N8, stage, tid, fb);
+                else issue_chunk(s1, c - s0.nch, N8, stage, tid, fb);
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar_addr(&sh.full[st]))
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp == kMmaWarp) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc =
+                (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(N8 >> 3) << 17) | (4u << 24);
+            const uint32_t bp = b_plane_bytes(N8);
+            const uint64_t dbase = smem_desc(smem_u32(dsm), 128, kGrp);   // stage 0, plane 0, k-step 0
+            int g = 0, grp = 0;
+            bool ok = true;
+            for (int i = blockIdx.x; i < n_items && ok; i += gridDim.x) {
+                Seg s0, s1;
+                it.segs(i, s0, s1);
+                const int nch = s0.nch + s1.nch;
+                for (int c = 0; c < nch && ok; ++c, ++g) {
+                    const int buf = grp & 1;
+                    if (c % kDrain == 0 && grp >= 2) {
+                        ok = role_wait(&sh.acce[buf], (uint32_t)(((grp >> 1) - 1) & 1), abort);
+                        if (!ok) break;
+                    }
+                    const int st = g % kRingStages, use = g / kRingStages;
+                    ok = role_wait(&sh.full[st], (uint32_t)(use & 1), abort);
+                    if (!ok) break;
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    // descriptors differ only in the start address (bits
+                    // 0-13, 16-byte units; shared addresses stay below 256 KiB
+                    // so adding an offset never carries out of the field)
+                    const uint64_t da = dbase + (uint64_t)((st * sb) >> 4);
+                    const uint64_t db = da + (uint64_t)(kChunkBytes >> 4);
+                    const uint32_t dm = tmem + (uint32_t)(256 * buf), dc = dm + kCorrCol;
+#pragma unroll
+                    for (int ks = 0; ks < kKC / 16; ++ks) {
+                        const uint64_t ko = (uint64_t)(ks * 256 >> 4);
+                        const uint32_t acc = (c % kDrain == 0 && ks == 0) ? 0u : 1u;
+                        const uint64_t a1 = da + ko, a2 = a1 + (kImg >> 4), a3 = a2 + (kImg >> 4);
+                        const uint64_t b1 = db + ko, b2 = b1 + (bp >> 4), b3 = b2 + (bp >> 4);
+                        mma_bf16(dm, a1, b1, idesc, acc);
+                        mma_bf16(dc, a1, b2, idesc, acc);
+                        mma_bf16(dc, a2, b1, idesc, 1u);
+                        mma_bf16(dc, a1, b3, idesc, 1u);
+                        mma_bf16(dc, a2, b2, idesc, 1u);
+                        mma_bf16(dc, a3, b1, idesc, 1u);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     bar_addr(&sh.empty[st]))
+                                 : "memory");
+                    if (c % kDrain == kDrain - 1 || c == nch - 1) {
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                bar_addr(&sh.accf[buf]))
+                            : "memory");
+                        ++grp;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ drainers and epilogue
+        const int q = warp & 3;                       // lane quarter
+        const int row = 16 * q + lane;                 // accumulator row of this thread (lanes 0-15)
+        const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
+        const int nblk = N8 / 8;
+        int grp = 0;
+        bool ok = true;
+        for (int i = blockIdx.x; i < n_items && ok; i += gridDim.x) {
+            Seg s0, s1;
+            it.segs(i, s0, s1);
+            const int nch = s0.nch + s1.nch;
+            float racc[kMaxBlkAll][8];
+#pragma unroll
+            for (int b = 0; b < kMaxBlkAll; ++b)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) racc[b][j] = 0.0f;
+            const int ngr = (nch + kDrain - 1) / kDrain;
+            for (int gg = 0; gg < ngr; ++gg, ++grp) {
+                const int buf = grp & 1;
+                ok = role_wait(&sh.accf[buf], (uint32_t)((grp >> 1) & 1), abort);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int b0 = 0; b0 < kMaxBlkAll; b0 += 3) {
+                    uint32_t r[3][16];
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) {
+                        const int b = b0 + t;
+                        if (b < nblk) {
+                            const uint32_t ad = lane_addr + (uint32_t)(256 * buf) + 8 * b;
+                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                         : "=r"(r[t][0]), "=r"(r[t][1]), "=r"(r[t][2]), "=r"(r[t][3]),
+                                           "=r"(r[t][4]), "=r"(r[t][5]), "=r"(r[t][6]), "=r"(r[t][7])
+                                         : "r"(ad));
+                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                                         : "=r"(r[t][8]), "=r"(r[t][9]), "=r"(r[t][10]), "=r"(r[t][11]),
+                                           "=r"(r[t][12]), "=r"(r[t][13]), "=r"(r[t][14]), "=r"(r[t][15])
+                                         : "r"(ad + kCorrCol));
+                        }
+                    }
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int t = 0; t < 3; ++t)
+                        if (b0 + t < nblk)
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                racc[b0 + t][j] += __uint_as_float(r[t][j]) + __uint_as_float(r[t][8 + j]);
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(&sh.acce[buf]);
+            }
+            // one outcome for all four drainer warps (they meet at the
+            // epilogue's named barrier below); a warp that gave up arrives
+            // here too, the others within their own bounded waits
+            uint32_t all_ok;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+                "bar.red.and.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+                : "=r"(all_ok)
+                : "r"((uint32_t)ok)
+                : "memory");
+            ok = all_ok != 0;
+            if (!ok) break;
+            // epilogue of item i
+            if (it.rows) {
+                // through a shared-memory tile, so that rows are written
+                // (and xin / b read) coalesced; the four drainer warps meet
+                // at named barrier 1
+                const Tile t = it.op.tiles[it.op.torder[i]];
+                float* tile = reinterpret_cast<float*>(dsm + (size_t)kRingStages * sb);
+                const int ldt = N8 + 1;
+                if (lane < 16)
+#pragma unroll
+                    for (int b = 0; b < kMaxBlkAll; ++b)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (b < nblk) tile[row * ldt + 8 * b + j] = racc[b][j];
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                for (int e = tid - 128; e < t.rows * nc; e += kDrainers) {
+                    const int r = e / nc, col = e - r * nc;
+                    epilogue_tc(epi, Y, ldy, t.r0 + r, col, tile[r * ldt + col]);
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+            } else if (lane < 16) {
+                {
+                    const GWork w = it.op.gwork[i];
+                    const Group gr = it.op.groups[w.g];
+                    if (row < w.rows) {
+                        // 8 columns of each plane per 16-byte store (rows of
+                        // N8 BF16 are 16-byte aligned)
+                        const long long base = (long long)(gr.toff + w.r0 + row) * N8;
+#pragma unroll
+                        for (int b = 0; b < kMaxBlkAll; ++b) {
+                            if (b >= nblk) continue;
+                            __align__(16) __nv_bfloat16 p1[8], p2[8], p3[8];
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) split3(8 * b + j < nc ? racc[b][j] : 0.0f, p1[j], p2[j], p3[j]);
+                            *reinterpret_cast<uint4*>(Tout + base + 8 * b) = *reinterpret_cast<const uint4*>(p1);
+                            *reinterpret_cast<uint4*>(Tout + tplane_out + base + 8 * b) = *reinterpret_cast<const uint4*>(p2);
+                            *reinterpret_cast<uint4*>(Tout + 2 * tplane_out + base + 8 * b) =
+                                *reinterpret_cast<const uint4*>(p3);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (tid == 0 && *abort) atomicExch(&g_tc_timeout, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
-// T rows of every far-field item = V^T panel rows times X rows c0 .. c0 + n.
-template <class FS>
-__global__ void __launch_bounds__(256, 2)
-tc_far_vt_kernel(OpView op, const float* __restrict__ X, int ldx, float* __restrict__ T, int ldt, int nc, int N8) {
-    extern __shared__ __align__(1024) unsigned char dsm[];
-    __shared__ TcShared sh;
-    tc_setup(sh);
-    const uint32_t tmem = sh.tmem;
-    const GWork w = op.gwork[blockIdx.x];
-    const Group gr = op.groups[w.g];
-    const int rows_pad = (w.rows + 3) / 4 * 4;
-    const Seg<FS> s0{static_cast<const FS*>(op.far_pool) + gr.voff + w.r0, gr.ld, rows_pad, gr.n, X, ldx, nullptr,
-                     gr.c0};
-    int b0, b1;
-    drain_blocks(N8, b0, b1);
-    float racc[kMaxBlk][8];
-    const bool ok = tc_item<FS, FS>(s0, s0, 1, N8, nc, dsm, tmem, smem_u32(&sh.bar[0]), smem_u32(&sh.bar[1]), b0, b1,
-                                    racc);
-    const int lane = threadIdx.x & 31, row = 16 * ((threadIdx.x >> 5) & 3) + lane;
-    if (ok) {
-        if (lane < 16 && row < w.rows)
-#pragma unroll
-            for (int i = 0; i < kMaxBlk; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int col = 8 * (b0 + i) + j;
-                    if (b0 + i < b1 && col < nc) T[(long long)(gr.toff + w.r0 + row) * ldt + col] = racc[i][j];
-                }
-    } else if (threadIdx.x == 0) {
-        atomicExch(&g_tc_timeout, 1);
-    }
-    tc_teardown(sh);
-}
+// Chunk images and split vector planes of one product.
+struct TcArgs {
+    const unsigned char* img;
+    const long long* tile_near0;   // first chunk of every tile's dense panel
+    const long long* tile_far0;    // first chunk of every tile's U panel
+    const long long* item0;        // first chunk of every far-field item
+    const __nv_bfloat16* Xs;       // three planes of n x N8
+    __nv_bfloat16* Ts;             // three planes of sum_rank x N8
+    long long xplane, tplane;
+    int nc, N8;
+};
 
-size_t tc_smem_bytes(int N8) {
-    return (size_t)kRawStages * raw_stage_bytes(N8) + 2 * 8 * kGroupStride + 2 * (N8 / 8) * kGroupStride;
-}
+inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 }  // namespace
 
-// Launchers (FP32 vectors; FS = panel storage of the low-rank factors).
-// X and T rows must be 16-byte aligned with leading dimensions that are
-// multiples of 4 (the vector quads are read 16 bytes at a time).
-template <class FS>
-void tc_rows(const OpView& op, const float* X, int ldx, const float* T, int ldt, void* Y, int ldy, int nc,
-             const Epi& epi, cudaStream_t s) {
+// ---------------------------------------------------------------- host side
+bool tc_supported(const rad_htree* h) { return h->compressed && !h->op_is_f64() && !h->from_dense; }
+
+void tc_drop_images(rad_htree* h) {
+    h->tc_img.release(nullptr);
+    h->tc_tile_near0.release(nullptr);
+    h->tc_tile_far0.release(nullptr);
+    h->tc_item0.release(nullptr);
+    h->tc_ready = false;
+}
+
+// The three BF16 chunk images of every panel (dense and U panels per tile,
+// V^T panels per far-field item), built once for the tensor-core path.
+void tc_build_images(rad_htree* h, cudaStream_t s) {
+    RAD_REQUIRE(tc_supported(h), RAD_EINVAL, "tensor-core products need an FP32 or BF16 operator");
+    if (h->tc_ready) return;
+    std::vector<GWork> gw(h->n_gwork);
+    if (h->n_gwork > 0)
+        RAD_CUDA(cudaMemcpyAsync(gw.data(), h->d_gwork.p, sizeof(GWork) * gw.size(), cudaMemcpyDeviceToHost, s));
+    RAD_CUDA(cudaStreamSynchronize(s));
+    const int nt = h->n_tiles;
+    std::vector<long long> near0(std::max(1, nt)), far0(std::max(1, nt)), item0(std::max<size_t>(1, gw.size()));
+    std::vector<PackJob> jn, jf;   // near pool jobs, factor pool jobs
+    long long cur = 0;
+    for (int t = 0; t < nt; ++t) {
+        const Tile& tl = h->tiles_h[t];
+        near0[t] = cur;
+        for (int k0 = 0; k0 < tl.kn; k0 += kKC) jn.push_back(PackJob{tl.noff, tl.ld, tl.rows, k0, tl.kn, cur++});
+        far0[t] = cur;
+        for (int k0 = 0; k0 < tl.kf; k0 += kKC) jf.push_back(PackJob{tl.foff, tl.ld, tl.rows, k0, tl.kf, cur++});
+    }
+    for (size_t w = 0; w < gw.size(); ++w) {
+        const Group& g = h->groups_h[gw[w].g];
+        item0[w] = cur;
+        for (int k0 = 0; k0 < g.n; k0 += kKC)
+            jf.push_back(PackJob{g.voff + gw[w].r0, g.ld, gw[w].rows, k0, g.n, cur++});
+    }
+    h->tc_img.alloc((size_t)std::max<long long>(cur, 1) * kChunkBytes, s);
+    h->tc_tile_near0.alloc(sizeof(long long) * near0.size(), s);
+    h->tc_tile_far0.alloc(sizeof(long long) * far0.size(), s);
+    h->tc_item0.alloc(sizeof(long long) * item0.size(), s);
+    RAD_CUDA(cudaMemcpyAsync(h->tc_tile_near0.p, near0.data(), sizeof(long long) * near0.size(), cudaMemcpyHostToDevice, s));
+    RAD_CUDA(cudaMemcpyAsync(h->tc_tile_far0.p, far0.data(), sizeof(long long) * far0.size(), cudaMemcpyHostToDevice, s));
+    RAD_CUDA(cudaMemcpyAsync(h->tc_item0.p, item0.data(), sizeof(long long) * item0.size(), cudaMemcpyHostToDevice, s));
+    Scratch ws(s);
+    for (int pass = 0; pass < 2; ++pass) {
+        const std::vector<PackJob>& jv = pass == 0 ? jn : jf;
+        if (jv.empty()) continue;
+        PackJob* d = ws.get_n<PackJob>(jv.size());
+        RAD_CUDA(cudaMemcpyAsync(d, jv.data(), sizeof(PackJob) * jv.size(), cudaMemcpyHostToDevice, s));
+        ProfScope ps_("tc_pack", s);
+        if (pass == 0) {
+            tc_pack_kernel<float><<<(unsigned)jv.size(), 256, 0, s>>>(h->near_pool.as<float>(), d, h->tc_img.as<unsigned char>());
+        } else if (h->factor_dtype == RAD_F32) {
+            tc_pack_kernel<float><<<(unsigned)jv.size(), 256, 0, s>>>(h->far_pool.as<float>(), d, h->tc_img.as<unsigned char>());
+        } else {
+            tc_pack_kernel<__nv_bfloat16><<<(unsigned)jv.size(), 256, 0, s>>>(h->far_pool.as<__nv_bfloat16>(), d,
+                                                                               h->tc_img.as<unsigned char>());
+        }
+        RAD_CHECK_LAUNCH();
+    }
+    RAD_CUDA(cudaStreamSynchronize(s));   // the host job lists go out of scope
+    h->tc_ready = true;
+}
+
+// Workspace of one tensor-core product of up to kMaxN8 columns: the split
+// planes of X (n rows) and of T (sum_rank rows).
+size_t tc_workspace_bytes(const rad_htree* h, int nrhs) {
+    const int N8 = std::min(kMaxN8, (nrhs + 7) / 8 * 8);
+    return align256((size_t)3 * h->n * N8 * 2) + align256((size_t)3 * std::max(1, h->sum_rank) * N8 * 2) + 256;
+}
+
+// Y = F X for nc <= 96 FP32 columns (rows of X at stride ldx), epilogue as
+// in apply_tree; ws holds tc_workspace_bytes(h, nc) bytes.
+void tc_product(const rad_htree* h, const OpView& op, const float* X, int ldx, void* Y, int ldy, int nc,
+                const Epi& epi, void* ws, cudaStream_t s) {
+    RAD_REQUIRE(h->tc_ready, RAD_EINVAL, "tensor-core images missing (select the path first)");
     const int N8 = (nc + 7) / 8 * 8;
-    const size_t bytes = tc_smem_bytes(N8);
+    const int n = (int)h->n;
+    unsigned char* base = reinterpret_cast<unsigned char*>(align256(reinterpret_cast<uintptr_t>(ws)));
+    TcArgs ta;
+    ta.img = h->tc_img.as<unsigned char>();
+    ta.tile_near0 = h->tc_tile_near0.as<long long>();
+    ta.tile_far0 = h->tc_tile_far0.as<long long>();
+    ta.item0 = h->tc_item0.as<long long>();
+    ta.xplane = (long long)n * N8;
+    ta.tplane = (long long)std::max(1, h->sum_rank) * N8;
+    ta.Xs = reinterpret_cast<const __nv_bfloat16*>(base);
+    ta.Ts = reinterpret_cast<__nv_bfloat16*>(base + align256((size_t)3 * ta.xplane * 2));
+    ta.nc = nc;
+    ta.N8 = N8;
+    const size_t smem = (size_t)kRingStages * stage_bytes(N8) + (size_t)kTileRows * (N8 + 1) * 4;
     static std::once_flag configured;
+    static int sms = 0;
     std::call_once(configured, [&] {
-        RAD_CUDA(cudaFuncSetAttribute(tc_rows_kernel<FS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)tc_smem_bytes(96)));
+        RAD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kRingStages * stage_bytes(kMaxN8) + kTileRows * (kMaxN8 + 1) * 4));
+        int dev = 0;
+        RAD_CUDA(cudaGetDevice(&dev));
+        RAD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     });
-    { ProfScope ps_("hmm_rows", s); tc_rows_kernel<FS><<<op.n_tiles, 256, bytes, s>>>(op, X, ldx, T, ldt, Y, ldy, nc, N8, epi); }
+    {
+        ProfScope ps_("tc_split", s);
+        const long long tot = ta.xplane;
+        tc_split_rows_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 4096), 256, 0, s>>>(
+            X, ldx, n, nc, N8, const_cast<__nv_bfloat16*>(ta.Xs), ta.xplane);
+    }
+    RAD_CHECK_LAUNCH();
+    if (op.n_gwork > 0) {
+        Items it{false, op, ta.item0, nullptr, ta.img, ta.Xs, ta.Ts, ta.xplane, ta.tplane};
+        ProfScope ps_("hmm_far_vt", s);
+        tc_gemm_kernel<<<std::min(op.n_gwork, sms), 256, smem, s>>>(it, nc, N8, nullptr, 0, epi, ta.Ts, ta.tplane);
+        RAD_CHECK_LAUNCH();
+    }
+    {
+        Items it{true, op, ta.tile_near0, ta.tile_far0, ta.img, ta.Xs, ta.Ts, ta.xplane, ta.tplane};
+        ProfScope ps_("hmm_rows", s);
+        tc_gemm_kernel<<<std::min(op.n_tiles, sms), 256, smem, s>>>(it, nc, N8, Y, ldy, epi, nullptr, 0);
+    }
     RAD_CHECK_LAUNCH();
 }
-template <class FS>
-void tc_far_vt(const OpView& op, const float* X, int ldx, float* T, int ldt, int nc, cudaStream_t s) {
-    const int N8 = (nc + 7) / 8 * 8;
-    const size_t bytes = tc_smem_bytes(N8);
-    static std::once_flag configured;
-    std::call_once(configured, [&] {
-        RAD_CUDA(cudaFuncSetAttribute(tc_far_vt_kernel<FS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)tc_smem_bytes(96)));
-    });
-    { ProfScope ps_("hmm_far_vt", s); tc_far_vt_kernel<FS><<<op.n_gwork, 256, bytes, s>>>(op, X, ldx, T, ldt, nc, N8); }
-    RAD_CHECK_LAUNCH();
-}
-template void tc_rows<float>(const OpView&, const float*, int, const float*, int, void*, int, int, const Epi&,
-                             cudaStream_t);
-template void tc_rows<__nv_bfloat16>(const OpView&, const float*, int, const float*, int, void*, int, int, const Epi&,
-                                     cudaStream_t);
-template void tc_far_vt<float>(const OpView&, const float*, int, float*, int, int, cudaStream_t);
-template void tc_far_vt<__nv_bfloat16>(const OpView&, const float*, int, float*, int, int, cudaStream_t);
 
 // Reads and clears the timeout flag of the tensor-core kernels.
 bool tc_take_timeout() {

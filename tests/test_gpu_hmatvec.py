@@ -102,8 +102,8 @@ def test_caller_provided_outputs(c1):
 @pytest.mark.parametrize("path", [0, 1])
 def test_many_column_paths_match_column_by_column(cyl, factor, path):
     """The many-column product, on CUDA cores (path 0) and on tensor cores
-    (path 1, split TF32), equals the one-column streaming product column by
-    column to FP32 accuracy, for FP32 and BF16 factors (same stored
+    (path 1, BF16 x 3 split), equals the one-column streaming product column
+    by column to FP32 accuracy, for FP32 and BF16 factors (same stored
     operator)."""
     verts, F = cyl
     r = rad()
@@ -118,3 +118,50 @@ def test_many_column_paths_match_column_by_column(cyl, factor, path):
         # FP32 rounding of sums of |F| |x|: scale by the product with |x|
         scale = np.abs(r.rad_hmatvec(h, np.ascontiguousarray(np.abs(X[:, c])))).max()
         assert np.abs(Y[:, c] - y1).max() <= 2e-6 * scale, c
+
+
+@pytest.mark.parametrize("nc", [5, 9, 64, 65, 96, 130])
+def test_tensor_core_product_against_the_dense_oracle(cyl, nc):
+    """The tensor-core product (path 1) against the oracle's dense F X, column
+    by column, beside the CUDA-core product (path 0): both within the FP32
+    bound of the operator (ACA tol 1e-7) and within FP32 rounding of each
+    other (a few FP32 ulps).  Covers one and two column chunks (96 per launch) and ragged
+    widths (N padded to a multiple of 8)."""
+    verts, F = cyl
+    r = rad()
+    h = r.rad_build_htree(verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-7, 64, "partial", "f32", "f32")
+    X = np.random.default_rng(nc).uniform(0.0, 1.0, size=(F.shape[0], nc)).astype(np.float32)
+    ref = F @ X.astype(np.float64)
+    out = {}
+    for path in (0, 1):
+        r.rad_htree_set_product_path(h, path)
+        out[path] = r.rad_hmatvec(h, X).astype(np.float64)
+        for c in range(nc):
+            assert rel(out[path][:, c], ref[:, c]) <= 1e-6, (path, c)
+    # the two paths round differently (FFMA sums whole panels in FP32, the
+    # tensor cores restart every 128 columns): FP32-level agreement
+    assert np.abs(out[1] - out[0]).max() <= 5e-6 * np.abs(ref).max()
+    r.rad_htree_free(h)
+
+
+def test_tensor_core_path_in_the_solver_meets_the_oracle():
+    """The flux solve with the tensor-core product (every GMRES product and
+    the flux epilogue) against the oracle's direct solve."""
+    r = rad()
+    verts = cv.closed_cylinder(1.0, 4.0, 40, 24, 4)
+    rng = np.random.default_rng(6)
+    eps = rng.uniform(0.3, 0.9, verts.shape[0])
+    T = rng.uniform(300, 1200, (verts.shape[0], 12))
+    F = viewfactor.dense(geometry.facets_from_triangles(verts))
+    from oracle import radiosity
+    qref, _, _ = radiosity.solve_flux(F, eps, T, SIGMA_SB)
+    h = r.rad_build_htree(verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-7, 64, "partial", "f32", "f32")
+    q0, i0 = r.rad_solve_flux(h, eps, T, SIGMA_SB, tol=1e-7)
+    r.rad_htree_set_product_path(h, 1)
+    q1, i1 = r.rad_solve_flux(h, eps, T, SIGMA_SB, tol=1e-7)
+    assert i0["status"] == 0 and i1["status"] == 0
+    for q in (q0, q1):
+        assert rel(q, qref) <= 1e-6
+    r.rad_htree_free(h)
