@@ -200,6 +200,8 @@ typedef struct {
     int32_t grid_a2, grid_b2;    /* grids of the 2-4 column launches            */
     int32_t product_path;        /* >= 5 FP32 columns: 0 CUDA cores, 1 tensor cores */
     int32_t closed;              /* 1 after rad_htree_close_cavity               */
+    int32_t one_column_path;     /* 1 column: 1 one fused launch, 0 two launches */
+    int32_t reserved;
 } rad_htree_stats;
 
 /* -------------------------------------------------------------------------
@@ -299,6 +301,19 @@ int rad_htree_autotune(rad_htree* h, void* stream);
  * on an FP64 operator. */
 int rad_htree_set_product_path(rad_htree* h, int32_t path);
 
+/* Kernel family of the one-column product (§5.2, y = F x; no counterpart in
+ * the paper): 1 = one fused launch (the default where the operator allows
+ * it: FP32 dense panels, FP32 or BF16 factors, panels of at most 1024 rows)
+ * in which every CTA streams panel chunks through a ring of shared-memory
+ * stages filled by 1-D bulk copies, the products T = V^T x and the dense
+ * panels first and the U panels after all of T is written; 0 = two launches
+ * (phase A: T and the dense panels, phase B: the U panels).  Both compute
+ * every output row in one CTA in a fixed order; they sum a row's terms in
+ * different orders, so results agree to rounding.  rad_htree_autotune picks
+ * the faster; compression resets it to 1.  RAD_EINVAL for another value, or
+ * for path 1 on an operator that does not allow it. */
+int rad_htree_set_one_column_path(rad_htree* h, int32_t path);
+
 /* Closed-cavity treatment of the view factors (§6, Eqs. rowsum,
  * clamped_rowsum and F_closed, with the textbook F): s_i = sum_j F_ij of
  * the stored operator (the FP32 accurate copy when the factors are BF16),
@@ -341,7 +356,7 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
  *   - x and y must be device arrays (host arrays are rejected: staging them
  *     would allocate);
  *   - it needs round256(s * n * p) + round256(s * n * nrhs)
- *     + round256(s * (max(sum_rank, 1) * p + (nrhs == 1 ? n : 0))) bytes,
+ *     + round256(s * (max(sum_rank, 1) * p + (nrhs == 1 ? n + 16 : 0))) bytes,
  *     s = 8 for an FP64 operator and 4 otherwise, p = 1 for one column and
  *     nrhs rounded up to a multiple of 4 otherwise (sum_rank from
  *     rad_htree_get_stats), plus round256(6 (n + max(sum_rank, 1)) q) + 512

@@ -174,7 +174,8 @@ class _Stats(C.Structure):
                 ("far_u_entries", C.c_int64), ("far_v_entries", C.c_int64), ("n_tiles", C.c_int64),
                 ("bytes_accurate", C.c_int64), ("tuned", C.c_int32), ("stream_rows", C.c_int32),
                 ("grid_a1", C.c_int32), ("grid_b1", C.c_int32), ("grid_a2", C.c_int32), ("grid_b2", C.c_int32),
-                ("product_path", C.c_int32), ("closed", C.c_int32)]
+                ("product_path", C.c_int32), ("closed", C.c_int32), ("one_column_path", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 def _load():
@@ -206,6 +207,7 @@ def _load():
         "rad_htree_free": (C.c_int, [H]),
         "rad_htree_autotune": (C.c_int, [H, vp]),
         "rad_htree_set_product_path": (C.c_int, [H, i32]),
+        "rad_htree_set_one_column_path": (C.c_int, [H, i32]),
         "rad_htree_close_cavity": (C.c_int, [H, vp, vp]),
         "rad_server_create": (C.c_int, [C.POINTER(_ServerParams), C.POINTER(vp)]),
         "rad_server_add_cavity": (C.c_int, [vp, i64, vp, C.POINTER(i64)]),
@@ -682,7 +684,8 @@ def rad_htree_autotune(h: HTree, stream=None) -> dict:
     this handle's operator; returns the chosen configuration."""
     _check(_lib.rad_htree_autotune(h.ptr, _stream(stream)))
     st = rad_htree_get_stats(h)
-    return {k: st[k] for k in ("stream_rows", "grid_a1", "grid_b1", "grid_a2", "grid_b2", "product_path")}
+    return {k: st[k] for k in ("stream_rows", "grid_a1", "grid_b1", "grid_a2", "grid_b2", "product_path",
+                               "one_column_path")}
 
 
 def rad_htree_close_cavity(h: HTree, stream=None) -> np.ndarray:
@@ -693,8 +696,13 @@ def rad_htree_close_cavity(h: HTree, stream=None) -> np.ndarray:
 
 
 def rad_htree_set_product_path(h: HTree, path: int) -> None:
-    """0: CUDA-core tiles, 1: tensor cores (split TF32) for >= 5 FP32 columns."""
+    """0: CUDA-core tiles, 1: tensor cores (BF16 x 3 split) for >= 5 FP32 columns."""
     _check(_lib.rad_htree_set_product_path(h.ptr, int(path)))
+
+
+def rad_htree_set_one_column_path(h: HTree, path: int) -> None:
+    """One-column product: 1 one fused launch, 0 two launches."""
+    _check(_lib.rad_htree_set_one_column_path(h.ptr, int(path)))
 
 
 def rad_htree_get_stats(h: HTree) -> dict:

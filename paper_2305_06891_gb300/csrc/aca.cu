@@ -1188,8 +1188,10 @@ static void upload_operator(rad_htree* h, const HVec<IdxRun>& near_runs, const H
     h2d(h->d_forder.as<int>(), forder, s);
     build_stream_lists(h, h->stream_rows, s);
     h->d_tiles.alloc(sizeof(Tile) * std::max<size_t>(1, h->tiles_h.size()), s);
-    h->d_xidx.alloc(sizeof(int) * std::max<long long>(1, nx), s);
-    h->d_tidx.alloc(sizeof(int) * std::max<long long>(1, nf), s);
+    // 4 ints of slack after each list: the fused one-column product copies
+    // index slices in whole 16-byte words
+    h->d_xidx.alloc(sizeof(int) * (std::max<long long>(1, nx) + 4), s);
+    h->d_tidx.alloc(sizeof(int) * (std::max<long long>(1, nf) + 4), s);
     h->d_gwork.alloc(sizeof(GWork) * std::max<size_t>(1, gwork.size()), s);
     h->d_groups.alloc(sizeof(Group) * std::max<size_t>(1, h->groups_h.size()), s);
     h2d(h->d_tiles.as<Tile>(), h->tiles_h, s);
@@ -1206,6 +1208,7 @@ static void upload_operator(rad_htree* h, const HVec<IdxRun>& near_runs, const H
         { ProfScope ps_("gather_lists", s); fill_runs_kernel<<<(unsigned)((rl.size() + 7) / 8), 256, 0, s>>>(d, (int)rl.size(), h->d_tiles.as<Tile>(), f, outs[f]); }
         RAD_CHECK_LAUNCH();
     }
+    hmv1_plan(h, s);
 }
 
 template <class S, class CT>
@@ -1625,6 +1628,7 @@ void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     h->grid_a1 = h->grid_b1 = h->grid_a2 = h->grid_b2 = 0;
     h->tuned = 0;
     h->mm_path = 0;
+    h->one_col_path = 1;
     tc_drop_images(h);
     h->closed = 0;
     h->compressed = false;

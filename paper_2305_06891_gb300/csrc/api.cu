@@ -523,7 +523,7 @@ static bool product_via_graph(const rad_htree* h, int32_t dtype, const void* x, 
 
 extern "C" {
 
-int rad_version(void) { return 10100; }
+int rad_version(void) { return 10200; }
 
 int rad_debug_bounds_checks(void) {
 #ifdef RAD_CHECK_BOUNDS
@@ -728,6 +728,7 @@ int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx, v
             scatter_tree_to_user(h, Y, nr, nr, op64, dtype, yd, n, s);
             RAD_CUDA(cudaMemcpy2DAsync(y, esz * ldy, yd, esz * n, esz * n, nr, cudaMemcpyDeviceToHost, s));
             RAD_CUDA(cudaStreamSynchronize(s));
+            RAD_REQUIRE(!wait_timed_out(), RAD_ECUDA, "a pipelined kernel's wait timed out (results are incomplete)");
         }
     });
 }
@@ -765,7 +766,7 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
             RAD_CUDA(cudaMemcpy2DAsync(q, 8 * ldq, qd, 8 * (size_t)n, 8 * (size_t)n, m, cudaMemcpyDeviceToHost, s));
             RAD_CUDA(cudaStreamSynchronize(s));
         }
-        RAD_REQUIRE(!tc_take_timeout(), RAD_ECUDA, "a tensor-core wait timed out (results are incomplete)");
+        RAD_REQUIRE(!wait_timed_out(), RAD_ECUDA, "a pipelined kernel's wait timed out (results are incomplete)");
         if (info) *info = local;
         solve_status = local.status;
         if (solve_status != RAD_OK) set_last_error("GMRES did not reach the tolerance");
@@ -805,7 +806,7 @@ int rad_solve_reflection(const rad_htree* h, const double* eps, const double* B,
             RAD_CUDA(cudaMemcpy2DAsync(Y, 8 * ldY, Yd, 8 * (size_t)n, 8 * (size_t)n, nrhs, cudaMemcpyDeviceToHost, s));
             RAD_CUDA(cudaStreamSynchronize(s));
         }
-        RAD_REQUIRE(!tc_take_timeout(), RAD_ECUDA, "a tensor-core wait timed out (results are incomplete)");
+        RAD_REQUIRE(!wait_timed_out(), RAD_ECUDA, "a pipelined kernel's wait timed out (results are incomplete)");
         if (info) *info = local;
         solve_status = local.status;
         if (solve_status != RAD_OK) set_last_error("GMRES did not reach the tolerance");
@@ -849,6 +850,8 @@ int rad_htree_get_stats(const rad_htree* h, rad_htree_stats* st) {
         st->grid_b2 = h->grid_b2;
         st->product_path = h->mm_path;
         st->closed = h->closed;
+        st->one_column_path = h->one_col_path == 1 && h->hmv1_ok ? 1 : 0;
+        st->reserved = 0;
     });
 }
 
@@ -938,6 +941,18 @@ int rad_htree_set_product_path(rad_htree* h, int32_t path) {
             tc_drop_images(h);
         }
         h->mm_path = path;
+    });
+}
+
+int rad_htree_set_one_column_path(rad_htree* h, int32_t path) {
+    return guarded(__func__, [&] {
+        RAD_REQUIRE(h != nullptr, RAD_EINVAL, "null argument");
+        RAD_REQUIRE(path == 0 || path == 1, RAD_EINVAL, "path must be 0 (two launches) or 1 (one fused launch)");
+        RAD_REQUIRE(path == 0 || h->hmv1_ok, RAD_EINVAL,
+                    "the fused one-column product needs a compressed operator with FP32 dense panels, FP32 or "
+                    "BF16 factors and panels of at most 1024 rows");
+        drop_product_graph(h);
+        h->one_col_path = path;
     });
 }
 

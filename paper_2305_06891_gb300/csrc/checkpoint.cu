@@ -20,7 +20,7 @@ namespace rad {
 namespace {
 
 constexpr char kMagic[8] = {'R', 'A', 'D', 'H', 'T', 'R', 'E', 'E'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 
 // Scalars of the handle, copied as one struct.
 struct Scalars {
@@ -34,6 +34,7 @@ struct Scalars {
     int64_t n_dense_fallback, near_entries, far_entries, aca_entries;
     int64_t far_u_entries, far_v_entries, stored_near, stored_far;
     int32_t stream_rows, grid_a1, grid_b1, grid_a2, grid_b2, tuned, mm_path, closed;
+    int32_t one_col_path, pad;
 };
 
 struct Writer {
@@ -157,6 +158,7 @@ int rad_htree_save(const rad_htree* h, void* buf, uint64_t* bytes) {
         sc.tuned = h->tuned;
         sc.mm_path = h->mm_path;
         sc.closed = h->closed;
+        sc.one_col_path = h->one_col_path;
         w.field(&sc, sizeof sc);
         w.vec(h->seg);
         w.vec(h->nodes);
@@ -242,6 +244,7 @@ int rad_htree_load(const void* buf, uint64_t bytes, const rad_tree_params* p, vo
         h->tuned = sc.tuned;
         h->mm_path = sc.mm_path;
         h->closed = sc.closed;
+        h->one_col_path = sc.one_col_path;
         r.vec(h->seg);
         r.vec(h->nodes);
         r.vec(h->boxes);
@@ -258,7 +261,9 @@ int rad_htree_load(const void* buf, uint64_t bytes, const rad_tree_params* p, vo
         RAD_REQUIRE(r.left == 0, RAD_EINVAL, "checkpoint blob has trailing bytes");
         RAD_REQUIRE(h->perm.bytes == sizeof(int) * (size_t)h->n && h->geo.bytes == sizeof(double) * 7 * (size_t)h->n,
                     RAD_EINVAL, "checkpoint device arrays do not fit the facet count");
-        if (h->mm_path == 1) tc_build_images(h.get(), s);   // derived data, rebuilt
+        // derived data, rebuilt: the fused one-column units, the split images
+        if (h->compressed) hmv1_plan(h.get(), s);
+        if (h->mm_path == 1) tc_build_images(h.get(), s);
         RAD_CUDA(cudaStreamSynchronize(s));
         check_bounds_after_call();
         *out = h.release();

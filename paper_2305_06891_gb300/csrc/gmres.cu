@@ -415,7 +415,9 @@ static void gmres_tree(const rad_htree* h, const double* eps_t, const double* B,
     const int* seg = red.nseg > 1 ? h->d_segrow.as<int>() : nullptr;
     double* W = ws.get_n<double>(nv);
     double* V = ws.get_n<double>(nv * (R + 1));
-    const int ldp = (nc + 3) / 4 * 4;                  // padded row stride of the FP32 copy
+    // row stride of the FP32 copy: the product's vector layout (1 for one
+    // column, else padded to a multiple of 4 for 16-byte rows)
+    const int ldp = tree_ld(nc);
     float* X32 = op64 ? nullptr : ws.get_n<float>((long long)n * ldp);
     void* Tws = ws.get(apply_workspace_bytes(h, nc));
     double* Hm = ws.get_n<double>((long long)R * (R + 1) * nvc);
@@ -657,7 +659,7 @@ void solve_flux(const rad_htree* h, const double* eps_dev, const double* T_dev, 
         { ProfScope ps_("flux", s); flux_kernel<double><<<grid_for((long long)n * m), 256, 0, s>>>(n, m, FY, h->perm.as<int>(), eps_dev, T_dev,
                                                                       ldT, sigma, q_dev, ldq); }
     } else {
-        const int ldp = (nc + 3) / 4 * 4;
+        const int ldp = tree_ld(nc);
         float* X32 = ws.get_n<float>((long long)n * ldp);
         float* FY = ws.get_n<float>(nv);
         { ProfScope ps_("gmres_convert", s); to_f32_kernel<<<grid_for(nv), 256, 0, s>>>(X, X32, nv, nc, ldp); }

@@ -20,6 +20,7 @@
 //   kReflect: w = xin - (1 - eps) o (F x)
 //   kResid:   r = b - (xin - (1 - eps) o (F x))
 
+#include <algorithm>
 #include <mutex>
 
 #include <type_traits>
@@ -751,6 +752,14 @@ void apply_t(const rad_htree* h, const OpView& op, const AT* X, int ldx, void* Y
              AT* T, cudaStream_t s) {
     if (nrhs == 1) {
         AT* Yn = T + std::max(1, op.sum_rank);
+        if constexpr (std::is_same<AT, float>::value && std::is_same<NS, float>::value) {
+            if (h->one_col_path == 1 && h->hmv1_ok) {
+                // the fused launch's two counters follow Yn, 16-byte aligned
+                const uintptr_t c = (reinterpret_cast<uintptr_t>(Yn + h->n) + 15) & ~(uintptr_t)15;
+                hmv1_product(h, X, T, Yn, reinterpret_cast<int*>(c), Y, epi, s);
+                return;
+            }
+        }
         { ProfScope ps_("hmv_phase_a", s); single_phase_a<NS, FS, AT><<<grid_of(h->grid_a1, op.n_aitems), 256, 0, s>>>(op, X, T, Yn); }
         RAD_CHECK_LAUNCH();
         { ProfScope ps_("hmv_phase_b", s); single_phase_b<FS, AT><<<grid_of(h->grid_b1, op.n_tiles), 256, 0, s>>>(op, T, Yn, Y, epi); }
@@ -822,10 +831,12 @@ __global__ void scatter_kernel(int n, int nrhs, const TI* __restrict__ Y, int ld
 
 size_t apply_workspace_bytes(const rad_htree* h, int nrhs) {
     const size_t esz = h->op_is_f64() ? 8 : 4;
-    // T = V^T X, plus the dense-panel partial sums of a one-column product,
-    // plus the split vector planes of the tensor-core path
+    // T = V^T X, plus (one column) the dense-panel partial sums and 16
+    // elements holding the fused launch's counters, plus the split vector
+    // planes of the tensor-core path
     const size_t tc = nrhs >= 5 && h->mm_path == 1 && !h->op_is_f64() ? tc_workspace_bytes(h, nrhs) : 0;
-    return esz * ((size_t)std::max(1, h->sum_rank) * (size_t)tree_ld(nrhs) + (nrhs == 1 ? (size_t)h->n : 0)) + tc;
+    return esz * ((size_t)std::max(1, h->sum_rank) * (size_t)tree_ld(nrhs) + (nrhs == 1 ? (size_t)h->n + 16 : 0)) +
+           tc;
 }
 
 void apply_tree(const rad_htree* h, const void* X, int ldx, void* Y, int ldy, int nrhs, const Epi& epi,
@@ -1062,6 +1073,18 @@ struct Tuner {
         h->grid_b1 = gb1;
         h->grid_a2 = ga2;
         h->grid_b2 = gb2;
+        // one column: the fused launch or the two tuned launches
+        if constexpr (std::is_same<AT, float>::value && std::is_same<NS, float>::value) {
+            if (h->hmv1_ok) {
+                const Epi epi{kStore, nullptr, nullptr, nullptr, 0};
+                float t1[2];
+                for (int path = 0; path < 2; ++path) {
+                    h->one_col_path = path;
+                    t1[path] = time([&] { apply_t<NS, FS, AT>(h, h->view(), X, 1, Y, 1, 1, epi, T, s); });
+                }
+                h->one_col_path = t1[1] <= t1[0] ? 1 : 0;
+            }
+        }
         // many-column product: CUDA-core tiles or tensor cores, 64 columns
         if constexpr (std::is_same<AT, float>::value && std::is_same<NS, float>::value) {
             float best = 1e30f;
@@ -1098,7 +1121,8 @@ void autotune(rad_htree* h, cudaStream_t s) {
     RAD_CUDA(cudaEventCreate(&e1));
     void* X = ws.get(esz * 2 * (size_t)n);
     void* Y = ws.get(8 * 64 * (size_t)n);
-    const size_t tb = std::max(apply_workspace_bytes(h, 4) + esz * (size_t)n, apply_workspace_bytes(h, 64)) +
+    const size_t tb = std::max({apply_workspace_bytes(h, 4) + esz * (size_t)n, apply_workspace_bytes(h, 64),
+                                apply_workspace_bytes(h, 1)}) +
                       (h->op_is_f64() ? 0 : tc_workspace_bytes(h, 64));
     void* T = ws.get(tb);
     void* X64 = ws.get(esz * 64 * (size_t)n);

@@ -407,6 +407,15 @@ struct rad_htree {
     // first chunk of every tile's dense / U panel and of every far item
     rad::DevBuf tc_img, tc_tile_near0, tc_tile_far0, tc_item0;
     bool tc_ready = false;
+    // one-column product: 1 = the fused single launch (when the operator
+    // allows it, hmv1_ok), 0 = the two launches (phase A, phase B); set by
+    // rad_htree_autotune or rad_htree_set_one_column_path.  The fused
+    // launch's work units (A units, then B units) are rebuilt with the
+    // operator.
+    int one_col_path = 1;
+    rad::DevBuf d_units1;
+    int n_units1 = 0, n_a1 = 0;
+    bool hmv1_ok = false;
     int closed = 0;   // rows normalised for a closed cavity (rad_htree_close_cavity)
     int64_t n = 0;
     rad::Allocator alloc;   // device memory of the handle and of calls on it
@@ -521,6 +530,19 @@ size_t tc_workspace_bytes(const rad_htree* h, int nrhs);
 void tc_product(const rad_htree* h, const OpView& op, const float* X, int ldx, void* Y, int ldy, int nc,
                 const Epi& epi, void* ws, cudaStream_t s);
 bool tc_take_timeout();
+// hmv1.cu: the fused one-column product (FP32 vectors, FP32 dense panels,
+// FP32 or BF16 factors)
+void hmv1_plan(rad_htree* h, cudaStream_t s);
+void hmv1_product(const rad_htree* h, const float* x, float* T, float* Yn, int* ctr, void* Y, const Epi& epi,
+                  cudaStream_t s);
+bool hmv1_take_timeout();
+// true when a bounded wait of a pipelined kernel gave up since the last call
+// (clears the flags)
+inline bool wait_timed_out() {
+    const bool a = tc_take_timeout();
+    const bool b = hmv1_take_timeout();
+    return a || b;
+}
 void build_stream_lists(rad_htree* h, int rows, cudaStream_t s);
 void autotune(rad_htree* h, cudaStream_t s);
 void close_cavity(rad_htree* h, double* s_tree_out, cudaStream_t s);

@@ -165,3 +165,53 @@ def test_tensor_core_path_in_the_solver_meets_the_oracle():
     for q in (q0, q1):
         assert rel(q, qref) <= 1e-6
     r.rad_htree_free(h)
+
+
+@pytest.mark.parametrize("factor", ["f32", "bf16"])
+def test_one_column_fused_and_two_launch_paths_against_the_oracle(cyl, factor):
+    """The one-column product in one fused launch (bulk-copy ring, A units
+    then B units) and in two launches: both within the FP32 bound of F x,
+    agreeing with each other to rounding, on a cavity whose column groups
+    span several 16 KiB stages and whose index slices start off 16-byte
+    boundaries."""
+    verts, F = cyl
+    r = rad()
+    x = np.random.default_rng(5).uniform(0.5, 1.5, size=F.shape[0])
+    yref = F @ x
+    h = r.rad_build_htree(verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-8, 64, "partial", factor, "f32")
+    assert r.rad_htree_get_stats(h)["one_column_path"] == 1
+    y1 = r.rad_hmatvec(h, x.astype(np.float32))
+    r.rad_htree_set_one_column_path(h, 0)
+    assert r.rad_htree_get_stats(h)["one_column_path"] == 0
+    y0 = r.rad_hmatvec(h, x.astype(np.float32))
+    bound = 1e-6 if factor == "f32" else 5e-3
+    assert rel(y1, yref) <= bound and rel(y0, yref) <= bound
+    assert rel(y1, y0) <= 2e-6
+    # repeated launches: the same bits (fixed summation order per row)
+    r.rad_htree_set_one_column_path(h, 1)
+    for _ in range(3):
+        np.testing.assert_array_equal(r.rad_hmatvec(h, x.astype(np.float32)), y1)
+    h.free()
+
+
+def test_one_column_fused_path_in_the_solver_and_after_closing(c1):
+    """The fused launch with the reflection epilogues of Eq. (11) inside
+    GMRES, and on a closed cavity (rows rescaled in place)."""
+    c, F = c1
+    r = rad()
+    h = r.rad_build_htree(c.verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-7, 64, "partial", "f32", "f32")
+    assert r.rad_htree_get_stats(h)["one_column_path"] == 1
+    T = np.asfortranarray(c.T[:, :1])
+    q1, i1 = r.rad_solve_flux(h, c.eps, T, SIGMA_SB, tol=1e-7)
+    r.rad_htree_set_one_column_path(h, 0)
+    q0, i0 = r.rad_solve_flux(h, c.eps, T, SIGMA_SB, tol=1e-7)
+    assert i1["status"] == 0 and i0["status"] == 0
+    assert rel(q1, q0) <= 1e-6
+    r.rad_htree_set_one_column_path(h, 1)
+    s = r.rad_htree_close_cavity(h)
+    y = r.rad_hmatvec(h, np.ones(h.n, dtype=np.float32))
+    expect = np.where((s > 0) & (s <= 1), 1.0, s)   # rows divided by clamp(s, 0, 1)
+    np.testing.assert_allclose(y, expect, rtol=0, atol=2e-6)
+    h.free()

@@ -124,3 +124,30 @@ def test_closed_cavity_rows_match_the_oracle(dt):
     ones = np.ones(f.c.shape[0]) if dt == "f64" else np.ones(f.c.shape[0], np.float32)
     assert np.abs(r.rad_hmatvec(h, ones) - 1.0).max() <= tol
     h.free()
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+def test_one_column_reflection_solve_in_fp32_storage_meets_the_direct_solve(dt):
+    """One right-hand side on an FP32 or BF16 operator (the one-column
+    product inside GMRES reads the FP32 copy of each Krylov vector), alone
+    and in a batch of two cavities, against the oracle's direct solve of
+    Eq. (11)."""
+    c = cv.config1()
+    f = geometry.facets_from_triangles(c.verts)
+    F = viewfactor.dense(f)
+    b = SIGMA_SB * c.eps * c.T[:, 0] ** 4
+    y_ref = np.linalg.solve(radiosity.reflection_matrix(F, c.eps), b)
+    r = rad()
+    h = r.rad_build_htree(c.verts, 32, 1.0)
+    r.rad_compress_aca(h, 1e-7, 64, "partial", dt, "f32", accurate_dtype="f32" if dt == "bf16" else None)
+    kw = dict(refine=True, inner_tol=1e-4, tol=1e-8) if dt == "bf16" else dict(tol=1e-7)
+    y, info = r.rad_solve_reflection(h, c.eps, b, **kw)
+    assert info["status"] == 0
+    assert rel(y, y_ref) <= 1e-6
+    h.free()
+    hb = r.rad_build_htree_batch(np.concatenate([c.verts, c.verts]), [c.n, c.n], 32, 1.0)
+    r.rad_compress_aca(hb, 1e-7, 64, "partial", dt, "f32", accurate_dtype="f32" if dt == "bf16" else None)
+    yb, info = r.rad_solve_reflection(hb, np.concatenate([c.eps, c.eps]), np.concatenate([b, 2 * b]), **kw)
+    assert info["status"] == 0
+    assert rel(yb[:c.n], y_ref) <= 1e-6 and rel(yb[c.n:], 2 * y_ref) <= 1e-6
+    hb.free()
