@@ -2,12 +2,13 @@
 // admissible blocks (§4.3, Eqs. 30-31), plus packing of the factors and the
 // row-tile tables used by the matrix-vector product.
 //
-// Partial-pivot ACA runs one warp per admissible block of at most 1024 rows
-// and 4096 columns and one 256-thread CTA per larger block, both in the same
-// launch.  Rows and columns of the block are evaluated on the fly from the
-// tree-ordered facet geometry; the residual row/column are written straight
-// into the block's slot of the U/V scratch (column-major, room for kmax
-// columns); pivots come from warp-shuffle (or block-wide) argmax reductions
+// Partial-pivot ACA runs one 256-thread CTA per admissible block with
+// m + n > kWarpMaxMN and, in the same launch, persistent warps that take the
+// other blocks one at a time (largest first) from a device counter.  Rows
+// and columns of the block are evaluated on the fly from the tree-ordered
+// facet geometry; the residual row/column are written straight into the
+// block's slot of the U/V scratch (column-major, room for kmax columns);
+// pivots come from warp-shuffle (or block-wide) argmax reductions
 // (ties: lowest index); the Frobenius-norm estimate of the cross and the dot
 // products accumulate in FP64 (or a two-sum FP32 pair where the tolerance
 // allows FP32 arithmetic).
@@ -38,6 +39,8 @@
 #include <cstring>
 #include <numeric>
 
+#include <mutex>
+
 #include "rad_device.cuh"
 
 namespace rad {
@@ -50,6 +53,10 @@ struct AcaJob {
 };
 
 constexpr int kAcaNT = 256;
+// Blocks with m + n above this run on a whole CTA: one warp would take
+// their ~m + n entries per step alone, and the largest of them would set
+// the length of the launch.
+constexpr int kWarpMaxMN = 768;
 
 // position of verification sample s (< m + n) of check c
 __device__ __forceinline__ void sample_pos(int s, int m, int n, int c, int& si, int& sj) {
@@ -115,17 +122,31 @@ __device__ int lowest_unused(const unsigned char* used, int m, int* sm) {
 }
 
 // For l < k: out[l] = sum_j a_j * B[l*ld + j] over this thread's j; plus
-// out[k] = sum_j a_j^2.  Results (FP64) land in red[0..k] for every thread.
+// out[k] = sum_j a_j^2.  Results land in red[0..k] for every thread.  Four
+// products per pass over the thread's j (their loads in flight together),
+// each summed over the warp by the same butterfly as warp_sum.
 template <class CT>
 __device__ void cross_dots(const CT* a, const CT* B, int len, long long ld, int k, CT (*part)[kMaxRank + 1],
                            CT* red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int l = 0; l <= k; ++l) {
-        CT s = 0;
-        const CT* bl = (l < k) ? B + (long long)l * ld : a;
-        for (int j = threadIdx.x; j < len; j += kAcaNT) s += a[j] * bl[j];
-        s = warp_sum(s);
-        if (lane == 0) part[warp][l] = s;
+    for (int l0 = 0; l0 <= k; l0 += 4) {
+        const int nq = min(4, k + 1 - l0);
+        const CT* rows[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rows[q] = (l0 + q < k) ? B + (long long)(l0 + q) * ld : a;
+        CT t[4] = {CT(0), CT(0), CT(0), CT(0)};
+        for (int j = threadIdx.x; j < len; j += kAcaNT) {
+            const CT aj = a[j];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < nq) t[q] += aj * rows[q][j];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) t[q] += __shfl_xor_sync(0xffffffffu, t[q], o);
+        if (lane == 0)
+            for (int q = 0; q < nq; ++q) part[warp][l0 + q] = t[q];
     }
     __syncthreads();
     if ((int)threadIdx.x <= k) {
@@ -413,12 +434,14 @@ __device__ void aca_warp_block(const Geo& g, const AcaJob& jb, int bidx, CT* Upo
 }
 
 // Blocks [0, n_big) of the grid take one large block each (CTA path); the
-// rest take eight small blocks each (one per warp).
+// other CTAs are persistent: each warp takes the next block of the `small`
+// list (largest first) from a device counter until the list is exhausted.
 template <class CT>
 __global__ void __launch_bounds__(kAcaNT, 4)
-aca_partial_kernel(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict__ big, int n_big,
-                   const int* __restrict__ small, int n_small, CT* Upool, CT* Vpool, unsigned char* used_pool,
-                   int* __restrict__ rank_out, long long* __restrict__ evals_out, double tol) {
+aca_partial_persistent(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict__ big, int n_big,
+                       const int* __restrict__ small, int n_small, int* __restrict__ next_small, CT* Upool,
+                       CT* Vpool, unsigned char* used_pool, int* __restrict__ rank_out,
+                       long long* __restrict__ evals_out, double tol) {
     __shared__ AcaSmem<CT> sm;
     if ((int)blockIdx.x < n_big) {
         const int bidx = big[blockIdx.x];
@@ -426,12 +449,17 @@ aca_partial_kernel(Geo g, const AcaJob* __restrict__ jobs, const int* __restrict
         aca_cta_block<CT>(g, jb, bidx, Upool, Vpool, used_pool, rank_out, evals_out, tol, sm);
         return;
     }
-    const int warp = threadIdx.x >> 5;
-    const int w = ((int)blockIdx.x - n_big) * (kAcaNT / 32) + warp;
-    if (w >= n_small) return;
-    const int bidx = small[w];
-    const AcaJob jb = jobs[bidx];
-    aca_warp_block<CT>(g, jb, bidx, Upool, Vpool, rank_out, evals_out, tol, sm.w_a[warp], sm.w_c[warp]);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(next_small, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= n_small) break;
+        const int bidx = small[w];
+        const AcaJob jb = jobs[bidx];
+        aca_warp_block<CT>(g, jb, bidx, Upool, Vpool, rank_out, evals_out, tol, sm.w_a[warp], sm.w_c[warp]);
+        __syncwarp();
+    }
 }
 
 // Full pivoting: the residual R (m x n, column-major) lives in scratch.
@@ -986,7 +1014,7 @@ void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>
         RAD_CUDA(cudaMemsetAsync(used, 0, std::max<long long>(sused, 1), s));
         std::vector<int> big, small;
         for (int b : order) {
-            if (jobs[b].m <= 1024 && jobs[b].n <= 4096) small.push_back(b);
+            if (jobs[b].m + jobs[b].n <= kWarpMaxMN) small.push_back(b);
             else big.push_back(b);
         }
         int* d_big = ws.get_n<int>(std::max<size_t>(1, big.size()));
@@ -994,8 +1022,19 @@ void launch_aca(rad_htree* h, const rad_aca_params* p, const std::vector<AcaJob>
         h2d(d_big, big, s);
         h2d(d_small, small, s);
         const int nb = (int)big.size(), nsm = (int)small.size();
-        const int grid = nb + (nsm + kAcaNT / 32 - 1) / (kAcaNT / 32);
-        { ProfScope ps_("aca_partial", s); aca_partial_kernel<CT><<<grid, kAcaNT, 0, s>>>(g, d_jobs, d_big, nb, d_small, nsm, Us, Vs, used, d_rank, d_evals, p->tol); }
+        int* d_next = ws.get_n<int>(1);
+        RAD_CUDA(cudaMemsetAsync(d_next, 0, sizeof(int), s));
+        static int persistent = 0;   // resident CTAs of the persistent kernel (one query per type)
+        static std::once_flag once;
+        std::call_once(once, [&] {
+            int dev = 0, sms = 0, per = 0;
+            RAD_CUDA(cudaGetDevice(&dev));
+            RAD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            RAD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, aca_partial_persistent<CT>, kAcaNT, 0));
+            persistent = std::max(1, per) * sms;
+        });
+        const int grid = nb + std::min(persistent, std::max(1, (nsm + kAcaNT / 32 - 1) / (kAcaNT / 32)));
+        { ProfScope ps_("aca_partial", s); aca_partial_persistent<CT><<<grid, kAcaNT, 0, s>>>(g, d_jobs, d_big, nb, d_small, nsm, d_next, Us, Vs, used, d_rank, d_evals, p->tol); }
     }
     RAD_CHECK_LAUNCH();
     ranks.resize(nj);

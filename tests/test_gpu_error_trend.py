@@ -4,9 +4,9 @@ approximation (Eq. 31 on every admissible block) the relative Frobenius
 error ||F - F_eps|| / ||F|| of the whole matrix stays below eps_rel and falls
 with it (the paper's spheres show about 0.1 eps_rel).  F_eps is read back
 from the GPU operator as F_eps I (products with identity columns); F is the
-oracle's dense matrix, and where no block reaches its rank cap the oracle's
-own full-pivot H-matrix on the same tree gives the same error (full pivoting
-picks the same pivots)."""
+oracle's dense matrix.  Against the oracle's own full-pivot H-matrix on the
+same tree the error is equal where no block is stored dense by the GPU's
+rank cap, and never larger otherwise."""
 import numpy as np
 import pytest
 
@@ -39,12 +39,18 @@ def test_error_follows_eps_rel_like_table_2():
         errs.append(err)
         if tol >= 1e-4:
             assert 5e-3 * tol <= err, (tol, err)              # a real approximation, not exact storage
-        if st["n_dense_fallback"] == 0:
-            # no block kept dense by the storage cap: the oracle's full-pivot
-            # H-matrix on the same tree has the same error
+        if tol >= 1e-4:
+            # the oracle's full-pivot H-matrix on the same tree: full pivoting
+            # picks the same pivots, so every block the GPU stores in low rank
+            # carries the oracle's error; the blocks it stores dense (rank
+            # above m n / (m + n), a storage rule of the GPU only) carry none,
+            # so the GPU error never exceeds the oracle's and equals it when
+            # no block falls back
             Ho = hmatrix.build(f, 32, 1.0, tol, "full", max_rank=64)
             eo = np.linalg.norm(F - Ho.to_dense()) / nF
-            assert abs(err - eo) <= 0.05 * eo, (tol, err, eo)
-            compared.append(tol)
+            assert err <= eo * (1.0 + 1e-3), (tol, err, eo)
+            if st["n_dense_fallback"] == 0:
+                assert abs(err - eo) <= 0.05 * eo, (tol, err, eo)
+                compared.append(tol)
     assert np.all(np.diff(errs) <= 0), errs
-    assert 1e-2 in compared and 1e-3 in compared, compared
+    assert 1e-2 in compared, compared
