@@ -486,6 +486,7 @@ template <> struct Chunk<float> { static constexpr int KC = 32; };
 template <> struct Chunk<double> { static constexpr int KC = 16; };
 constexpr int kMaxCols = 96;    // right-hand sides per launch (multiple of 4)
 constexpr int kStages = 3;
+constexpr int kRPT = 8;         // panel rows per thread of the many-column GEMM (divides 64)
 
 // Copy unit of the panel operand: 16 bytes (FP32, FP64) or 8 bytes (BF16,
 // whose panel columns are only 8-byte aligned).
@@ -542,18 +543,20 @@ template <> struct Quad<double> {
     }
 };
 
-// acc(4 x 4 per thread) += A(rows x K) B(K x nc).  A: column-major panel
-// (leading dimension lda, a chunk of <= 64 rows padded to rows_pad = 4 RG);
+// acc(kRPT x 4 per thread) += A(rows x K) B(K x nc).  A: column-major
+// panel (leading dimension lda, a chunk of rows_pad <= 64 rows, rows_pad a
+// multiple of 4; rows up to the next multiple of kRPT are zero-filled);
 // B(k, :) = row bsel(k) of the vector block Bv (leading dimension ldb).
-// Thread (rg, cq) = (tid / CQ, tid % CQ) owns rows 4 rg .. 4 rg + 3 and
-// columns 4 cq .. 4 cq + 3; per k it reads one quad of A and one quad of B
-// from shared memory (lanes of a row group share the A quad) for 16 FMAs.
+// Thread (rg, cq) = (tid / CQ, tid % CQ) owns rows kRPT rg .. kRPT rg +
+// kRPT - 1 and columns 4 cq .. 4 cq + 3; per k it reads kRPT / 4 quads of A
+// and one quad of B from shared memory (lanes of a row group share the A
+// quads) for 4 kRPT FMAs.
 // Chunks of KC panel columns and the KC matching rows of B go through a
 // kStages-deep cp.async ring; B rows move as 16-byte quads when VB (rows
 // 16-byte aligned, padded to 4 CQ columns), else element by element with
 // zero fill past nc.
 template <class AS, class AT, bool VB, class BSel>
-__device__ __forceinline__ void panel_gemm(AT (&acc)[4][4], unsigned char* smem, const AS* __restrict__ A,
+__device__ __forceinline__ void panel_gemm(AT (&acc)[kRPT][4], unsigned char* smem, const AS* __restrict__ A,
                                            long long lda, int rows_pad, int K, BSel bsel,
                                            const AT* __restrict__ Bv, int ldb, int nc, int CQ) {
     using L = GemmLayout<AS, AT>;
@@ -564,10 +567,12 @@ __device__ __forceinline__ void panel_gemm(AT (&acc)[4][4], unsigned char* smem,
     if (nchunks == 0) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int rg = tid / CQ, cq = tid - rg * CQ;
-    const bool active = rg < rows_pad / 4;
+    const int rows_up = (rows_pad + kRPT - 1) / kRPT * kRPT;
+    const bool active = rg < rows_up / kRPT;
     const int BS = 4 * CQ;                               // B row stride in shared memory
     const size_t stage = L::stage(CQ);
-    const int upc = rows_pad / EPU;                      // A copy units per panel column
+    const int upc = rows_up / EPU;                       // A copy units per panel column
+    const int upv = rows_pad / EPU;                      // ... of which hold panel rows
     auto issue = [&](int ch) {
         unsigned char* st = smem + (size_t)(ch % kStages) * stage;
         AS* As = reinterpret_cast<AS*>(st);
@@ -575,7 +580,7 @@ __device__ __forceinline__ void panel_gemm(AT (&acc)[4][4], unsigned char* smem,
         const int k0 = ch * KC;
         for (int u = tid; u < KC * upc; u += nt) {
             const int kk = u / upc, w = u - kk * upc;
-            const bool ok = k0 + kk < K;
+            const bool ok = k0 + kk < K && w < upv;
             const AS* src = ok ? A + (long long)(k0 + kk) * lda + w * EPU : A;
             cp_async_n<AU>(As + kk * kTileRows + w * EPU, src, ok);
         }
@@ -611,11 +616,12 @@ __device__ __forceinline__ void panel_gemm(AT (&acc)[4][4], unsigned char* smem,
             // chunk entries past K were filled with zeros
 #pragma unroll 8
             for (int kk = 0; kk < KC; ++kk) {
-                AT a[4], b[4];
-                Vec4<AS, AT>::load(As + kk * kTileRows + rg * 4, a);
+                AT a[kRPT], b[4];
+#pragma unroll
+                for (int h = 0; h < kRPT / 4; ++h) Vec4<AS, AT>::load(As + kk * kTileRows + rg * kRPT + 4 * h, a + 4 * h);
                 Quad<AT>::load(Bs + kk * BS + 4 * cq, b);
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < kRPT; ++r)
 #pragma unroll
                     for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
             }
@@ -641,13 +647,13 @@ far_vt_multi(OpView op, const AT* __restrict__ X, int ldx, AT* __restrict__ T, i
     const GWork w = op.gwork[blockIdx.x];
     const Group gr = op.groups[w.g];
     const int rows_pad = (w.rows + 3) / 4 * 4;
-    AT acc[4][4] = {};
+    AT acc[kRPT][4] = {};
     panel_gemm<FS, AT, VB>(acc, dsm, static_cast<const FS*>(op.far_pool) + gr.voff + w.r0, gr.ld, rows_pad, gr.n,
                            AffineRows{gr.c0}, X, ldx, nc, CQ);
     const int rg = threadIdx.x / CQ, cq = threadIdx.x - rg * CQ;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int row = rg * 4 + r;
+    for (int r = 0; r < kRPT; ++r) {
+        const int row = rg * kRPT + r;
         if (row >= w.rows) continue;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -663,7 +669,7 @@ rows_multi(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ 
            int CQ, Epi epi) {
     extern __shared__ __align__(128) unsigned char dsm[];
     const Tile t = op.tiles[op.torder[blockIdx.x]];
-    AT acc[4][4] = {};
+    AT acc[kRPT][4] = {};
     panel_gemm<NS, AT, VB>(acc, dsm, static_cast<const NS*>(op.near_pool) + t.noff, t.ld, t.ld, t.kn,
                            IndexRows{op.xidx + t.ixn}, X, ldx, nc, CQ);
     // T rows are always padded to a multiple of 4 columns and 16-byte aligned
@@ -671,8 +677,8 @@ rows_multi(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ 
                                                        t.ld, t.kf, IndexRows{op.tidx + t.ixf}, T, ldt, nc, CQ);
     const int rg = threadIdx.x / CQ, cq = threadIdx.x - rg * CQ;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int row = rg * 4 + r;
+    for (int r = 0; r < kRPT; ++r) {
+        const int row = rg * kRPT + r;
         if (row >= t.rows) continue;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -682,9 +688,9 @@ rows_multi(OpView op, const AT* __restrict__ X, int ldx, const AT* __restrict__ 
     }
 }
 
-// Threads of the panel GEMM for nc columns: 16 row groups x ceil(nc / 4)
-// column quads, rounded up to whole warps.
-inline int gemm_threads(int cq) { return (16 * cq + 31) / 32 * 32; }
+// Threads of the panel GEMM for nc columns: 64 / kRPT row groups x
+// ceil(nc / 4) column quads, rounded up to whole warps.
+inline int gemm_threads(int cq) { return (64 / kRPT * cq + 31) / 32 * 32; }
 
 template <class FS, class AT, bool VB>
 void launch_far_vt(const OpView& op, const AT* X, int ldx, AT* T, int ldt, int nc, cudaStream_t s) {
