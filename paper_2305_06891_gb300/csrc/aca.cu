@@ -1294,7 +1294,7 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     long long ou = 0, ov = 0, oused = 0;
     {
         const int64_t na = (int64_t)adm.size();
-        const int P = na >= 50000 ? 16 : 1;
+        const int P = na >= 8000 ? 16 : 1;
         std::vector<long long> su(P + 1, 0), sv(P + 1, 0), ss(P + 1, 0);
         auto kmax_of = [&](int m, int n) {
             const long long brk = (long long)m * n / (m + n);
@@ -1436,7 +1436,7 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     int64_t fallback = 0;
     // row ranges of the parallel plan (below): cut at tile starts
     const int nb = (int)h->blocks.size();
-    const int parts = nb >= 100000 ? 16 : nb >= 20000 ? 8 : 1;
+    const int parts = nb >= 20000 ? 16 : nb >= 8000 ? 8 : 1;
     std::vector<int> cut(parts + 1, 0);
     cut[parts] = (int)h->n;
     for (int q = 1; q < parts; ++q) {
@@ -1492,7 +1492,7 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     }
     h->sum_rank = toff;
     // Per-tile panel columns, gather runs and fill work.  Large plans are
-    // split into row ranges (8 from 20,000 blocks, 16 from 100,000) cut at
+    // split into row ranges (8 from 8,000 blocks, 16 from 20,000) cut at
     // tile starts and built by threads (each range owns its tiles); the
     // pieces of blocks whose rows cross a cut come first in each range.
     // The layout is deterministic for a given block list (the part count
@@ -1580,7 +1580,7 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
         near_runs.resize(onr[np]); far_runs.resize(ofr[np]);
         h->near_pieces.resize(opn[np]);
         h->far_pieces.resize(opf[np]);
-        const bool par = nb >= 100000;
+        const bool par = nb >= 8000;
         parallel_parts(par ? np : 1, [&](int q0) {
             for (int q = (par ? q0 : 0); q < (par ? q0 + 1 : np); ++q) {
                 const PlanPart& o = pp[q];

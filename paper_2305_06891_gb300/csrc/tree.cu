@@ -525,7 +525,7 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
 
     HostScope hs_sort("host_block_list");
     // Blocks ordered by (row start, column start), which identifies a block
-    // uniquely.  Lists of 100,000 blocks or more: the pairs are bucketed by
+    // uniquely.  Lists of 8,000 blocks or more: the pairs are bucketed by
     // row range (counts per input chunk and range, then a scatter) and each
     // range is ordered by row start (counting) and, within a row start, by
     // column start, on kListParts host threads; the order does not depend on
@@ -535,7 +535,7 @@ void build_trees(rad_htree* h, const double* geo_user, cudaStream_t s) {
     RAD_REQUIRE(nb < INT32_MAX, RAD_ELIMIT, "too many blocks");
     auto pair_at = [&](int64_t i) { return i < nfp ? far_pairs[i] : near_pairs[i - nfp]; };
     constexpr int kListParts = 16;
-    if (nb < 100000) {
+    if (nb < 8000) {
         // small lists: build in input order, then two stable counting
         // passes (column start, then row start) over the block array
         blocks.clear();
