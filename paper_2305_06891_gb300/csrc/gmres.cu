@@ -148,23 +148,27 @@ __global__ void col_scale_kernel(int nvc, const double* __restrict__ ss, const i
 }
 
 // out[l * nvc + vc] = sum over the chunks of vc's segment of
-// partial[l][c][chunk]: one warp per output, lanes take chunks lane,
-// lane + 32, ..., then a fixed butterfly (the same summation order on every
-// call).  Chunks never straddle segments.
-__global__ void reduce_chunks_kernel(const double* __restrict__ partial, const int* __restrict__ seg_chunk0, int L,
-                                     int nc, int nvc, int nchunks, double* out) {
-    const int e = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (e >= L * nvc) return;
+// partial[l][c][chunk]: one 128-thread CTA per output; thread t adds chunks
+// k0 + t, k0 + t + 128, ... in order, then a fixed butterfly per warp and
+// the four warp sums in order (the same summation order on every call).
+// Chunks never straddle segments.
+__global__ void __launch_bounds__(128)
+reduce_chunks_kernel(const double* __restrict__ partial, const int* __restrict__ seg_chunk0, int L, int nc,
+                     int nvc, int nchunks, double* out) {
+    __shared__ double wsum[4];
+    const int e = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int l = e / nvc, vc = e - l * nvc;
     const int sg = vc / nc, c = vc - sg * nc;
     const int k0 = seg_chunk0[sg], k1 = seg_chunk0[sg + 1];
-    double s = 0.0;
     const double* pc = partial + ((long long)l * nc + c) * nchunks;
-    for (int k = k0 + lane; k < k1; k += 32) s += pc[k];
+    double s = 0.0;
+    for (int k = k0 + (int)threadIdx.x; k < k1; k += 128) s += pc[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[e] = s;
+    if (lane == 0) wsum[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) out[e] = (wsum[0] + wsum[1]) + (wsum[2] + wsum[3]);
 }
 
 __global__ void add_kernel(double* __restrict__ a, const double* __restrict__ b, long long cnt) {
@@ -374,7 +378,7 @@ struct ColReducer {
             mdot_wide_kernel<<<dim3(nchunks, (nc + 31) / 32), 256, 0, s>>>(A, strideA, L, Bv, chunk, nc, partial);
         }
         RAD_CHECK_LAUNCH();
-        { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<grid_for((long long)L * nvc, 8), 256, 0, s>>>(partial, seg_chunk0, L, nc, nvc,
+        { ProfScope ps_("gmres_dots", s); reduce_chunks_kernel<<<(unsigned)(L * nvc), 128, 0, s>>>(partial, seg_chunk0, L, nc, nvc,
                                                                           nchunks, out); }
         RAD_CHECK_LAUNCH();
     }
