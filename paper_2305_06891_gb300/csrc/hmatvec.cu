@@ -573,6 +573,21 @@ __device__ __forceinline__ void panel_gemm(AT (&acc)[kRPT][4], unsigned char* sm
     const size_t stage = L::stage(CQ);
     const int upc = rows_up / EPU;                       // A copy units per panel column
     const int upv = rows_pad / EPU;                      // ... of which hold panel rows
+    // gathered B rows of this thread's copy units of the next chunk to
+    // issue, loaded one chunk ahead so that the index loads do not stall
+    // the copies (16-byte B rows only; at most KC kRPT / 64 units a thread)
+    constexpr int kBU = (KC * kRPT + 63) / 64;
+    int brow[kBU];
+    auto load_rows = [&](int ch) {
+        if constexpr (VB) {
+            const int k0 = ch * KC;
+#pragma unroll
+            for (int i = 0; i < kBU; ++i) {
+                const int u = tid + i * nt, kk = u / CQ;
+                brow[i] = (u < KC * CQ && k0 + kk < K) ? bsel(k0 + kk) : 0;
+            }
+        }
+    };
     auto issue = [&](int ch) {
         unsigned char* st = smem + (size_t)(ch % kStages) * stage;
         AS* As = reinterpret_cast<AS*>(st);
@@ -585,10 +600,13 @@ __device__ __forceinline__ void panel_gemm(AT (&acc)[kRPT][4], unsigned char* sm
             cp_async_n<AU>(As + kk * kTileRows + w * EPU, src, ok);
         }
         if constexpr (VB) {
-            for (int u = tid; u < KC * CQ; u += nt) {
+#pragma unroll
+            for (int i = 0; i < kBU; ++i) {
+                const int u = tid + i * nt;
+                if (u >= KC * CQ) break;
                 const int kk = u / CQ, q = u - kk * CQ;
                 const bool ok = k0 + kk < K;
-                const AT* src = ok ? Bv + (long long)bsel(k0 + kk) * ldb + 4 * q : Bv;
+                const AT* src = ok ? Bv + (long long)brow[i] * ldb + 4 * q : Bv;
                 cp_async_16(Bs + kk * BS + 4 * q, src, ok);
             }
         } else {
@@ -601,14 +619,21 @@ __device__ __forceinline__ void panel_gemm(AT (&acc)[kRPT][4], unsigned char* sm
         }
         cp_async_commit();
     };
+    load_rows(0);
     issue(0);
+    load_rows(1);
     if (nchunks > 1) issue(1);
     else cp_async_commit();
+    load_rows(2);
     for (int ch = 0; ch < nchunks; ++ch) {
         cp_async_wait<kStages - 2>();
         __syncthreads();
-        if (ch + 2 < nchunks) issue(ch + 2);
-        else cp_async_commit();
+        if (ch + 2 < nchunks) {
+            issue(ch + 2);
+            load_rows(ch + 3);
+        } else {
+            cp_async_commit();
+        }
         if (active) {
             const unsigned char* st = smem + (size_t)(ch % kStages) * stage;
             const AS* As = reinterpret_cast<const AS*>(st);
