@@ -302,11 +302,17 @@ def run_ours(args, rank: int, world: int, profile_steps: int | None = None, e2e:
     prof, prof_times = {}, []
     if rank == 0:
         k = profile_steps or min(args.steps, 5)
-        rad.rad_profile_enable(True)
-        prof_times, _ = timed_steps(step, k, stream, flush)
-        torch.cuda.synchronize()
-        prof = rad.rad_profile_read()
-        rad.rad_profile_enable(False)
+        # a pass that ran far slower than the timed steps (a disturbance of
+        # the GPU or the host while it ran) is taken again, once: its per-kernel
+        # table is what the roofline and the kernel shares are read from
+        for attempt in range(2):
+            rad.rad_profile_enable(True)
+            prof_times, _ = timed_steps(step, k, stream, flush)
+            torch.cuda.synchronize()
+            prof = rad.rad_profile_read()
+            rad.rad_profile_enable(False)
+            if statistics.median(prof_times) <= 1.5 * statistics.median(times):
+                break
     extra = {}
     if rank == 0:
         extra = measure_extras(args, rad, torch, dev, cav, verts_d, flush, stream, e2e=e2e)
