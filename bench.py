@@ -428,7 +428,7 @@ def measure_extras(args, rad, torch, dev, cav, verts_d, flush, stream, e2e=True)
 # DRAM bytes (read + write) per launch of a workload's dominant kernel, from
 # the ncu capture summarised in profiles/ (kept only while the kernel is
 # unchanged since that capture).
-TRAFFIC = {("cylinder", "hmm_rows"): 284.72e6 + 6.27e6}
+TRAFFIC = {("cylinder", "hmm_rows"): 282.92e6 + 3.33e6}
 
 
 def roofline(prof: dict, st: dict, steps: int, nc: int, sms: int):
