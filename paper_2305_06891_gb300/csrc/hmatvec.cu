@@ -573,19 +573,30 @@ __device__ __forceinline__ void panel_gemm(AT (&acc)[kRPT][4], unsigned char* sm
     const size_t stage = L::stage(CQ);
     const int upc = rows_up / EPU;                       // A copy units per panel column
     const int upv = rows_pad / EPU;                      // ... of which hold panel rows
+    // A thread's copy units are the same in every chunk: unit u = tid + i nt
+    // is panel column u / upc, piece u % upc of the A chunk, and row u / CQ,
+    // quad u % CQ of the B chunk.  The divisions are done once here; the
+    // chunk loop only steps through them.
+    const int a_k0 = tid / upc, a_w0 = tid - a_k0 * upc;
+    const int a_dk = nt / upc, a_dw = nt - a_dk * upc;
+    const int a_units = KC * upc;
     // gathered B rows of this thread's copy units of the next chunk to
     // issue, loaded one chunk ahead so that the index loads do not stall
     // the copies (16-byte B rows only; at most KC kRPT / 64 units a thread)
     constexpr int kBU = (KC * kRPT + 63) / 64;
     int brow[kBU];
+    int bkk[kBU], bq[kBU];
+#pragma unroll
+    for (int i = 0; i < kBU; ++i) {
+        const int u = tid + i * nt;
+        bkk[i] = u < KC * CQ ? u / CQ : KC;              // KC: no unit
+        bq[i] = u - (u / CQ) * CQ;
+    }
     auto load_rows = [&](int ch) {
         if constexpr (VB) {
             const int k0 = ch * KC;
 #pragma unroll
-            for (int i = 0; i < kBU; ++i) {
-                const int u = tid + i * nt, kk = u / CQ;
-                brow[i] = (u < KC * CQ && k0 + kk < K) ? bsel(k0 + kk) : 0;
-            }
+            for (int i = 0; i < kBU; ++i) brow[i] = (bkk[i] < KC && k0 + bkk[i] < K) ? bsel(k0 + bkk[i]) : 0;
         }
     };
     auto issue = [&](int ch) {
@@ -593,21 +604,25 @@ __device__ __forceinline__ void panel_gemm(AT (&acc)[kRPT][4], unsigned char* sm
         AS* As = reinterpret_cast<AS*>(st);
         AT* Bs = reinterpret_cast<AT*>(st + L::a_bytes);
         const int k0 = ch * KC;
-        for (int u = tid; u < KC * upc; u += nt) {
-            const int kk = u / upc, w = u - kk * upc;
+        const AS* Ak = A + (long long)k0 * lda;
+        for (int u = tid, kk = a_k0, w = a_w0; u < a_units; u += nt) {
             const bool ok = k0 + kk < K && w < upv;
-            const AS* src = ok ? A + (long long)(k0 + kk) * lda + w * EPU : A;
+            const AS* src = ok ? Ak + (long long)kk * lda + w * EPU : A;
             cp_async_n<AU>(As + kk * kTileRows + w * EPU, src, ok);
+            kk += a_dk;
+            w += a_dw;
+            if (w >= upc) {
+                w -= upc;
+                ++kk;
+            }
         }
         if constexpr (VB) {
 #pragma unroll
             for (int i = 0; i < kBU; ++i) {
-                const int u = tid + i * nt;
-                if (u >= KC * CQ) break;
-                const int kk = u / CQ, q = u - kk * CQ;
-                const bool ok = k0 + kk < K;
-                const AT* src = ok ? Bv + (long long)brow[i] * ldb + 4 * q : Bv;
-                cp_async_16(Bs + kk * BS + 4 * q, src, ok);
+                if (bkk[i] >= KC) break;
+                const bool ok = k0 + bkk[i] < K;
+                const AT* src = ok ? Bv + (long long)brow[i] * ldb + 4 * bq[i] : Bv;
+                cp_async_16(Bs + bkk[i] * BS + 4 * bq[i], src, ok);
             }
         } else {
             for (int u = tid; u < KC * BS; u += nt) {

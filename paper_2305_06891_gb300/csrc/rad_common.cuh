@@ -403,9 +403,11 @@ struct rad_htree {
     // 1 = tensor cores (BF16 x 3 split); set by rad_htree_autotune or
     // rad_htree_set_product_path
     int mm_path = 0;
-    // tensor-core path: the three BF16 chunk images of every panel and the
-    // first chunk of every tile's dense / U panel and of every far item
-    rad::DevBuf tc_img, tc_tile_near0, tc_tile_far0, tc_item0;
+    // tensor-core path: the BF16 chunk images of every work item, the work
+    // items (row tiles, far-field slices; heaviest first) and their K-groups
+    // (source vector rows of runs of up to 8 panel columns)
+    rad::DevBuf tc_img, tc_rows_items, tc_far_items, tc_kgs;
+    int tc_n_rows = 0, tc_n_far = 0, tc_r8max = 8;   // items; their largest row count rounded up to 8
     bool tc_ready = false;
     // one-column product: 1 = the fused single launch (when the operator
     // allows it, hmv1_ok), 0 = the two launches (phase A, phase B); set by

@@ -1,45 +1,66 @@
 // Tensor-core (tcgen05) panel GEMMs of the many-column product, FP32
 // operands at FP32-level accuracy.
 //
-// A panel times gathered vector rows, D[64 x N] += A[64 x K] B[K x N], runs
-// on the 5th-generation tensor cores (kind::f16 with BF16 operands, FP32
-// accumulators in tensor memory).  BF16 keeps 8 mantissa bits, so every
-// FP32 operand x is split into three BF16 pieces, x1 = bf16(x),
-// x2 = bf16(x - x1), x3 = bf16(x - x1 - x2), which together carry its 24
-// bits; the product takes the six terms a1 b1 (the "main" accumulator) and
-// a1 b2 + a2 b1 + a1 b3 + a2 b2 + a3 b1 (a second, "correction" accumulator),
-// dropping terms of order 2^-24 relative.  The tensor core's accumulation
-// truncates, so the accumulators start from zero every 128 panel columns
-// and are added into FP32 registers (round to nearest): the rounding stays
-// at the level of an FP32 FFMA loop (measured below it).
+// The product of one work item (a row tile, or a slice of at most 64 rows of
+// a column group's V^T panel) runs transposed on the 5th-generation tensor
+// cores: D[M x N] = sum_k A[M x k] B[k x N] with M = the right-hand-side
+// columns (64 or 128, the MMA's M), N = the item's rows (rounded up to 8 or
+// 16), K = the item's panel columns.  Column k of A is the vector row that
+// panel column k multiplies (a row of X, or of T = V^T X); B is the panel
+// transposed.  D sits in tensor memory with one lane per right-hand side, so
+// the epilogue writes every output row with consecutive lanes on consecutive
+// columns.
 //
-// The split is never done inside the kernel:
-//   - panels (dense blocks, U and V^T factors) are split once, when the path
-//     is selected, into three 64 x 32 BF16 images per chunk of 32 panel
-//     columns, laid out as the MMA reads them (K-major core matrices of
-//     8 rows x 16 bytes, no swizzle: 8-row groups 512 bytes apart, K-adjacent
-//     cores 128 bytes apart), zero-padded past the panel's rows and columns;
-//   - vector rows (X, and T = V^T X) are split once per product into three
-//     BF16 planes of N8 = 8 ceil(nc / 8) columns; a gathered row lands in
-//     shared memory by 16-byte copies as MN-major core matrices (8 columns x
-//     8 rows of 16 bytes; 8-column groups 512 bytes apart, K-adjacent cores
-//     128 bytes apart), which the MMA reads with the B-transpose bit set.
-// Persistent, warp-specialised kernel (one CTA of 256 threads per SM,
-// items taken round-robin, heaviest first): warps 0-2 copy chunks (12 KiB of
-// panel images by one bulk copy, 3 x N8 x 32 x 2 bytes of gathered vector
-// rows by 16-byte copies) into a ring of six shared-memory stages; one thread of warp 3 issues every chunk's 2
-// k-steps x 6 MMAs (M = 64, K = 16) into one of two accumulator pairs in
-// tensor memory; warps 4-7 (whose tensor-memory lane quarters hold rows
-// 16 q .. 16 q + 15 in lanes 0-15) add a pair into FP32 registers after
-// every 4 chunks of an item and write the item's rows at its end.  The roles
-// hand over through mbarriers (stage full / empty, accumulators full /
-// empty) and never wait for the whole CTA.  Every wait is bounded: after
-// a bounded number of tries a role raises an abort flag that the others see, the CTA
-// records the timeout in a device flag (checked by the host at its next
-// synchronisation) and frees its tensor memory.
+// Accuracy: kind::f16 with BF16 operands and FP32 accumulators.  BF16 keeps
+// 8 mantissa bits, so every FP32 operand x is split into three BF16 pieces,
+// x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2), which together
+// carry its 24 bits; the product takes the six terms a1 b1 (the "main"
+// accumulator) and a1 b2 + a2 b1 + a1 b3 + a2 b2 + a3 b1 (a second,
+// "correction" accumulator), dropping terms of order 2^-24 relative.  The
+// tensor core's accumulation truncates, so the accumulators start from zero
+// every 128 panel columns and are added into FP32 registers (round to
+// nearest): the rounding stays at the level of an FP32 FFMA loop.
+//
+// Data movement (no gathers by threads):
+//   - panel columns are cut into K-groups: runs of at most 8 columns whose
+//     vector rows are consecutive (a dense block's columns, a low-rank
+//     block's T rows).  Each K-group's 8 vector rows arrive by one TMA tile
+//     copy from vector planes stored group-major, [plane][column group][row]
+//     [8 columns]: 8 consecutive rows of a column group are 128 contiguous
+//     bytes, so the box (64 elements x G = ceil(columns / 8) groups x 3
+//     planes) moves whole 128-byte lines and lands as MN-major core matrices
+//     (8 rows of 16 bytes; column groups 128 bytes apart, planes 128 G bytes
+//     apart, K-groups one box apart).  The MMA reads M/8 groups per plane:
+//     those past G (the next plane's data) only reach rows of D past the
+//     last column, which are never read.
+//     Panel columns past a run's end are zero in the image, so the box's
+//     other rows (neighbouring vector rows, or the zeros the copy fills in
+//     past the last row or column group) add nothing;
+//   - the panels are split once, when the path is selected, into chunk
+//     images of 8 K-groups, [plane][K-group][8-row group][8 rows][8 columns]
+//     (K-major core matrices), rows padded with zeros to a multiple of 8; a
+//     chunk moves by one bulk copy.
+// Persistent, warp-specialised kernel (one CTA of 192 threads per SM, items
+// taken round-robin, heaviest first): lane 0 of warp 0 issues the copies of
+// every chunk (8 tensor copies and one bulk copy, completing on the stage's
+// "full" mbarrier) into a ring of shared-memory stages, with the K-group
+// rows of the next 32 to 64 chunks already in the warp's registers; lane 0 of warp 1
+// issues each chunk's 4 k-steps x 6 MMAs into one of four accumulator pairs
+// in tensor memory (so that it runs up to three drains ahead); warps 2-5 (tensor-memory lane quarters 2, 3, 0, 1) add
+// a pair into FP32 registers after every 2 chunks of an item and write the
+// item's rows at its end.  The roles hand over through mbarriers and never
+// wait for the whole CTA.  Every wait is bounded: after a bounded number of
+// tries a role raises an abort flag that the others see, the CTA records the
+// timeout in a device flag (checked by the host at its next
+// synchronisation), waits (bounded) for its own copies and MMAs in flight
+// and frees its tensor memory.
 
 #include <cstdint>
 #include <mutex>
+#include <algorithm>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "rad_device.cuh"
 
@@ -49,12 +70,33 @@ __device__ int g_tc_timeout = 0;
 
 namespace {
 
-constexpr int kKC = 32;                          // panel columns per chunk
-constexpr int kImg = kTileRows * kKC * 2;        // one BF16 image of a chunk: 4 KiB
-constexpr int kChunkBytes = 3 * kImg;            // the three split images
-constexpr int kGrp = (kKC / 8) * 128;            // 512: 8-row / 8-column group stride
-constexpr uint32_t kCorrCol = 128;               // correction accumulator: 128 columns after the main one
-constexpr int kMaxN8 = 96;
+constexpr int kKG = 8;                        // panel columns per K-group
+constexpr int kGPC = 8;                       // K-groups per chunk (four MMA k-steps)
+constexpr int kMaxN = kTileRows;              // rows of an item
+constexpr int kDrain = 128 / (kGPC * kKG);    // chunks accumulated in tensor memory between drains (128 columns)
+constexpr int kAccBufs = 4;                   // accumulator pairs in tensor memory (MMA runs up to 3 drains ahead)
+constexpr uint32_t kTmemCols = 128 * kAccBufs; // each pair: main and correction, <= 64 columns each
+constexpr int kThreads = 192;
+constexpr int kTFlag = 1 << 30;               // K-group source: a row of T (else of X)
+
+// a K-group's box: 3 planes x G column groups of 8 rows x 16 bytes
+__host__ __device__ constexpr int box_bytes(int G) { return 3 * G * 128; }
+__host__ __device__ constexpr int chunk_img_bytes(int rows8) { return 3 * kGPC * rows8 * kKG * 2; }
+// A stage: the 4 boxes, then one chunk image of the launch's tallest item
+// (r8max rows) and 128 bytes that the MMA may read past an image (N rounded
+// up to 16), in 1 KiB units; as many stages as fit in kRingBytes.  The MMA
+// reads M / 8 column groups of each plane, past the boxes' G when M > 8 G:
+// at most 16 M - 128 G bytes past the boxes, inside the image region
+// (16 M <= 128 G + 1536 for every M, G the launch can have).
+constexpr int kMaxStages = 12;
+constexpr int kRingBytes = 220 * 1024;
+constexpr size_t kSmemBytes = (size_t)kRingBytes + 1024;
+__host__ __device__ constexpr int stage_bytes(int G, int r8max) {
+    return (kGPC * box_bytes(G) + chunk_img_bytes(r8max) + 128 + 1023) / 1024 * 1024;
+}
+__host__ __device__ constexpr int ring_stages(int G, int r8max) {
+    return kRingBytes / stage_bytes(G, r8max) < kMaxStages ? kRingBytes / stage_bytes(G, r8max) : kMaxStages;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -88,40 +130,49 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16&
 }
 
 // ---------------------------------------------------------------- packing
-// One chunk of a panel: rows [0, rows) and columns [k0, k0 + 32) of the
-// column-major panel at pool + src (leading dimension ld, K columns in all).
-struct PackJob {
-    long long src;
-    int ld, rows, k0, K;
-    long long chunk;
+// One K-group of an item's panel: columns [0, valid) of the column-major
+// panel at pool + off (leading dimension ld, rows rows), into slot `slot`
+// of the chunk image at img + dst (rows padded to rows8).
+struct KgJob {
+    long long off, dst;
+    int ld, rows, valid, slot, rows8, pool;   // pool: 0 dense panels, 1 factor panels
 };
 template <class FS>
-__global__ void __launch_bounds__(256) tc_pack_kernel(const FS* __restrict__ pool, const PackJob* __restrict__ jobs,
-                                                      unsigned char* __restrict__ img) {
-    const PackJob j = jobs[blockIdx.x];
-    unsigned char* dst = img + j.chunk * kChunkBytes;
-    for (int e = threadIdx.x; e < kTileRows * kKC; e += blockDim.x) {
-        const int m = e % kTileRows, k = e / kTileRows;
+__global__ void __launch_bounds__(256) tc_pack_kernel(const float* __restrict__ near_pool,
+                                                      const FS* __restrict__ far_pool,
+                                                      const KgJob* __restrict__ jobs, unsigned char* __restrict__ img) {
+    const KgJob j = jobs[blockIdx.x];
+    __nv_bfloat16* c = reinterpret_cast<__nv_bfloat16*>(img + j.dst);
+    const long long pstride = (long long)kGPC * j.rows8 * kKG;    // elements of one plane of the chunk
+    for (int e = threadIdx.x; e < j.rows8 * kKG; e += blockDim.x) {
+        const int n = e % j.rows8, kk = e / j.rows8;
         float x = 0.0f;
-        if (m < j.rows && j.k0 + k < j.K) x = (float)Store<FS>::get(pool[j.src + m + (long long)(j.k0 + k) * j.ld]);
-        __nv_bfloat16 a, b, c;
-        split3(x, a, b, c);
-        const int off = (m >> 3) * kGrp + (k >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2;
-        *reinterpret_cast<__nv_bfloat16*>(dst + off) = a;
-        *reinterpret_cast<__nv_bfloat16*>(dst + kImg + off) = b;
-        *reinterpret_cast<__nv_bfloat16*>(dst + 2 * kImg + off) = c;
+        if (n < j.rows && kk < j.valid) {
+            const long long at = j.off + n + (long long)kk * j.ld;
+            x = j.pool ? (float)Store<FS>::get(far_pool[at]) : near_pool[at];
+        }
+        __nv_bfloat16 a, b, d;
+        split3(x, a, b, d);
+        const long long o = (long long)j.slot * j.rows8 * kKG + (n >> 3) * 64 + (n & 7) * 8 + kk;
+        c[o] = a;
+        c[pstride + o] = b;
+        c[2 * pstride + o] = d;
     }
 }
 
-// vector rows -> three BF16 planes of N8 columns (zero past nc)
-__global__ void tc_split_rows_kernel(const float* __restrict__ X, int ldx, int rows, int nc, int N8,
-                                     __nv_bfloat16* __restrict__ P, long long plane) {
-    const long long total = (long long)rows * N8;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+// vector rows -> three BF16 planes, group-major: element (row i, column
+// 8 g + c) of plane p at ((p G + g) rows + i) 8 + c; zero past nc
+__global__ void tc_split_rows_kernel(const float* __restrict__ X, int ldx, int rows, int nc, int G,
+                                     __nv_bfloat16* __restrict__ P) {
+    const long long plane = (long long)G * rows * kKG;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < plane;
          e += (long long)gridDim.x * blockDim.x) {
-        const long long i = e / N8;
-        const int c = (int)(e - i * N8);
-        const float x = c < nc ? X[i * ldx + c] : 0.0f;
+        const int c = (int)(e & 7);
+        const long long q = e >> 3;
+        const int g = (int)(q / rows);
+        const long long i = q - (long long)g * rows;
+        const int col = 8 * g + c;
+        const float x = col < nc ? X[i * ldx + col] : 0.0f;
         __nv_bfloat16 a, b, d;
         split3(x, a, b, d);
         P[e] = a;
@@ -131,71 +182,16 @@ __global__ void tc_split_rows_kernel(const float* __restrict__ X, int ldx, int r
 }
 
 // ---------------------------------------------------------------- GEMM
-__device__ __forceinline__ void cp16(void* sdst, const void* gsrc, bool pred) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(sdst)), "l"(gsrc),
-                 "r"(pred ? 16 : 0));
-}
-
-// One K segment of a work item: nch chunk images from img, and the vector
-// rows idx[k] (or base + k) of three BF16 planes (plane elements apart, N8
-// columns) for k < K.
-struct Seg {
-    const unsigned char* img;
-    int nch, K;
-    const __nv_bfloat16* B;
-    long long plane;
-    const int* idx;
-    int base;
+// A work item: its image chunks from byte img, its K-groups kgs[kg0 ..
+// kg0 + nkg) (nkg a multiple of kGPC), its rows and first output row (the Y
+// row of a tile, the T row of a far-field slice).
+struct TcItem {
+    long long img;
+    int kg0, nkg, rows, orow, pad[2];
 };
 
-__host__ __device__ constexpr int b_plane_bytes(int N8) { return (N8 / 8) * kGrp; }
-__host__ __device__ constexpr int stage_bytes(int N8) { return kChunkBytes + 3 * b_plane_bytes(N8); }
-
-constexpr int kProducers = 96;     // warps 0-2 copy chunks into the stage ring
-constexpr int kMmaWarp = 3;        // lane 0 issues the MMAs
-constexpr int kDrainers = 128;     // warps 4-7 read the accumulators (lane quarters 0-3)
-constexpr int kDrain = 4;          // chunks accumulated in tensor memory between drains
-constexpr int kRingStages = 6;     // chunks in flight
-constexpr int kMaxBlkAll = kMaxN8 / 8;
-
-// chunk c of a segment into a stage, by producer thread pt (0 .. 95): the
-// three panel images (12 KiB, contiguous) by one bulk copy that completes
-// on the stage's "full" mbarrier, the gathered vector rows by 16-byte
-// copies
-__device__ __forceinline__ void issue_chunk(const Seg& sg, int c, int N8, unsigned char* st, int pt, uint32_t full) {
-    if (pt == 0) {
-        const unsigned char* a = sg.img + (size_t)c * kChunkBytes;
-        asm volatile("{\n\t.reg .b64 tk;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 tk, [%0], %1;\n\t}\n" ::"r"(full),
-                     "r"(kChunkBytes)
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                smem_u32(st)),
-            "l"(a), "r"(kChunkBytes), "r"(full)
-            : "memory");
-    }
-    // warp w copies plane w: the chunk's 32 row indices are read once per
-    // warp (one coalesced load, lane k holding row k) and handed out by
-    // shuffles, so the copies do not wait on dependent index loads
-    unsigned char* b = st + kChunkBytes + (pt >> 5) * b_plane_bytes(N8);
-    const int lane = pt & 31, q = pt >> 5;
-    const int nj = N8 / 8;
-    const int k0 = c * kKC;
-    const bool okl = k0 + lane < sg.K;
-    const int myrow = okl ? (sg.idx ? sg.idx[k0 + lane] : sg.base + k0 + lane) : 0;
-    const __nv_bfloat16* plane = sg.B + q * sg.plane;
-    for (int it = 0; it < nj; ++it) {
-        const int r = it * 32 + lane;               // copy r of this plane: row k, 16-byte piece j
-        const int k = r / nj, j = r - k * nj;
-        const int row = __shfl_sync(0xffffffffu, myrow, k);
-        const bool ok = k0 + k < sg.K;
-        const __nv_bfloat16* src = ok ? plane + (long long)row * N8 + 8 * j : sg.B;
-        cp16(b + j * kGrp + (k >> 3) * 128 + (k & 7) * 16, src, ok);
-    }
-}
-
 struct TcShared {
-    unsigned long long full[kRingStages], empty[kRingStages], accf[2], acce[2];
+    unsigned long long full[kMaxStages], empty[kMaxStages], accf[kAccBufs], acce[kAccBufs];
     uint32_t tmem;
     int abort;
 };
@@ -209,7 +205,7 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
 }
 // blocking test of an mbarrier phase: the thread may be suspended in hardware
 // for up to about 1 microsecond (the hint, in nanoseconds) instead of
-// spinning, which keeps shared memory free for the copies being waited for
+// spinning
 constexpr long kTryLimit = 1l << 22;   // tries (each returns within about a microsecond)
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
@@ -232,35 +228,13 @@ __device__ __forceinline__ bool role_wait(unsigned long long* b, uint32_t parity
     atomicExch((int*)abort, 1);
     return false;
 }
-
-// The work items of one launch: tiles (rows) or far-field items (far_vt).
-struct Items {
-    bool rows;
-    OpView op;
-    const long long* first;    // rows: tile_near0; far_vt: item0
-    const long long* first2;   // rows: tile_far0
-    const unsigned char* img;
-    const __nv_bfloat16 *Xs, *Ts;
-    long long xplane, tplane;
-    __device__ __forceinline__ int count() const { return rows ? op.n_tiles : op.n_gwork; }
-    // the two segments of item i (the second is empty for far-field items)
-    __device__ __forceinline__ void segs(int i, Seg& s0, Seg& s1) const {
-        if (rows) {
-            const int ti = op.torder[i];
-            const Tile t = op.tiles[ti];
-            s0 = Seg{img + first[ti] * (long long)kChunkBytes, (t.kn + kKC - 1) / kKC, t.kn, Xs, xplane,
-                     op.xidx + t.ixn, 0};
-            s1 = Seg{img + first2[ti] * (long long)kChunkBytes, (t.kf + kKC - 1) / kKC, t.kf, Ts, tplane,
-                     op.tidx + t.ixf, 0};
-        } else {
-            const GWork w = op.gwork[i];
-            const Group gr = op.groups[w.g];
-            s0 = Seg{img + first[i] * (long long)kChunkBytes, (gr.n + kKC - 1) / kKC, gr.n, Xs, xplane, nullptr,
-                     gr.c0};
-            s1 = Seg{nullptr, 0, 0, nullptr, 0, nullptr, 0};
-        }
-    }
-};
+// bounded wait for a phase that completes whatever the other roles do (own
+// copies or MMAs in flight), used on the way out
+__device__ __forceinline__ void drain_wait(unsigned long long* b, uint32_t parity) {
+    const uint32_t a = bar_addr(b);
+    for (long it = 0; it < 4096; ++it)
+        if (mbar_try_wait(a, parity)) return;
+}
 
 __device__ __forceinline__ void epilogue_tc(const Epi& epi, void* Y, int ldy, int row, int col, float acc) {
     if (epi.mode == kStore) {
@@ -273,36 +247,55 @@ __device__ __forceinline__ void epilogue_tc(const Epi& epi, void* Y, int ldy, in
     }
 }
 
-// Persistent, warp-specialised panel GEMM: CTA b takes items b, b + grid,
-// ... (heaviest first).  Producers fill a ring of kRingStages chunk stages
-// (cp.async, arriving on the stage's "full" mbarrier when the copies land);
-// the MMA thread waits "full", issues the chunk's 12 MMAs into one of two
-// tensor-memory accumulator pairs and commits them to the stage's "empty"
-// mbarrier (the producers' licence to refill it); after every kDrain chunks
-// of an item (and at its end) it commits the pair to "acc full"; the
-// drainers add the pair to FP32 registers, release it ("acc empty") and,
-// at the end of an item, write its rows.
-__global__ void __launch_bounds__(256, 1) tc_gemm_kernel(Items it, int nc, int N8, void* Y, int ldy, Epi epi,
-                                                          __nv_bfloat16* Tout, long long tplane_out) {
-    extern __shared__ __align__(1024) unsigned char dsm[];
+// the box of vector rows row .. row + 7: inner coordinate 8 row (elements;
+// a multiple of 16 bytes), all column groups and planes
+__device__ __forceinline__ void tma_box(unsigned char* dst, const CUtensorMap* tm, int row, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(kKG * row), "r"(0), "r"(0), "r"(bar)
+        : "memory");
+}
+
+// Output of a launch: rows mode writes Y through the epilogue; far mode
+// writes the three BF16 planes of T (group-major, G column groups, nT rows).
+struct TcOut {
+    void* Y;
+    int ldy;
+    Epi epi;
+    __nv_bfloat16* T;
+    int G;
+    long long nT;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmt,
+               const TcItem* __restrict__ items, int n_items, const int* __restrict__ kgs,
+               const unsigned char* __restrict__ img, int M, int nc, int r8max, int rows_mode, TcOut out) {
+    extern __shared__ __align__(1024) unsigned char dsm_raw[];
     __shared__ TcShared sh;
+    unsigned char* dsm = dsm_raw + ((1024u - (smem_u32(dsm_raw) & 1023u)) & 1023u);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int sb = stage_bytes(N8);
+    // boxes hold the G = ceil(nc / 8) column groups that carry data; the MMA
+    // reads M / 8 groups per plane, the others (neighbouring data) only
+    // reach rows of D past nc, which are never read
+    const int G = (nc + 7) >> 3;
+    const int S = ring_stages(G, r8max), sb = stage_bytes(G, r8max), bb = box_bytes(G);
     if (tid == 0) {
-        for (int i = 0; i < kRingStages; ++i) {
-            mbar_init(&sh.full[i], kProducers + 1);   // 96 copy arrivals + the bulk copy's expect_tx
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&sh.full[i], 1);     // the producer's arrival with the expected bytes
             mbar_init(&sh.empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kAccBufs; ++i) {
             mbar_init(&sh.accf[i], 1);
-            mbar_init(&sh.acce[i], kDrainers);
+            mbar_init(&sh.acce[i], 128);
         }
         sh.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh.tmem)),
-                     "r"(512));
+                     "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -310,143 +303,218 @@ __global__ void __launch_bounds__(256, 1) tc_gemm_kernel(Items it, int nc, int N
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = sh.tmem;
     volatile int* abort = &sh.abort;
-    const int n_items = it.count();
 
-    if (warp < kProducers / 32) {
-        // ------------------------------------------------ producers
-        int g = 0;   // global chunk counter of this CTA
-        for (int i = blockIdx.x; i < n_items && !*abort; i += gridDim.x) {
-            Seg s0, s1;
-            it.segs(i, s0, s1);
-            const int nch = s0.nch + s1.nch;
-            for (int c = 0; c < nch; ++c, ++g) {
-                const int st = g % kRingStages, use = g / kRingStages;
-                if (use > 0) {
-                    // warp-uniform outcome: the copies below shuffle across the warp
-                    const bool w = __all_sync(0xffffffffu, role_wait(&sh.empty[st], (uint32_t)((use - 1) & 1), abort));
-                    if (!w) break;
+    if (warp == 0) {
+        // ------------------------------------------------ producer
+        // lane 0 issues the copies; the warp loads the K-group rows of the
+        // item's chunks 32 at a time, one batch of 32 ahead (lane j holds
+        // chunk j's four rows), so that no copy waits on an index load
+        int g = 0, pst = 0;          // chunks issued; stage of the next one
+        uint32_t pph = 0;            // its use of the stage, mod 2
+        bool ok = true;
+        const int4 z4 = make_int4(0, 0, 0, 0);
+        for (int i = blockIdx.x; i < n_items && ok; i += gridDim.x) {
+            const TcItem itm = items[i];
+            const int rows8 = (itm.rows + 7) & ~7;
+            const int cb = chunk_img_bytes(rows8);
+            const int nch = itm.nkg / kGPC;
+            const unsigned char* src = img + itm.img;
+            constexpr int Q = kGPC / 4;                  // int4 of K-group rows per chunk
+            const int4* kq = reinterpret_cast<const int4*>(kgs + itm.kg0);
+            int4 cur[Q], nxt[Q];
+#pragma unroll
+            for (int h = 0; h < Q; ++h) {
+                cur[h] = lane < nch ? kq[Q * lane + h] : z4;
+                nxt[h] = 32 + lane < nch ? kq[Q * (32 + lane) + h] : z4;
+            }
+            for (int c = 0; c < nch; ++c) {
+                const int j = c & 31;
+                if (j == 0 && c > 0) {
+#pragma unroll
+                    for (int h = 0; h < Q; ++h) {
+                        cur[h] = nxt[h];
+                        nxt[h] = c + 32 + lane < nch ? kq[Q * (c + 32 + lane) + h] : z4;
+                    }
                 }
-                unsigned char* stage = dsm + (size_t)st * sb;
-                const uint32_t fb = bar_addr(&sh.full[st]);
-                if (c < s0.nch) issue_chunk(s0, c, N8, stage, tid, fb);
-                else issue_chunk(s1, c - s0.nch, N8, stage, tid, fb);
-                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar_addr(&sh.full[st]))
-                             : "memory");
+                int r4[kGPC];
+#pragma unroll
+                for (int h = 0; h < Q; ++h) {
+                    r4[4 * h] = __shfl_sync(0xffffffffu, cur[h].x, j);
+                    r4[4 * h + 1] = __shfl_sync(0xffffffffu, cur[h].y, j);
+                    r4[4 * h + 2] = __shfl_sync(0xffffffffu, cur[h].z, j);
+                    r4[4 * h + 3] = __shfl_sync(0xffffffffu, cur[h].w, j);
+                }
+                if (lane == 0) {
+                    if (g >= S && !role_wait(&sh.empty[pst], pph ^ 1u, abort)) {
+                        ok = false;
+                    } else {
+                        unsigned char* stage = dsm + (size_t)pst * sb;
+                        const uint32_t fb = bar_addr(&sh.full[pst]);
+                        asm volatile(
+                            "{\n\t.reg .b64 tk;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 tk, [%0], %1;\n\t}\n" ::"r"(fb),
+                            "r"(kGPC * bb + cb)
+                            : "memory");
+#pragma unroll
+                        for (int q = 0; q < kGPC; ++q)
+                            tma_box(stage + q * bb, (r4[q] & kTFlag) ? &tmt : &tmx, r4[q] & (kTFlag - 1), fb);
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                                smem_u32(stage + kGPC * bb)),
+                            "l"(src + (size_t)c * cb), "r"(cb), "r"(fb)
+                            : "memory");
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) break;
+                ++g;
+                if (++pst == S) {
+                    pst = 0;
+                    pph ^= 1u;
+                }
             }
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-    } else if (warp == kMmaWarp) {
+        // copies still in flight (an aborted run): wait for them, bounded
+        if (lane == 0)
+            for (int q = g > S ? g - S : 0; q < g; ++q) drain_wait(&sh.full[q % S], (uint32_t)((q / S) & 1));
+        __syncwarp();
+    } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc =
-                (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(N8 >> 3) << 17) | (4u << 24);
-            const uint32_t bp = b_plane_bytes(N8);
-            const uint64_t dbase = smem_desc(smem_u32(dsm), 128, kGrp);   // stage 0, plane 0, k-step 0
-            int g = 0, grp = 0;
+            // kind::f16: FP32 D, BF16 A and B, A MN-major (bit 15), B K-major
+            const uint32_t ibase = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(M >> 4) << 24);
+            const uint32_t dsm_a = smem_u32(dsm);
+            // descriptors are built once per item and stepped by adding
+            // 16-byte address units (shared addresses stay below 256 KiB, so
+            // the 14-bit start field never carries); stage and phase advance
+            // by counters
+            const uint64_t sstep = (uint64_t)(sb >> 4);
+            int st = 0, grp = 0, last_st = -1;
+            uint32_t ph = 0, last_ph = 0;
+            uint64_t soff = 0;
             bool ok = true;
+            TcItem nitm = blockIdx.x < n_items ? items[blockIdx.x] : TcItem{};
             for (int i = blockIdx.x; i < n_items && ok; i += gridDim.x) {
-                Seg s0, s1;
-                it.segs(i, s0, s1);
-                const int nch = s0.nch + s1.nch;
-                for (int c = 0; c < nch && ok; ++c, ++g) {
-                    const int buf = grp & 1;
-                    if (c % kDrain == 0 && grp >= 2) {
-                        ok = role_wait(&sh.acce[buf], (uint32_t)(((grp >> 1) - 1) & 1), abort);
+                const TcItem itm = nitm;
+                if (i + (int)gridDim.x < n_items) nitm = items[i + gridDim.x];   // one item ahead
+                const int rows8 = (itm.rows + 7) & ~7;
+                const int N = M > 64 ? (itm.rows + 15) & ~15 : rows8;
+                const uint32_t idesc = ibase | ((uint32_t)(N >> 3) << 17);
+                const int nch = itm.nkg / kGPC;
+                const uint32_t pstride = (uint32_t)(kGPC * rows8 * kKG * 2);   // bytes of one image plane
+                // A: plane p of K-groups 2 ks, 2 ks + 1 (boxes bb bytes apart,
+                // column groups 128 bytes apart, planes 128 G apart); B: plane
+                // p of the image (K-groups rows8 x 16 bytes apart, 8-row groups
+                // 128 apart, planes pstride apart)
+                const uint64_t adesc = smem_desc(dsm_a, bb, 128);
+                const uint64_t bdesc = smem_desc(dsm_a + (uint32_t)(kGPC * bb), rows8 * 16, 128);
+                const uint64_t ap = (uint64_t)(8 * G), aks = (uint64_t)((2 * bb) >> 4);
+                const uint64_t bp = (uint64_t)(pstride >> 4), bks = (uint64_t)(2 * rows8);
+                int cd = 0;                                    // chunk within the drain group
+                for (int c = 0; c < nch; ++c) {
+                    const int buf = grp % kAccBufs;
+                    if (cd == 0 && grp >= kAccBufs) {
+                        ok = role_wait(&sh.acce[buf], (uint32_t)((grp / kAccBufs - 1) & 1), abort);
                         if (!ok) break;
                     }
-                    const int st = g % kRingStages, use = g / kRingStages;
-                    ok = role_wait(&sh.full[st], (uint32_t)(use & 1), abort);
+                    ok = role_wait(&sh.full[st], ph, abort);
                     if (!ok) break;
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    // descriptors differ only in the start address (bits
-                    // 0-13, 16-byte units; shared addresses stay below 256 KiB
-                    // so adding an offset never carries out of the field)
-                    const uint64_t da = dbase + (uint64_t)((st * sb) >> 4);
-                    const uint64_t db = da + (uint64_t)(kChunkBytes >> 4);
-                    const uint32_t dm = tmem + (uint32_t)(256 * buf), dc = dm + kCorrCol;
+                    const uint32_t dm = tmem + (uint32_t)(128 * buf), dc = dm + 64;
+                    uint64_t a1 = adesc + soff, b1 = bdesc + soff;
 #pragma unroll
-                    for (int ks = 0; ks < kKC / 16; ++ks) {
-                        const uint64_t ko = (uint64_t)(ks * 256 >> 4);
-                        const uint32_t acc = (c % kDrain == 0 && ks == 0) ? 0u : 1u;
-                        const uint64_t a1 = da + ko, a2 = a1 + (kImg >> 4), a3 = a2 + (kImg >> 4);
-                        const uint64_t b1 = db + ko, b2 = b1 + (bp >> 4), b3 = b2 + (bp >> 4);
+                    for (int ks = 0; ks < kGPC / 2; ++ks) {
+                        const uint32_t acc = (cd == 0 && ks == 0) ? 0u : 1u;
+                        const uint64_t a2 = a1 + ap, a3 = a2 + ap, b2 = b1 + bp, b3 = b2 + bp;
                         mma_bf16(dm, a1, b1, idesc, acc);
                         mma_bf16(dc, a1, b2, idesc, acc);
                         mma_bf16(dc, a2, b1, idesc, 1u);
                         mma_bf16(dc, a1, b3, idesc, 1u);
                         mma_bf16(dc, a2, b2, idesc, 1u);
                         mma_bf16(dc, a3, b1, idesc, 1u);
+                        a1 += aks;
+                        b1 += bks;
                     }
                     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                      bar_addr(&sh.empty[st]))
                                  : "memory");
-                    if (c % kDrain == kDrain - 1 || c == nch - 1) {
+                    last_st = st;
+                    last_ph = ph;
+                    if (++cd == kDrain || c == nch - 1) {
                         asm volatile(
                             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                 bar_addr(&sh.accf[buf]))
                             : "memory");
                         ++grp;
+                        cd = 0;
+                    }
+                    soff += sstep;
+                    if (++st == S) {
+                        st = 0;
+                        ph ^= 1u;
+                        soff = 0;
                     }
                 }
             }
+            // MMAs still in flight (an aborted run): the last commit
+            if (last_st >= 0) drain_wait(&sh.empty[last_st], last_ph);
         }
         __syncwarp();
     } else {
         // ------------------------------------------------ drainers and epilogue
-        const int q = warp & 3;                       // lane quarter
-        const int row = 16 * q + lane;                 // accumulator row of this thread (lanes 0-15)
+        // lane quarter q holds D rows 32 q .. 32 q + 31 for M = 128, rows
+        // 16 q .. 16 q + 15 (in lanes 0-15) for M = 64; D row = column m
+        const int q = warp & 3;
+        const int m = M > 64 ? 32 * q + lane : (lane < 16 ? 16 * q + lane : nc);
+        const bool live = (M > 64 ? 32 * q : 16 * q) < nc;   // warp-uniform
         const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16);
-        const int nblk = N8 / 8;
         int grp = 0;
         bool ok = true;
+        TcItem nitm = blockIdx.x < n_items ? items[blockIdx.x] : TcItem{};
         for (int i = blockIdx.x; i < n_items && ok; i += gridDim.x) {
-            Seg s0, s1;
-            it.segs(i, s0, s1);
-            const int nch = s0.nch + s1.nch;
-            float racc[kMaxBlkAll][8];
+            const TcItem itm = nitm;
+            if (i + (int)gridDim.x < n_items) nitm = items[i + gridDim.x];   // one item ahead
+            const int rows8 = (itm.rows + 7) & ~7;
+            const int N = M > 64 ? (itm.rows + 15) & ~15 : rows8;
+            const int nch = itm.nkg / kGPC;
+            float racc[kMaxN];
 #pragma unroll
-            for (int b = 0; b < kMaxBlkAll; ++b)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) racc[b][j] = 0.0f;
+            for (int n = 0; n < kMaxN; ++n) racc[n] = 0.0f;
             const int ngr = (nch + kDrain - 1) / kDrain;
             for (int gg = 0; gg < ngr; ++gg, ++grp) {
-                const int buf = grp & 1;
-                ok = role_wait(&sh.accf[buf], (uint32_t)((grp >> 1) & 1), abort);
+                const int buf = grp % kAccBufs;
+                ok = role_wait(&sh.accf[buf], (uint32_t)((grp / kAccBufs) & 1), abort);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (live) {
 #pragma unroll
-                for (int b0 = 0; b0 < kMaxBlkAll; b0 += 3) {
-                    uint32_t r[3][16];
+                    for (int c16 = 0; c16 < kMaxN / 16; ++c16) {
+                        if (16 * c16 >= N) break;
+                        uint32_t r[32];
+                        const uint32_t ad = lane_addr + (uint32_t)(128 * buf + 16 * c16);
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                            "[%16];"
+                            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                              "=r"(r[14]), "=r"(r[15])
+                            : "r"(ad));
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                            "[%16];"
+                            : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                              "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                            : "r"(ad + 64));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int t = 0; t < 3; ++t) {
-                        const int b = b0 + t;
-                        if (b < nblk) {
-                            const uint32_t ad = lane_addr + (uint32_t)(256 * buf) + 8 * b;
-                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                         : "=r"(r[t][0]), "=r"(r[t][1]), "=r"(r[t][2]), "=r"(r[t][3]),
-                                           "=r"(r[t][4]), "=r"(r[t][5]), "=r"(r[t][6]), "=r"(r[t][7])
-                                         : "r"(ad));
-                            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                                         : "=r"(r[t][8]), "=r"(r[t][9]), "=r"(r[t][10]), "=r"(r[t][11]),
-                                           "=r"(r[t][12]), "=r"(r[t][13]), "=r"(r[t][14]), "=r"(r[t][15])
-                                         : "r"(ad + kCorrCol));
-                        }
+                        for (int j = 0; j < 16; ++j)
+                            racc[16 * c16 + j] += __uint_as_float(r[j]) + __uint_as_float(r[16 + j]);
                     }
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int t = 0; t < 3; ++t)
-                        if (b0 + t < nblk)
-#pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                racc[b0 + t][j] += __uint_as_float(r[t][j]) + __uint_as_float(r[t][8 + j]);
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 mbar_arrive(&sh.acce[buf]);
             }
-            // one outcome for all four drainer warps (they meet at the
-            // epilogue's named barrier below); a warp that gave up arrives
-            // here too, the others within their own bounded waits
+            // one outcome for all four drainer warps (named barrier 1)
             uint32_t all_ok;
             asm volatile(
                 "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
@@ -456,44 +524,22 @@ __global__ void __launch_bounds__(256, 1) tc_gemm_kernel(Items it, int nc, int N
                 : "memory");
             ok = all_ok != 0;
             if (!ok) break;
-            // epilogue of item i
-            if (it.rows) {
-                // through a shared-memory tile, so that rows are written
-                // (and xin / b read) coalesced; the four drainer warps meet
-                // at named barrier 1
-                const Tile t = it.op.tiles[it.op.torder[i]];
-                float* tile = reinterpret_cast<float*>(dsm + (size_t)kRingStages * sb);
-                const int ldt = N8 + 1;
-                if (lane < 16)
+            if (m < nc) {
+                if (rows_mode) {
 #pragma unroll
-                    for (int b = 0; b < kMaxBlkAll; ++b)
+                    for (int n = 0; n < kMaxN; ++n)
+                        if (n < itm.rows) epilogue_tc(out.epi, out.Y, out.ldy, itm.orow + n, m, racc[n]);
+                } else {
+                    const long long plane = (long long)out.G * out.nT * kKG;
+                    __nv_bfloat16* t0 = out.T + ((long long)(m >> 3) * out.nT + itm.orow) * kKG + (m & 7);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            if (b < nblk) tile[row * ldt + 8 * b + j] = racc[b][j];
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                for (int e = tid - 128; e < t.rows * nc; e += kDrainers) {
-                    const int r = e / nc, col = e - r * nc;
-                    epilogue_tc(epi, Y, ldy, t.r0 + r, col, tile[r * ldt + col]);
-                }
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-            } else if (lane < 16) {
-                {
-                    const GWork w = it.op.gwork[i];
-                    const Group gr = it.op.groups[w.g];
-                    if (row < w.rows) {
-                        // 8 columns of each plane per 16-byte store (rows of
-                        // N8 BF16 are 16-byte aligned)
-                        const long long base = (long long)(gr.toff + w.r0 + row) * N8;
-#pragma unroll
-                        for (int b = 0; b < kMaxBlkAll; ++b) {
-                            if (b >= nblk) continue;
-                            __align__(16) __nv_bfloat16 p1[8], p2[8], p3[8];
-#pragma unroll
-                            for (int j = 0; j < 8; ++j) split3(8 * b + j < nc ? racc[b][j] : 0.0f, p1[j], p2[j], p3[j]);
-                            *reinterpret_cast<uint4*>(Tout + base + 8 * b) = *reinterpret_cast<const uint4*>(p1);
-                            *reinterpret_cast<uint4*>(Tout + tplane_out + base + 8 * b) = *reinterpret_cast<const uint4*>(p2);
-                            *reinterpret_cast<uint4*>(Tout + 2 * tplane_out + base + 8 * b) =
-                                *reinterpret_cast<const uint4*>(p3);
+                    for (int n = 0; n < kMaxN; ++n) {
+                        if (n < itm.rows) {
+                            __nv_bfloat16 a, b, d;
+                            split3(racc[n], a, b, d);
+                            t0[n * kKG] = a;
+                            t0[plane + n * kKG] = b;
+                            t0[2 * plane + n * kKG] = d;
                         }
                     }
                 }
@@ -503,22 +549,41 @@ __global__ void __launch_bounds__(256, 1) tc_gemm_kernel(Items it, int nc, int N
     if (tid == 0 && *abort) atomicExch(&g_tc_timeout, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-// Chunk images and split vector planes of one product.
-struct TcArgs {
-    const unsigned char* img;
-    const long long* tile_near0;   // first chunk of every tile's dense panel
-    const long long* tile_far0;    // first chunk of every tile's U panel
-    const long long* item0;        // first chunk of every far-field item
-    const __nv_bfloat16* Xs;       // three planes of n x N8
-    __nv_bfloat16* Ts;             // three planes of sum_rank x N8
-    long long xplane, tplane;
-    int nc, N8;
-};
-
 inline size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        (void)cudaGetLastError();
+    });
+    RAD_REQUIRE(fn != nullptr, RAD_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    return fn;
+}
+
+// Tensor map over three group-major BF16 planes of `rows` rows and G column
+// groups, seen as 3-D: (rows x 8 elements of a column group, G groups, 3
+// planes), so that 8 consecutive rows of a group are one contiguous 128-byte
+// line of the box (one core matrix).  Box = 64 elements x G groups x 3
+// planes; rows past `rows` read as zeros.
+void encode_planes(CUtensorMap* tm, const __nv_bfloat16* base, long long rows, int G) {
+    const cuuint64_t dims[3] = {(cuuint64_t)rows * kKG, (cuuint64_t)G, 3};
+    const cuuint64_t strides[2] = {(cuuint64_t)rows * 16, (cuuint64_t)rows * 16 * G};
+    const cuuint32_t box[3] = {(cuuint32_t)(kKG * kKG), (cuuint32_t)G, 3};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = encode_fn()(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(base), dims,
+                                   strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    RAD_REQUIRE(r == CUDA_SUCCESS, RAD_ECUDA, "tensor map encoding failed");
+}
 
 }  // namespace
 
@@ -527,71 +592,123 @@ bool tc_supported(const rad_htree* h) { return h->compressed && !h->op_is_f64() 
 
 void tc_drop_images(rad_htree* h) {
     h->tc_img.release(nullptr);
-    h->tc_tile_near0.release(nullptr);
-    h->tc_tile_far0.release(nullptr);
-    h->tc_item0.release(nullptr);
+    h->tc_rows_items.release(nullptr);
+    h->tc_far_items.release(nullptr);
+    h->tc_kgs.release(nullptr);
+    h->tc_n_rows = h->tc_n_far = 0;
     h->tc_ready = false;
 }
 
-// The three BF16 chunk images of every panel (dense and U panels per tile,
-// V^T panels per far-field item), built once for the tensor-core path.
+// The K-groups and chunk images of every work item (row tiles and far-field
+// slices), built once for the tensor-core path.
 void tc_build_images(rad_htree* h, cudaStream_t s) {
     RAD_REQUIRE(tc_supported(h), RAD_EINVAL, "tensor-core products need an FP32 or BF16 operator");
     if (h->tc_ready) return;
-    std::vector<GWork> gw(h->n_gwork);
-    if (h->n_gwork > 0)
-        RAD_CUDA(cudaMemcpyAsync(gw.data(), h->d_gwork.p, sizeof(GWork) * gw.size(), cudaMemcpyDeviceToHost, s));
-    RAD_CUDA(cudaStreamSynchronize(s));
     const int nt = h->n_tiles;
-    std::vector<long long> near0(std::max(1, nt)), far0(std::max(1, nt)), item0(std::max<size_t>(1, gw.size()));
-    std::vector<PackJob> jn, jf;   // near pool jobs, factor pool jobs
-    long long cur = 0;
+    long long nx = 0, nf = 0;
     for (int t = 0; t < nt; ++t) {
         const Tile& tl = h->tiles_h[t];
-        near0[t] = cur;
-        for (int k0 = 0; k0 < tl.kn; k0 += kKC) jn.push_back(PackJob{tl.noff, tl.ld, tl.rows, k0, tl.kn, cur++});
-        far0[t] = cur;
-        for (int k0 = 0; k0 < tl.kf; k0 += kKC) jf.push_back(PackJob{tl.foff, tl.ld, tl.rows, k0, tl.kf, cur++});
+        nx = std::max<long long>(nx, (long long)tl.ixn + tl.kn);
+        nf = std::max<long long>(nf, (long long)tl.ixf + tl.kf);
+    }
+    std::vector<GWork> gw(h->n_gwork);
+    std::vector<int> xidx(std::max<long long>(nx, 1)), tidx(std::max<long long>(nf, 1));
+    if (h->n_gwork > 0)
+        RAD_CUDA(cudaMemcpyAsync(gw.data(), h->d_gwork.p, sizeof(GWork) * gw.size(), cudaMemcpyDeviceToHost, s));
+    if (nx > 0) RAD_CUDA(cudaMemcpyAsync(xidx.data(), h->d_xidx.p, sizeof(int) * nx, cudaMemcpyDeviceToHost, s));
+    if (nf > 0) RAD_CUDA(cudaMemcpyAsync(tidx.data(), h->d_tidx.p, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
+    RAD_CUDA(cudaStreamSynchronize(s));
+
+    std::vector<int> kgs;
+    std::vector<KgJob> jobs;
+    std::vector<TcItem> rows_items, far_items;
+    long long img = 0;
+    // one item: K-groups from `add` (which calls kg(src, off, ld, valid)),
+    // padded with empty K-groups to whole chunks
+    auto item = [&](int rows, int orow, auto&& add) {
+        TcItem it{img, (int)kgs.size(), 0, rows, orow, {0, 0}};
+        const int rows8 = (rows + 7) & ~7;
+        auto kg = [&](int src, long long off, int ld, int valid, int pool) {
+            const int slot = it.nkg % kGPC;
+            const long long dst = img + (long long)(it.nkg / kGPC) * chunk_img_bytes(rows8);
+            jobs.push_back(KgJob{off, dst, ld, rows, valid, slot, rows8, pool});
+            kgs.push_back(src);
+            ++it.nkg;
+        };
+        add(kg);
+        while (it.nkg % kGPC) kg(0, 0, 1, 0, 0);
+        img += (long long)(it.nkg / kGPC) * chunk_img_bytes(rows8);
+        return it;
+    };
+    // runs of consecutive source rows, cut into K-groups of at most 8
+    auto runs = [&](auto& kg, const int* idx, int K, long long base, int ld, int flag, int pool) {
+        for (int k = 0; k < K;) {
+            int len = 1;
+            while (k + len < K && len < kKG && idx[k + len] == idx[k] + len) ++len;
+            kg(idx[k] | flag, base + (long long)k * ld, ld, len, pool);
+            k += len;
+        }
+    };
+    for (int t = 0; t < nt; ++t) {
+        const Tile& tl = h->tiles_h[t];
+        rows_items.push_back(item(tl.rows, tl.r0, [&](auto& kg) {
+            runs(kg, xidx.data() + tl.ixn, tl.kn, tl.noff, tl.ld, 0, 0);
+            runs(kg, tidx.data() + tl.ixf, tl.kf, tl.foff, tl.ld, kTFlag, 1);
+        }));
     }
     for (size_t w = 0; w < gw.size(); ++w) {
         const Group& g = h->groups_h[gw[w].g];
-        item0[w] = cur;
-        for (int k0 = 0; k0 < g.n; k0 += kKC)
-            jf.push_back(PackJob{g.voff + gw[w].r0, g.ld, gw[w].rows, k0, g.n, cur++});
+        far_items.push_back(item(gw[w].rows, g.toff + gw[w].r0, [&](auto& kg) {
+            for (int k = 0; k < g.n; k += kKG)
+                kg(g.c0 + k, g.voff + gw[w].r0 + (long long)k * g.ld, g.ld, std::min(kKG, g.n - k), 1);
+        }));
     }
-    h->tc_img.alloc((size_t)std::max<long long>(cur, 1) * kChunkBytes, s);
-    h->tc_tile_near0.alloc(sizeof(long long) * near0.size(), s);
-    h->tc_tile_far0.alloc(sizeof(long long) * far0.size(), s);
-    h->tc_item0.alloc(sizeof(long long) * item0.size(), s);
-    RAD_CUDA(cudaMemcpyAsync(h->tc_tile_near0.p, near0.data(), sizeof(long long) * near0.size(), cudaMemcpyHostToDevice, s));
-    RAD_CUDA(cudaMemcpyAsync(h->tc_tile_far0.p, far0.data(), sizeof(long long) * far0.size(), cudaMemcpyHostToDevice, s));
-    RAD_CUDA(cudaMemcpyAsync(h->tc_item0.p, item0.data(), sizeof(long long) * item0.size(), cudaMemcpyHostToDevice, s));
-    Scratch ws(s);
-    for (int pass = 0; pass < 2; ++pass) {
-        const std::vector<PackJob>& jv = pass == 0 ? jn : jf;
-        if (jv.empty()) continue;
-        PackJob* d = ws.get_n<PackJob>(jv.size());
-        RAD_CUDA(cudaMemcpyAsync(d, jv.data(), sizeof(PackJob) * jv.size(), cudaMemcpyHostToDevice, s));
+    // heaviest first
+    auto heavy = [](const TcItem& a, const TcItem& b) {
+        return (long long)a.nkg * ((a.rows + 7) & ~7) > (long long)b.nkg * ((b.rows + 7) & ~7);
+    };
+    std::stable_sort(rows_items.begin(), rows_items.end(), heavy);
+    std::stable_sort(far_items.begin(), far_items.end(), heavy);
+
+    h->tc_img.alloc((size_t)std::max<long long>(img, 16), s);
+    h->tc_rows_items.alloc(sizeof(TcItem) * std::max<size_t>(1, rows_items.size()), s);
+    h->tc_far_items.alloc(sizeof(TcItem) * std::max<size_t>(1, far_items.size()), s);
+    h->tc_kgs.alloc(sizeof(int) * std::max<size_t>(4, kgs.size()), s);
+    if (!rows_items.empty())
+        RAD_CUDA(cudaMemcpyAsync(h->tc_rows_items.p, rows_items.data(), sizeof(TcItem) * rows_items.size(),
+                                 cudaMemcpyHostToDevice, s));
+    if (!far_items.empty())
+        RAD_CUDA(cudaMemcpyAsync(h->tc_far_items.p, far_items.data(), sizeof(TcItem) * far_items.size(),
+                                 cudaMemcpyHostToDevice, s));
+    if (!kgs.empty()) RAD_CUDA(cudaMemcpyAsync(h->tc_kgs.p, kgs.data(), sizeof(int) * kgs.size(), cudaMemcpyHostToDevice, s));
+    if (!jobs.empty()) {
+        Scratch ws(s);
+        KgJob* d = ws.get_n<KgJob>(jobs.size());
+        RAD_CUDA(cudaMemcpyAsync(d, jobs.data(), sizeof(KgJob) * jobs.size(), cudaMemcpyHostToDevice, s));
         ProfScope ps_("tc_pack", s);
-        if (pass == 0) {
-            tc_pack_kernel<float><<<(unsigned)jv.size(), 256, 0, s>>>(h->near_pool.as<float>(), d, h->tc_img.as<unsigned char>());
-        } else if (h->factor_dtype == RAD_F32) {
-            tc_pack_kernel<float><<<(unsigned)jv.size(), 256, 0, s>>>(h->far_pool.as<float>(), d, h->tc_img.as<unsigned char>());
-        } else {
-            tc_pack_kernel<__nv_bfloat16><<<(unsigned)jv.size(), 256, 0, s>>>(h->far_pool.as<__nv_bfloat16>(), d,
-                                                                               h->tc_img.as<unsigned char>());
-        }
+        if (h->factor_dtype == RAD_F32)
+            tc_pack_kernel<float><<<(unsigned)jobs.size(), 128, 0, s>>>(h->near_pool.as<float>(), h->far_pool.as<float>(),
+                                                                        d, h->tc_img.as<unsigned char>());
+        else
+            tc_pack_kernel<__nv_bfloat16><<<(unsigned)jobs.size(), 128, 0, s>>>(
+                h->near_pool.as<float>(), h->far_pool.as<__nv_bfloat16>(), d, h->tc_img.as<unsigned char>());
         RAD_CHECK_LAUNCH();
+        RAD_CUDA(cudaStreamSynchronize(s));   // the host job list goes out of scope
     }
-    RAD_CUDA(cudaStreamSynchronize(s));   // the host job lists go out of scope
+    h->tc_n_rows = (int)rows_items.size();
+    h->tc_n_far = (int)far_items.size();
+    h->tc_r8max = 8;
+    for (const auto* v : {&rows_items, &far_items})
+        for (const TcItem& it : *v) h->tc_r8max = std::max(h->tc_r8max, (it.rows + 7) & ~7);
     h->tc_ready = true;
 }
 
-// Workspace of one tensor-core product of up to kMaxN8 columns: the split
-// planes of X (n rows) and of T (sum_rank rows).
+// Workspace of one tensor-core product of up to 96 columns: the split
+// planes of X (n rows) and of T (sum_rank rows), G = ceil(columns / 8)
+// column groups each.
 size_t tc_workspace_bytes(const rad_htree* h, int nrhs) {
-    const int N8 = std::min(kMaxN8, (nrhs + 7) / 8 * 8);
-    return align256((size_t)3 * h->n * N8 * 2) + align256((size_t)3 * std::max(1, h->sum_rank) * N8 * 2) + 256;
+    const int G = (std::min(96, nrhs) + 7) / 8;
+    return align256((size_t)3 * h->n * G * kKG * 2) + align256((size_t)3 * std::max(1, h->sum_rank) * G * kKG * 2) + 256;
 }
 
 // Y = F X for nc <= 96 FP32 columns (rows of X at stride ldx), epilogue as
@@ -599,47 +716,47 @@ size_t tc_workspace_bytes(const rad_htree* h, int nrhs) {
 void tc_product(const rad_htree* h, const OpView& op, const float* X, int ldx, void* Y, int ldy, int nc,
                 const Epi& epi, void* ws, cudaStream_t s) {
     RAD_REQUIRE(h->tc_ready, RAD_EINVAL, "tensor-core images missing (select the path first)");
-    const int N8 = (nc + 7) / 8 * 8;
+    RAD_REQUIRE(nc >= 1 && nc <= 96, RAD_EINVAL, "tensor-core product: 1 to 96 columns per launch");
+    const int G = (nc + 7) / 8;
+    const int M = nc <= 64 ? 64 : 128;
     const int n = (int)h->n;
+    const long long nT = std::max(1, op.sum_rank);
     unsigned char* base = reinterpret_cast<unsigned char*>(align256(reinterpret_cast<uintptr_t>(ws)));
-    TcArgs ta;
-    ta.img = h->tc_img.as<unsigned char>();
-    ta.tile_near0 = h->tc_tile_near0.as<long long>();
-    ta.tile_far0 = h->tc_tile_far0.as<long long>();
-    ta.item0 = h->tc_item0.as<long long>();
-    ta.xplane = (long long)n * N8;
-    ta.tplane = (long long)std::max(1, h->sum_rank) * N8;
-    ta.Xs = reinterpret_cast<const __nv_bfloat16*>(base);
-    ta.Ts = reinterpret_cast<__nv_bfloat16*>(base + align256((size_t)3 * ta.xplane * 2));
-    ta.nc = nc;
-    ta.N8 = N8;
-    const size_t smem = (size_t)kRingStages * stage_bytes(N8) + (size_t)kTileRows * (N8 + 1) * 4;
+    __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(base);
+    __nv_bfloat16* Ts = reinterpret_cast<__nv_bfloat16*>(base + align256((size_t)3 * n * G * kKG * 2));
+    CUtensorMap tmx, tmt;
+    encode_planes(&tmx, Xs, n, G);
+    encode_planes(&tmt, Ts, nT, G);
     static std::once_flag configured;
     static int sms = 0;
     std::call_once(configured, [&] {
-        RAD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      kRingStages * stage_bytes(kMaxN8) + kTileRows * (kMaxN8 + 1) * 4));
+        RAD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
         int dev = 0;
         RAD_CUDA(cudaGetDevice(&dev));
         RAD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     });
+    const int r8max = h->tc_r8max;
+    const size_t smem = (size_t)ring_stages(G, r8max) * stage_bytes(G, r8max) + 1024;
     {
         ProfScope ps_("tc_split", s);
-        const long long tot = ta.xplane;
-        tc_split_rows_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 4096), 256, 0, s>>>(
-            X, ldx, n, nc, N8, const_cast<__nv_bfloat16*>(ta.Xs), ta.xplane);
+        const long long tot = (long long)G * n * kKG;
+        tc_split_rows_kernel<<<(unsigned)std::min<long long>((tot + 255) / 256, 4096), 256, 0, s>>>(X, ldx, n, nc, G, Xs);
     }
     RAD_CHECK_LAUNCH();
-    if (op.n_gwork > 0) {
-        Items it{false, op, ta.item0, nullptr, ta.img, ta.Xs, ta.Ts, ta.xplane, ta.tplane};
+    const unsigned char* img = h->tc_img.as<unsigned char>();
+    const int* kgs = h->tc_kgs.as<int>();
+    if (h->tc_n_far > 0) {
+        TcOut o{nullptr, 0, epi, Ts, G, nT};
         ProfScope ps_("hmm_far_vt", s);
-        tc_gemm_kernel<<<std::min(op.n_gwork, sms), 256, smem, s>>>(it, nc, N8, nullptr, 0, epi, ta.Ts, ta.tplane);
+        tc_gemm_kernel<<<std::min(h->tc_n_far, sms), kThreads, smem, s>>>(
+            tmx, tmt, h->tc_far_items.as<TcItem>(), h->tc_n_far, kgs, img, M, nc, r8max, 0, o);
         RAD_CHECK_LAUNCH();
     }
     {
-        Items it{true, op, ta.tile_near0, ta.tile_far0, ta.img, ta.Xs, ta.Ts, ta.xplane, ta.tplane};
+        TcOut o{Y, ldy, epi, nullptr, G, nT};
         ProfScope ps_("hmm_rows", s);
-        tc_gemm_kernel<<<std::min(op.n_tiles, sms), 256, smem, s>>>(it, nc, N8, Y, ldy, epi, nullptr, 0);
+        tc_gemm_kernel<<<std::min(h->tc_n_rows, sms), kThreads, smem, s>>>(
+            tmx, tmt, h->tc_rows_items.as<TcItem>(), h->tc_n_rows, kgs, img, M, nc, r8max, 1, o);
     }
     RAD_CHECK_LAUNCH();
 }
