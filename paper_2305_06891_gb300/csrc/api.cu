@@ -706,6 +706,7 @@ int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx, v
         RAD_REQUIRE(nrhs >= 1 && nrhs <= 4096, RAD_EINVAL, "nrhs must be in [1, 4096]");
         RAD_REQUIRE(ldx >= h->n && ldy >= h->n, RAD_EINVAL, "leading dimension smaller than n");
         cudaStream_t s = static_cast<cudaStream_t>(stream);
+        tc_prepare(h, (int)nrhs, s);
         if (is_device_ptr(x) && is_device_ptr(y) && product_via_graph(h, dtype, x, ldx, y, ldy, nrhs, s)) return;
         const int n = (int)h->n;
         const int nr = (int)nrhs;
@@ -761,6 +762,7 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
         const bool qdev = is_device_ptr(q);
         double* qd = qdev ? q : ws.get_n<double>((size_t)n * m);
         rad_solve_info local{};
+        tc_prepare(h, (int)m + 1, s);
         solve_flux(h, epsd, Td, ldTd, (int)m, sigma, p, qd, qdev ? ldq : n, &local, s);
         if (!qdev) {
             RAD_CUDA(cudaMemcpy2DAsync(q, 8 * ldq, qd, 8 * (size_t)n, 8 * (size_t)n, m, cudaMemcpyDeviceToHost, s));
@@ -801,6 +803,7 @@ int rad_solve_reflection(const rad_htree* h, const double* eps, const double* B,
         const bool ydev = is_device_ptr(Y);
         double* Yd = ydev ? Y : ws.get_n<double>((size_t)n * nrhs);
         rad_solve_info local{};
+        tc_prepare(h, (int)nrhs, s);
         solve_reflection(h, epsd, Bd, ldBd, (int)nrhs, p, Yd, ydev ? ldY : n, &local, s);
         if (!ydev) {
             RAD_CUDA(cudaMemcpy2DAsync(Y, 8 * ldY, Yd, 8 * (size_t)n, 8 * (size_t)n, nrhs, cudaMemcpyDeviceToHost, s));

@@ -261,9 +261,9 @@ int rad_htree_load(const void* buf, uint64_t bytes, const rad_tree_params* p, vo
         RAD_REQUIRE(r.left == 0, RAD_EINVAL, "checkpoint blob has trailing bytes");
         RAD_REQUIRE(h->perm.bytes == sizeof(int) * (size_t)h->n && h->geo.bytes == sizeof(double) * 7 * (size_t)h->n,
                     RAD_EINVAL, "checkpoint device arrays do not fit the facet count");
-        // derived data, rebuilt: the fused one-column units, the split images
+        // derived data, rebuilt: the fused one-column units now, the
+        // tensor-core images at the first many-column product
         if (h->compressed) hmv1_plan(h.get(), s);
-        if (h->mm_path == 1) tc_build_images(h.get(), s);
         RAD_CUDA(cudaStreamSynchronize(s));
         check_bounds_after_call();
         *out = h.release();

@@ -400,8 +400,9 @@ struct rad_htree {
     int grid_a1 = 0, grid_b1 = 0, grid_a2 = 0, grid_b2 = 0;
     int tuned = 0;
     // many-column product of FP32 vectors: 0 = CUDA-core register tiles,
-    // 1 = tensor cores (BF16 x 3 split); set by rad_htree_autotune or
-    // rad_htree_set_product_path
+    // 1 = tensor cores (BF16 x 3 split; the default for FP32 and BF16
+    // operators, images built at the first product of 5 or more columns);
+    // set by rad_htree_autotune or rad_htree_set_product_path
     int mm_path = 0;
     // tensor-core path: the BF16 chunk images of every work item, the work
     // items (row tiles, far-field slices; heaviest first) and their K-groups
@@ -409,6 +410,7 @@ struct rad_htree {
     rad::DevBuf tc_img, tc_rows_items, tc_far_items, tc_kgs;
     int tc_n_rows = 0, tc_n_far = 0, tc_r8max = 8;   // items; their largest row count rounded up to 8
     bool tc_ready = false;
+    std::mutex tc_mu;                                 // first-use build of the images
     // one-column product: 1 = the fused single launch (when the operator
     // allows it, hmv1_ok), 0 = the two launches (phase A, phase B); set by
     // rad_htree_autotune or rad_htree_set_one_column_path.  The fused
@@ -527,6 +529,7 @@ size_t apply_workspace_bytes(const rad_htree* h, int nrhs);
 // tcgemm.cu: tensor-core panel GEMMs (BF16 x 3 split, FP32 vectors)
 bool tc_supported(const rad_htree* h);
 void tc_build_images(rad_htree* h, cudaStream_t s);
+void tc_prepare(const rad_htree* h, int ncols, cudaStream_t s);
 void tc_drop_images(rad_htree* h);
 size_t tc_workspace_bytes(const rad_htree* h, int nrhs);
 void tc_product(const rad_htree* h, const OpView& op, const float* X, int ldx, void* Y, int ldy, int nc,

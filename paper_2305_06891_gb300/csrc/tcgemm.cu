@@ -130,33 +130,142 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16&
 }
 
 // ---------------------------------------------------------------- packing
-// One K-group of an item's panel: columns [0, valid) of the column-major
-// panel at pool + off (leading dimension ld, rows rows), into slot `slot`
-// of the chunk image at img + dst (rows padded to rows8).
-struct KgJob {
-    long long off, dst;
-    int ld, rows, valid, slot, rows8, pool;   // pool: 0 dense panels, 1 factor panels
+// K-groups of a tile's panel columns [0, K) with source rows idx[k]: column
+// k starts one when it starts a run of consecutive source rows or lies a
+// multiple of 8 columns into a run.  The warp walks 32 columns at a time
+// (in column order, so the K-groups of a tile do not depend on who builds
+// them) and calls f(k, idx[k], rank) for every start k, rank = number of
+// starts before it; returns the number of K-groups.
+template <class F>
+__device__ __forceinline__ int kgroup_scan(const int* __restrict__ idx, int K, F&& f) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int prev = 0, rs = 0, count = 0;     // last source row and run start of the previous window
+    for (int base = 0; base < K; base += 32) {
+        const int k = base + lane;
+        const bool valid = k < K;
+        const int v = valid ? idx[k] : 0;
+        int pv = __shfl_up_sync(full, v, 1);
+        if (lane == 0) pv = prev;
+        const bool brk = valid && (k == 0 || v != pv + 1);
+        int r = brk ? k : -1;            // run start: last break at or before k
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(full, r, o);
+            if (lane >= o) r = max(r, t);
+        }
+        r = max(r, rs);
+        const bool st = valid && ((k - r) & 7) == 0;
+        const unsigned m = __ballot_sync(full, st);
+        if (st) f(k, v, count + __popc(m & ((1u << lane) - 1u)));
+        count += __popc(m);
+        prev = __shfl_sync(full, v, 31);
+        rs = __shfl_sync(full, r, 31);
+    }
+    return count;
+}
+
+// K-groups of every row tile (dense panel, then U panel): one warp per tile
+__global__ void __launch_bounds__(256) tc_count_kernel(const Tile* __restrict__ tiles, int nt,
+                                                       const int* __restrict__ xidx, const int* __restrict__ tidx,
+                                                       int* __restrict__ cnt) {
+    const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (t >= nt) return;
+    const Tile tl = tiles[t];
+    auto none = [](int, int, int) {};
+    const int c = kgroup_scan(xidx + tl.ixn, tl.kn, none) + kgroup_scan(tidx + tl.ixf, tl.kf, none);
+    if ((threadIdx.x & 31) == 0) cnt[t] = c;
+}
+
+// An item of the image build: its chunk images from byte img, its K-groups
+// kgs[kg0 .. kg0 + nkg) of which the first nreal hold columns; panel
+// segment 0 (a tile's dense panel, len0 columns, near pool at base0) and
+// segment 1 (a tile's U panel or a far item's V^T slice, len1 columns,
+// factor pool at base1), leading dimension ld; c0: a far item's first
+// vector row.
+struct PackItem {
+    long long img, base0, base1;
+    int kg0, nkg, nreal, rows, ld, len0, len1, far, c0, pad;
 };
+
+// K-group rows (and their first panel column, kcol) of the row tiles (one
+// warp per tile) and of the far items (whose runs are their whole column
+// cluster), padded with empty K-groups to whole chunks
+__global__ void __launch_bounds__(256) tc_kgroups_kernel(const Tile* __restrict__ tiles, int nt,
+                                                         const int* __restrict__ xidx, const int* __restrict__ tidx,
+                                                         const PackItem* __restrict__ pk, int n_items,
+                                                         int* __restrict__ kgs, int* __restrict__ kcol) {
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= n_items) return;
+    const int lane = threadIdx.x & 31;
+    const PackItem it = pk[i];
+    int* kg = kgs + it.kg0;
+    int* kc = kcol + it.kg0;
+    if (i < nt) {
+        const Tile tl = tiles[i];
+        const int c0 = kgroup_scan(xidx + tl.ixn, tl.kn, [&](int k, int v, int r) {
+            kg[r] = v;
+            kc[r] = k;
+        });
+        kgroup_scan(tidx + tl.ixf, tl.kf, [&](int k, int v, int r) {
+            kg[c0 + r] = v | kTFlag;
+            kc[c0 + r] = k;
+        });
+    } else {
+        for (int j = lane; j < it.nreal; j += 32) {
+            kg[j] = it.c0 + kKG * j;
+            kc[j] = kKG * j;
+        }
+    }
+    for (int j = it.nreal + lane; j < it.nkg; j += 32) {
+        kg[j] = 0;
+        kc[j] = 0;
+    }
+}
+
+// The three BF16 chunk images of one item (one CTA per item): K-group j in
+// slot j % kGPC of chunk j / kGPC, [plane][slot][8-row group][8 rows][8
+// columns], rows padded to rows8 and columns past the K-group with zeros.
 template <class FS>
 __global__ void __launch_bounds__(256) tc_pack_kernel(const float* __restrict__ near_pool,
                                                       const FS* __restrict__ far_pool,
-                                                      const KgJob* __restrict__ jobs, unsigned char* __restrict__ img) {
-    const KgJob j = jobs[blockIdx.x];
-    __nv_bfloat16* c = reinterpret_cast<__nv_bfloat16*>(img + j.dst);
-    const long long pstride = (long long)kGPC * j.rows8 * kKG;    // elements of one plane of the chunk
-    for (int e = threadIdx.x; e < j.rows8 * kKG; e += blockDim.x) {
-        const int n = e % j.rows8, kk = e / j.rows8;
-        float x = 0.0f;
-        if (n < j.rows && kk < j.valid) {
-            const long long at = j.off + n + (long long)kk * j.ld;
-            x = j.pool ? (float)Store<FS>::get(far_pool[at]) : near_pool[at];
+                                                      const PackItem* __restrict__ pk, const int* __restrict__ kgs,
+                                                      const int* __restrict__ kcol, unsigned char* __restrict__ img) {
+    const PackItem it = pk[blockIdx.x];
+    const int rows8 = (it.rows + 7) & ~7;
+    const int cb = chunk_img_bytes(rows8);
+    const long long pstride = (long long)kGPC * rows8 * kKG;    // elements of one plane of a chunk
+    for (int j = 0; j < it.nkg; ++j) {
+        int valid = 0, col = 0;
+        bool seg1 = it.far != 0;
+        if (j < it.nreal) {
+            const int src = kgs[it.kg0 + j];
+            col = kcol[it.kg0 + j];
+            seg1 = it.far || (src & kTFlag);
+            int next = seg1 ? it.len1 : it.len0;
+            if (j + 1 < it.nreal) {
+                const bool s2 = it.far || (kgs[it.kg0 + j + 1] & kTFlag);
+                if (s2 == seg1) next = kcol[it.kg0 + j + 1];
+            }
+            valid = next - col;
         }
-        __nv_bfloat16 a, b, d;
-        split3(x, a, b, d);
-        const long long o = (long long)j.slot * j.rows8 * kKG + (n >> 3) * 64 + (n & 7) * 8 + kk;
-        c[o] = a;
-        c[pstride + o] = b;
-        c[2 * pstride + o] = d;
+        const long long base = (seg1 ? it.base1 : it.base0) + (long long)col * it.ld;
+        __nv_bfloat16* c =
+            reinterpret_cast<__nv_bfloat16*>(img + it.img + (long long)(j / kGPC) * cb) + (long long)(j % kGPC) * rows8 * kKG;
+        for (int e = threadIdx.x; e < rows8 * kKG; e += blockDim.x) {
+            const int n = e % rows8, kk = e / rows8;
+            float x = 0.0f;
+            if (n < it.rows && kk < valid) {
+                const long long at = base + n + (long long)kk * it.ld;
+                x = seg1 ? (float)Store<FS>::get(far_pool[at]) : near_pool[at];
+            }
+            __nv_bfloat16 a, b, d;
+            split3(x, a, b, d);
+            const int o = (n >> 3) * 64 + (n & 7) * 8 + kk;
+            c[o] = a;
+            c[pstride + o] = b;
+            c[2 * pstride + o] = d;
+        }
     }
 }
 
@@ -600,70 +709,51 @@ void tc_drop_images(rad_htree* h) {
 }
 
 // The K-groups and chunk images of every work item (row tiles and far-field
-// slices), built once for the tensor-core path.
+// slices) for the tensor-core path: the tiles' K-group counts on the device
+// (one read back), the layout on the host, K-groups and images on the device.
 void tc_build_images(rad_htree* h, cudaStream_t s) {
     RAD_REQUIRE(tc_supported(h), RAD_EINVAL, "tensor-core products need an FP32 or BF16 operator");
     if (h->tc_ready) return;
-    const int nt = h->n_tiles;
-    long long nx = 0, nf = 0;
-    for (int t = 0; t < nt; ++t) {
-        const Tile& tl = h->tiles_h[t];
-        nx = std::max<long long>(nx, (long long)tl.ixn + tl.kn);
-        nf = std::max<long long>(nf, (long long)tl.ixf + tl.kf);
+    const int nt = h->n_tiles, nw = h->n_gwork;
+    Scratch ws(s);
+    std::vector<int> cnt(std::max(1, nt));
+    std::vector<GWork> gw(nw);
+    {
+        int* d_cnt = ws.get_n<int>(std::max(1, nt));
+        if (nt > 0) {
+            tc_count_kernel<<<(unsigned)((nt + 7) / 8), 256, 0, s>>>(h->d_tiles.as<Tile>(), nt, h->d_xidx.as<int>(),
+                                                                     h->d_tidx.as<int>(), d_cnt);
+            RAD_CHECK_LAUNCH();
+            RAD_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int) * nt, cudaMemcpyDeviceToHost, s));
+        }
+        if (nw > 0) RAD_CUDA(cudaMemcpyAsync(gw.data(), h->d_gwork.p, sizeof(GWork) * nw, cudaMemcpyDeviceToHost, s));
+        RAD_CUDA(cudaStreamSynchronize(s));
     }
-    std::vector<GWork> gw(h->n_gwork);
-    std::vector<int> xidx(std::max<long long>(nx, 1)), tidx(std::max<long long>(nf, 1));
-    if (h->n_gwork > 0)
-        RAD_CUDA(cudaMemcpyAsync(gw.data(), h->d_gwork.p, sizeof(GWork) * gw.size(), cudaMemcpyDeviceToHost, s));
-    if (nx > 0) RAD_CUDA(cudaMemcpyAsync(xidx.data(), h->d_xidx.p, sizeof(int) * nx, cudaMemcpyDeviceToHost, s));
-    if (nf > 0) RAD_CUDA(cudaMemcpyAsync(tidx.data(), h->d_tidx.p, sizeof(int) * nf, cudaMemcpyDeviceToHost, s));
-    RAD_CUDA(cudaStreamSynchronize(s));
-
-    std::vector<int> kgs;
-    std::vector<KgJob> jobs;
+    std::vector<PackItem> pk;
+    pk.reserve((size_t)nt + nw);
     std::vector<TcItem> rows_items, far_items;
     long long img = 0;
-    // one item: K-groups from `add` (which calls kg(src, off, ld, valid)),
-    // padded with empty K-groups to whole chunks
-    auto item = [&](int rows, int orow, auto&& add) {
-        TcItem it{img, (int)kgs.size(), 0, rows, orow, {0, 0}};
-        const int rows8 = (rows + 7) & ~7;
-        auto kg = [&](int src, long long off, int ld, int valid, int pool) {
-            const int slot = it.nkg % kGPC;
-            const long long dst = img + (long long)(it.nkg / kGPC) * chunk_img_bytes(rows8);
-            jobs.push_back(KgJob{off, dst, ld, rows, valid, slot, rows8, pool});
-            kgs.push_back(src);
-            ++it.nkg;
-        };
-        add(kg);
-        while (it.nkg % kGPC) kg(0, 0, 1, 0, 0);
-        img += (long long)(it.nkg / kGPC) * chunk_img_bytes(rows8);
-        return it;
-    };
-    // runs of consecutive source rows, cut into K-groups of at most 8
-    auto runs = [&](auto& kg, const int* idx, int K, long long base, int ld, int flag, int pool) {
-        for (int k = 0; k < K;) {
-            int len = 1;
-            while (k + len < K && len < kKG && idx[k + len] == idx[k] + len) ++len;
-            kg(idx[k] | flag, base + (long long)k * ld, ld, len, pool);
-            k += len;
-        }
+    int kg = 0;
+    auto add = [&](PackItem p, int orow, std::vector<TcItem>& list) {
+        const int rows8 = (p.rows + 7) & ~7;
+        p.nkg = (p.nreal + kGPC - 1) / kGPC * kGPC;
+        p.kg0 = kg;
+        p.img = img;
+        pk.push_back(p);
+        list.push_back(TcItem{img, kg, p.nkg, p.rows, orow, {0, 0}});
+        kg += p.nkg;
+        img += (long long)(p.nkg / kGPC) * chunk_img_bytes(rows8);
     };
     for (int t = 0; t < nt; ++t) {
         const Tile& tl = h->tiles_h[t];
-        rows_items.push_back(item(tl.rows, tl.r0, [&](auto& kg) {
-            runs(kg, xidx.data() + tl.ixn, tl.kn, tl.noff, tl.ld, 0, 0);
-            runs(kg, tidx.data() + tl.ixf, tl.kf, tl.foff, tl.ld, kTFlag, 1);
-        }));
+        add(PackItem{0, tl.noff, tl.foff, 0, 0, cnt[t], tl.rows, tl.ld, tl.kn, tl.kf, 0, 0, 0}, tl.r0, rows_items);
     }
-    for (size_t w = 0; w < gw.size(); ++w) {
+    for (int w = 0; w < nw; ++w) {
         const Group& g = h->groups_h[gw[w].g];
-        far_items.push_back(item(gw[w].rows, g.toff + gw[w].r0, [&](auto& kg) {
-            for (int k = 0; k < g.n; k += kKG)
-                kg(g.c0 + k, g.voff + gw[w].r0 + (long long)k * g.ld, g.ld, std::min(kKG, g.n - k), 1);
-        }));
+        add(PackItem{0, 0, g.voff + gw[w].r0, 0, 0, (g.n + kKG - 1) / kKG, gw[w].rows, g.ld, 0, g.n, 1, g.c0, 0},
+            g.toff + gw[w].r0, far_items);
     }
-    // heaviest first
+    // the launch order: heaviest first
     auto heavy = [](const TcItem& a, const TcItem& b) {
         return (long long)a.nkg * ((a.rows + 7) & ~7) > (long long)b.nkg * ((b.rows + 7) & ~7);
     };
@@ -673,27 +763,32 @@ void tc_build_images(rad_htree* h, cudaStream_t s) {
     h->tc_img.alloc((size_t)std::max<long long>(img, 16), s);
     h->tc_rows_items.alloc(sizeof(TcItem) * std::max<size_t>(1, rows_items.size()), s);
     h->tc_far_items.alloc(sizeof(TcItem) * std::max<size_t>(1, far_items.size()), s);
-    h->tc_kgs.alloc(sizeof(int) * std::max<size_t>(4, kgs.size()), s);
+    h->tc_kgs.alloc(sizeof(int) * (size_t)std::max(kGPC, kg), s);
     if (!rows_items.empty())
         RAD_CUDA(cudaMemcpyAsync(h->tc_rows_items.p, rows_items.data(), sizeof(TcItem) * rows_items.size(),
                                  cudaMemcpyHostToDevice, s));
     if (!far_items.empty())
         RAD_CUDA(cudaMemcpyAsync(h->tc_far_items.p, far_items.data(), sizeof(TcItem) * far_items.size(),
                                  cudaMemcpyHostToDevice, s));
-    if (!kgs.empty()) RAD_CUDA(cudaMemcpyAsync(h->tc_kgs.p, kgs.data(), sizeof(int) * kgs.size(), cudaMemcpyHostToDevice, s));
-    if (!jobs.empty()) {
-        Scratch ws(s);
-        KgJob* d = ws.get_n<KgJob>(jobs.size());
-        RAD_CUDA(cudaMemcpyAsync(d, jobs.data(), sizeof(KgJob) * jobs.size(), cudaMemcpyHostToDevice, s));
+    if (!pk.empty()) {
+        PackItem* d_pk = ws.get_n<PackItem>(pk.size());
+        int* d_kcol = ws.get_n<int>((size_t)std::max(kGPC, kg));
+        RAD_CUDA(cudaMemcpyAsync(d_pk, pk.data(), sizeof(PackItem) * pk.size(), cudaMemcpyHostToDevice, s));
         ProfScope ps_("tc_pack", s);
-        if (h->factor_dtype == RAD_F32)
-            tc_pack_kernel<float><<<(unsigned)jobs.size(), 128, 0, s>>>(h->near_pool.as<float>(), h->far_pool.as<float>(),
-                                                                        d, h->tc_img.as<unsigned char>());
-        else
-            tc_pack_kernel<__nv_bfloat16><<<(unsigned)jobs.size(), 128, 0, s>>>(
-                h->near_pool.as<float>(), h->far_pool.as<__nv_bfloat16>(), d, h->tc_img.as<unsigned char>());
+        const int ni = (int)pk.size();
+        tc_kgroups_kernel<<<(unsigned)((ni + 7) / 8), 256, 0, s>>>(h->d_tiles.as<Tile>(), nt, h->d_xidx.as<int>(),
+                                                                   h->d_tidx.as<int>(), d_pk, ni,
+                                                                   h->tc_kgs.as<int>(), d_kcol);
         RAD_CHECK_LAUNCH();
-        RAD_CUDA(cudaStreamSynchronize(s));   // the host job list goes out of scope
+        if (h->factor_dtype == RAD_F32)
+            tc_pack_kernel<float><<<(unsigned)ni, 256, 0, s>>>(h->near_pool.as<float>(), h->far_pool.as<float>(), d_pk,
+                                                               h->tc_kgs.as<int>(), d_kcol, h->tc_img.as<unsigned char>());
+        else
+            tc_pack_kernel<__nv_bfloat16><<<(unsigned)ni, 256, 0, s>>>(h->near_pool.as<float>(),
+                                                                       h->far_pool.as<__nv_bfloat16>(), d_pk,
+                                                                       h->tc_kgs.as<int>(), d_kcol,
+                                                                       h->tc_img.as<unsigned char>());
+        RAD_CHECK_LAUNCH();
     }
     h->tc_n_rows = (int)rows_items.size();
     h->tc_n_far = (int)far_items.size();
@@ -701,6 +796,15 @@ void tc_build_images(rad_htree* h, cudaStream_t s) {
     for (const auto* v : {&rows_items, &far_items})
         for (const TcItem& it : *v) h->tc_r8max = std::max(h->tc_r8max, (it.rows + 7) & ~7);
     h->tc_ready = true;
+}
+
+// Builds the tensor-core images on first use: the product path is the
+// tensor cores and a product of ncols >= 5 columns is coming.
+void tc_prepare(const rad_htree* hc, int ncols, cudaStream_t s) {
+    rad_htree* h = const_cast<rad_htree*>(hc);
+    if (ncols < 5 || h->mm_path != 1 || h->tc_ready || !tc_supported(h)) return;
+    std::lock_guard<std::mutex> lk(h->tc_mu);
+    if (!h->tc_ready) tc_build_images(h, s);
 }
 
 // Workspace of one tensor-core product of up to 96 columns: the split
