@@ -290,15 +290,18 @@ int rad_htree_autotune(rad_htree* h, void* stream);
 
 /* Kernel family of the product with 5 or more FP32 columns (no counterpart
  * in the paper): 0 = CUDA-core register tiles (FP32 FFMA, the default),
- * 1 = tensor cores (tcgen05 kind::f16: every FP32 operand split into three
- * BF16 pieces carrying its 24 bits, six partial products per k-step, the
- * leading and the correction terms in two accumulators restarted every 32
- * panel columns and summed in FP32 registers, so results agree with path 0
- * to FP32 rounding).  Selecting path 1 builds the split panel images once
- * (1.5 times the FP32 operator's bytes; synchronous); path 0 releases them.
+ * 1 = tensor cores (tcgen05 kind::f16, computed transposed: the right-hand
+ * sides are the MMA's M, a row tile's rows its N; every FP32 operand split
+ * into three BF16 pieces carrying its 24 bits, six partial products per
+ * k-step, the leading and the correction terms in two accumulators
+ * restarted every 128 panel columns and summed in FP32 registers, so
+ * results agree with path 0 to FP32 rounding).  Selecting path 1 builds the
+ * split panel images once (about 1.5 times the FP32 operator's bytes, rows
+ * padded to 8 and runs of columns to 8; synchronous); path 0 releases them.
  * rad_htree_autotune picks the faster path for the handle's operator;
- * recompression resets it to 0.  RAD_EINVAL for another value, or for path 1
- * on an FP64 operator. */
+ * recompression resets it to 0; a loaded checkpoint keeps the path and
+ * rebuilds the images at its first product of 5 or more columns.
+ * RAD_EINVAL for another value, or for path 1 on an FP64 operator. */
 int rad_htree_set_product_path(rad_htree* h, int32_t path);
 
 /* Kernel family of the one-column product (§5.2, y = F x; no counterpart in

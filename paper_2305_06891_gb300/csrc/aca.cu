@@ -1221,6 +1221,7 @@ static void upload_operator(rad_htree* h, const HVec<IdxRun>& near_runs, const H
     const std::vector<int> forder = order_desc(fkey);
     h->n_tiles = (int)h->tiles_h.size();
     h->n_gwork = (int)gwork.size();
+    h->gwork_h = gwork;
     h->d_torder.alloc(sizeof(int) * std::max<size_t>(1, torder.size()), s);
     h->d_forder.alloc(sizeof(int) * std::max<size_t>(1, forder.size()), s);
     h2d(h->d_torder.as<int>(), torder, s);
@@ -1639,6 +1640,9 @@ void compress_t(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     h->far_u_entries = far_u;
     h->far_v_entries = far_v;
     h->far_entries = far_u + far_v;
+    // K-groups of the tensor-core path, counted now so that its images can be
+    // built at the first many-column product without another synchronisation
+    if (h->mm_path == 1) tc_count_async(h, s);
     hs_up.reset();
     HostScope hs_sync("host_compress_final_wait");
     RAD_CUDA(cudaStreamSynchronize(s));
@@ -1666,9 +1670,10 @@ void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     h->stream_rows = kStreamRows;
     h->grid_a1 = h->grid_b1 = h->grid_a2 = h->grid_b2 = 0;
     h->tuned = 0;
-    h->mm_path = p->near_dtype == RAD_F64 ? 0 : 1;   // tensor cores for FP32 / BF16 operators
+    h->mm_path = 0;   // CUDA-core tiles until rad_htree_autotune or rad_htree_set_product_path picks the tensor cores
     h->one_col_path = 1;
-    tc_drop_images(h);
+    tc_drop_images(h, s);
+    h->tc_cnt_h.clear();
     h->closed = 0;
     h->compressed = false;
     h->factor_dtype = p->factor_dtype;

@@ -941,7 +941,7 @@ int rad_htree_set_product_path(rad_htree* h, int32_t path) {
         if (path == 1) {
             tc_build_images(h, nullptr);
         } else {
-            tc_drop_images(h);
+            tc_drop_images(h, nullptr);
         }
         h->mm_path = path;
     });

@@ -1148,7 +1148,7 @@ struct Tuner {
                 }
             }
             h->mm_path = pick;
-            if (pick == 0) tc_drop_images(h);
+            if (pick == 0) tc_drop_images(h, s);
         }
         h->tuned = 1;
     }

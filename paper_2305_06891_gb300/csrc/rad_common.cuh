@@ -399,10 +399,11 @@ struct rad_htree {
     int stream_rows = rad::kStreamRows;
     int grid_a1 = 0, grid_b1 = 0, grid_a2 = 0, grid_b2 = 0;
     int tuned = 0;
-    // many-column product of FP32 vectors: 0 = CUDA-core register tiles,
-    // 1 = tensor cores (BF16 x 3 split; the default for FP32 and BF16
-    // operators, images built at the first product of 5 or more columns);
-    // set by rad_htree_autotune or rad_htree_set_product_path
+    // many-column product of FP32 vectors: 0 = CUDA-core register tiles
+    // (after rad_compress_aca), 1 = tensor cores (BF16 x 3 split; images
+    // built when the path is chosen, or at the first product of 5 or more
+    // columns after a checkpoint load); set by rad_htree_autotune or
+    // rad_htree_set_product_path
     int mm_path = 0;
     // tensor-core path: the BF16 chunk images of every work item, the work
     // items (row tiles, far-field slices; heaviest first) and their K-groups
@@ -411,6 +412,14 @@ struct rad_htree {
     int tc_n_rows = 0, tc_n_far = 0, tc_r8max = 8;   // items; their largest row count rounded up to 8
     bool tc_ready = false;
     std::mutex tc_mu;                                 // first-use build of the images
+    std::vector<int> tc_cnt_h;                        // K-groups per row tile, counted with the operator
+    // the last product's two tensor maps (X and T planes), reused while the
+    // workspace address and the column-group count stay the same
+    struct TcMaps {
+        const void* ws = nullptr;
+        int G = 0;
+        alignas(64) unsigned char map[2][128];
+    } tc_maps;
     // one-column product: 1 = the fused single launch (when the operator
     // allows it, hmv1_ok), 0 = the two launches (phase A, phase B); set by
     // rad_htree_autotune or rad_htree_set_one_column_path.  The fused
@@ -453,6 +462,7 @@ struct rad_htree {
     int pivoting = RAD_ACA_PARTIAL;
     std::vector<rad::Tile> tiles_h;
     std::vector<rad::Group> groups_h;
+    std::vector<rad::GWork> gwork_h;          // far-field items (launch order)
     rad::HVec<rad::Piece> near_pieces, far_pieces;     // per tile, in panel order
     rad::DevBuf near_pool, far_pool;
     rad::DevBuf far_pool_acc;          // FP32 factors kept for refinement
@@ -530,7 +540,8 @@ size_t apply_workspace_bytes(const rad_htree* h, int nrhs);
 bool tc_supported(const rad_htree* h);
 void tc_build_images(rad_htree* h, cudaStream_t s);
 void tc_prepare(const rad_htree* h, int ncols, cudaStream_t s);
-void tc_drop_images(rad_htree* h);
+void tc_count_async(rad_htree* h, cudaStream_t s);
+void tc_drop_images(rad_htree* h, cudaStream_t s);   // frees stream-ordered on s
 size_t tc_workspace_bytes(const rad_htree* h, int nrhs);
 void tc_product(const rad_htree* h, const OpView& op, const float* X, int ldx, void* Y, int ldy, int nc,
                 const Epi& epi, void* ws, cudaStream_t s);

@@ -56,6 +56,7 @@
 // and frees its tensor memory.
 
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 #include <algorithm>
 
@@ -188,13 +189,24 @@ struct PackItem {
     int kg0, nkg, nreal, rows, ld, len0, len1, far, c0, pad;
 };
 
+// What the pack needs of one K-group: its first panel element (pool
+// offset), the byte offset of its image slot, the panel's leading dimension
+// and rows, and its columns (valid, 0 for padding) and pool (seg: 0 dense
+// panels, 1 factor panels).
+struct KgDesc {
+    long long src, dst;
+    int ld, rows, valid, seg;
+};
+
 // K-group rows (and their first panel column, kcol) of the row tiles (one
 // warp per tile) and of the far items (whose runs are their whole column
-// cluster), padded with empty K-groups to whole chunks
+// cluster), padded with empty K-groups to whole chunks; then every K-group's
+// pack descriptor
 __global__ void __launch_bounds__(256) tc_kgroups_kernel(const Tile* __restrict__ tiles, int nt,
                                                          const int* __restrict__ xidx, const int* __restrict__ tidx,
                                                          const PackItem* __restrict__ pk, int n_items,
-                                                         int* __restrict__ kgs, int* __restrict__ kcol) {
+                                                         int* __restrict__ kgs, int* __restrict__ kcol,
+                                                         KgDesc* __restrict__ desc) {
     const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (i >= n_items) return;
     const int lane = threadIdx.x & 31;
@@ -221,50 +233,56 @@ __global__ void __launch_bounds__(256) tc_kgroups_kernel(const Tile* __restrict_
         kg[j] = 0;
         kc[j] = 0;
     }
+    __syncwarp();
+    // columns of K-group j: up to the next K-group of the same panel, or the
+    // panel's end
+    const int rows8 = (it.rows + 7) & ~7;
+    for (int j = lane; j < it.nkg; j += 32) {
+        KgDesc d{0, it.img + (long long)(j / kGPC) * chunk_img_bytes(rows8) + (long long)(j % kGPC) * rows8 * kKG * 2,
+                 it.ld, it.rows, 0, it.far};
+        if (j < it.nreal) {
+            const bool seg1 = it.far || (kg[j] & kTFlag);
+            int next = seg1 ? it.len1 : it.len0;
+            if (j + 1 < it.nreal && (it.far || (kg[j + 1] & kTFlag)) == seg1) next = kc[j + 1];
+            d.valid = next - kc[j];
+            d.seg = seg1 ? 1 : 0;
+            d.src = (seg1 ? it.base1 : it.base0) + (long long)kc[j] * it.ld;
+        }
+        desc[it.kg0 + j] = d;
+    }
 }
 
-// The three BF16 chunk images of one item (one CTA per item): K-group j in
-// slot j % kGPC of chunk j / kGPC, [plane][slot][8-row group][8 rows][8
-// columns], rows padded to rows8 and columns past the K-group with zeros.
+// The three BF16 images of every K-group (one warp per K-group): K-group j
+// of an item in slot j % kGPC of chunk j / kGPC, [plane][slot][8-row
+// group][8 rows][8 columns], rows padded to rows8 and columns past the
+// K-group with zeros.  Lane n splits row n's 8 columns (column reads
+// coalesced across the lanes) and stores each plane's 16 bytes at once.
 template <class FS>
 __global__ void __launch_bounds__(256) tc_pack_kernel(const float* __restrict__ near_pool,
                                                       const FS* __restrict__ far_pool,
-                                                      const PackItem* __restrict__ pk, const int* __restrict__ kgs,
-                                                      const int* __restrict__ kcol, unsigned char* __restrict__ img) {
-    const PackItem it = pk[blockIdx.x];
-    const int rows8 = (it.rows + 7) & ~7;
-    const int cb = chunk_img_bytes(rows8);
-    const long long pstride = (long long)kGPC * rows8 * kKG;    // elements of one plane of a chunk
-    for (int j = 0; j < it.nkg; ++j) {
-        int valid = 0, col = 0;
-        bool seg1 = it.far != 0;
-        if (j < it.nreal) {
-            const int src = kgs[it.kg0 + j];
-            col = kcol[it.kg0 + j];
-            seg1 = it.far || (src & kTFlag);
-            int next = seg1 ? it.len1 : it.len0;
-            if (j + 1 < it.nreal) {
-                const bool s2 = it.far || (kgs[it.kg0 + j + 1] & kTFlag);
-                if (s2 == seg1) next = kcol[it.kg0 + j + 1];
+                                                      const KgDesc* __restrict__ desc, int n_kg,
+                                                      unsigned char* __restrict__ img) {
+    const int lane = threadIdx.x & 31;
+    for (int q = blockIdx.x * 8 + (threadIdx.x >> 5); q < n_kg; q += gridDim.x * 8) {
+        const KgDesc d = desc[q];
+        const int rows8 = (d.rows + 7) & ~7;
+        const long long pstride = (long long)kGPC * rows8 * kKG;    // elements of one plane of a chunk
+        __nv_bfloat16* c = reinterpret_cast<__nv_bfloat16*>(img + d.dst);
+        for (int n = lane; n < rows8; n += 32) {
+            __align__(16) __nv_bfloat16 p1[kKG], p2[kKG], p3[kKG];
+#pragma unroll
+            for (int kk = 0; kk < kKG; ++kk) {
+                float x = 0.0f;
+                if (n < d.rows && kk < d.valid) {
+                    const long long at = d.src + n + (long long)kk * d.ld;
+                    x = d.seg ? (float)Store<FS>::get(far_pool[at]) : near_pool[at];
+                }
+                split3(x, p1[kk], p2[kk], p3[kk]);
             }
-            valid = next - col;
-        }
-        const long long base = (seg1 ? it.base1 : it.base0) + (long long)col * it.ld;
-        __nv_bfloat16* c =
-            reinterpret_cast<__nv_bfloat16*>(img + it.img + (long long)(j / kGPC) * cb) + (long long)(j % kGPC) * rows8 * kKG;
-        for (int e = threadIdx.x; e < rows8 * kKG; e += blockDim.x) {
-            const int n = e % rows8, kk = e / rows8;
-            float x = 0.0f;
-            if (n < it.rows && kk < valid) {
-                const long long at = base + n + (long long)kk * it.ld;
-                x = seg1 ? (float)Store<FS>::get(far_pool[at]) : near_pool[at];
-            }
-            __nv_bfloat16 a, b, d;
-            split3(x, a, b, d);
-            const int o = (n >> 3) * 64 + (n & 7) * 8 + kk;
-            c[o] = a;
-            c[pstride + o] = b;
-            c[2 * pstride + o] = d;
+            const int o = (n >> 3) * 64 + (n & 7) * 8;
+            *reinterpret_cast<uint4*>(c + o) = *reinterpret_cast<const uint4*>(p1);
+            *reinterpret_cast<uint4*>(c + pstride + o) = *reinterpret_cast<const uint4*>(p2);
+            *reinterpret_cast<uint4*>(c + 2 * pstride + o) = *reinterpret_cast<const uint4*>(p3);
         }
     }
 }
@@ -343,17 +361,6 @@ __device__ __forceinline__ void drain_wait(unsigned long long* b, uint32_t parit
     const uint32_t a = bar_addr(b);
     for (long it = 0; it < 4096; ++it)
         if (mbar_try_wait(a, parity)) return;
-}
-
-__device__ __forceinline__ void epilogue_tc(const Epi& epi, void* Y, int ldy, int row, int col, float acc) {
-    if (epi.mode == kStore) {
-        static_cast<float*>(Y)[(long long)row * ldy + col] = acc;
-    } else {
-        const double e = epi.eps[row];
-        double w = epi.xin[(long long)row * epi.ld64 + col] - (1.0 - e) * (double)acc;
-        if (epi.mode == kResid) w = epi.b[(long long)row * epi.ld64 + col] - w;
-        static_cast<double*>(Y)[(long long)row * ldy + col] = w;
-    }
 }
 
 // the box of vector rows row .. row + 7: inner coordinate 8 row (elements;
@@ -634,10 +641,38 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
             ok = all_ok != 0;
             if (!ok) break;
             if (m < nc) {
-                if (rows_mode) {
+                if (rows_mode && out.epi.mode == kStore) {
+                    float* Y = static_cast<float*>(out.Y) + (long long)itm.orow * out.ldy + m;
 #pragma unroll
                     for (int n = 0; n < kMaxN; ++n)
-                        if (n < itm.rows) epilogue_tc(out.epi, out.Y, out.ldy, itm.orow + n, m, racc[n]);
+                        if (n < itm.rows) Y[(long long)n * out.ldy] = racc[n];
+                } else if (rows_mode) {
+                    // FP64 epilogue (Eq. 11 products): the inputs of 16 rows are
+                    // loaded (read-only path) before any of their results is
+                    // stored, so the loads overlap instead of alternating with
+                    // the stores
+                    const Epi& e = out.epi;
+                    const bool resid = e.mode == kResid;
+#pragma unroll
+                    for (int n0 = 0; n0 < kMaxN; n0 += 16) {
+                        if (n0 >= itm.rows) break;
+                        double ev[16], xv[16], bv[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int row = itm.orow + n0 + j;
+                            const bool in = n0 + j < itm.rows;
+                            ev[j] = in ? __ldg(e.eps + row) : 0.0;
+                            xv[j] = in ? __ldg(e.xin + (long long)row * e.ld64 + m) : 0.0;
+                            bv[j] = in && resid ? __ldg(e.b + (long long)row * e.ld64 + m) : 0.0;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (n0 + j >= itm.rows) continue;
+                            double w = xv[j] - (1.0 - ev[j]) * (double)racc[n0 + j];
+                            if (resid) w = bv[j] - w;
+                            static_cast<double*>(out.Y)[(long long)(itm.orow + n0 + j) * out.ldy + m] = w;
+                        }
+                    }
                 } else {
                     const long long plane = (long long)out.G * out.nT * kKG;
                     __nv_bfloat16* t0 = out.T + ((long long)(m >> 3) * out.nT + itm.orow) * kKG + (m & 7);
@@ -699,11 +734,12 @@ void encode_planes(CUtensorMap* tm, const __nv_bfloat16* base, long long rows, i
 // ---------------------------------------------------------------- host side
 bool tc_supported(const rad_htree* h) { return h->compressed && !h->op_is_f64() && !h->from_dense; }
 
-void tc_drop_images(rad_htree* h) {
-    h->tc_img.release(nullptr);
-    h->tc_rows_items.release(nullptr);
-    h->tc_far_items.release(nullptr);
-    h->tc_kgs.release(nullptr);
+void tc_drop_images(rad_htree* h, cudaStream_t s) {
+    h->tc_maps.ws = nullptr;
+    h->tc_img.release(s);
+    h->tc_rows_items.release(s);
+    h->tc_far_items.release(s);
+    h->tc_kgs.release(s);
     h->tc_n_rows = h->tc_n_far = 0;
     h->tc_ready = false;
 }
@@ -714,21 +750,23 @@ void tc_drop_images(rad_htree* h) {
 void tc_build_images(rad_htree* h, cudaStream_t s) {
     RAD_REQUIRE(tc_supported(h), RAD_EINVAL, "tensor-core products need an FP32 or BF16 operator");
     if (h->tc_ready) return;
+    HostScope hs_("host_tc_build");
     const int nt = h->n_tiles, nw = h->n_gwork;
     Scratch ws(s);
-    std::vector<int> cnt(std::max(1, nt));
-    std::vector<GWork> gw(nw);
-    {
-        int* d_cnt = ws.get_n<int>(std::max(1, nt));
-        if (nt > 0) {
-            tc_count_kernel<<<(unsigned)((nt + 7) / 8), 256, 0, s>>>(h->d_tiles.as<Tile>(), nt, h->d_xidx.as<int>(),
-                                                                     h->d_tidx.as<int>(), d_cnt);
-            RAD_CHECK_LAUNCH();
-            RAD_CUDA(cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int) * nt, cudaMemcpyDeviceToHost, s));
-        }
-        if (nw > 0) RAD_CUDA(cudaMemcpyAsync(gw.data(), h->d_gwork.p, sizeof(GWork) * nw, cudaMemcpyDeviceToHost, s));
+    // per-tile K-group counts and the far items: kept with the operator by
+    // rad_compress_aca, else (a loaded checkpoint) read back here
+    if ((int)h->tc_cnt_h.size() != nt) {
+        tc_count_async(h, s);
         RAD_CUDA(cudaStreamSynchronize(s));
     }
+    if ((int)h->gwork_h.size() != nw) {
+        h->gwork_h.resize(nw);
+        if (nw > 0)
+            RAD_CUDA(cudaMemcpyAsync(h->gwork_h.data(), h->d_gwork.p, sizeof(GWork) * nw, cudaMemcpyDeviceToHost, s));
+        RAD_CUDA(cudaStreamSynchronize(s));
+    }
+    const std::vector<int>& cnt = h->tc_cnt_h;
+    const std::vector<GWork>& gw = h->gwork_h;
     std::vector<PackItem> pk;
     pk.reserve((size_t)nt + nw);
     std::vector<TcItem> rows_items, far_items;
@@ -773,22 +811,32 @@ void tc_build_images(rad_htree* h, cudaStream_t s) {
     if (!pk.empty()) {
         PackItem* d_pk = ws.get_n<PackItem>(pk.size());
         int* d_kcol = ws.get_n<int>((size_t)std::max(kGPC, kg));
+        KgDesc* d_desc = ws.get_n<KgDesc>((size_t)std::max(kGPC, kg));
         RAD_CUDA(cudaMemcpyAsync(d_pk, pk.data(), sizeof(PackItem) * pk.size(), cudaMemcpyHostToDevice, s));
         ProfScope ps_("tc_pack", s);
         const int ni = (int)pk.size();
         tc_kgroups_kernel<<<(unsigned)((ni + 7) / 8), 256, 0, s>>>(h->d_tiles.as<Tile>(), nt, h->d_xidx.as<int>(),
                                                                    h->d_tidx.as<int>(), d_pk, ni,
-                                                                   h->tc_kgs.as<int>(), d_kcol);
+                                                                   h->tc_kgs.as<int>(), d_kcol, d_desc);
         RAD_CHECK_LAUNCH();
-        if (h->factor_dtype == RAD_F32)
-            tc_pack_kernel<float><<<(unsigned)ni, 256, 0, s>>>(h->near_pool.as<float>(), h->far_pool.as<float>(), d_pk,
-                                                               h->tc_kgs.as<int>(), d_kcol, h->tc_img.as<unsigned char>());
-        else
-            tc_pack_kernel<__nv_bfloat16><<<(unsigned)ni, 256, 0, s>>>(h->near_pool.as<float>(),
-                                                                       h->far_pool.as<__nv_bfloat16>(), d_pk,
-                                                                       h->tc_kgs.as<int>(), d_kcol,
-                                                                       h->tc_img.as<unsigned char>());
-        RAD_CHECK_LAUNCH();
+        static int sms = 0;
+        static std::once_flag once;
+        std::call_once(once, [] {
+            int dev = 0;
+            RAD_CUDA(cudaGetDevice(&dev));
+            RAD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        });
+        const unsigned grid = (unsigned)std::min<long long>((kg + 7) / 8, 16ll * sms);
+        if (kg > 0) {
+            if (h->factor_dtype == RAD_F32)
+                tc_pack_kernel<float><<<grid, 256, 0, s>>>(h->near_pool.as<float>(), h->far_pool.as<float>(), d_desc,
+                                                           kg, h->tc_img.as<unsigned char>());
+            else
+                tc_pack_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(h->near_pool.as<float>(),
+                                                                   h->far_pool.as<__nv_bfloat16>(), d_desc, kg,
+                                                                   h->tc_img.as<unsigned char>());
+            RAD_CHECK_LAUNCH();
+        }
     }
     h->tc_n_rows = (int)rows_items.size();
     h->tc_n_far = (int)far_items.size();
@@ -796,6 +844,20 @@ void tc_build_images(rad_htree* h, cudaStream_t s) {
     for (const auto* v : {&rows_items, &far_items})
         for (const TcItem& it : *v) h->tc_r8max = std::max(h->tc_r8max, (it.rows + 7) & ~7);
     h->tc_ready = true;
+}
+
+// K-groups per row tile into h->tc_cnt_h (complete at the stream's next
+// synchronisation)
+void tc_count_async(rad_htree* h, cudaStream_t s) {
+    const int nt = h->n_tiles;
+    h->tc_cnt_h.assign(nt, 0);
+    if (nt == 0) return;
+    Scratch ws(s);
+    int* d_cnt = ws.get_n<int>(nt);
+    tc_count_kernel<<<(unsigned)((nt + 7) / 8), 256, 0, s>>>(h->d_tiles.as<Tile>(), nt, h->d_xidx.as<int>(),
+                                                             h->d_tidx.as<int>(), d_cnt);
+    RAD_CHECK_LAUNCH();
+    RAD_CUDA(cudaMemcpyAsync(h->tc_cnt_h.data(), d_cnt, sizeof(int) * nt, cudaMemcpyDeviceToHost, s));
 }
 
 // Builds the tensor-core images on first use: the product path is the
@@ -828,9 +890,25 @@ void tc_product(const rad_htree* h, const OpView& op, const float* X, int ldx, v
     unsigned char* base = reinterpret_cast<unsigned char*>(align256(reinterpret_cast<uintptr_t>(ws)));
     __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(base);
     __nv_bfloat16* Ts = reinterpret_cast<__nv_bfloat16*>(base + align256((size_t)3 * n * G * kKG * 2));
+    static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
     CUtensorMap tmx, tmt;
-    encode_planes(&tmx, Xs, n, G);
-    encode_planes(&tmt, Ts, nT, G);
+    {
+        // encoding is a driver call: reuse the last maps of this handle when
+        // the workspace and the column groups are the same
+        rad_htree* hm = const_cast<rad_htree*>(h);
+        std::lock_guard<std::mutex> lk(hm->tc_mu);
+        if (hm->tc_maps.ws != ws || hm->tc_maps.G != G) {
+            encode_planes(&tmx, Xs, n, G);
+            encode_planes(&tmt, Ts, nT, G);
+            std::memcpy(hm->tc_maps.map[0], &tmx, 128);
+            std::memcpy(hm->tc_maps.map[1], &tmt, 128);
+            hm->tc_maps.ws = ws;
+            hm->tc_maps.G = G;
+        } else {
+            std::memcpy(&tmx, hm->tc_maps.map[0], 128);
+            std::memcpy(&tmt, hm->tc_maps.map[1], 128);
+        }
+    }
     static std::once_flag configured;
     static int sms = 0;
     std::call_once(configured, [&] {
