@@ -151,6 +151,17 @@ def load_peaks():
         return 6800.0, 2070.0, "fallback"
 
 
+def load_bf16_peak():
+    """Dense BF16 tensor throughput (TFLOP/s) sustained over seconds: the
+    peak of a kernel timed inside a long step."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 1700.0, "fallback"
+
+
 def sm_count(dev=None) -> int:
     import torch
     return int(torch.cuda.get_device_properties(dev if dev is not None else 0).multi_processor_count)
@@ -425,10 +436,12 @@ def measure_extras(args, rad, torch, dev, cav, verts_d, flush, stream, e2e=True)
     return out
 
 
-# DRAM bytes (read + write) per launch of a workload's dominant kernel, from
-# the ncu capture summarised in profiles/ (kept only while the kernel is
-# unchanged since that capture).
-TRAFFIC = {("cylinder", "hmm_rows"): 282.92e6 + 3.33e6}
+# DRAM bytes (read + write) per launch of a workload's dominant kernel on a
+# product path (0 CUDA cores, 1 tensor cores), from the ncu capture
+# summarised in profiles/ (kept only while the kernel is unchanged since that
+# capture).
+TRAFFIC = {("cylinder", "hmm_rows", 1): 524.12e6 + 9.98e6,
+           ("cylinder", "hmm_far_vt", 1): 253.13e6 + 69.50e6}
 
 
 def roofline(prof: dict, st: dict, steps: int, nc: int, sms: int):
@@ -437,12 +450,23 @@ def roofline(prof: dict, st: dict, steps: int, nc: int, sms: int):
     if not prof:
         return None
     name, (cnt, ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    traffic = TRAFFIC.get((workload_key(), name)) if PRODUCT_PATH in (None, 0) else None
+    path = int(st.get("product_path", 0))
+    traffic = TRAFFIC.get((workload_key(), name, path))
     avg_s = ms / cnt * 1e-3
     fp32_peak = sms * FP32_LANES_PER_SM * 2 * smax * 1e6 / 1e12
     note = f"FP32 FFMA: {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x {smax:.0f} MHz (of derived)"
     base = {"kernel": name, "launches": cnt, "avg_ms": ms / cnt,
             "measured": f"CUDA events around every launch on its stream, profiled pass of {steps} steps"}
+    if name in ("hmm_rows", "hmm_far_vt") and path == 1:
+        # tensor cores: every FP32 operand in three BF16 pieces, six BF16
+        # partial products per FP32 multiply-add (padding not counted)
+        ents = st["near_entries"] + st["far_u_entries"] if name == "hmm_rows" else st["far_v_entries"]
+        flops = 6 * 2.0 * nc * ents
+        ach = flops / avg_s / 1e12
+        bf16, bsrc = load_bf16_peak()
+        return dict(base, bound="tensor", achieved=ach, peak=bf16, unit="TFLOP/s", frac=ach / bf16, traffic=traffic,
+                    peak_note=f"dense BF16, sustained (of {bsrc}); achieved counts the six BF16 partial products of "
+                              "the three-way split per FP32 multiply-add")
     if name == "hmm_rows":
         flops = 2.0 * nc * (st["near_entries"] + st["far_u_entries"])
         ach = flops / avg_s / 1e12

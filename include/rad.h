@@ -289,8 +289,9 @@ int rad_hmatvec(const rad_htree* h, int32_t dtype, const void* x, int64_t ldx,
 int rad_htree_autotune(rad_htree* h, void* stream);
 
 /* Kernel family of the product with 5 or more FP32 columns (no counterpart
- * in the paper): 0 = CUDA-core register tiles (FP32 FFMA, the default),
- * 1 = tensor cores (tcgen05 kind::f16, computed transposed: the right-hand
+ * in the paper): 0 = CUDA-core register tiles (FP32 FFMA; the default for
+ * FP64 operators), 1 = tensor cores (the default after rad_compress_aca for
+ * FP32 and BF16 operators; tcgen05 kind::f16, computed transposed: the right-hand
  * sides are the MMA's M, a row tile's rows its N; every FP32 operand split
  * into three BF16 pieces carrying its 24 bits, six partial products per
  * k-step, the leading and the correction terms in two accumulators
@@ -299,8 +300,11 @@ int rad_htree_autotune(rad_htree* h, void* stream);
  * split panel images once (about 1.5 times the FP32 operator's bytes, rows
  * padded to 8 and runs of columns to 8; synchronous); path 0 releases them.
  * rad_htree_autotune picks the faster path for the handle's operator;
- * recompression resets it to 0; a loaded checkpoint keeps the path and
- * rebuilds the images at its first product of 5 or more columns.
+ * recompression resets it to the default; a loaded checkpoint keeps the path and
+ * rebuilds the images at its first product of 5 or more columns.  After
+ * rad_compress_aca the images are built at the first rad_hmatvec,
+ * rad_solve_flux or rad_solve_reflection call with 5 or more columns (one
+ * synchronisation), never for one-column use.
  * RAD_EINVAL for another value, or for path 1 on an FP64 operator. */
 int rad_htree_set_product_path(rad_htree* h, int32_t path);
 

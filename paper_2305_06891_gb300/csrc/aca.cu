@@ -1670,7 +1670,7 @@ void compress(rad_htree* h, const rad_aca_params* p, cudaStream_t s) {
     h->stream_rows = kStreamRows;
     h->grid_a1 = h->grid_b1 = h->grid_a2 = h->grid_b2 = 0;
     h->tuned = 0;
-    h->mm_path = 0;   // CUDA-core tiles until rad_htree_autotune or rad_htree_set_product_path picks the tensor cores
+    h->mm_path = p->near_dtype == RAD_F64 ? 0 : 1;   // tensor cores for FP32 / BF16 operators
     h->one_col_path = 1;
     tc_drop_images(h, s);
     h->tc_cnt_h.clear();

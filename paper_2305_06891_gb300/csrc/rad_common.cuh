@@ -399,11 +399,11 @@ struct rad_htree {
     int stream_rows = rad::kStreamRows;
     int grid_a1 = 0, grid_b1 = 0, grid_a2 = 0, grid_b2 = 0;
     int tuned = 0;
-    // many-column product of FP32 vectors: 0 = CUDA-core register tiles
-    // (after rad_compress_aca), 1 = tensor cores (BF16 x 3 split; images
-    // built when the path is chosen, or at the first product of 5 or more
-    // columns after a checkpoint load); set by rad_htree_autotune or
-    // rad_htree_set_product_path
+    // many-column product of FP32 vectors: 0 = CUDA-core register tiles,
+    // 1 = tensor cores (BF16 x 3 split; the default after rad_compress_aca
+    // for FP32 and BF16 operators; images built at the first product of 5
+    // or more columns, never for one-column use); set by
+    // rad_htree_autotune or rad_htree_set_product_path
     int mm_path = 0;
     // tensor-core path: the BF16 chunk images of every work item, the work
     // items (row tiles, far-field slices; heaviest first) and their K-groups
