@@ -36,24 +36,31 @@
 //     Panel columns past a run's end are zero in the image, so the box's
 //     other rows (neighbouring vector rows, or the zeros the copy fills in
 //     past the last row or column group) add nothing;
-//   - the panels are split once, when the path is selected, into chunk
-//     images of 8 K-groups, [plane][K-group][8-row group][8 rows][8 columns]
-//     (K-major core matrices), rows padded with zeros to a multiple of 8; a
-//     chunk moves by one bulk copy.
+//   - the panels are split once per operator (at its first product of 5 or
+//     more columns, or when the path is selected) into chunk images of 8
+//     K-groups, [plane][K-group][8-row group][8 rows][8 columns] (K-major
+//     core matrices), rows padded with zeros to a multiple of 8; a chunk
+//     moves by one bulk copy.  The K-groups of a row tile are found by one
+//     warp walking its gather indices in column order, so the layout does
+//     not depend on who builds it.
 // Persistent, warp-specialised kernel (one CTA of 192 threads per SM, items
-// taken round-robin, heaviest first): lane 0 of warp 0 issues the copies of
-// every chunk (8 tensor copies and one bulk copy, completing on the stage's
-// "full" mbarrier) into a ring of shared-memory stages, with the K-group
-// rows of the next 32 to 64 chunks already in the warp's registers; lane 0 of warp 1
-// issues each chunk's 4 k-steps x 6 MMAs into one of four accumulator pairs
-// in tensor memory (so that it runs up to three drains ahead); warps 2-5 (tensor-memory lane quarters 2, 3, 0, 1) add
-// a pair into FP32 registers after every 2 chunks of an item and write the
-// item's rows at its end.  The roles hand over through mbarriers and never
-// wait for the whole CTA.  Every wait is bounded: after a bounded number of
-// tries a role raises an abort flag that the others see, the CTA records the
-// timeout in a device flag (checked by the host at its next
-// synchronisation), waits (bounded) for its own copies and MMAs in flight
-// and frees its tensor memory.
+// taken round-robin, heaviest first):
+//   - lane 0 of warp 0 issues the copies of every chunk (8 tensor copies and
+//     one bulk copy, completing on the stage's "full" mbarrier) into a ring
+//     of shared-memory stages, with the K-group rows of the next 32 to 64
+//     chunks already in the warp's registers;
+//   - lane 0 of warp 1 issues each chunk's 4 k-steps x 6 MMAs into one of
+//     four accumulator pairs in tensor memory (so that it runs up to three
+//     drains ahead), with descriptors stepped by additions;
+//   - warps 2-5 (tensor-memory lane quarters 2, 3, 0, 1) add a pair into
+//     FP32 registers after every 2 chunks of an item and write the item's
+//     rows at its end (the FP64 epilogue's inputs loaded 16 rows ahead of
+//     the stores).
+// The roles hand over through mbarriers and never wait for the whole CTA.
+// Every wait is bounded: after a bounded number of tries a role raises an
+// abort flag that the others see, the CTA records the timeout in a device
+// flag (checked by the host at its next synchronisation), waits (bounded)
+// for its own copies and MMAs in flight and frees its tensor memory.
 
 #include <cstdint>
 #include <cstring>
