@@ -259,23 +259,31 @@ __global__ void __launch_bounds__(256) tc_kgroups_kernel(const Tile* __restrict_
     }
 }
 
-// The three BF16 images of every K-group (one warp per K-group): K-group j
-// of an item in slot j % kGPC of chunk j / kGPC, [plane][slot][8-row
-// group][8 rows][8 columns], rows padded to rows8 and columns past the
-// K-group with zeros.  Lane n splits row n's 8 columns (column reads
-// coalesced across the lanes) and stores each plane's 16 bytes at once.
+// The three BF16 images of every chunk (one warp per chunk of kGPC
+// K-groups, which all belong to one item): K-group j of an item in slot
+// j % kGPC of chunk j / kGPC, [plane][slot][8-row group][8 rows][8
+// columns], rows padded to rows8 and columns past the K-group with zeros.
+// The chunk's descriptors are staged in shared memory; the lanes then take
+// its (K-group, row) pairs, each splitting the row's 8 columns (reads
+// coalesced across consecutive rows) and storing each plane's 16 bytes at
+// once.
 template <class FS>
 __global__ void __launch_bounds__(256) tc_pack_kernel(const float* __restrict__ near_pool,
                                                       const FS* __restrict__ far_pool,
                                                       const KgDesc* __restrict__ desc, int n_kg,
                                                       unsigned char* __restrict__ img) {
-    const int lane = threadIdx.x & 31;
-    for (int q = blockIdx.x * 8 + (threadIdx.x >> 5); q < n_kg; q += gridDim.x * 8) {
-        const KgDesc d = desc[q];
-        const int rows8 = (d.rows + 7) & ~7;
+    __shared__ KgDesc sd[8][kGPC];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nch = n_kg / kGPC;
+    for (int ch = blockIdx.x * 8 + w; ch < nch; ch += gridDim.x * 8) {
+        if (lane < kGPC) sd[w][lane] = desc[ch * kGPC + lane];
+        __syncwarp();
+        const int rows8 = (sd[w][0].rows + 7) & ~7;
         const long long pstride = (long long)kGPC * rows8 * kKG;    // elements of one plane of a chunk
-        __nv_bfloat16* c = reinterpret_cast<__nv_bfloat16*>(img + d.dst);
-        for (int n = lane; n < rows8; n += 32) {
+        for (int q = lane; q < kGPC * rows8; q += 32) {
+            const int j = q / rows8, n = q - j * rows8;
+            const KgDesc d = sd[w][j];
+            __nv_bfloat16* c = reinterpret_cast<__nv_bfloat16*>(img + d.dst);
             __align__(16) __nv_bfloat16 p1[kKG], p2[kKG], p3[kKG];
 #pragma unroll
             for (int kk = 0; kk < kKG; ++kk) {
@@ -291,6 +299,7 @@ __global__ void __launch_bounds__(256) tc_pack_kernel(const float* __restrict__ 
             *reinterpret_cast<uint4*>(c + pstride + o) = *reinterpret_cast<const uint4*>(p2);
             *reinterpret_cast<uint4*>(c + 2 * pstride + o) = *reinterpret_cast<const uint4*>(p3);
         }
+        __syncwarp();
     }
 }
 
@@ -833,7 +842,7 @@ void tc_build_images(rad_htree* h, cudaStream_t s) {
             RAD_CUDA(cudaGetDevice(&dev));
             RAD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         });
-        const unsigned grid = (unsigned)std::min<long long>((kg + 7) / 8, 16ll * sms);
+        const unsigned grid = (unsigned)std::min<long long>((kg / kGPC + 7) / 8, 16ll * sms);
         if (kg > 0) {
             if (h->factor_dtype == RAD_F32)
                 tc_pack_kernel<float><<<grid, 256, 0, s>>>(h->near_pool.as<float>(), h->far_pool.as<float>(), d_desc,
