@@ -304,7 +304,9 @@ int rad_htree_autotune(rad_htree* h, void* stream);
  * rebuilds the images at its first product of 5 or more columns.  After
  * rad_compress_aca the images are built at the first rad_hmatvec,
  * rad_solve_flux or rad_solve_reflection call with 5 or more columns (one
- * synchronisation), never for one-column use.
+ * synchronisation), never for one-column use; a call made while its
+ * stream is being captured into a graph does not build them and runs on
+ * the CUDA-core tiles.
  * RAD_EINVAL for another value, or for path 1 on an FP64 operator. */
 int rad_htree_set_product_path(rad_htree* h, int32_t path);
 

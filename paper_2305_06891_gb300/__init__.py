@@ -696,7 +696,8 @@ def rad_htree_close_cavity(h: HTree, stream=None) -> np.ndarray:
 
 
 def rad_htree_set_product_path(h: HTree, path: int) -> None:
-    """0: CUDA-core tiles, 1: tensor cores (BF16 x 3 split) for >= 5 FP32 columns."""
+    """0: CUDA-core tiles, 1: tensor cores (BF16 x 3 split; the default after
+    compression for FP32 / BF16 operators) for >= 5 FP32 columns."""
     _check(_lib.rad_htree_set_product_path(h.ptr, int(path)))
 
 

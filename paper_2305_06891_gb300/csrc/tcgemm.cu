@@ -877,10 +877,18 @@ void tc_count_async(rad_htree* h, cudaStream_t s) {
 }
 
 // Builds the tensor-core images on first use: the product path is the
-// tensor cores and a product of ncols >= 5 columns is coming.
+// tensor cores and a product of ncols >= 5 columns is coming.  The build
+// synchronises the stream, so it is skipped while the stream is being
+// captured into a graph (that product then runs on the CUDA-core tiles).
 void tc_prepare(const rad_htree* hc, int ncols, cudaStream_t s) {
     rad_htree* h = const_cast<rad_htree*>(hc);
     if (ncols < 5 || h->mm_path != 1 || h->tc_ready || !tc_supported(h)) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lk(h->tc_mu);
     if (!h->tc_ready) tc_build_images(h, s);
 }
