@@ -737,6 +737,10 @@ def config_dict(work=None):
          "accumulation": ("f64 (operator, Krylov, inner products)" if W["near"] == "f64" else
                           "f32 (operator), f64 (Krylov, inner products, residuals)"),
          "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+    tc = PRODUCT_PATH == 1 or (PRODUCT_PATH is None and W["near"] != "f64")
+    d["many_column_product"] = ("tensor cores (tcgen05): FP32 operands split into three BF16 pieces, six partial "
+                                "products, FP32 accumulation" if tc else
+                                f"CUDA-core tiles ({'FP64' if W['near'] == 'f64' else 'FP32'} FMA)")
     if work is not None and work.batch:
         d["cavities"] = len(work.counts)
         d["facets_total"] = work.n
