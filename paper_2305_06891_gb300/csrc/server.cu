@@ -167,6 +167,11 @@ struct rad_server {
                 h = nullptr;
                 rc = rad_build_htree(c.n, c.verts.data(), &p.tree, st, &h);
                 if (rc == RAD_OK) rc = rad_compress_aca(h, &p.aca, st);
+                // resident operators keep the CUDA-core tiles for many-field
+                // requests: the tensor-core images (about 1.5 times the
+                // operator) would grow a handle past the bytes its admission
+                // counted
+                if (rc == RAD_OK) rc = rad_htree_set_product_path(h, 0);
             }
             int64_t op_bytes = 0;
             if (r->builds && rc == RAD_OK) {
