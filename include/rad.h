@@ -356,7 +356,12 @@ int rad_solve_flux(const rad_htree* h, const double* eps, const double* T, int64
 
 /* -------------------------------------------------------------------------
  * rad_hmatvec_noalloc — the product of rad_hmatvec (same arguments, same
- * result) for callers that cannot let the library allocate device memory,
+ * result; with 5 or more columns on the tensor-core path, once the handle's
+ * tensor-core images exist — built by its first rad_hmatvec or solve with 5
+ * or more columns, or by rad_htree_set_product_path — before that it runs
+ * the CUDA-core tiles, which agree to FP32 rounding, since building the
+ * images would allocate) for callers that cannot let the library allocate
+ * device memory,
  * e.g. a serving engine that has already reserved the GPU's memory for its
  * own pool, or a latency-critical loop that must stay out of the allocator.
  * The paper has no counterpart; this is an interface convenience.
