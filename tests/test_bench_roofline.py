@@ -3,9 +3,6 @@ tensor-core product launches count the six BF16 partial products of the
 three-way split per FP32 multiply-add against the sustained BF16 peak, the
 CUDA-core tiles count FP32 FMAs against the derived FFMA peak, vector
 kernels are HBM bound.  Pure host arithmetic, checked on the CPU."""
-import json
-import os
-
 import pytest
 
 import bench
@@ -16,11 +13,6 @@ NC = 65
 SMS = 152
 
 
-def _peaks():
-    with open(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")) as f:
-        return json.load(f)
-
-
 def test_tensor_core_row_launch_counts_six_bf16_products_against_the_sustained_peak():
     st = dict(STATS, product_path=1)
     avg_ms = 0.172
@@ -28,7 +20,7 @@ def test_tensor_core_row_launch_counts_six_bf16_products_against_the_sustained_p
     flops = 6 * 2.0 * NC * (st["near_entries"] + st["far_u_entries"])
     assert r["kernel"] == "hmm_rows" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
     assert r["achieved"] == pytest.approx(flops / (avg_ms * 1e-3) / 1e12)
-    assert r["peak"] == pytest.approx(float(_peaks()["bf16_tflops_sustained"]))
+    assert r["peak"] == pytest.approx(bench.load_bf16_peak()[0])
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     # DRAM traffic of the tensor-core row launch from its capture
     assert r["traffic"] == bench.TRAFFIC[(bench.workload_key(), "hmm_rows", 1)]
@@ -45,7 +37,7 @@ def test_cuda_core_tiles_count_fp32_fmas_against_the_derived_peak():
     st = dict(STATS, product_path=0)
     avg_ms = 0.268
     r = bench.roofline({"hmm_rows": (60, 60 * avg_ms)}, st, 5, NC, SMS)
-    smax = float(_peaks().get("sm_max_mhz", 2070.0))
+    smax = bench.load_peaks()[1]
     assert r["bound"] == "alu"
     assert r["peak"] == pytest.approx(SMS * 128 * 2 * smax * 1e6 / 1e12)
     assert r["achieved"] == pytest.approx(2.0 * NC * (st["near_entries"] + st["far_u_entries"]) / (avg_ms * 1e-3) / 1e12)
@@ -56,4 +48,4 @@ def test_cuda_core_tiles_count_fp32_fmas_against_the_derived_peak():
 def test_vector_kernels_are_hbm_bound():
     r = bench.roofline({"gmres_cgs_update": (36, 5.0)}, dict(STATS, product_path=1), 1, NC, SMS)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
-    assert r["peak"] == pytest.approx(float(_peaks()["hbm_gbs"]))
+    assert r["peak"] == pytest.approx(bench.load_peaks()[0])
